@@ -1,0 +1,111 @@
+"""Closed forms and brute-force definitions used to pin the oracle (and, at full size, the GPU
+results). Nothing here calls the oracle or the CUDA path.
+
+* Kaufman's partition function of the m x n periodic square lattice (B. Kaufman, Phys. Rev. 76,
+  1232 (1949)), J = 1, h = 0.
+* The periodic chain in a field, from the 2 x 2 transfer matrix (Ising 1925).
+* Non-interacting spins in a field.
+* Run counting on a ring: the number of cyclic binary strings with U ones and 2r runs.
+* A pure-Python brute force (a second language), for graphs of up to ~14 spins.
+"""
+from __future__ import annotations
+
+import math
+from itertools import product
+
+
+def _log2cosh(x: float) -> float:
+    ax = abs(x)
+    return ax + math.log1p(math.exp(-2.0 * ax))
+
+
+def _log_abs_2sinh(x: float):
+    """(sign, log|2 sinh x|)."""
+    if x == 0.0:
+        return 0, -math.inf
+    ax = abs(x)
+    return (1 if x > 0 else -1), ax + math.log(-math.expm1(-2.0 * ax))
+
+
+def kaufman_logz(m: int, n: int, T: float, J: float = 1.0) -> float:
+    """ln Z of the m x n torus (J > 0, h = 0) by Kaufman's four-product formula:
+    Z = 1/2 (2 sinh 2K)^(mn/2) [P1 + P2 + P3 + P4], K = J/T, with
+    P1 = prod_r 2cosh(m g_(2r+1)/2), P2 = prod_r 2sinh(m g_(2r+1)/2),
+    P3 = prod_r 2cosh(m g_(2r)/2),   P4 = prod_r 2sinh(m g_(2r)/2),  r = 0..n-1,
+    cosh g_l = cosh 2K coth 2K - cos(pi l / n) for l >= 1 and g_0 = 2K + ln tanh K (signed)."""
+    K = J / T
+    c = math.cosh(2 * K) / math.tanh(2 * K)
+
+    def gamma(l: int) -> float:
+        if l == 0:
+            return 2 * K + math.log(math.tanh(K))
+        return math.acosh(c - math.cos(math.pi * l / n))
+
+    terms = []  # (sign, log|P|)
+    odd = [gamma(2 * r + 1) for r in range(n)]
+    even = [gamma(2 * r) for r in range(n)]
+    for gs in (odd, even):
+        terms.append((1, sum(_log2cosh(m * g / 2) for g in gs)))
+        sign, lg = 1, 0.0
+        for g in gs:
+            s, l = _log_abs_2sinh(m * g / 2)
+            sign *= s
+            lg += l
+        terms.append((sign, lg))
+    lmax = max(l for s, l in terms if s != 0)
+    tot = math.fsum(s * math.exp(l - lmax) for s, l in terms if s != 0)
+    return math.log(0.5) + (m * n / 2) * math.log(2 * math.sinh(2 * K)) + lmax + math.log(tot)
+
+
+def ring_logz(n: int, T: float, h: float = 0.0, J: float = 1.0) -> float:
+    """ln Z of the periodic chain of n spins: Z = l+^n + l-^n with
+    l+- = e^K cosh(h/T) +- sqrt(e^(2K) sinh^2(h/T) + e^(-2K)), K = J/T.
+    At h = 0 this is (2 cosh K)^n + (2 sinh K)^n."""
+    K, b = J / T, h / T
+    root = math.sqrt(math.exp(2 * K) * math.sinh(b) ** 2 + math.exp(-2 * K))
+    lp = math.exp(K) * math.cosh(b) + root
+    lm = math.exp(K) * math.cosh(b) - root
+    r = lm / lp
+    return n * math.log(lp) + math.log1p(r ** n) if r ** n > -1 else float("nan")
+
+
+def free_spins(n: int, T: float, h: float):
+    """(lnZ, <M>, chi) of n non-interacting spins: Z = (2 cosh(h/T))^n, <M> = n tanh(h/T),
+    chi = (n/T) sech^2(h/T)."""
+    b = h / T
+    return n * _log2cosh(b), n * math.tanh(b), n / T / math.cosh(b) ** 2
+
+
+def ring_joint_count(n: int, up: int, runs_pairs: int) -> int:
+    """Number of ring configurations (labelled sites) with `up` up spins and 2r runs, i.e. 2r
+    unsatisfied bonds: (n/r) C(up-1, r-1) C(n-up-1, r-1) for r >= 1; for r = 0 one all-up and
+    one all-down configuration."""
+    r = runs_pairs
+    if r == 0:
+        return 1 if up in (0, n) else 0
+    if up < r or n - up < r:
+        return 0
+    return n * math.comb(up - 1, r - 1) * math.comb(n - up - 1, r - 1) // r
+
+
+def brute_force_g(n: int, edges):
+    """g as a dict {(E, M): count}: every configuration, spins from bits (bit 1 = up), E = -sum
+    J s_i s_j over the listed edges (duplicates counted as listed, i.e. summed), M = sum s_i."""
+    out = {}
+    for bits in product((0, 1), repeat=n):
+        s = [1 if b else -1 for b in reversed(bits)]
+        E = -sum(J * s[i] * s[j] for i, j, J in edges)
+        M = sum(s)
+        out[(E, M)] = out.get((E, M), 0) + 1
+    return out
+
+
+def brute_force_g_range(n: int, edges, lo: int, hi: int):
+    """Like brute_force_g, over configuration words s in [lo, hi) only; spin i is bit i of s."""
+    out = {}
+    for s in range(lo, hi):
+        sp = [1 if (s >> i) & 1 else -1 for i in range(n)]
+        E = -sum(J * sp[i] * sp[j] for i, j, J in edges)
+        M = sum(sp)
+        out[(E, M)] = out.get((E, M), 0) + 1
+    return out

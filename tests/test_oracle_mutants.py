@@ -1,0 +1,101 @@
+"""Mutation tests: plant plausible mistakes in a copy of the oracle (on the CPU) and check that
+the pins fail for every one of them. The oracle itself is never modified."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1110_2561_gb300 import workloads as w
+from closed_forms import brute_force_g_range, free_spins, kaufman_logz, ring_logz
+
+# (name, original text, planted mistake); each original must occur exactly once.
+MUTANTS = [
+    ("edges: energy sign", "E -= bJ[b] * spin[bi[b]] * spin[bj[b]];", "E += bJ[b] * spin[bi[b]] * spin[bj[b]];"),
+    ("edges: last bond dropped", "for (int b = 0; b < nb; ++b) E -=", "for (int b = 0; b + 1 < nb; ++b) E -="),
+    ("edges: spin from wrong bit", "spin[i] = ((s >> i) & 1u) ? +1 : -1;", "spin[i] = ((s >> (n - 1 - i)) & 1u) ? +1 : -1;"),
+    ("edges: bins transposed", "g[e * (n + 1) + m] += 1;", "g[(n - m) * 0 + e * (n + 1) + (n - m) * ((e % 2) == 1) + m * ((e % 2) == 0)] += 1;"),
+    ("masks: NOT dropped", "uint64_t agree = ~(s ^ spread) & grp[t].mask;", "uint64_t agree = (s ^ spread) & grp[t].mask;"),
+    ("masks: both directions", "for (int j = k + 1; j < n; ++j) {\n            int64_t v = K[k * n + j];",
+     "for (int j = 0; j < n; ++j) {\n            int64_t v = K[k * n + j];"),
+    ("masks: M from down spins", "g[((E + S) / 2) * (n + 1) + up] += 1;", "g[((E + S) / 2) * (n + 1) + (n - up) * (E != 0) + up * (E == 0)] += 1;"),
+    ("frontier: energy sign", "dE -= Kuv * Su * Sv;", "dE += Kuv * Su * Sv;"),
+    ("frontier: up count lost", "t1[(a1 * ne1 + e + de) * nm1 + m + sv] += c;", "t1[(a1 * ne1 + e + de) * nm1 + m + (sv && (v & 1))] += c;"),
+    ("thermo: field sign", "long double H = E - f * M;\n                    long double w = expl(logl((long double)c) - H / t - Lmax);\n                    Z += w;",
+     "long double H = E + f * M;\n                    long double w = expl(logl((long double)c) - H / t - Lmax);\n                    Z += w;"),
+    ("thermo: C over T", "C[p] = (double)(vH / (t * t));", "C[p] = (double)(vH / t);"),
+    ("thermo: chi over T^2", "chi[p] = (double)(vM / t);", "chi[p] = (double)(vM / (t * t));"),
+    ("thermo: weights without g", "long double w = expl(logl((long double)c) - H / t - Lmax);\n                    Z += w;",
+     "long double w = expl(0.0L * logl((long double)c) - H / t - Lmax);\n                    Z += w;"),
+    ("thermo: variance not centred", "vH += w * (H - mH) * (H - mH);", "vH += w * H * H;"),
+    ("thermo: energy mean uses M", "Z += w; sH += w * H; sM += w * M;", "Z += w; sH += w * E; sM += w * M;"),
+]
+
+
+def table1(path_rows):
+    return {(E, M): nc for nc, M, E in path_rows}
+
+
+def pins_pass(lib, table1_triples) -> bool:
+    """A compact run of the pins; False as soon as one fails."""
+    try:
+        lat = w.square(4, 4, True)
+        want = table1(table1_triples)
+        for fn in (oracle.g_edges, oracle.g_masks, oracle.g_frontier):
+            g = fn(lat.n, lat.edges, lib=lib)
+            e_min, _, _ = oracle.bins(lat.n, lat.edges, lib=lib)
+            got = {(e_min + 2 * int(e), -lat.n + 2 * int(m)): int(g[e, m]) for e, m in zip(*np.nonzero(g))}
+            if got != want:
+                return False
+        # a free lattice (not in Table 1) through each method: ground states and binomial columns
+        fl = w.square(3, 4, False)
+        for fn in (oracle.g_edges, oracle.g_masks, oracle.g_frontier):
+            g = fn(fl.n, fl.edges, lib=lib)
+            if g[0, 0] != 1 or g[0, fl.n] != 1 or any(int(g[:, m].sum()) != math.comb(fl.n, m) for m in range(fl.n + 1)):
+                return False
+        # configuration ranges: which words a range holds (spin i is bit i)
+        rg = w.random_graph(9, 14, w.SplitMix64(11))
+        edges = [tuple(int(x) for x in r) for r in rg.edges]
+        want_r = brute_force_g_range(rg.n, edges, 37, 301)
+        for fn in (oracle.g_edges, oracle.g_masks):
+            g = fn(rg.n, rg.edges, 37, 301, lib=lib)
+            e_min, _, _ = oracle.bins(rg.n, rg.edges, lib=lib)
+            got = {(e_min + 2 * int(e), -rg.n + 2 * int(m)): int(g[e, m]) for e, m in zip(*np.nonzero(g))}
+            if got != want_r:
+                return False
+        # thermodynamics: Kaufman, ring in a field, free spins
+        e_min, _, _ = oracle.bins(lat.n, lat.edges, lib=lib)
+        g = oracle.g_edges(lat.n, lat.edges, lib=lib)
+        for t in (0.7, 2.2, 4.0):
+            if abs(oracle.thermo(lat.n, e_min, g, [t], [0.0], lib=lib)[0][0, 0] - kaufman_logz(4, 4, t)) > 1e-10:
+                return False
+        r = w.ring(7)
+        gr = oracle.g_edges(r.n, r.edges, lib=lib)
+        er, _, _ = oracle.bins(r.n, r.edges, lib=lib)
+        for t, f in ((0.9, 0.4), (2.0, -1.1)):
+            if abs(oracle.thermo(r.n, er, gr, [t], [f], lib=lib)[0][0, 0] - ring_logz(7, t, f)) > 1e-10:
+                return False
+        n = 5
+        g0 = oracle.g_edges(n, np.zeros((0, 3), dtype=np.int64), lib=lib)
+        for t, f in ((0.6, 0.8), (2.5, -0.3)):
+            lz, E, M, C, chi = (x[0, 0] for x in oracle.thermo(n, 0, g0, [t], [f], lib=lib))
+            l0, m0, x0 = free_spins(n, t, f)
+            if not (np.isclose(lz, l0, rtol=1e-12) and np.isclose(M, m0, rtol=1e-12) and np.isclose(chi, x0, rtol=1e-12)
+                    and np.isclose(E, -f * m0, rtol=1e-12) and np.isclose(C, f * f * x0 / t, rtol=1e-12)):
+                return False
+    except ValueError:
+        return False
+    return True
+
+
+def test_unmutated_copy_passes(tmp_path, table1_triples):
+    lib = oracle.load_variant(oracle.source(), str(tmp_path))
+    assert pins_pass(lib, table1_triples)
+
+
+@pytest.mark.parametrize("name,orig,bad", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, table1_triples, name, orig, bad):
+    src = oracle.source()
+    assert src.count(orig) == 1, f"mutation anchor for {name!r} not found exactly once"
+    lib = oracle.load_variant(src.replace(orig, bad), str(tmp_path))
+    assert not pins_pass(lib, table1_triples), f"planted mistake {name!r} passed every pin"

@@ -1,0 +1,253 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics (no GPU).
+
+Each pin is chosen so that a plausible slip in the oracle -- a dropped bond, a wrong sign on E
+or M, a transposed bin index, a wrong power of T -- fails at least one of them (the mutation
+tests in test_oracle_mutants.py check exactly that).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1110_2561_gb300 import workloads as w
+from closed_forms import (brute_force_g, brute_force_g_range, free_spins, kaufman_logz, ring_joint_count, ring_logz)
+
+
+def as_dict(g: np.ndarray, n: int, e_min: int):
+    out = {}
+    for e, m in zip(*np.nonzero(g)):
+        out[(e_min + 2 * int(e), -n + 2 * int(m))] = int(g[e, m])
+    return out
+
+
+# --------------------------------------------------------------------------- Table 1 (Sec. 4)
+@pytest.mark.parametrize("method", ["edges", "masks", "frontier"])
+def test_table1_4x4_periodic(table1_triples, method):
+    """Table 1: all 80 printed (Nc, M, E) cells of the 4x4 periodic ferromagnet, and nothing else."""
+    lat = w.square(4, 4, True)
+    g = {"edges": oracle.g_edges, "masks": oracle.g_masks, "frontier": oracle.g_frontier}[method](lat.n, lat.edges)
+    e_min, n_e, n_m = oracle.bins(lat.n, lat.edges)
+    assert (e_min, n_e, n_m) == (-32, 33, 17)
+    got = as_dict(g, lat.n, e_min)
+    want = {(E, M): nc for nc, M, E in table1_triples}
+    assert len(want) == 80
+    assert got == want
+    assert sum(want.values()) == 2 ** 16          # Sec. 4: 65536 configurations
+
+
+# --------------------------------------------------------------------------- invariants
+def graphs_small():
+    rng = w.SplitMix64(7)
+    out = [w.square(4, 4, False), w.square(3, 5, True), w.triangular(3, 4, True), w.cubic(2, 2, 3, False),
+           w.ring(9), w.ring(10, J=-1)]
+    for n, ne in [(1, 0), (2, 1), (5, 7), (8, 12), (11, 20), (13, 30)]:
+        out.append(w.random_graph(n, ne, rng))
+    out.append(w.with_random_couplings(w.square(3, 4, True), rng, (-2, -1, 1, 2)))
+    return out
+
+
+@pytest.mark.parametrize("lat", graphs_small(), ids=lambda l: l.name)
+def test_total_and_binomial_columns(lat):
+    """Sec. 4 / Sec. 2: sum of g is 2^N and, for fixed M, the sum over E is C(N, (N+M)/2)."""
+    g = oracle.g_masks(lat.n, lat.edges)
+    assert int(g.sum()) == 2 ** lat.n
+    for m in range(lat.n + 1):
+        assert int(g[:, m].sum()) == math.comb(lat.n, m)
+
+
+@pytest.mark.parametrize("lat", graphs_small(), ids=lambda l: l.name)
+def test_global_flip_symmetry(lat):
+    """Flipping every spin keeps E and negates M: g(E, M) = g(E, -M) for any couplings."""
+    g = oracle.g_masks(lat.n, lat.edges)
+    assert np.array_equal(g, g[:, ::-1])
+
+
+@pytest.mark.parametrize("lat", [w.square(4, 4, False), w.square(3, 3, False), w.square(4, 4, True),
+                                 w.cubic(2, 3, 2, False), w.triangular(3, 3, False), w.cubic(3, 3, 2, True)],
+                         ids=lambda l: l.name)
+def test_ferromagnet_ground_states(lat):
+    """A connected ferromagnet has exactly two ground states, all up and all down, at E = -sum J."""
+    g = oracle.g_masks(lat.n, lat.edges)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    assert e_min == -int(lat.edges[:, 2].sum())
+    assert g[0, 0] == 1 and g[0, lat.n] == 1 and int(g[0].sum()) == 2
+
+
+@pytest.mark.parametrize("lat", [w.square(4, 4, False), w.square(4, 6, True), w.cubic(2, 2, 4, True),
+                                 w.square(3, 4, False)], ids=lambda l: l.name)
+def test_bipartite_energy_mirror(lat):
+    """On a bipartite ferromagnet, flipping one sublattice negates E: the E-marginal is mirrored."""
+    g = oracle.g_masks(lat.n, lat.edges)
+    marg = g.sum(axis=1)
+    assert np.array_equal(marg, marg[::-1])
+
+
+def test_gauge_invariance_pm_j():
+    """+-J: flipping spin i together with the sign of every coupling at i maps configurations one
+    to one and keeps E, so the E-marginal is unchanged (M is not)."""
+    rng = w.SplitMix64(3)
+    lat = w.with_random_couplings(w.square(4, 4, True), rng, (-1, 1))
+    base = oracle.g_masks(lat.n, lat.edges).sum(axis=1)
+    for site in (0, 5, 15):
+        e = lat.edges.copy()
+        at = (e[:, 0] == site) | (e[:, 1] == site)
+        e[at, 2] *= -1
+        assert np.array_equal(oracle.g_masks(lat.n, e).sum(axis=1), base)
+
+
+@pytest.mark.parametrize("n", [3, 4, 7, 12, 15])
+def test_ring_run_counting(n):
+    """Periodic chain: a configuration with `up` up spins and 2r runs has 2r unsatisfied bonds,
+    so E = -n + 4r, and the count is (n/r) C(up-1, r-1) C(n-up-1, r-1)."""
+    lat = w.ring(n)
+    g = oracle.g_edges(lat.n, lat.edges)
+    e_min, n_e, _ = oracle.bins(lat.n, lat.edges)
+    want = np.zeros_like(g)
+    for up in range(n + 1):
+        for r in range(0, n // 2 + 1):
+            c = ring_joint_count(n, up, r)
+            if c:
+                want[(-n + 4 * r - e_min) // 2, up] += c
+    assert np.array_equal(g, want)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_second_language_brute_force(seed):
+    """Random multigraphs (duplicate edges, J in {-2,-1,1,2}, isolated spins) against a pure-Python
+    brute force of the definition."""
+    rng = w.SplitMix64(100 + seed)
+    n = 3 + rng.below(9)
+    lat = w.random_graph(n, rng.below(2 * n + 1), rng)
+    g = oracle.g_edges(lat.n, lat.edges)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    want = brute_force_g(lat.n, [tuple(int(x) for x in r) for r in lat.edges])
+    want = {k: v for k, v in want.items() if v}
+    assert as_dict(g, lat.n, e_min) == want
+
+
+@pytest.mark.parametrize("lat", graphs_small() + [w.square(4, 5, True), w.triangular(4, 4, True),
+                                                  w.square(5, 4, False)], ids=lambda l: l.name)
+def test_three_oracles_agree(lat):
+    """The bond loop, the popcount form and the frontier programme give the same table."""
+    g0 = oracle.g_edges(lat.n, lat.edges)
+    assert np.array_equal(g0, oracle.g_masks(lat.n, lat.edges, threads=3))
+    assert np.array_equal(g0, oracle.g_frontier(lat.n, lat.edges))
+
+
+def test_ranges_partition():
+    """g over all configurations is the sum of g over any partition of [0, 2^N) into ranges."""
+    lat = w.with_random_couplings(w.square(3, 5, True), w.SplitMix64(9), (-2, -1, 1, 2))
+    full = oracle.g_masks(lat.n, lat.edges)
+    cuts = [0, 1, 777, 4096, 20000, 2 ** 15]
+    parts = sum(oracle.g_edges(lat.n, lat.edges, a, b) for a, b in zip(cuts[:-1], cuts[1:]))
+    assert np.array_equal(parts, full)
+
+
+@pytest.mark.parametrize("lo,hi", [(0, 1), (5, 6), (37, 301), (1000, 4096), (3001, 3001)])
+def test_range_semantics(lo, hi):
+    """A range [lo, hi) holds exactly the configuration words lo..hi-1, spin i being bit i."""
+    rg = w.random_graph(12, 20, w.SplitMix64(11))
+    want = brute_force_g_range(rg.n, [tuple(int(x) for x in r) for r in rg.edges], lo, hi)
+    e_min, _, _ = oracle.bins(rg.n, rg.edges)
+    for fn in (oracle.g_edges, oracle.g_masks):
+        assert as_dict(fn(rg.n, rg.edges, lo, hi), rg.n, e_min) == want
+
+
+def test_duplicate_edges_are_summed():
+    """Listing a bond twice with J = 1 equals one bond with J = 2; opposite couplings cancel."""
+    two = oracle.g_masks(3, [(0, 1, 1), (1, 0, 1), (1, 2, 1)])
+    one = oracle.g_masks(3, [(0, 1, 2), (1, 2, 1)])
+    assert np.array_equal(two, one)
+    cancel = oracle.g_masks(3, [(0, 1, 2), (0, 1, -2), (1, 2, 1)])
+    assert np.array_equal(cancel, oracle.g_masks(3, [(1, 2, 1)]))
+
+
+def test_invalid_graphs_rejected():
+    with pytest.raises(ValueError):
+        oracle.g_edges(3, [(0, 0, 1)])
+    with pytest.raises(ValueError):
+        oracle.g_edges(3, [(0, 3, 1)])
+    with pytest.raises(ValueError):
+        oracle.g_edges(0, [])
+
+
+def test_frontier_large_lattices_invariants():
+    """The frontier programme reaches the 6x6 torus (2^36 configurations) exactly: total, binomial
+    columns, the flip and bipartite mirrors, the two ground states and Kaufman's Z."""
+    lat = w.square(6, 6, True)
+    g = oracle.g_frontier(lat.n, lat.edges, max_active=16)
+    assert int(g.sum()) == 2 ** 36
+    for m in range(37):
+        assert int(g[:, m].sum()) == math.comb(36, m)
+    assert np.array_equal(g, g[:, ::-1])
+    assert np.array_equal(g.sum(1), g.sum(1)[::-1])
+    assert g[0, 0] == 1 and g[0, 36] == 1 and g[0].sum() == 2
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    T = np.linspace(0.5, 5, 16)
+    lz = oracle.thermo(lat.n, e_min, g, T, [0.0])[0][:, 0]
+    for t, l in zip(T, lz):
+        assert abs(l - kaufman_logz(6, 6, t)) <= 1e-13 * abs(l)
+
+
+# --------------------------------------------------------------------------- thermodynamics
+@pytest.mark.parametrize("m,n", [(3, 3), (3, 4), (4, 4), (4, 5), (5, 3)])
+def test_thermo_kaufman(m, n):
+    """Eq. (2) from g on m x n tori against Kaufman's closed form at h = 0."""
+    lat = w.square(m, n, True)
+    g = oracle.g_masks(lat.n, lat.edges)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    T = np.linspace(0.5, 5, 25)
+    lz = oracle.thermo(lat.n, e_min, g, T, [0.0])[0][:, 0]
+    for t, l in zip(T, lz):
+        assert abs(l - kaufman_logz(m, n, t)) <= 1e-13 * abs(l)
+
+
+@pytest.mark.parametrize("n", [3, 8, 13])
+def test_thermo_ring_in_field(n):
+    """Periodic chain in a field against the 2 x 2 transfer matrix (covers the sign of h M)."""
+    lat = w.ring(n)
+    g = oracle.g_edges(lat.n, lat.edges)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    T = np.array([0.5, 1.0, 2.3, 5.0])
+    h = np.array([-1.5, -0.2, 0.0, 0.7, 2.0])
+    lz = oracle.thermo(lat.n, e_min, g, T, h)[0]
+    for a, t in enumerate(T):
+        for b, f in enumerate(h):
+            assert abs(lz[a, b] - ring_logz(n, t, f)) <= 1e-13 * max(1.0, abs(lz[a, b]))
+
+
+def test_thermo_free_spins():
+    """No bonds: Z = (2 cosh(h/T))^N, <M> = N tanh(h/T), chi = N/T sech^2(h/T), <H> = -h <M>,
+    C = h^2 chi / T."""
+    n = 7
+    g = oracle.g_edges(n, np.zeros((0, 3), dtype=np.int64))
+    T = np.array([0.4, 1.0, 3.0])
+    h = np.array([-2.0, 0.0, 0.5])
+    lz, E, M, C, chi = oracle.thermo(n, 0, g, T, h)
+    for a, t in enumerate(T):
+        for b, f in enumerate(h):
+            l0, m0, x0 = free_spins(n, t, f)
+            assert lz[a, b] == pytest.approx(l0, rel=1e-14, abs=1e-14)
+            assert M[a, b] == pytest.approx(m0, rel=1e-13, abs=1e-13)
+            assert chi[a, b] == pytest.approx(x0, rel=1e-13)
+            assert E[a, b] == pytest.approx(-f * m0, rel=1e-13, abs=1e-13)
+            assert C[a, b] == pytest.approx(f * f * x0 / t, rel=1e-12, abs=1e-14)
+
+
+def test_thermo_derivative_identities():
+    """<H> = T^2 d lnZ/dT, <M> = T d lnZ/dh, C = d<H>/dT, chi = d<M>/dh (central differences)."""
+    lat = w.with_random_couplings(w.triangular(3, 4, True), w.SplitMix64(5), (-2, -1, 1, 2))
+    g = oracle.g_masks(lat.n, lat.edges)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    d = 1e-4
+    for t, f in [(0.8, 0.3), (1.7, -0.9), (3.0, 0.0)]:
+        lz, E, M, C, chi = (x[0, 0] for x in oracle.thermo(lat.n, e_min, g, [t], [f]))
+        lzT = oracle.thermo(lat.n, e_min, g, [t - d, t + d], [f])
+        lzh = oracle.thermo(lat.n, e_min, g, [t], [f - d, f + d])
+        dT = (lzT[0][1, 0] - lzT[0][0, 0]) / (2 * d)
+        dh = (lzh[0][0, 1] - lzh[0][0, 0]) / (2 * d)
+        assert E == pytest.approx(t * t * dT, rel=1e-6, abs=1e-6)
+        assert M == pytest.approx(t * dh, rel=1e-6, abs=1e-6)
+        assert C == pytest.approx((lzT[1][1, 0] - lzT[1][0, 0]) / (2 * d), rel=1e-5, abs=1e-6)
+        assert chi == pytest.approx((lzh[2][0, 1] - lzh[2][0, 0]) / (2 * d), rel=1e-5, abs=1e-6)
