@@ -1,0 +1,341 @@
+"""Benchmark: spin configurations per second into the exact table g(E, M) on one GB300.
+
+Workload (one step): the 6x6 square torus with J = +1 on all 72 bonds (N = 36, 2^36
+configurations) enumerated into its int64 table g(E, M) by isg_enumerate, followed by isg_thermo
+on 256 temperatures in [0.5, 5] at h = 0 in FP64 (Eq. 2). Inputs are synthetic and seeded.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the launching
+stream, an L2 flush (a 256 MiB write) between steps outside the events, a barrier and
+synchronisation around the timed region, max over ranks. Under torchrun every rank runs the
+same workload on its own GPU (replicas; the method's shards need no exchange), so `value` is
+the configurations of all ranks per second of the slowest rank.
+
+`--impl reference` runs the CPU oracle (oracle/, plain C, all host cores) on a bounded sample of
+the same workload and reports the same metric, extrapolated from the sample to a full step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spin configs/sec into exact g(E,M) on 1 GB300, % INT roofline; batched vs plain"
+UNIT = "configs/s"
+WORKLOAD = ("6x6 square torus (periodic), J=+1 on 72 bonds, N=36, 2^36 configurations -> int64 g(E,M); "
+            "then FP64 thermodynamics on 256 T in [0.5,5] at h=0")
+T_GRID = np.linspace(0.5, 5.0, 256)
+H_GRID = np.array([0.0])
+SM_MAX_MHZ_FALLBACK = 2070.0
+# Algorithmic integer operations per configuration of the Gray-step method: one update of the
+# bin address and one counter increment.
+OPS_PER_CONFIG = 2
+# DRAM traffic of one enumeration launch on this workload from the committed ncu capture
+# (profiles/enumerate_kernel_torus6x6.md), valid only for the kernel sources it was taken on.
+TRAFFIC_BYTES = None
+TRAFFIC_SOURCES_SHA = None
+
+
+def kernel_sources_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("enum_core.cuh", "enumerate.cu"):
+        with open(os.path.join(ROOT, "paper_1110_2561_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------------------------ GPU (isg) arm
+def run_isg(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1110_2561_gb300 import isg, workloads
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    lat = workloads.square(6, 6, True)
+    n_configs = 1 << lat.n
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    shape = isg.table_shape(gh)
+    plan = isg.isg_debug_plan(gh)
+    stream = torch.cuda.current_stream()
+    g = torch.zeros(shape, dtype=torch.int64, device=dev)
+    outs = tuple(torch.empty((len(T_GRID), 1), dtype=torch.float64, device=dev) for _ in range(5))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    peaks = isg.isg_probe_peaks(stream)
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        isg.isg_enumerate(gh, g, stream)
+        if ev:
+            ev[1].record(stream)
+        isg.isg_thermo(g, gh, T_GRID, H_GRID, isg.ISG_FP64, stream, out=outs)
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # correctness of the last warm-up result (cheap invariants; parity lives in the tests)
+    gc = g.cpu().numpy()
+    assert int(gc.sum()) == n_configs and all(int(gc[:, m].sum()) == math.comb(lat.n, m) for m in range(lat.n + 1))
+
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    uuid = str(getattr(torch.cuda.get_device_properties(dev), "uuid", local))
+    gpu_id = uuid if uuid.startswith("GPU-") or uuid.isdigit() else "GPU-" + uuid
+    with ClockSampler(gpu_id) as clk:
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)                      # L2 flush between timed steps, outside the events
+            step(evs[k])
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(c) for a, b, c in evs]
+    enum_ms = [a.elapsed_time(b) for a, b, c in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # end to end through the public API with host buffers (copies inside the timed region)
+    e2e_steps = max(1, min(args.steps, 5))
+    h2d = plan["blob_bytes"] + T_GRID.nbytes + H_GRID.nbytes
+    d2h = int(np.prod(shape)) * 8 + 5 * len(T_GRID) * len(H_GRID) * 8
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        gh_host = isg.isg_enumerate(gh, None, stream)                       # host table: D2H inside
+        isg.isg_thermo(gh_host, gh, T_GRID, H_GRID, isg.ISG_FP64, stream)  # host g: H2D inside, host outputs
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    assert np.array_equal(gh_host, gc)
+
+    clocks = clk.summary()
+    if rank == 0:
+        ms_per_step = total_ms / args.steps
+        value = world * n_configs / (ms_per_step * 1e-3)
+        enum_s = statistics.mean(enum_ms) * 1e-3
+        sm_max = clocks.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or SM_MAX_MHZ_FALLBACK
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        alu_peak = sms * 4 * 32 * sm_max * 1e6                     # 4 schedulers x 32 lanes per SM per clock
+        achieved_ops = OPS_PER_CONFIG * n_configs / enum_s
+        traffic = TRAFFIC_BYTES if TRAFFIC_SOURCES_SHA == kernel_sources_sha() else None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": world, "seq_len": None,
+                       "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)",
+                       "plan": {k: plan[k] for k in ("q", "b", "tasks", "threads", "copies", "G", "n_e_compact")}},
+            "roofline": {"bound": "alu", "achieved": achieved_ops / 1e9, "peak": alu_peak / 1e9, "unit": "Gop/s",
+                         "frac": achieved_ops / alu_peak, "traffic": traffic,
+                         "kernel": "enumerate_kernel<6>", "ops_per_config": OPS_PER_CONFIG,
+                         "peak_source": f"{sms} SMs x 128 lanes/clk x {sm_max:.0f} MHz (unit counts and clock)"},
+            "roofline_smem_atomic": {"bound": "smem_atomic", "achieved": n_configs / enum_s / 1e9,
+                                     "peak": peaks["red_conflict_free"] / 1e9,
+                                     "peak_scattered": peaks["red_scattered"] / 1e9, "unit": "Gred/s",
+                                     "frac": n_configs / enum_s / peaks["red_conflict_free"],
+                                     "peak_source": "isg_probe_peaks (red.shared.add.u32, measured in this run)"},
+            "enumerate_ms": statistics.mean(enum_ms), "thermo_ms": statistics.mean(
+                [b.elapsed_time(c) for a, b, c in evs]),
+            "e2e": {"value": world * n_configs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+def oracle_step(lat, sample_configs: int, threads: int):
+    """One bounded step of the oracle: the first `sample_configs` configurations of the workload,
+    then the FP64 thermodynamics on the full grid from the (exact) table. Returns the seconds of
+    each part."""
+    import oracle
+    t0 = time.perf_counter()
+    g = oracle.g_masks(lat.n, lat.edges, 0, sample_configs, threads=threads)
+    t1 = time.perf_counter()
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    oracle.thermo(lat.n, e_min, g, T_GRID, H_GRID)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1
+
+
+def calibrate_sample(lat, threads: int, seconds: float) -> int:
+    import oracle
+    n = 1 << 20
+    while True:
+        t0 = time.perf_counter()
+        oracle.g_masks(lat.n, lat.edges, 0, n, threads=threads)
+        dt = time.perf_counter() - t0
+        if dt > 0.5 or n >= 1 << 34:
+            break
+        n <<= 1
+    target = int(n * seconds / max(dt, 1e-6))
+    return max(1 << 20, min(1 << lat.n, 1 << max(20, target.bit_length() - 1)))
+
+
+def cpu_baseline(seconds: float):
+    from paper_1110_2561_gb300 import workloads
+    lat = workloads.square(6, 6, True)
+    threads = os.cpu_count() or 1
+    sample = calibrate_sample(lat, threads, seconds)
+    t_enum, t_thermo = oracle_step(lat, sample, threads)
+    full_step = t_enum * ((1 << lat.n) / sample) + t_thermo
+    return {"value": (1 << lat.n) / full_step, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {sample} of 2^36 configurations ({t_enum:.2f} s, O1 popcount oracle, {threads} OpenMP "
+                      f"threads) plus the full FP64 thermodynamics ({t_thermo:.3f} s); rate extrapolated to a full step"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1110_2561_gb300 import workloads
+    import oracle
+    oracle.build()
+    lat = workloads.square(6, 6, True)
+    threads = os.cpu_count() or 1
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    sample = calibrate_sample(lat, threads, per_step)
+    for _ in range(args.warmup):
+        oracle_step(lat, sample, threads)
+    ext = []
+    for _ in range(args.steps):
+        t_enum, t_thermo = oracle_step(lat, sample, threads)
+        ext.append(t_enum * ((1 << lat.n) / sample) + t_thermo)
+    ms_per_step = 1e3 * statistics.mean(ext)
+    value = (1 << lat.n) / (ms_per_step * 1e-3)
+    desc = (f"each step: first {sample} of 2^36 configurations (O1 popcount oracle, {threads} OpenMP threads) plus "
+            f"the full FP64 thermodynamics, extrapolated to a full step")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "global_batch": 1, "seq_len": None, "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("isg", "reference"), default="isg")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target seconds of the oracle sample")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "isg":
+        ap.error("at least 3 warm-up steps")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_isg(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,149 @@
+/*
+ * isg.h -- C ABI of libisg: exact degeneracy table g(E,M) of finite Ising systems on GB300.
+ *
+ * Method: Peretyatko, Bogatyrev, Kapitan, Kirienko, Nefedev, Belokon, "Rigorous Calculation of
+ * the Partition Function for the Finite Number of Ising Spins" (arXiv:1110.2561).
+ *
+ * Conventions shared by every call (Sec. 2, Eq. 1 and Eq. 2 of the paper):
+ *  - A graph has N spins (1 <= N <= 64) and bonds (i, j, J_ij) with integer J_ij of either sign
+ *    (Sec. 2: J "could be sign-changing"). Bonds listed more than once are summed; a pair whose
+ *    summed coupling is 0 carries no bond.
+ *  - Configuration word s: spin i is up (S_i = +1) when bit i of s is 1, down otherwise (Sec. 3a).
+ *  - E(s) = -sum over bonds of J_ij S_i S_j: Eq. (1) without the field term, each bond once.
+ *  - M(s) = sum_i S_i, the spin excess (Sec. 2, Sec. 3a).
+ *  - g(E, M) = number of configurations with that E and M (Sec. 2); the full table sums to 2^N
+ *    and its column at fixed M sums to C(N, (N+M)/2) (Sec. 2, Sec. 4).
+ *  - Table layout: int64, E-major, n_e x n_m. With S = sum over bonds of |J|:
+ *    bin (e, m) holds E = e_min + 2e and M = -N + 2m, e_min = -S, n_e = S + 1, n_m = N + 1.
+ *  - Thermodynamics: H = E - h M (Eq. 1), Z = sum over configurations of exp(-H/T) (Eq. 2),
+ *    k_B = 1. Reported per system: ln Z, <E> := <H>, <M>, C = Var(H)/T^2, chi = Var(M)/T.
+ *
+ * General rules:
+ *  - No call throws; every call returns an isg_status, and isg_last_error() returns a message
+ *    for the last failing call on the calling thread.
+ *  - The caller owns every buffer it passes; the library owns isg_graph and isg_server handles.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = the legacy default stream). Calls that
+ *    read or write host buffers synchronise that stream before returning; calls whose buffers
+ *    are all on the device only enqueue work on it.
+ *  - Device pointers must belong to the current CUDA device; the library works on the device
+ *    that is current when the call is made.
+ */
+#ifndef ISG_H
+#define ISG_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ISG_API __attribute__((visibility("default")))
+#else
+#define ISG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ISG_OK = 0,
+    ISG_ERR_INVALID = 1,    /* bad argument: graph, range, options or pointer */
+    ISG_ERR_TOO_LARGE = 2,  /* N or the table exceeds a limit */
+    ISG_ERR_NOMEM = 3,      /* host or device allocation failed */
+    ISG_ERR_CUDA = 4,       /* a CUDA runtime call failed (message in isg_last_error) */
+    ISG_ERR_TIMEOUT = 5,    /* a bounded device-side wait ran out */
+    ISG_ERR_BUSY = 6,       /* server queue full */
+    ISG_ERR_NOT_READY = 7,  /* server result not finished yet */
+    ISG_ERR_INTERNAL = 8    /* a kernel self-check failed (bug): the result is not valid */
+} isg_status;
+
+typedef struct isg_graph isg_graph;
+
+/* Thermodynamics precision (isg_thermo). */
+#define ISG_FP64 0
+#define ISG_FP32 1
+
+/*
+ * Enumeration options. Initialise with isg_options_init and change fields; every zero field
+ * means "planner's choice". Results never depend on the planning fields (only on the graph and
+ * the shard range); they exist for tuning and for tests that force every code path.
+ */
+typedef struct {
+    int32_t struct_size;     /* sizeof(isg_options); set by isg_options_init */
+    int32_t max_spins;       /* isg_enumerate refuses N > max_spins (default 40; at most 62) */
+    int32_t inner_bits;      /* q: each thread walks 2^q configurations per task (0 = plan) */
+    int32_t low_bits;        /* b <= 6: unrolled innermost Gray bits (0 = plan) */
+    int32_t block_threads;   /* threads per CTA, multiple of 32, <= 1024 (0 = plan) */
+    int32_t copies;          /* privatised 32-bit histogram copies per CTA (0 = plan) */
+    int32_t ctas_per_sm;     /* resident CTAs per SM to launch (0 = plan) */
+    int32_t flush_tasks;     /* flush the 32-bit bins after this many tasks per warp (0 = the
+                                largest count that cannot overflow a 32-bit bin) */
+    int32_t shard_bits;      /* k: the 2^N configurations form 2^k shards, shard j holding the
+                                words whose top k bits (spins N-k .. N-1) equal j */
+    int32_t reserved0;
+    int64_t shard_lo;        /* enumerate shards [shard_lo, shard_hi) only; 0,0 = all */
+    int64_t shard_hi;
+    int32_t accumulate;      /* 1: add the counts into g_out; 0: overwrite g_out */
+    int32_t reserved1;
+} isg_options;
+
+/* Fill *opt with the defaults (all planner choices, full range, overwrite). */
+ISG_API void isg_options_init(isg_options* opt);
+
+/*
+ * Build a graph from an edge list: n_edges bonds (i[b], j[b], J[b]), host arrays, copied.
+ * Validation: 1 <= n_spins <= 64; 0 <= i, j < n_spins; i != j; J != 0; |J| <= 2^20.
+ * Duplicate pairs are summed (a zero sum drops the bond). Sec. 2 / Eq. 1.
+ * On success *out receives a handle to free with isg_graph_destroy.
+ * Errors: ISG_ERR_INVALID (bad edge or count), ISG_ERR_NOMEM.
+ */
+ISG_API isg_status isg_graph_create(int32_t n_spins, int64_t n_edges, const int32_t* i, const int32_t* j,
+                            const int32_t* J, isg_graph** out);
+
+/* Free a graph handle (NULL is ignored). */
+ISG_API void isg_graph_destroy(isg_graph* graph);
+
+/*
+ * Geometry of the table g for this graph (see the header comment): e_min = -S, e_step = 2,
+ * n_e = S + 1, m_min = -N, n_m = N + 1. Any output pointer may be NULL.
+ */
+ISG_API isg_status isg_graph_bins(const isg_graph* graph, int32_t* e_min, int32_t* e_step, int32_t* n_e,
+                          int32_t* m_min, int32_t* n_m);
+
+/* Number of spins and of distinct bonds after summing duplicates. */
+ISG_API isg_status isg_graph_size(const isg_graph* graph, int32_t* n_spins, int32_t* n_bonds);
+
+/*
+ * Enumerate all 2^N configurations (or the shard range of opt) and produce the exact table g
+ * (Sec. 2: the degeneracy of M over E; Sec. 3: every configuration is visited).
+ * g_out: n_e * n_m int64 (isg_graph_bins), on the device if g_out_on_device != 0 (the call then
+ * only enqueues on stream) or on the host (the call synchronises stream). opt may be NULL.
+ * Errors: ISG_ERR_INVALID, ISG_ERR_TOO_LARGE (N > max_spins, or the table does not fit the
+ * shared-memory histogram), ISG_ERR_NOMEM, ISG_ERR_CUDA, ISG_ERR_INTERNAL (host-buffer calls
+ * only: a kernel self-check failed).
+ */
+ISG_API isg_status isg_enumerate(const isg_graph* graph, void* stream, int64_t* g_out, int32_t g_out_on_device,
+                         const isg_options* opt);
+
+/*
+ * Thermodynamics on the grid T[0..nT) x h[0..nh) from a table g of this graph's geometry
+ * (Eq. 2 summed over the degeneracy table of Sec. 2). T > 0, host arrays. Outputs are
+ * nT * nh doubles each, point (a, b) at index a * nh + b: logZ = ln Z, E = <H>, M = <M>,
+ * C = Var(H)/T^2, chi = Var(M)/T; any output may be NULL. precision ISG_FP64 or ISG_FP32 (the
+ * latter computes weights and sums in float, converting counts and finishing ln Z in double).
+ * g on the device if g_on_device, outputs on the device if out_on_device; a call with any host
+ * buffer synchronises stream. Errors: ISG_ERR_INVALID, ISG_ERR_NOMEM, ISG_ERR_CUDA.
+ */
+ISG_API isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const isg_graph* graph, int32_t nT,
+                      const double* T, int32_t nh, const double* h, int32_t precision, void* stream,
+                      int32_t out_on_device, double* logZ, double* E, double* M, double* C, double* chi);
+
+/* Message of the last failing call on this thread ("" if none). Valid until the next call. */
+ISG_API const char* isg_last_error(void);
+
+/* Library version string. */
+ISG_API const char* isg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISG_H */

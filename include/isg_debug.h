@@ -1,0 +1,47 @@
+/*
+ * isg_debug.h -- inspection calls of libisg for tests and tuning. They run on the host only and
+ * make no CUDA call.
+ */
+#ifndef ISG_DEBUG_H
+#define ISG_DEBUG_H
+
+#include <stdint.h>
+
+#include "isg.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * The plan isg_enumerate would use for this graph and these options on a device with `sms`
+ * multiprocessors (0 = 152). out[0..12] = small-kernel flag, inner bits q, low-block size b,
+ * warp tasks, threads per CTA, histogram copies, CTAs per SM, tasks per flush round, grid,
+ * shared-memory bytes per CTA, energy stride G, compact energy bins, bytes of the program that
+ * isg_enumerate copies to the device. Errors as isg_enumerate.
+ */
+ISG_API isg_status isg_debug_plan(const isg_graph* graph, const isg_options* opt, int32_t sms, int64_t* out);
+
+/*
+ * Run the enumeration kernels' per-thread walk on the host, with every counter address checked,
+ * and write g (host buffer, isg_graph_bins geometry) as isg_enumerate would. The walk visits
+ * 2^N configurations one by one (Sec. 3), so this is for small N. Returns ISG_ERR_INTERNAL if
+ * an address leaves the histogram or the incrementally tracked bin of a thread's last
+ * configuration differs from its recomputation.
+ */
+ISG_API isg_status isg_debug_emulate(const isg_graph* graph, const isg_options* opt, int64_t* g_out);
+
+/*
+ * Measured peaks of the units that bound the enumeration kernel on the current device, in
+ * lane-operations per second over the whole GPU: shared-memory 32-bit reductions with each lane
+ * in its own bank (red_conflict_free) and with scattered addresses (red_scattered), and integer
+ * ALU operations (alu: independent xor/add chains). Runs three short kernels on `stream` and
+ * synchronises it. Any output may be NULL. Errors: ISG_ERR_CUDA.
+ */
+ISG_API isg_status isg_probe_peaks(void* stream, double* red_conflict_free, double* red_scattered, double* alu);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISG_DEBUG_H */

@@ -1,0 +1,186 @@
+// enum_core.cuh -- the per-thread Gray-code walk that visits 2^q configurations and counts each
+// one into a histogram of (E, M) bins. Compiled twice: into the CUDA kernels (device) and into
+// the host emulation that checks the same index arithmetic on the CPU.
+//
+// Method (arXiv:1110.2561): every configuration of N bit-packed spins is visited (Sec. 3, the
+// nested loops over bit-vectors), its spin excess M comes from the number of up bits (Sec. 3a)
+// and its energy from counting satisfied bonds with XOR / NOT / mask / popcount (Sec. 3b-3c).
+// This walk orders the visits as a binary reflected Gray code, so consecutive configurations
+// differ in one spin k and E changes by 2 S_k h_k with the local field h_k = sum_j J_kj S_j.
+//
+// Internal spin order. Positions 0..B-1 (the "low block") hold spins with no bond among
+// themselves. Inside one low block the fields on those B spins come only from spins outside it,
+// which stay fixed for 2^B consecutive visits; the bin address then moves by +-G_k per visit,
+// with G_k a per-thread register and the sign known at compile time. A spin above the low block
+// ("mid flip") is flipped every 2^B visits; its field is recomputed from the popcount of the
+// configuration word against that spin's neighbour masks.
+//
+// Bin address. Reachable energies are E = e_lo + G e' with G >= 2 the energy stride of the graph
+// (every single flip changes E by a multiple of G). The histogram stores bin (e', m) at byte
+// offset 4 (e' n_m + m), m = number of up spins. One unit of field moves the address by
+// sE = 8 n_m / G bytes: dE = 2 S_k h_k gives de' = 2 S_k h_k / G, and dm = -S_k.
+#pragma once
+#include <cstdint>
+
+#if defined(__CUDACC__)
+#define ISG_HD __host__ __device__ __forceinline__
+#define ISG_CHD __host__ __device__
+#else
+#define ISG_HD inline
+#define ISG_CHD
+#endif
+
+namespace isg {
+
+constexpr int kMaxSpins = 64;
+constexpr int kMaxClasses = 21;   // |J| <= 2^20 decomposes into at most 21 binary weights
+constexpr int kMaxLow = 6;        // largest low block
+
+// Program header, the first kHeaderWords words of a program blob (fields 32-bit unless noted).
+struct ProgHeader {
+    int32_t n;         // spins
+    int32_t q;         // inner bits walked per thread: 2^q configurations per task lane
+    int32_t b;         // low-block size
+    int32_t nc;        // weight classes
+    int32_t n_m;       // N + 1
+    int32_t n_e_c;     // compact energy bins
+    int32_t nbins_c;   // n_e_c * n_m
+    int32_t sE;        // address bytes per unit of field
+    int32_t G;         // energy stride
+    int32_t words;     // blob length in 64-bit words
+    int64_t e_lo;      // energy of compact bin 0
+    int64_t S;         // sum |J|; public bin e = (E + S) / 2
+    int32_t off_sgn;   // word offsets of the arrays below
+    int32_t off_mask;
+    int32_t off_i32;   // int32 area: w[nc], degw[n], A[n * kMaxLow]
+    int32_t pad;
+};
+constexpr int kHeaderWords = (int)(sizeof(ProgHeader) / 8);
+static_assert(sizeof(ProgHeader) % 8 == 0, "program header must be whole words");
+
+// Read-only view of a program (in shared memory on the device, host memory in emulation).
+struct ProgView {
+    int n, q, b, nc, n_m, sE, G;
+    int64_t e_lo;
+    const uint64_t* sgn;    // [n]       neighbours of k with negative coupling
+    const uint64_t* mask;   // [n * nc]  neighbours of k whose |J| has class c
+    const int32_t* w;       // [nc]      class weights
+    const int32_t* degw;    // [n]       sum_j |J_kj|
+    const int32_t* A;       // [n * kMaxLow] A[r * kMaxLow + k] = -2 J_kr sE for low spins k
+};
+
+ISG_HD ProgView make_view(const uint64_t* blob) {
+    const ProgHeader* h = reinterpret_cast<const ProgHeader*>(blob);
+    ProgView v;
+    v.n = h->n; v.q = h->q; v.b = h->b; v.nc = h->nc; v.n_m = h->n_m; v.sE = h->sE; v.G = h->G;
+    v.e_lo = h->e_lo;
+    v.sgn = blob + h->off_sgn;
+    v.mask = blob + h->off_mask;
+    const int32_t* i32 = reinterpret_cast<const int32_t*>(blob + h->off_i32);
+    v.w = i32;
+    v.degw = i32 + h->nc;
+    v.A = i32 + h->nc + h->n;
+    return v;
+}
+
+ISG_HD int popc64(uint64_t x) {
+#if defined(__CUDA_ARCH__)
+    return __popcll(x);
+#else
+    return __builtin_popcountll(x);
+#endif
+}
+
+ISG_HD int ctz32(uint32_t x) {  // x != 0
+#if defined(__CUDA_ARCH__)
+    return __ffs(static_cast<int>(x)) - 1;
+#else
+    return __builtin_ctz(x);
+#endif
+}
+
+// Compile-time helpers for the unrolled low block.
+ISG_CHD constexpr int ctz_c(int u) { return (u & 1) ? 0 : 1 + ctz_c(u >> 1); }
+ISG_CHD constexpr int gray_c(int u) { return u ^ (u >> 1); }
+
+// Local field h_k = sum_j J_kj S_j of configuration st: a neighbour j with J_kj = +-w contributes
+// +w when (bit_j XOR [J_kj < 0]) is 1 and -w otherwise (Sec. 3b: XOR, mask, count).
+ISG_HD int field(const ProgView& p, uint64_t st, int k) {
+    const uint64_t x = st ^ p.sgn[k];
+    int acc = 0;
+#pragma unroll 1
+    for (int c = 0; c < p.nc; ++c) acc += p.w[c] * popc64(x & p.mask[k * p.nc + c]);
+    return 2 * acc - p.degw[k];
+}
+
+// Byte offset of the bin of configuration st, from scratch: E = -1/2 sum_k S_k h_k (Eq. 1 with
+// each bond once), m = popcount (Sec. 3a).
+ISG_HD uint32_t bin_offset(const ProgView& p, uint64_t st) {
+    int64_t sum = 0;
+#pragma unroll 1
+    for (int k = 0; k < p.n; ++k) {
+        const int h = field(p, st, k);
+        sum += ((st >> k) & 1) ? h : -h;
+    }
+    const int64_t E = -sum / 2;
+    const int64_t ec = (E - p.e_lo) / p.G;
+    return static_cast<uint32_t>((ec * p.n_m + popc64(st)) * 4);
+}
+
+// One low block: count the current configuration, then 2^B - 1 Gray flips inside the block, each
+// followed by a count. ODD blocks start from low state 2^(B-1) instead of 0 (the reflected code
+// alternates), which reverses the direction of the flip of spin B-1 only.
+template <int B, bool ODD, class Sink>
+ISG_HD void low_block(uint32_t& idx, const int32_t (&Gk)[B], Sink& sink) {
+    sink(idx);
+#pragma unroll
+    for (int u = 1; u < (1 << B); ++u) {
+        const int k = ctz_c(u);
+        const int before = gray_c(u - 1) ^ (ODD ? (1 << (B - 1)) : 0);
+        if ((before >> k) & 1) idx += static_cast<uint32_t>(Gk[k]);   // spin k up -> down
+        else idx -= static_cast<uint32_t>(Gk[k]);                     // spin k down -> up
+        sink(idx);
+    }
+}
+
+// Flip spin r (r >= B) of st: the address moves by S_r (h_r sE - 4) (dE = 2 S_r h_r, dm = -S_r),
+// and every low spin k bonded to r sees its field change by -2 S_r J_kr.
+template <int B>
+ISG_HD void mid_flip(const ProgView& p, uint64_t& st, int r, uint32_t& idx, int32_t (&Gk)[B]) {
+    const int h = field(p, st, r);
+    const bool up = (st >> r) & 1;
+    const int32_t d = h * p.sE - 4;
+    idx += static_cast<uint32_t>(up ? d : -d);
+    const int32_t* Ar = p.A + r * kMaxLow;
+#pragma unroll
+    for (int k = 0; k < B; ++k) Gk[k] += up ? Ar[k] : -Ar[k];
+    st ^= 1ull << r;
+}
+
+// Visit the 2^q configurations prefix * 2^q + inner, inner in Gray order, counting each through
+// sink(byte offset). Returns the last configuration and its incrementally tracked offset so the
+// caller can check them against a from-scratch recomputation.
+template <int B, class Sink>
+ISG_HD void lane_walk(const ProgView& p, uint64_t prefix, uint32_t base, Sink& sink, uint64_t& last_state,
+                      uint32_t& last_idx) {
+    uint64_t st = prefix << p.q;
+    uint32_t idx = base + bin_offset(p, st);
+    int32_t Gk[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) Gk[k] = field(p, st, k) * p.sE - 4;
+    const uint32_t nblocks = 1u << (p.q - B);
+    for (uint32_t t = 0; t < nblocks; t += 2) {
+        low_block<B, false>(idx, Gk, sink);
+        st ^= 1ull << (B - 1);
+        if (t + 1 < nblocks) {
+            mid_flip<B>(p, st, B, idx, Gk);
+            low_block<B, true>(idx, Gk, sink);
+            st ^= 1ull << (B - 1);
+            if (t + 2 < nblocks) mid_flip<B>(p, st, B + ctz32(t + 2), idx, Gk);
+        }
+    }
+    last_state = st;
+    last_idx = idx;
+}
+
+}  // namespace isg

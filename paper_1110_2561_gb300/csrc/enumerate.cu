@@ -1,0 +1,253 @@
+// enumerate.cu -- sm_103a kernels that enumerate all configurations of a graph into the exact
+// degeneracy table g(E, M) (arXiv:1110.2561, Sec. 2-3), and the isg_enumerate entry point.
+//
+// Work decomposition (the paper splits the outer loops over MPI ranks, Sec. 3d; here the outer
+// configuration bits are split over warps of one GPU): a task is 32 consecutive outer prefixes,
+// one per lane; each lane walks the 2^q inner configurations of its prefix in Gray order
+// (enum_core.cuh). Warps take tasks from a global counter, so uneven progress balances itself.
+// Counts go into 32-bit shared-memory bins privatised per group of warps (red.shared.add), which
+// a CTA-wide flush adds into the int64 table with 64-bit global atomics before any bin can wrap.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "isg_internal.h"
+
+namespace isg {
+
+// Counts one configuration at a shared-memory byte address. The address is an in/out operand so
+// the compiler keeps the Gray chain of addresses in step with the reductions instead of
+// computing the whole unrolled block of addresses ahead (which exhausts registers).
+struct SmemSink {
+    __device__ __forceinline__ void operator()(uint32_t& addr) const {
+        asm volatile("red.shared.add.u32 [%0], 1;" : "+r"(addr) : : "memory");
+    }
+};
+
+struct EnumArgs {
+    const uint64_t* blob;
+    int64_t* g;                     // public table (n_e * n_m int64)
+    unsigned long long* counter;    // next task
+    unsigned int* status;           // bit 0: a lane's tracked bin disagreed with its recomputation
+    uint64_t prefix_base;           // first lane prefix
+    uint64_t n_tasks;
+    int32_t blob_words;
+    int32_t copies;
+    int32_t flush_rounds;
+    int32_t pad;
+};
+
+__device__ __forceinline__ void stage_blob(uint64_t* dst, const uint64_t* src, int words) {
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+}
+
+// Add the CTA's privatised bins into the public int64 table and clear them.
+__device__ __forceinline__ void flush_bins(const ProgHeader* hd, uint32_t* hist, int copies, int64_t* g) {
+    const int nb = hd->nbins_c, n_m = hd->n_m;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        unsigned long long s = 0;
+        for (int c = 0; c < copies; ++c) {
+            s += hist[c * nb + i];
+            hist[c * nb + i] = 0;
+        }
+        if (s) {
+            const int64_t ec = i / n_m, m = i - ec * n_m;
+            const int64_t e = (hd->e_lo + hd->G * ec + hd->S) / 2;
+            atomicAdd(reinterpret_cast<unsigned long long*>(g + e * n_m + m), s);
+        }
+    }
+}
+
+template <int B>
+__global__ void __launch_bounds__(512) enumerate_kernel(EnumArgs a) {
+    extern __shared__ __align__(16) uint64_t smem[];
+    stage_blob(smem, a.blob, a.blob_words);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(smem + ((a.blob_words + 1) & ~1));
+    __shared__ int s_done;
+    if (threadIdx.x == 0) s_done = 0;
+    __syncthreads();
+    const ProgHeader* hd = reinterpret_cast<const ProgHeader*>(smem);
+    const ProgView v = make_view(smem);
+    const int nb = hd->nbins_c;
+    for (int i = threadIdx.x; i < a.copies * nb; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(hist + (warp % a.copies) * nb));
+    SmemSink sink;
+    bool done = false;
+    for (;;) {
+        for (int r = 0; r < a.flush_rounds; ++r) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(a.counter, 1ull);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= a.n_tasks) { done = true; break; }
+            uint64_t last_state;
+            uint32_t last_idx;
+            lane_walk<B>(v, a.prefix_base + t * 32 + lane, base, sink, last_state, last_idx);
+            if (last_idx != base + bin_offset(v, last_state)) atomicOr(a.status, 1u);
+        }
+        if (done) s_done = 1;
+        __syncthreads();
+        flush_bins(hd, hist, a.copies, a.g);
+        __syncthreads();
+        if (s_done) break;
+    }
+}
+
+// Small graphs (fewer than 11 free spins): one thread per configuration, counted straight into
+// the int64 table.
+__global__ void enumerate_small_kernel(const uint64_t* blob, int words, uint64_t s_lo, uint64_t s_hi, int64_t* g) {
+    extern __shared__ __align__(16) uint64_t smem[];
+    stage_blob(smem, blob, words);
+    __syncthreads();
+    const ProgHeader* hd = reinterpret_cast<const ProgHeader*>(smem);
+    const ProgView v = make_view(smem);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t s = s_lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < s_hi; s += stride) {
+        const int64_t i = bin_offset(v, s) >> 2;
+        const int64_t ec = i / hd->n_m, m = i - ec * hd->n_m;
+        const int64_t e = (hd->e_lo + hd->G * ec + hd->S) / 2;
+        atomicAdd(reinterpret_cast<unsigned long long*>(g + e * hd->n_m + m), 1ull);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------------------
+#define ISG_CUDA(call)                                                                              \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            fail(e_ == cudaErrorMemoryAllocation ? ISG_ERR_NOMEM : ISG_ERR_CUDA,                    \
+                 std::string(#call) + ": " + cudaGetErrorString(e_));                               \
+    } while (0)
+
+DeviceInfo device_info() {
+    static std::mutex mu;
+    static std::vector<DeviceInfo> cache;
+    static std::vector<char> have;
+    int dev = 0;
+    ISG_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)cache.size() <= dev) { cache.resize(dev + 1); have.resize(dev + 1, 0); }
+    if (!have[dev]) {
+        DeviceInfo d;
+        int v = 0;
+        ISG_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+        d.sms = v;
+        ISG_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        d.smem_optin = (size_t)v;
+        ISG_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        d.smem_per_sm = (size_t)v;
+        cache[dev] = d;
+        have[dev] = 1;
+    }
+    return cache[dev];
+}
+
+// Grid: the planned CTAs per SM, capped by what the registers and shared memory of this
+// instantiation allow (cudaOccupancyMaxActiveBlocksPerMultiprocessor), never more than tasks.
+template <int B>
+static void launch_b(const Plan& p, const EnumArgs& a, cudaStream_t s) {
+    const int smem = (int)(p.smem_bytes + 16);
+    ISG_CUDA(cudaFuncSetAttribute(enumerate_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int occ = 0;
+    ISG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, enumerate_kernel<B>, p.threads, smem));
+    if (occ < 1) fail(ISG_ERR_TOO_LARGE, "enumeration kernel does not fit an SM with this block size");
+    const DeviceInfo d = device_info();
+    const uint64_t want = (uint64_t)d.sms * (uint64_t)std::min(occ, p.ctas_per_sm);
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, p.n_tasks));
+    enumerate_kernel<B><<<grid, p.threads, smem, s>>>(a);
+    ISG_CUDA(cudaGetLastError());
+}
+
+// Enqueue the kernels of one plan; `table` must be zeroed (or hold counts to add to).
+void launch_enumeration(const Plan& p, const uint64_t* d_blob, int blob_words, int64_t* table,
+                        unsigned long long* counter, unsigned int* status, cudaStream_t s) {
+    if (p.small) {
+        ISG_CUDA(cudaFuncSetAttribute(enumerate_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      blob_words * 8));
+        enumerate_small_kernel<<<p.grid, p.threads, blob_words * 8, s>>>(d_blob, blob_words, p.s_lo, p.s_hi, table);
+        ISG_CUDA(cudaGetLastError());
+        return;
+    }
+    EnumArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.blob = d_blob;
+    a.g = table;
+    a.counter = counter;
+    a.status = status;
+    a.prefix_base = p.prefix_base;
+    a.n_tasks = p.n_tasks;
+    a.blob_words = blob_words;
+    a.copies = p.copies;
+    a.flush_rounds = p.flush_rounds;
+    switch (p.b) {
+        case 1: launch_b<1>(p, a, s); break;
+        case 2: launch_b<2>(p, a, s); break;
+        case 3: launch_b<3>(p, a, s); break;
+        case 4: launch_b<4>(p, a, s); break;
+        case 5: launch_b<5>(p, a, s); break;
+        case 6: launch_b<6>(p, a, s); break;
+        default: fail(ISG_ERR_INTERNAL, "bad low block size");
+    }
+}
+
+}  // namespace isg
+
+using namespace isg;
+
+extern "C" isg_status isg_enumerate(const isg_graph* graph, void* stream, int64_t* g_out, int32_t g_out_on_device,
+                                    const isg_options* opt) {
+    try {
+        clear_error();
+        if (!graph || !g_out) fail(ISG_ERR_INVALID, "graph or g_out is NULL");
+        const isg_options o = resolve_options(opt);
+        const DeviceInfo d = device_info();
+        const Plan p = make_plan(*graph, o, d);
+        const std::vector<uint64_t> blob = build_program(*graph, p);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const size_t table_bytes = sizeof(int64_t) * (size_t)public_bins(*graph);
+        const size_t blob_bytes = blob.size() * 8;
+        // scratch: [counter 8][status 8][blob][host-mode table]
+        const size_t off_blob = 16, off_table = (off_blob + blob_bytes + 255) & ~(size_t)255;
+        const size_t scratch_bytes = off_table + (g_out_on_device ? 0 : table_bytes);
+        char* scratch = nullptr;
+        ISG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&scratch), scratch_bytes, s));
+        struct Free {
+            char* p; cudaStream_t s;
+            ~Free() { if (p) cudaFreeAsync(p, s); }
+        } guard{scratch, s};
+        ISG_CUDA(cudaMemsetAsync(scratch, 0, 16, s));
+        ISG_CUDA(cudaMemcpyAsync(scratch + off_blob, blob.data(), blob_bytes, cudaMemcpyHostToDevice, s));
+        int64_t* table = g_out_on_device ? g_out : reinterpret_cast<int64_t*>(scratch + off_table);
+        if (!g_out_on_device || !o.accumulate) ISG_CUDA(cudaMemsetAsync(table, 0, table_bytes, s));
+        launch_enumeration(p, reinterpret_cast<const uint64_t*>(scratch + off_blob), (int)blob.size(), table,
+                           reinterpret_cast<unsigned long long*>(scratch), reinterpret_cast<unsigned int*>(scratch + 8), s);
+        if (!g_out_on_device) {
+            std::vector<int64_t> host((size_t)public_bins(*graph));
+            unsigned int status = 0;
+            ISG_CUDA(cudaMemcpyAsync(host.data(), table, table_bytes, cudaMemcpyDeviceToHost, s));
+            ISG_CUDA(cudaMemcpyAsync(&status, scratch + 8, sizeof status, cudaMemcpyDeviceToHost, s));
+            ISG_CUDA(cudaStreamSynchronize(s));
+            if (status) fail(ISG_ERR_INTERNAL, "enumeration self-check failed (status " + std::to_string(status) + ")");
+            if (o.accumulate) for (size_t i = 0; i < host.size(); ++i) g_out[i] += host[i];
+            else std::memcpy(g_out, host.data(), table_bytes);
+        }
+        return ISG_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return ISG_ERR_NOMEM;
+    } catch (...) {
+        set_error("unexpected exception");
+        return ISG_ERR_INTERNAL;
+    }
+}

@@ -1,0 +1,424 @@
+// host.cpp -- graph model, options, planner, program blobs, errors and the host emulation of the
+// enumeration kernels (no CUDA calls in this file).
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "isg_internal.h"
+
+namespace isg {
+
+static thread_local std::string t_last_error;
+
+void set_error(const std::string& msg) { t_last_error = msg; }
+void clear_error() { t_last_error.clear(); }
+[[noreturn]] void fail(isg_status s, const std::string& msg) { throw Error{s, msg}; }
+
+isg_options resolve_options(const isg_options* opt) {
+    isg_options o;
+    isg_options_init(&o);
+    if (opt) {
+        if (opt->struct_size != (int32_t)sizeof(isg_options))
+            fail(ISG_ERR_INVALID, "isg_options.struct_size mismatch (initialise with isg_options_init)");
+        o = *opt;
+    }
+    if (o.max_spins <= 0) o.max_spins = 40;
+    if (o.max_spins > 62) o.max_spins = 62;
+    return o;
+}
+
+static int64_t igcd(int64_t a, int64_t b) {
+    a = a < 0 ? -a : a;
+    b = b < 0 ? -b : b;
+    while (b) { int64_t t = a % b; a = b; b = t; }
+    return a;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Planner
+// ---------------------------------------------------------------------------------------------
+static int weight_classes(const isg_graph& g, std::vector<int32_t>& w) {
+    std::vector<int64_t> vals;
+    int64_t bits = 0;
+    for (size_t b = 0; b < g.bJ.size(); ++b) {
+        int64_t a = g.bJ[b] < 0 ? -g.bJ[b] : g.bJ[b];
+        vals.push_back(a);
+        bits |= a;
+    }
+    std::sort(vals.begin(), vals.end());
+    vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
+    int nbits = 0;
+    for (int t = 0; t < 63; ++t) if ((bits >> t) & 1) ++nbits;
+    w.clear();
+    if (vals.empty()) { w.push_back(1); return 0; }       // no bonds: one empty class
+    if ((int)vals.size() <= nbits || (int)vals.size() <= 4) {
+        for (int64_t v : vals) w.push_back((int32_t)v);
+        return 0;                                          // distinct-value classes
+    }
+    for (int t = 0; t < 63; ++t) if ((bits >> t) & 1) w.push_back((int32_t)(1 << t));
+    return 1;                                              // binary classes
+}
+
+static size_t blob_words(int n, int nc) {
+    size_t i32 = (size_t)nc + n + (size_t)n * kMaxLow;
+    return kHeaderWords + (size_t)n + (size_t)n * nc + (i32 + 1) / 2;
+}
+
+Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d) {
+    Plan p;
+    const int n = g.n;
+    if (n > o.max_spins)
+        fail(ISG_ERR_TOO_LARGE, "graph has " + std::to_string(n) + " spins, more than max_spins = " +
+                                    std::to_string(o.max_spins));
+    const int k = o.shard_bits;
+    if (k < 0 || k > n) fail(ISG_ERR_INVALID, "shard_bits must lie in [0, N]");
+    int64_t lo = o.shard_lo, hi = o.shard_hi;
+    if (lo == 0 && hi == 0) hi = (int64_t)1 << k;
+    if (lo < 0 || lo >= hi || hi > ((int64_t)1 << k)) fail(ISG_ERR_INVALID, "shard range must satisfy 0 <= lo < hi <= 2^shard_bits");
+    const int free = n - k;
+    p.perm.resize(n);
+    std::iota(p.perm.begin(), p.perm.end(), 0);
+
+    const bool forced = o.inner_bits > 0 || o.low_bits > 0;
+    if (free < 6 || (free < 11 && !forced)) {
+        p.small = true;
+        p.s_lo = (uint64_t)lo << free;
+        p.s_hi = (uint64_t)hi << free;
+        p.q = 0;
+        p.b = 0;
+        p.threads = 256;
+        const uint64_t states = p.s_hi - p.s_lo;
+        p.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((states + p.threads - 1) / p.threads, (uint64_t)d.sms * 8));
+        p.smem_bytes = blob_words(n, 21) * 8;
+        return p;
+    }
+
+    // Low block: greedy independent set among the spins below the shard bits, lowest degree first.
+    int bmax = o.low_bits > 0 ? o.low_bits : kMaxLow;
+    if (bmax > kMaxLow) fail(ISG_ERR_INVALID, "low_bits must be <= 6");
+    bmax = std::min(bmax, free - 5);
+    std::vector<int> cand(free);
+    std::iota(cand.begin(), cand.end(), 0);
+    std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) { return g.degree[a] < g.degree[b]; });
+    std::vector<int> low;
+    for (int c : cand) {
+        if ((int)low.size() >= bmax) break;
+        bool ok = true;
+        for (int l : low) if (g.K[(size_t)c * n + l] != 0) { ok = false; break; }
+        if (ok) low.push_back(c);
+    }
+    std::sort(low.begin(), low.end());
+    if (o.low_bits > 0 && (int)low.size() < o.low_bits)
+        fail(ISG_ERR_INVALID, "no independent set of low_bits spins below the shard bits");
+    p.b = (int)low.size();
+    {
+        std::vector<char> used(n, 0);
+        int pos = 0;
+        for (int l : low) { p.perm[pos++] = l; used[l] = 1; }
+        for (int s = 0; s < free; ++s) if (!used[s]) p.perm[pos++] = s;
+        for (int s = free; s < n; ++s) p.perm[pos++] = s;
+    }
+
+    // Inner bits.
+    const int shards_log2 = [&] { int t = 0; while (((int64_t)1 << t) < (hi - lo)) ++t; return t; }();
+    if (o.inner_bits > 0) {
+        p.q = o.inner_bits;
+        if (p.q < p.b || p.q > free - 5 || p.q > 26)
+            fail(ISG_ERR_INVALID, "inner_bits must satisfy low block <= q <= N - shard_bits - 5 and q <= 26");
+    } else {
+        int q = free - 5 - std::max(0, 17 - shards_log2);
+        q = std::min(q, 20);
+        q = std::min(q, free - 5);
+        p.q = std::max(q, p.b);
+    }
+    const int pk = free - p.q;               // outer bits below the shard bits
+    p.prefix_base = (uint64_t)lo << pk;
+    p.n_tasks = ((uint64_t)(hi - lo) << pk) / 32;
+
+    // Launch shape and shared memory.
+    p.threads = o.block_threads > 0 ? o.block_threads : 512;
+    if (p.threads % 32 || p.threads < 32 || p.threads > 1024) fail(ISG_ERR_INVALID, "block_threads must be a multiple of 32 in [32, 1024]");
+    const int warps = p.threads / 32;
+    std::vector<int32_t> w;
+    weight_classes(g, w);
+    const size_t prog_bytes = blob_words(n, (int)w.size()) * 8;
+    const size_t bin_bytes = (size_t)g.n_e_c * (n + 1) * 4;
+    if (prog_bytes + bin_bytes > d.smem_optin)
+        fail(ISG_ERR_TOO_LARGE, "histogram of " + std::to_string(g.n_e_c * (n + 1)) + " bins does not fit shared memory");
+    p.ctas_per_sm = o.ctas_per_sm > 0 ? o.ctas_per_sm : 2;
+    if (o.copies > 0) {
+        p.copies = o.copies;
+        if (p.copies > warps) fail(ISG_ERR_INVALID, "copies must not exceed warps per CTA");
+        if (prog_bytes + p.copies * bin_bytes > d.smem_optin) fail(ISG_ERR_TOO_LARGE, "copies do not fit shared memory");
+    } else {
+        const size_t per_cta = std::min(d.smem_optin, d.smem_per_sm / p.ctas_per_sm - 1024);
+        int c = 1;
+        while (c * 2 <= warps && prog_bytes + (size_t)(c * 2) * bin_bytes <= per_cta) c *= 2;
+        p.copies = c;
+    }
+    p.smem_bytes = prog_bytes + (size_t)p.copies * bin_bytes;
+    while (p.ctas_per_sm > 1 && (p.smem_bytes + 1024) * p.ctas_per_sm > d.smem_per_sm) --p.ctas_per_sm;
+    const uint64_t per_copy_warps = (uint64_t)((warps + p.copies - 1) / p.copies);
+    const uint64_t per_round = per_copy_warps << (p.q + 5);      // max increments of a bin per round
+    uint64_t F = 0xffffffffull / per_round;
+    if (F < 1) fail(ISG_ERR_INVALID, "inner_bits too large for 32-bit bins with this many warps per copy");
+    if (o.flush_tasks > 0) F = std::min<uint64_t>(F, (uint64_t)o.flush_tasks);
+    p.flush_rounds = (int)std::min<uint64_t>(F, 1u << 30);
+    p.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(p.n_tasks, (uint64_t)d.sms * p.ctas_per_sm));
+    return p;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Program blob
+// ---------------------------------------------------------------------------------------------
+std::vector<uint64_t> build_program(const isg_graph& g, const Plan& p) {
+    const int n = g.n;
+    std::vector<int32_t> w;
+    const int binary = weight_classes(g, w);
+    const int nc = (int)w.size();
+    const size_t words = blob_words(n, nc);
+    std::vector<uint64_t> blob(words, 0);
+    ProgHeader h{};
+    h.n = n;
+    h.q = p.q;
+    h.b = p.b;
+    h.nc = nc;
+    h.n_m = n + 1;
+    h.n_e_c = (int32_t)g.n_e_c;
+    h.nbins_c = (int32_t)(g.n_e_c * (n + 1));
+    h.G = (int32_t)g.G;
+    h.sE = (int32_t)(8 * (n + 1) / g.G);
+    h.words = (int32_t)words;
+    h.e_lo = g.e_lo;
+    h.S = g.S;
+    h.off_sgn = kHeaderWords;
+    h.off_mask = kHeaderWords + n;
+    h.off_i32 = kHeaderWords + n + n * nc;
+    std::memcpy(blob.data(), &h, sizeof h);
+    uint64_t* sgn = blob.data() + h.off_sgn;
+    uint64_t* mask = blob.data() + h.off_mask;
+    int32_t* i32 = reinterpret_cast<int32_t*>(blob.data() + h.off_i32);
+    int32_t* wv = i32;
+    int32_t* degw = i32 + nc;
+    int32_t* A = i32 + nc + n;
+    for (int c = 0; c < nc; ++c) wv[c] = w[c];
+    for (int a = 0; a < n; ++a) {
+        const int ca = p.perm[a];
+        int64_t dw = 0;
+        for (int b = 0; b < n; ++b) {
+            const int64_t J = g.K[(size_t)ca * n + p.perm[b]];
+            if (!J) continue;
+            const int64_t aJ = J < 0 ? -J : J;
+            dw += aJ;
+            if (J < 0) sgn[a] |= 1ull << b;
+            for (int c = 0; c < nc; ++c) {
+                const bool in = binary ? ((aJ & w[c]) != 0) : (aJ == w[c]);
+                if (in) mask[(size_t)a * nc + c] |= 1ull << b;
+            }
+        }
+        degw[a] = (int32_t)dw;
+    }
+    for (int r = 0; r < n; ++r)
+        for (int k = 0; k < p.b; ++k)
+            A[r * kMaxLow + k] = (r >= p.b) ? (int32_t)(-2 * g.K[(size_t)p.perm[k] * n + p.perm[r]] * h.sE) : 0;
+    return blob;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host emulation of the kernels (same lane walk, bounds-checked counting)
+// ---------------------------------------------------------------------------------------------
+struct HostSink {
+    std::vector<uint32_t>* hist;
+    uint32_t limit;
+    bool bad = false;
+    void operator()(uint32_t& idx) {
+        if ((idx & 3u) || idx >= limit) { bad = true; return; }
+        (*hist)[idx >> 2] += 1;
+    }
+};
+
+template <int B>
+static void emulate_tasks(const ProgView& v, const Plan& p, std::vector<uint32_t>& hist, bool& bad) {
+    HostSink sink{&hist, (uint32_t)(hist.size() * 4)};
+    for (uint64_t t = 0; t < p.n_tasks; ++t)
+        for (int lane = 0; lane < 32; ++lane) {
+            uint64_t last_state;
+            uint32_t last_idx;
+            lane_walk<B>(v, p.prefix_base + t * 32 + lane, 0u, sink, last_state, last_idx);
+            if (last_idx != bin_offset(v, last_state)) bad = true;
+        }
+    if (sink.bad) bad = true;
+}
+
+}  // namespace isg
+
+using namespace isg;
+
+template <class F>
+static isg_status guarded(F&& f) {
+    try {
+        clear_error();
+        f();
+        return ISG_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return ISG_ERR_NOMEM;
+    } catch (...) {
+        set_error("unexpected exception");
+        return ISG_ERR_INTERNAL;
+    }
+}
+
+extern "C" {
+
+void isg_options_init(isg_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof *opt);
+    opt->struct_size = (int32_t)sizeof(isg_options);
+    opt->max_spins = 40;
+}
+
+const char* isg_last_error(void) { return t_last_error.c_str(); }
+
+const char* isg_version(void) { return "isg 0.1 (sm_103a)"; }
+
+isg_status isg_graph_create(int32_t n_spins, int64_t n_edges, const int32_t* ei, const int32_t* ej,
+                            const int32_t* J, isg_graph** out) {
+    return guarded([&] {
+        if (!out) fail(ISG_ERR_INVALID, "out is NULL");
+        *out = nullptr;
+        if (n_spins < 1 || n_spins > kMaxSpins) fail(ISG_ERR_INVALID, "n_spins must lie in [1, 64]");
+        if (n_edges < 0) fail(ISG_ERR_INVALID, "n_edges must be >= 0");
+        if (n_edges > 0 && (!ei || !ej || !J)) fail(ISG_ERR_INVALID, "edge arrays are NULL");
+        isg_graph* g = new isg_graph();
+        try {
+            const int n = n_spins;
+            g->n = n;
+            g->K.assign((size_t)n * n, 0);
+            for (int64_t b = 0; b < n_edges; ++b) {
+                const int i = ei[b], j = ej[b];
+                if (i < 0 || j < 0 || i >= n || j >= n) fail(ISG_ERR_INVALID, "edge " + std::to_string(b) + " has an endpoint out of range");
+                if (i == j) fail(ISG_ERR_INVALID, "edge " + std::to_string(b) + " is a self loop");
+                if (J[b] == 0 || J[b] > (1 << 20) || J[b] < -(1 << 20)) fail(ISG_ERR_INVALID, "edge " + std::to_string(b) + " has J = 0 or |J| > 2^20");
+                g->K[(size_t)i * n + j] += J[b];
+                g->K[(size_t)j * n + i] += J[b];
+            }
+            g->degree.assign(n, 0);
+            int64_t gg = 0;
+            for (int i = 0; i < n; ++i) {
+                int64_t sum = 0, gi = 0;
+                bool any = false;
+                for (int j = 0; j < n; ++j) {
+                    const int64_t v = g->K[(size_t)i * n + j];
+                    if (!v) continue;
+                    if (std::llabs(v) > (1 << 20)) fail(ISG_ERR_INVALID, "summed coupling exceeds 2^20 in magnitude");
+                    any = true;
+                    g->degree[i]++;
+                    sum += v;
+                    gi = igcd(gi, 2 * v);
+                    if (j > i) { g->bi.push_back(i); g->bj.push_back(j); g->bJ.push_back(v); g->S += std::llabs(v); }
+                }
+                if (any) gg = igcd(gg, igcd(sum, gi));
+            }
+            g->e_ref = 0;
+            for (size_t b = 0; b < g->bJ.size(); ++b) g->e_ref -= g->bJ[b];
+            int64_t G = gg ? 2 * gg : 2;
+            G = igcd(G, 8 * (int64_t)(n + 1));          // keep 8 (N + 1) / G integral
+            g->G = G;
+            g->e_lo = g->e_ref - G * ((g->e_ref + g->S) / G);
+            g->n_e_c = (g->S - g->e_lo) / G + 1;
+        } catch (...) {
+            delete g;
+            throw;
+        }
+        *out = g;
+    });
+}
+
+void isg_graph_destroy(isg_graph* graph) { delete graph; }
+
+isg_status isg_graph_bins(const isg_graph* g, int32_t* e_min, int32_t* e_step, int32_t* n_e, int32_t* m_min,
+                          int32_t* n_m) {
+    return guarded([&] {
+        if (!g) fail(ISG_ERR_INVALID, "graph is NULL");
+        if (g->S > (int64_t)1 << 30) fail(ISG_ERR_TOO_LARGE, "energy range exceeds int32");
+        if (e_min) *e_min = (int32_t)(-g->S);
+        if (e_step) *e_step = 2;
+        if (n_e) *n_e = (int32_t)(g->S + 1);
+        if (m_min) *m_min = -g->n;
+        if (n_m) *n_m = g->n + 1;
+    });
+}
+
+isg_status isg_graph_size(const isg_graph* g, int32_t* n_spins, int32_t* n_bonds) {
+    return guarded([&] {
+        if (!g) fail(ISG_ERR_INVALID, "graph is NULL");
+        if (n_spins) *n_spins = g->n;
+        if (n_bonds) *n_bonds = (int32_t)g->bJ.size();
+    });
+}
+
+isg_status isg_debug_plan(const isg_graph* g, const isg_options* opt, int32_t sms, int64_t* out) {
+    return guarded([&] {
+        if (!g || !out) fail(ISG_ERR_INVALID, "NULL argument");
+        isg_options o = resolve_options(opt);
+        DeviceInfo d;
+        if (sms > 0) d.sms = sms;
+        Plan p = make_plan(*g, o, d);
+        out[0] = p.small;
+        out[1] = p.q;
+        out[2] = p.b;
+        out[3] = (int64_t)p.n_tasks;
+        out[4] = p.threads;
+        out[5] = p.copies;
+        out[6] = p.ctas_per_sm;
+        out[7] = p.flush_rounds;
+        out[8] = p.grid;
+        out[9] = (int64_t)p.smem_bytes;
+        out[10] = g->G;
+        out[11] = g->n_e_c;
+        out[12] = (int64_t)build_program(*g, p).size() * 8;
+    });
+}
+
+isg_status isg_debug_emulate(const isg_graph* g, const isg_options* opt, int64_t* g_out) {
+    return guarded([&] {
+        if (!g || !g_out) fail(ISG_ERR_INVALID, "NULL argument");
+        isg_options o = resolve_options(opt);
+        Plan p = make_plan(*g, o, DeviceInfo{});
+        std::vector<uint64_t> blob = build_program(*g, p);
+        const ProgView v = make_view(blob.data());
+        const int64_t nb = g->n_e_c * (g->n + 1);
+        std::vector<uint32_t> hist((size_t)nb, 0);
+        bool bad = false;
+        if (p.small) {
+            for (uint64_t s = p.s_lo; s < p.s_hi; ++s) {
+                const uint32_t off = bin_offset(v, s);
+                if ((off & 3u) || off >= nb * 4) { bad = true; continue; }
+                hist[off >> 2] += 1;
+            }
+        } else {
+            switch (p.b) {
+                case 1: emulate_tasks<1>(v, p, hist, bad); break;
+                case 2: emulate_tasks<2>(v, p, hist, bad); break;
+                case 3: emulate_tasks<3>(v, p, hist, bad); break;
+                case 4: emulate_tasks<4>(v, p, hist, bad); break;
+                case 5: emulate_tasks<5>(v, p, hist, bad); break;
+                case 6: emulate_tasks<6>(v, p, hist, bad); break;
+                default: fail(ISG_ERR_INTERNAL, "bad low block size");
+            }
+        }
+        if (bad) fail(ISG_ERR_INTERNAL, "emulated walk left the histogram or lost track of its bin");
+        if (!o.accumulate) std::memset(g_out, 0, sizeof(int64_t) * public_bins(*g));
+        for (int64_t i = 0; i < nb; ++i)
+            if (hist[i]) g_out[public_bin(*g, i)] += hist[i];
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// isg_internal.h -- host-side model shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/isg.h"
+#include "../../include/isg_debug.h"
+#include "enum_core.cuh"
+
+struct isg_graph {
+    int n = 0;
+    std::vector<int64_t> K;                 // n*n summed couplings, symmetric, zero diagonal
+    std::vector<int32_t> bi, bj;            // distinct bonds (i < j)
+    std::vector<int64_t> bJ;
+    int64_t S = 0;                          // sum |J|
+    int64_t G = 2;                          // energy stride of reachable energies
+    int64_t e_ref = 0;                      // energy of the all-down configuration
+    int64_t e_lo = 0;                       // smallest reachable-class energy >= -S
+    int64_t n_e_c = 1;                      // compact energy bins
+    std::vector<int> degree;                // distinct neighbours per spin
+};
+
+namespace isg {
+
+// Thread-local error message.
+void set_error(const std::string& msg);
+void clear_error();
+
+// Exception type used inside the library; converted to a status at the ABI.
+struct Error {
+    isg_status status;
+    std::string msg;
+};
+[[noreturn]] void fail(isg_status s, const std::string& msg);
+
+// Resolved options with defaults applied.
+isg_options resolve_options(const isg_options* opt);
+
+// Execution plan of one enumeration.
+struct Plan {
+    bool small = false;        // thread-per-configuration kernel over [s_lo, s_hi)
+    uint64_t s_lo = 0, s_hi = 0;
+    int q = 0, b = 0;          // inner bits, low-block size
+    std::vector<int> perm;     // internal position -> caller spin
+    uint64_t prefix_base = 0;  // first lane prefix (multiple of 32)
+    uint64_t n_tasks = 0;      // warp tasks: 32 lane prefixes each
+    int threads = 512, copies = 1, ctas_per_sm = 2, flush_rounds = 1;
+    int grid = 0;
+    size_t smem_bytes = 0;
+};
+
+struct DeviceInfo {
+    int sms = 152;
+    size_t smem_optin = 232448;
+    size_t smem_per_sm = 233472;
+};
+
+// Plan an enumeration of graph g under options o on a device with properties d.
+Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d);
+
+// Build the program blob (64-bit words) of graph g for a plan: spins in internal order.
+std::vector<uint64_t> build_program(const isg_graph& g, const Plan& p);
+
+// Map compact bin i = e' * n_m + m of the internal histogram to the public table index.
+inline int64_t public_bin(const isg_graph& g, int64_t compact) {
+    const int64_t n_m = g.n + 1;
+    const int64_t ec = compact / n_m, m = compact % n_m;
+    const int64_t E = g.e_lo + g.G * ec;
+    return ((E + g.S) / 2) * n_m + m;
+}
+
+inline int64_t public_bins(const isg_graph& g) { return (g.S + 1) * (int64_t)(g.n + 1); }
+
+}  // namespace isg

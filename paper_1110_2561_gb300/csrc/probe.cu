@@ -1,0 +1,100 @@
+// probe.cu -- measured peaks of the units that bound the enumeration kernel: shared-memory
+// 32-bit reductions (red.shared.add.u32) with conflict-free and with scattered addresses, and
+// integer ALU issue. Each warp works on its own 2048-word table; every address is masked into
+// it. The rates are lane-operations per second over the whole GPU, timed with CUDA events.
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "isg_internal.h"
+
+namespace isg {
+
+constexpr int kProbeWords = 2048;   // words per warp table (power of two)
+
+template <int MODE>
+__global__ void __launch_bounds__(512) probe_kernel(int iters, unsigned* sink) {
+    extern __shared__ unsigned tbl[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned* t = tbl + warp * kProbeWords;
+    for (int i = lane; i < kProbeWords; i += 32) t[i] = 0;
+    __syncthreads();
+    const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(t));
+    unsigned a = (lane * 97u) & (kProbeWords - 1);
+    const unsigned s = ((lane * 2654435761u) >> 7) | 1u;
+    unsigned x0 = lane, x1 = lane * 3u, x2 = lane * 5u, x3 = lane * 7u;
+    for (int i = 0; i < iters; ++i) {
+        if (MODE == 0) {          // conflict-free: lane l always in bank l
+            uint32_t ad = base + 4u * ((((unsigned)i & 63u) << 5) | lane);
+            asm volatile("red.shared.add.u32 [%0], 1;" : "+r"(ad) : : "memory");
+        } else if (MODE == 1) {   // scattered: independent strides per lane
+            a = (a + s) & (kProbeWords - 1);
+            uint32_t ad = base + 4u * a;
+            asm volatile("red.shared.add.u32 [%0], 1;" : "+r"(ad) : : "memory");
+        } else {                  // integer ALU: 4 independent xor/add chains
+            x0 = (x0 ^ x1) + i; x1 = (x1 ^ x2) + i; x2 = (x2 ^ x3) + i; x3 = (x3 ^ x0) + i;
+        }
+    }
+    __syncthreads();
+    unsigned tot = x0 + x1 + x2 + x3;
+    for (int i = lane; i < kProbeWords; i += 32) tot += t[i];
+    atomicAdd(sink, tot);
+}
+
+#define ISG_CUDA(call)                                                                              \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) fail(ISG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <int MODE>
+static double probe_rate(cudaStream_t s, unsigned* sink, int sms, double ops_per_iter) {
+    const int threads = 512, iters = 1 << 16;
+    const size_t smem = (size_t)(threads / 32) * kProbeWords * 4;
+    ISG_CUDA(cudaFuncSetAttribute(probe_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    probe_kernel<MODE><<<sms, threads, smem, s>>>(iters, sink);      // warm-up
+    ISG_CUDA(cudaGetLastError());
+    cudaEvent_t e0, e1;
+    ISG_CUDA(cudaEventCreate(&e0));
+    ISG_CUDA(cudaEventCreate(&e1));
+    ISG_CUDA(cudaEventRecord(e0, s));
+    probe_kernel<MODE><<<sms, threads, smem, s>>>(iters, sink);
+    ISG_CUDA(cudaEventRecord(e1, s));
+    ISG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    ISG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return (double)sms * threads * iters * ops_per_iter / (ms * 1e-3);
+}
+
+}  // namespace isg
+
+using namespace isg;
+
+extern "C" isg_status isg_probe_peaks(void* stream, double* red_conflict_free, double* red_scattered, double* alu) {
+    try {
+        clear_error();
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        int dev = 0, sms = 0;
+        ISG_CUDA(cudaGetDevice(&dev));
+        ISG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        unsigned* sink = nullptr;
+        ISG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&sink), 4, s));
+        const double r0 = probe_rate<0>(s, sink, sms, 1.0);
+        const double r1 = probe_rate<1>(s, sink, sms, 1.0);
+        const double r2 = probe_rate<2>(s, sink, sms, 8.0);
+        ISG_CUDA(cudaFreeAsync(sink, s));
+        ISG_CUDA(cudaStreamSynchronize(s));
+        if (red_conflict_free) *red_conflict_free = r0;
+        if (red_scattered) *red_scattered = r1;
+        if (alu) *alu = r2;
+        return ISG_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.status;
+    } catch (...) {
+        set_error("unexpected exception");
+        return ISG_ERR_INTERNAL;
+    }
+}

@@ -1,0 +1,270 @@
+// thermo.cu -- partition function and moments from the degeneracy table (arXiv:1110.2561,
+// Eq. 2 summed over the table g(E, M) of Sec. 2), on a grid of temperatures T and fields h.
+//
+// Z(T, h) = sum_{E,M} g(E, M) exp(-(E - h M) / T) factors exactly over M:
+//   Z = sum_M exp(h M / T) A_T(M),   A_T(M) = sum_E g(E, M) exp(-E / T).
+// Stage 1 (per T and M, the expensive part, independent of h) keeps, log-shifted by the largest
+// term, L_T(M) = ln A_T(M) and the conditional mean and variance of E at fixed M. Stage 2 (per
+// T and h) combines them over the N + 1 values of M with a log-sum-exp:
+//   <H> = sum_M p(M) (mu_E(M) - h M),  Var(H) = sum_M p(M) [var_E(M) + (mu_E(M) - h M - <H>)^2],
+// with p(M) proportional to exp(L_T(M) + h M / T). Var(H) is a sum of non-negative terms, so no
+// cancellation enters C = Var(H)/T^2 or chi = Var(M)/T.
+//
+// FP64: everything in double. FP32: the counts are converted to ln g in double once and rounded
+// to float; every exponential and every sum runs in float, relative to the row or column
+// maximum; ln Z is finished in double from the float sum.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "isg_internal.h"
+
+namespace isg {
+
+struct ThermoArgs {
+    const int64_t* g;   // n_e x n_m counts
+    const double* T;    // nT
+    const double* h;    // nh
+    double* logZ;
+    double* E;
+    double* M;
+    double* C;
+    double* chi;
+    int n, n_e, n_m, nT, nh;
+    int64_t e_min;
+};
+
+template <class F> __device__ __forceinline__ F ex(F x);
+template <> __device__ __forceinline__ double ex<double>(double x) { return exp(x); }
+template <> __device__ __forceinline__ float ex<float>(float x) { return expf(x); }
+template <class F> __device__ __forceinline__ F lg(F x);
+template <> __device__ __forceinline__ double lg<double>(double x) { return log(x); }
+template <> __device__ __forceinline__ float lg<float>(float x) { return logf(x); }
+
+template <class F>
+__device__ __forceinline__ F warp_max(F v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+template <class F>
+__device__ __forceinline__ F warp_sum(F v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ln g for every bin (double, from the int64 count); -inf marks an empty bin.
+__global__ void log_counts_kernel(const int64_t* g, int nbins, double* lng) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nbins; i += gridDim.x * blockDim.x) {
+        const int64_t c = g[i];
+        lng[i] = c > 0 ? log((double)c) : -INFINITY;
+    }
+}
+
+// One CTA per temperature. Shared memory: L[n_m] (double), mu[n_m], var[n_m] (F).
+template <class F>
+__global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double* lng) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    double* L = reinterpret_cast<double*>(sm);
+    F* mu = reinterpret_cast<F*>(L + a.n_m);
+    F* var = mu + a.n_m;
+    __shared__ double s_Lmax;
+    const int it = blockIdx.x;
+    const double T = a.T[it];
+    const F invT = (F)(1.0 / T);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+
+    // Stage 1: per column M (one warp each).
+    for (int m = warp; m < a.n_m; m += nw) {
+        F xmax = (F)-INFINITY;
+        int earg = 0;
+        for (int e = lane; e < a.n_e; e += 32) {
+            const double l = lng[(size_t)e * a.n_m + m];
+            if (l == -INFINITY) continue;
+            const F x = (F)l - (F)(a.e_min + 2 * e) * invT;
+            if (x > xmax) { xmax = x; earg = e; }
+        }
+        const F wmax = warp_max(xmax);
+        // a lane holding the maximum names the reference energy (any tie is fine)
+        const unsigned hit = __ballot_sync(0xffffffffu, xmax == wmax && wmax != (F)-INFINITY);
+        if (!hit) {
+            if (lane == 0) { L[m] = -INFINITY; mu[m] = 0; var[m] = 0; }
+            continue;
+        }
+        const F Eref = (F)(a.e_min + 2 * __shfl_sync(0xffffffffu, earg, __ffs(hit) - 1));
+        F s0 = 0, s1 = 0;
+        for (int e = lane; e < a.n_e; e += 32) {
+            const double l = lng[(size_t)e * a.n_m + m];
+            if (l == -INFINITY) continue;
+            const F En = (F)(a.e_min + 2 * e);
+            const F w = ex<F>((F)l - En * invT - wmax);
+            s0 += w;
+            s1 += w * (En - Eref);
+        }
+        s0 = warp_sum(s0);
+        s1 = warp_sum(s1);
+        const F m1 = Eref + s1 / s0;
+        F s2 = 0;
+        for (int e = lane; e < a.n_e; e += 32) {
+            const double l = lng[(size_t)e * a.n_m + m];
+            if (l == -INFINITY) continue;
+            const F En = (F)(a.e_min + 2 * e);
+            const F w = ex<F>((F)l - En * invT - wmax);
+            const F d = En - m1;
+            s2 += w * d * d;
+        }
+        s2 = warp_sum(s2);
+        if (lane == 0) {
+            L[m] = (double)wmax + log((double)s0);
+            mu[m] = m1;
+            var[m] = s2 / s0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mx = -INFINITY;
+        for (int m = 0; m < a.n_m; ++m) mx = fmax(mx, L[m]);
+        s_Lmax = mx;
+    }
+    __syncthreads();
+    const double Lmax = s_Lmax;
+
+    // Stage 2: one thread per field value.
+    for (int ih = threadIdx.x; ih < a.nh; ih += blockDim.x) {
+        const double hd = a.h[ih];
+        const F hT = (F)(hd / T), hF = (F)hd;
+        F amax = (F)-INFINITY;
+        for (int m = 0; m < a.n_m; ++m) {
+            if (L[m] == -INFINITY) continue;
+            const F am = (F)(L[m] - Lmax) + hT * (F)(2 * m - a.n);
+            amax = fmax(amax, am);
+        }
+        F z = 0, zM = 0, zH = 0;
+        for (int m = 0; m < a.n_m; ++m) {
+            if (L[m] == -INFINITY) continue;
+            const F Mm = (F)(2 * m - a.n);
+            const F p = ex<F>((F)(L[m] - Lmax) + hT * Mm - amax);
+            z += p;
+            zM += p * Mm;
+            zH += p * (mu[m] - hF * Mm);
+        }
+        const F mM = zM / z, mH = zH / z;
+        F vH = 0, vM = 0;
+        for (int m = 0; m < a.n_m; ++m) {
+            if (L[m] == -INFINITY) continue;
+            const F Mm = (F)(2 * m - a.n);
+            const F p = ex<F>((F)(L[m] - Lmax) + hT * Mm - amax);
+            const F dH = mu[m] - hF * Mm - mH, dM = Mm - mM;
+            vH += p * (var[m] + dH * dH);
+            vM += p * dM * dM;
+        }
+        vH /= z;
+        vM /= z;
+        const size_t o = (size_t)it * a.nh + ih;
+        if (a.logZ) a.logZ[o] = Lmax + (double)amax + log((double)z);
+        if (a.E) a.E[o] = (double)mH;
+        if (a.M) a.M[o] = (double)mM;
+        if (a.C) a.C[o] = (double)vH / (T * T);
+        if (a.chi) a.chi[o] = (double)vM / T;
+    }
+}
+
+#define ISG_CUDA(call)                                                                              \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            fail(e_ == cudaErrorMemoryAllocation ? ISG_ERR_NOMEM : ISG_ERR_CUDA,                    \
+                 std::string(#call) + ": " + cudaGetErrorString(e_));                               \
+    } while (0)
+
+// Enqueue the thermodynamics kernels; all pointers on the device. lng: n_e * n_m doubles scratch.
+void launch_thermo(const ThermoArgs& a, double* lng, int precision, cudaStream_t s) {
+    const int nbins = a.n_e * a.n_m;
+    log_counts_kernel<<<std::min(1024, (nbins + 255) / 256), 256, 0, s>>>(a.g, nbins, lng);
+    ISG_CUDA(cudaGetLastError());
+    if (precision == ISG_FP64) {
+        const size_t smem = (size_t)a.n_m * (8 + 2 * sizeof(double));
+        thermo_kernel<double><<<a.nT, 256, smem, s>>>(a, lng);
+    } else {
+        const size_t smem = (size_t)a.n_m * (8 + 2 * sizeof(float));
+        thermo_kernel<float><<<a.nT, 256, smem, s>>>(a, lng);
+    }
+    ISG_CUDA(cudaGetLastError());
+}
+
+}  // namespace isg
+
+using namespace isg;
+
+extern "C" isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const isg_graph* graph, int32_t nT,
+                                 const double* T, int32_t nh, const double* h, int32_t precision, void* stream,
+                                 int32_t out_on_device, double* logZ, double* E, double* M, double* C, double* chi) {
+    try {
+        clear_error();
+        if (!g || !graph || !T || !h) fail(ISG_ERR_INVALID, "NULL argument");
+        if (nT < 1 || nh < 1) fail(ISG_ERR_INVALID, "nT and nh must be >= 1");
+        if (precision != ISG_FP64 && precision != ISG_FP32) fail(ISG_ERR_INVALID, "precision must be ISG_FP64 or ISG_FP32");
+        for (int i = 0; i < nT; ++i)
+            if (!(T[i] > 0) || !std::isfinite(T[i])) fail(ISG_ERR_INVALID, "temperatures must be finite and > 0");
+        for (int i = 0; i < nh; ++i)
+            if (!std::isfinite(h[i])) fail(ISG_ERR_INVALID, "fields must be finite");
+        if (graph->S > (1 << 24)) fail(ISG_ERR_TOO_LARGE, "energy range too large for the thermodynamics kernels");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const int n_m = graph->n + 1, n_e = (int)(graph->S + 1);
+        const size_t gbytes = sizeof(int64_t) * (size_t)n_e * n_m;
+        const size_t pts = (size_t)nT * nh;
+        // scratch: [lng][T][h][g copy if host][outputs if host]
+        size_t off = 0;
+        auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) & ~(size_t)255; return o; };
+        const size_t o_lng = take(sizeof(double) * (size_t)n_e * n_m);
+        const size_t o_T = take(sizeof(double) * nT), o_h = take(sizeof(double) * nh);
+        const size_t o_g = g_on_device ? 0 : take(gbytes);
+        const size_t o_out = out_on_device ? 0 : take(5 * sizeof(double) * pts);
+        char* scratch = nullptr;
+        ISG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&scratch), off, s));
+        struct Free {
+            char* p; cudaStream_t s;
+            ~Free() { if (p) cudaFreeAsync(p, s); }
+        } guard{scratch, s};
+        ThermoArgs a;
+        std::memset(&a, 0, sizeof a);
+        a.n = graph->n; a.n_e = n_e; a.n_m = n_m; a.nT = nT; a.nh = nh; a.e_min = -graph->S;
+        a.T = reinterpret_cast<double*>(scratch + o_T);
+        a.h = reinterpret_cast<double*>(scratch + o_h);
+        ISG_CUDA(cudaMemcpyAsync(scratch + o_T, T, sizeof(double) * nT, cudaMemcpyHostToDevice, s));
+        ISG_CUDA(cudaMemcpyAsync(scratch + o_h, h, sizeof(double) * nh, cudaMemcpyHostToDevice, s));
+        if (g_on_device) a.g = g;
+        else {
+            ISG_CUDA(cudaMemcpyAsync(scratch + o_g, g, gbytes, cudaMemcpyHostToDevice, s));
+            a.g = reinterpret_cast<int64_t*>(scratch + o_g);
+        }
+        double* outs_host[5] = {logZ, E, M, C, chi};
+        double* outs_dev[5];
+        for (int k = 0; k < 5; ++k)
+            outs_dev[k] = !outs_host[k] ? nullptr
+                          : out_on_device ? outs_host[k]
+                                          : reinterpret_cast<double*>(scratch + o_out) + k * pts;
+        a.logZ = outs_dev[0]; a.E = outs_dev[1]; a.M = outs_dev[2]; a.C = outs_dev[3]; a.chi = outs_dev[4];
+        launch_thermo(a, reinterpret_cast<double*>(scratch + o_lng), precision, s);
+        if (!out_on_device) {
+            for (int k = 0; k < 5; ++k)
+                if (outs_host[k])
+                    ISG_CUDA(cudaMemcpyAsync(outs_host[k], outs_dev[k], sizeof(double) * pts, cudaMemcpyDeviceToHost, s));
+        }
+        if (!out_on_device || !g_on_device) ISG_CUDA(cudaStreamSynchronize(s));
+        return ISG_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return ISG_ERR_NOMEM;
+    } catch (...) {
+        set_error("unexpected exception");
+        return ISG_ERR_INTERNAL;
+    }
+}

@@ -1,0 +1,251 @@
+"""Python binding of libisg: the C entry points of include/isg.h under the same names.
+
+Argument marshalling only -- every step of the computation runs in libisg's CUDA kernels.
+Device buffers are torch CUDA tensors (passed as raw pointers) and streams are torch streams
+(passed as cudaStream_t); PyTorch supplies memory and streams, nothing else. If libisg.so has
+not been built, every call raises RuntimeError: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+ISG_FP64, ISG_FP32 = 0, 1
+STATUS = {0: "ISG_OK", 1: "ISG_ERR_INVALID", 2: "ISG_ERR_TOO_LARGE", 3: "ISG_ERR_NOMEM", 4: "ISG_ERR_CUDA",
+          5: "ISG_ERR_TIMEOUT", 6: "ISG_ERR_BUSY", 7: "ISG_ERR_NOT_READY", 8: "ISG_ERR_INTERNAL"}
+
+
+class IsgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class isg_options(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in (
+        "struct_size", "max_spins", "inner_bits", "low_bits", "block_threads", "copies", "ctas_per_sm",
+        "flush_tasks", "shard_bits", "reserved0")] + [
+        ("shard_lo", ctypes.c_int64), ("shard_hi", ctypes.c_int64),
+        ("accumulate", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+_SIGS = {
+    "isg_options_init": (None, [vp]),
+    "isg_graph_create": (i32, [i32, i64, vp, vp, vp, ctypes.POINTER(vp)]),
+    "isg_graph_destroy": (None, [vp]),
+    "isg_graph_bins": (i32, [vp, vp, vp, vp, vp, vp]),
+    "isg_graph_size": (i32, [vp, vp, vp]),
+    "isg_enumerate": (i32, [vp, vp, vp, i32, vp]),
+    "isg_thermo": (i32, [vp, i32, vp, i32, vp, i32, vp, i32, vp, i32, vp, vp, vp, vp, vp]),
+    "isg_last_error": (ctypes.c_char_p, []),
+    "isg_version": (ctypes.c_char_p, []),
+    "isg_debug_plan": (i32, [vp, vp, i32, vp]),
+    "isg_debug_emulate": (i32, [vp, vp, vp]),
+    "isg_probe_peaks": (i32, [vp, vp, vp, vp]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded libisg.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                                   "(python -m paper_1110_2561_gb300.build); there is no fallback")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise IsgError(status, lib().isg_last_error().decode())
+
+
+def _options(**kw) -> isg_options:
+    o = isg_options()
+    lib().isg_options_init(ctypes.byref(o))
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k!r}")
+        setattr(o, k, int(v))
+    return o
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Graph:
+    """Owning handle of an isg_graph (freed with isg_graph_destroy)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.ptr = ptr
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.isg_graph_destroy(self.ptr)
+            self.ptr = None
+
+    @property
+    def _as_parameter_(self):
+        return ctypes.c_void_p(self.ptr)
+
+
+def isg_graph_create(n_spins: int, edges) -> Graph:
+    """Graph of n_spins spins from rows (i, j, J) (int arrays are copied)."""
+    e = np.asarray(edges, dtype=np.int64).reshape(-1, 3)
+    i = np.ascontiguousarray(e[:, 0], dtype=np.int32)
+    j = np.ascontiguousarray(e[:, 1], dtype=np.int32)
+    J = np.ascontiguousarray(e[:, 2], dtype=np.int32)
+    out = ctypes.c_void_p()
+    _check(lib().isg_graph_create(n_spins, len(i), i.ctypes.data, j.ctypes.data, J.ctypes.data, ctypes.byref(out)))
+    return Graph(out.value, n_spins)
+
+
+def isg_graph_destroy(graph: Graph):
+    if graph.ptr:
+        lib().isg_graph_destroy(graph.ptr)
+        graph.ptr = None
+
+
+def isg_graph_bins(graph: Graph):
+    """(e_min, e_step, n_e, m_min, n_m)."""
+    v = [ctypes.c_int32() for _ in range(5)]
+    _check(lib().isg_graph_bins(graph, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def isg_graph_size(graph: Graph):
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().isg_graph_size(graph, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def table_shape(graph: Graph):
+    _, _, n_e, _, n_m = isg_graph_bins(graph)
+    return n_e, n_m
+
+
+def isg_enumerate(graph: Graph, g_out=None, stream=None, **options):
+    """Exact g(E, M) of the graph (Sec. 2-3 of arXiv:1110.2561).
+
+    g_out: a torch int64 CUDA tensor of table_shape(graph) (filled asynchronously on `stream`),
+    a numpy int64 array (host; the call synchronises), or None for a new numpy array.
+    options: fields of isg_options (inner_bits, low_bits, block_threads, copies, ctas_per_sm,
+    flush_tasks, shard_bits, shard_lo, shard_hi, accumulate, max_spins)."""
+    shape = table_shape(graph)
+    o = _options(**options)
+    if g_out is None:
+        g_out = np.zeros(shape, dtype=np.int64)
+    if isinstance(g_out, np.ndarray):
+        if g_out.dtype != np.int64 or not g_out.flags.c_contiguous or g_out.shape != shape:
+            raise ValueError(f"g_out must be a C-contiguous int64 array of shape {shape}")
+        _check(lib().isg_enumerate(graph, _stream_handle(stream) if stream is not None else None,
+                                   g_out.ctypes.data, 0, ctypes.byref(o)))
+        return g_out
+    _check_tensor(g_out, shape, "int64")
+    _check(lib().isg_enumerate(graph, _stream_handle(stream), g_out.data_ptr(), 1, ctypes.byref(o)))
+    return g_out
+
+
+def _check_tensor(t, shape, dtype: str):
+    import torch
+    want = getattr(torch, dtype)
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == want and t.is_contiguous()
+            and tuple(t.shape) == tuple(shape)):
+        raise ValueError(f"expected a contiguous {dtype} CUDA tensor of shape {tuple(shape)}")
+
+
+def isg_thermo(g, graph: Graph, T, h, precision: int = ISG_FP64, stream=None, out=None):
+    """ln Z, <H>, <M>, C, chi on the grid T x h (Eq. 2 over g).
+
+    g: torch int64 CUDA tensor or numpy int64 array of table_shape(graph). out: None (numpy
+    results, the call synchronises) or a tuple of 5 float64 CUDA tensors of shape (len(T), len(h))
+    (filled asynchronously; None entries are skipped)."""
+    T = np.ascontiguousarray(np.atleast_1d(T), dtype=np.float64)
+    h = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
+    shape = table_shape(graph)
+    if isinstance(g, np.ndarray):
+        g = np.ascontiguousarray(g, dtype=np.int64)
+        if g.shape != shape:
+            raise ValueError(f"g must have shape {shape}")
+        g_ptr, g_dev = g.ctypes.data, 0
+    else:
+        _check_tensor(g, shape, "int64")
+        g_ptr, g_dev = g.data_ptr(), 1
+    s = _stream_handle(stream) if (stream is not None or g_dev or out is not None) else None
+    if out is None:
+        res = [np.zeros((len(T), len(h)), dtype=np.float64) for _ in range(5)]
+        ptrs = [r.ctypes.data for r in res]
+        _check(lib().isg_thermo(g_ptr, g_dev, graph, len(T), T.ctypes.data, len(h), h.ctypes.data, precision, s, 0,
+                                *ptrs))
+        return tuple(res)
+    ptrs = []
+    for t in out:
+        if t is None:
+            ptrs.append(None)
+        else:
+            _check_tensor(t, (len(T), len(h)), "float64")
+            ptrs.append(t.data_ptr())
+    _check(lib().isg_thermo(g_ptr, g_dev, graph, len(T), T.ctypes.data, len(h), h.ctypes.data, precision, s, 1,
+                            *ptrs))
+    return out
+
+
+def isg_debug_plan(graph: Graph, sms: int = 0, **options) -> dict:
+    out = np.zeros(13, dtype=np.int64)
+    o = _options(**options)
+    _check(lib().isg_debug_plan(graph, ctypes.byref(o), sms, out.ctypes.data))
+    keys = ("small", "q", "b", "tasks", "threads", "copies", "ctas_per_sm", "flush_rounds", "grid", "smem_bytes",
+            "G", "n_e_compact", "blob_bytes")
+    return dict(zip(keys, (int(x) for x in out)))
+
+
+def isg_debug_emulate(graph: Graph, **options) -> np.ndarray:
+    """The enumeration kernels' per-thread walk run on the host (small N only)."""
+    g = np.zeros(table_shape(graph), dtype=np.int64)
+    o = _options(**options)
+    _check(lib().isg_debug_emulate(graph, ctypes.byref(o), g.ctypes.data))
+    return g
+
+
+def isg_probe_peaks(stream=None) -> dict:
+    """Measured lane-op rates (per second, whole GPU) of red.shared (conflict-free, scattered) and ALU."""
+    v = [ctypes.c_double() for _ in range(3)]
+    _check(lib().isg_probe_peaks(_stream_handle(stream), *[ctypes.byref(x) for x in v]))
+    return {"red_conflict_free": v[0].value, "red_scattered": v[1].value, "alu": v[2].value}
+
+
+def isg_last_error() -> str:
+    return lib().isg_last_error().decode()
+
+
+def isg_version() -> str:
+    return lib().isg_version().decode()

@@ -25,3 +25,20 @@ def table1_triples():
                 nc, m, e = (int(x) for x in line.split())
                 rows.append((nc, m, e))
     return rows
+
+
+@pytest.fixture(scope="session")
+def isg():
+    """The native binding, with libisg.so built (build() is a no-op when it is up to date)."""
+    from paper_1110_2561_gb300 import build as _build, isg as _isg
+    _build.build()
+    _isg.lib()
+    return _isg
+
+
+@pytest.fixture(scope="session")
+def cuda(isg):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")

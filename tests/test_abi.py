@@ -1,0 +1,125 @@
+"""The C ABI on the CPU: the library loads, exports every declared entry point, validates its
+inputs, and its kernels' per-thread walk (run on the host by isg_debug_emulate) reproduces the
+oracle bit for bit over many plans. No GPU is used."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1110_2561_gb300 import workloads as w
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not hdr.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"ISG_API\s+[\w\s\*]+?\b(isg_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(isg):
+    names = declared_functions()
+    assert "isg_enumerate" in names and "isg_thermo" in names and "isg_graph_create" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", isg.library_path()], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (isg_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+    lib = isg.lib()
+    for n in names:
+        assert getattr(lib, n) is not None
+
+
+def test_version(isg):
+    assert "sm_103a" in isg.isg_version()
+
+
+@pytest.mark.parametrize("n,edges,msg", [
+    (0, [], "n_spins"), (65, [], "n_spins"), (3, [(0, 3, 1)], "out of range"), (3, [(1, 1, 1)], "self loop"),
+    (3, [(0, 1, 0)], "J = 0"), (3, [(0, 1, (1 << 20) + 1)], "2^20"), (3, [(0, 1, 1 << 20), (0, 1, 1 << 20)], "2^20")])
+def test_graph_validation(isg, n, edges, msg):
+    with pytest.raises(isg.IsgError) as ei:
+        isg.isg_graph_create(n, edges)
+    assert ei.value.status == 1 and msg in str(ei.value)
+
+
+def test_bins_geometry(isg):
+    for lat in [w.square(4, 4, True), w.square(4, 4, False), w.random_graph(9, 20, w.SplitMix64(2))]:
+        g = isg.isg_graph_create(lat.n, lat.edges)
+        e_min, n_e, n_m = oracle.bins(lat.n, lat.edges)
+        assert isg.isg_graph_bins(g) == (e_min, 2, n_e, -lat.n, n_m)
+
+
+def test_duplicate_bonds_summed(isg):
+    g = isg.isg_graph_create(3, [(0, 1, 1), (1, 0, 1), (1, 2, 3), (2, 1, -3)])
+    assert isg.isg_graph_size(g) == (3, 1)
+    assert isg.isg_graph_bins(g)[:3] == (-2, 2, 3)
+
+
+def test_options_validation(isg):
+    g = isg.isg_graph_create(16, w.square(4, 4, True).edges)
+    for bad in [dict(shard_bits=17), dict(shard_bits=2, shard_lo=3, shard_hi=2), dict(shard_bits=2, shard_lo=0, shard_hi=5),
+                dict(low_bits=7), dict(inner_bits=12), dict(block_threads=48), dict(copies=99)]:
+        with pytest.raises(isg.IsgError) as ei:
+            isg.isg_debug_plan(g, **bad)
+        assert ei.value.status == 1, bad
+    with pytest.raises(isg.IsgError) as ei:
+        isg.isg_debug_plan(g, max_spins=15)
+    assert ei.value.status == 2
+
+
+def test_plan_torus_6x6(isg):
+    """The 6x6 torus plan: energy stride 4 compacts 73 energy bins to 37; the low block is an
+    independent set of 6 spins; the inner walk and task count cover 2^36 configurations."""
+    g = isg.isg_graph_create(36, w.square(6, 6, True).edges)
+    p = isg.isg_debug_plan(g)
+    assert p["small"] == 0 and p["G"] == 4 and p["n_e_compact"] == 37 and p["b"] == 6
+    assert p["tasks"] * 32 << p["q"] == 1 << 36
+    assert p["flush_rounds"] >= 1
+
+
+EMU_GRAPHS = [w.square(4, 4, True), w.square(4, 4, False), w.square(3, 5, True), w.triangular(4, 4, True),
+              w.cubic(2, 2, 4, True), w.ring(13),
+              w.with_random_couplings(w.square(4, 4, True), w.SplitMix64(1), (-1, 1)),
+              w.with_random_couplings(w.triangular(3, 5, False), w.SplitMix64(2), (-2, -1, 1, 2)),
+              w.random_graph(14, 30, w.SplitMix64(3)), w.random_graph(13, 60, w.SplitMix64(4)),
+              w.random_graph(12, 12, w.SplitMix64(5), couplings=(-7, 3, 5, 11, 13, 1000)),
+              w.induced_lattice("cubic", 17, True, w.SplitMix64(6)), w.lattice("square", (1, 12), True)]
+EMU_PLANS = [{}, dict(inner_bits=6), dict(low_bits=1, inner_bits=3), dict(low_bits=3, inner_bits=5),
+             dict(low_bits=2, inner_bits=2), dict(shard_bits=2, shard_lo=1, shard_hi=3), dict(shard_bits=4, shard_lo=9, shard_hi=10)]
+
+
+@pytest.mark.parametrize("lat", EMU_GRAPHS, ids=lambda l: l.name)
+def test_emulated_walk_matches_oracle(isg, lat):
+    """Every plan of the GPU walk, run on the host with bounds-checked counters, equals the oracle."""
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    full = oracle.g_masks(lat.n, lat.edges)
+    for kw in EMU_PLANS:
+        if "shard_bits" in kw:
+            k = kw["shard_bits"]
+            ref = oracle.g_masks(lat.n, lat.edges, kw["shard_lo"] << (lat.n - k), kw["shard_hi"] << (lat.n - k))
+        else:
+            ref = full
+        try:
+            got = isg.isg_debug_emulate(g, **kw)
+        except isg.IsgError as e:       # a forced plan this graph cannot take (e.g. no independent set)
+            assert e.status == 1, (kw, e)
+            continue
+        assert np.array_equal(got, ref), kw
+
+
+def test_emulated_accumulate(isg):
+    lat = w.square(3, 4, True)
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    ref = oracle.g_masks(lat.n, lat.edges)
+    a = isg.isg_debug_emulate(g, shard_bits=1, shard_lo=0, shard_hi=1)
+    b = isg.isg_debug_emulate(g, shard_bits=1, shard_lo=1, shard_hi=2)
+    assert np.array_equal(a + b, ref)

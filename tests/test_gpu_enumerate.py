@@ -1,0 +1,153 @@
+"""GPU parity of isg_enumerate against the CPU oracle: bit-exact int64 tables.
+
+Small graphs are compared in full; the full-size workloads (6x6 torus, 3x3x4 cubic torus,
+N = 36) run in the same launch configuration as the benchmark and are checked against the
+exact frontier programme of the oracle (6x6), against the oracle on sampled shards, and against
+invariants that hold at any size (sum 2^N, binomial columns, the M mirror, ground states)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1110_2561_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 1
+
+
+def gpu_table(isg, cuda, lat, **opt):
+    import torch
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    out = torch.zeros(isg.table_shape(g), dtype=torch.int64, device=cuda)
+    isg.isg_enumerate(g, out, **opt)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def check_invariants(g: np.ndarray, n: int):
+    assert int(g.sum()) == 2 ** n
+    for m in range(n + 1):
+        assert int(g[:, m].sum()) == math.comb(n, m)
+    assert np.array_equal(g, g[:, ::-1])
+    assert (g >= 0).all()
+
+
+SMALL = [w.square(4, 4, False), w.square(4, 4, True), w.square(3, 5, True), w.triangular(4, 4, True),
+         w.cubic(2, 2, 4, True), w.ring(13), w.ring(5), w.square(1, 2, False),
+         w.with_random_couplings(w.square(4, 5, True), w.SplitMix64(1), (-1, 1)),
+         w.with_random_couplings(w.triangular(4, 5, False), w.SplitMix64(2), (-2, -1, 1, 2)),
+         w.random_graph(18, 40, w.SplitMix64(3)), w.random_graph(16, 90, w.SplitMix64(4)),
+         w.random_graph(15, 15, w.SplitMix64(5), couplings=(-7, 3, 5, 11, 13, 1000)),
+         w.induced_lattice("cubic", 19, True, w.SplitMix64(6)), w.lattice("square", (1, 14), True)]
+
+
+@pytest.mark.parametrize("lat", SMALL, ids=lambda l: l.name)
+def test_small_graphs_device_and_host(isg, cuda, lat):
+    ref = oracle.g_masks(lat.n, lat.edges)
+    assert np.array_equal(gpu_table(isg, cuda, lat), ref)
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    assert np.array_equal(isg.isg_enumerate(g), ref)          # host buffer: synchronous, self-checked
+
+
+def test_single_and_isolated_spins(isg, cuda):
+    for n in (1, 2, 3, 7):
+        g = isg.isg_graph_create(n, np.zeros((0, 3), np.int64))
+        ref = oracle.g_edges(n, np.zeros((0, 3), np.int64))
+        assert np.array_equal(isg.isg_enumerate(g), ref)
+    lat = w.Lattice(20, np.array([(0, 1, 1), (5, 9, -2), (17, 3, 1)], dtype=np.int64))
+    assert np.array_equal(gpu_table(isg, cuda, lat), oracle.g_masks(lat.n, lat.edges))
+
+
+def test_table1_on_gpu(isg, cuda, table1_triples):
+    """Table 1 of the paper from the GPU: the 4x4 periodic ferromagnet, all 80 cells."""
+    lat = w.square(4, 4, True)
+    g = gpu_table(isg, cuda, lat)
+    e_min = -32
+    got = {(e_min + 2 * int(e), -16 + 2 * int(m)): int(g[e, m]) for e, m in zip(*np.nonzero(g))}
+    assert got == {(E, M): nc for nc, M, E in table1_triples}
+
+
+PLANS = [dict(inner_bits=6), dict(low_bits=1, inner_bits=4), dict(low_bits=4, inner_bits=9), dict(low_bits=6, inner_bits=12),
+         dict(block_threads=64, copies=1), dict(block_threads=1024, copies=32), dict(block_threads=256, copies=3),
+         dict(flush_tasks=1), dict(ctas_per_sm=1, flush_tasks=1, block_threads=96, copies=2), dict(low_bits=2, inner_bits=2)]
+
+
+@pytest.mark.parametrize("kw", PLANS, ids=lambda k: ",".join(f"{a}={b}" for a, b in k.items()))
+def test_plan_invariance(isg, cuda, kw):
+    """Every planner choice gives the same table (forced tiny flush intervals included)."""
+    lat = w.with_random_couplings(w.triangular(4, 5, True), w.SplitMix64(8), (-2, -1, 1, 2))
+    ref = oracle.g_masks(lat.n, lat.edges, threads=THREADS)
+    assert np.array_equal(gpu_table(isg, cuda, lat, **kw), ref)
+
+
+def test_shards_and_accumulate(isg, cuda):
+    import torch
+    lat = w.with_random_couplings(w.square(4, 5, True), w.SplitMix64(9), (-1, 1))
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    out = torch.zeros(isg.table_shape(g), dtype=torch.int64, device=cuda)
+    for lo, hi in [(0, 3), (3, 4), (4, 16)]:
+        isg.isg_enumerate(g, out, shard_bits=4, shard_lo=lo, shard_hi=hi, accumulate=1)
+        torch.cuda.synchronize()
+        part = isg.isg_enumerate(g, shard_bits=4, shard_lo=lo, shard_hi=hi)
+        assert np.array_equal(part, oracle.g_masks(lat.n, lat.edges, lo << 16, hi << 16))
+    assert np.array_equal(out.cpu().numpy(), oracle.g_masks(lat.n, lat.edges))
+
+
+def test_rejections(isg, cuda):
+    g = isg.isg_graph_create(41, w.random_graph(41, 60, w.SplitMix64(1)).edges)
+    with pytest.raises(isg.IsgError) as ei:
+        isg.isg_enumerate(g)
+    assert ei.value.status == 2
+    big = w.ring(30, J=1 << 20)           # 2^20-sized couplings: far too many energy bins for shared memory
+    with pytest.raises(isg.IsgError) as ei:
+        isg.isg_enumerate(isg.isg_graph_create(big.n, big.edges))
+    assert ei.value.status == 2
+
+
+# ----------------------------------------------------------------------------------- full size
+def test_torus_6x6_full_against_frontier_oracle(isg, cuda):
+    """6x6 periodic ferromagnet, N = 36, 2^36 configurations, default (benchmark) plan: every one
+    of the table's bins equals the oracle's exact frontier programme."""
+    lat = w.square(6, 6, True)
+    got = gpu_table(isg, cuda, lat)
+    ref = oracle.g_frontier(lat.n, lat.edges, max_active=16)
+    assert np.array_equal(got, ref)
+    check_invariants(got, 36)
+
+
+def test_torus_6x6_sampled_shards(isg, cuda):
+    """Shards of the 6x6 torus in the benchmark's inner-bit split, against the popcount oracle."""
+    lat = w.square(6, 6, True)
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    q = isg.isg_debug_plan(g)["q"]
+    for shard in (0, 777, 4095):
+        got = isg.isg_enumerate(g, shard_bits=12, shard_lo=shard, shard_hi=shard + 1, inner_bits=q)
+        ref = oracle.g_masks(lat.n, lat.edges, shard << 24, (shard + 1) << 24, threads=THREADS)
+        assert np.array_equal(got, ref)
+
+
+def test_cubic_3x3x4_full_invariants_and_shards(isg, cuda):
+    """3x3x4 simple cubic torus (Z = 6, 108 bonds), N = 36: full table by invariants and ground
+    states, and sampled shards in the benchmark's split against the oracle bit for bit."""
+    lat = w.cubic(3, 3, 4, True)
+    full = gpu_table(isg, cuda, lat)
+    check_invariants(full, 36)
+    assert full[0, 0] == 1 and full[0, 36] == 1 and full[0].sum() == 2
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    q = isg.isg_debug_plan(g)["q"]
+    tot = np.zeros_like(full)
+    rng = w.SplitMix64(4)
+    for shard in sorted({rng.below(4096) for _ in range(6)}):
+        got = isg.isg_enumerate(g, shard_bits=12, shard_lo=shard, shard_hi=shard + 1, inner_bits=q)
+        ref = oracle.g_masks(lat.n, lat.edges, shard << 24, (shard + 1) << 24, threads=THREADS)
+        assert np.array_equal(got, ref)
+        tot += got
+    assert (tot <= full).all()
+
+
+def test_largest_default_size_n40(isg, cuda):
+    """N = 40 (the default max_spins): 2^40 configurations; invariants at full size."""
+    lat = w.with_random_couplings(w.square(5, 8, True), w.SplitMix64(40), (-2, -1, 1, 2))
+    check_invariants(gpu_table(isg, cuda, lat), 40)

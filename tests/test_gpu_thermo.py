@@ -1,0 +1,107 @@
+"""GPU thermodynamics (isg_thermo) against the oracle's direct evaluation of Eq. (2), and the
+FP32 path against the FP64 path within the stated bounds."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1110_2561_gb300 import workloads as w
+from closed_forms import kaufman_logz
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_close(a, b, rtol, atol):
+    return np.all(np.abs(a - b) <= rtol * np.abs(b) + atol)
+
+
+def fp64_vs_oracle(isg, lat, T, h, sample=None):
+    g_ref = oracle.g_masks(lat.n, lat.edges) if lat.n <= 24 else oracle.g_frontier(lat.n, lat.edges, 16)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    got = isg.isg_thermo(g_ref, gh, T, h, isg.ISG_FP64)
+    ref = oracle.thermo(lat.n, e_min, g_ref, T, h)
+    names = ["logZ", "E", "M", "C", "chi"]
+    for k, (a, b) in enumerate(zip(got, ref)):
+        # <M> vanishes at h = 0 by symmetry: absolute tolerance 1e-12 N there
+        assert rel_close(a, b, 1e-12, 1e-12 * lat.n), (names[k], np.max(np.abs(a - b) / (np.abs(b) + 1e-300)))
+    return got, g_ref, gh
+
+
+@pytest.mark.parametrize("lat", [w.square(4, 4, False), w.ring(11), w.with_random_couplings(w.triangular(3, 5, True), w.SplitMix64(3), (-2, -1, 1, 2)),
+                                 w.Lattice(6, np.zeros((0, 3), np.int64))], ids=lambda l: l.name or "free")
+def test_fp64_small(isg, cuda, lat):
+    T = np.linspace(0.5, 5, 64)
+    h = np.array([-2.0, -0.3, 0.0, 0.1, 1.7])
+    fp64_vs_oracle(isg, lat, T, h)
+
+
+def test_config_4x4_free_fp64(isg, cuda):
+    """4x4 free ferromagnet, 64 temperatures in [0.5, 5] at h = 0, FP64."""
+    fp64_vs_oracle(isg, w.square(4, 4, False), np.linspace(0.5, 5, 64), np.array([0.0]))
+
+
+def test_torus_6x6_kaufman(isg, cuda):
+    """6x6 torus: ln Z from the GPU table and GPU thermodynamics against Kaufman's closed form on
+    256 temperatures in [0.5, 5], h = 0, FP64."""
+    import torch
+    lat = w.square(6, 6, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=cuda)
+    isg.isg_enumerate(gh, g)
+    T = np.linspace(0.5, 5, 256)
+    lz = isg.isg_thermo(g, gh, T, [0.0], isg.ISG_FP64)[0][:, 0]
+    ref = np.array([kaufman_logz(6, 6, t) for t in T])
+    assert np.max(np.abs(lz - ref) / np.abs(ref)) <= 1e-12
+
+
+def test_cubic_grid_fp32_vs_fp64(isg, cuda):
+    """3x3x4 cubic torus on the 512 x 256 (T, h) grid: FP64 against the oracle on sampled points,
+    FP32 against FP64 everywhere within the bounds |dlnZ| <= 2e-5, |d<E>| <= 1e-5 (S + N |h|max),
+    |d<M>| <= 1e-5 N, C and chi within 1e-3 relative (or 1e-3 of the grid maximum)."""
+    lat = w.cubic(3, 3, 4, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = isg.isg_enumerate(gh)
+    T = np.linspace(0.5, 8, 512)
+    h = np.linspace(-2, 2, 256)
+    d = isg.isg_thermo(g, gh, T, h, isg.ISG_FP64)
+    f = isg.isg_thermo(g, gh, T, h, isg.ISG_FP32)
+    rng = w.SplitMix64(12)
+    pts = [(rng.below(512), rng.below(256)) for _ in range(24)]
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    for a, b in pts:
+        ref = oracle.thermo(lat.n, e_min, g, T[a:a + 1], h[b:b + 1])
+        for k in range(5):
+            assert abs(d[k][a, b] - ref[k][0, 0]) <= 1e-12 * abs(ref[k][0, 0]) + 1e-12 * lat.n, (k, a, b)
+    S, N = 108, 36
+    assert np.max(np.abs(f[0] - d[0])) <= 2e-5
+    assert np.max(np.abs(f[1] - d[1])) <= 1e-5 * (S + N * 2)
+    assert np.max(np.abs(f[2] - d[2])) <= 1e-5 * N
+    for k in (3, 4):
+        scale = np.max(np.abs(d[k]))
+        err = np.abs(f[k] - d[k])
+        assert np.all(err <= np.maximum(1e-3 * np.abs(d[k]), 1e-3 * scale)), k
+
+
+def test_thermo_device_outputs(isg, cuda):
+    import torch
+    lat = w.square(4, 4, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=cuda)
+    isg.isg_enumerate(gh, g)
+    T = np.linspace(1, 3, 7)
+    h = np.linspace(-1, 1, 5)
+    outs = tuple(torch.empty((7, 5), dtype=torch.float64, device=cuda) for _ in range(5))
+    isg.isg_thermo(g, gh, T, h, isg.ISG_FP64, out=outs)
+    torch.cuda.synchronize()
+    ref = isg.isg_thermo(g.cpu().numpy(), gh, T, h, isg.ISG_FP64)
+    for a, b in zip(outs, ref):
+        assert np.array_equal(a.cpu().numpy(), b)
+
+
+def test_thermo_rejects_bad_grid(isg, cuda):
+    gh = isg.isg_graph_create(4, w.ring(4).edges)
+    g = np.zeros(isg.table_shape(gh), np.int64)
+    with pytest.raises(isg.IsgError):
+        isg.isg_thermo(g, gh, [0.0], [0.0])
+    with pytest.raises(isg.IsgError):
+        isg.isg_thermo(g, gh, [1.0], [np.nan])
