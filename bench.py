@@ -140,10 +140,12 @@ def run_isg(args):
         dist.init_process_group("nccl", device_id=dev)
 
     lat = workloads.square(6, 6, True)
-    n_configs = 1 << lat.n
     gh = isg.isg_graph_create(lat.n, lat.edges)
     shape = isg.table_shape(gh)
     plan = isg.isg_debug_plan(gh)
+    # --shard-bits k (profiling case): each step enumerates shard 0 of 2^k, same kernel and split
+    shard = dict(shard_bits=args.shard_bits, shard_lo=0, shard_hi=1, inner_bits=plan["q"]) if args.shard_bits else {}
+    n_configs = 1 << (lat.n - args.shard_bits)
     stream = torch.cuda.current_stream()
     g = torch.zeros(shape, dtype=torch.int64, device=dev)
     outs = tuple(torch.empty((len(T_GRID), 1), dtype=torch.float64, device=dev) for _ in range(5))
@@ -154,7 +156,7 @@ def run_isg(args):
     def step(ev=None):
         if ev:
             ev[0].record(stream)
-        isg.isg_enumerate(gh, g, stream)
+        isg.isg_enumerate(gh, g, stream, **shard)
         if ev:
             ev[1].record(stream)
         isg.isg_thermo(g, gh, T_GRID, H_GRID, isg.ISG_FP64, stream, out=outs)
@@ -166,7 +168,9 @@ def run_isg(args):
     torch.cuda.synchronize()
     # correctness of the last warm-up result (cheap invariants; parity lives in the tests)
     gc = g.cpu().numpy()
-    assert int(gc.sum()) == n_configs and all(int(gc[:, m].sum()) == math.comb(lat.n, m) for m in range(lat.n + 1))
+    assert int(gc.sum()) == n_configs
+    if not shard:
+        assert all(int(gc[:, m].sum()) == math.comb(lat.n, m) for m in range(lat.n + 1))
 
     evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(args.steps)]
     if world > 1:
@@ -198,7 +202,7 @@ def run_isg(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        gh_host = isg.isg_enumerate(gh, None, stream)                       # host table: D2H inside
+        gh_host = isg.isg_enumerate(gh, None, stream, **shard)              # host table: D2H inside
         isg.isg_thermo(gh_host, gh, T_GRID, H_GRID, isg.ISG_FP64, stream)  # host g: H2D inside, host outputs
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if world > 1:
@@ -221,7 +225,8 @@ def run_isg(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": world, "seq_len": None,
+            "config": {"workload": WORKLOAD if not shard else f"shard 0 of 2^{args.shard_bits} of: " + WORKLOAD,
+                       "global_batch": world, "seq_len": None,
                        "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)",
                        "plan": {k: plan[k] for k in ("q", "b", "tasks", "threads", "copies", "G", "n_e_compact")}},
             "roofline": {"bound": "alu", "achieved": achieved_ops / 1e9, "peak": alu_peak / 1e9, "unit": "Gop/s",
@@ -328,6 +333,8 @@ def main():
     ap.add_argument("--impl", choices=("isg", "reference"), default="isg")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target seconds of the oracle sample")
+    ap.add_argument("--shard-bits", type=int, default=0,
+                    help="profiling case: enumerate only shard 0 of 2^k per step (not a benchmark line)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "isg":
         ap.error("at least 3 warm-up steps")

@@ -21,6 +21,7 @@
 // sE = 8 n_m / G bytes: dE = 2 S_k h_k gives de' = 2 S_k h_k / G, and dm = -S_k.
 #pragma once
 #include <cstdint>
+#include <utility>
 
 #if defined(__CUDACC__)
 #define ISG_HD __host__ __device__ __forceinline__
@@ -127,20 +128,31 @@ ISG_HD uint32_t bin_offset(const ProgView& p, uint64_t st) {
     return static_cast<uint32_t>((ec * p.n_m + popc64(st)) * 4);
 }
 
-// One low block: count the current configuration, then 2^B - 1 Gray flips inside the block, each
-// followed by a count. ODD blocks start from low state 2^(B-1) instead of 0 (the reflected code
-// alternates), which reverses the direction of the flip of spin B-1 only.
+// One Gray step inside a low block, fully resolved at compile time: step U flips spin k =
+// ctz(U); its state before the flip is bit k of gray(U - 1), with spin B-1 inverted in ODD
+// blocks (the reflected code starts those from low state 2^(B-1) instead of 0). Spin k going
+// up -> down moves the address by +G_k, down -> up by -G_k; then the configuration is counted.
+template <int B, bool ODD, int U, class Sink>
+ISG_HD void low_step(uint32_t& idx, const int32_t (&Gk)[B], Sink& sink) {
+    constexpr int k = ctz_c(U);
+    constexpr int before = gray_c(U - 1) ^ (ODD ? (1 << (B - 1)) : 0);
+    if constexpr (((before >> k) & 1) != 0) idx += static_cast<uint32_t>(Gk[k]);
+    else idx -= static_cast<uint32_t>(Gk[k]);
+    sink(idx);
+}
+
+template <int B, bool ODD, class Sink, int... U>
+ISG_HD void low_steps(uint32_t& idx, const int32_t (&Gk)[B], Sink& sink, std::integer_sequence<int, U...>) {
+    (low_step<B, ODD, U + 1>(idx, Gk, sink), ...);
+}
+
+// One low block: count the current configuration, then the 2^B - 1 Gray flips of the low spins,
+// each followed by a count (a fold over a compile-time sequence, so every flip site, sign and
+// register index is a constant).
 template <int B, bool ODD, class Sink>
 ISG_HD void low_block(uint32_t& idx, const int32_t (&Gk)[B], Sink& sink) {
     sink(idx);
-#pragma unroll
-    for (int u = 1; u < (1 << B); ++u) {
-        const int k = ctz_c(u);
-        const int before = gray_c(u - 1) ^ (ODD ? (1 << (B - 1)) : 0);
-        if ((before >> k) & 1) idx += static_cast<uint32_t>(Gk[k]);   // spin k up -> down
-        else idx -= static_cast<uint32_t>(Gk[k]);                     // spin k down -> up
-        sink(idx);
-    }
+    low_steps<B, ODD>(idx, Gk, sink, std::make_integer_sequence<int, (1 << B) - 1>{});
 }
 
 // Flip spin r (r >= B) of st: the address moves by S_r (h_r sE - 4) (dE = 2 S_r h_r, dm = -S_r),

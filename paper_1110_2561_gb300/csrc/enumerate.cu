@@ -63,7 +63,7 @@ __device__ __forceinline__ void flush_bins(const ProgHeader* hd, uint32_t* hist,
 }
 
 template <int B>
-__global__ void __launch_bounds__(512) enumerate_kernel(EnumArgs a) {
+__global__ void __launch_bounds__(1024) enumerate_kernel(EnumArgs a) {
     extern __shared__ __align__(16) uint64_t smem[];
     stage_blob(smem, a.blob, a.blob_words);
     uint32_t* hist = reinterpret_cast<uint32_t*>(smem + ((a.blob_words + 1) & ~1));

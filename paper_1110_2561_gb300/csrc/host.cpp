@@ -100,15 +100,22 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d) {
     int bmax = o.low_bits > 0 ? o.low_bits : kMaxLow;
     if (bmax > kMaxLow) fail(ISG_ERR_INVALID, "low_bits must be <= 6");
     bmax = std::min(bmax, free - 5);
-    std::vector<int> cand(free);
-    std::iota(cand.begin(), cand.end(), 0);
-    std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) { return g.degree[a] < g.degree[b]; });
+    // Minimum-residual-degree greedy: repeatedly take the candidate with the fewest neighbours
+    // among the remaining candidates (ties: lowest index), then drop it and its neighbours.
+    std::vector<char> alive(free, 1);
     std::vector<int> low;
-    for (int c : cand) {
-        if ((int)low.size() >= bmax) break;
-        bool ok = true;
-        for (int l : low) if (g.K[(size_t)c * n + l] != 0) { ok = false; break; }
-        if (ok) low.push_back(c);
+    while ((int)low.size() < bmax) {
+        int best = -1, best_deg = 1 << 30;
+        for (int c = 0; c < free; ++c) {
+            if (!alive[c]) continue;
+            int d = 0;
+            for (int o = 0; o < free; ++o) if (alive[o] && o != c && g.K[(size_t)c * n + o] != 0) ++d;
+            if (d < best_deg) { best_deg = d; best = c; }
+        }
+        if (best < 0) break;
+        low.push_back(best);
+        alive[best] = 0;
+        for (int o = 0; o < free; ++o) if (g.K[(size_t)best * n + o] != 0) alive[o] = 0;
     }
     std::sort(low.begin(), low.end());
     if (o.low_bits > 0 && (int)low.size() < o.low_bits)
@@ -129,7 +136,10 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d) {
         if (p.q < p.b || p.q > free - 5 || p.q > 26)
             fail(ISG_ERR_INVALID, "inner_bits must satisfy low block <= q <= N - shard_bits - 5 and q <= 26");
     } else {
-        int q = free - 5 - std::max(0, 17 - shards_log2);
+        // about 2^15 warp tasks (several per resident warp, so the dynamic queue balances), but at
+        // least 2^12 configurations per lane so the from-scratch start of a task stays negligible
+        int q = free - 5 - std::max(0, 15 - shards_log2);
+        q = std::max(q, std::min(12, free - 5));
         q = std::min(q, 20);
         q = std::min(q, free - 5);
         p.q = std::max(q, p.b);

@@ -10,28 +10,33 @@
 
 namespace isg {
 
-constexpr int kProbeWords = 2048;   // words per warp table (power of two)
+constexpr int kProbeWords = 2048;   // words per warp table (power of two); two warps share one
 
+// MODE 0: each lane adds to 32 words of its own bank (lane + 32 j), addresses held in registers,
+// so the loop is nothing but reductions. MODE 1: 32 scattered per-lane addresses in registers
+// (independent odd strides per lane), the same reductions with bank conflicts. MODE 2: integer
+// ALU, four independent xor/add chains.
 template <int MODE>
 __global__ void __launch_bounds__(512) probe_kernel(int iters, unsigned* sink) {
     extern __shared__ unsigned tbl[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned* t = tbl + warp * kProbeWords;
+    unsigned* t = tbl + (warp >> 1) * kProbeWords;     // warps 2w and 2w+1 share table w
     for (int i = lane; i < kProbeWords; i += 32) t[i] = 0;
     __syncthreads();
     const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(t));
-    unsigned a = (lane * 97u) & (kProbeWords - 1);
-    const unsigned s = ((lane * 2654435761u) >> 7) | 1u;
     unsigned x0 = lane, x1 = lane * 3u, x2 = lane * 5u, x3 = lane * 7u;
-    for (int i = 0; i < iters; ++i) {
-        if (MODE == 0) {          // conflict-free: lane l always in bank l
-            uint32_t ad = base + 4u * ((((unsigned)i & 63u) << 5) | lane);
-            asm volatile("red.shared.add.u32 [%0], 1;" : "+r"(ad) : : "memory");
-        } else if (MODE == 1) {   // scattered: independent strides per lane
-            a = (a + s) & (kProbeWords - 1);
-            uint32_t ad = base + 4u * a;
-            asm volatile("red.shared.add.u32 [%0], 1;" : "+r"(ad) : : "memory");
-        } else {                  // integer ALU: 4 independent xor/add chains
+    if (MODE == 0 || MODE == 1) {
+        uint32_t a[32];
+        const unsigned s = ((lane * 2654435761u) >> 7) | 1u;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            a[j] = base + 4u * (MODE == 0 ? (unsigned)(lane + 32 * j) : ((lane * 97u + j * s) & (kProbeWords - 1)));
+        for (int i = 0; i < iters; i += 32) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a[j]) : "memory");
+        }
+    } else {
+        for (int i = 0; i < iters; ++i) {
             x0 = (x0 ^ x1) + i; x1 = (x1 ^ x2) + i; x2 = (x2 ^ x3) + i; x3 = (x3 ^ x0) + i;
         }
     }
@@ -49,23 +54,23 @@ __global__ void __launch_bounds__(512) probe_kernel(int iters, unsigned* sink) {
 
 template <int MODE>
 static double probe_rate(cudaStream_t s, unsigned* sink, int sms, double ops_per_iter) {
-    const int threads = 512, iters = 1 << 16;
-    const size_t smem = (size_t)(threads / 32) * kProbeWords * 4;
+    const int threads = 512, iters = 1 << 16, per_sm = 3;   // 3 x 64 KB tables: 48 warps per SM
+    const size_t smem = (size_t)(threads / 32) * kProbeWords * 4 / 2;
     ISG_CUDA(cudaFuncSetAttribute(probe_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    probe_kernel<MODE><<<sms, threads, smem, s>>>(iters, sink);      // warm-up
+    probe_kernel<MODE><<<sms * per_sm, threads, smem, s>>>(iters, sink);      // warm-up
     ISG_CUDA(cudaGetLastError());
     cudaEvent_t e0, e1;
     ISG_CUDA(cudaEventCreate(&e0));
     ISG_CUDA(cudaEventCreate(&e1));
     ISG_CUDA(cudaEventRecord(e0, s));
-    probe_kernel<MODE><<<sms, threads, smem, s>>>(iters, sink);
+    probe_kernel<MODE><<<sms * per_sm, threads, smem, s>>>(iters, sink);
     ISG_CUDA(cudaEventRecord(e1, s));
     ISG_CUDA(cudaEventSynchronize(e1));
     float ms = 0;
     ISG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    return (double)sms * threads * iters * ops_per_iter / (ms * 1e-3);
+    return (double)sms * per_sm * threads * iters * ops_per_iter / (ms * 1e-3);
 }
 
 }  // namespace isg

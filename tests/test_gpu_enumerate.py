@@ -39,7 +39,7 @@ SMALL = [w.square(4, 4, False), w.square(4, 4, True), w.square(3, 5, True), w.tr
          w.with_random_couplings(w.square(4, 5, True), w.SplitMix64(1), (-1, 1)),
          w.with_random_couplings(w.triangular(4, 5, False), w.SplitMix64(2), (-2, -1, 1, 2)),
          w.random_graph(18, 40, w.SplitMix64(3)), w.random_graph(16, 90, w.SplitMix64(4)),
-         w.random_graph(15, 15, w.SplitMix64(5), couplings=(-7, 3, 5, 11, 13, 1000)),
+         w.random_graph(15, 15, w.SplitMix64(5), couplings=(-7, 3, 5, 11, 13, 100)),
          w.induced_lattice("cubic", 19, True, w.SplitMix64(6)), w.lattice("square", (1, 14), True)]
 
 
@@ -69,8 +69,8 @@ def test_table1_on_gpu(isg, cuda, table1_triples):
     assert got == {(E, M): nc for nc, M, E in table1_triples}
 
 
-PLANS = [dict(inner_bits=6), dict(low_bits=1, inner_bits=4), dict(low_bits=4, inner_bits=9), dict(low_bits=6, inner_bits=12),
-         dict(block_threads=64, copies=1), dict(block_threads=1024, copies=32), dict(block_threads=256, copies=3),
+PLANS = [dict(inner_bits=6), dict(low_bits=1, inner_bits=4), dict(low_bits=4, inner_bits=9), dict(low_bits=5, inner_bits=12),
+         dict(block_threads=64, copies=1), dict(block_threads=1024, copies=16), dict(block_threads=256, copies=3),
          dict(flush_tasks=1), dict(ctas_per_sm=1, flush_tasks=1, block_threads=96, copies=2), dict(low_bits=2, inner_bits=2)]
 
 
@@ -103,6 +103,10 @@ def test_rejections(isg, cuda):
     big = w.ring(30, J=1 << 20)           # 2^20-sized couplings: far too many energy bins for shared memory
     with pytest.raises(isg.IsgError) as ei:
         isg.isg_enumerate(isg.isg_graph_create(big.n, big.edges))
+    assert ei.value.status == 2
+    odd = w.random_graph(15, 15, w.SplitMix64(5), couplings=(-7, 3, 5, 11, 13, 1000))   # 81488 bins
+    with pytest.raises(isg.IsgError) as ei:
+        isg.isg_enumerate(isg.isg_graph_create(odd.n, odd.edges))
     assert ei.value.status == 2
 
 

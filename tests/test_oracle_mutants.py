@@ -1,6 +1,10 @@
 """Mutation tests: plant plausible mistakes in a copy of the oracle (on the CPU) and check that
-the pins fail for every one of them. The oracle itself is never modified."""
+the pins fail for every one of them. The oracle itself is never modified. Each mutant runs in a
+child process: a mutant that writes outside its table may crash, which also counts as caught."""
 import math
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -88,14 +92,41 @@ def pins_pass(lib, table1_triples) -> bool:
     return True
 
 
-def test_unmutated_copy_passes(tmp_path, table1_triples):
-    lib = oracle.load_variant(oracle.source(), str(tmp_path))
-    assert pins_pass(lib, table1_triples)
+def run_child(index: int, workdir: str) -> int:
+    """Exit status of a child that compiles mutant `index` (-1: no mutation) and runs the pins:
+    0 = every pin passed, 1 = a pin failed, anything else = the child crashed."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    env = dict(os.environ, PYTHONPATH=os.pathsep.join([os.path.dirname(here), here]))
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), str(index), workdir], env=env,
+                       capture_output=True, text=True, timeout=300)
+    return r.returncode
 
 
-@pytest.mark.parametrize("name,orig,bad", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_mutant_is_caught(tmp_path, table1_triples, name, orig, bad):
+def test_unmutated_copy_passes(tmp_path):
+    assert run_child(-1, str(tmp_path)) == 0
+
+
+@pytest.mark.parametrize("index", range(len(MUTANTS)), ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, index):
+    name, orig, bad = MUTANTS[index]
+    assert oracle.source().count(orig) == 1, f"mutation anchor for {name!r} not found exactly once"
+    assert run_child(index, str(tmp_path)) != 0, f"planted mistake {name!r} passed every pin"
+
+
+def _table1_from_golden():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table1_4x4_periodic.txt")
+    rows = []
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(tuple(int(x) for x in line.split()))
+    return rows
+
+
+if __name__ == "__main__":
+    idx, work = int(sys.argv[1]), sys.argv[2]
     src = oracle.source()
-    assert src.count(orig) == 1, f"mutation anchor for {name!r} not found exactly once"
-    lib = oracle.load_variant(src.replace(orig, bad), str(tmp_path))
-    assert not pins_pass(lib, table1_triples), f"planted mistake {name!r} passed every pin"
+    if idx >= 0:
+        src = src.replace(MUTANTS[idx][1], MUTANTS[idx][2])
+    sys.exit(0 if pins_pass(oracle.load_variant(src, work), _table1_from_golden()) else 1)
