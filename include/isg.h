@@ -124,6 +124,27 @@ ISG_API isg_status isg_enumerate(const isg_graph* graph, void* stream, int64_t* 
                          const isg_options* opt);
 
 /*
+ * isg_enumerate for callers that cannot allocate device memory: the paper has no counterpart
+ * to this call. It is meant for a caller whose device memory is owned by another allocator, or
+ * that runs the enumeration inside a fixed memory budget or a loop that must not enter an
+ * allocator. It computes the same table as isg_enumerate with g_out on the device, but makes no
+ * cudaMalloc, cudaFree or other allocating call: its task counter, status word and device copy
+ * of the graph program live in one 16 KiB array of device memory inside the library, which
+ * every GPU that loads the library keeps until the process exits.
+ * g_out_device: n_e * n_m int64 on the current device (isg_graph_bins); the call only enqueues
+ * work on stream. opt as for isg_enumerate (NULL = defaults).
+ * The first call on each device looks up that device's address of the array (with the device
+ * current); make that first call before any stream capture. All calls share the array and it
+ * keeps the last call's contents (each call clears the counter and status words it needs), so
+ * calls whose work overlaps on the GPU (different streams, or different host threads) race and
+ * give wrong tables: issue them on one stream.
+ * Errors: ISG_ERR_INVALID, ISG_ERR_TOO_LARGE (the graph program exceeds the 16128 bytes left for
+ * it, or as isg_enumerate), ISG_ERR_CUDA.
+ */
+ISG_API isg_status isg_enumerate_noalloc(const isg_graph* graph, void* stream, int64_t* g_out_device,
+                                         const isg_options* opt);
+
+/*
  * Thermodynamics on the grid T[0..nT) x h[0..nh) from a table g of this graph's geometry
  * (Eq. 2 summed over the degeneracy table of Sec. 2). T > 0, host arrays. Outputs are
  * nT * nh doubles each, point (a, b) at index a * nh + b: logZ = ln Z, E = <H>, M = <M>,

@@ -50,6 +50,7 @@ _SIGS = {
     "isg_debug_plan": (i32, [vp, vp, i32, vp]),
     "isg_debug_emulate": (i32, [vp, vp, vp]),
     "isg_probe_peaks": (i32, [vp, vp, vp, vp]),
+    "isg_enumerate_noalloc": (i32, [vp, vp, vp, vp]),
 }
 
 
@@ -172,6 +173,20 @@ def isg_enumerate(graph: Graph, g_out=None, stream=None, **options):
         return g_out
     _check_tensor(g_out, shape, "int64")
     _check(lib().isg_enumerate(graph, _stream_handle(stream), g_out.data_ptr(), 1, ctypes.byref(o)))
+    return g_out
+
+
+def isg_enumerate_noalloc(graph: Graph, g_out, stream=None, **options):
+    """isg_enumerate into a torch int64 CUDA tensor without any device allocation by the library.
+
+    For callers that cannot allocate device memory (memory owned by another allocator, a fixed
+    budget, or a loop that must not enter an allocator): the library's scratch is a 16 KiB array
+    of device memory it holds for the life of the process. Calls share that array, so calls whose
+    work overlaps on the GPU race: issue them on one stream. The first call on a device sets up
+    that device's address of the array; make it before any stream capture."""
+    _check_tensor(g_out, table_shape(graph), "int64")
+    o = _options(**options)
+    _check(lib().isg_enumerate_noalloc(graph, _stream_handle(stream), g_out.data_ptr(), ctypes.byref(o)))
     return g_out
 
 
