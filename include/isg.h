@@ -78,7 +78,8 @@ typedef struct {
                                 largest count that cannot overflow a 32-bit bin) */
     int32_t shard_bits;      /* k: the 2^N configurations form 2^k shards, shard j holding the
                                 words whose top k bits (spins N-k .. N-1) equal j */
-    int32_t reserved0;
+    int32_t bin_stride;      /* row stride (bins per energy row) of the shared histogram, >= N + 1
+                                (0 = plan: padded against shared-memory bank conflicts) */
     int64_t shard_lo;        /* enumerate shards [shard_lo, shard_hi) only; 0,0 = all */
     int64_t shard_hi;
     int32_t accumulate;      /* 1: add the counts into g_out; 0: overwrite g_out */
@@ -122,6 +123,50 @@ ISG_API isg_status isg_graph_size(const isg_graph* graph, int32_t* n_spins, int3
  */
 ISG_API isg_status isg_enumerate(const isg_graph* graph, void* stream, int64_t* g_out, int32_t g_out_on_device,
                          const isg_options* opt);
+
+/*
+ * Enumerate n_graphs independent graphs (for example disorder realisations) in one persistent
+ * launch: every warp task (32 outer prefixes x 2^q configurations) of every graph is a tile of
+ * one queue that the warps of one grid drain (Sec. 3d splits one lattice's outer loops over
+ * processes; here the tiles of many lattices share one GPU). g_out[k] receives the table of
+ * graphs[k] in its own geometry (isg_graph_bins), all on the device or all on the host
+ * (on_device). opt: planning fields apply to every graph (inner_bits = per-lane walk length
+ * target, low_bits, block_threads <= 512, ctas_per_sm); shard and accumulate fields must be 0.
+ * The call synchronises stream. It plans, allocates and frees its own device memory; repeated
+ * batches should use isg_batch_create / isg_batch_run. Errors as isg_enumerate.
+ */
+ISG_API isg_status isg_enumerate_batch(int32_t n_graphs, const isg_graph* const* graphs, void* stream,
+                                       int64_t* const* g_out, int32_t on_device, const isg_options* opt);
+
+typedef struct isg_batch isg_batch;
+
+/*
+ * Prepare a batch once: plan every graph, and place the programs, the tile descriptors and one
+ * output table per graph in device memory owned by the batch (on the current device). Options as
+ * isg_enumerate_batch. The graphs may be destroyed afterwards. Errors: ISG_ERR_INVALID,
+ * ISG_ERR_TOO_LARGE, ISG_ERR_NOMEM, ISG_ERR_CUDA.
+ */
+ISG_API isg_status isg_batch_create(int32_t n_graphs, const isg_graph* const* graphs, const isg_options* opt,
+                                    isg_batch** out);
+
+/*
+ * Enqueue one run of a prepared batch on stream: zero its tables and task counter, then the
+ * persistent launch. The first run captures these steps into a CUDA graph (on a stream of the
+ * batch's own); every run launches that graph on `stream`. Runs of one batch share its tables:
+ * a run overwrites the previous run's results. Errors: ISG_ERR_INVALID, ISG_ERR_CUDA.
+ */
+ISG_API isg_status isg_batch_run(isg_batch* batch, void* stream);
+
+/* Device pointer of graph k's table inside the batch (isg_graph_bins geometry of graphs[k]),
+ * valid until isg_batch_destroy. */
+ISG_API isg_status isg_batch_table(const isg_batch* batch, int32_t k, int64_t** device_table);
+
+/* Synchronise stream and report the kernels' self-check of the last run (ISG_ERR_INTERNAL if a
+ * thread's tracked bin disagreed with its recomputation). */
+ISG_API isg_status isg_batch_status(isg_batch* batch, void* stream);
+
+/* Free a prepared batch (NULL is ignored). Synchronises the device's work on its memory. */
+ISG_API void isg_batch_destroy(isg_batch* batch);
 
 /*
  * isg_enumerate for callers that cannot allocate device memory: the paper has no counterpart

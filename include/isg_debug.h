@@ -15,10 +15,10 @@ extern "C" {
 
 /*
  * The plan isg_enumerate would use for this graph and these options on a device with `sms`
- * multiprocessors (0 = 152). out[0..12] = small-kernel flag, inner bits q, low-block size b,
+ * multiprocessors (0 = 152). out[0..13] = small-kernel flag, inner bits q, low-block size b,
  * warp tasks, threads per CTA, histogram copies, CTAs per SM, tasks per flush round, grid,
  * shared-memory bytes per CTA, energy stride G, compact energy bins, bytes of the program that
- * isg_enumerate copies to the device. Errors as isg_enumerate.
+ * isg_enumerate copies to the device, histogram row stride. Errors as isg_enumerate.
  */
 ISG_API isg_status isg_debug_plan(const isg_graph* graph, const isg_options* opt, int32_t sms, int64_t* out);
 

@@ -17,8 +17,10 @@
 //
 // Bin address. Reachable energies are E = e_lo + G e' with G >= 2 the energy stride of the graph
 // (every single flip changes E by a multiple of G). The histogram stores bin (e', m) at byte
-// offset 4 (e' n_m + m), m = number of up spins. One unit of field moves the address by
-// sE = 8 n_m / G bytes: dE = 2 S_k h_k gives de' = 2 S_k h_k / G, and dm = -S_k.
+// offset 4 (e' R + m), m = number of up spins, R >= N + 1 the row stride. One unit of field moves
+// the address by sE = 8 R / G bytes: dE = 2 S_k h_k gives de' = 2 S_k h_k / G, and dm = -S_k.
+// R is padded so that lanes whose bins differ by a few rows and a few columns fall in different
+// shared-memory banks (R = -1 mod 32, for instance, puts (e' + d, m + d) in the same bank).
 #pragma once
 #include <cstdint>
 #include <utility>
@@ -54,14 +56,14 @@ struct ProgHeader {
     int32_t off_sgn;   // word offsets of the arrays below
     int32_t off_mask;
     int32_t off_i32;   // int32 area: w[nc], degw[n], A[n * kMaxLow]
-    int32_t pad;
+    int32_t stride;    // histogram row stride in bins (>= n_m), chosen against bank conflicts
 };
 constexpr int kHeaderWords = (int)(sizeof(ProgHeader) / 8);
 static_assert(sizeof(ProgHeader) % 8 == 0, "program header must be whole words");
 
 // Read-only view of a program (in shared memory on the device, host memory in emulation).
 struct ProgView {
-    int n, q, b, nc, n_m, sE, G;
+    int n, q, b, nc, n_m, stride, sE, G;
     int64_t e_lo;
     const uint64_t* sgn;    // [n]       neighbours of k with negative coupling
     const uint64_t* mask;   // [n * nc]  neighbours of k whose |J| has class c
@@ -73,7 +75,8 @@ struct ProgView {
 ISG_HD ProgView make_view(const uint64_t* blob) {
     const ProgHeader* h = reinterpret_cast<const ProgHeader*>(blob);
     ProgView v;
-    v.n = h->n; v.q = h->q; v.b = h->b; v.nc = h->nc; v.n_m = h->n_m; v.sE = h->sE; v.G = h->G;
+    v.n = h->n; v.q = h->q; v.b = h->b; v.nc = h->nc; v.n_m = h->n_m; v.stride = h->stride; v.sE = h->sE;
+    v.G = h->G;
     v.e_lo = h->e_lo;
     v.sgn = blob + h->off_sgn;
     v.mask = blob + h->off_mask;
@@ -125,7 +128,7 @@ ISG_HD uint32_t bin_offset(const ProgView& p, uint64_t st) {
     }
     const int64_t E = -sum / 2;
     const int64_t ec = (E - p.e_lo) / p.G;
-    return static_cast<uint32_t>((ec * p.n_m + popc64(st)) * 4);
+    return static_cast<uint32_t>((ec * p.stride + popc64(st)) * 4);
 }
 
 // One Gray step inside a low block, fully resolved at compile time: step U flips spin k =

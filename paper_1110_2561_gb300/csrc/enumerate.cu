@@ -47,15 +47,15 @@ __device__ __forceinline__ void stage_blob(uint64_t* dst, const uint64_t* src, i
 
 // Add the CTA's privatised bins into the public int64 table and clear them.
 __device__ __forceinline__ void flush_bins(const ProgHeader* hd, uint32_t* hist, int copies, int64_t* g) {
-    const int nb = hd->nbins_c, n_m = hd->n_m;
+    const int nb = hd->nbins_c, n_m = hd->n_m, R = hd->stride;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         unsigned long long s = 0;
         for (int c = 0; c < copies; ++c) {
             s += hist[c * nb + i];
             hist[c * nb + i] = 0;
         }
-        if (s) {
-            const int64_t ec = i / n_m, m = i - ec * n_m;
+        const int64_t ec = i / R, m = i - ec * R;
+        if (s && m < n_m) {                 // padding columns m > N are never counted
             const int64_t e = (hd->e_lo + hd->G * ec + hd->S) / 2;
             atomicAdd(reinterpret_cast<unsigned long long*>(g + e * n_m + m), s);
         }
@@ -110,7 +110,7 @@ __global__ void enumerate_small_kernel(const uint64_t* blob, int words, uint64_t
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t s = s_lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < s_hi; s += stride) {
         const int64_t i = bin_offset(v, s) >> 2;
-        const int64_t ec = i / hd->n_m, m = i - ec * hd->n_m;
+        const int64_t ec = i / hd->stride, m = i - ec * hd->stride;
         const int64_t e = (hd->e_lo + hd->G * ec + hd->S) / 2;
         atomicAdd(reinterpret_cast<unsigned long long*>(g + e * hd->n_m + m), 1ull);
     }

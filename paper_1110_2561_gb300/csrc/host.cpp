@@ -62,6 +62,24 @@ static int weight_classes(const isg_graph& g, std::vector<int32_t>& w) {
     return 1;                                              // binary classes
 }
 
+int choose_stride(const isg_graph& g, int requested) {
+    const int n_m = g.n + 1;
+    if (requested > 0) {
+        if (requested < n_m || (8 * (int64_t)requested) % g.G)
+            fail(ISG_ERR_INVALID, "bin_stride must be >= N + 1 and make 8 * stride a multiple of the energy stride");
+        return requested;
+    }
+    // Residues of the stride mod 32, best first: lanes of a warp differ in five outer spins, so
+    // their bins differ by a few columns (|dm| <= 5) and a few rows; these residues send the
+    // common small offsets (de * stride + dm) to distinct banks (a residue of 31 or 1 collides
+    // whenever de = dm or de = -dm).
+    static const int pref[] = {6, 26, 7, 25, 13, 19, 9, 23, 5, 27, 11, 21};
+    for (int r : pref)
+        for (int s = n_m; s < n_m + 32; ++s)
+            if (s % 32 == r && (8 * (int64_t)s) % g.G == 0) return s;
+    return n_m;
+}
+
 static size_t blob_words(int n, int nc) {
     size_t i32 = (size_t)nc + n + (size_t)n * kMaxLow;
     return kHeaderWords + (size_t)n + (size_t)n * nc + (i32 + 1) / 2;
@@ -85,6 +103,7 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d) {
     const bool forced = o.inner_bits > 0 || o.low_bits > 0;
     if (free < 6 || (free < 11 && !forced)) {
         p.small = true;
+        p.stride = n + 1;
         p.s_lo = (uint64_t)lo << free;
         p.s_hi = (uint64_t)hi << free;
         p.q = 0;
@@ -155,7 +174,9 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d) {
     std::vector<int32_t> w;
     weight_classes(g, w);
     const size_t prog_bytes = blob_words(n, (int)w.size()) * 8;
-    const size_t bin_bytes = (size_t)g.n_e_c * (n + 1) * 4;
+    p.stride = choose_stride(g, o.bin_stride);
+    if (prog_bytes + (size_t)g.n_e_c * p.stride * 4 > d.smem_optin && o.bin_stride == 0) p.stride = n + 1;
+    const size_t bin_bytes = (size_t)g.n_e_c * p.stride * 4;
     if (prog_bytes + bin_bytes > d.smem_optin)
         fail(ISG_ERR_TOO_LARGE, "histogram of " + std::to_string(g.n_e_c * (n + 1)) + " bins does not fit shared memory");
     p.ctas_per_sm = o.ctas_per_sm > 0 ? o.ctas_per_sm : 2;
@@ -198,9 +219,11 @@ std::vector<uint64_t> build_program(const isg_graph& g, const Plan& p) {
     h.nc = nc;
     h.n_m = n + 1;
     h.n_e_c = (int32_t)g.n_e_c;
-    h.nbins_c = (int32_t)(g.n_e_c * (n + 1));
+    const int stride = p.stride > 0 ? p.stride : n + 1;
+    h.stride = stride;
+    h.nbins_c = (int32_t)(g.n_e_c * stride);
     h.G = (int32_t)g.G;
-    h.sE = (int32_t)(8 * (n + 1) / g.G);
+    h.sE = (int32_t)(8 * stride / g.G);
     h.words = (int32_t)words;
     h.e_lo = g.e_lo;
     h.S = g.S;
@@ -394,6 +417,7 @@ isg_status isg_debug_plan(const isg_graph* g, const isg_options* opt, int32_t sm
         out[10] = g->G;
         out[11] = g->n_e_c;
         out[12] = (int64_t)build_program(*g, p).size() * 8;
+        out[13] = p.stride;
     });
 }
 
@@ -404,7 +428,8 @@ isg_status isg_debug_emulate(const isg_graph* g, const isg_options* opt, int64_t
         Plan p = make_plan(*g, o, DeviceInfo{});
         std::vector<uint64_t> blob = build_program(*g, p);
         const ProgView v = make_view(blob.data());
-        const int64_t nb = g->n_e_c * (g->n + 1);
+        const int64_t stride = p.stride > 0 ? p.stride : g->n + 1;
+        const int64_t nb = g->n_e_c * stride;
         std::vector<uint32_t> hist((size_t)nb, 0);
         bool bad = false;
         if (p.small) {
@@ -427,7 +452,11 @@ isg_status isg_debug_emulate(const isg_graph* g, const isg_options* opt, int64_t
         if (bad) fail(ISG_ERR_INTERNAL, "emulated walk left the histogram or lost track of its bin");
         if (!o.accumulate) std::memset(g_out, 0, sizeof(int64_t) * public_bins(*g));
         for (int64_t i = 0; i < nb; ++i)
-            if (hist[i]) g_out[public_bin(*g, i)] += hist[i];
+            if (hist[i]) {
+                const int64_t pb = public_bin(*g, i, stride);
+                if (pb < 0) fail(ISG_ERR_INTERNAL, "emulated walk counted a padding column");
+                g_out[pb] += hist[i];
+            }
     });
 }
 

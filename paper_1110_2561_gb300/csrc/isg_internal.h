@@ -45,6 +45,7 @@ struct Plan {
     std::vector<int> perm;     // internal position -> caller spin
     uint64_t prefix_base = 0;  // first lane prefix (multiple of 32)
     uint64_t n_tasks = 0;      // warp tasks: 32 lane prefixes each
+    int stride = 0;            // histogram row stride (bins)
     int threads = 512, copies = 1, ctas_per_sm = 2, flush_rounds = 1;
     int grid = 0;
     size_t smem_bytes = 0;
@@ -62,13 +63,18 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d);
 // Build the program blob (64-bit words) of graph g for a plan: spins in internal order.
 std::vector<uint64_t> build_program(const isg_graph& g, const Plan& p);
 
-// Map compact bin i = e' * n_m + m of the internal histogram to the public table index.
-inline int64_t public_bin(const isg_graph& g, int64_t compact) {
+// Map bin i = e' * stride + m of the internal histogram to the public table index (-1 for the
+// padding columns m > N, which are never counted).
+inline int64_t public_bin(const isg_graph& g, int64_t compact, int64_t stride) {
     const int64_t n_m = g.n + 1;
-    const int64_t ec = compact / n_m, m = compact % n_m;
+    const int64_t ec = compact / stride, m = compact % stride;
+    if (m >= n_m) return -1;
     const int64_t E = g.e_lo + g.G * ec;
     return ((E + g.S) / 2) * n_m + m;
 }
+
+// Row stride of the shared histogram for a graph (>= N + 1), padded against bank conflicts.
+int choose_stride(const isg_graph& g, int requested);
 
 inline int64_t public_bins(const isg_graph& g) { return (g.S + 1) * (int64_t)(g.n + 1); }
 

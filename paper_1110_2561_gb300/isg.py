@@ -29,7 +29,7 @@ class IsgError(RuntimeError):
 class isg_options(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "struct_size", "max_spins", "inner_bits", "low_bits", "block_threads", "copies", "ctas_per_sm",
-        "flush_tasks", "shard_bits", "reserved0")] + [
+        "flush_tasks", "shard_bits", "bin_stride")] + [
         ("shard_lo", ctypes.c_int64), ("shard_hi", ctypes.c_int64),
         ("accumulate", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
@@ -51,6 +51,12 @@ _SIGS = {
     "isg_debug_emulate": (i32, [vp, vp, vp]),
     "isg_probe_peaks": (i32, [vp, vp, vp, vp]),
     "isg_enumerate_noalloc": (i32, [vp, vp, vp, vp]),
+    "isg_enumerate_batch": (i32, [i32, vp, vp, vp, i32, vp]),
+    "isg_batch_create": (i32, [i32, vp, vp, ctypes.POINTER(vp)]),
+    "isg_batch_run": (i32, [vp, vp]),
+    "isg_batch_table": (i32, [vp, i32, ctypes.POINTER(vp)]),
+    "isg_batch_status": (i32, [vp, vp]),
+    "isg_batch_destroy": (None, [vp]),
 }
 
 
@@ -190,6 +196,82 @@ def isg_enumerate_noalloc(graph: Graph, g_out, stream=None, **options):
     return g_out
 
 
+def _graph_array(graphs):
+    arr = (ctypes.c_void_p * len(graphs))(*[g.ptr for g in graphs])
+    return arr
+
+
+def isg_enumerate_batch(graphs, g_out=None, stream=None, **options):
+    """Tables of many graphs from one persistent launch. g_out: None (new numpy arrays), a list of
+    numpy int64 arrays, or a list of torch int64 CUDA tensors, one per graph in its table_shape."""
+    shapes = [table_shape(g) for g in graphs]
+    if g_out is None:
+        g_out = [np.zeros(s, dtype=np.int64) for s in shapes]
+    on_device = 0 if isinstance(g_out[0], np.ndarray) else 1
+    ptrs = []
+    for t, s in zip(g_out, shapes):
+        if on_device:
+            _check_tensor(t, s, "int64")
+            ptrs.append(t.data_ptr())
+        else:
+            if t.dtype != np.int64 or not t.flags.c_contiguous or t.shape != s:
+                raise ValueError(f"host tables must be C-contiguous int64 arrays of shape {s}")
+            ptrs.append(t.ctypes.data)
+    arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+    o = _options(**options)
+    sh = _stream_handle(stream) if (stream is not None or on_device) else None
+    _check(lib().isg_enumerate_batch(len(graphs), _graph_array(graphs), sh, arr, on_device, ctypes.byref(o)))
+    return g_out
+
+
+class Batch:
+    """Prepared batch (isg_batch_create): device-resident programs and tables, runs replayed from
+    a captured CUDA graph."""
+
+    def __init__(self, graphs, **options):
+        o = _options(**options)
+        out = ctypes.c_void_p()
+        _check(lib().isg_batch_create(len(graphs), _graph_array(graphs), ctypes.byref(o), ctypes.byref(out)))
+        self.ptr = out.value
+        self.shapes = [table_shape(g) for g in graphs]
+
+    def run(self, stream=None):
+        _check(lib().isg_batch_run(self.ptr, _stream_handle(stream)))
+
+    def status(self, stream=None):
+        _check(lib().isg_batch_status(self.ptr, _stream_handle(stream)))
+
+    def table_ptr(self, k: int) -> int:
+        p = ctypes.c_void_p()
+        _check(lib().isg_batch_table(self.ptr, k, ctypes.byref(p)))
+        return p.value
+
+    def table(self, k: int):
+        """Graph k's table as a torch int64 CUDA tensor viewing the batch's memory (no copy)."""
+        import torch
+        n_e, n_m = self.shapes[k]
+        return _tensor_view(self.table_ptr(k), n_e * n_m, torch.int64).view(n_e, n_m)
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            lib().isg_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        if _lib is not None:
+            self.close()
+
+
+def _tensor_view(ptr: int, numel: int, dtype):
+    """A torch CUDA tensor aliasing device memory owned by the library (via __cuda_array_interface__)."""
+    import torch
+
+    class _Holder:
+        __cuda_array_interface__ = {"shape": (numel,), "typestr": "<i8", "data": (ptr, False), "version": 3,
+                                    "strides": None}
+    return torch.as_tensor(_Holder(), device="cuda")
+
+
 def _check_tensor(t, shape, dtype: str):
     import torch
     want = getattr(torch, dtype)
@@ -235,11 +317,11 @@ def isg_thermo(g, graph: Graph, T, h, precision: int = ISG_FP64, stream=None, ou
 
 
 def isg_debug_plan(graph: Graph, sms: int = 0, **options) -> dict:
-    out = np.zeros(13, dtype=np.int64)
+    out = np.zeros(14, dtype=np.int64)
     o = _options(**options)
     _check(lib().isg_debug_plan(graph, ctypes.byref(o), sms, out.ctypes.data))
     keys = ("small", "q", "b", "tasks", "threads", "copies", "ctas_per_sm", "flush_rounds", "grid", "smem_bytes",
-            "G", "n_e_compact", "blob_bytes")
+            "G", "n_e_compact", "blob_bytes", "stride")
     return dict(zip(keys, (int(x) for x in out)))
 
 
