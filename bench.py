@@ -325,6 +325,61 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------ serving mode
+def run_serving(args):
+    """Poisson stream of lattice requests (seeded; N uniform in 16..38, square / triangular / cubic,
+    periodic or free, J uniform in {-2,-1,1,2}) submitted at their arrival times to isg_server;
+    reports latency percentiles, throughput and offered vs achieved load."""
+    import torch
+    from paper_1110_2561_gb300 import isg, workloads
+
+    torch.cuda.set_device(0)
+    reqs = workloads.serving_stream(args.requests, rate_per_s=args.rate)
+    graphs = [isg.isg_graph_create(r.lattice.n, r.lattice.edges) for r in reqs]
+    srv = isg.Server(step_ms=args.step_ms)
+    warm = srv.submit(isg.isg_graph_create(20, workloads.square(4, 5, True).edges))
+    srv.wait(warm)
+    srv.result(warm)
+    tickets = []
+    t0 = time.perf_counter()
+    for r, g in zip(reqs, graphs):
+        delay = r.arrival_s - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(g))
+    lat, queued, configs = [], [], 0
+    bad = 0
+    last_done = 0.0
+    for t, r in zip(tickets, reqs):
+        srv.wait(t)
+        g, times = srv.result(t)
+        lat.append(times[2])
+        queued.append(times[0])
+        last_done = max(last_done, times[3] + times[2])
+        configs += 1 << r.lattice.n
+        if int(g.sum()) != 1 << r.lattice.n:
+            bad += 1
+    st = srv.stats()
+    srv.close()
+    first = reqs[0].arrival_s
+    span_arrivals = reqs[-1].arrival_s - first
+    lat_ms = np.array(lat) * 1e3
+    line = {
+        "metric": "serving latency and throughput (continuous batching)", "unit": "ms",
+        "workload": f"{args.requests} requests, Poisson {args.rate}/s, N uniform 16..38, square/triangular/cubic, "
+                    "periodic or free, J uniform in {-2,-1,1,2} (seeded)",
+        "p50_ms": float(np.percentile(lat_ms, 50)), "p90_ms": float(np.percentile(lat_ms, 90)),
+        "p99_ms": float(np.percentile(lat_ms, 99)), "max_ms": float(lat_ms.max()),
+        "mean_queue_ms": float(np.mean(queued) * 1e3),
+        "offered_configs_per_s": configs / max(1e-9, span_arrivals),
+        "achieved_configs_per_s": configs / max(1e-9, (time.perf_counter() - t0)),
+        "device_busy_frac": st["device_ms"] * 1e-3 / max(1e-9, time.perf_counter() - t0),
+        "device_configs_per_s": st["configs"] / max(1e-9, st["device_ms"] * 1e-3),
+        "steps": int(st["steps"]), "step_ms": args.step_ms, "invariant_failures": bad,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -333,12 +388,18 @@ def main():
     ap.add_argument("--impl", choices=("isg", "reference"), default="isg")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target seconds of the oracle sample")
+    ap.add_argument("--serving", action="store_true", help="run the request-stream (serving) benchmark instead")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--step-ms", type=float, default=20.0)
     ap.add_argument("--shard-bits", type=int, default=0,
                     help="profiling case: enumerate only shard 0 of 2^k per step (not a benchmark line)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "isg":
         ap.error("at least 3 warm-up steps")
-    if args.impl == "reference":
+    if args.serving:
+        run_serving(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_isg(args)

@@ -202,6 +202,65 @@ ISG_API isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const isg_g
                       const double* T, int32_t nh, const double* h, int32_t precision, void* stream,
                       int32_t out_on_device, double* logZ, double* E, double* M, double* C, double* chi);
 
+/*
+ * Request server with continuous batching. A worker thread owns one stream on the device that is
+ * current at isg_server_create and runs engine steps: each step is one launch of the batched
+ * kernel over warp tasks drawn from every admitted request, shortest remaining work first, up to
+ * step_ms of device time, so a request that arrives while others run joins the next step. A
+ * request is admitted when one of max_inflight slots and room for its table in the device arena
+ * are free; its table accumulates on the device and is copied out by the step carrying its last
+ * task. Two steps are in flight at a time.
+ */
+typedef struct isg_server isg_server;
+
+typedef struct {
+    int32_t struct_size;     /* sizeof(isg_server_options); set by isg_server_options_init */
+    int32_t max_spins;       /* largest N accepted (default 40) */
+    int32_t max_inflight;    /* admitted requests at a time (default 256) */
+    int32_t max_queued;      /* requests waiting for admission before submit returns BUSY (65536) */
+    int64_t arena_bytes;     /* device memory for the admitted requests' tables and programs (64 MiB),
+                                mirrored by as much pinned host memory */
+    double step_ms;          /* device time per engine step (default 20 ms) */
+    int32_t block_threads;   /* threads per CTA of the batched kernel, <= 512 (0 = 512) */
+    int32_t ctas_per_sm;     /* 0 = 2 */
+} isg_server_options;
+
+ISG_API void isg_server_options_init(isg_server_options* opt);
+
+/* Start a server on the current device (allocates the arena, its pinned mirror and a stream).
+ * Errors: ISG_ERR_INVALID, ISG_ERR_NOMEM, ISG_ERR_CUDA. */
+ISG_API isg_status isg_server_create(const isg_server_options* opt, isg_server** out);
+
+/* Queue the enumeration of all 2^N configurations of a graph (planned and copied at once; the
+ * graph may be destroyed afterwards). *ticket identifies the request. Errors: ISG_ERR_TOO_LARGE
+ * (N > max_spins, or its table exceeds the arena), ISG_ERR_BUSY (max_queued requests waiting). */
+ISG_API isg_status isg_server_submit(isg_server* server, const isg_graph* graph, int64_t* ticket);
+
+/* *done = 1 once the request has finished (successfully or not). */
+ISG_API isg_status isg_server_poll(isg_server* server, int64_t ticket, int32_t* done);
+
+/* Block until the request finishes, at most timeout_ms (< 0: no limit). ISG_ERR_TIMEOUT if the
+ * wait ran out (the request continues). */
+ISG_API isg_status isg_server_wait(isg_server* server, int64_t ticket, int64_t timeout_ms);
+
+/* Copy a finished request's table into g_out (host, its graph's isg_graph_bins geometry) and
+ * release the ticket. times (NULL or 4 doubles): seconds queued before admission, seconds from
+ * admission to completion, seconds from submission to completion, submission time since the
+ * server started. Errors: ISG_ERR_NOT_READY, ISG_ERR_INVALID (unknown ticket), or the request's
+ * own failure status. */
+ISG_API isg_status isg_server_result(isg_server* server, int64_t ticket, int64_t* g_out, double* times);
+
+/* Drop a request: queued ones at once, running ones after the steps carrying them finish. */
+ISG_API isg_status isg_server_cancel(isg_server* server, int64_t ticket);
+
+/* stats[8]: steps completed, configurations enumerated, device milliseconds of the steps, queued
+ * requests, admitted requests, current rate estimate (configurations per second), seconds since
+ * creation, open tickets. */
+ISG_API isg_status isg_server_stats(isg_server* server, double* stats);
+
+/* Finish the in-flight steps, stop the worker and free everything (queued requests are dropped). */
+ISG_API void isg_server_destroy(isg_server* server);
+
 /* Message of the last failing call on this thread ("" if none). Valid until the next call. */
 ISG_API const char* isg_last_error(void);
 

@@ -14,8 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libisg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["host.cpp", "enumerate.cu", "thermo.cu", "probe.cu", "noalloc.cu", "batch.cu"]
-HEADERS = ["enum_core.cuh", "isg_internal.h"]
+SOURCES = ["host.cpp", "enumerate.cu", "thermo.cu", "probe.cu", "noalloc.cu", "batch.cu", "server.cu"]
+HEADERS = ["enum_core.cuh", "isg_internal.h", "batch_internal.h"]
 
 
 def _nvcc() -> str:

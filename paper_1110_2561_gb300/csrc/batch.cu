@@ -20,21 +20,12 @@
 #include <string>
 #include <vector>
 
+#include "batch_internal.h"
 #include "isg_internal.h"
 
 namespace isg {
 
 DeviceInfo device_info();
-
-struct BatchInst {
-    int64_t* g;              // public table of this instance (device)
-    uint64_t prefix_base;    // lane prefix of task 0
-    uint64_t task_lo;        // first task of this instance in this launch
-    uint64_t tile_begin;     // first tile of this instance in the launch's tile numbering
-    uint64_t n_tiles;        // tiles (= tasks) of this instance in this launch
-    uint32_t blob_off;       // word offset of the program in the blob array
-    uint32_t blob_words;
-};
 
 struct BatchArgs {
     const BatchInst* inst;
@@ -139,18 +130,6 @@ __global__ void batch_small_kernel(const BatchInst* inst, const int* small_ids, 
 // ---------------------------------------------------------------------------------------------
 // Host planning of a batch
 // ---------------------------------------------------------------------------------------------
-struct BatchPlan {
-    int B = kMaxLow;
-    std::vector<BatchInst> inst;        // device descriptors (g filled by the caller), tile order
-    std::vector<int> order;             // inst[k] describes graphs[order[k]]
-    std::vector<uint64_t> blobs;
-    std::vector<int> small_ids;         // descriptors of instances for the small kernel
-    uint64_t n_tiles = 0;
-    int prog_words = 0, slot_words = 0, threads = 512, warps_per_cta = 16, small_max_words = 0;
-    size_t smem = 0;
-    int grid = 0;
-};
-
 // Tasks of the whole configuration space of graph g under a plan with q inner bits.
 static BatchPlan plan_batch(int n, const isg_graph* const* graphs, const isg_options& o, const DeviceInfo& d) {
     BatchPlan bp;

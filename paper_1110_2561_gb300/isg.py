@@ -57,6 +57,15 @@ _SIGS = {
     "isg_batch_table": (i32, [vp, i32, ctypes.POINTER(vp)]),
     "isg_batch_status": (i32, [vp, vp]),
     "isg_batch_destroy": (None, [vp]),
+    "isg_server_options_init": (None, [vp]),
+    "isg_server_create": (i32, [vp, ctypes.POINTER(vp)]),
+    "isg_server_submit": (i32, [vp, vp, ctypes.POINTER(i64)]),
+    "isg_server_poll": (i32, [vp, i64, ctypes.POINTER(i32)]),
+    "isg_server_wait": (i32, [vp, i64, i64]),
+    "isg_server_result": (i32, [vp, i64, vp, vp]),
+    "isg_server_cancel": (i32, [vp, i64]),
+    "isg_server_stats": (i32, [vp, vp]),
+    "isg_server_destroy": (None, [vp]),
 }
 
 
@@ -255,6 +264,69 @@ class Batch:
     def close(self):
         if getattr(self, "ptr", None):
             lib().isg_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        if _lib is not None:
+            self.close()
+
+
+class isg_server_options(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int32), ("max_spins", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("max_queued", ctypes.c_int32), ("arena_bytes", ctypes.c_int64), ("step_ms", ctypes.c_double),
+                ("block_threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+
+class Server:
+    """isg_server_*: a continuously batching request server on the current device."""
+
+    def __init__(self, **options):
+        o = isg_server_options()
+        lib().isg_server_options_init(ctypes.byref(o))
+        for k, v in options.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown server option {k!r}")
+            setattr(o, k, v)
+        out = ctypes.c_void_p()
+        _check(lib().isg_server_create(ctypes.byref(o), ctypes.byref(out)))
+        self.ptr = out.value
+        self.shapes = {}
+
+    def submit(self, graph: Graph) -> int:
+        t = ctypes.c_int64()
+        _check(lib().isg_server_submit(self.ptr, graph, ctypes.byref(t)))
+        self.shapes[t.value] = table_shape(graph)
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        d = ctypes.c_int32()
+        _check(lib().isg_server_poll(self.ptr, ticket, ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        _check(lib().isg_server_wait(self.ptr, ticket, timeout_ms))
+
+    def result(self, ticket: int):
+        """(table, times) with times = (queued s, service s, latency s, submitted at s)."""
+        g = np.zeros(self.shapes[ticket], dtype=np.int64)
+        times = (ctypes.c_double * 4)()
+        _check(lib().isg_server_result(self.ptr, ticket, g.ctypes.data, times))
+        del self.shapes[ticket]
+        return g, tuple(times)
+
+    def cancel(self, ticket: int):
+        _check(lib().isg_server_cancel(self.ptr, ticket))
+        self.shapes.pop(ticket, None)
+
+    def stats(self) -> dict:
+        v = (ctypes.c_double * 8)()
+        _check(lib().isg_server_stats(self.ptr, v))
+        keys = ("steps", "configs", "device_ms", "queued", "admitted", "rate_est", "uptime_s", "tickets")
+        return dict(zip(keys, list(v)))
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            lib().isg_server_destroy(self.ptr)
             self.ptr = None
 
     def __del__(self):

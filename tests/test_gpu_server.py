@@ -1,0 +1,81 @@
+"""The request server (continuous batching): every result equals the same graph enumerated
+alone, whatever else was in flight; admission limits, cancellation and timeouts are reported on
+the host without disturbing the other requests."""
+import os
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1110_2561_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 1
+
+
+def alone(isg, lat):
+    return isg.isg_enumerate(isg.isg_graph_create(lat.n, lat.edges))
+
+
+def test_mix_equals_alone(isg, cuda):
+    """A seeded request stream (N 16..32, square / triangular / cubic, free or periodic, J in
+    {-2,-1,1,2}) submitted at once from one thread: each table equals isg_enumerate alone, and the
+    small ones equal the oracle."""
+    reqs = w.serving_stream(48, n_range=(16, 32), seed=7)
+    srv = isg.Server(step_ms=5.0)
+    tickets = [(srv.submit(isg.isg_graph_create(r.lattice.n, r.lattice.edges)), r.lattice) for r in reqs]
+    for t, lat in tickets:
+        srv.wait(t, 60000)
+        g, times = srv.result(t)
+        assert np.array_equal(g, alone(isg, lat)), lat.name
+        assert times[2] >= times[1] >= 0 and times[0] >= 0
+        if lat.n <= 22:
+            assert np.array_equal(g, oracle.g_masks(lat.n, lat.edges, threads=THREADS)), lat.name
+    st = srv.stats()
+    assert st["tickets"] == 0 and st["admitted"] == 0 and st["steps"] >= 1
+    srv.close()
+
+
+def test_staggered_arrivals_and_small_arena(isg, cuda):
+    """Requests arriving while others run, with an arena that holds only a few tables at a time and
+    two admission slots: all finish and match."""
+    lats = [w.square(5, 6, True), w.cubic(2, 3, 4, True), w.triangular(4, 5, False), w.square(4, 4, False),
+            w.with_random_couplings(w.square(6, 5, True), w.SplitMix64(3), (-1, 1)), w.ring(12)]
+    srv = isg.Server(max_inflight=2, arena_bytes=1 << 20, step_ms=2.0)
+    tickets = []
+    for lat in lats:
+        tickets.append((srv.submit(isg.isg_graph_create(lat.n, lat.edges)), lat))
+        time.sleep(0.002)
+    for t, lat in tickets:
+        srv.wait(t)
+        assert np.array_equal(srv.result(t)[0], alone(isg, lat)), lat.name
+    srv.close()
+
+
+def test_limits_cancel_timeout(isg, cuda):
+    srv = isg.Server(max_inflight=1, max_queued=1, step_ms=1.0)
+    big = w.square(5, 8, True)                              # 2^40 configurations: ~0.15 s of steps
+    gb = isg.isg_graph_create(big.n, big.edges)
+    t1 = srv.submit(gb)
+    with pytest.raises(isg.IsgError) as ei:                 # N > max_spins
+        srv.submit(isg.isg_graph_create(41, w.random_graph(41, 50, w.SplitMix64(1)).edges))
+    assert ei.value.status == 2
+    time.sleep(0.01)                                        # let t1 be admitted
+    small = w.square(4, 4, True)
+    t2 = srv.submit(isg.isg_graph_create(small.n, small.edges))   # waits: the only slot is busy
+    with pytest.raises(isg.IsgError) as ei:                 # queue of one is full
+        srv.submit(isg.isg_graph_create(small.n, small.edges))
+    assert ei.value.status == 6
+    with pytest.raises(isg.IsgError) as ei:                 # not finished within 0 ms
+        srv.wait(t1, 0)
+    assert ei.value.status == 5
+    with pytest.raises(isg.IsgError) as ei:
+        srv.result(t2)
+    assert ei.value.status in (7,)
+    srv.cancel(t1)                                          # frees the slot after its steps drain
+    srv.wait(t2, 60000)
+    assert np.array_equal(srv.result(t2)[0], alone(isg, small))
+    with pytest.raises(isg.IsgError):
+        srv.poll(t1)                                        # cancelled ticket is gone
+    srv.close()
