@@ -143,8 +143,10 @@ def run_isg(args):
     gh = isg.isg_graph_create(lat.n, lat.edges)
     shape = isg.table_shape(gh)
     plan = isg.isg_debug_plan(gh)
-    # --shard-bits k (profiling case): each step enumerates shard 0 of 2^k, same kernel and split
-    shard = dict(shard_bits=args.shard_bits, shard_lo=0, shard_hi=1, inner_bits=plan["q"]) if args.shard_bits else {}
+    # --shard-bits k (profiling case): each step enumerates shard 0 of 2^k with q - k inner bits,
+    # so the launch has the same number of warp tasks as the full one
+    shard = dict(shard_bits=args.shard_bits, shard_lo=0, shard_hi=1,
+                 inner_bits=max(plan["b"], plan["q"] - args.shard_bits)) if args.shard_bits else {}
     n_configs = 1 << (lat.n - args.shard_bits)
     stream = torch.cuda.current_stream()
     g = torch.zeros(shape, dtype=torch.int64, device=dev)
@@ -235,7 +237,8 @@ def run_isg(args):
                          "peak_source": f"{sms} SMs x 128 lanes/clk x {sm_max:.0f} MHz (unit counts and clock)"},
             "roofline_smem_atomic": {"bound": "smem_atomic", "achieved": n_configs / enum_s / 1e9,
                                      "peak": peaks["red_conflict_free"] / 1e9,
-                                     "peak_scattered": peaks["red_scattered"] / 1e9, "unit": "Gred/s",
+                                     "peak_scattered": peaks["red_scattered"] / 1e9,
+                                     "match_any_aggregated": peaks["match_aggregated"] / 1e9, "unit": "Gred/s",
                                      "frac": n_configs / enum_s / peaks["red_conflict_free"],
                                      "peak_source": "isg_probe_peaks (red.shared.add.u32, measured in this run)"},
             "enumerate_ms": statistics.mean(enum_ms), "thermo_ms": statistics.mean(
@@ -245,11 +248,97 @@ def run_isg(args):
             "gpu_launches": 3 * args.steps,
             "clocks": clocks,
         }
+        if not args.no_extras:
+            line["workloads"] = extra_measurements(stream, dev)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------ other workloads
+def _event_ms(fn, stream, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def extra_measurements(stream, dev):
+    """The other workloads of the method, measured once each (not part of the timed step):
+    4x4 free lattice latency, 4096 EA instances batched vs per-instance, and the 3x3x4 cubic
+    torus thermodynamics on a 512 x 256 (T, h) grid in FP32 vs FP64."""
+    import torch
+    from paper_1110_2561_gb300 import isg, workloads
+
+    out = {}
+    # 4x4 free ferromagnet: enumerate + FP64 thermodynamics on 64 temperatures, one call each
+    lat = workloads.square(4, 4, False)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=dev)
+    T = np.linspace(0.5, 5, 64)
+    o64 = tuple(torch.empty((64, 1), dtype=torch.float64, device=dev) for _ in range(5))
+
+    def small_step():
+        isg.isg_enumerate(gh, g, stream)
+        isg.isg_thermo(g, gh, T, [0.0], isg.ISG_FP64, stream, out=o64)
+    dev_ms = _event_ms(small_step, stream, 50)
+    t0 = time.perf_counter()
+    for _ in range(50):
+        small_step()
+    torch.cuda.synchronize()
+    out["square4x4_free"] = {"device_us_per_call": dev_ms * 1e3, "host_us_per_call": (time.perf_counter() - t0) / 50 * 1e6,
+                             "what": "isg_enumerate (65,536 configurations) + isg_thermo (64 T, FP64), device buffers"}
+    # EA +-J batch: one prepared batch (graph replay) vs a loop of per-instance launches
+    lats = workloads.ea_instances()
+    hs = [isg.isg_graph_create(l.n, l.edges) for l in lats]
+    configs = sum(1 << l.n for l in lats)
+    b = isg.Batch(hs)
+    bat_ms = _event_ms(lambda: b.run(stream), stream, 3)
+    b.status(stream)
+    b.close()
+    outs = [torch.zeros(isg.table_shape(h), dtype=torch.int64, device=dev) for h in hs]
+
+    def plain():
+        for h, t in zip(hs, outs):
+            isg.isg_enumerate(h, t, stream)
+    pl_ms = _event_ms(plain, stream, 2)
+    out["ea_4096_batched_vs_plain"] = {
+        "instances": len(lats), "configs": configs,
+        "batched_ms": bat_ms, "batched_instances_per_s": len(lats) / (bat_ms * 1e-3),
+        "batched_configs_per_s": configs / (bat_ms * 1e-3),
+        "plain_ms": pl_ms, "plain_instances_per_s": len(lats) / (pl_ms * 1e-3),
+        "plain_configs_per_s": configs / (pl_ms * 1e-3), "speedup": pl_ms / bat_ms}
+    # cubic 3x3x4 torus: thermodynamics on 512 T x 256 h, FP32 vs FP64
+    lat = workloads.cubic(3, 3, 4, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=dev)
+    enum_ms = _event_ms(lambda: isg.isg_enumerate(gh, g, stream), stream, 3)
+    T = np.linspace(0.5, 8, 512)
+    h = np.linspace(-2, 2, 256)
+    r64 = tuple(torch.empty((512, 256), dtype=torch.float64, device=dev) for _ in range(5))
+    r32 = tuple(torch.empty((512, 256), dtype=torch.float64, device=dev) for _ in range(5))
+    t64 = _event_ms(lambda: isg.isg_thermo(g, gh, T, h, isg.ISG_FP64, stream, out=r64), stream, 5)
+    t32 = _event_ms(lambda: isg.isg_thermo(g, gh, T, h, isg.ISG_FP32, stream, out=r32), stream, 5)
+    names = ("logZ", "E", "M", "C", "chi")
+    err = {}
+    for k, nm in enumerate(names):
+        d = (r32[k] - r64[k]).abs()
+        err[nm] = {"max_abs": float(d.max()), "max_rel": float((d / r64[k].abs().clamp_min(1e-300)).max()),
+                   "max_rel_of_grid_max": float(d.max() / r64[k].abs().max())}
+    out["cubic3x3x4_thermo"] = {"enumerate_ms": enum_ms, "enumerate_configs_per_s": (1 << 36) / (enum_ms * 1e-3),
+                                "grid": "512 T in [0.5,8] x 256 h in [-2,2]", "fp64_ms": t64, "fp32_ms": t32,
+                                "fp32_speedup": t64 / t32, "fp32_vs_fp64": err}
+    return out
 
 
 # ------------------------------------------------------------------------------ CPU oracle
@@ -380,6 +469,42 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------ profiling cases
+def run_profile_case(args):
+    """Small cases of the other kernels for ncu captures: W untimed + K timed launches each."""
+    import torch
+    from paper_1110_2561_gb300 import isg, workloads
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    res = {"case": args.profile_case}
+    if args.profile_case == "ea-batch":
+        lats = workloads.ea_instances()[:256]                     # shuffled order: all four shapes
+        b = isg.Batch([isg.isg_graph_create(l.n, l.edges) for l in lats])
+        for _ in range(args.warmup):
+            b.run(stream)
+        res["ms"] = _event_ms(lambda: b.run(stream), stream, args.steps)
+        res["configs_per_s"] = sum(1 << l.n for l in lats) / (res["ms"] * 1e-3)
+        b.status(stream)
+        b.close()
+    elif args.profile_case == "cubic-thermo":
+        lat = workloads.cubic(3, 3, 4, True)
+        gh = isg.isg_graph_create(lat.n, lat.edges)
+        g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=dev)
+        isg.isg_enumerate(gh, g, stream)
+        T, h = np.linspace(0.5, 8, 512), np.linspace(-2, 2, 256)
+        outs = tuple(torch.empty((512, 256), dtype=torch.float64, device=dev) for _ in range(5))
+        for prec, name in ((isg.ISG_FP64, "fp64_ms"), (isg.ISG_FP32, "fp32_ms")):
+            for _ in range(args.warmup):
+                isg.isg_thermo(g, gh, T, h, prec, stream, out=outs)
+            res[name] = _event_ms(lambda: isg.isg_thermo(g, gh, T, h, prec, stream, out=outs), stream, args.steps)
+    else:
+        raise SystemExit(f"unknown profile case {args.profile_case}")
+    torch.cuda.synchronize()
+    print(json.dumps(res), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -387,8 +512,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("isg", "reference"), default="isg")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target seconds of the oracle sample")
     ap.add_argument("--serving", action="store_true", help="run the request-stream (serving) benchmark instead")
+    ap.add_argument("--profile-case", choices=("ea-batch", "cubic-thermo"), default=None,
+                    help="run only a small case of another kernel (for ncu captures)")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--step-ms", type=float, default=20.0)
@@ -397,7 +525,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "isg":
         ap.error("at least 3 warm-up steps")
-    if args.serving:
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.serving:
         run_serving(args)
     elif args.impl == "reference":
         run_reference(args)

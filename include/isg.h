@@ -83,7 +83,8 @@ typedef struct {
     int64_t shard_lo;        /* enumerate shards [shard_lo, shard_hi) only; 0,0 = all */
     int64_t shard_hi;
     int32_t accumulate;      /* 1: add the counts into g_out; 0: overwrite g_out */
-    int32_t reserved1;
+    int32_t warp_aggregate;  /* 1: combine a warp's equal bins with __match_any_sync before the
+                                shared-memory reduction (kept for comparison; 0 is faster on GB300) */
 } isg_options;
 
 /* Fill *opt with the defaults (all planner choices, full range, overwrite). */

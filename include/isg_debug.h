@@ -34,11 +34,14 @@ ISG_API isg_status isg_debug_emulate(const isg_graph* graph, const isg_options* 
 /*
  * Measured peaks of the units that bound the enumeration kernel on the current device, in
  * lane-operations per second over the whole GPU: shared-memory 32-bit reductions with each lane
- * in its own bank (red_conflict_free) and with scattered addresses (red_scattered), and integer
- * ALU operations (alu: independent xor/add chains). Runs three short kernels on `stream` and
- * synchronises it. Any output may be NULL. Errors: ISG_ERR_CUDA.
+ * in its own bank (red_conflict_free) and with scattered addresses (red_scattered), integer ALU
+ * operations (alu: independent xor/add chains), and the scattered reductions counted through
+ * __match_any_sync warp aggregation (match_aggregated: lanes counted per second). Runs short
+ * kernels on `stream` and synchronises it. Any output may be NULL (a NULL match_aggregated
+ * skips that kernel). Errors: ISG_ERR_CUDA.
  */
-ISG_API isg_status isg_probe_peaks(void* stream, double* red_conflict_free, double* red_scattered, double* alu);
+ISG_API isg_status isg_probe_peaks(void* stream, double* red_conflict_free, double* red_scattered, double* alu,
+                                   double* match_aggregated);
 
 #ifdef __cplusplus
 }

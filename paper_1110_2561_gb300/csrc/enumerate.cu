@@ -28,6 +28,20 @@ struct SmemSink {
     }
 };
 
+// Warp-aggregated counting: lanes holding the same address elect one lane, which adds the
+// number of such lanes. Kept to measure against SmemSink: on GB300 match.any issues far more
+// slowly than the reduction it saves.
+struct MatchSink {
+    __device__ __forceinline__ void operator()(uint32_t& addr) const {
+        const unsigned peers = __match_any_sync(0xffffffffu, addr);
+        const int leader = __ffs(static_cast<int>(peers)) - 1;
+        if ((int)(threadIdx.x & 31) == leader) {
+            const unsigned cnt = static_cast<unsigned>(__popc(peers));
+            asm volatile("red.shared.add.u32 [%0], %1;" : "+r"(addr) : "r"(cnt) : "memory");
+        }
+    }
+};
+
 struct EnumArgs {
     const uint64_t* blob;
     int64_t* g;                     // public table (n_e * n_m int64)
@@ -62,7 +76,7 @@ __device__ __forceinline__ void flush_bins(const ProgHeader* hd, uint32_t* hist,
     }
 }
 
-template <int B>
+template <int B, class Sink>
 __global__ void __launch_bounds__(1024) enumerate_kernel(EnumArgs a) {
     extern __shared__ __align__(16) uint64_t smem[];
     stage_blob(smem, a.blob, a.blob_words);
@@ -78,7 +92,7 @@ __global__ void __launch_bounds__(1024) enumerate_kernel(EnumArgs a) {
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(hist + (warp % a.copies) * nb));
-    SmemSink sink;
+    Sink sink;
     bool done = false;
     for (;;) {
         for (int r = 0; r < a.flush_rounds; ++r) {
@@ -152,18 +166,24 @@ DeviceInfo device_info() {
 
 // Grid: the planned CTAs per SM, capped by what the registers and shared memory of this
 // instantiation allow (cudaOccupancyMaxActiveBlocksPerMultiprocessor), never more than tasks.
-template <int B>
-static void launch_b(const Plan& p, const EnumArgs& a, cudaStream_t s) {
+template <int B, class Sink>
+static void launch_bs(const Plan& p, const EnumArgs& a, cudaStream_t s) {
     const int smem = (int)(p.smem_bytes + 16);
-    ISG_CUDA(cudaFuncSetAttribute(enumerate_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    ISG_CUDA(cudaFuncSetAttribute(enumerate_kernel<B, Sink>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int occ = 0;
-    ISG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, enumerate_kernel<B>, p.threads, smem));
+    ISG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, enumerate_kernel<B, Sink>, p.threads, smem));
     if (occ < 1) fail(ISG_ERR_TOO_LARGE, "enumeration kernel does not fit an SM with this block size");
     const DeviceInfo d = device_info();
     const uint64_t want = (uint64_t)d.sms * (uint64_t)std::min(occ, p.ctas_per_sm);
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, p.n_tasks));
-    enumerate_kernel<B><<<grid, p.threads, smem, s>>>(a);
+    enumerate_kernel<B, Sink><<<grid, p.threads, smem, s>>>(a);
     ISG_CUDA(cudaGetLastError());
+}
+
+template <int B>
+static void launch_b(const Plan& p, const EnumArgs& a, cudaStream_t s) {
+    if (p.aggregate) launch_bs<B, MatchSink>(p, a, s);
+    else launch_bs<B, SmemSink>(p, a, s);
 }
 
 // Enqueue the kernels of one plan; `table` must be zeroed (or hold counts to add to).

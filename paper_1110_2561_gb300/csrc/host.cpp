@@ -199,6 +199,7 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d) {
     if (o.flush_tasks > 0) F = std::min<uint64_t>(F, (uint64_t)o.flush_tasks);
     p.flush_rounds = (int)std::min<uint64_t>(F, 1u << 30);
     p.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(p.n_tasks, (uint64_t)d.sms * p.ctas_per_sm));
+    p.aggregate = o.warp_aggregate != 0;
     return p;
 }
 

@@ -46,6 +46,7 @@ struct Plan {
     uint64_t prefix_base = 0;  // first lane prefix (multiple of 32)
     uint64_t n_tasks = 0;      // warp tasks: 32 lane prefixes each
     int stride = 0;            // histogram row stride (bins)
+    bool aggregate = false;    // warp-aggregated counting (__match_any_sync)
     int threads = 512, copies = 1, ctas_per_sm = 2, flush_rounds = 1;
     int grid = 0;
     size_t smem_bytes = 0;

@@ -12,6 +12,8 @@ namespace isg {
 
 constexpr int kProbeWords = 2048;   // words per warp table (power of two); two warps share one
 
+// MODE 3: MODE 1's addresses, aggregated first: __match_any_sync, one leader lane per address
+// adds the count (what a warp-aggregated histogram does per configuration).
 // MODE 0: each lane adds to 32 words of its own bank (lane + 32 j), addresses held in registers,
 // so the loop is nothing but reductions. MODE 1: 32 scattered per-lane addresses in registers
 // (independent odd strides per lane), the same reductions with bank conflicts. MODE 2: integer
@@ -25,7 +27,7 @@ __global__ void __launch_bounds__(512) probe_kernel(int iters, unsigned* sink) {
     __syncthreads();
     const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(t));
     unsigned x0 = lane, x1 = lane * 3u, x2 = lane * 5u, x3 = lane * 7u;
-    if (MODE == 0 || MODE == 1) {
+    if (MODE == 0 || MODE == 1 || MODE == 3) {
         uint32_t a[32];
         const unsigned s = ((lane * 2654435761u) >> 7) | 1u;
 #pragma unroll
@@ -33,7 +35,15 @@ __global__ void __launch_bounds__(512) probe_kernel(int iters, unsigned* sink) {
             a[j] = base + 4u * (MODE == 0 ? (unsigned)(lane + 32 * j) : ((lane * 97u + j * s) & (kProbeWords - 1)));
         for (int i = 0; i < iters; i += 32) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a[j]) : "memory");
+            for (int j = 0; j < 32; ++j) {
+                if (MODE == 3) {
+                    const unsigned peers = __match_any_sync(0xffffffffu, a[j]);
+                    if (lane == __ffs(static_cast<int>(peers)) - 1)
+                        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a[j]), "r"((unsigned)__popc(peers)) : "memory");
+                } else {
+                    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a[j]) : "memory");
+                }
+            }
         }
     } else {
         for (int i = 0; i < iters; ++i) {
@@ -77,7 +87,8 @@ static double probe_rate(cudaStream_t s, unsigned* sink, int sms, double ops_per
 
 using namespace isg;
 
-extern "C" isg_status isg_probe_peaks(void* stream, double* red_conflict_free, double* red_scattered, double* alu) {
+extern "C" isg_status isg_probe_peaks(void* stream, double* red_conflict_free, double* red_scattered, double* alu,
+                                      double* match_aggregated) {
     try {
         clear_error();
         cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -89,11 +100,13 @@ extern "C" isg_status isg_probe_peaks(void* stream, double* red_conflict_free, d
         const double r0 = probe_rate<0>(s, sink, sms, 1.0);
         const double r1 = probe_rate<1>(s, sink, sms, 1.0);
         const double r2 = probe_rate<2>(s, sink, sms, 8.0);
+        const double r3 = match_aggregated ? probe_rate<3>(s, sink, sms, 1.0) : 0.0;
         ISG_CUDA(cudaFreeAsync(sink, s));
         ISG_CUDA(cudaStreamSynchronize(s));
         if (red_conflict_free) *red_conflict_free = r0;
         if (red_scattered) *red_scattered = r1;
         if (alu) *alu = r2;
+        if (match_aggregated) *match_aggregated = r3;
         return ISG_OK;
     } catch (const Error& e) {
         set_error(e.msg);

@@ -31,7 +31,7 @@ class isg_options(ctypes.Structure):
         "struct_size", "max_spins", "inner_bits", "low_bits", "block_threads", "copies", "ctas_per_sm",
         "flush_tasks", "shard_bits", "bin_stride")] + [
         ("shard_lo", ctypes.c_int64), ("shard_hi", ctypes.c_int64),
-        ("accumulate", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+        ("accumulate", ctypes.c_int32), ("warp_aggregate", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -49,7 +49,7 @@ _SIGS = {
     "isg_version": (ctypes.c_char_p, []),
     "isg_debug_plan": (i32, [vp, vp, i32, vp]),
     "isg_debug_emulate": (i32, [vp, vp, vp]),
-    "isg_probe_peaks": (i32, [vp, vp, vp, vp]),
+    "isg_probe_peaks": (i32, [vp, vp, vp, vp, vp]),
     "isg_enumerate_noalloc": (i32, [vp, vp, vp, vp]),
     "isg_enumerate_batch": (i32, [i32, vp, vp, vp, i32, vp]),
     "isg_batch_create": (i32, [i32, vp, vp, ctypes.POINTER(vp)]),
@@ -407,9 +407,10 @@ def isg_debug_emulate(graph: Graph, **options) -> np.ndarray:
 
 def isg_probe_peaks(stream=None) -> dict:
     """Measured lane-op rates (per second, whole GPU) of red.shared (conflict-free, scattered) and ALU."""
-    v = [ctypes.c_double() for _ in range(3)]
+    v = [ctypes.c_double() for _ in range(4)]
     _check(lib().isg_probe_peaks(_stream_handle(stream), *[ctypes.byref(x) for x in v]))
-    return {"red_conflict_free": v[0].value, "red_scattered": v[1].value, "alu": v[2].value}
+    return {"red_conflict_free": v[0].value, "red_scattered": v[1].value, "alu": v[2].value,
+            "match_aggregated": v[3].value}
 
 
 def isg_last_error() -> str:

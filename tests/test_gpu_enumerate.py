@@ -71,7 +71,8 @@ def test_table1_on_gpu(isg, cuda, table1_triples):
 
 PLANS = [dict(inner_bits=6), dict(low_bits=1, inner_bits=4), dict(low_bits=4, inner_bits=9), dict(low_bits=5, inner_bits=12),
          dict(block_threads=64, copies=1), dict(block_threads=1024, copies=16), dict(block_threads=256, copies=3),
-         dict(flush_tasks=1), dict(ctas_per_sm=1, flush_tasks=1, block_threads=96, copies=2), dict(low_bits=2, inner_bits=2)]
+         dict(flush_tasks=1), dict(ctas_per_sm=1, flush_tasks=1, block_threads=96, copies=2), dict(low_bits=2, inner_bits=2),
+         dict(warp_aggregate=1), dict(bin_stride=64), dict(bin_stride=33, warp_aggregate=1, copies=1)]
 
 
 @pytest.mark.parametrize("kw", PLANS, ids=lambda k: ",".join(f"{a}={b}" for a, b in k.items()))
