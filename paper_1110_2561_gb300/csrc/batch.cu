@@ -196,7 +196,7 @@ static BatchPlan plan_batch(int n, const isg_graph* const* graphs, const isg_opt
     for (auto& in : bp.inst) { in.tile_begin = t; t += in.n_tiles; }
     bp.n_tiles = t;
     bp.prog_words = (max_words + 1) & ~1;
-    bp.slot_words = bp.prog_words + (max_bins + 1) / 2;
+    bp.slot_words = (bp.prog_words + (max_bins + 1) / 2 + 1) & ~1;   // even: slots stay 16-byte aligned
     bp.threads = o.block_threads > 0 ? o.block_threads : 512;
     if (bp.threads % 32 || bp.threads > 512) fail(ISG_ERR_INVALID, "batch block_threads must be a multiple of 32, at most 512");
     bp.warps_per_cta = bp.threads / 32;

@@ -39,6 +39,17 @@ constexpr int kMaxSpins = 64;
 constexpr int kMaxClasses = 21;   // |J| <= 2^20 decomposes into at most 21 binary weights
 constexpr int kMaxLow = 6;        // largest low block
 
+// Per-spin record of a program, 48 bytes and 16-byte aligned, so a mid flip reads everything it
+// needs about its spin with three 128-bit shared-memory loads.
+struct alignas(16) SiteRec {
+    uint64_t sgn;            // neighbours j with J_kj < 0
+    uint64_t mask0;          // neighbours whose |J_kj| has weight class 0
+    int32_t degw;            // sum_j |J_kj|
+    int32_t A[kMaxLow];      // A[k] = -2 J_{k,this} sE for the low spins k (this spin outside the block)
+    int32_t pad;
+};
+static_assert(sizeof(SiteRec) == 48, "site record must be three 16-byte words");
+
 // Program header, the first kHeaderWords words of a program blob (fields 32-bit unless noted).
 struct ProgHeader {
     int32_t n;         // spins
@@ -47,44 +58,66 @@ struct ProgHeader {
     int32_t nc;        // weight classes
     int32_t n_m;       // N + 1
     int32_t n_e_c;     // compact energy bins
-    int32_t nbins_c;   // n_e_c * n_m
+    int32_t nbins_c;   // n_e_c * stride
     int32_t sE;        // address bytes per unit of field
     int32_t G;         // energy stride
     int32_t words;     // blob length in 64-bit words
     int64_t e_lo;      // energy of compact bin 0
     int64_t S;         // sum |J|; public bin e = (E + S) / 2
-    int32_t off_sgn;   // word offsets of the arrays below
-    int32_t off_mask;
-    int32_t off_i32;   // int32 area: w[nc], degw[n], A[n * kMaxLow]
+    int32_t off_site;  // word offsets: site records [n], extra class masks [n * (nc - 1)], weights [nc]
+    int32_t off_maskx;
+    int32_t off_w;
     int32_t stride;    // histogram row stride in bins (>= n_m), chosen against bank conflicts
+    int32_t w0;        // weight of class 0
+    int32_t pad;
 };
 constexpr int kHeaderWords = (int)(sizeof(ProgHeader) / 8);
-static_assert(sizeof(ProgHeader) % 8 == 0, "program header must be whole words");
+static_assert(sizeof(ProgHeader) % 16 == 0, "program header must keep the site records 16-byte aligned");
 
 // Read-only view of a program (in shared memory on the device, host memory in emulation).
 struct ProgView {
-    int n, q, b, nc, n_m, stride, sE, G;
+    int n, q, b, nc, n_m, stride, sE, G, w0;
     int64_t e_lo;
-    const uint64_t* sgn;    // [n]       neighbours of k with negative coupling
-    const uint64_t* mask;   // [n * nc]  neighbours of k whose |J| has class c
-    const int32_t* w;       // [nc]      class weights
-    const int32_t* degw;    // [n]       sum_j |J_kj|
-    const int32_t* A;       // [n * kMaxLow] A[r * kMaxLow + k] = -2 J_kr sE for low spins k
+    const SiteRec* site;     // [n]
+    const uint64_t* maskx;   // [n * (nc - 1)] masks of classes 1.. (class c of spin k at k*(nc-1)+c-1)
+    const int32_t* w;        // [nc] class weights
 };
 
 ISG_HD ProgView make_view(const uint64_t* blob) {
     const ProgHeader* h = reinterpret_cast<const ProgHeader*>(blob);
     ProgView v;
     v.n = h->n; v.q = h->q; v.b = h->b; v.nc = h->nc; v.n_m = h->n_m; v.stride = h->stride; v.sE = h->sE;
-    v.G = h->G;
+    v.G = h->G; v.w0 = h->w0;
     v.e_lo = h->e_lo;
-    v.sgn = blob + h->off_sgn;
-    v.mask = blob + h->off_mask;
-    const int32_t* i32 = reinterpret_cast<const int32_t*>(blob + h->off_i32);
-    v.w = i32;
-    v.degw = i32 + h->nc;
-    v.A = i32 + h->nc + h->n;
+    v.site = reinterpret_cast<const SiteRec*>(blob + h->off_site);
+    v.maskx = blob + h->off_maskx;
+    v.w = reinterpret_cast<const int32_t*>(blob + h->off_w);
     return v;
+}
+
+// The fields of one site record, read with three 128-bit loads on the device.
+struct SiteVals {
+    uint64_t sgn, mask0;
+    int32_t degw;
+    int32_t A[kMaxLow];
+};
+
+ISG_HD void load_site(const ProgView& p, int k, SiteVals& v) {
+#if defined(__CUDA_ARCH__)
+    const uint4* r = reinterpret_cast<const uint4*>(p.site + k);
+    const uint4 a = r[0], b = r[1], c = r[2];
+    v.sgn = (uint64_t)a.x | ((uint64_t)a.y << 32);
+    v.mask0 = (uint64_t)a.z | ((uint64_t)a.w << 32);
+    v.degw = (int32_t)b.x;
+    v.A[0] = (int32_t)b.y; v.A[1] = (int32_t)b.z; v.A[2] = (int32_t)b.w;
+    v.A[3] = (int32_t)c.x; v.A[4] = (int32_t)c.y; v.A[5] = (int32_t)c.z;
+#else
+    const SiteRec& r = p.site[k];
+    v.sgn = r.sgn;
+    v.mask0 = r.mask0;
+    v.degw = r.degw;
+    for (int i = 0; i < kMaxLow; ++i) v.A[i] = r.A[i];
+#endif
 }
 
 ISG_HD int popc64(uint64_t x) {
@@ -109,12 +142,18 @@ ISG_CHD constexpr int gray_c(int u) { return u ^ (u >> 1); }
 
 // Local field h_k = sum_j J_kj S_j of configuration st: a neighbour j with J_kj = +-w contributes
 // +w when (bit_j XOR [J_kj < 0]) is 1 and -w otherwise (Sec. 3b: XOR, mask, count).
-ISG_HD int field(const ProgView& p, uint64_t st, int k) {
-    const uint64_t x = st ^ p.sgn[k];
-    int acc = 0;
+ISG_HD int field_of(const ProgView& p, const SiteVals& sv, uint64_t st, int k) {
+    const uint64_t x = st ^ sv.sgn;
+    int acc = p.w0 * popc64(x & sv.mask0);
 #pragma unroll 1
-    for (int c = 0; c < p.nc; ++c) acc += p.w[c] * popc64(x & p.mask[k * p.nc + c]);
-    return 2 * acc - p.degw[k];
+    for (int c = 1; c < p.nc; ++c) acc += p.w[c] * popc64(x & p.maskx[k * (p.nc - 1) + c - 1]);
+    return 2 * acc - sv.degw;
+}
+
+ISG_HD int field(const ProgView& p, uint64_t st, int k) {
+    SiteVals sv;
+    load_site(p, k, sv);
+    return field_of(p, sv, st, k);
 }
 
 // Byte offset of the bin of configuration st, from scratch: E = -1/2 sum_k S_k h_k (Eq. 1 with
@@ -162,13 +201,14 @@ ISG_HD void low_block(uint32_t& idx, const int32_t (&Gk)[B], Sink& sink) {
 // and every low spin k bonded to r sees its field change by -2 S_r J_kr.
 template <int B>
 ISG_HD void mid_flip(const ProgView& p, uint64_t& st, int r, uint32_t& idx, int32_t (&Gk)[B]) {
-    const int h = field(p, st, r);
+    SiteVals sv;
+    load_site(p, r, sv);
+    const int h = field_of(p, sv, st, r);
     const bool up = (st >> r) & 1;
     const int32_t d = h * p.sE - 4;
     idx += static_cast<uint32_t>(up ? d : -d);
-    const int32_t* Ar = p.A + r * kMaxLow;
 #pragma unroll
-    for (int k = 0; k < B; ++k) Gk[k] += up ? Ar[k] : -Ar[k];
+    for (int k = 0; k < B; ++k) Gk[k] += up ? sv.A[k] : -sv.A[k];
     st ^= 1ull << r;
 }
 

@@ -81,8 +81,7 @@ int choose_stride(const isg_graph& g, int requested) {
 }
 
 static size_t blob_words(int n, int nc) {
-    size_t i32 = (size_t)nc + n + (size_t)n * kMaxLow;
-    return kHeaderWords + (size_t)n + (size_t)n * nc + (i32 + 1) / 2;
+    return kHeaderWords + (size_t)n * (sizeof(SiteRec) / 8) + (size_t)n * (nc - 1) + ((size_t)nc + 1) / 2;
 }
 
 Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d) {
@@ -228,36 +227,36 @@ std::vector<uint64_t> build_program(const isg_graph& g, const Plan& p) {
     h.words = (int32_t)words;
     h.e_lo = g.e_lo;
     h.S = g.S;
-    h.off_sgn = kHeaderWords;
-    h.off_mask = kHeaderWords + n;
-    h.off_i32 = kHeaderWords + n + n * nc;
+    h.off_site = kHeaderWords;
+    h.off_maskx = kHeaderWords + n * (int)(sizeof(SiteRec) / 8);
+    h.off_w = h.off_maskx + n * (nc - 1);
+    h.w0 = w[0];
     std::memcpy(blob.data(), &h, sizeof h);
-    uint64_t* sgn = blob.data() + h.off_sgn;
-    uint64_t* mask = blob.data() + h.off_mask;
-    int32_t* i32 = reinterpret_cast<int32_t*>(blob.data() + h.off_i32);
-    int32_t* wv = i32;
-    int32_t* degw = i32 + nc;
-    int32_t* A = i32 + nc + n;
+    SiteRec* site = reinterpret_cast<SiteRec*>(blob.data() + h.off_site);
+    uint64_t* maskx = blob.data() + h.off_maskx;
+    int32_t* wv = reinterpret_cast<int32_t*>(blob.data() + h.off_w);
     for (int c = 0; c < nc; ++c) wv[c] = w[c];
     for (int a = 0; a < n; ++a) {
         const int ca = p.perm[a];
+        SiteRec& rec = site[a];
         int64_t dw = 0;
         for (int b = 0; b < n; ++b) {
             const int64_t J = g.K[(size_t)ca * n + p.perm[b]];
             if (!J) continue;
             const int64_t aJ = J < 0 ? -J : J;
             dw += aJ;
-            if (J < 0) sgn[a] |= 1ull << b;
+            if (J < 0) rec.sgn |= 1ull << b;
             for (int c = 0; c < nc; ++c) {
                 const bool in = binary ? ((aJ & w[c]) != 0) : (aJ == w[c]);
-                if (in) mask[(size_t)a * nc + c] |= 1ull << b;
+                if (!in) continue;
+                if (c == 0) rec.mask0 |= 1ull << b;
+                else maskx[(size_t)a * (nc - 1) + c - 1] |= 1ull << b;
             }
         }
-        degw[a] = (int32_t)dw;
-    }
-    for (int r = 0; r < n; ++r)
+        rec.degw = (int32_t)dw;
         for (int k = 0; k < p.b; ++k)
-            A[r * kMaxLow + k] = (r >= p.b) ? (int32_t)(-2 * g.K[(size_t)p.perm[k] * n + p.perm[r]] * h.sE) : 0;
+            rec.A[k] = (a >= p.b) ? (int32_t)(-2 * g.K[(size_t)p.perm[k] * n + ca] * h.sE) : 0;
+    }
     return blob;
 }
 

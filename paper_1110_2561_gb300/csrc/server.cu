@@ -245,7 +245,7 @@ static bool issue_step_locked(isg_server* s) {
     bp.inst = desc;
     bp.n_tiles = tiles;
     bp.prog_words = (max_words + 1) & ~1;
-    bp.slot_words = bp.prog_words + (max_bins + 1) / 2;
+    bp.slot_words = (bp.prog_words + (max_bins + 1) / 2 + 1) & ~1;   // even: slots stay 16-byte aligned
     bp.threads = s->opt.block_threads > 0 ? std::min(512, s->opt.block_threads) : 512;
     bp.warps_per_cta = bp.threads / 32;
     bp.smem = (size_t)bp.slot_words * 8 * bp.warps_per_cta;

@@ -57,21 +57,30 @@ __device__ __forceinline__ F warp_sum(F v) {
     return v;
 }
 
-// ln g for every bin (double, from the int64 count); -inf marks an empty bin.
-__global__ void log_counts_kernel(const int64_t* g, int nbins, double* lng) {
+// ln g for every bin, computed in double from the int64 count and stored in double and (rounded)
+// in float; -inf marks an empty bin.
+__global__ void log_counts_kernel(const int64_t* g, int nbins, double* lng, float* lngf) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nbins; i += gridDim.x * blockDim.x) {
         const int64_t c = g[i];
-        lng[i] = c > 0 ? log((double)c) : -INFINITY;
+        const double l = c > 0 ? log((double)c) : -INFINITY;
+        lng[i] = l;
+        lngf[i] = (float)l;
     }
 }
 
-// One CTA per temperature. Shared memory: L[n_m] (double), mu[n_m], var[n_m] (F).
+template <class F> __device__ __forceinline__ const F* pick(const double* d, const float* f);
+template <> __device__ __forceinline__ const double* pick<double>(const double* d, const float*) { return d; }
+template <> __device__ __forceinline__ const float* pick<float>(const double*, const float* f) { return f; }
+
+// One CTA per temperature. Shared memory: L[n_m] (double), mu[n_m], var[n_m], Lr[n_m] (F).
 template <class F>
-__global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double* lng) {
+__global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double* lngd, const float* lngf) {
+    const F* lng = pick<F>(lngd, lngf);
     extern __shared__ __align__(16) unsigned char sm[];
     double* L = reinterpret_cast<double*>(sm);
     F* mu = reinterpret_cast<F*>(L + a.n_m);
     F* var = mu + a.n_m;
+    F* Lr = var + a.n_m;                 // L - max L, in the working precision (-inf: empty column)
     __shared__ double s_Lmax;
     const int it = blockIdx.x;
     const double T = a.T[it];
@@ -83,9 +92,9 @@ __global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double*
         F xmax = (F)-INFINITY;
         int earg = 0;
         for (int e = lane; e < a.n_e; e += 32) {
-            const double l = lng[(size_t)e * a.n_m + m];
-            if (l == -INFINITY) continue;
-            const F x = (F)l - (F)(a.e_min + 2 * e) * invT;
+            const F l = lng[(size_t)e * a.n_m + m];
+            if (l == (F)-INFINITY) continue;
+            const F x = l - (F)(a.e_min + 2 * e) * invT;
             if (x > xmax) { xmax = x; earg = e; }
         }
         const F wmax = warp_max(xmax);
@@ -98,10 +107,10 @@ __global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double*
         const F Eref = (F)(a.e_min + 2 * __shfl_sync(0xffffffffu, earg, __ffs(hit) - 1));
         F s0 = 0, s1 = 0;
         for (int e = lane; e < a.n_e; e += 32) {
-            const double l = lng[(size_t)e * a.n_m + m];
-            if (l == -INFINITY) continue;
+            const F l = lng[(size_t)e * a.n_m + m];
+            if (l == (F)-INFINITY) continue;
             const F En = (F)(a.e_min + 2 * e);
-            const F w = ex<F>((F)l - En * invT - wmax);
+            const F w = ex<F>(l - En * invT - wmax);
             s0 += w;
             s1 += w * (En - Eref);
         }
@@ -110,10 +119,10 @@ __global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double*
         const F m1 = Eref + s1 / s0;
         F s2 = 0;
         for (int e = lane; e < a.n_e; e += 32) {
-            const double l = lng[(size_t)e * a.n_m + m];
-            if (l == -INFINITY) continue;
+            const F l = lng[(size_t)e * a.n_m + m];
+            if (l == (F)-INFINITY) continue;
             const F En = (F)(a.e_min + 2 * e);
-            const F w = ex<F>((F)l - En * invT - wmax);
+            const F w = ex<F>(l - En * invT - wmax);
             const F d = En - m1;
             s2 += w * d * d;
         }
@@ -132,6 +141,8 @@ __global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double*
     }
     __syncthreads();
     const double Lmax = s_Lmax;
+    for (int m = threadIdx.x; m < a.n_m; m += blockDim.x) Lr[m] = L[m] == -INFINITY ? (F)-INFINITY : (F)(L[m] - Lmax);
+    __syncthreads();
 
     // Stage 2: one thread per field value.
     for (int ih = threadIdx.x; ih < a.nh; ih += blockDim.x) {
@@ -139,15 +150,15 @@ __global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double*
         const F hT = (F)(hd / T), hF = (F)hd;
         F amax = (F)-INFINITY;
         for (int m = 0; m < a.n_m; ++m) {
-            if (L[m] == -INFINITY) continue;
-            const F am = (F)(L[m] - Lmax) + hT * (F)(2 * m - a.n);
+            if (Lr[m] == (F)-INFINITY) continue;
+            const F am = Lr[m] + hT * (F)(2 * m - a.n);
             amax = fmax(amax, am);
         }
         F z = 0, zM = 0, zH = 0;
         for (int m = 0; m < a.n_m; ++m) {
-            if (L[m] == -INFINITY) continue;
+            if (Lr[m] == (F)-INFINITY) continue;
             const F Mm = (F)(2 * m - a.n);
-            const F p = ex<F>((F)(L[m] - Lmax) + hT * Mm - amax);
+            const F p = ex<F>(Lr[m] + hT * Mm - amax);
             z += p;
             zM += p * Mm;
             zH += p * (mu[m] - hF * Mm);
@@ -155,9 +166,9 @@ __global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double*
         const F mM = zM / z, mH = zH / z;
         F vH = 0, vM = 0;
         for (int m = 0; m < a.n_m; ++m) {
-            if (L[m] == -INFINITY) continue;
+            if (Lr[m] == (F)-INFINITY) continue;
             const F Mm = (F)(2 * m - a.n);
-            const F p = ex<F>((F)(L[m] - Lmax) + hT * Mm - amax);
+            const F p = ex<F>(Lr[m] + hT * Mm - amax);
             const F dH = mu[m] - hF * Mm - mH, dM = Mm - mM;
             vH += p * (var[m] + dH * dH);
             vM += p * dM * dM;
@@ -181,17 +192,18 @@ __global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double*
                  std::string(#call) + ": " + cudaGetErrorString(e_));                               \
     } while (0)
 
-// Enqueue the thermodynamics kernels; all pointers on the device. lng: n_e * n_m doubles scratch.
-void launch_thermo(const ThermoArgs& a, double* lng, int precision, cudaStream_t s) {
+// Enqueue the thermodynamics kernels; all pointers on the device. lng: n_e * n_m doubles, lngf:
+// n_e * n_m floats of scratch.
+void launch_thermo(const ThermoArgs& a, double* lng, float* lngf, int precision, cudaStream_t s) {
     const int nbins = a.n_e * a.n_m;
-    log_counts_kernel<<<std::min(1024, (nbins + 255) / 256), 256, 0, s>>>(a.g, nbins, lng);
+    log_counts_kernel<<<std::min(1024, (nbins + 255) / 256), 256, 0, s>>>(a.g, nbins, lng, lngf);
     ISG_CUDA(cudaGetLastError());
     if (precision == ISG_FP64) {
-        const size_t smem = (size_t)a.n_m * (8 + 2 * sizeof(double));
-        thermo_kernel<double><<<a.nT, 256, smem, s>>>(a, lng);
+        const size_t smem = (size_t)a.n_m * (8 + 3 * sizeof(double));
+        thermo_kernel<double><<<a.nT, 256, smem, s>>>(a, lng, lngf);
     } else {
-        const size_t smem = (size_t)a.n_m * (8 + 2 * sizeof(float));
-        thermo_kernel<float><<<a.nT, 256, smem, s>>>(a, lng);
+        const size_t smem = (size_t)a.n_m * (8 + 3 * sizeof(float));
+        thermo_kernel<float><<<a.nT, 256, smem, s>>>(a, lng, lngf);
     }
     ISG_CUDA(cudaGetLastError());
 }
@@ -221,6 +233,7 @@ extern "C" isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const is
         size_t off = 0;
         auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) & ~(size_t)255; return o; };
         const size_t o_lng = take(sizeof(double) * (size_t)n_e * n_m);
+        const size_t o_lngf = take(sizeof(float) * (size_t)n_e * n_m);
         const size_t o_T = take(sizeof(double) * nT), o_h = take(sizeof(double) * nh);
         const size_t o_g = g_on_device ? 0 : take(gbytes);
         const size_t o_out = out_on_device ? 0 : take(5 * sizeof(double) * pts);
@@ -249,7 +262,7 @@ extern "C" isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const is
                           : out_on_device ? outs_host[k]
                                           : reinterpret_cast<double*>(scratch + o_out) + k * pts;
         a.logZ = outs_dev[0]; a.E = outs_dev[1]; a.M = outs_dev[2]; a.C = outs_dev[3]; a.chi = outs_dev[4];
-        launch_thermo(a, reinterpret_cast<double*>(scratch + o_lng), precision, s);
+        launch_thermo(a, reinterpret_cast<double*>(scratch + o_lng), reinterpret_cast<float*>(scratch + o_lngf), precision, s);
         if (!out_on_device) {
             for (int k = 0; k < 5; ++k)
                 if (outs_host[k])
