@@ -70,7 +70,7 @@ typedef struct {
     int32_t struct_size;     /* sizeof(isg_options); set by isg_options_init */
     int32_t max_spins;       /* isg_enumerate refuses N > max_spins (default 40; at most 62) */
     int32_t inner_bits;      /* q: each thread walks 2^q configurations per task (0 = plan) */
-    int32_t low_bits;        /* b <= 6: unrolled innermost Gray bits (0 = plan) */
+    int32_t low_bits;        /* b <= 7: unrolled innermost Gray bits (0 = plan) */
     int32_t block_threads;   /* threads per CTA, multiple of 32, <= 1024 (0 = plan) */
     int32_t copies;          /* privatised 32-bit histogram copies per CTA (0 = plan) */
     int32_t ctas_per_sm;     /* resident CTAs per SM to launch (0 = plan) */

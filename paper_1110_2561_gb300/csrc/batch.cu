@@ -245,6 +245,7 @@ void launch_batch(const BatchPlan& bp, const BatchInst* d_inst, const uint64_t* 
         case 4: launch_batch_b<4>(bp, a, s, ctas_per_sm); break;
         case 5: launch_batch_b<5>(bp, a, s, ctas_per_sm); break;
         case 6: launch_batch_b<6>(bp, a, s, ctas_per_sm); break;
+        case 7: launch_batch_b<7>(bp, a, s, ctas_per_sm); break;
         default: fail(ISG_ERR_INTERNAL, "bad low block size");
     }
     if (!bp.small_ids.empty()) {

@@ -37,7 +37,7 @@ namespace isg {
 
 constexpr int kMaxSpins = 64;
 constexpr int kMaxClasses = 21;   // |J| <= 2^20 decomposes into at most 21 binary weights
-constexpr int kMaxLow = 6;        // largest low block
+constexpr int kMaxLow = 7;        // largest low block
 
 // Per-spin record of a program, 48 bytes and 16-byte aligned, so a mid flip reads everything it
 // needs about its spin with three 128-bit shared-memory loads.
@@ -46,7 +46,6 @@ struct alignas(16) SiteRec {
     uint64_t mask0;          // neighbours whose |J_kj| has weight class 0
     int32_t degw;            // sum_j |J_kj|
     int32_t A[kMaxLow];      // A[k] = -2 J_{k,this} sE for the low spins k (this spin outside the block)
-    int32_t pad;
 };
 static_assert(sizeof(SiteRec) == 48, "site record must be three 16-byte words");
 
@@ -110,7 +109,7 @@ ISG_HD void load_site(const ProgView& p, int k, SiteVals& v) {
     v.mask0 = (uint64_t)a.z | ((uint64_t)a.w << 32);
     v.degw = (int32_t)b.x;
     v.A[0] = (int32_t)b.y; v.A[1] = (int32_t)b.z; v.A[2] = (int32_t)b.w;
-    v.A[3] = (int32_t)c.x; v.A[4] = (int32_t)c.y; v.A[5] = (int32_t)c.z;
+    v.A[3] = (int32_t)c.x; v.A[4] = (int32_t)c.y; v.A[5] = (int32_t)c.z; v.A[6] = (int32_t)c.w;
 #else
     const SiteRec& r = p.site[k];
     v.sgn = r.sgn;

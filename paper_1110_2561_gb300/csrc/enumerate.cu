@@ -214,6 +214,7 @@ void launch_enumeration(const Plan& p, const uint64_t* d_blob, int blob_words, i
         case 4: launch_b<4>(p, a, s); break;
         case 5: launch_b<5>(p, a, s); break;
         case 6: launch_b<6>(p, a, s); break;
+        case 7: launch_b<7>(p, a, s); break;
         default: fail(ISG_ERR_INTERNAL, "bad low block size");
     }
 }

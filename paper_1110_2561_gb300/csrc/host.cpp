@@ -116,7 +116,7 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d) {
 
     // Low block: greedy independent set among the spins below the shard bits, lowest degree first.
     int bmax = o.low_bits > 0 ? o.low_bits : kMaxLow;
-    if (bmax > kMaxLow) fail(ISG_ERR_INVALID, "low_bits must be <= 6");
+    if (bmax > kMaxLow) fail(ISG_ERR_INVALID, "low_bits must be <= 7");
     bmax = std::min(bmax, free - 5);
     // Minimum-residual-degree greedy: repeatedly take the candidate with the fewest neighbours
     // among the remaining candidates (ties: lowest index), then drop it and its neighbours.
@@ -446,6 +446,7 @@ isg_status isg_debug_emulate(const isg_graph* g, const isg_options* opt, int64_t
                 case 4: emulate_tasks<4>(v, p, hist, bad); break;
                 case 5: emulate_tasks<5>(v, p, hist, bad); break;
                 case 6: emulate_tasks<6>(v, p, hist, bad); break;
+                case 7: emulate_tasks<7>(v, p, hist, bad); break;
                 default: fail(ISG_ERR_INTERNAL, "bad low block size");
             }
         }

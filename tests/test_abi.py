@@ -67,7 +67,7 @@ def test_duplicate_bonds_summed(isg):
 def test_options_validation(isg):
     g = isg.isg_graph_create(16, w.square(4, 4, True).edges)
     for bad in [dict(shard_bits=17), dict(shard_bits=2, shard_lo=3, shard_hi=2), dict(shard_bits=2, shard_lo=0, shard_hi=5),
-                dict(low_bits=7), dict(inner_bits=12), dict(block_threads=48), dict(copies=99)]:
+                dict(low_bits=8), dict(inner_bits=12), dict(block_threads=48), dict(copies=99)]:
         with pytest.raises(isg.IsgError) as ei:
             isg.isg_debug_plan(g, **bad)
         assert ei.value.status == 1, bad
@@ -78,10 +78,10 @@ def test_options_validation(isg):
 
 def test_plan_torus_6x6(isg):
     """The 6x6 torus plan: energy stride 4 compacts 73 energy bins to 37; the low block is an
-    independent set of 6 spins; the inner walk and task count cover 2^36 configurations."""
+    independent set of 7 spins; the inner walk and task count cover 2^36 configurations."""
     g = isg.isg_graph_create(36, w.square(6, 6, True).edges)
     p = isg.isg_debug_plan(g)
-    assert p["small"] == 0 and p["G"] == 4 and p["n_e_compact"] == 37 and p["b"] == 6
+    assert p["small"] == 0 and p["G"] == 4 and p["n_e_compact"] == 37 and p["b"] == 7
     assert p["tasks"] * 32 << p["q"] == 1 << 36
     assert p["flush_rounds"] >= 1
 
@@ -95,7 +95,7 @@ EMU_GRAPHS = [w.square(4, 4, True), w.square(4, 4, False), w.square(3, 5, True),
               w.induced_lattice("cubic", 17, True, w.SplitMix64(6)), w.lattice("square", (1, 12), True)]
 EMU_PLANS = [{}, dict(inner_bits=6), dict(low_bits=1, inner_bits=3), dict(low_bits=3, inner_bits=5),
              dict(low_bits=2, inner_bits=2), dict(shard_bits=2, shard_lo=1, shard_hi=3), dict(shard_bits=4, shard_lo=9, shard_hi=10),
-             dict(bin_stride=64), dict(bin_stride=100, low_bits=4)]
+             dict(bin_stride=64), dict(bin_stride=100, low_bits=4), dict(low_bits=7, inner_bits=8)]
 
 
 @pytest.mark.parametrize("lat", EMU_GRAPHS, ids=lambda l: l.name)
