@@ -63,7 +63,8 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clock and throttle-reason samples every 200 ms while running."""
+    """nvidia-smi clock and throttle-reason samples every 25 ms while running (the sampler is
+    started, and its first sample awaited, before the timed region begins)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -77,10 +78,14 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "25"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.lines.clear()                 # keep only samples taken during the timed region
         except (OSError, ValueError):
             self.proc = None
         return self
@@ -233,7 +238,7 @@ def run_isg(args):
                        "plan": {k: plan[k] for k in ("q", "b", "tasks", "threads", "copies", "G", "n_e_compact")}},
             "roofline": {"bound": "alu", "achieved": achieved_ops / 1e9, "peak": alu_peak / 1e9, "unit": "Gop/s",
                          "frac": achieved_ops / alu_peak, "traffic": traffic,
-                         "kernel": "enumerate_kernel<6>", "ops_per_config": OPS_PER_CONFIG,
+                         "kernel": f"enumerate_kernel<{plan['b']}>", "ops_per_config": OPS_PER_CONFIG,
                          "peak_source": f"{sms} SMs x 128 lanes/clk x {sm_max:.0f} MHz (unit counts and clock)"},
             "roofline_smem_atomic": {"bound": "smem_atomic", "achieved": n_configs / enum_s / 1e9,
                                      "peak": peaks["red_conflict_free"] / 1e9,
@@ -508,7 +513,7 @@ def run_profile_case(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("isg", "reference"), default="isg")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
