@@ -147,7 +147,9 @@ def run_isg(args):
     lat = workloads.square(6, 6, True)
     gh = isg.isg_graph_create(lat.n, lat.edges)
     shape = isg.table_shape(gh)
-    plan = isg.isg_debug_plan(gh)
+    tuned = isg.isg_autotune(gh, torch.cuda.current_stream()) if not args.shard_bits else {}
+    tuned_fields = {k: tuned[k] for k in ("stride_residue", "block_threads", "ctas_per_sm")} if tuned else {}
+    plan = isg.isg_debug_plan(gh, **tuned_fields)
     # --shard-bits k (profiling case): each step enumerates shard 0 of 2^k with q - k inner bits,
     # so the launch has the same number of warp tasks as the full one
     shard = dict(shard_bits=args.shard_bits, shard_lo=0, shard_hi=1,
@@ -163,7 +165,7 @@ def run_isg(args):
     def step(ev=None):
         if ev:
             ev[0].record(stream)
-        isg.isg_enumerate(gh, g, stream, **shard)
+        isg.isg_enumerate(gh, g, stream, autotune=1, **shard)
         if ev:
             ev[1].record(stream)
         isg.isg_thermo(g, gh, T_GRID, H_GRID, isg.ISG_FP64, stream, out=outs)
@@ -209,7 +211,7 @@ def run_isg(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        gh_host = isg.isg_enumerate(gh, None, stream, **shard)              # host table: D2H inside
+        gh_host = isg.isg_enumerate(gh, None, stream, autotune=1, **shard)  # host table: D2H inside
         isg.isg_thermo(gh_host, gh, T_GRID, H_GRID, isg.ISG_FP64, stream)  # host g: H2D inside, host outputs
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if world > 1:
@@ -235,7 +237,9 @@ def run_isg(args):
             "config": {"workload": WORKLOAD if not shard else f"shard 0 of 2^{args.shard_bits} of: " + WORKLOAD,
                        "global_batch": world, "seq_len": None,
                        "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)",
-                       "plan": {k: plan[k] for k in ("q", "b", "tasks", "threads", "copies", "G", "n_e_compact")}},
+                       "plan": {k: plan[k] for k in ("q", "b", "tasks", "threads", "copies", "ctas_per_sm", "G",
+                                                     "n_e_compact", "stride")},
+                       "autotuned": tuned_fields},
             "roofline": {"bound": "alu", "achieved": achieved_ops / 1e9, "peak": alu_peak / 1e9, "unit": "Gop/s",
                          "frac": achieved_ops / alu_peak, "traffic": traffic,
                          "kernel": f"enumerate_kernel<{plan['b']}>", "ops_per_config": OPS_PER_CONFIG,
@@ -307,7 +311,7 @@ def extra_measurements(stream, dev):
     lats = workloads.ea_instances()
     hs = [isg.isg_graph_create(l.n, l.edges) for l in lats]
     configs = sum(1 << l.n for l in lats)
-    b = isg.Batch(hs)
+    b = isg.Batch(hs, autotune=1)
     bat_ms = _event_ms(lambda: b.run(stream), stream, 3)
     b.status(stream)
     b.close()
@@ -327,7 +331,7 @@ def extra_measurements(stream, dev):
     lat = workloads.cubic(3, 3, 4, True)
     gh = isg.isg_graph_create(lat.n, lat.edges)
     g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=dev)
-    enum_ms = _event_ms(lambda: isg.isg_enumerate(gh, g, stream), stream, 3)
+    enum_ms = _event_ms(lambda: isg.isg_enumerate(gh, g, stream, autotune=1), stream, 3)
     T = np.linspace(0.5, 8, 512)
     h = np.linspace(-2, 2, 256)
     r64 = tuple(torch.empty((512, 256), dtype=torch.float64, device=dev) for _ in range(5))

@@ -85,6 +85,10 @@ typedef struct {
     int32_t accumulate;      /* 1: add the counts into g_out; 0: overwrite g_out */
     int32_t warp_aggregate;  /* 1: combine a warp's equal bins with __match_any_sync before the
                                 shared-memory reduction (kept for comparison; 0 is faster on GB300) */
+    int32_t stride_residue;  /* preferred residue mod 32 of the histogram row stride (0 = plan;
+                                bin_stride, if set, wins) */
+    int32_t autotune;        /* 1: pick the unset planning fields by timing candidates (see
+                                isg_autotune); results are cached per graph and device */
 } isg_options;
 
 /* Fill *opt with the defaults (all planner choices, full range, overwrite). */
@@ -144,8 +148,10 @@ typedef struct isg_batch isg_batch;
 /*
  * Prepare a batch once: plan every graph, and place the programs, the tile descriptors and one
  * output table per graph in device memory owned by the batch (on the current device). Options as
- * isg_enumerate_batch. The graphs may be destroyed afterwards. Errors: ISG_ERR_INVALID,
- * ISG_ERR_TOO_LARGE, ISG_ERR_NOMEM, ISG_ERR_CUDA.
+ * isg_enumerate_batch; with opt->autotune the unset fields among inner_bits (per-lane walk
+ * length), block_threads and stride_residue are chosen by timing candidate plans on every 8th
+ * graph first (synchronous; results never depend on them). The graphs may be destroyed
+ * afterwards. Errors: ISG_ERR_INVALID, ISG_ERR_TOO_LARGE, ISG_ERR_NOMEM, ISG_ERR_CUDA.
  */
 ISG_API isg_status isg_batch_create(int32_t n_graphs, const isg_graph* const* graphs, const isg_options* opt,
                                     isg_batch** out);
@@ -168,6 +174,18 @@ ISG_API isg_status isg_batch_status(isg_batch* batch, void* stream);
 
 /* Free a prepared batch (NULL is ignored). Synchronises the device's work on its memory. */
 ISG_API void isg_batch_destroy(isg_batch* batch);
+
+/*
+ * Autotune the planning fields of isg_enumerate for this graph on the current device: candidate
+ * launch shapes (histogram row-stride residue, threads per CTA, CTAs per SM) are timed with CUDA
+ * events on one shard of the configuration space that holds as many warp tasks as the full
+ * launch, and the fastest is written to *tuned (a copy of opt, or of the defaults, with the
+ * fields filled in) and cached for the graph's program on this device, which isg_enumerate then
+ * uses when opt->autotune is set. Results never depend on these fields. Synchronises stream;
+ * allocates and frees scratch. Graphs with fewer than 30 spins are not worth timing: their
+ * defaults are returned. Errors as isg_enumerate.
+ */
+ISG_API isg_status isg_autotune(const isg_graph* graph, void* stream, const isg_options* opt, isg_options* tuned);
 
 /*
  * isg_enumerate for callers that cannot allocate device memory: the paper has no counterpart

@@ -288,6 +288,89 @@ static void batch_enqueue(isg_batch* b, cudaStream_t s) {
     launch_batch(b->plan, b->d_inst, b->d_blobs, b->d_small, b->d_counter, b->d_status, s, b->ctas_per_sm);
 }
 
+// Time a batch plan on a subset of the graphs: its own device buffers, one warm-up and two timed
+// runs, best of two (ms). Used by the batch autotuner; the tables are thrown away.
+static float time_batch(int n, const isg_graph* const* graphs, const isg_options& o, cudaStream_t s, int ctas_per_sm) {
+    const DeviceInfo d = device_info();
+    BatchPlan bp = plan_batch(n, graphs, o, d);
+    size_t words = 0;
+    std::vector<size_t> off(bp.order.size());
+    for (size_t k = 0; k < bp.order.size(); ++k) { off[k] = words; words += (size_t)public_bins(*graphs[bp.order[k]]); }
+    size_t at = 0;
+    auto take = [&](size_t bytes) { size_t o2 = at; at = (at + bytes + 255) & ~(size_t)255; return o2; };
+    const size_t o_cnt = take(16), o_inst = take(sizeof(BatchInst) * bp.inst.size());
+    const size_t o_small = take(sizeof(int) * std::max<size_t>(1, bp.small_ids.size()));
+    const size_t o_blobs = take(8 * bp.blobs.size()), o_tab = take(8 * words);
+    char* mem = nullptr;
+    ISG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&mem), at, s));
+    struct Free {
+        char* p; cudaStream_t s;
+        ~Free() { if (p) { cudaFreeAsync(p, s); cudaStreamSynchronize(s); } }
+    } guard{mem, s};
+    int64_t* tables = reinterpret_cast<int64_t*>(mem + o_tab);
+    for (size_t k = 0; k < bp.order.size(); ++k) bp.inst[k].g = tables + off[k];
+    ISG_CUDA(cudaMemcpyAsync(mem + o_inst, bp.inst.data(), sizeof(BatchInst) * bp.inst.size(), cudaMemcpyHostToDevice, s));
+    if (!bp.small_ids.empty())
+        ISG_CUDA(cudaMemcpyAsync(mem + o_small, bp.small_ids.data(), sizeof(int) * bp.small_ids.size(), cudaMemcpyHostToDevice, s));
+    ISG_CUDA(cudaMemcpyAsync(mem + o_blobs, bp.blobs.data(), 8 * bp.blobs.size(), cudaMemcpyHostToDevice, s));
+    cudaEvent_t e0, e1;
+    ISG_CUDA(cudaEventCreate(&e0));
+    ISG_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+        ISG_CUDA(cudaMemsetAsync(tables, 0, 8 * words, s));
+        ISG_CUDA(cudaMemsetAsync(mem + o_cnt, 0, 16, s));
+        ISG_CUDA(cudaEventRecord(e0, s));
+        launch_batch(bp, reinterpret_cast<BatchInst*>(mem + o_inst), reinterpret_cast<uint64_t*>(mem + o_blobs),
+                     reinterpret_cast<int*>(mem + o_small), reinterpret_cast<unsigned long long*>(mem + o_cnt),
+                     reinterpret_cast<unsigned int*>(mem + o_cnt + 8), s, ctas_per_sm);
+        ISG_CUDA(cudaEventRecord(e1, s));
+        ISG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        ISG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+// Batch autotuner: per-lane walk length, block size and histogram stride residue, timed on every
+// 8th graph (the subset keeps the batch's mix of sizes). Unset fields of o are filled in.
+static void autotune_batch(int n, const isg_graph* const* graphs, isg_options& o, int& ctas_per_sm) {
+    std::vector<const isg_graph*> sub;
+    for (int k = 0; k < n; k += 8) sub.push_back(graphs[k]);
+    cudaStream_t s = nullptr;
+    ISG_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    struct Destroy {
+        cudaStream_t s;
+        ~Destroy() { cudaStreamDestroy(s); }
+    } dguard{s};
+    static const int qs[] = {16, 18, 14};
+    static const int threads[] = {512, 256};
+    static const int residues[] = {6, 13};
+    float best_ms = 1e30f;
+    isg_options best = o;
+    for (int q : qs)
+        for (int t : threads)
+            for (int r : residues) {
+                isg_options c = o;
+                c.autotune = 0;
+                if (!c.inner_bits) c.inner_bits = q;
+                if (!c.block_threads) c.block_threads = t;
+                if (!c.stride_residue && !c.bin_stride) c.stride_residue = r;
+                float ms;
+                try {
+                    ms = time_batch((int)sub.size(), sub.data(), c, s, ctas_per_sm);
+                } catch (const Error&) {
+                    continue;
+                }
+                if (ms < best_ms) { best_ms = ms; best = c; }
+            }
+    o = best;
+    o.autotune = 0;
+}
+
 template <class F>
 static isg_status guarded_cuda(F&& f) {
     try {
@@ -314,12 +397,13 @@ isg_status isg_batch_create(int32_t n_graphs, const isg_graph* const* graphs, co
         *out = nullptr;
         if (n_graphs < 1 || !graphs) fail(ISG_ERR_INVALID, "need at least one graph");
         for (int k = 0; k < n_graphs; ++k) if (!graphs[k]) fail(ISG_ERR_INVALID, "graph " + std::to_string(k) + " is NULL");
-        const isg_options o = resolve_options(opt);
+        isg_options o = resolve_options(opt);
         const DeviceInfo d = device_info();
         std::unique_ptr<isg_batch> b(new isg_batch());
         ISG_CUDA(cudaGetDevice(&b->device));
-        b->plan = plan_batch(n_graphs, graphs, o, d);
         b->ctas_per_sm = o.ctas_per_sm > 0 ? o.ctas_per_sm : 2;
+        if (o.autotune) autotune_batch(n_graphs, graphs, o, b->ctas_per_sm);
+        b->plan = plan_batch(n_graphs, graphs, o, d);
         BatchPlan& bp = b->plan;
         b->table_off.assign(n_graphs, 0);
         b->table_len.assign(n_graphs, 0);

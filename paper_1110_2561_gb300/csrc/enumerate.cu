@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -219,20 +220,158 @@ void launch_enumeration(const Plan& p, const uint64_t* d_blob, int blob_words, i
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Autotuning: time candidate launch shapes on one shard and cache the winner per graph/device.
+// ---------------------------------------------------------------------------------------------
+static uint64_t graph_signature(const isg_graph& g) {
+    uint64_t h = 1469598103934665603ull;                      // FNV-1a over N and the bond list
+    auto mix = [&](uint64_t v) { for (int b = 0; b < 8; ++b) { h ^= (v >> (8 * b)) & 0xff; h *= 1099511628211ull; } };
+    mix((uint64_t)g.n);
+    for (size_t k = 0; k < g.bJ.size(); ++k) { mix((uint64_t)g.bi[k]); mix((uint64_t)g.bj[k]); mix((uint64_t)g.bJ[k]); }
+    return h;
+}
+
+struct TunedShape {
+    int stride_residue = 0, block_threads = 0, ctas_per_sm = 0;
+};
+
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, uint64_t>, TunedShape> g_tune_cache;
+
+// Time one plan on its own scratch: one warm-up and three timed launches, best of three (ms).
+static float time_plan(const isg_graph& g, const isg_options& o, cudaStream_t s, int64_t* table, char* scratch) {
+    const DeviceInfo d = device_info();
+    const Plan p = make_plan(g, o, d);
+    const std::vector<uint64_t> blob = build_program(g, p);
+    ISG_CUDA(cudaMemcpyAsync(scratch + 16, blob.data(), blob.size() * 8, cudaMemcpyHostToDevice, s));
+    cudaEvent_t e0, e1;
+    ISG_CUDA(cudaEventCreate(&e0));
+    ISG_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        ISG_CUDA(cudaMemsetAsync(scratch, 0, 16, s));
+        ISG_CUDA(cudaEventRecord(e0, s));
+        launch_enumeration(p, reinterpret_cast<const uint64_t*>(scratch + 16), (int)blob.size(), table,
+                           reinterpret_cast<unsigned long long*>(scratch), reinterpret_cast<unsigned int*>(scratch + 8), s);
+        ISG_CUDA(cudaEventRecord(e1, s));
+        ISG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        ISG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+static TunedShape run_autotune(const isg_graph& g, const isg_options& base, cudaStream_t s) {
+    TunedShape best;
+    if (g.n < 30) return best;
+    const DeviceInfo d = device_info();
+    isg_options o0 = base;
+    o0.autotune = 0;
+    o0.shard_bits = 0; o0.shard_lo = 0; o0.shard_hi = 0; o0.accumulate = 0;
+    const Plan p0 = make_plan(g, o0, d);
+    if (p0.small) return best;
+    const int k = std::min(4, p0.q - p0.b);      // a shard of 1/2^k with q - k inner bits: same task count
+    if (k < 1) return best;
+    const size_t table_bytes = sizeof(int64_t) * (size_t)public_bins(g);
+    char* scratch = nullptr;
+    ISG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&scratch), 16 + 8 * (size_t)1700 + table_bytes + 256, s));
+    struct Free {
+        char* p; cudaStream_t s;
+        ~Free() { if (p) { cudaFreeAsync(p, s); cudaStreamSynchronize(s); } }
+    } guard{scratch, s};
+    int64_t* table = reinterpret_cast<int64_t*>(scratch + ((16 + 8 * 1700 + 255) & ~(size_t)255));
+    ISG_CUDA(cudaMemsetAsync(table, 0, table_bytes, s));
+    static const int residues[] = {6, 13, 19, 5, 27};
+    static const int shapes[][2] = {{512, 2}, {256, 4}, {1024, 1}};
+    float best_ms = 1e30f;
+    for (int r : residues)
+        for (auto& sh : shapes) {
+            isg_options c = o0;
+            c.stride_residue = base.stride_residue ? base.stride_residue : r;
+            c.block_threads = base.block_threads ? base.block_threads : sh[0];
+            c.ctas_per_sm = base.ctas_per_sm ? base.ctas_per_sm : sh[1];
+            c.shard_bits = k;
+            c.shard_lo = 0;
+            c.shard_hi = 1;
+            c.inner_bits = p0.q - k;
+            c.accumulate = 1;                       // the scratch table just absorbs the counts
+            float ms;
+            try {
+                ms = time_plan(g, c, s, table, scratch);
+            } catch (const Error&) {
+                continue;                           // a shape this graph cannot take
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best.stride_residue = c.stride_residue;
+                best.block_threads = c.block_threads;
+                best.ctas_per_sm = c.ctas_per_sm;
+            }
+        }
+    return best;
+}
+
+// Fill the unset planning fields of o from the cache (tuning on a miss).
+static void apply_autotune(const isg_graph& g, isg_options& o, cudaStream_t s) {
+    int dev = 0;
+    ISG_CUDA(cudaGetDevice(&dev));
+    const std::pair<int, uint64_t> key(dev, graph_signature(g));
+    TunedShape t;
+    bool have = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) { t = it->second; have = true; }
+    }
+    if (!have) {
+        t = run_autotune(g, o, s);
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = t;
+    }
+    if (!o.stride_residue && !o.bin_stride) o.stride_residue = t.stride_residue;
+    if (!o.block_threads) o.block_threads = t.block_threads;
+    if (!o.ctas_per_sm) o.ctas_per_sm = t.ctas_per_sm;
+}
+
 }  // namespace isg
 
 using namespace isg;
+
+extern "C" isg_status isg_autotune(const isg_graph* graph, void* stream, const isg_options* opt, isg_options* tuned) {
+    try {
+        clear_error();
+        if (!graph || !tuned) fail(ISG_ERR_INVALID, "graph or tuned is NULL");
+        isg_options o = resolve_options(opt);
+        o.autotune = 1;
+        apply_autotune(*graph, o, static_cast<cudaStream_t>(stream));
+        *tuned = o;
+        return ISG_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return ISG_ERR_NOMEM;
+    } catch (...) {
+        set_error("unexpected exception");
+        return ISG_ERR_INTERNAL;
+    }
+}
 
 extern "C" isg_status isg_enumerate(const isg_graph* graph, void* stream, int64_t* g_out, int32_t g_out_on_device,
                                     const isg_options* opt) {
     try {
         clear_error();
         if (!graph || !g_out) fail(ISG_ERR_INVALID, "graph or g_out is NULL");
-        const isg_options o = resolve_options(opt);
+        isg_options o = resolve_options(opt);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (o.autotune) apply_autotune(*graph, o, s);
         const DeviceInfo d = device_info();
         const Plan p = make_plan(*graph, o, d);
         const std::vector<uint64_t> blob = build_program(*graph, p);
-        cudaStream_t s = static_cast<cudaStream_t>(stream);
         const size_t table_bytes = sizeof(int64_t) * (size_t)public_bins(*graph);
         const size_t blob_bytes = blob.size() * 8;
         // scratch: [counter 8][status 8][blob][host-mode table]

@@ -62,8 +62,13 @@ static int weight_classes(const isg_graph& g, std::vector<int32_t>& w) {
     return 1;                                              // binary classes
 }
 
-int choose_stride(const isg_graph& g, int requested) {
+int choose_stride(const isg_graph& g, int requested, int residue) {
     const int n_m = g.n + 1;
+    if (requested == 0 && residue > 0) {
+        if (residue >= 32) fail(ISG_ERR_INVALID, "stride_residue must lie in [1, 31]");
+        for (int s = n_m; s < n_m + 64; ++s)
+            if (s % 32 == residue && (8 * (int64_t)s) % g.G == 0) return s;
+    }
     if (requested > 0) {
         if (requested < n_m || (8 * (int64_t)requested) % g.G)
             fail(ISG_ERR_INVALID, "bin_stride must be >= N + 1 and make 8 * stride a multiple of the energy stride");
@@ -173,7 +178,7 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d) {
     std::vector<int32_t> w;
     weight_classes(g, w);
     const size_t prog_bytes = blob_words(n, (int)w.size()) * 8;
-    p.stride = choose_stride(g, o.bin_stride);
+    p.stride = choose_stride(g, o.bin_stride, o.stride_residue);
     if (prog_bytes + (size_t)g.n_e_c * p.stride * 4 > d.smem_optin && o.bin_stride == 0) p.stride = n + 1;
     const size_t bin_bytes = (size_t)g.n_e_c * p.stride * 4;
     if (prog_bytes + bin_bytes > d.smem_optin)

@@ -75,7 +75,7 @@ inline int64_t public_bin(const isg_graph& g, int64_t compact, int64_t stride) {
 }
 
 // Row stride of the shared histogram for a graph (>= N + 1), padded against bank conflicts.
-int choose_stride(const isg_graph& g, int requested);
+int choose_stride(const isg_graph& g, int requested, int residue);
 
 inline int64_t public_bins(const isg_graph& g) { return (g.S + 1) * (int64_t)(g.n + 1); }
 

@@ -31,7 +31,8 @@ class isg_options(ctypes.Structure):
         "struct_size", "max_spins", "inner_bits", "low_bits", "block_threads", "copies", "ctas_per_sm",
         "flush_tasks", "shard_bits", "bin_stride")] + [
         ("shard_lo", ctypes.c_int64), ("shard_hi", ctypes.c_int64),
-        ("accumulate", ctypes.c_int32), ("warp_aggregate", ctypes.c_int32)]
+        ("accumulate", ctypes.c_int32), ("warp_aggregate", ctypes.c_int32),
+        ("stride_residue", ctypes.c_int32), ("autotune", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -51,6 +52,7 @@ _SIGS = {
     "isg_debug_emulate": (i32, [vp, vp, vp]),
     "isg_probe_peaks": (i32, [vp, vp, vp, vp, vp]),
     "isg_enumerate_noalloc": (i32, [vp, vp, vp, vp]),
+    "isg_autotune": (i32, [vp, vp, vp, vp]),
     "isg_enumerate_batch": (i32, [i32, vp, vp, vp, i32, vp]),
     "isg_batch_create": (i32, [i32, vp, vp, ctypes.POINTER(vp)]),
     "isg_batch_run": (i32, [vp, vp]),
@@ -189,6 +191,14 @@ def isg_enumerate(graph: Graph, g_out=None, stream=None, **options):
     _check_tensor(g_out, shape, "int64")
     _check(lib().isg_enumerate(graph, _stream_handle(stream), g_out.data_ptr(), 1, ctypes.byref(o)))
     return g_out
+
+
+def isg_autotune(graph: Graph, stream=None, **options) -> dict:
+    """Timed choice of the planning fields for this graph (cached in the library); returns them."""
+    o = _options(**options)
+    t = isg_options()
+    _check(lib().isg_autotune(graph, _stream_handle(stream), ctypes.byref(o), ctypes.byref(t)))
+    return {name: getattr(t, name) for name, _ in t._fields_ if name != "struct_size"}
 
 
 def isg_enumerate_noalloc(graph: Graph, g_out, stream=None, **options):

@@ -64,6 +64,21 @@ def test_prepared_batch_replay(isg, cuda):
     b.close()
 
 
+def test_autotuned_batch(isg, cuda):
+    """A batch planned by the autotuner gives the same tables as the default plan."""
+    import torch
+    lats = w.ea_instances(count=256, seed=99)
+    hs = [isg.isg_graph_create(l.n, l.edges) for l in lats]
+    b0, b1 = isg.Batch(hs), isg.Batch(hs, autotune=1)
+    b0.run()
+    b1.run()
+    b1.status()
+    for k in range(len(lats)):
+        assert torch.equal(b0.table(k), b1.table(k)), lats[k].name
+    b0.close()
+    b1.close()
+
+
 def test_ea_4096_batch(isg, cuda):
     """The 4096 Edwards-Anderson +-J instances (4x4, 4x5, 5x5, 5x6 periodic, equal shares) in one
     prepared batch: every table by invariants; a sample of each shape bit for bit against the

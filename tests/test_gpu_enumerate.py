@@ -156,3 +156,18 @@ def test_largest_default_size_n40(isg, cuda):
     """N = 40 (the default max_spins): 2^40 configurations; invariants at full size."""
     lat = w.with_random_couplings(w.square(5, 8, True), w.SplitMix64(40), (-2, -1, 1, 2))
     check_invariants(gpu_table(isg, cuda, lat), 40)
+
+
+def test_autotune_torus_6x6(isg, cuda):
+    """The autotuner's choice (cached per graph) gives the same table as the oracle's frontier
+    programme; a second isg_autotune call returns the cached fields."""
+    import torch
+    lat = w.square(6, 6, True)
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    t1 = isg.isg_autotune(g)
+    t2 = isg.isg_autotune(g)
+    assert t1 == t2 and t1["stride_residue"] > 0 and t1["block_threads"] > 0
+    out = torch.zeros(isg.table_shape(g), dtype=torch.int64, device=cuda)
+    isg.isg_enumerate(g, out, autotune=1)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), oracle.g_frontier(lat.n, lat.edges, max_active=16))
