@@ -327,6 +327,21 @@ def extra_measurements(stream, dev):
         "batched_configs_per_s": configs / (bat_ms * 1e-3),
         "plain_ms": pl_ms, "plain_instances_per_s": len(lats) / (pl_ms * 1e-3),
         "plain_configs_per_s": configs / (pl_ms * 1e-3), "speedup": pl_ms / bat_ms}
+    # spin-flip symmetry halving (a NEXT row, reported apart from the headline): half the visits
+    lat = workloads.square(6, 6, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=dev)
+    sym_ms = _event_ms(lambda: isg.isg_enumerate(gh, g, stream, autotune=1, symmetry=1), stream, 5)
+    b = isg.Batch(hs, autotune=1, symmetry=1)
+    bsym_ms = _event_ms(lambda: b.run(stream), stream, 3)
+    b.status(stream)
+    b.close()
+    out["symmetry_halving"] = {
+        "what": "enumerate only spin N-1 up, add the M -> -M mirror (exact for any couplings)",
+        "torus6x6_ms": sym_ms, "torus6x6_effective_configs_per_s": (1 << 36) / (sym_ms * 1e-3),
+        "torus6x6_enumerated_configs_per_s": (1 << 35) / (sym_ms * 1e-3),
+        "ea_4096_batched_ms": bsym_ms, "ea_4096_batched_instances_per_s": len(lats) / (bsym_ms * 1e-3),
+        "ea_4096_effective_configs_per_s": configs / (bsym_ms * 1e-3)}
     # cubic 3x3x4 torus: thermodynamics on 512 T x 256 h, FP32 vs FP64
     lat = workloads.cubic(3, 3, 4, True)
     gh = isg.isg_graph_create(lat.n, lat.edges)

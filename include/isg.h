@@ -89,6 +89,11 @@ typedef struct {
                                 bin_stride, if set, wins) */
     int32_t autotune;        /* 1: pick the unset planning fields by timing candidates (see
                                 isg_autotune); results are cached per graph and device */
+    int32_t symmetry;        /* 1: enumerate only the configurations with spin N-1 up and add the
+                                mirror image M -> -M (a global flip keeps E and negates M for any
+                                couplings): the same exact table from half the visits. Not with
+                                shards; isg_enumerate_noalloc ignores it */
+    int32_t reserved2;
 } isg_options;
 
 /* Fill *opt with the defaults (all planner choices, full range, overwrite). */
@@ -136,7 +141,8 @@ ISG_API isg_status isg_enumerate(const isg_graph* graph, void* stream, int64_t* 
  * processes; here the tiles of many lattices share one GPU). g_out[k] receives the table of
  * graphs[k] in its own geometry (isg_graph_bins), all on the device or all on the host
  * (on_device). opt: planning fields apply to every graph (inner_bits = per-lane walk length
- * target, low_bits, block_threads <= 512, ctas_per_sm); shard and accumulate fields must be 0.
+ * target, low_bits, block_threads <= 512, ctas_per_sm, symmetry); shard and accumulate fields
+ * must be 0.
  * The call synchronises stream. It plans, allocates and frees its own device memory; repeated
  * batches should use isg_batch_create / isg_batch_run. Errors as isg_enumerate.
  */

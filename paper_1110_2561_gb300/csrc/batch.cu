@@ -119,6 +119,24 @@ __global__ void batch_small_kernel(const BatchInst* inst, const int* small_ids, 
     }
 }
 
+// Symmetry completion in place, one CTA per instance: the table holds the configurations with
+// spin N-1 up; bins M and -M both become half(E, M) + half(E, -M).
+__global__ void batch_mirror_kernel(const BatchInst* inst, const int* ids, const uint64_t* blobs) {
+    const BatchInst in = inst[ids[blockIdx.x]];
+    const ProgHeader* hd = reinterpret_cast<const ProgHeader*>(blobs + in.blob_off);
+    const int n_m = hd->n_m, n_e = (int)(hd->S + 1), half = (n_m + 1) / 2;
+    for (int i = threadIdx.x; i < n_e * half; i += blockDim.x) {
+        const int e = i / half, m = i - e * half, m2 = n_m - 1 - m;
+        int64_t* row = in.g + (size_t)e * n_m;
+        if (m == m2) row[m] *= 2;
+        else {
+            const int64_t v = row[m] + row[m2];
+            row[m] = v;
+            row[m2] = v;
+        }
+    }
+}
+
 #define ISG_CUDA(call)                                                                              \
     do {                                                                                            \
         cudaError_t e_ = (call);                                                                    \
@@ -135,6 +153,7 @@ static BatchPlan plan_batch(int n, const isg_graph* const* graphs, const isg_opt
     BatchPlan bp;
     if (o.shard_bits || o.shard_lo || o.shard_hi || o.accumulate)
         fail(ISG_ERR_INVALID, "batches take no shard or accumulate options");
+    const bool sym = o.symmetry != 0;
     // common low block: the largest size every large-enough instance supports
     std::vector<int> b_of(n, 0);
     for (int k = 0; k < n; ++k) {
@@ -157,7 +176,7 @@ static BatchPlan plan_batch(int n, const isg_graph* const* graphs, const isg_opt
         const isg_graph& g = *graphs[k];
         BatchInst in{};
         Plan p;
-        const bool small = g.n < B + 5 || b_of[k] == 0;
+        const bool small = g.n < B + 5 + (sym ? 1 : 0) || b_of[k] == 0;
         isg_options ok = o;
         if (small) {
             ok.inner_bits = 0;
@@ -169,7 +188,8 @@ static BatchPlan plan_batch(int n, const isg_graph* const* graphs, const isg_opt
             std::iota(p.perm.begin(), p.perm.end(), 0);
         } else {
             ok.low_bits = B;
-            ok.inner_bits = std::max(B, std::min(q_target, g.n - 5));
+            if (sym) { ok.shard_bits = 1; ok.shard_lo = 1; ok.shard_hi = 2; }     // spin N-1 up only
+            ok.inner_bits = std::max(B, std::min(q_target, g.n - (sym ? 6 : 5)));
             p = make_plan(g, ok, d);
         }
         const std::vector<uint64_t> blob = build_program(g, p);
@@ -182,9 +202,10 @@ static BatchPlan plan_batch(int n, const isg_graph* const* graphs, const isg_opt
             bp.small_max_words = std::max(bp.small_max_words, (int)blob.size());
             in.n_tiles = 0;
         } else {
-            in.prefix_base = 0;
+            in.prefix_base = p.prefix_base;
             in.task_lo = 0;
             in.n_tiles = p.n_tasks;
+            if (sym) bp.mirror_ids.push_back((int)bp.inst.size());
             max_words = std::max(max_words, (int)blob.size());
             max_bins = std::max(max_bins, (int)(g.n_e_c * p.stride));
         }
@@ -254,6 +275,10 @@ void launch_batch(const BatchPlan& bp, const BatchInst* d_inst, const uint64_t* 
         batch_small_kernel<<<(int)bp.small_ids.size(), 256, smem, s>>>(d_inst, d_small, d_blobs);
         ISG_CUDA(cudaGetLastError());
     }
+    if (!bp.mirror_ids.empty()) {
+        batch_mirror_kernel<<<(int)bp.mirror_ids.size(), 256, 0, s>>>(d_inst, d_small + bp.small_ids.size(), d_blobs);
+        ISG_CUDA(cudaGetLastError());
+    }
 }
 
 }  // namespace isg
@@ -299,7 +324,9 @@ static float time_batch(int n, const isg_graph* const* graphs, const isg_options
     size_t at = 0;
     auto take = [&](size_t bytes) { size_t o2 = at; at = (at + bytes + 255) & ~(size_t)255; return o2; };
     const size_t o_cnt = take(16), o_inst = take(sizeof(BatchInst) * bp.inst.size());
-    const size_t o_small = take(sizeof(int) * std::max<size_t>(1, bp.small_ids.size()));
+    std::vector<int> ids(bp.small_ids);
+    ids.insert(ids.end(), bp.mirror_ids.begin(), bp.mirror_ids.end());
+    const size_t o_small = take(sizeof(int) * std::max<size_t>(1, ids.size()));
     const size_t o_blobs = take(8 * bp.blobs.size()), o_tab = take(8 * words);
     char* mem = nullptr;
     ISG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&mem), at, s));
@@ -310,8 +337,8 @@ static float time_batch(int n, const isg_graph* const* graphs, const isg_options
     int64_t* tables = reinterpret_cast<int64_t*>(mem + o_tab);
     for (size_t k = 0; k < bp.order.size(); ++k) bp.inst[k].g = tables + off[k];
     ISG_CUDA(cudaMemcpyAsync(mem + o_inst, bp.inst.data(), sizeof(BatchInst) * bp.inst.size(), cudaMemcpyHostToDevice, s));
-    if (!bp.small_ids.empty())
-        ISG_CUDA(cudaMemcpyAsync(mem + o_small, bp.small_ids.data(), sizeof(int) * bp.small_ids.size(), cudaMemcpyHostToDevice, s));
+    if (!ids.empty())
+        ISG_CUDA(cudaMemcpyAsync(mem + o_small, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice, s));
     ISG_CUDA(cudaMemcpyAsync(mem + o_blobs, bp.blobs.data(), 8 * bp.blobs.size(), cudaMemcpyHostToDevice, s));
     cudaEvent_t e0, e1;
     ISG_CUDA(cudaEventCreate(&e0));
@@ -418,8 +445,10 @@ isg_status isg_batch_create(int32_t n_graphs, const isg_graph* const* graphs, co
         // layout: [counter 8][status 8][inst][small ids][blobs][tables], 256-byte aligned pieces
         size_t off = 0;
         auto take = [&](size_t bytes) { size_t o2 = off; off = (off + bytes + 255) & ~(size_t)255; return o2; };
+        std::vector<int> ids(bp.small_ids);
+        ids.insert(ids.end(), bp.mirror_ids.begin(), bp.mirror_ids.end());
         const size_t o_cnt = take(16), o_inst = take(sizeof(BatchInst) * bp.inst.size());
-        const size_t o_small = take(sizeof(int) * std::max<size_t>(1, bp.small_ids.size()));
+        const size_t o_small = take(sizeof(int) * std::max<size_t>(1, ids.size()));
         const size_t o_blobs = take(8 * bp.blobs.size()), o_tab = take(8 * words);
         ISG_CUDA(cudaMalloc(reinterpret_cast<void**>(&b->mem), off));
         b->d_counter = reinterpret_cast<unsigned long long*>(b->mem + o_cnt);
@@ -430,8 +459,8 @@ isg_status isg_batch_create(int32_t n_graphs, const isg_graph* const* graphs, co
         b->d_tables = reinterpret_cast<int64_t*>(b->mem + o_tab);
         for (size_t k = 0; k < bp.order.size(); ++k) bp.inst[k].g = b->d_tables + b->table_off[bp.order[k]];
         ISG_CUDA(cudaMemcpy(b->d_inst, bp.inst.data(), sizeof(BatchInst) * bp.inst.size(), cudaMemcpyHostToDevice));
-        if (!bp.small_ids.empty())
-            ISG_CUDA(cudaMemcpy(b->d_small, bp.small_ids.data(), sizeof(int) * bp.small_ids.size(), cudaMemcpyHostToDevice));
+        if (!ids.empty())
+            ISG_CUDA(cudaMemcpy(b->d_small, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice));
         ISG_CUDA(cudaMemcpy(b->d_blobs, bp.blobs.data(), 8 * bp.blobs.size(), cudaMemcpyHostToDevice));
         ISG_CUDA(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
         *out = b.release();

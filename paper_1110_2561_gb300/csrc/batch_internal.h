@@ -25,6 +25,7 @@ struct BatchPlan {
     std::vector<int> order;             // inst[k] describes graphs[order[k]]
     std::vector<uint64_t> blobs;
     std::vector<int> small_ids;         // descriptors of instances for the small kernel
+    std::vector<int> mirror_ids;        // symmetry: instances whose half table is completed in place
     uint64_t n_tiles = 0;
     int prog_words = 0, slot_words = 0, threads = 512, warps_per_cta = 16, small_max_words = 0;
     size_t smem = 0;
@@ -32,6 +33,7 @@ struct BatchPlan {
 };
 
 // Enqueue the batch kernels of a plan (device descriptors, programs and small-instance ids).
+// d_small holds small_ids followed by mirror_ids.
 void launch_batch(const BatchPlan& bp, const BatchInst* d_inst, const uint64_t* d_blobs, const int* d_small,
                   unsigned long long* counter, unsigned int* status, cudaStream_t s, int ctas_per_sm);
 

@@ -131,6 +131,17 @@ __global__ void enumerate_small_kernel(const uint64_t* blob, int words, uint64_t
     }
 }
 
+// Symmetry completion: out (=/+=) half(E, M) + half(E, -M), where half counts the configurations
+// with spin N-1 up (a global flip keeps E and negates M).
+__global__ void mirror_kernel(const int64_t* half, int64_t* out, int n_e, int n_m, int accumulate) {
+    const int total = n_e * n_m;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int e = i / n_m, m = i - e * n_m;
+        const int64_t v = half[i] + half[(size_t)e * n_m + (n_m - 1 - m)];
+        out[i] = accumulate ? out[i] + v : v;
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------------------
@@ -369,14 +380,17 @@ extern "C" isg_status isg_enumerate(const isg_graph* graph, void* stream, int64_
         isg_options o = resolve_options(opt);
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         if (o.autotune) apply_autotune(*graph, o, s);
+        const bool sym = o.symmetry != 0;
+        if (sym) { o.shard_bits = 1; o.shard_lo = 1; o.shard_hi = 2; }      // spin N-1 up only
         const DeviceInfo d = device_info();
         const Plan p = make_plan(*graph, o, d);
         const std::vector<uint64_t> blob = build_program(*graph, p);
         const size_t table_bytes = sizeof(int64_t) * (size_t)public_bins(*graph);
         const size_t blob_bytes = blob.size() * 8;
-        // scratch: [counter 8][status 8][blob][host-mode table]
+        // scratch: [counter 8][status 8][blob][table: host mode or symmetry half]
         const size_t off_blob = 16, off_table = (off_blob + blob_bytes + 255) & ~(size_t)255;
-        const size_t scratch_bytes = off_table + (g_out_on_device ? 0 : table_bytes);
+        const bool own_table = !g_out_on_device || sym;
+        const size_t scratch_bytes = off_table + (own_table ? table_bytes : 0) + (sym && !g_out_on_device ? table_bytes : 0);
         char* scratch = nullptr;
         ISG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&scratch), scratch_bytes, s));
         struct Free {
@@ -385,10 +399,18 @@ extern "C" isg_status isg_enumerate(const isg_graph* graph, void* stream, int64_
         } guard{scratch, s};
         ISG_CUDA(cudaMemsetAsync(scratch, 0, 16, s));
         ISG_CUDA(cudaMemcpyAsync(scratch + off_blob, blob.data(), blob_bytes, cudaMemcpyHostToDevice, s));
-        int64_t* table = g_out_on_device ? g_out : reinterpret_cast<int64_t*>(scratch + off_table);
-        if (!g_out_on_device || !o.accumulate) ISG_CUDA(cudaMemsetAsync(table, 0, table_bytes, s));
+        int64_t* table = own_table ? reinterpret_cast<int64_t*>(scratch + off_table) : g_out;
+        if (own_table || !o.accumulate) ISG_CUDA(cudaMemsetAsync(table, 0, table_bytes, s));
         launch_enumeration(p, reinterpret_cast<const uint64_t*>(scratch + off_blob), (int)blob.size(), table,
                            reinterpret_cast<unsigned long long*>(scratch), reinterpret_cast<unsigned int*>(scratch + 8), s);
+        if (sym) {
+            const int n_m = graph->n + 1, n_e = (int)(graph->S + 1);
+            int64_t* full = g_out_on_device ? g_out : reinterpret_cast<int64_t*>(scratch + off_table + table_bytes);
+            const int acc = g_out_on_device ? o.accumulate : 0;
+            mirror_kernel<<<std::min(1024, (n_e * n_m + 255) / 256), 256, 0, s>>>(table, full, n_e, n_m, acc);
+            ISG_CUDA(cudaGetLastError());
+            table = full;
+        }
         if (!g_out_on_device) {
             std::vector<int64_t> host((size_t)public_bins(*graph));
             unsigned int status = 0;

@@ -27,6 +27,8 @@ isg_options resolve_options(const isg_options* opt) {
     }
     if (o.max_spins <= 0) o.max_spins = 40;
     if (o.max_spins > 62) o.max_spins = 62;
+    if (o.symmetry && (o.shard_bits || o.shard_lo || o.shard_hi))
+        fail(ISG_ERR_INVALID, "symmetry cannot be combined with shards");
     return o;
 }
 
@@ -430,6 +432,8 @@ isg_status isg_debug_emulate(const isg_graph* g, const isg_options* opt, int64_t
     return guarded([&] {
         if (!g || !g_out) fail(ISG_ERR_INVALID, "NULL argument");
         isg_options o = resolve_options(opt);
+        const bool sym = o.symmetry != 0;
+        if (sym) { o.shard_bits = 1; o.shard_lo = 1; o.shard_hi = 2; }     // spin N-1 up only
         Plan p = make_plan(*g, o, DeviceInfo{});
         std::vector<uint64_t> blob = build_program(*g, p);
         const ProgView v = make_view(blob.data());
@@ -456,13 +460,18 @@ isg_status isg_debug_emulate(const isg_graph* g, const isg_options* opt, int64_t
             }
         }
         if (bad) fail(ISG_ERR_INTERNAL, "emulated walk left the histogram or lost track of its bin");
-        if (!o.accumulate) std::memset(g_out, 0, sizeof(int64_t) * public_bins(*g));
+        std::vector<int64_t> tab((size_t)public_bins(*g), 0);
         for (int64_t i = 0; i < nb; ++i)
             if (hist[i]) {
                 const int64_t pb = public_bin(*g, i, stride);
                 if (pb < 0) fail(ISG_ERR_INTERNAL, "emulated walk counted a padding column");
-                g_out[pb] += hist[i];
+                tab[pb] += hist[i];
             }
+        if (!o.accumulate) std::memset(g_out, 0, sizeof(int64_t) * public_bins(*g));
+        const int64_t n_m = g->n + 1;
+        for (int64_t e = 0; e <= g->S; ++e)
+            for (int64_t m = 0; m < n_m; ++m)
+                g_out[e * n_m + m] += tab[e * n_m + m] + (sym ? tab[e * n_m + (n_m - 1 - m)] : 0);
     });
 }
 

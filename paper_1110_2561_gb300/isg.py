@@ -32,7 +32,8 @@ class isg_options(ctypes.Structure):
         "flush_tasks", "shard_bits", "bin_stride")] + [
         ("shard_lo", ctypes.c_int64), ("shard_hi", ctypes.c_int64),
         ("accumulate", ctypes.c_int32), ("warp_aggregate", ctypes.c_int32),
-        ("stride_residue", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+        ("stride_residue", ctypes.c_int32), ("autotune", ctypes.c_int32),
+        ("symmetry", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 _lock = threading.Lock()

@@ -95,7 +95,8 @@ EMU_GRAPHS = [w.square(4, 4, True), w.square(4, 4, False), w.square(3, 5, True),
               w.induced_lattice("cubic", 17, True, w.SplitMix64(6)), w.lattice("square", (1, 12), True)]
 EMU_PLANS = [{}, dict(inner_bits=6), dict(low_bits=1, inner_bits=3), dict(low_bits=3, inner_bits=5),
              dict(low_bits=2, inner_bits=2), dict(shard_bits=2, shard_lo=1, shard_hi=3), dict(shard_bits=4, shard_lo=9, shard_hi=10),
-             dict(bin_stride=64), dict(bin_stride=100, low_bits=4), dict(low_bits=7, inner_bits=8)]
+             dict(bin_stride=64), dict(bin_stride=100, low_bits=4), dict(low_bits=7, inner_bits=8),
+             dict(symmetry=1), dict(symmetry=1, low_bits=3, inner_bits=4)]
 
 
 @pytest.mark.parametrize("lat", EMU_GRAPHS, ids=lambda l: l.name)
@@ -115,6 +116,13 @@ def test_emulated_walk_matches_oracle(isg, lat):
             assert e.status in (1, 2), (kw, e)
             continue
         assert np.array_equal(got, ref), kw
+
+
+def test_symmetry_rejects_shards(isg):
+    g = isg.isg_graph_create(16, w.square(4, 4, True).edges)
+    with pytest.raises(isg.IsgError) as ei:
+        isg.isg_debug_emulate(g, symmetry=1, shard_bits=1, shard_hi=1)
+    assert ei.value.status == 1
 
 
 def test_emulated_accumulate(isg):

@@ -43,6 +43,21 @@ def test_batch_device_tables_and_options(isg, cuda):
             assert np.array_equal(o.cpu().numpy(), r), (l.name, kw)
 
 
+def test_batch_symmetry(isg, cuda):
+    """Symmetry halving in a batch (mixed sizes, small graphs included) equals the oracle."""
+    lats = mixed_graphs()
+    hs = [isg.isg_graph_create(l.n, l.edges) for l in lats]
+    outs = isg.isg_enumerate_batch(hs, symmetry=1)
+    for l, g in zip(lats, outs):
+        assert np.array_equal(g, oracle.g_masks(l.n, l.edges, threads=THREADS)), l.name
+    b = isg.Batch(hs, symmetry=1)
+    b.run()
+    b.status()
+    for k, l in enumerate(lats):
+        assert np.array_equal(b.table(k).cpu().numpy(), oracle.g_masks(l.n, l.edges)), l.name
+    b.close()
+
+
 def test_batch_rejects_shards(isg, cuda):
     h = isg.isg_graph_create(16, w.square(4, 4, True).edges)
     with pytest.raises(isg.IsgError) as ei:

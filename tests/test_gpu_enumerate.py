@@ -72,7 +72,8 @@ def test_table1_on_gpu(isg, cuda, table1_triples):
 PLANS = [dict(inner_bits=6), dict(low_bits=1, inner_bits=4), dict(low_bits=4, inner_bits=9), dict(low_bits=5, inner_bits=12),
          dict(block_threads=64, copies=1), dict(block_threads=1024, copies=16), dict(block_threads=256, copies=3),
          dict(flush_tasks=1), dict(ctas_per_sm=1, flush_tasks=1, block_threads=96, copies=2), dict(low_bits=2, inner_bits=2),
-         dict(warp_aggregate=1), dict(bin_stride=64), dict(bin_stride=33, warp_aggregate=1, copies=1)]
+         dict(warp_aggregate=1), dict(bin_stride=64), dict(bin_stride=33, warp_aggregate=1, copies=1),
+         dict(symmetry=1), dict(symmetry=1, low_bits=3, inner_bits=6, block_threads=128)]
 
 
 @pytest.mark.parametrize("kw", PLANS, ids=lambda k: ",".join(f"{a}={b}" for a, b in k.items()))
@@ -81,6 +82,24 @@ def test_plan_invariance(isg, cuda, kw):
     lat = w.with_random_couplings(w.triangular(4, 5, True), w.SplitMix64(8), (-2, -1, 1, 2))
     ref = oracle.g_masks(lat.n, lat.edges, threads=THREADS)
     assert np.array_equal(gpu_table(isg, cuda, lat, **kw), ref)
+
+
+def test_symmetry_host_device_accumulate(isg, cuda):
+    """Symmetry halving (spin N-1 up, then the M mirror) gives the oracle's table on the host, on
+    the device, added into a table, on +-J couplings, and on the 6x6 torus at full size."""
+    import torch
+    lat = w.with_random_couplings(w.cubic(2, 3, 3, True), w.SplitMix64(13), (-1, 1))
+    ref = oracle.g_masks(lat.n, lat.edges, threads=THREADS)
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    assert np.array_equal(isg.isg_enumerate(g, symmetry=1), ref)
+    out = torch.zeros(isg.table_shape(g), dtype=torch.int64, device=cuda)
+    isg.isg_enumerate(g, out, symmetry=1)
+    isg.isg_enumerate(g, out, symmetry=1, accumulate=1)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), 2 * ref)
+    t6 = w.square(6, 6, True)
+    gt = isg.isg_graph_create(t6.n, t6.edges)
+    assert np.array_equal(isg.isg_enumerate(gt, symmetry=1), oracle.g_frontier(t6.n, t6.edges, max_active=16))
 
 
 def test_shards_and_accumulate(isg, cuda):
