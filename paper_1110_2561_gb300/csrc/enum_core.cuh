@@ -199,9 +199,7 @@ ISG_HD void low_block(uint32_t& idx, const int32_t (&Gk)[B], Sink& sink) {
 // Flip spin r (r >= B) of st: the address moves by S_r (h_r sE - 4) (dE = 2 S_r h_r, dm = -S_r),
 // and every low spin k bonded to r sees its field change by -2 S_r J_kr.
 template <int B>
-ISG_HD void mid_flip(const ProgView& p, uint64_t& st, int r, uint32_t& idx, int32_t (&Gk)[B]) {
-    SiteVals sv;
-    load_site(p, r, sv);
+ISG_HD void mid_flip_with(const ProgView& p, const SiteVals& sv, uint64_t& st, int r, uint32_t& idx, int32_t (&Gk)[B]) {
     const int h = field_of(p, sv, st, r);
     const bool up = (st >> r) & 1;
     const int32_t d = h * p.sE - 4;
@@ -209,6 +207,13 @@ ISG_HD void mid_flip(const ProgView& p, uint64_t& st, int r, uint32_t& idx, int3
 #pragma unroll
     for (int k = 0; k < B; ++k) Gk[k] += up ? sv.A[k] : -sv.A[k];
     st ^= 1ull << r;
+}
+
+template <int B>
+ISG_HD void mid_flip(const ProgView& p, uint64_t& st, int r, uint32_t& idx, int32_t (&Gk)[B]) {
+    SiteVals sv;
+    load_site(p, r, sv);
+    mid_flip_with<B>(p, sv, st, r, idx, Gk);
 }
 
 // Visit the 2^q configurations prefix * 2^q + inner, inner in Gray order, counting each through
@@ -223,11 +228,13 @@ ISG_HD void lane_walk(const ProgView& p, uint64_t prefix, uint32_t base, Sink& s
 #pragma unroll
     for (int k = 0; k < B; ++k) Gk[k] = field(p, st, k) * p.sE - 4;
     const uint32_t nblocks = 1u << (p.q - B);
+    SiteVals svB;                     // spin B takes every other mid flip: its record stays in registers
+    if (nblocks > 1) load_site(p, B, svB);
     for (uint32_t t = 0; t < nblocks; t += 2) {
         low_block<B, false>(idx, Gk, sink);
         st ^= 1ull << (B - 1);
         if (t + 1 < nblocks) {
-            mid_flip<B>(p, st, B, idx, Gk);
+            mid_flip_with<B>(p, svB, st, B, idx, Gk);
             low_block<B, true>(idx, Gk, sink);
             st ^= 1ull << (B - 1);
             if (t + 2 < nblocks) mid_flip<B>(p, st, B + ctz32(t + 2), idx, Gk);

@@ -279,9 +279,9 @@ static TunedShape run_autotune(const isg_graph& g, const isg_options& base, cuda
     TunedShape best;
     if (g.n < 30) return best;
     const DeviceInfo d = device_info();
-    isg_options o0 = base;
+    isg_options o0 = base;                          // the full launch at the planner's own split
     o0.autotune = 0;
-    o0.shard_bits = 0; o0.shard_lo = 0; o0.shard_hi = 0; o0.accumulate = 0;
+    o0.shard_bits = 0; o0.shard_lo = 0; o0.shard_hi = 0; o0.accumulate = 0; o0.inner_bits = 0;
     const Plan p0 = make_plan(g, o0, d);
     if (p0.small) return best;
     const int k = std::min(4, p0.q - p0.b);      // a shard of 1/2^k with q - k inner bits: same task count

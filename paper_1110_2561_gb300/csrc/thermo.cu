@@ -11,8 +11,9 @@
 // cancellation enters C = Var(H)/T^2 or chi = Var(M)/T.
 //
 // FP64: everything in double. FP32: the counts are converted to ln g in double once and rounded
-// to float; every exponential and every sum runs in float, relative to the row or column
-// maximum; ln Z is finished in double from the float sum.
+// to float; every exponential and every sum runs in float, relative to the column maximum in
+// stage 1 and to the dominant column of each (T, h) point in stage 2, whose large offsets are
+// carried as pairs of floats; ln Z is finished in double from the float sum.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -59,12 +60,13 @@ __device__ __forceinline__ F warp_sum(F v) {
 
 // ln g for every bin, computed in double from the int64 count and stored in double and (rounded)
 // in float; -inf marks an empty bin.
-__global__ void log_counts_kernel(const int64_t* g, int nbins, double* lng, float* lngf) {
+__global__ void log_counts_kernel(const int64_t* g, int nbins, double* lng, float* lngf, float* lnglo) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nbins; i += gridDim.x * blockDim.x) {
         const int64_t c = g[i];
         const double l = c > 0 ? log((double)c) : -INFINITY;
         lng[i] = l;
         lngf[i] = (float)l;
+        lnglo[i] = c > 0 ? (float)(l - (double)(float)l) : 0.0f;     // remainder: lngf + lnglo = ln g
     }
 }
 
@@ -72,19 +74,28 @@ template <class F> __device__ __forceinline__ const F* pick(const double* d, con
 template <> __device__ __forceinline__ const double* pick<double>(const double* d, const float*) { return d; }
 template <> __device__ __forceinline__ const float* pick<float>(const double*, const float* f) { return f; }
 
-// One CTA per temperature. Shared memory: L[n_m] (double), mu[n_m], var[n_m], Lr[n_m] (F).
+// One CTA per temperature. Shared memory: L[n_m] (double), mu, var, Lr, Llo [n_m] (F).
+//
+// Stage 2 forms every exponent relative to the dominant column m* of its (T, h) point:
+//   d_m = (Lr[m] - Lr[m*]) + (Llo[m] - Llo[m*]) + (h/T)(M_m - M_m*),
+// with Lr + Llo = L - max L and h/T = hT + hTlo held as pairs of the working precision (for
+// float this is what keeps ln Z accurate to ~1e-7 although L - max L reaches hundreds), and
+// finishes ln Z = max L + (L[m*] - max L) + (h/T) M_m* + ln(sum exp d_m) in double.
 template <class F>
-__global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double* lngd, const float* lngf) {
+__global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double* lngd, const float* lngf,
+                                                     const float* lnglo) {
     const F* lng = pick<F>(lngd, lngf);
+    const bool pair = sizeof(F) == sizeof(float);   // float: ln g carried as lngf + lnglo
     extern __shared__ __align__(16) unsigned char sm[];
     double* L = reinterpret_cast<double*>(sm);
     F* mu = reinterpret_cast<F*>(L + a.n_m);
     F* var = mu + a.n_m;
-    F* Lr = var + a.n_m;                 // L - max L, in the working precision (-inf: empty column)
+    F* Lr = var + a.n_m;                 // L - max L, rounded to F (-inf: empty column)
+    F* Llo = Lr + a.n_m;                 // the rounding remainder of Lr
     __shared__ double s_Lmax;
     const int it = blockIdx.x;
-    const double T = a.T[it];
-    const F invT = (F)(1.0 / T);
+    const double T = a.T[it], invTd = 1.0 / T;
+    const F invT = (F)invTd, invTlo = (F)(invTd - (double)invT);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
 
     // Stage 1: per column M (one warp each).
@@ -104,13 +115,23 @@ __global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double*
             if (lane == 0) { L[m] = -INFINITY; mu[m] = 0; var[m] = 0; }
             continue;
         }
-        const F Eref = (F)(a.e_min + 2 * __shfl_sync(0xffffffffu, earg, __ffs(hit) - 1));
+        // exponents relative to the maximising bin e*: (ln g_e - ln g_e*) - (E_e - E_e*) / T, the
+        // differences formed from the (hi, lo) pairs so no large value is rounded on the way
+        const int es = __shfl_sync(0xffffffffu, earg, __ffs(hit) - 1);
+        const size_t is = (size_t)es * a.n_m + m;
+        const F ls = lng[is], lls = pair ? (F)lnglo[is] : (F)0;
+        const F Eref = (F)(a.e_min + 2 * es);
+        auto arg = [&](int e, F l) {
+            const F dE = (F)(2 * (e - es));
+            const F dl = (l - ls) + (pair ? (F)lnglo[(size_t)e * a.n_m + m] - lls : (F)0);
+            return dl - fma(dE, invT, dE * invTlo);
+        };
         F s0 = 0, s1 = 0;
         for (int e = lane; e < a.n_e; e += 32) {
             const F l = lng[(size_t)e * a.n_m + m];
             if (l == (F)-INFINITY) continue;
             const F En = (F)(a.e_min + 2 * e);
-            const F w = ex<F>(l - En * invT - wmax);
+            const F w = ex<F>(arg(e, l));
             s0 += w;
             s1 += w * (En - Eref);
         }
@@ -122,13 +143,13 @@ __global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double*
             const F l = lng[(size_t)e * a.n_m + m];
             if (l == (F)-INFINITY) continue;
             const F En = (F)(a.e_min + 2 * e);
-            const F w = ex<F>(l - En * invT - wmax);
+            const F w = ex<F>(arg(e, l));
             const F d = En - m1;
             s2 += w * d * d;
         }
         s2 = warp_sum(s2);
         if (lane == 0) {
-            L[m] = (double)wmax + log((double)s0);
+            L[m] = (lngd[is] - (double)(a.e_min + 2 * es) * invTd) + log((double)s0);
             mu[m] = m1;
             var[m] = s2 / s0;
         }
@@ -141,24 +162,32 @@ __global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double*
     }
     __syncthreads();
     const double Lmax = s_Lmax;
-    for (int m = threadIdx.x; m < a.n_m; m += blockDim.x) Lr[m] = L[m] == -INFINITY ? (F)-INFINITY : (F)(L[m] - Lmax);
+    for (int m = threadIdx.x; m < a.n_m; m += blockDim.x) {
+        if (L[m] == -INFINITY) { Lr[m] = (F)-INFINITY; Llo[m] = 0; continue; }
+        const double r = L[m] - Lmax;
+        Lr[m] = (F)r;
+        Llo[m] = (F)(r - (double)(F)r);
+    }
     __syncthreads();
 
     // Stage 2: one thread per field value.
     for (int ih = threadIdx.x; ih < a.nh; ih += blockDim.x) {
-        const double hd = a.h[ih];
-        const F hT = (F)(hd / T), hF = (F)hd;
+        const double hd = a.h[ih], hTd = hd * invTd;
+        const F hT = (F)hTd, hTlo = (F)(hTd - (double)hT), hF = (F)hd;
         F amax = (F)-INFINITY;
+        int ms = 0;
         for (int m = 0; m < a.n_m; ++m) {
             if (Lr[m] == (F)-INFINITY) continue;
             const F am = Lr[m] + hT * (F)(2 * m - a.n);
-            amax = fmax(amax, am);
+            if (am > amax) { amax = am; ms = m; }
         }
+        const F Ls = Lr[ms], Lls = Llo[ms];
+        const int Ms = 2 * ms - a.n;
         F z = 0, zM = 0, zH = 0;
         for (int m = 0; m < a.n_m; ++m) {
             if (Lr[m] == (F)-INFINITY) continue;
-            const F Mm = (F)(2 * m - a.n);
-            const F p = ex<F>(Lr[m] + hT * Mm - amax);
+            const F Mm = (F)(2 * m - a.n), dMs = (F)(2 * m - a.n - Ms);
+            const F p = ex<F>((Lr[m] - Ls) + (Llo[m] - Lls) + fma(hT, dMs, hTlo * dMs));
             z += p;
             zM += p * Mm;
             zH += p * (mu[m] - hF * Mm);
@@ -167,8 +196,8 @@ __global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double*
         F vH = 0, vM = 0;
         for (int m = 0; m < a.n_m; ++m) {
             if (Lr[m] == (F)-INFINITY) continue;
-            const F Mm = (F)(2 * m - a.n);
-            const F p = ex<F>(Lr[m] + hT * Mm - amax);
+            const F Mm = (F)(2 * m - a.n), dMs = (F)(2 * m - a.n - Ms);
+            const F p = ex<F>((Lr[m] - Ls) + (Llo[m] - Lls) + fma(hT, dMs, hTlo * dMs));
             const F dH = mu[m] - hF * Mm - mH, dM = Mm - mM;
             vH += p * (var[m] + dH * dH);
             vM += p * dM * dM;
@@ -176,11 +205,11 @@ __global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double*
         vH /= z;
         vM /= z;
         const size_t o = (size_t)it * a.nh + ih;
-        if (a.logZ) a.logZ[o] = Lmax + (double)amax + log((double)z);
+        if (a.logZ) a.logZ[o] = L[ms] + hTd * (double)Ms + (double)lg<F>(z);
         if (a.E) a.E[o] = (double)mH;
         if (a.M) a.M[o] = (double)mM;
-        if (a.C) a.C[o] = (double)vH / (T * T);
-        if (a.chi) a.chi[o] = (double)vM / T;
+        if (a.C) a.C[o] = (double)vH * (invTd * invTd);
+        if (a.chi) a.chi[o] = (double)vM * invTd;
     }
 }
 
@@ -193,17 +222,18 @@ __global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double*
     } while (0)
 
 // Enqueue the thermodynamics kernels; all pointers on the device. lng: n_e * n_m doubles, lngf:
-// n_e * n_m floats of scratch.
+// 2 * n_e * n_m floats of scratch.
 void launch_thermo(const ThermoArgs& a, double* lng, float* lngf, int precision, cudaStream_t s) {
     const int nbins = a.n_e * a.n_m;
-    log_counts_kernel<<<std::min(1024, (nbins + 255) / 256), 256, 0, s>>>(a.g, nbins, lng, lngf);
+    float* lnglo = lngf + nbins;
+    log_counts_kernel<<<std::min(1024, (nbins + 255) / 256), 256, 0, s>>>(a.g, nbins, lng, lngf, lnglo);
     ISG_CUDA(cudaGetLastError());
     if (precision == ISG_FP64) {
-        const size_t smem = (size_t)a.n_m * (8 + 3 * sizeof(double));
-        thermo_kernel<double><<<a.nT, 256, smem, s>>>(a, lng, lngf);
+        const size_t smem = (size_t)a.n_m * (8 + 4 * sizeof(double));
+        thermo_kernel<double><<<a.nT, 256, smem, s>>>(a, lng, lngf, lnglo);
     } else {
-        const size_t smem = (size_t)a.n_m * (8 + 3 * sizeof(float));
-        thermo_kernel<float><<<a.nT, 256, smem, s>>>(a, lng, lngf);
+        const size_t smem = (size_t)a.n_m * (8 + 4 * sizeof(float));
+        thermo_kernel<float><<<a.nT, 256, smem, s>>>(a, lng, lngf, lnglo);
     }
     ISG_CUDA(cudaGetLastError());
 }
@@ -233,7 +263,7 @@ extern "C" isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const is
         size_t off = 0;
         auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) & ~(size_t)255; return o; };
         const size_t o_lng = take(sizeof(double) * (size_t)n_e * n_m);
-        const size_t o_lngf = take(sizeof(float) * (size_t)n_e * n_m);
+        const size_t o_lngf = take(2 * sizeof(float) * (size_t)n_e * n_m);      // lngf, then lnglo
         const size_t o_T = take(sizeof(double) * nT), o_h = take(sizeof(double) * nh);
         const size_t o_g = g_on_device ? 0 : take(gbytes);
         const size_t o_out = out_on_device ? 0 : take(5 * sizeof(double) * pts);
