@@ -43,8 +43,8 @@ SM_MAX_MHZ_FALLBACK = 2070.0
 OPS_PER_CONFIG = 2
 # DRAM traffic of one enumeration launch on this workload from the committed ncu capture
 # (profiles/enumerate_kernel_torus6x6.md), valid only for the kernel sources it was taken on.
-TRAFFIC_BYTES = None
-TRAFFIC_SOURCES_SHA = None
+TRAFFIC_BYTES = 34816          # dram__bytes_read.sum + dram__bytes_write.sum of one launch (program + flush)
+TRAFFIC_SOURCES_SHA = "c7bad2eada67e7ad"
 
 
 def kernel_sources_sha() -> str:
