@@ -302,13 +302,25 @@ def extra_measurements(stream, dev):
     def small_step():
         isg.isg_enumerate(gh, g, stream)
         isg.isg_thermo(g, gh, T, [0.0], isg.ISG_FP64, stream, out=o64)
-    dev_ms = _event_ms(small_step, stream, 50)
-    t0 = time.perf_counter()
-    for _ in range(50):
-        small_step()
-    torch.cuda.synchronize()
-    out["square4x4_free"] = {"device_us_per_call": dev_ms * 1e3, "host_us_per_call": (time.perf_counter() - t0) / 50 * 1e6,
-                             "what": "isg_enumerate (65,536 configurations) + isg_thermo (64 T, FP64), device buffers"}
+    pe = isg.prepare_enumerate(gh, g, stream)
+    pt = isg.prepare_thermo(g, gh, T, [0.0], o64, isg.ISG_FP64, stream)
+
+    def prepared_step():
+        pe()
+        pt()
+
+    def host_us(fn, n=200):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / n * 1e6
+    out["square4x4_free"] = {
+        "what": "isg_enumerate (65,536 configurations) + isg_thermo (64 T, FP64), device buffers, back to back",
+        "us_per_call_prepared": host_us(prepared_step), "us_per_call_python_binding": host_us(small_step),
+        "device_us_per_call_isolated": _event_ms(prepared_step, stream, 50) * 1e3}
     # EA +-J batch: one prepared batch (graph replay) vs a loop of per-instance launches
     lats = workloads.ea_instances()
     hs = [isg.isg_graph_create(l.n, l.edges) for l in lats]

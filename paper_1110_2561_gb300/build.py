@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libisg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["host.cpp", "enumerate.cu", "thermo.cu", "probe.cu", "noalloc.cu", "batch.cu", "server.cu"]
-HEADERS = ["enum_core.cuh", "isg_internal.h", "batch_internal.h"]
+HEADERS = ["enum_core.cuh", "isg_internal.h", "batch_internal.h", "nvtx_range.h"]
 
 
 def _nvcc() -> str:

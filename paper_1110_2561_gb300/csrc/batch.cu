@@ -22,6 +22,7 @@
 
 #include "batch_internal.h"
 #include "isg_internal.h"
+#include "nvtx_range.h"
 
 namespace isg {
 
@@ -423,6 +424,7 @@ isg_status isg_batch_create(int32_t n_graphs, const isg_graph* const* graphs, co
         if (!out) fail(ISG_ERR_INVALID, "out is NULL");
         *out = nullptr;
         if (n_graphs < 1 || !graphs) fail(ISG_ERR_INVALID, "need at least one graph");
+        NvtxRange nvtx("isg_batch_create");
         for (int k = 0; k < n_graphs; ++k) if (!graphs[k]) fail(ISG_ERR_INVALID, "graph " + std::to_string(k) + " is NULL");
         isg_options o = resolve_options(opt);
         const DeviceInfo d = device_info();
@@ -470,6 +472,7 @@ isg_status isg_batch_create(int32_t n_graphs, const isg_graph* const* graphs, co
 isg_status isg_batch_run(isg_batch* b, void* stream) {
     return guarded_cuda([&] {
         if (!b) fail(ISG_ERR_INVALID, "batch is NULL");
+        NvtxRange nvtx("isg_batch_run");
         std::lock_guard<std::mutex> lk(b->mu);
         int dev = 0;
         ISG_CUDA(cudaGetDevice(&dev));

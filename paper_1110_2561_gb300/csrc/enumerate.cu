@@ -12,11 +12,13 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
 
 #include "isg_internal.h"
+#include "nvtx_range.h"
 
 namespace isg {
 
@@ -60,6 +62,15 @@ __device__ __forceinline__ void stage_blob(uint64_t* dst, const uint64_t* src, i
     for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
 }
 
+// Programs up to this many words travel inside the kernel parameters (no host-to-device copy);
+// every graph of up to 64 spins with at most two weight classes fits.
+constexpr int kInlineProgramWords = 512;
+
+struct EnumParams {
+    EnumArgs a;                                 // a.blob == NULL: the program is in `program`
+    uint64_t program[kInlineProgramWords];
+};
+
 // Add the CTA's privatised bins into the public int64 table and clear them.
 __device__ __forceinline__ void flush_bins(const ProgHeader* hd, uint32_t* hist, int copies, int64_t* g) {
     const int nb = hd->nbins_c, n_m = hd->n_m, R = hd->stride;
@@ -78,9 +89,10 @@ __device__ __forceinline__ void flush_bins(const ProgHeader* hd, uint32_t* hist,
 }
 
 template <int B, class Sink>
-__global__ void __launch_bounds__(1024) enumerate_kernel(EnumArgs a) {
+__global__ void __launch_bounds__(1024) enumerate_kernel(const __grid_constant__ EnumParams P) {
+    const EnumArgs& a = P.a;
     extern __shared__ __align__(16) uint64_t smem[];
-    stage_blob(smem, a.blob, a.blob_words);
+    stage_blob(smem, a.blob ? a.blob : P.program, a.blob_words);
     uint32_t* hist = reinterpret_cast<uint32_t*>(smem + ((a.blob_words + 1) & ~1));
     __shared__ int s_done;
     if (threadIdx.x == 0) s_done = 0;
@@ -116,9 +128,11 @@ __global__ void __launch_bounds__(1024) enumerate_kernel(EnumArgs a) {
 
 // Small graphs (fewer than 11 free spins): one thread per configuration, counted straight into
 // the int64 table.
-__global__ void enumerate_small_kernel(const uint64_t* blob, int words, uint64_t s_lo, uint64_t s_hi, int64_t* g) {
+__global__ void enumerate_small_kernel(const __grid_constant__ EnumParams P, uint64_t s_lo, uint64_t s_hi) {
+    const int words = P.a.blob_words;
+    int64_t* g = P.a.g;
     extern __shared__ __align__(16) uint64_t smem[];
-    stage_blob(smem, blob, words);
+    stage_blob(smem, P.a.blob ? P.a.blob : P.program, words);
     __syncthreads();
     const ProgHeader* hd = reinterpret_cast<const ProgHeader*>(smem);
     const ProgView v = make_view(smem);
@@ -179,7 +193,7 @@ DeviceInfo device_info() {
 // Grid: the planned CTAs per SM, capped by what the registers and shared memory of this
 // instantiation allow (cudaOccupancyMaxActiveBlocksPerMultiprocessor), never more than tasks.
 template <int B, class Sink>
-static void launch_bs(const Plan& p, const EnumArgs& a, cudaStream_t s) {
+static void launch_bs(const Plan& p, const EnumParams& a, cudaStream_t s) {
     const int smem = (int)(p.smem_bytes + 16);
     ISG_CUDA(cudaFuncSetAttribute(enumerate_kernel<B, Sink>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int occ = 0;
@@ -193,23 +207,35 @@ static void launch_bs(const Plan& p, const EnumArgs& a, cudaStream_t s) {
 }
 
 template <int B>
-static void launch_b(const Plan& p, const EnumArgs& a, cudaStream_t s) {
+static void launch_b(const Plan& p, const EnumParams& a, cudaStream_t s) {
     if (p.aggregate) launch_bs<B, MatchSink>(p, a, s);
     else launch_bs<B, SmemSink>(p, a, s);
 }
 
-// Enqueue the kernels of one plan; `table` must be zeroed (or hold counts to add to).
+// Enqueue the kernels of one plan; `table` must be zeroed (or hold counts to add to). The program
+// is read from d_blob (device), or, when d_blob is NULL, from host_blob, which must then fit the
+// kernel parameters (program_fits_inline).
+bool program_fits_inline(size_t words) { return words <= (size_t)kInlineProgramWords; }
+
 void launch_enumeration(const Plan& p, const uint64_t* d_blob, int blob_words, int64_t* table,
-                        unsigned long long* counter, unsigned int* status, cudaStream_t s) {
+                        unsigned long long* counter, unsigned int* status, cudaStream_t s,
+                        const uint64_t* host_blob) {
+    std::unique_ptr<EnumParams> P(new EnumParams());
+    EnumArgs& a = P->a;
+    if (!d_blob) {
+        if (!host_blob || !program_fits_inline((size_t)blob_words)) fail(ISG_ERR_INTERNAL, "program does not fit inline");
+        std::memcpy(P->program, host_blob, sizeof(uint64_t) * (size_t)blob_words);
+    }
     if (p.small) {
+        a.blob = d_blob;
+        a.blob_words = blob_words;
+        a.g = table;
         ISG_CUDA(cudaFuncSetAttribute(enumerate_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       blob_words * 8));
-        enumerate_small_kernel<<<p.grid, p.threads, blob_words * 8, s>>>(d_blob, blob_words, p.s_lo, p.s_hi, table);
+        enumerate_small_kernel<<<p.grid, p.threads, blob_words * 8, s>>>(*P, p.s_lo, p.s_hi);
         ISG_CUDA(cudaGetLastError());
         return;
     }
-    EnumArgs a;
-    std::memset(&a, 0, sizeof a);
     a.blob = d_blob;
     a.g = table;
     a.counter = counter;
@@ -220,13 +246,13 @@ void launch_enumeration(const Plan& p, const uint64_t* d_blob, int blob_words, i
     a.copies = p.copies;
     a.flush_rounds = p.flush_rounds;
     switch (p.b) {
-        case 1: launch_b<1>(p, a, s); break;
-        case 2: launch_b<2>(p, a, s); break;
-        case 3: launch_b<3>(p, a, s); break;
-        case 4: launch_b<4>(p, a, s); break;
-        case 5: launch_b<5>(p, a, s); break;
-        case 6: launch_b<6>(p, a, s); break;
-        case 7: launch_b<7>(p, a, s); break;
+        case 1: launch_b<1>(p, *P, s); break;
+        case 2: launch_b<2>(p, *P, s); break;
+        case 3: launch_b<3>(p, *P, s); break;
+        case 4: launch_b<4>(p, *P, s); break;
+        case 5: launch_b<5>(p, *P, s); break;
+        case 6: launch_b<6>(p, *P, s); break;
+        case 7: launch_b<7>(p, *P, s); break;
         default: fail(ISG_ERR_INTERNAL, "bad low block size");
     }
 }
@@ -263,7 +289,8 @@ static float time_plan(const isg_graph& g, const isg_options& o, cudaStream_t s,
         ISG_CUDA(cudaMemsetAsync(scratch, 0, 16, s));
         ISG_CUDA(cudaEventRecord(e0, s));
         launch_enumeration(p, reinterpret_cast<const uint64_t*>(scratch + 16), (int)blob.size(), table,
-                           reinterpret_cast<unsigned long long*>(scratch), reinterpret_cast<unsigned int*>(scratch + 8), s);
+                           reinterpret_cast<unsigned long long*>(scratch), reinterpret_cast<unsigned int*>(scratch + 8), s,
+                           nullptr);
         ISG_CUDA(cudaEventRecord(e1, s));
         ISG_CUDA(cudaEventSynchronize(e1));
         float ms = 0;
@@ -354,6 +381,7 @@ using namespace isg;
 extern "C" isg_status isg_autotune(const isg_graph* graph, void* stream, const isg_options* opt, isg_options* tuned) {
     try {
         clear_error();
+        NvtxRange nvtx("isg_autotune");
         if (!graph || !tuned) fail(ISG_ERR_INVALID, "graph or tuned is NULL");
         isg_options o = resolve_options(opt);
         o.autotune = 1;
@@ -376,6 +404,7 @@ extern "C" isg_status isg_enumerate(const isg_graph* graph, void* stream, int64_
                                     const isg_options* opt) {
     try {
         clear_error();
+        NvtxRange nvtx("isg_enumerate");
         if (!graph || !g_out) fail(ISG_ERR_INVALID, "graph or g_out is NULL");
         isg_options o = resolve_options(opt);
         cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -398,11 +427,13 @@ extern "C" isg_status isg_enumerate(const isg_graph* graph, void* stream, int64_
             ~Free() { if (p) cudaFreeAsync(p, s); }
         } guard{scratch, s};
         ISG_CUDA(cudaMemsetAsync(scratch, 0, 16, s));
-        ISG_CUDA(cudaMemcpyAsync(scratch + off_blob, blob.data(), blob_bytes, cudaMemcpyHostToDevice, s));
+        const bool inl = program_fits_inline(blob.size());
+        if (!inl) ISG_CUDA(cudaMemcpyAsync(scratch + off_blob, blob.data(), blob_bytes, cudaMemcpyHostToDevice, s));
         int64_t* table = own_table ? reinterpret_cast<int64_t*>(scratch + off_table) : g_out;
         if (own_table || !o.accumulate) ISG_CUDA(cudaMemsetAsync(table, 0, table_bytes, s));
-        launch_enumeration(p, reinterpret_cast<const uint64_t*>(scratch + off_blob), (int)blob.size(), table,
-                           reinterpret_cast<unsigned long long*>(scratch), reinterpret_cast<unsigned int*>(scratch + 8), s);
+        launch_enumeration(p, inl ? nullptr : reinterpret_cast<const uint64_t*>(scratch + off_blob), (int)blob.size(),
+                           table, reinterpret_cast<unsigned long long*>(scratch), reinterpret_cast<unsigned int*>(scratch + 8),
+                           s, blob.data());
         if (sym) {
             const int n_m = graph->n + 1, n_e = (int)(graph->S + 1);
             int64_t* full = g_out_on_device ? g_out : reinterpret_cast<int64_t*>(scratch + off_table + table_bytes);

@@ -32,7 +32,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 
 DeviceInfo device_info();
 void launch_enumeration(const Plan& p, const uint64_t* d_blob, int blob_words, int64_t* table,
-                        unsigned long long* counter, unsigned int* status, cudaStream_t s);
+                        unsigned long long* counter, unsigned int* status, cudaStream_t s,
+                        const uint64_t* host_blob);
 
 // Device address of the scratch array on the current device, looked up on the first call that
 // runs on that device (with that device current) and cached.
@@ -86,7 +87,7 @@ extern "C" isg_status isg_enumerate_noalloc(const isg_graph* graph, void* stream
                   "cudaMemsetAsync(g_out)");
         launch_enumeration(p, reinterpret_cast<const uint64_t*>(scratch + kNoallocProgramOffset), (int)blob.size(),
                            g_out_device, reinterpret_cast<unsigned long long*>(scratch),
-                           reinterpret_cast<unsigned int*>(scratch + 8), s);
+                           reinterpret_cast<unsigned int*>(scratch + 8), s, nullptr);
         return ISG_OK;
     } catch (const Error& e) {
         set_error(e.msg);

@@ -27,6 +27,7 @@
 
 #include "batch_internal.h"
 #include "isg_internal.h"
+#include "nvtx_range.h"
 
 namespace isg {
 
@@ -177,6 +178,7 @@ static void release_locked(isg_server* s, Request& r) {
 
 // Build and enqueue one engine step (caller holds mu; CUDA calls are asynchronous).
 static bool issue_step_locked(isg_server* s) {
+    NvtxRange nvtx("isg_server_step");
     int buf = -1;
     for (int k = 0; k < 2; ++k) if (!s->buf_busy[k]) { buf = k; break; }
     if (buf < 0 || s->active.empty()) return false;

@@ -18,17 +18,21 @@
 
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
 #include "isg_internal.h"
+#include "nvtx_range.h"
 
 namespace isg {
 
+constexpr int kInlineGrid = 1024;   // T and h values passed inside the kernel parameters
+
 struct ThermoArgs {
     const int64_t* g;   // n_e x n_m counts
-    const double* T;    // nT
-    const double* h;    // nh
+    const double* T;    // nT (device), or NULL: inline[0 .. nT)
+    const double* h;    // nh (device), or NULL: inline[nT .. nT + nh)
     double* logZ;
     double* E;
     double* M;
@@ -36,6 +40,13 @@ struct ThermoArgs {
     double* chi;
     int n, n_e, n_m, nT, nh;
     int64_t e_min;
+};
+
+// Kernel parameters: the arguments plus small grids inline, so a call on a small grid needs no
+// host-to-device copy.
+struct ThermoParams {
+    ThermoArgs a;
+    double grid[kInlineGrid];
 };
 
 template <class F> __device__ __forceinline__ F ex(F x);
@@ -82,8 +93,11 @@ template <> __device__ __forceinline__ const float* pick<float>(const double*, c
 // float this is what keeps ln Z accurate to ~1e-7 although L - max L reaches hundreds), and
 // finishes ln Z = max L + (L[m*] - max L) + (h/T) M_m* + ln(sum exp d_m) in double.
 template <class F>
-__global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double* lngd, const float* lngf,
-                                                     const float* lnglo) {
+__global__ void __launch_bounds__(256) thermo_kernel(const __grid_constant__ ThermoParams P, const double* lngd,
+                                                     const float* lngf, const float* lnglo) {
+    const ThermoArgs& a = P.a;
+    const double* Tv = a.T ? a.T : P.grid;
+    const double* hv = a.h ? a.h : P.grid + a.nT;
     const F* lng = pick<F>(lngd, lngf);
     const bool pair = sizeof(F) == sizeof(float);   // float: ln g carried as lngf + lnglo
     extern __shared__ __align__(16) unsigned char sm[];
@@ -94,7 +108,7 @@ __global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double*
     F* Llo = Lr + a.n_m;                 // the rounding remainder of Lr
     __shared__ double s_Lmax;
     const int it = blockIdx.x;
-    const double T = a.T[it], invTd = 1.0 / T;
+    const double T = Tv[it], invTd = 1.0 / T;
     const F invT = (F)invTd, invTlo = (F)(invTd - (double)invT);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
 
@@ -172,7 +186,7 @@ __global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double*
 
     // Stage 2: one thread per field value.
     for (int ih = threadIdx.x; ih < a.nh; ih += blockDim.x) {
-        const double hd = a.h[ih], hTd = hd * invTd;
+        const double hd = hv[ih], hTd = hd * invTd;
         const F hT = (F)hTd, hTlo = (F)(hTd - (double)hT), hF = (F)hd;
         F amax = (F)-INFINITY;
         int ms = 0;
@@ -223,17 +237,18 @@ __global__ void __launch_bounds__(256) thermo_kernel(ThermoArgs a, const double*
 
 // Enqueue the thermodynamics kernels; all pointers on the device. lng: n_e * n_m doubles, lngf:
 // 2 * n_e * n_m floats of scratch.
-void launch_thermo(const ThermoArgs& a, double* lng, float* lngf, int precision, cudaStream_t s) {
+void launch_thermo(const ThermoParams& P, double* lng, float* lngf, int precision, cudaStream_t s) {
+    const ThermoArgs& a = P.a;
     const int nbins = a.n_e * a.n_m;
     float* lnglo = lngf + nbins;
     log_counts_kernel<<<std::min(1024, (nbins + 255) / 256), 256, 0, s>>>(a.g, nbins, lng, lngf, lnglo);
     ISG_CUDA(cudaGetLastError());
     if (precision == ISG_FP64) {
         const size_t smem = (size_t)a.n_m * (8 + 4 * sizeof(double));
-        thermo_kernel<double><<<a.nT, 256, smem, s>>>(a, lng, lngf, lnglo);
+        thermo_kernel<double><<<a.nT, 256, smem, s>>>(P, lng, lngf, lnglo);
     } else {
         const size_t smem = (size_t)a.n_m * (8 + 4 * sizeof(float));
-        thermo_kernel<float><<<a.nT, 256, smem, s>>>(a, lng, lngf, lnglo);
+        thermo_kernel<float><<<a.nT, 256, smem, s>>>(P, lng, lngf, lnglo);
     }
     ISG_CUDA(cudaGetLastError());
 }
@@ -247,6 +262,7 @@ extern "C" isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const is
                                  int32_t out_on_device, double* logZ, double* E, double* M, double* C, double* chi) {
     try {
         clear_error();
+        NvtxRange nvtx("isg_thermo");
         if (!g || !graph || !T || !h) fail(ISG_ERR_INVALID, "NULL argument");
         if (nT < 1 || nh < 1) fail(ISG_ERR_INVALID, "nT and nh must be >= 1");
         if (precision != ISG_FP64 && precision != ISG_FP32) fail(ISG_ERR_INVALID, "precision must be ISG_FP64 or ISG_FP32");
@@ -264,7 +280,8 @@ extern "C" isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const is
         auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) & ~(size_t)255; return o; };
         const size_t o_lng = take(sizeof(double) * (size_t)n_e * n_m);
         const size_t o_lngf = take(2 * sizeof(float) * (size_t)n_e * n_m);      // lngf, then lnglo
-        const size_t o_T = take(sizeof(double) * nT), o_h = take(sizeof(double) * nh);
+        const bool inline_grid = nT + nh <= kInlineGrid;
+        const size_t o_T = inline_grid ? 0 : take(sizeof(double) * nT), o_h = inline_grid ? 0 : take(sizeof(double) * nh);
         const size_t o_g = g_on_device ? 0 : take(gbytes);
         const size_t o_out = out_on_device ? 0 : take(5 * sizeof(double) * pts);
         char* scratch = nullptr;
@@ -273,13 +290,20 @@ extern "C" isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const is
             char* p; cudaStream_t s;
             ~Free() { if (p) cudaFreeAsync(p, s); }
         } guard{scratch, s};
-        ThermoArgs a;
-        std::memset(&a, 0, sizeof a);
+        std::unique_ptr<ThermoParams> P(new ThermoParams());
+        ThermoArgs& a = P->a;
         a.n = graph->n; a.n_e = n_e; a.n_m = n_m; a.nT = nT; a.nh = nh; a.e_min = -graph->S;
-        a.T = reinterpret_cast<double*>(scratch + o_T);
-        a.h = reinterpret_cast<double*>(scratch + o_h);
-        ISG_CUDA(cudaMemcpyAsync(scratch + o_T, T, sizeof(double) * nT, cudaMemcpyHostToDevice, s));
-        ISG_CUDA(cudaMemcpyAsync(scratch + o_h, h, sizeof(double) * nh, cudaMemcpyHostToDevice, s));
+        if (inline_grid) {
+            std::memcpy(P->grid, T, sizeof(double) * nT);
+            std::memcpy(P->grid + nT, h, sizeof(double) * nh);
+            a.T = nullptr;
+            a.h = nullptr;
+        } else {
+            a.T = reinterpret_cast<double*>(scratch + o_T);
+            a.h = reinterpret_cast<double*>(scratch + o_h);
+            ISG_CUDA(cudaMemcpyAsync(scratch + o_T, T, sizeof(double) * nT, cudaMemcpyHostToDevice, s));
+            ISG_CUDA(cudaMemcpyAsync(scratch + o_h, h, sizeof(double) * nh, cudaMemcpyHostToDevice, s));
+        }
         if (g_on_device) a.g = g;
         else {
             ISG_CUDA(cudaMemcpyAsync(scratch + o_g, g, gbytes, cudaMemcpyHostToDevice, s));
@@ -292,7 +316,7 @@ extern "C" isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const is
                           : out_on_device ? outs_host[k]
                                           : reinterpret_cast<double*>(scratch + o_out) + k * pts;
         a.logZ = outs_dev[0]; a.E = outs_dev[1]; a.M = outs_dev[2]; a.C = outs_dev[3]; a.chi = outs_dev[4];
-        launch_thermo(a, reinterpret_cast<double*>(scratch + o_lng), reinterpret_cast<float*>(scratch + o_lngf), precision, s);
+        launch_thermo(*P, reinterpret_cast<double*>(scratch + o_lng), reinterpret_cast<float*>(scratch + o_lngf), precision, s);
         if (!out_on_device) {
             for (int k = 0; k < 5; ++k)
                 if (outs_host[k])

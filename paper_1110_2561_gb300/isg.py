@@ -126,6 +126,7 @@ class Graph:
     def __init__(self, ptr: int, n: int):
         self.ptr = ptr
         self.n = n
+        self._shape = None
 
     def __del__(self):
         if getattr(self, "ptr", None) and _lib is not None:
@@ -168,8 +169,10 @@ def isg_graph_size(graph: Graph):
 
 
 def table_shape(graph: Graph):
-    _, _, n_e, _, n_m = isg_graph_bins(graph)
-    return n_e, n_m
+    if graph._shape is None:
+        _, _, n_e, _, n_m = isg_graph_bins(graph)
+        graph._shape = (n_e, n_m)
+    return graph._shape
 
 
 def isg_enumerate(graph: Graph, g_out=None, stream=None, **options):
@@ -355,12 +358,22 @@ def _tensor_view(ptr: int, numel: int, dtype):
     return torch.as_tensor(_Holder(), device="cuda")
 
 
+_TORCH = {}
+
+
 def _check_tensor(t, shape, dtype: str):
-    import torch
-    want = getattr(torch, dtype)
-    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == want and t.is_contiguous()
-            and tuple(t.shape) == tuple(shape)):
+    if not _TORCH:
+        import torch
+        _TORCH.update(torch=torch, int64=torch.int64, float64=torch.float64)
+    if not (isinstance(t, _TORCH["torch"].Tensor) and t.is_cuda and t.dtype is _TORCH[dtype] and t.is_contiguous()
+            and t.shape == shape):
         raise ValueError(f"expected a contiguous {dtype} CUDA tensor of shape {tuple(shape)}")
+
+
+def _f64(x) -> np.ndarray:
+    if isinstance(x, np.ndarray) and x.dtype == np.float64 and x.ndim == 1 and x.flags.c_contiguous:
+        return x
+    return np.ascontiguousarray(np.atleast_1d(x), dtype=np.float64)
 
 
 def isg_thermo(g, graph: Graph, T, h, precision: int = ISG_FP64, stream=None, out=None):
@@ -369,8 +382,7 @@ def isg_thermo(g, graph: Graph, T, h, precision: int = ISG_FP64, stream=None, ou
     g: torch int64 CUDA tensor or numpy int64 array of table_shape(graph). out: None (numpy
     results, the call synchronises) or a tuple of 5 float64 CUDA tensors of shape (len(T), len(h))
     (filled asynchronously; None entries are skipped)."""
-    T = np.ascontiguousarray(np.atleast_1d(T), dtype=np.float64)
-    h = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
+    T, h = _f64(T), _f64(h)
     shape = table_shape(graph)
     if isinstance(g, np.ndarray):
         g = np.ascontiguousarray(g, dtype=np.int64)
@@ -388,15 +400,52 @@ def isg_thermo(g, graph: Graph, T, h, precision: int = ISG_FP64, stream=None, ou
                                 *ptrs))
         return tuple(res)
     ptrs = []
+    oshape = (len(T), len(h))
+    for t in out:
+        if t is None:
+            ptrs.append(None)
+        else:
+            _check_tensor(t, oshape, "float64")
+            ptrs.append(t.data_ptr())
+    _check(lib().isg_thermo(g_ptr, g_dev, graph, len(T), T.ctypes.data, len(h), h.ctypes.data, precision, s, 1,
+                            *ptrs))
+    return out
+
+
+class PreparedCall:
+    """A C entry point with its arguments validated and marshalled once; calling it again costs
+    only the C call (for latency-bound loops over small problems). The caller keeps the buffers
+    alive and unchanged in shape while the prepared call is in use."""
+
+    def __init__(self, fn, args, keep):
+        self._fn, self._args, self._keep = fn, args, keep
+
+    def __call__(self):
+        _check(self._fn(*self._args))
+
+
+def prepare_enumerate(graph: Graph, g_out, stream=None, **options) -> PreparedCall:
+    """isg_enumerate into a torch int64 CUDA tensor, prepared once."""
+    _check_tensor(g_out, table_shape(graph), "int64")
+    o = _options(**options)
+    args = (graph.ptr, _stream_handle(stream), g_out.data_ptr(), 1, ctypes.byref(o))
+    return PreparedCall(lib().isg_enumerate, args, (graph, g_out, o))
+
+
+def prepare_thermo(g, graph: Graph, T, h, out, precision: int = ISG_FP64, stream=None) -> PreparedCall:
+    """isg_thermo from a device table into five float64 CUDA tensors, prepared once."""
+    T, h = _f64(T), _f64(h)
+    _check_tensor(g, table_shape(graph), "int64")
+    ptrs = []
     for t in out:
         if t is None:
             ptrs.append(None)
         else:
             _check_tensor(t, (len(T), len(h)), "float64")
             ptrs.append(t.data_ptr())
-    _check(lib().isg_thermo(g_ptr, g_dev, graph, len(T), T.ctypes.data, len(h), h.ctypes.data, precision, s, 1,
-                            *ptrs))
-    return out
+    args = (g.data_ptr(), 1, graph.ptr, len(T), T.ctypes.data, len(h), h.ctypes.data, precision,
+            _stream_handle(stream), 1, *ptrs)
+    return PreparedCall(lib().isg_thermo, args, (graph, g, T, h, out))
 
 
 def isg_debug_plan(graph: Graph, sms: int = 0, **options) -> dict:

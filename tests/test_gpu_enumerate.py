@@ -190,3 +190,16 @@ def test_autotune_torus_6x6(isg, cuda):
     isg.isg_enumerate(g, out, autotune=1)
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), oracle.g_frontier(lat.n, lat.edges, max_active=16))
+
+
+def test_checkpoint_and_resume(isg, cuda, tmp_path):
+    """A long enumeration is resumable: shards [0, 5) of 2^4 into a host table, saved to disk,
+    reloaded, then shards [5, 16) added with accumulate, equal the full oracle table."""
+    lat = w.with_random_couplings(w.triangular(4, 5, True), w.SplitMix64(17), (-2, -1, 1, 2))
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    part = np.zeros(isg.table_shape(g), dtype=np.int64)
+    isg.isg_enumerate(g, part, shard_bits=4, shard_lo=0, shard_hi=5, accumulate=1)
+    np.save(tmp_path / "checkpoint.npy", part)
+    resumed = np.load(tmp_path / "checkpoint.npy")
+    isg.isg_enumerate(g, resumed, shard_bits=4, shard_lo=5, shard_hi=16, accumulate=1)
+    assert np.array_equal(resumed, oracle.g_masks(lat.n, lat.edges, threads=THREADS))
