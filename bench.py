@@ -317,10 +317,21 @@ def extra_measurements(stream, dev):
             fn()
         torch.cuda.synchronize()
         return (time.perf_counter() - t0) / n * 1e6
+    def latency_us(fn, n=200):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(n):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return statistics.median(ts) * 1e6
     out["square4x4_free"] = {
-        "what": "isg_enumerate (65,536 configurations) + isg_thermo (64 T, FP64), device buffers, back to back",
-        "us_per_call_prepared": host_us(prepared_step), "us_per_call_python_binding": host_us(small_step),
-        "device_us_per_call_isolated": _event_ms(prepared_step, stream, 50) * 1e3}
+        "what": "isg_enumerate (65,536 configurations) + isg_thermo (64 T, FP64), device buffers",
+        "latency_us": latency_us(prepared_step),
+        "back_to_back_us_per_call": host_us(prepared_step),
+        "back_to_back_us_per_call_python_binding": host_us(small_step)}
     # EA +-J batch: one prepared batch (graph replay) vs a loop of per-instance launches
     lats = workloads.ea_instances()
     hs = [isg.isg_graph_create(l.n, l.edges) for l in lats]

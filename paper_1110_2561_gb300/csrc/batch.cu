@@ -330,7 +330,7 @@ static float time_batch(int n, const isg_graph* const* graphs, const isg_options
     const size_t o_small = take(sizeof(int) * std::max<size_t>(1, ids.size()));
     const size_t o_blobs = take(8 * bp.blobs.size()), o_tab = take(8 * words);
     char* mem = nullptr;
-    ISG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&mem), at, s));
+    mem = static_cast<char*>(scratch_alloc(at, s));
     struct Free {
         char* p; cudaStream_t s;
         ~Free() { if (p) { cudaFreeAsync(p, s); cudaStreamSynchronize(s); } }

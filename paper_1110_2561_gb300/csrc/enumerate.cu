@@ -167,6 +167,32 @@ __global__ void mirror_kernel(const int64_t* half, int64_t* out, int n_e, int n_
                  std::string(#call) + ": " + cudaGetErrorString(e_));                               \
     } while (0)
 
+void* scratch_alloc(size_t bytes, void* stream) {
+    static std::mutex mu;
+    static std::vector<cudaMemPool_t> pools;
+    int dev = 0;
+    ISG_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
+        if (!pools[dev]) {
+            cudaMemPoolProps props;
+            std::memset(&props, 0, sizeof props);
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            ISG_CUDA(cudaMemPoolCreate(&pools[dev], &props));
+            uint64_t keep = ~0ull;
+            ISG_CUDA(cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+        }
+        pool = pools[dev];
+    }
+    void* p = nullptr;
+    ISG_CUDA(cudaMallocFromPoolAsync(&p, bytes, pool, static_cast<cudaStream_t>(stream)));
+    return p;
+}
+
 DeviceInfo device_info() {
     static std::mutex mu;
     static std::vector<DeviceInfo> cache;
@@ -315,7 +341,7 @@ static TunedShape run_autotune(const isg_graph& g, const isg_options& base, cuda
     if (k < 1) return best;
     const size_t table_bytes = sizeof(int64_t) * (size_t)public_bins(g);
     char* scratch = nullptr;
-    ISG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&scratch), 16 + 8 * (size_t)1700 + table_bytes + 256, s));
+    scratch = static_cast<char*>(scratch_alloc(16 + 8 * (size_t)1700 + table_bytes + 256, s));
     struct Free {
         char* p; cudaStream_t s;
         ~Free() { if (p) { cudaFreeAsync(p, s); cudaStreamSynchronize(s); } }
@@ -421,7 +447,7 @@ extern "C" isg_status isg_enumerate(const isg_graph* graph, void* stream, int64_
         const bool own_table = !g_out_on_device || sym;
         const size_t scratch_bytes = off_table + (own_table ? table_bytes : 0) + (sym && !g_out_on_device ? table_bytes : 0);
         char* scratch = nullptr;
-        ISG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&scratch), scratch_bytes, s));
+        scratch = static_cast<char*>(scratch_alloc(scratch_bytes, s));
         struct Free {
             char* p; cudaStream_t s;
             ~Free() { if (p) cudaFreeAsync(p, s); }

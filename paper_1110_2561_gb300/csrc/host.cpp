@@ -164,7 +164,10 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d) {
         // about 2^15 warp tasks (several per resident warp, so the dynamic queue balances), but at
         // least 2^12 configurations per lane so the from-scratch start of a task stays negligible
         int q = free - 5 - std::max(0, 15 - shards_log2);
-        q = std::max(q, std::min(12, free - 5));
+        int qmin = std::min(12, free - 5);
+        // small problems are latency-bound: spread them over >= 256 warp tasks where they allow it
+        if (free - 5 - qmin < 8) qmin = std::max(p.b, free - 5 - 8);
+        q = std::max(q, qmin);
         q = std::min(q, 20);
         q = std::min(q, free - 5);
         p.q = std::max(q, p.b);

@@ -74,6 +74,12 @@ inline int64_t public_bin(const isg_graph& g, int64_t compact, int64_t stride) {
     return ((E + g.S) / 2) * n_m + m;
 }
 
+// Stream-ordered scratch from the library's own memory pool on the current device (free it with
+// cudaFreeAsync). The pool keeps freed memory for reuse instead of returning it at every
+// synchronisation, so a call's few kilobytes of scratch cost no remapping. `stream` is a
+// cudaStream_t.
+void* scratch_alloc(size_t bytes, void* stream);
+
 // Row stride of the shared histogram for a graph (>= N + 1), padded against bank conflicts.
 int choose_stride(const isg_graph& g, int requested, int residue);
 

@@ -1,7 +1,7 @@
 // noalloc.cu -- isg_enumerate_noalloc: the enumeration entry point for callers that must not
 // allocate device memory.
 //
-// isg_enumerate takes a few kilobytes of stream-ordered scratch per call (cudaMallocAsync) for
+// isg_enumerate takes a few kilobytes of stream-ordered scratch per call (a pool allocation) for
 // its task counter, its status word and the device copy of the graph program. Some callers
 // cannot allow that: a process whose device memory is fully reserved by another allocator (for
 // example a framework's caching allocator holding the whole GPU), a real-time or serving loop

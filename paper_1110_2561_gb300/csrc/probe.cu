@@ -96,7 +96,7 @@ extern "C" isg_status isg_probe_peaks(void* stream, double* red_conflict_free, d
         ISG_CUDA(cudaGetDevice(&dev));
         ISG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         unsigned* sink = nullptr;
-        ISG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&sink), 4, s));
+        sink = static_cast<unsigned*>(scratch_alloc(4, s));
         const double r0 = probe_rate<0>(s, sink, sms, 1.0);
         const double r1 = probe_rate<1>(s, sink, sms, 1.0);
         const double r2 = probe_rate<2>(s, sink, sms, 8.0);

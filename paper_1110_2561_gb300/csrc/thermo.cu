@@ -93,7 +93,7 @@ template <> __device__ __forceinline__ const float* pick<float>(const double*, c
 // float this is what keeps ln Z accurate to ~1e-7 although L - max L reaches hundreds), and
 // finishes ln Z = max L + (L[m*] - max L) + (h/T) M_m* + ln(sum exp d_m) in double.
 template <class F>
-__global__ void __launch_bounds__(256) thermo_kernel(const __grid_constant__ ThermoParams P, const double* lngd,
+__global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ ThermoParams P, const double* lngd,
                                                      const float* lngf, const float* lnglo) {
     const ThermoArgs& a = P.a;
     const double* Tv = a.T ? a.T : P.grid;
@@ -140,8 +140,23 @@ __global__ void __launch_bounds__(256) thermo_kernel(const __grid_constant__ The
             const F dl = (l - ls) + (pair ? (F)lnglo[(size_t)e * a.n_m + m] - lls : (F)0);
             return dl - fma(dE, invT, dE * invTlo);
         };
+        // weights of the first kCache bins of each lane stay in registers for the second pass
+        constexpr int kCache = 8;
+        F wc[kCache];
         F s0 = 0, s1 = 0;
-        for (int e = lane; e < a.n_e; e += 32) {
+#pragma unroll
+        for (int j = 0; j < kCache; ++j) {
+            const int e = lane + 32 * j;
+            wc[j] = 0;
+            if (e >= a.n_e) continue;
+            const F l = lng[(size_t)e * a.n_m + m];
+            if (l == (F)-INFINITY) continue;
+            const F w = ex<F>(arg(e, l));
+            wc[j] = w;
+            s0 += w;
+            s1 += w * ((F)(a.e_min + 2 * e) - Eref);
+        }
+        for (int e = lane + 32 * kCache; e < a.n_e; e += 32) {
             const F l = lng[(size_t)e * a.n_m + m];
             if (l == (F)-INFINITY) continue;
             const F En = (F)(a.e_min + 2 * e);
@@ -153,7 +168,12 @@ __global__ void __launch_bounds__(256) thermo_kernel(const __grid_constant__ The
         s1 = warp_sum(s1);
         const F m1 = Eref + s1 / s0;
         F s2 = 0;
-        for (int e = lane; e < a.n_e; e += 32) {
+#pragma unroll
+        for (int j = 0; j < kCache; ++j) {
+            const F d = (F)(a.e_min + 2 * (lane + 32 * j)) - m1;
+            s2 += wc[j] * d * d;
+        }
+        for (int e = lane + 32 * kCache; e < a.n_e; e += 32) {
             const F l = lng[(size_t)e * a.n_m + m];
             if (l == (F)-INFINITY) continue;
             const F En = (F)(a.e_min + 2 * e);
@@ -184,21 +204,30 @@ __global__ void __launch_bounds__(256) thermo_kernel(const __grid_constant__ The
     }
     __syncthreads();
 
-    // Stage 2: one thread per field value.
-    for (int ih = threadIdx.x; ih < a.nh; ih += blockDim.x) {
+    // Stage 2. Many field values: one thread per point, a serial loop over M. Few field values
+    // (fewer than 64): one warp per point, lanes over M, shuffle reductions.
+    const bool by_warp = a.nh < 64;
+    const int step = by_warp ? nw : blockDim.x, first = by_warp ? warp : threadIdx.x;
+    const int mstep = by_warp ? 32 : 1, mfirst = by_warp ? lane : 0;
+    for (int ih = first; ih < a.nh; ih += step) {
         const double hd = hv[ih], hTd = hd * invTd;
         const F hT = (F)hTd, hTlo = (F)(hTd - (double)hT), hF = (F)hd;
         F amax = (F)-INFINITY;
         int ms = 0;
-        for (int m = 0; m < a.n_m; ++m) {
+        for (int m = mfirst; m < a.n_m; m += mstep) {
             if (Lr[m] == (F)-INFINITY) continue;
             const F am = Lr[m] + hT * (F)(2 * m - a.n);
             if (am > amax) { amax = am; ms = m; }
         }
+        if (by_warp) {                        // the lowest lane holding the warp maximum names m*
+            const F wm = warp_max(amax);
+            const unsigned hit = __ballot_sync(0xffffffffu, amax == wm && wm != (F)-INFINITY);
+            ms = __shfl_sync(0xffffffffu, ms, hit ? __ffs(hit) - 1 : 0);
+        }
         const F Ls = Lr[ms], Lls = Llo[ms];
         const int Ms = 2 * ms - a.n;
         F z = 0, zM = 0, zH = 0;
-        for (int m = 0; m < a.n_m; ++m) {
+        for (int m = mfirst; m < a.n_m; m += mstep) {
             if (Lr[m] == (F)-INFINITY) continue;
             const F Mm = (F)(2 * m - a.n), dMs = (F)(2 * m - a.n - Ms);
             const F p = ex<F>((Lr[m] - Ls) + (Llo[m] - Lls) + fma(hT, dMs, hTlo * dMs));
@@ -206,15 +235,21 @@ __global__ void __launch_bounds__(256) thermo_kernel(const __grid_constant__ The
             zM += p * Mm;
             zH += p * (mu[m] - hF * Mm);
         }
+        if (by_warp) { z = warp_sum(z); zM = warp_sum(zM); zH = warp_sum(zH); }
         const F mM = zM / z, mH = zH / z;
         F vH = 0, vM = 0;
-        for (int m = 0; m < a.n_m; ++m) {
+        for (int m = mfirst; m < a.n_m; m += mstep) {
             if (Lr[m] == (F)-INFINITY) continue;
             const F Mm = (F)(2 * m - a.n), dMs = (F)(2 * m - a.n - Ms);
             const F p = ex<F>((Lr[m] - Ls) + (Llo[m] - Lls) + fma(hT, dMs, hTlo * dMs));
             const F dH = mu[m] - hF * Mm - mH, dM = Mm - mM;
             vH += p * (var[m] + dH * dH);
             vM += p * dM * dM;
+        }
+        if (by_warp) {
+            vH = warp_sum(vH);
+            vM = warp_sum(vM);
+            if (lane != 0) continue;
         }
         vH /= z;
         vM /= z;
@@ -243,12 +278,19 @@ void launch_thermo(const ThermoParams& P, double* lng, float* lngf, int precisio
     float* lnglo = lngf + nbins;
     log_counts_kernel<<<std::min(1024, (nbins + 255) / 256), 256, 0, s>>>(a.g, nbins, lng, lngf, lnglo);
     ISG_CUDA(cudaGetLastError());
+    // Few temperatures (fewer CTAs than SMs): one warp per column in stage 1, up to 32 warps, so
+    // latency-bound small grids run their columns side by side. Otherwise 256 threads per CTA,
+    // several CTAs per SM.
+    int sms = 0, dev = 0;
+    ISG_CUDA(cudaGetDevice(&dev));
+    ISG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int threads = a.nT < sms ? 32 * std::min(32, std::max(8, a.n_m)) : 256;
     if (precision == ISG_FP64) {
         const size_t smem = (size_t)a.n_m * (8 + 4 * sizeof(double));
-        thermo_kernel<double><<<a.nT, 256, smem, s>>>(P, lng, lngf, lnglo);
+        thermo_kernel<double><<<a.nT, threads, smem, s>>>(P, lng, lngf, lnglo);
     } else {
         const size_t smem = (size_t)a.n_m * (8 + 4 * sizeof(float));
-        thermo_kernel<float><<<a.nT, 256, smem, s>>>(P, lng, lngf, lnglo);
+        thermo_kernel<float><<<a.nT, threads, smem, s>>>(P, lng, lngf, lnglo);
     }
     ISG_CUDA(cudaGetLastError());
 }
@@ -285,7 +327,7 @@ extern "C" isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const is
         const size_t o_g = g_on_device ? 0 : take(gbytes);
         const size_t o_out = out_on_device ? 0 : take(5 * sizeof(double) * pts);
         char* scratch = nullptr;
-        ISG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&scratch), off, s));
+        scratch = static_cast<char*>(scratch_alloc(off, s));
         struct Free {
             char* p; cudaStream_t s;
             ~Free() { if (p) cudaFreeAsync(p, s); }
