@@ -367,6 +367,14 @@ def extra_measurements(stream, dev):
         "torus6x6_enumerated_configs_per_s": (1 << 35) / (sym_ms * 1e-3),
         "ea_4096_batched_ms": bsym_ms, "ea_4096_batched_instances_per_s": len(lats) / (bsym_ms * 1e-3),
         "ea_4096_effective_configs_per_s": configs / (bsym_ms * 1e-3)}
+    # derived physics: the temperature of the specific-heat maximum of the 6x6 torus (h = 0)
+    lat = workloads.square(6, 6, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=dev)
+    isg.isg_enumerate(gh, g, stream, autotune=1)
+    t0 = time.perf_counter()
+    tc, cmax = isg.isg_specific_heat_peak(g, gh, 0.0, 1.0, 4.0, isg.ISG_FP64, stream)
+    out["torus6x6_specific_heat_peak"] = {"T_peak": tc, "C_peak": cmax, "ms": (time.perf_counter() - t0) * 1e3}
     # cubic 3x3x4 torus: thermodynamics on 512 T x 256 h, FP32 vs FP64
     lat = workloads.cubic(3, 3, 4, True)
     gh = isg.isg_graph_create(lat.n, lat.edges)

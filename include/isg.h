@@ -228,6 +228,20 @@ ISG_API isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const isg_g
                       int32_t out_on_device, double* logZ, double* E, double* M, double* C, double* chi);
 
 /*
+ * Temperature of the specific-heat maximum at field h within [T_lo, T_hi] (the finite-system
+ * transition temperature that motivates exact counting, Sec. 1): C(T) = Var(H)/T^2 from Eq. (2)
+ * over the table g is evaluated by the thermodynamics kernels on a uniform grid of 257
+ * temperatures; the bracket then shrinks to the two neighbours of the best grid point and the
+ * grid is re-evaluated, until the bracket is below 1e-12 of the temperature (at most 12 rounds).
+ * With several maxima the one that is highest on the first grid wins. g on the device or host
+ * (g_on_device); synchronises stream. *T_peak receives the temperature, *C_peak (may be NULL)
+ * the value of C there. Errors: ISG_ERR_INVALID, ISG_ERR_NOMEM, ISG_ERR_CUDA.
+ */
+ISG_API isg_status isg_specific_heat_peak(const int64_t* g, int32_t g_on_device, const isg_graph* graph, double h,
+                                          double T_lo, double T_hi, int32_t precision, void* stream,
+                                          double* T_peak, double* C_peak);
+
+/*
  * Request server with continuous batching. A worker thread owns one stream on the device that is
  * current at isg_server_create and runs engine steps: each step is one launch of the batched
  * kernel over warp tasks drawn from every admitted request, shortest remaining work first, up to

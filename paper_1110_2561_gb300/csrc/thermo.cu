@@ -299,6 +299,77 @@ void launch_thermo(const ThermoParams& P, double* lng, float* lngf, int precisio
 
 using namespace isg;
 
+extern "C" isg_status isg_specific_heat_peak(const int64_t* g, int32_t g_on_device, const isg_graph* graph, double h,
+                                             double T_lo, double T_hi, int32_t precision, void* stream,
+                                             double* T_peak, double* C_peak) {
+    try {
+        clear_error();
+        NvtxRange nvtx("isg_specific_heat_peak");
+        if (!g || !graph || !T_peak) fail(ISG_ERR_INVALID, "NULL argument");
+        if (!(T_lo > 0) || !(T_hi > T_lo) || !std::isfinite(T_hi) || !std::isfinite(h))
+            fail(ISG_ERR_INVALID, "need 0 < T_lo < T_hi, finite, and a finite field");
+        if (precision != ISG_FP64 && precision != ISG_FP32) fail(ISG_ERR_INVALID, "precision must be ISG_FP64 or ISG_FP32");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const int n_m = graph->n + 1, n_e = (int)(graph->S + 1);
+        const size_t gbytes = sizeof(int64_t) * (size_t)n_e * n_m;
+        constexpr int kGrid = 257;                   // odd: the bracket keeps a centre point
+        size_t off = 0;
+        auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) & ~(size_t)255; return o; };
+        const size_t o_lng = take(sizeof(double) * (size_t)n_e * n_m);
+        const size_t o_lngf = take(2 * sizeof(float) * (size_t)n_e * n_m);
+        const size_t o_g = g_on_device ? 0 : take(gbytes);
+        const size_t o_C = take(sizeof(double) * kGrid);
+        char* scratch = static_cast<char*>(scratch_alloc(off, s));
+        struct Free {
+            char* p; cudaStream_t s;
+            ~Free() { if (p) cudaFreeAsync(p, s); }
+        } guard{scratch, s};
+        std::unique_ptr<ThermoParams> P(new ThermoParams());
+        ThermoArgs& a = P->a;
+        a.n = graph->n; a.n_e = n_e; a.n_m = n_m; a.nT = kGrid; a.nh = 1; a.e_min = -graph->S;
+        a.T = nullptr;
+        a.h = nullptr;
+        if (g_on_device) a.g = g;
+        else {
+            ISG_CUDA(cudaMemcpyAsync(scratch + o_g, g, gbytes, cudaMemcpyHostToDevice, s));
+            a.g = reinterpret_cast<int64_t*>(scratch + o_g);
+        }
+        a.C = reinterpret_cast<double*>(scratch + o_C);
+        std::vector<double> C(kGrid);
+        double lo = T_lo, hi = T_hi, best_T = T_lo, best_C = -1;
+        // a uniform grid over the bracket, then the bracket shrinks to the two neighbours of the
+        // best grid point, until it is narrower than 1e-12 of the temperature
+        for (int round = 0; round < 12; ++round) {
+            for (int k = 0; k < kGrid; ++k) P->grid[k] = lo + (hi - lo) * k / (kGrid - 1);
+            P->grid[kGrid] = h;
+            launch_thermo(*P, reinterpret_cast<double*>(scratch + o_lng), reinterpret_cast<float*>(scratch + o_lngf),
+                          precision, s);
+            ISG_CUDA(cudaMemcpyAsync(C.data(), a.C, sizeof(double) * kGrid, cudaMemcpyDeviceToHost, s));
+            ISG_CUDA(cudaStreamSynchronize(s));
+            int kb = 0;
+            for (int k = 1; k < kGrid; ++k) if (C[k] > C[kb]) kb = k;
+            best_T = P->grid[kb];
+            best_C = C[kb];
+            const double step = (hi - lo) / (kGrid - 1);
+            lo = std::max(T_lo, best_T - step);
+            hi = std::min(T_hi, best_T + step);
+            if (hi - lo < 1e-12 * best_T) break;
+        }
+        *T_peak = best_T;
+        if (C_peak) *C_peak = best_C;
+        return ISG_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return ISG_ERR_NOMEM;
+    } catch (...) {
+        set_error("unexpected exception");
+        return ISG_ERR_INTERNAL;
+    }
+}
+
 extern "C" isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const isg_graph* graph, int32_t nT,
                                  const double* T, int32_t nh, const double* h, int32_t precision, void* stream,
                                  int32_t out_on_device, double* logZ, double* E, double* M, double* C, double* chi) {

@@ -54,6 +54,7 @@ _SIGS = {
     "isg_probe_peaks": (i32, [vp, vp, vp, vp, vp]),
     "isg_enumerate_noalloc": (i32, [vp, vp, vp, vp]),
     "isg_autotune": (i32, [vp, vp, vp, vp]),
+    "isg_specific_heat_peak": (i32, [vp, i32, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, i32, vp, vp, vp]),
     "isg_enumerate_batch": (i32, [i32, vp, vp, vp, i32, vp]),
     "isg_batch_create": (i32, [i32, vp, vp, ctypes.POINTER(vp)]),
     "isg_batch_run": (i32, [vp, vp]),
@@ -446,6 +447,23 @@ def prepare_thermo(g, graph: Graph, T, h, out, precision: int = ISG_FP64, stream
     args = (g.data_ptr(), 1, graph.ptr, len(T), T.ctypes.data, len(h), h.ctypes.data, precision,
             _stream_handle(stream), 1, *ptrs)
     return PreparedCall(lib().isg_thermo, args, (graph, g, T, h, out))
+
+
+def isg_specific_heat_peak(g, graph: Graph, h: float, T_lo: float, T_hi: float, precision: int = ISG_FP64,
+                           stream=None):
+    """(T, C) at the maximum of the specific heat C(T) at field h on [T_lo, T_hi]."""
+    if isinstance(g, np.ndarray):
+        g = np.ascontiguousarray(g, dtype=np.int64)
+        if g.shape != table_shape(graph):
+            raise ValueError(f"g must have shape {table_shape(graph)}")
+        ptr, dev = g.ctypes.data, 0
+    else:
+        _check_tensor(g, table_shape(graph), "int64")
+        ptr, dev = g.data_ptr(), 1
+    t, c = ctypes.c_double(), ctypes.c_double()
+    sh = _stream_handle(stream) if (stream is not None or dev) else None
+    _check(lib().isg_specific_heat_peak(ptr, dev, graph, h, T_lo, T_hi, precision, sh, ctypes.byref(t), ctypes.byref(c)))
+    return t.value, c.value
 
 
 def isg_debug_plan(graph: Graph, sms: int = 0, **options) -> dict:

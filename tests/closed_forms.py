@@ -109,3 +109,39 @@ def brute_force_g_range(n: int, edges, lo: int, hi: int):
         M = sum(sp)
         out[(E, M)] = out.get((E, M), 0) + 1
     return out
+
+
+def kaufman_C(m: int, n: int, T: float, J: float = 1.0) -> float:
+    """Specific heat of the m x n torus from Kaufman's ln Z by central differences:
+    C = T^2 d^2lnZ/dT^2 + 2 T dlnZ/dT (accurate to ~1e-7 relative)."""
+    d = 1e-4 * T
+    f0, fp, fm = kaufman_logz(m, n, T, J), kaufman_logz(m, n, T + d, J), kaufman_logz(m, n, T - d, J)
+    return T * T * (fp - 2 * f0 + fm) / (d * d) + 2 * T * (fp - fm) / (2 * d)
+
+
+def golden_max(f, lo: float, hi: float, tol: float = 1e-10) -> float:
+    """Argument of the maximum of a unimodal f on [lo, hi] by golden-section search."""
+    r = (math.sqrt(5) - 1) / 2
+    a, b = lo, hi
+    c, d = b - r * (b - a), a + r * (b - a)
+    fc, fd = f(c), f(d)
+    while b - a > tol * max(1.0, abs(a)):
+        if fc > fd:
+            b, d, fd = d, c, fc
+            c = b - r * (b - a)
+            fc = f(c)
+        else:
+            a, c, fc = c, d, fd
+            d = a + r * (b - a)
+            fd = f(d)
+    return 0.5 * (a + b)
+
+
+def kaufman_C_peak(m: int, n: int, near: float, step: float = 0.001) -> float:
+    """Peak of Kaufman's C(T) near `near`: vertex of the least-squares parabola through C at
+    near + k*step, k = -3..3 (the curvature there dwarfs the finite-difference noise of C, and
+    the fitted vertex is biased by the asymmetry of the peak only at order step^2, ~2e-6 here)."""
+    import numpy as np
+    ts = near + step * np.arange(-3, 4)
+    a, b, _ = np.polyfit(ts - near, [kaufman_C(m, n, t) for t in ts], 2)
+    return near - b / (2 * a)

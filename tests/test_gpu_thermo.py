@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_1110_2561_gb300 import workloads as w
-from closed_forms import kaufman_logz
+from closed_forms import golden_max, kaufman_C_peak, kaufman_logz
 
 pytestmark = pytest.mark.gpu
 
@@ -105,3 +105,31 @@ def test_thermo_rejects_bad_grid(isg, cuda):
         isg.isg_thermo(g, gh, [0.0], [0.0])
     with pytest.raises(isg.IsgError):
         isg.isg_thermo(g, gh, [1.0], [np.nan])
+
+
+def test_specific_heat_peak(isg, cuda):
+    """isg_specific_heat_peak on the 6x6 torus equals the oracle's peak (golden-section search on
+    its C(T)) and Kaufman's; on a triangular +-J lattice in a field too. In FP32 the location is
+    limited by the float error of C (~1e-6 relative) on a flat maximum: within 1e-4 relative."""
+    lat = w.square(6, 6, True)
+    g = oracle.g_frontier(lat.n, lat.edges, max_active=16)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    t_gpu, c_gpu = isg.isg_specific_heat_peak(g, gh, 0.0, 1.0, 4.0)
+    c_oracle = lambda t: oracle.thermo(lat.n, e_min, g, [t], [0.0])[3][0, 0]
+    t_or = golden_max(c_oracle, 1.5, 3.5, tol=1e-11)
+    assert abs(t_gpu - t_or) <= 1e-7 * t_or
+    assert abs(c_gpu - c_oracle(t_gpu)) <= 1e-12 * c_gpu
+    assert abs(t_gpu - kaufman_C_peak(6, 6, t_gpu)) <= 1e-5
+    t32, _ = isg.isg_specific_heat_peak(g, gh, 0.0, 1.0, 4.0, isg.ISG_FP32)
+    assert abs(t32 - t_or) <= 1e-4 * t_or
+    tri = w.with_random_couplings(w.triangular(3, 4, True), w.SplitMix64(6), (-1, 1))
+    gt = oracle.g_masks(tri.n, tri.edges)
+    ht = isg.isg_graph_create(tri.n, tri.edges)
+    et, _, _ = oracle.bins(tri.n, tri.edges)
+    t_gpu, _ = isg.isg_specific_heat_peak(gt, ht, 0.3, 0.2, 6.0)
+    c_or = lambda t: oracle.thermo(tri.n, et, gt, [t], [0.3])[3][0, 0]
+    grid = np.linspace(0.2, 6.0, 400)
+    t0 = grid[int(np.argmax([c_or(t) for t in grid]))]
+    t_or = golden_max(c_or, t0 - 0.03, t0 + 0.03, tol=1e-11)
+    assert abs(t_gpu - t_or) <= 1e-7 * t_or

@@ -11,7 +11,9 @@ import pytest
 
 import oracle
 from paper_1110_2561_gb300 import workloads as w
-from closed_forms import (brute_force_g, brute_force_g_range, free_spins, kaufman_logz, ring_joint_count, ring_logz)
+from closed_forms import (brute_force_g, brute_force_g_range, free_spins, golden_max, kaufman_C, kaufman_C_peak,
+                          kaufman_logz,
+                          ring_joint_count, ring_logz)
 
 
 def as_dict(g: np.ndarray, n: int, e_min: int):
@@ -251,3 +253,15 @@ def test_thermo_derivative_identities():
         assert M == pytest.approx(t * dh, rel=1e-6, abs=1e-6)
         assert C == pytest.approx((lzT[1][1, 0] - lzT[1][0, 0]) / (2 * d), rel=1e-5, abs=1e-6)
         assert chi == pytest.approx((lzh[2][0, 1] - lzh[2][0, 0]) / (2 * d), rel=1e-5, abs=1e-6)
+
+
+def test_specific_heat_peak_against_kaufman():
+    """The oracle's specific heat C(T) on the 6x6 torus (frontier table) peaks where Kaufman's
+    closed form does (C from second differences of ln Z), and its values agree there."""
+    lat = w.square(6, 6, True)
+    g = oracle.g_frontier(lat.n, lat.edges, max_active=16)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    c_oracle = lambda t: oracle.thermo(lat.n, e_min, g, [t], [0.0])[3][0, 0]
+    t_or = golden_max(c_oracle, 1.5, 3.5)
+    assert abs(t_or - kaufman_C_peak(6, 6, t_or)) <= 1e-5
+    assert abs(c_oracle(t_or) - kaufman_C(6, 6, t_or)) <= 1e-5 * c_oracle(t_or)
