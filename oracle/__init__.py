@@ -15,6 +15,7 @@ passage of Peretyatko et al. (arXiv:1110.2561) it follows:
 * ``g_frontier`` -- an exact dynamic programme over the site order (no 2^N loop), for pinning
                     large lattices.
 * ``thermo``     -- Z, <H>, <M>, C, chi from g by the definition of Eq. (2), fp64/long double.
+* ``magnetisation`` -- <|M|>, <M^2>, <M^4> and Binder's cumulant from g by the same weights.
 """
 from __future__ import annotations
 
@@ -58,8 +59,10 @@ def _bind(path: str):
     lib.oracle_g_frontier.argtypes = [ctypes.c_int, i64, i32p, i32p, i32p, ctypes.c_int, i64p]
     lib.oracle_thermo.argtypes = [ctypes.c_int, i64, i64, i64p, ctypes.c_int, f64p,
                                   ctypes.c_int, f64p, f64p, f64p, f64p, f64p, f64p]
+    lib.oracle_magnetisation.argtypes = [ctypes.c_int, i64, i64, i64p, ctypes.c_int, f64p,
+                                         ctypes.c_int, f64p, f64p, f64p, f64p, f64p]
     for f in (lib.oracle_bins, lib.oracle_g_edges, lib.oracle_g_masks,
-              lib.oracle_g_frontier, lib.oracle_thermo):
+              lib.oracle_g_frontier, lib.oracle_thermo, lib.oracle_magnetisation):
         f.restype = ctypes.c_int
     return lib
 
@@ -147,6 +150,19 @@ def thermo(n: int, e_min: int, g: np.ndarray, T, h, lib=None):
     _check(lib.oracle_thermo(n, e_min, g.shape[0], _ptr(g, ctypes.c_int64), len(T), _ptr(T, ctypes.c_double),
                              len(h), _ptr(h, ctypes.c_double), *[_ptr(o, ctypes.c_double) for o in outs]),
            "thermo")
+    return tuple(outs)
+
+
+def magnetisation(n: int, e_min: int, g: np.ndarray, T, h, lib=None):
+    """<|M|>, <M^2>, <M^4> and Binder's cumulant on the grid T x h (shape (len(T), len(h)))."""
+    lib = lib or _load()
+    g = np.ascontiguousarray(g, dtype=np.int64)
+    T = np.ascontiguousarray(np.atleast_1d(T), dtype=np.float64)
+    h = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
+    outs = [np.zeros((len(T), len(h)), dtype=np.float64) for _ in range(4)]
+    _check(lib.oracle_magnetisation(n, e_min, g.shape[0], _ptr(g, ctypes.c_int64), len(T),
+                                    _ptr(T, ctypes.c_double), len(h), _ptr(h, ctypes.c_double),
+                                    *[_ptr(o, ctypes.c_double) for o in outs]), "magnetisation")
     return tuple(outs)
 
 

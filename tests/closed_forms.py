@@ -145,3 +145,40 @@ def kaufman_C_peak(m: int, n: int, near: float, step: float = 0.001) -> float:
     ts = near + step * np.arange(-3, 4)
     a, b, _ = np.polyfit(ts - near, [kaufman_C(m, n, t) for t in ts], 2)
     return near - b / (2 * a)
+
+
+def free_spin_moments(n: int, T: float, h: float):
+    """(<|M|>, <M^2>, <M^4>) of n non-interacting spins in a field: each spin is +1 with
+    probability p = (1 + tanh(h/T)) / 2, so the number of up spins is binomial(n, p). <|M|> is
+    the binomial sum; the even moments come from the cumulants of one spin (mean t, variance
+    1 - t^2, third -2t(1 - t^2), fourth -2(1 - t^2)(1 - 3t^2)), which add over the n spins."""
+    t = math.tanh(h / T)
+    p = (1 + t) / 2
+    absm = math.fsum(math.comb(n, k) * p ** k * (1 - p) ** (n - k) * abs(2 * k - n) for k in range(n + 1))
+    k1, k2 = n * t, n * (1 - t * t)
+    k3, k4 = n * -2 * t * (1 - t * t), n * -2 * (1 - t * t) * (1 - 3 * t * t)
+    m2 = k2 + k1 * k1
+    m4 = k4 + 4 * k3 * k1 + 3 * k2 * k2 + 6 * k2 * k1 * k1 + k1 ** 4
+    return absm, m2, m4
+
+
+def ring_M2(n: int, T: float, J: float = 1.0) -> float:
+    """<M^2> of the periodic chain at h = 0: n times the sum over distances r of the correlation
+    <s_0 s_r> = (t^r + t^(n-r)) / (1 + t^n), t = tanh(J/T) (the 2 x 2 transfer matrix)."""
+    t = math.tanh(J / T)
+    return n * math.fsum((t ** r + t ** (n - r)) / (1 + t ** n) for r in range(n))
+
+
+def brute_force_magnetisation(n: int, edges, T: float, h: float):
+    """(<|M|>, <M^2>, <M^4>) by summing over every configuration with its Boltzmann weight
+    exp(-(E - h M)/T), E = -sum J s_i s_j (no table in between)."""
+    terms = []
+    for s in range(1 << n):
+        sp = [1 if (s >> i) & 1 else -1 for i in range(n)]
+        E = -sum(J * sp[i] * sp[j] for i, j, J in edges)
+        M = sum(sp)
+        terms.append((-(E - h * M) / T, M))
+    lmax = max(l for l, _ in terms)
+    w = [(math.exp(l - lmax), M) for l, M in terms]
+    Z = math.fsum(x for x, _ in w)
+    return tuple(math.fsum(x * f(M) for x, M in w) / Z for f in (abs, lambda M: M * M, lambda M: M ** 4))

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 from paper_1110_2561_gb300 import workloads as w
-from closed_forms import brute_force_g_range, free_spins, kaufman_logz, ring_logz
+from closed_forms import brute_force_g_range, free_spin_moments, free_spins, kaufman_logz, ring_logz
 
 # (name, original text, planted mistake); each original must occur exactly once.
 MUTANTS = [
@@ -33,6 +33,13 @@ MUTANTS = [
      "long double w = expl(0.0L * logl((long double)c) - H / t - Lmax);\n                    Z += w;"),
     ("thermo: variance not centred", "vH += w * (H - mH) * (H - mH);", "vH += w * H * H;"),
     ("thermo: energy mean uses M", "Z += w; sH += w * H; sM += w * M;", "Z += w; sH += w * E; sM += w * M;"),
+    ("magnetisation: |M| dropped", "sA += w * fabsl(M);", "sA += w * M;"),
+    ("magnetisation: cube for fourth", "s4 += w * M * M * M * M;", "s4 += w * M * M * M * fabsl(M) / (fabsl(M) + 1);"),
+    # (a flipped field sign is an equivalent mutant here: every full table is symmetric in M, so
+    # |M| and the even moments are even in h)
+    ("magnetisation: field not over T", "long double w = expl(logl((long double)c) - (E - f * M) / t - Lmax);",
+     "long double w = expl(logl((long double)c) - E / t + f * M - Lmax);"),
+    ("magnetisation: Binder factor", "1.0L - m4 / (3.0L * m2 * m2)", "1.0L - m4 / (2.0L * m2 * m2)"),
 ]
 
 
@@ -86,6 +93,11 @@ def pins_pass(lib, table1_triples) -> bool:
             l0, m0, x0 = free_spins(n, t, f)
             if not (np.isclose(lz, l0, rtol=1e-12) and np.isclose(M, m0, rtol=1e-12) and np.isclose(chi, x0, rtol=1e-12)
                     and np.isclose(E, -f * m0, rtol=1e-12) and np.isclose(C, f * f * x0 / t, rtol=1e-12)):
+                return False
+            a, m2, m4, u = (x[0, 0] for x in oracle.magnetisation(n, 0, g0, [t], [f], lib=lib))
+            a0, m20, m40 = free_spin_moments(n, t, f)
+            if not (np.isclose(a, a0, rtol=1e-12) and np.isclose(m2, m20, rtol=1e-12) and np.isclose(m4, m40, rtol=1e-12)
+                    and np.isclose(u, 1 - m40 / (3 * m20 * m20), rtol=1e-12)):
                 return False
     except ValueError:
         return False

@@ -11,9 +11,9 @@ import pytest
 
 import oracle
 from paper_1110_2561_gb300 import workloads as w
-from closed_forms import (brute_force_g, brute_force_g_range, free_spins, golden_max, kaufman_C, kaufman_C_peak,
-                          kaufman_logz,
-                          ring_joint_count, ring_logz)
+from closed_forms import (brute_force_g, brute_force_g_range, brute_force_magnetisation, free_spin_moments,
+                          free_spins, golden_max, kaufman_C, kaufman_C_peak, kaufman_logz, ring_joint_count,
+                          ring_logz, ring_M2)
 
 
 def as_dict(g: np.ndarray, n: int, e_min: int):
@@ -265,3 +265,63 @@ def test_specific_heat_peak_against_kaufman():
     t_or = golden_max(c_oracle, 1.5, 3.5)
     assert abs(t_or - kaufman_C_peak(6, 6, t_or)) <= 1e-5
     assert abs(c_oracle(t_or) - kaufman_C(6, 6, t_or)) <= 1e-5 * c_oracle(t_or)
+
+
+# --------------------------------------------------------------------------- magnetisation
+def test_magnetisation_free_spins():
+    """No bonds: the number of up spins is binomial(N, (1 + tanh(h/T))/2); <|M|> from the
+    binomial sum, <M^2> and <M^4> from the cumulants of one spin."""
+    n = 9
+    g = oracle.g_edges(n, np.zeros((0, 3), dtype=np.int64))
+    T = np.array([0.3, 1.0, 4.0])
+    h = np.array([-1.2, 0.0, 0.35])
+    a, m2, m4, u = oracle.magnetisation(n, 0, g, T, h)
+    for i, t in enumerate(T):
+        for j, f in enumerate(h):
+            a0, m20, m40 = free_spin_moments(n, t, f)
+            assert a[i, j] == pytest.approx(a0, rel=1e-13)
+            assert m2[i, j] == pytest.approx(m20, rel=1e-13)
+            assert m4[i, j] == pytest.approx(m40, rel=1e-12)
+            assert u[i, j] == pytest.approx(1 - m40 / (3 * m20 * m20), rel=1e-12, abs=1e-14)
+
+
+@pytest.mark.parametrize("n", [4, 9, 14])
+def test_magnetisation_ring(n):
+    """Periodic chain at h = 0: <M^2> = n sum_r (t^r + t^(n-r)) / (1 + t^n), t = tanh(1/T)."""
+    lat = w.ring(n)
+    g = oracle.g_edges(lat.n, lat.edges)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    T = np.array([0.4, 1.1, 2.5, 6.0])
+    m2 = oracle.magnetisation(lat.n, e_min, g, T, [0.0])[1][:, 0]
+    for t, v in zip(T, m2):
+        assert v == pytest.approx(ring_M2(n, t), rel=1e-13)
+
+
+@pytest.mark.parametrize("seed", [3, 8])
+def test_magnetisation_brute_force(seed):
+    """Random couplings in {-2, -1, 1, 2} on 11 spins: every moment against a direct sum over the
+    2^11 configurations with their Boltzmann weights (no table in between), in a field too."""
+    lat = w.random_graph(11, 20, w.SplitMix64(seed))
+    edges = [tuple(int(x) for x in r) for r in lat.edges]
+    g = oracle.g_edges(lat.n, lat.edges)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    for t, f in [(0.7, 0.0), (1.9, -0.4), (3.3, 1.1)]:
+        a, m2, m4, u = (x[0, 0] for x in oracle.magnetisation(lat.n, e_min, g, [t], [f]))
+        a0, m20, m40 = brute_force_magnetisation(lat.n, edges, t, f)
+        assert (a, m2, m4) == pytest.approx((a0, m20, m40), rel=1e-12)
+        assert u == pytest.approx(1 - m40 / (3 * m20 * m20), rel=1e-12)
+
+
+def test_magnetisation_limits_and_chi():
+    """4x4 ferromagnet: ordered at low T (<|M|> -> N, Binder cumulant -> 2/3), free at high T
+    (cumulant -> 2/(3N)); at any (T, h), <M^2> - <M>^2 = T chi from the thermodynamics."""
+    lat = w.square(4, 4, True)
+    g = oracle.g_edges(lat.n, lat.edges)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    a, m2, m4, u = oracle.magnetisation(lat.n, e_min, g, [0.05, 1e7], [0.0])
+    assert a[0, 0] == pytest.approx(16, rel=1e-12) and u[0, 0] == pytest.approx(2 / 3, rel=1e-12)
+    assert u[1, 0] == pytest.approx(2 / (3 * 16), rel=1e-5)
+    T, h = [0.9, 2.27, 4.0], [-0.5, 0.0, 0.3]
+    _, _, M, _, chi = oracle.thermo(lat.n, e_min, g, T, h)
+    m2 = oracle.magnetisation(lat.n, e_min, g, T, h)[1]
+    assert np.allclose(m2 - M * M, np.array(T)[:, None] * chi, rtol=1e-11, atol=1e-11)
