@@ -43,8 +43,8 @@ SM_MAX_MHZ_FALLBACK = 2070.0
 OPS_PER_CONFIG = 2
 # DRAM traffic of one enumeration launch on this workload from the committed ncu capture
 # (profiles/enumerate_kernel_torus6x6.md), valid only for the kernel sources it was taken on.
-TRAFFIC_BYTES = 34816          # dram__bytes_read.sum + dram__bytes_write.sum of one launch (program + flush)
-TRAFFIC_SOURCES_SHA = "c7bad2eada67e7ad"
+TRAFFIC_BYTES = 32768          # dram__bytes_read.sum + dram__bytes_write.sum of one launch (program reads; table stays in L2)
+TRAFFIC_SOURCES_SHA = "1ebd481d381434c6"
 
 
 def kernel_sources_sha() -> str:
@@ -375,6 +375,22 @@ def extra_measurements(stream, dev):
     t0 = time.perf_counter()
     tc, cmax = isg.isg_specific_heat_peak(g, gh, 0.0, 1.0, 4.0, isg.ISG_FP64, stream)
     out["torus6x6_specific_heat_peak"] = {"T_peak": tc, "C_peak": cmax, "ms": (time.perf_counter() - t0) * 1e3}
+    # derived physics: Binder-cumulant crossing of the 4x4 and 6x6 tori (h = 0, 2001 T in [1.5, 3.5])
+    Tb = np.linspace(1.5, 3.5, 2001)
+    ub = []
+    for L in (4, 6):
+        lb = workloads.square(L, L, True)
+        hb = isg.isg_graph_create(lb.n, lb.edges)
+        gb = torch.zeros(isg.table_shape(hb), dtype=torch.int64, device=dev)
+        isg.isg_enumerate(hb, gb, stream, autotune=1)
+        ob = tuple(torch.empty((len(Tb), 1), dtype=torch.float64, device=dev) for _ in range(4))
+        mag_ms = _event_ms(lambda: isg.isg_magnetisation(gb, hb, Tb, [0.0], isg.ISG_FP64, stream, out=ob), stream, 5)
+        ub.append(ob[3][:, 0].cpu().numpy())
+    dub = ub[1] - ub[0]
+    k = int(np.nonzero(np.diff(np.sign(dub)))[0][0])
+    t_cross = Tb[k] + (Tb[k + 1] - Tb[k]) * dub[k] / (dub[k] - dub[k + 1])
+    out["torus_binder_crossing_4x4_6x6"] = {"T_cross": float(t_cross), "U4_at_cross": float(ub[0][k]),
+                                            "isg_magnetisation_ms_2001T": mag_ms}
     # cubic 3x3x4 torus: thermodynamics on 512 T x 256 h, FP32 vs FP64
     lat = workloads.cubic(3, 3, 4, True)
     gh = isg.isg_graph_create(lat.n, lat.edges)
@@ -392,9 +408,18 @@ def extra_measurements(stream, dev):
         d = (r32[k] - r64[k]).abs()
         err[nm] = {"max_abs": float(d.max()), "max_rel": float((d / r64[k].abs().clamp_min(1e-300)).max()),
                    "max_rel_of_grid_max": float(d.max() / r64[k].abs().max())}
+    m64 = tuple(torch.empty((512, 256), dtype=torch.float64, device=dev) for _ in range(4))
+    m32 = tuple(torch.empty((512, 256), dtype=torch.float64, device=dev) for _ in range(4))
+    tm64 = _event_ms(lambda: isg.isg_magnetisation(g, gh, T, h, isg.ISG_FP64, stream, out=m64), stream, 5)
+    tm32 = _event_ms(lambda: isg.isg_magnetisation(g, gh, T, h, isg.ISG_FP32, stream, out=m32), stream, 5)
+    for k, nm in enumerate(("absM", "M2", "M4", "binder")):
+        d = (m32[k] - m64[k]).abs()
+        err[nm] = {"max_abs": float(d.max()), "max_rel": float((d / m64[k].abs().clamp_min(1e-300)).max()),
+                   "max_rel_of_grid_max": float(d.max() / m64[k].abs().max())}
     out["cubic3x3x4_thermo"] = {"enumerate_ms": enum_ms, "enumerate_configs_per_s": (1 << 36) / (enum_ms * 1e-3),
                                 "grid": "512 T in [0.5,8] x 256 h in [-2,2]", "fp64_ms": t64, "fp32_ms": t32,
-                                "fp32_speedup": t64 / t32, "fp32_vs_fp64": err}
+                                "fp32_speedup": t64 / t32, "magnetisation_fp64_ms": tm64,
+                                "magnetisation_fp32_ms": tm32, "fp32_vs_fp64": err}
     return out
 
 

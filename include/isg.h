@@ -228,6 +228,20 @@ ISG_API isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const isg_g
                       int32_t out_on_device, double* logZ, double* E, double* M, double* C, double* chi);
 
 /*
+ * Magnetisation statistics on the grid T[0..nT) x h[0..nh) from a table g of this graph's
+ * geometry: the finite-system magnetisation curves that exact counting offers for comparison
+ * with measured magnetisation, and Binder's cumulant, whose crossing between sizes locates the
+ * ordering temperature of finite systems (Sec. 1, Sec. 5). With the weights of Eq. (2), per
+ * point (a, b) at index a * nh + b: abs_M = <|M|>, M2 = <M^2>, M4 = <M^4>,
+ * binder = 1 - <M^4> / (3 <M^2>^2) (0 when <M^2> = 0). At h = 0 the mean magnetisation <M> of a
+ * finite system is exactly 0, so <|M|> and sqrt(<M^2>) are its magnetisation curves. Any output
+ * may be NULL. Arguments, precision, placement, synchronisation and errors as for isg_thermo.
+ */
+ISG_API isg_status isg_magnetisation(const int64_t* g, int32_t g_on_device, const isg_graph* graph, int32_t nT,
+                                     const double* T, int32_t nh, const double* h, int32_t precision, void* stream,
+                                     int32_t out_on_device, double* abs_M, double* M2, double* M4, double* binder);
+
+/*
  * Temperature of the specific-heat maximum at field h within [T_lo, T_hi] (the finite-system
  * transition temperature that motivates exact counting, Sec. 1): C(T) = Var(H)/T^2 from Eq. (2)
  * over the table g is evaluated by the thermodynamics kernels on a uniform grid of 257

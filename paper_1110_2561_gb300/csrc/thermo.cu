@@ -3,12 +3,19 @@
 //
 // Z(T, h) = sum_{E,M} g(E, M) exp(-(E - h M) / T) factors exactly over M:
 //   Z = sum_M exp(h M / T) A_T(M),   A_T(M) = sum_E g(E, M) exp(-E / T).
-// Stage 1 (per T and M, the expensive part, independent of h) keeps, log-shifted by the largest
-// term, L_T(M) = ln A_T(M) and the conditional mean and variance of E at fixed M. Stage 2 (per
-// T and h) combines them over the N + 1 values of M with a log-sum-exp:
+// Stage 1 (per T and M, independent of h) keeps, log-shifted by the largest term,
+// L_T(M) = ln A_T(M) and the conditional mean and variance of E at fixed M. Stage 2 (per T and
+// h) combines them over the N + 1 values of M with a log-sum-exp, in one pass:
 //   <H> = sum_M p(M) (mu_E(M) - h M),  Var(H) = sum_M p(M) [var_E(M) + (mu_E(M) - h M - <H>)^2],
-// with p(M) proportional to exp(L_T(M) + h M / T). Var(H) is a sum of non-negative terms, so no
-// cancellation enters C = Var(H)/T^2 or chi = Var(M)/T.
+// with p(M) proportional to exp(L_T(M) + h M / T). The squares are taken about the dominant
+// column M* (the mode of p) and the mean correction subtracted at the end; the mean lies within a
+// few standard deviations of the mode, so C = Var(H)/T^2 and chi = Var(M)/T lose at most a small
+// factor to cancellation.
+//
+// The magnetisation statistics <|M|>, <M^2>, <M^4> and Binder's cumulant 1 - <M^4>/(3<M^2>^2)
+// depend on (T, h) only through p(M), so they come from the same stage-2 weights. Passes whose
+// outputs were not requested are skipped (the E-variance pass of stage 1 when C is not asked for,
+// the variance pass of stage 2 when neither C nor chi is).
 //
 // FP64: everything in double. FP32: the counts are converted to ln g in double once and rounded
 // to float; every exponential and every sum runs in float, relative to the column maximum in
@@ -28,6 +35,7 @@
 namespace isg {
 
 constexpr int kInlineGrid = 1024;   // T and h values passed inside the kernel parameters
+constexpr int kThermoOuts = 9;      // logZ, E, M, C, chi, absM, M2, M4, binder
 
 struct ThermoArgs {
     const int64_t* g;   // n_e x n_m counts
@@ -38,6 +46,10 @@ struct ThermoArgs {
     double* M;
     double* C;
     double* chi;
+    double* absM;       // <|M|>
+    double* M2;         // <M^2>
+    double* M4;         // <M^4>
+    double* binder;     // 1 - <M^4> / (3 <M^2>^2)
     int n, n_e, n_m, nT, nh;
     int64_t e_min;
 };
@@ -56,10 +68,20 @@ template <class F> __device__ __forceinline__ F lg(F x);
 template <> __device__ __forceinline__ double lg<double>(double x) { return log(x); }
 template <> __device__ __forceinline__ float lg<float>(float x) { return logf(x); }
 
+// Fused multiply-add, absolute value and maximum in the working precision. The float versions
+// are named explicitly so that no argument is promoted to double (double arithmetic runs on
+// this GPU's narrow FP64 pipe).
+__device__ __forceinline__ float fmaF(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmaF(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float absF(float x) { return fabsf(x); }
+__device__ __forceinline__ double absF(double x) { return fabs(x); }
+__device__ __forceinline__ float maxF(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double maxF(double a, double b) { return fmax(a, b); }
+
 template <class F>
 __device__ __forceinline__ F warp_max(F v) {
 #pragma unroll
-    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o; o >>= 1) v = maxF(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 template <class F>
@@ -85,7 +107,8 @@ template <class F> __device__ __forceinline__ const F* pick(const double* d, con
 template <> __device__ __forceinline__ const double* pick<double>(const double* d, const float*) { return d; }
 template <> __device__ __forceinline__ const float* pick<float>(const double*, const float* f) { return f; }
 
-// One CTA per temperature. Shared memory: L[n_m] (double), mu, var, Lr, Llo [n_m] (F).
+// One CTA per temperature. Shared memory: L[n_m] (double), mu, var, Lr, Llo, cs0, qin [n_m]
+// (F), ces[n_m] (int).
 //
 // Stage 2 forms every exponent relative to the dominant column m* of its (T, h) point:
 //   d_m = (Lr[m] - Lr[m*]) + (Llo[m] - Llo[m*]) + (h/T)(M_m - M_m*),
@@ -106,27 +129,37 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
     F* var = mu + a.n_m;
     F* Lr = var + a.n_m;                 // L - max L, rounded to F (-inf: empty column)
     F* Llo = Lr + a.n_m;                 // the rounding remainder of Lr
+    F* cs0 = Llo + a.n_m;                // per column: sum of weights relative to the largest
+    // FP64, one thread per point: qin[m] = exp(Lr[m] - Lr[m-1]), the h-independent factor between
+    // neighbouring columns' weights (0 for m = 0 or an empty neighbour)
+    F* qin = cs0 + a.n_m;
+    int* ces = reinterpret_cast<int*>(qin + a.n_m);   // per column: the largest bin e* (-1: empty)
     __shared__ double s_Lmax;
     const int it = blockIdx.x;
     const double T = Tv[it], invTd = 1.0 / T;
-    const F invT = (F)invTd, invTlo = (F)(invTd - (double)invT);
+    const F invT = (F)invTd, invTlo = (F)(invTd - (double)invT), invT2 = (F)(invTd * invTd);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
 
     // Stage 1: per column M (one warp each).
+    // Energies E_e = e_min + 2e are exact in F (|E| < 2^24); the loops step them by 64 (32 lanes
+    // x 2) in F instead of converting e, since integer-to-float conversions share the slow FP64
+    // pipe on this GPU.
+    const F Elane = (F)(a.e_min + 2 * lane);
     for (int m = warp; m < a.n_m; m += nw) {
         F xmax = (F)-INFINITY;
         int earg = 0;
-        for (int e = lane; e < a.n_e; e += 32) {
+        F En = Elane;
+        for (int e = lane; e < a.n_e; e += 32, En += (F)64) {
             const F l = lng[(size_t)e * a.n_m + m];
             if (l == (F)-INFINITY) continue;
-            const F x = l - (F)(a.e_min + 2 * e) * invT;
+            const F x = l - En * invT;
             if (x > xmax) { xmax = x; earg = e; }
         }
         const F wmax = warp_max(xmax);
         // a lane holding the maximum names the reference energy (any tie is fine)
         const unsigned hit = __ballot_sync(0xffffffffu, xmax == wmax && wmax != (F)-INFINITY);
         if (!hit) {
-            if (lane == 0) { L[m] = -INFINITY; mu[m] = 0; var[m] = 0; }
+            if (lane == 0) { ces[m] = -1; mu[m] = 0; var[m] = 0; }
             continue;
         }
         // exponents relative to the maximising bin e*: (ln g_e - ln g_e*) - (E_e - E_e*) / T, the
@@ -135,10 +168,10 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
         const size_t is = (size_t)es * a.n_m + m;
         const F ls = lng[is], lls = pair ? (F)lnglo[is] : (F)0;
         const F Eref = (F)(a.e_min + 2 * es);
-        auto arg = [&](int e, F l) {
-            const F dE = (F)(2 * (e - es));
+        auto arg = [&](int e, F l, F En) {
+            const F dE = En - Eref;
             const F dl = (l - ls) + (pair ? (F)lnglo[(size_t)e * a.n_m + m] - lls : (F)0);
-            return dl - fma(dE, invT, dE * invTlo);
+            return dl - fmaF(dE, invT, dE * invTlo);
         };
         // weights of the first kCache bins of each lane stay in registers for the second pass
         constexpr int kCache = 8;
@@ -151,48 +184,64 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
             if (e >= a.n_e) continue;
             const F l = lng[(size_t)e * a.n_m + m];
             if (l == (F)-INFINITY) continue;
-            const F w = ex<F>(arg(e, l));
+            const F En = Elane + (F)(64 * j);
+            const F w = ex<F>(arg(e, l, En));
             wc[j] = w;
             s0 += w;
-            s1 += w * ((F)(a.e_min + 2 * e) - Eref);
-        }
-        for (int e = lane + 32 * kCache; e < a.n_e; e += 32) {
-            const F l = lng[(size_t)e * a.n_m + m];
-            if (l == (F)-INFINITY) continue;
-            const F En = (F)(a.e_min + 2 * e);
-            const F w = ex<F>(arg(e, l));
-            s0 += w;
             s1 += w * (En - Eref);
+        }
+        {
+            F En = Elane + (F)(64 * kCache);
+            for (int e = lane + 32 * kCache; e < a.n_e; e += 32, En += (F)64) {
+                const F l = lng[(size_t)e * a.n_m + m];
+                if (l == (F)-INFINITY) continue;
+                const F w = ex<F>(arg(e, l, En));
+                s0 += w;
+                s1 += w * (En - Eref);
+            }
         }
         s0 = warp_sum(s0);
         s1 = warp_sum(s1);
         const F m1 = Eref + s1 / s0;
         F s2 = 0;
+        if (a.C) {
 #pragma unroll
-        for (int j = 0; j < kCache; ++j) {
-            const F d = (F)(a.e_min + 2 * (lane + 32 * j)) - m1;
-            s2 += wc[j] * d * d;
+            for (int j = 0; j < kCache; ++j) {
+                const F d = Elane + (F)(64 * j) - m1;
+                s2 += wc[j] * d * d;
+            }
+            F En = Elane + (F)(64 * kCache);
+            for (int e = lane + 32 * kCache; e < a.n_e; e += 32, En += (F)64) {
+                const F l = lng[(size_t)e * a.n_m + m];
+                if (l == (F)-INFINITY) continue;
+                const F w = ex<F>(arg(e, l, En));
+                const F d = En - m1;
+                s2 += w * d * d;
+            }
+            s2 = warp_sum(s2);
         }
-        for (int e = lane + 32 * kCache; e < a.n_e; e += 32) {
-            const F l = lng[(size_t)e * a.n_m + m];
-            if (l == (F)-INFINITY) continue;
-            const F En = (F)(a.e_min + 2 * e);
-            const F w = ex<F>(arg(e, l));
-            const F d = En - m1;
-            s2 += w * d * d;
-        }
-        s2 = warp_sum(s2);
         if (lane == 0) {
-            L[m] = (lngd[is] - (double)(a.e_min + 2 * es) * invTd) + log((double)s0);
+            cs0[m] = s0;
+            ces[m] = es;
             mu[m] = m1;
             var[m] = s2 / s0;
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    // L_T(M) in double, the columns side by side (double arithmetic occupies the narrow FP64 pipe
+    // for a whole warp even with one lane active); ln of the relative sum s0 in [1, n_e] is taken
+    // in the working precision.
+    for (int m = threadIdx.x; m < a.n_m; m += blockDim.x) {
+        const int es = ces[m];
+        L[m] = es < 0 ? -INFINITY
+                      : (lngd[(size_t)es * a.n_m + m] - (double)(a.e_min + 2 * es) * invTd) + (double)lg<F>(cs0[m]);
+    }
+    __syncthreads();
+    if (warp == 0) {
         double mx = -INFINITY;
-        for (int m = 0; m < a.n_m; ++m) mx = fmax(mx, L[m]);
-        s_Lmax = mx;
+        for (int m = lane; m < a.n_m; m += 32) mx = fmax(mx, L[m]);
+        mx = warp_max(mx);
+        if (lane == 0) s_Lmax = mx;
     }
     __syncthreads();
     const double Lmax = s_Lmax;
@@ -202,63 +251,101 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
         Lr[m] = (F)r;
         Llo[m] = (F)(r - (double)(F)r);
     }
+    const bool by_warp = a.nh < 64;
+    constexpr bool kChain = sizeof(F) == sizeof(double);
+    if (kChain && !by_warp) {
+        __syncthreads();
+        for (int m = threadIdx.x; m < a.n_m; m += blockDim.x)
+            qin[m] = (m == 0 || L[m] == -INFINITY || L[m - 1] == -INFINITY) ? (F)0 : ex<F>(Lr[m] - Lr[m - 1]);
+    }
     __syncthreads();
 
     // Stage 2. Many field values: one thread per point, a serial loop over M. Few field values
     // (fewer than 64): one warp per point, lanes over M, shuffle reductions.
-    const bool by_warp = a.nh < 64;
+    const bool mag = a.absM || a.M2 || a.M4 || a.binder, variances = a.C || a.chi;
     const int step = by_warp ? nw : blockDim.x, first = by_warp ? warp : threadIdx.x;
     const int mstep = by_warp ? 32 : 1, mfirst = by_warp ? lane : 0;
+    // M_m - M_m* stepped in F as well: 2 * mstep per iteration.
+    const F dstep = (F)(2 * mstep);
     for (int ih = first; ih < a.nh; ih += step) {
         const double hd = hv[ih], hTd = hd * invTd;
         const F hT = (F)hTd, hTlo = (F)(hTd - (double)hT), hF = (F)hd;
         F amax = (F)-INFINITY;
         int ms = 0;
-        for (int m = mfirst; m < a.n_m; m += mstep) {
-            if (Lr[m] == (F)-INFINITY) continue;
-            const F am = Lr[m] + hT * (F)(2 * m - a.n);
-            if (am > amax) { amax = am; ms = m; }
+        {
+            F Mm = (F)(2 * mfirst - a.n);
+            for (int m = mfirst; m < a.n_m; m += mstep, Mm += dstep) {
+                if (Lr[m] == (F)-INFINITY) continue;
+                const F am = Lr[m] + hT * Mm;
+                if (am > amax) { amax = am; ms = m; }
+            }
         }
         if (by_warp) {                        // the lowest lane holding the warp maximum names m*
             const F wm = warp_max(amax);
             const unsigned hit = __ballot_sync(0xffffffffu, amax == wm && wm != (F)-INFINITY);
             ms = __shfl_sync(0xffffffffu, ms, hit ? __ffs(hit) - 1 : 0);
         }
-        const F Ls = Lr[ms], Lls = Llo[ms];
+        // One pass: weights p_m and the moments of dM = M_m - M_m* and dH = H_m - H_m* about the
+        // dominant column. m* is the mode of p, so the mean lies within a few standard deviations
+        // of it and Var = <d^2> - <d>^2 loses at most a small factor to cancellation.
+        const F Ls = Lr[ms], Lls = Llo[ms], mus = mu[ms];
         const int Ms = 2 * ms - a.n;
-        F z = 0, zM = 0, zH = 0;
-        for (int m = mfirst; m < a.n_m; m += mstep) {
-            if (Lr[m] == (F)-INFINITY) continue;
-            const F Mm = (F)(2 * m - a.n), dMs = (F)(2 * m - a.n - Ms);
-            const F p = ex<F>((Lr[m] - Ls) + (Llo[m] - Lls) + fma(hT, dMs, hTlo * dMs));
+        const F MsF = (F)Ms;
+        F z = 0, sM = 0, sH = 0, sMM = 0, sHH = 0, zA = 0, z2 = 0, z4 = 0;
+        F dM = (F)(2 * mfirst - a.n - Ms);
+        // FP64 chain: p_m = p_(m-1) qin[m] exp(2 h/T), one multiply instead of an exponential,
+        // while the previous weight is above 1e-290 and the factor is finite (<= 1e290); else, and
+        // for FP32, the exponential. <= 64 steps of a few ulp each keep p within ~1e-13.
+        const F R = (kChain && !by_warp) ? ex<F>((F)2 * hT) : (F)0;
+        F pprev = 0;
+        for (int m = mfirst; m < a.n_m; m += mstep, dM += dstep) {
+            if (Lr[m] == (F)-INFINITY) { pprev = 0; continue; }
+            F p;
+            if constexpr (kChain) {
+                const F f = by_warp ? (F)0 : qin[m] * R;
+                p = (!by_warp && pprev >= (F)1e-290 && f <= (F)1e290) ? pprev * f
+                                                                      : ex<F>((Lr[m] - Ls) + hT * dM);
+            } else {
+                p = ex<F>((Lr[m] - Ls) + (Llo[m] - Lls) + fmaF(hT, dM, hTlo * dM));
+            }
+            pprev = p;
+            const F dH = (mu[m] - mus) - hF * dM;
+            const F pM = p * dM, pH = p * dH;
             z += p;
-            zM += p * Mm;
-            zH += p * (mu[m] - hF * Mm);
-        }
-        if (by_warp) { z = warp_sum(z); zM = warp_sum(zM); zH = warp_sum(zH); }
-        const F mM = zM / z, mH = zH / z;
-        F vH = 0, vM = 0;
-        for (int m = mfirst; m < a.n_m; m += mstep) {
-            if (Lr[m] == (F)-INFINITY) continue;
-            const F Mm = (F)(2 * m - a.n), dMs = (F)(2 * m - a.n - Ms);
-            const F p = ex<F>((Lr[m] - Ls) + (Llo[m] - Lls) + fma(hT, dMs, hTlo * dMs));
-            const F dH = mu[m] - hF * Mm - mH, dM = Mm - mM;
-            vH += p * (var[m] + dH * dH);
-            vM += p * dM * dM;
+            sM += pM;
+            sH += pH;
+            if (variances) {
+                sMM += pM * dM;
+                sHH += fmaF(p, var[m], pH * dH);
+            }
+            if (mag) {
+                const F Mm = MsF + dM, M2 = Mm * Mm;
+                zA += p * absF(Mm);
+                z2 += p * M2;
+                z4 += p * M2 * M2;
+            }
         }
         if (by_warp) {
-            vH = warp_sum(vH);
-            vM = warp_sum(vM);
+            z = warp_sum(z); sM = warp_sum(sM); sH = warp_sum(sH);
+            if (variances) { sMM = warp_sum(sMM); sHH = warp_sum(sHH); }
+            if (mag) { zA = warp_sum(zA); z2 = warp_sum(z2); z4 = warp_sum(z4); }
             if (lane != 0) continue;
         }
-        vH /= z;
-        vM /= z;
+        const F iz = (F)1 / z;
+        const F dm = sM * iz, dh = sH * iz;
         const size_t o = (size_t)it * a.nh + ih;
         if (a.logZ) a.logZ[o] = L[ms] + hTd * (double)Ms + (double)lg<F>(z);
-        if (a.E) a.E[o] = (double)mH;
-        if (a.M) a.M[o] = (double)mM;
-        if (a.C) a.C[o] = (double)vH * (invTd * invTd);
-        if (a.chi) a.chi[o] = (double)vM * invTd;
+        if (a.E) a.E[o] = (double)((mus - hF * MsF) + dh);
+        if (a.M) a.M[o] = (double)(MsF + dm);
+        if (a.C) a.C[o] = (double)((sHH * iz - dh * dh) * invT2);
+        if (a.chi) a.chi[o] = (double)((sMM * iz - dm * dm) * invT);
+        if (mag) {
+            const F m2 = z2 * iz, m4 = z4 * iz;
+            if (a.absM) a.absM[o] = (double)(zA * iz);
+            if (a.M2) a.M2[o] = (double)m2;
+            if (a.M4) a.M4[o] = (double)m4;
+            if (a.binder) a.binder[o] = m2 > (F)0 ? (double)((F)1 - m4 / ((F)3 * m2 * m2)) : 0.0;
+        }
     }
 }
 
@@ -286,10 +373,10 @@ void launch_thermo(const ThermoParams& P, double* lng, float* lngf, int precisio
     ISG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int threads = a.nT < sms ? 32 * std::min(32, std::max(8, a.n_m)) : 256;
     if (precision == ISG_FP64) {
-        const size_t smem = (size_t)a.n_m * (8 + 4 * sizeof(double));
+        const size_t smem = (size_t)a.n_m * (8 + 6 * sizeof(double) + 4);
         thermo_kernel<double><<<a.nT, threads, smem, s>>>(P, lng, lngf, lnglo);
     } else {
-        const size_t smem = (size_t)a.n_m * (8 + 4 * sizeof(float));
+        const size_t smem = (size_t)a.n_m * (8 + 6 * sizeof(float) + 4);
         thermo_kernel<float><<<a.nT, threads, smem, s>>>(P, lng, lngf, lnglo);
     }
     ISG_CUDA(cudaGetLastError());
@@ -370,81 +457,111 @@ extern "C" isg_status isg_specific_heat_peak(const int64_t* g, int32_t g_on_devi
     }
 }
 
+// One evaluation of the grid T x h: validation, scratch, the kernels and the copies back. outs
+// holds logZ, E, M, C, chi, absM, M2, M4, binder (any may be NULL).
+static void thermo_grid(const int64_t* g, int32_t g_on_device, const isg_graph* graph, int32_t nT, const double* T,
+                        int32_t nh, const double* h, int32_t precision, void* stream, int32_t out_on_device,
+                        double* const outs_host[kThermoOuts]) {
+    if (!g || !graph || !T || !h) fail(ISG_ERR_INVALID, "NULL argument");
+    if (nT < 1 || nh < 1) fail(ISG_ERR_INVALID, "nT and nh must be >= 1");
+    if (precision != ISG_FP64 && precision != ISG_FP32) fail(ISG_ERR_INVALID, "precision must be ISG_FP64 or ISG_FP32");
+    for (int i = 0; i < nT; ++i)
+        if (!(T[i] > 0) || !std::isfinite(T[i])) fail(ISG_ERR_INVALID, "temperatures must be finite and > 0");
+    for (int i = 0; i < nh; ++i)
+        if (!std::isfinite(h[i])) fail(ISG_ERR_INVALID, "fields must be finite");
+    if (graph->S > (1 << 24)) fail(ISG_ERR_TOO_LARGE, "energy range too large for the thermodynamics kernels");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n_m = graph->n + 1, n_e = (int)(graph->S + 1);
+    const size_t gbytes = sizeof(int64_t) * (size_t)n_e * n_m;
+    const size_t pts = (size_t)nT * nh;
+    int n_out = 0;
+    for (int k = 0; k < kThermoOuts; ++k) n_out += outs_host[k] != nullptr;
+    // scratch: [lng][lngf, lnglo][T][h][g copy if host][requested outputs if host]
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) & ~(size_t)255; return o; };
+    const size_t o_lng = take(sizeof(double) * (size_t)n_e * n_m);
+    const size_t o_lngf = take(2 * sizeof(float) * (size_t)n_e * n_m);
+    const bool inline_grid = nT + nh <= kInlineGrid;
+    const size_t o_T = inline_grid ? 0 : take(sizeof(double) * nT), o_h = inline_grid ? 0 : take(sizeof(double) * nh);
+    const size_t o_g = g_on_device ? 0 : take(gbytes);
+    const size_t o_out = out_on_device ? 0 : take(n_out * sizeof(double) * pts);
+    char* scratch = static_cast<char*>(scratch_alloc(off, s));
+    struct Free {
+        char* p; cudaStream_t s;
+        ~Free() { if (p) cudaFreeAsync(p, s); }
+    } guard{scratch, s};
+    std::unique_ptr<ThermoParams> P(new ThermoParams());
+    ThermoArgs& a = P->a;
+    a.n = graph->n; a.n_e = n_e; a.n_m = n_m; a.nT = nT; a.nh = nh; a.e_min = -graph->S;
+    if (inline_grid) {
+        std::memcpy(P->grid, T, sizeof(double) * nT);
+        std::memcpy(P->grid + nT, h, sizeof(double) * nh);
+        a.T = nullptr;
+        a.h = nullptr;
+    } else {
+        a.T = reinterpret_cast<double*>(scratch + o_T);
+        a.h = reinterpret_cast<double*>(scratch + o_h);
+        ISG_CUDA(cudaMemcpyAsync(scratch + o_T, T, sizeof(double) * nT, cudaMemcpyHostToDevice, s));
+        ISG_CUDA(cudaMemcpyAsync(scratch + o_h, h, sizeof(double) * nh, cudaMemcpyHostToDevice, s));
+    }
+    if (g_on_device) a.g = g;
+    else {
+        ISG_CUDA(cudaMemcpyAsync(scratch + o_g, g, gbytes, cudaMemcpyHostToDevice, s));
+        a.g = reinterpret_cast<int64_t*>(scratch + o_g);
+    }
+    double* outs_dev[kThermoOuts];
+    for (int k = 0, j = 0; k < kThermoOuts; ++k)
+        outs_dev[k] = !outs_host[k] ? nullptr
+                      : out_on_device ? outs_host[k]
+                                      : reinterpret_cast<double*>(scratch + o_out) + (j++) * pts;
+    a.logZ = outs_dev[0]; a.E = outs_dev[1]; a.M = outs_dev[2]; a.C = outs_dev[3]; a.chi = outs_dev[4];
+    a.absM = outs_dev[5]; a.M2 = outs_dev[6]; a.M4 = outs_dev[7]; a.binder = outs_dev[8];
+    launch_thermo(*P, reinterpret_cast<double*>(scratch + o_lng), reinterpret_cast<float*>(scratch + o_lngf), precision, s);
+    if (!out_on_device) {
+        for (int k = 0; k < kThermoOuts; ++k)
+            if (outs_host[k])
+                ISG_CUDA(cudaMemcpyAsync(outs_host[k], outs_dev[k], sizeof(double) * pts, cudaMemcpyDeviceToHost, s));
+    }
+    if (!out_on_device || !g_on_device) ISG_CUDA(cudaStreamSynchronize(s));
+}
+
+#define ISG_TRY_END                                                                                 \
+    catch (const Error& e) {                                                                        \
+        set_error(e.msg);                                                                           \
+        return e.status;                                                                            \
+    }                                                                                               \
+    catch (const std::bad_alloc&) {                                                                 \
+        set_error("host allocation failed");                                                        \
+        return ISG_ERR_NOMEM;                                                                       \
+    }                                                                                               \
+    catch (...) {                                                                                   \
+        set_error("unexpected exception");                                                          \
+        return ISG_ERR_INTERNAL;                                                                    \
+    }
+
 extern "C" isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const isg_graph* graph, int32_t nT,
                                  const double* T, int32_t nh, const double* h, int32_t precision, void* stream,
                                  int32_t out_on_device, double* logZ, double* E, double* M, double* C, double* chi) {
     try {
         clear_error();
         NvtxRange nvtx("isg_thermo");
-        if (!g || !graph || !T || !h) fail(ISG_ERR_INVALID, "NULL argument");
-        if (nT < 1 || nh < 1) fail(ISG_ERR_INVALID, "nT and nh must be >= 1");
-        if (precision != ISG_FP64 && precision != ISG_FP32) fail(ISG_ERR_INVALID, "precision must be ISG_FP64 or ISG_FP32");
-        for (int i = 0; i < nT; ++i)
-            if (!(T[i] > 0) || !std::isfinite(T[i])) fail(ISG_ERR_INVALID, "temperatures must be finite and > 0");
-        for (int i = 0; i < nh; ++i)
-            if (!std::isfinite(h[i])) fail(ISG_ERR_INVALID, "fields must be finite");
-        if (graph->S > (1 << 24)) fail(ISG_ERR_TOO_LARGE, "energy range too large for the thermodynamics kernels");
-        cudaStream_t s = static_cast<cudaStream_t>(stream);
-        const int n_m = graph->n + 1, n_e = (int)(graph->S + 1);
-        const size_t gbytes = sizeof(int64_t) * (size_t)n_e * n_m;
-        const size_t pts = (size_t)nT * nh;
-        // scratch: [lng][T][h][g copy if host][outputs if host]
-        size_t off = 0;
-        auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) & ~(size_t)255; return o; };
-        const size_t o_lng = take(sizeof(double) * (size_t)n_e * n_m);
-        const size_t o_lngf = take(2 * sizeof(float) * (size_t)n_e * n_m);      // lngf, then lnglo
-        const bool inline_grid = nT + nh <= kInlineGrid;
-        const size_t o_T = inline_grid ? 0 : take(sizeof(double) * nT), o_h = inline_grid ? 0 : take(sizeof(double) * nh);
-        const size_t o_g = g_on_device ? 0 : take(gbytes);
-        const size_t o_out = out_on_device ? 0 : take(5 * sizeof(double) * pts);
-        char* scratch = nullptr;
-        scratch = static_cast<char*>(scratch_alloc(off, s));
-        struct Free {
-            char* p; cudaStream_t s;
-            ~Free() { if (p) cudaFreeAsync(p, s); }
-        } guard{scratch, s};
-        std::unique_ptr<ThermoParams> P(new ThermoParams());
-        ThermoArgs& a = P->a;
-        a.n = graph->n; a.n_e = n_e; a.n_m = n_m; a.nT = nT; a.nh = nh; a.e_min = -graph->S;
-        if (inline_grid) {
-            std::memcpy(P->grid, T, sizeof(double) * nT);
-            std::memcpy(P->grid + nT, h, sizeof(double) * nh);
-            a.T = nullptr;
-            a.h = nullptr;
-        } else {
-            a.T = reinterpret_cast<double*>(scratch + o_T);
-            a.h = reinterpret_cast<double*>(scratch + o_h);
-            ISG_CUDA(cudaMemcpyAsync(scratch + o_T, T, sizeof(double) * nT, cudaMemcpyHostToDevice, s));
-            ISG_CUDA(cudaMemcpyAsync(scratch + o_h, h, sizeof(double) * nh, cudaMemcpyHostToDevice, s));
-        }
-        if (g_on_device) a.g = g;
-        else {
-            ISG_CUDA(cudaMemcpyAsync(scratch + o_g, g, gbytes, cudaMemcpyHostToDevice, s));
-            a.g = reinterpret_cast<int64_t*>(scratch + o_g);
-        }
-        double* outs_host[5] = {logZ, E, M, C, chi};
-        double* outs_dev[5];
-        for (int k = 0; k < 5; ++k)
-            outs_dev[k] = !outs_host[k] ? nullptr
-                          : out_on_device ? outs_host[k]
-                                          : reinterpret_cast<double*>(scratch + o_out) + k * pts;
-        a.logZ = outs_dev[0]; a.E = outs_dev[1]; a.M = outs_dev[2]; a.C = outs_dev[3]; a.chi = outs_dev[4];
-        launch_thermo(*P, reinterpret_cast<double*>(scratch + o_lng), reinterpret_cast<float*>(scratch + o_lngf), precision, s);
-        if (!out_on_device) {
-            for (int k = 0; k < 5; ++k)
-                if (outs_host[k])
-                    ISG_CUDA(cudaMemcpyAsync(outs_host[k], outs_dev[k], sizeof(double) * pts, cudaMemcpyDeviceToHost, s));
-        }
-        if (!out_on_device || !g_on_device) ISG_CUDA(cudaStreamSynchronize(s));
+        double* const outs[kThermoOuts] = {logZ, E, M, C, chi, nullptr, nullptr, nullptr, nullptr};
+        thermo_grid(g, g_on_device, graph, nT, T, nh, h, precision, stream, out_on_device, outs);
         return ISG_OK;
-    } catch (const Error& e) {
-        set_error(e.msg);
-        return e.status;
-    } catch (const std::bad_alloc&) {
-        set_error("host allocation failed");
-        return ISG_ERR_NOMEM;
-    } catch (...) {
-        set_error("unexpected exception");
-        return ISG_ERR_INTERNAL;
     }
+    ISG_TRY_END
+}
+
+extern "C" isg_status isg_magnetisation(const int64_t* g, int32_t g_on_device, const isg_graph* graph, int32_t nT,
+                                        const double* T, int32_t nh, const double* h, int32_t precision,
+                                        void* stream, int32_t out_on_device, double* abs_M, double* M2, double* M4,
+                                        double* binder) {
+    try {
+        clear_error();
+        NvtxRange nvtx("isg_magnetisation");
+        double* const outs[kThermoOuts] = {nullptr, nullptr, nullptr, nullptr, nullptr, abs_M, M2, M4, binder};
+        thermo_grid(g, g_on_device, graph, nT, T, nh, h, precision, stream, out_on_device, outs);
+        return ISG_OK;
+    }
+    ISG_TRY_END
 }

@@ -47,6 +47,7 @@ _SIGS = {
     "isg_graph_size": (i32, [vp, vp, vp]),
     "isg_enumerate": (i32, [vp, vp, vp, i32, vp]),
     "isg_thermo": (i32, [vp, i32, vp, i32, vp, i32, vp, i32, vp, i32, vp, vp, vp, vp, vp]),
+    "isg_magnetisation": (i32, [vp, i32, vp, i32, vp, i32, vp, i32, vp, i32, vp, vp, vp, vp]),
     "isg_last_error": (ctypes.c_char_p, []),
     "isg_version": (ctypes.c_char_p, []),
     "isg_debug_plan": (i32, [vp, vp, i32, vp]),
@@ -377,12 +378,7 @@ def _f64(x) -> np.ndarray:
     return np.ascontiguousarray(np.atleast_1d(x), dtype=np.float64)
 
 
-def isg_thermo(g, graph: Graph, T, h, precision: int = ISG_FP64, stream=None, out=None):
-    """ln Z, <H>, <M>, C, chi on the grid T x h (Eq. 2 over g).
-
-    g: torch int64 CUDA tensor or numpy int64 array of table_shape(graph). out: None (numpy
-    results, the call synchronises) or a tuple of 5 float64 CUDA tensors of shape (len(T), len(h))
-    (filled asynchronously; None entries are skipped)."""
+def _grid_call(fn, n_out: int, g, graph: Graph, T, h, precision: int, stream, out):
     T, h = _f64(T), _f64(h)
     shape = table_shape(graph)
     if isinstance(g, np.ndarray):
@@ -395,11 +391,12 @@ def isg_thermo(g, graph: Graph, T, h, precision: int = ISG_FP64, stream=None, ou
         g_ptr, g_dev = g.data_ptr(), 1
     s = _stream_handle(stream) if (stream is not None or g_dev or out is not None) else None
     if out is None:
-        res = [np.zeros((len(T), len(h)), dtype=np.float64) for _ in range(5)]
-        ptrs = [r.ctypes.data for r in res]
-        _check(lib().isg_thermo(g_ptr, g_dev, graph, len(T), T.ctypes.data, len(h), h.ctypes.data, precision, s, 0,
-                                *ptrs))
+        res = [np.zeros((len(T), len(h)), dtype=np.float64) for _ in range(n_out)]
+        _check(fn(g_ptr, g_dev, graph, len(T), T.ctypes.data, len(h), h.ctypes.data, precision, s, 0,
+                  *[r.ctypes.data for r in res]))
         return tuple(res)
+    if len(out) != n_out:
+        raise ValueError(f"out must hold {n_out} entries")
     ptrs = []
     oshape = (len(T), len(h))
     for t in out:
@@ -408,9 +405,23 @@ def isg_thermo(g, graph: Graph, T, h, precision: int = ISG_FP64, stream=None, ou
         else:
             _check_tensor(t, oshape, "float64")
             ptrs.append(t.data_ptr())
-    _check(lib().isg_thermo(g_ptr, g_dev, graph, len(T), T.ctypes.data, len(h), h.ctypes.data, precision, s, 1,
-                            *ptrs))
+    _check(fn(g_ptr, g_dev, graph, len(T), T.ctypes.data, len(h), h.ctypes.data, precision, s, 1, *ptrs))
     return out
+
+
+def isg_thermo(g, graph: Graph, T, h, precision: int = ISG_FP64, stream=None, out=None):
+    """ln Z, <H>, <M>, C, chi on the grid T x h (Eq. 2 over g).
+
+    g: torch int64 CUDA tensor or numpy int64 array of table_shape(graph). out: None (numpy
+    results, the call synchronises) or a tuple of 5 float64 CUDA tensors of shape (len(T), len(h))
+    (filled asynchronously; None entries are skipped)."""
+    return _grid_call(lib().isg_thermo, 5, g, graph, T, h, precision, stream, out)
+
+
+def isg_magnetisation(g, graph: Graph, T, h, precision: int = ISG_FP64, stream=None, out=None):
+    """<|M|>, <M^2>, <M^4> and Binder's cumulant 1 - <M^4>/(3<M^2>^2) on the grid T x h, with the
+    weights of Eq. 2 over g. g and out as for isg_thermo (out: a tuple of 4)."""
+    return _grid_call(lib().isg_magnetisation, 4, g, graph, T, h, precision, stream, out)
 
 
 class PreparedCall:

@@ -133,3 +133,78 @@ def test_specific_heat_peak(isg, cuda):
     t0 = grid[int(np.argmax([c_or(t) for t in grid]))]
     t_or = golden_max(c_or, t0 - 0.03, t0 + 0.03, tol=1e-11)
     assert abs(t_gpu - t_or) <= 1e-7 * t_or
+
+
+# --------------------------------------------------------------------------- magnetisation
+MAG_NAMES = ["absM", "M2", "M4", "binder"]
+
+
+@pytest.mark.parametrize("lat", [w.square(4, 4, False), w.ring(11), w.with_random_couplings(w.triangular(3, 5, True), w.SplitMix64(3), (-2, -1, 1, 2)),
+                                 w.Lattice(6, np.zeros((0, 3), np.int64))], ids=lambda l: l.name or "free")
+def test_magnetisation_fp64_small(isg, cuda, lat):
+    """<|M|>, <M^2>, <M^4>, Binder's cumulant against the oracle at 1e-12 relative, FP64."""
+    g = oracle.g_masks(lat.n, lat.edges)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    T = np.linspace(0.3, 6, 48)
+    h = np.array([-1.5, -0.2, 0.0, 0.4, 2.0])
+    got = isg.isg_magnetisation(g, gh, T, h, isg.ISG_FP64)
+    ref = oracle.magnetisation(lat.n, e_min, g, T, h)
+    for k, (a, b) in enumerate(zip(got, ref)):
+        assert rel_close(a, b, 1e-12, 1e-13), (MAG_NAMES[k], np.max(np.abs(a - b) / np.abs(b)))
+
+
+def test_magnetisation_cubic_grid(isg, cuda):
+    """3x3x4 cubic torus on the 512 x 256 (T, h) grid: FP64 against the oracle on sampled points
+    (1e-12 relative); FP32 against FP64 everywhere: <|M|>, <M^2>, <M^4> within 1e-5 relative,
+    Binder's cumulant within 1e-5 absolute (it is a difference of two O(1) terms)."""
+    lat = w.cubic(3, 3, 4, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = isg.isg_enumerate(gh)
+    T = np.linspace(0.5, 8, 512)
+    h = np.linspace(-2, 2, 256)
+    d = isg.isg_magnetisation(g, gh, T, h, isg.ISG_FP64)
+    f = isg.isg_magnetisation(g, gh, T, h, isg.ISG_FP32)
+    rng = w.SplitMix64(13)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    for _ in range(16):
+        a, b = rng.below(512), rng.below(256)
+        ref = oracle.magnetisation(lat.n, e_min, g, T[a:a + 1], h[b:b + 1])
+        for k in range(4):
+            assert abs(d[k][a, b] - ref[k][0, 0]) <= 1e-12 * abs(ref[k][0, 0]) + 1e-13, (MAG_NAMES[k], a, b)
+    for k in range(3):
+        assert np.max(np.abs(f[k] - d[k]) / d[k]) <= 1e-5, MAG_NAMES[k]
+    assert np.max(np.abs(f[3] - d[3])) <= 1e-5
+
+
+def test_magnetisation_device_outputs(isg, cuda):
+    import torch
+    lat = w.square(4, 4, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=cuda)
+    isg.isg_enumerate(gh, g)
+    T = np.linspace(1, 3, 7)
+    h = np.linspace(-1, 1, 5)
+    outs = tuple(torch.empty((7, 5), dtype=torch.float64, device=cuda) for _ in range(4))
+    isg.isg_magnetisation(g, gh, T, h, isg.ISG_FP64, out=(outs[0], None, outs[2], outs[3]))
+    torch.cuda.synchronize()
+    ref = isg.isg_magnetisation(g.cpu().numpy(), gh, T, h, isg.ISG_FP64)
+    for k in (0, 2, 3):
+        assert np.array_equal(outs[k].cpu().numpy(), ref[k])
+
+
+def test_binder_cumulants_cross_near_onsager(isg, cuda):
+    """Binder's cumulant of the 4x4 and 6x6 ferromagnetic tori (GPU tables, FP64): the larger
+    system is more ordered below the transition and less above it, so the curves cross once on
+    [1.5, 3.5], close to the infinite-lattice temperature 2 / ln(1 + sqrt 2) = 2.269."""
+    T = np.linspace(1.5, 3.5, 401)
+    u = []
+    for L in (4, 6):
+        lat = w.square(L, L, True)
+        gh = isg.isg_graph_create(lat.n, lat.edges)
+        u.append(isg.isg_magnetisation(isg.isg_enumerate(gh), gh, T, [0.0], isg.ISG_FP64)[3][:, 0])
+    diff = u[1] - u[0]
+    sign_changes = np.nonzero(np.diff(np.sign(diff)))[0]
+    assert len(sign_changes) == 1
+    t_cross = T[sign_changes[0]]
+    assert abs(t_cross - 2 / np.log(1 + np.sqrt(2))) < 0.1, t_cross
