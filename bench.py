@@ -391,6 +391,21 @@ def extra_measurements(stream, dev):
     t_cross = Tb[k] + (Tb[k + 1] - Tb[k]) * dub[k] / (dub[k] - dub[k + 1])
     out["torus_binder_crossing_4x4_6x6"] = {"T_cross": float(t_cross), "U4_at_cross": float(ub[0][k]),
                                             "isg_magnetisation_ms_2001T": mag_ms}
+    # split-and-convolve (a variant of the full enumeration, reported apart from the headline):
+    # the same exact tables from 2^|S| * sum 2^|C| visits
+    split = {}
+    for name, lat in (("torus6x6", workloads.square(6, 6, True)), ("cubic3x3x4", workloads.cubic(3, 3, 4, True)),
+                      ("torus7x7", workloads.square(7, 7, True))):
+        hs = isg.isg_graph_create(lat.n, lat.edges)
+        gs = torch.zeros(isg.table_shape(hs), dtype=torch.int64, device=dev)
+        plan_s = isg.isg_split_plan(hs)
+        ms = _event_ms(lambda: isg.isg_enumerate_split(hs, gs, stream), stream, 3)
+        tot = int(gs.sum().item())
+        split[name] = {"N": lat.n, "ms": ms, "boundary_spins": plan_s["boundary_spins"],
+                       "components": plan_s["components"], "largest_component": plan_s["largest_component"],
+                       "visits": plan_s["visits"], "effective_configs_per_s": 2.0 ** lat.n / (ms * 1e-3),
+                       "visits_per_s": plan_s["visits"] / (ms * 1e-3), "sum_g_equals_2^N": tot == 2 ** lat.n}
+    out["split_and_convolve"] = split
     # cubic 3x3x4 torus: thermodynamics on 512 T x 256 h, FP32 vs FP64
     lat = workloads.cubic(3, 3, 4, True)
     gh = isg.isg_graph_create(lat.n, lat.edges)
@@ -581,6 +596,14 @@ def run_profile_case(args):
             for _ in range(args.warmup):
                 isg.isg_thermo(g, gh, T, h, prec, stream, out=outs)
             res[name] = _event_ms(lambda: isg.isg_thermo(g, gh, T, h, prec, stream, out=outs), stream, args.steps)
+    elif args.profile_case == "split-torus6x6":
+        lat = workloads.square(6, 6, True)
+        gh = isg.isg_graph_create(lat.n, lat.edges)
+        g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=dev)
+        for _ in range(args.warmup):
+            isg.isg_enumerate_split(gh, g, stream)
+        res["ms"] = _event_ms(lambda: isg.isg_enumerate_split(gh, g, stream), stream, args.steps)
+        res["sum_ok"] = int(g.sum().item()) == 2 ** 36
     else:
         raise SystemExit(f"unknown profile case {args.profile_case}")
     torch.cuda.synchronize()
@@ -597,7 +620,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target seconds of the oracle sample")
     ap.add_argument("--serving", action="store_true", help="run the request-stream (serving) benchmark instead")
-    ap.add_argument("--profile-case", choices=("ea-batch", "cubic-thermo"), default=None,
+    ap.add_argument("--profile-case", choices=("ea-batch", "cubic-thermo", "split-torus6x6"), default=None,
                     help="run only a small case of another kernel (for ncu captures)")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=50.0)

@@ -194,6 +194,41 @@ ISG_API void isg_batch_destroy(isg_batch* batch);
 ISG_API isg_status isg_autotune(const isg_graph* graph, void* stream, const isg_options* opt, isg_options* tuned);
 
 /*
+ * Split-and-convolve enumeration: the same exact table as isg_enumerate, computed with fewer
+ * than 2^N configuration visits. This is a variant of the paper's full enumeration (Sec. 3), not
+ * the paper's method. A boundary set S of spins is chosen whose removal leaves components with no
+ * bond between them. For each of the 2^|S| configurations of S, each component's configurations
+ * are enumerated under the field that S exerts on it (Eq. 1 restricted to the component and its
+ * bonds to S), and the components' (E, M) histograms are convolved and shifted by the energy and
+ * up count of S's own bonds and spins. The result is g(E, M) exactly (integer arithmetic
+ * throughout). The global spin flip maps a configuration of S and its components' walks onto
+ * the complement's with M negated and E kept, so only the configurations of S with its last spin
+ * down are walked and each result is also added at -M. Visits: 2^(|S|-1) * sum over components
+ * of 2^|C| (2^0 * sum 2^|C| when S is empty).
+ * boundary: a mask of spins (bit i = spin i) to use as S, or 0 to let the library choose: the
+ * cheapest, under a work model, among windows of consecutive indices, residue classes of the
+ * index and the complement of an independent set. Each component must have at most 30 spins,
+ * S at most 40, at most 16 distinct couplings, and the per-warp buffers (two (sum S_c + 2) x
+ * (sum |C| + 1) accumulators) must fit in shared memory with the (S + 1)(N + 1) int64 table.
+ * g_out: n_e * n_m int64 (isg_graph_bins), on the device if g_out_on_device (only enqueued) or on
+ * the host (synchronises stream). The output is overwritten.
+ * Errors: ISG_ERR_INVALID (NULL, mask beyond N), ISG_ERR_TOO_LARGE (no admissible boundary, or
+ * none cheaper than the full enumeration when boundary = 0), ISG_ERR_NOMEM, ISG_ERR_CUDA,
+ * ISG_ERR_INTERNAL (a walk's self-check failed; host output only).
+ */
+ISG_API isg_status isg_enumerate_split(const isg_graph* graph, void* stream, int64_t* g_out, int32_t g_out_on_device,
+                                       uint64_t boundary);
+
+/*
+ * The boundary set isg_enumerate_split would use (boundary as there) and its cost: *chosen the
+ * mask of S, *n_components and *largest_component the components left by removing it, *visits
+ * = 2^(|S|-1) * sum 2^|C| (the walked configurations), *work_ratio the modelled work relative to the full enumeration (below 1:
+ * cheaper). Host only; any output may be NULL. Errors as isg_enumerate_split's planning.
+ */
+ISG_API isg_status isg_split_plan(const isg_graph* graph, uint64_t boundary, uint64_t* chosen, int32_t* n_components,
+                                  int32_t* largest_component, double* visits, double* work_ratio);
+
+/*
  * isg_enumerate for callers that cannot allocate device memory: the paper has no counterpart
  * to this call. It is meant for a caller whose device memory is owned by another allocator, or
  * that runs the enumeration inside a fixed memory budget or a loop that must not enter an

@@ -32,6 +32,14 @@ ISG_API isg_status isg_debug_plan(const isg_graph* graph, const isg_options* opt
 ISG_API isg_status isg_debug_emulate(const isg_graph* graph, const isg_options* opt, int64_t* g_out);
 
 /*
+ * Run the split kernel's per-warp work (isg_enumerate_split with the same boundary argument) on
+ * the host, lane by lane, with every histogram, accumulator and table index checked, and write g
+ * (host buffer, isg_graph_bins geometry). For small boundary sets and components only. Returns
+ * ISG_ERR_INTERNAL if an index leaves its buffer or a parity or range check fails.
+ */
+ISG_API isg_status isg_debug_emulate_split(const isg_graph* graph, uint64_t boundary, int64_t* g_out);
+
+/*
  * Measured peaks of the units that bound the enumeration kernel on the current device, in
  * lane-operations per second over the whole GPU: shared-memory 32-bit reductions with each lane
  * in its own bank (red_conflict_free) and with scattered addresses (red_scattered), integer ALU

@@ -1,0 +1,314 @@
+// split.cu -- split-and-convolve enumeration on the device (the identity and the program layout
+// are in split_internal.h): one warp per configuration s of the boundary set S.
+//
+// Per s (half of them: the other half are their global-flip mirrors), a warp computes the boundary
+// energy and up count, then for each component C_c the field
+// S exerts on each of its spins, walks the 2^|C_c| configurations of C_c (32 lanes, each a
+// reflected Gray walk over the low |C_c| - 5 bits with its lane index in the top five) into a
+// 32-bit shared histogram, and convolves that histogram into the warp's accumulator: the nonzero
+// bins of both are listed, each lane holds a few accumulator bins in registers, and every product
+// is a shared-memory reduction into the next accumulator.
+// The accumulator, shifted by the boundary's bin, is added into the CTA's int64 table in shared
+// memory, which is flushed to the output with 64-bit atomics at the end.
+//
+// The enumeration walks visit 2^(|S|-1) * sum_c 2^|C_c| configurations instead of 2^N; the
+// convolutions are exact integer arithmetic, so the table equals the full enumeration's.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "isg_internal.h"
+#include "nvtx_range.h"
+#include "split_internal.h"
+
+namespace isg {
+
+DeviceInfo device_info();
+
+struct SplitArgs {
+    const uint64_t* blob;          // device program
+    int blob_words;
+    unsigned long long* table;     // (S + 1)(N + 1) counts, accumulated into
+    unsigned int* status;          // bit 0: a walk lost track of its bin
+    unsigned long long n_s;        // 2^|S|
+};
+
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// sum_t J_t (2 popc(m_t & bits) - popc(m_t)) over the classes' masks m_t = masks[t * stride]
+__device__ __forceinline__ int split_field(const int64_t* cls, int ncl, const uint64_t* masks, int stride, uint64_t bits) {
+    int f = 0;
+    for (int t = 0; t < ncl; ++t) {
+        const uint64_t m = masks[t * stride];
+        f += (int)cls[t] * (2 * __popcll(m & bits) - __popcll(m));
+    }
+    return f;
+}
+
+template <class Acc>
+__global__ void __launch_bounds__(512) split_kernel(const __grid_constant__ SplitArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    uint64_t* prog = reinterpret_cast<uint64_t*>(sm);
+    for (int i = threadIdx.x; i < a.blob_words; i += blockDim.x) prog[i] = a.blob[i];
+    __syncthreads();
+    const SplitView v = split_view(prog);
+    const SplitHeader& H = *v.h;
+    const int ncl = H.n_cls, MO = H.MO;
+    // the CTA's table as 32-bit low and high words: 32-bit shared atomics, the carry of a low-word
+    // addition detected from the value it returned
+    unsigned int* tlo = reinterpret_cast<unsigned int*>(sm + split_prog_bytes(a.blob_words));
+    unsigned int* thi = tlo + H.n_bins;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const SplitWarpLayout WL = split_warp_layout(H, sizeof(Acc) == 8);
+    unsigned char* wbase = sm + split_prog_bytes(a.blob_words) + split_table_bytes(H) + (size_t)warp * WL.bytes;
+    Acc* bufA = reinterpret_cast<Acc*>(wbase + WL.acc_a);
+    Acc* bufB = reinterpret_cast<Acc*>(wbase + WL.acc_b);
+    uint64_t* hlist = reinterpret_cast<uint64_t*>(wbase + WL.hlist);
+    uint32_t* list = reinterpret_cast<uint32_t*>(wbase + WL.list);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(wbase + WL.hist);
+    for (int i = threadIdx.x; i < 2 * H.n_bins; i += blockDim.x) tlo[i] = 0;
+    __syncthreads();
+    auto table_add = [&](int i, unsigned long long v) {
+        const unsigned int vl = (unsigned int)v, vh = (unsigned int)(v >> 32);
+        const unsigned int old = atomicAdd(&tlo[i], vl);
+        const unsigned int carry = (unsigned int)(old + vl < old);
+        if (vh + carry) atomicAdd(&thi[i], vh + carry);
+    };
+
+    const unsigned FULL = 0xffffffffu;
+    const unsigned long long wpb = blockDim.x >> 5;
+    bool bad = false;
+    // The global flip (every spin reversed) keeps E and negates M, so the boundary configurations
+    // with the top boundary bit set give the mirror images of the others: only s < n_s / 2 are
+    // walked and each result is added at M and at -M.
+    const unsigned long long n_walk = H.ns ? a.n_s >> 1 : a.n_s;
+    for (unsigned long long s = blockIdx.x * wpb + warp; s < n_walk; s += gridDim.x * wpb) {
+        // boundary: sum_j S_j a_j = -2 E_SS over its own bonds; up count
+        int part = 0;
+        for (int j = lane; j < H.ns; j += 32) {
+            const int f = split_field(v.cls, ncl, v.ss + (size_t)j * ncl, 1, s);
+            part += ((s >> j) & 1) ? f : -f;
+        }
+        part = warp_sum_i(part);
+        const int e_SS = (-part / 2 + H.S_SS) / 2;
+        const int m_S = __popcll(s);
+        Acc* acc = bufA;
+        Acc* out = bufB;
+        int rows = 0;
+        if (H.n_comp == 0) {                  // every spin is boundary: the empty convolution
+            if (lane == 0) acc[0] = 1;
+            __syncwarp();
+        }
+        for (int c = 0; c < H.n_comp; ++c) {
+            const SplitComp cp = v.comp[c];
+            const int nc = cp.nc, MC = nc + 1;
+            const uint64_t* sp = v.spin + (size_t)cp.first * ncl * 2;
+            // field on component spin `lane` from the boundary (nc <= 30)
+            const int myf = lane < nc ? split_field(v.cls, ncl, sp + (size_t)lane * ncl * 2 + 1, 2, s) : 0;
+            for (int i = lane; i < cp.h_words; i += 32) hist[i] = 0;
+            __syncwarp();
+            const int L = nc > 5 ? nc - 5 : 0;
+            const bool active = nc > 5 || lane < (1 << nc);
+            uint32_t x = (uint32_t)lane << L;
+            // 2 E_c(x) = -sum_q S_q (internal field_q + 2 f_q), from scratch
+            int twoE = 0;
+            for (int q = 0; q < nc; ++q) {
+                const int fq = __shfl_sync(FULL, myf, q);
+                const int hin = split_field(v.cls, ncl, sp + (size_t)q * ncl * 2, 2, x);
+                twoE -= ((x >> q) & 1) ? hin + 2 * fq : -(hin + 2 * fq);
+            }
+            int e = (twoE / 2 + cp.Sc) / 2;
+            int m = __popc(x);
+            // a bin outside the histogram (a bug) is recorded and skipped, never written
+            auto count = [&](int ee, int mm) {
+                if ((unsigned)ee <= (unsigned)cp.Sc && (unsigned)mm <= (unsigned)nc) atomicAdd(&hist[ee * MC + mm], 1u);
+                else bad = true;
+            };
+            if (active) count(e, m);
+            for (uint32_t t = 1; t < (1u << L); ++t) {
+                const int k = __ffs(t) - 1;                          // the same spin in every lane
+                const bool up = (x >> k) & 1;
+                const int hk = split_field(v.cls, ncl, sp + (size_t)k * ncl * 2, 2, x) + __shfl_sync(FULL, myf, k);
+                e += up ? hk : -hk;
+                m += up ? -1 : 1;
+                x ^= 1u << k;
+                count(e, m);
+            }
+            // self-check: the tracked bin of the lane's last configuration against a recomputation
+            {
+                int twoE2 = 0;
+                for (int q = 0; q < nc; ++q) {
+                    const int fq = __shfl_sync(FULL, myf, q);
+                    const int hin = split_field(v.cls, ncl, sp + (size_t)q * ncl * 2, 2, x);
+                    twoE2 -= ((x >> q) & 1) ? hin + 2 * fq : -(hin + 2 * fq);
+                }
+                if (active && (e != (twoE2 / 2 + cp.Sc) / 2 || m != __popc(x))) bad = true;
+            }
+            __syncwarp();
+            if (c == 0) {
+                for (int i = lane; i < H.acc_words; i += 32) acc[i] = 0;
+                __syncwarp();
+                for (int i = lane; i < cp.h_words; i += 32) {
+                    const int e1 = i / MC, m1 = i - e1 * MC;
+                    acc[e1 * MO + m1] = hist[i];
+                }
+            } else {
+                // the accumulator's nonzero bins, listed once
+                const int used = (rows + 1) * MO;
+                int nl = 0;
+                for (int base = 0; base < used; base += 32) {
+                    const int i = base + lane;
+                    const bool nz = i < used && acc[i] != 0;
+                    const unsigned bal = __ballot_sync(FULL, nz);
+                    if (nz) list[nl + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)i;
+                    nl += __popc(bal);
+                }
+                // the histogram's nonzero bins as (shift in the accumulator's layout, count)
+                int nh = 0;
+                for (int base = 0; base < cp.h_words; base += 32) {
+                    const int i = base + lane;
+                    const uint32_t hv = i < cp.h_words ? hist[i] : 0u;
+                    const unsigned bal = __ballot_sync(FULL, hv != 0);
+                    if (hv) {
+                        const int e1 = i / MC, m1 = i - e1 * MC;
+                        hlist[nh + __popc(bal & ((1u << lane) - 1u))] =
+                            (uint64_t)(uint32_t)(e1 * MO + m1) | ((uint64_t)hv << 32);
+                    }
+                    nh += __popc(bal);
+                }
+                for (int i = lane; i < H.acc_words; i += 32) out[i] = 0;
+                __syncwarp();
+                // out[a + shift] += count * acc[a] over all pairs: each lane keeps up to kRegs of the
+                // accumulator's nonzero bins in registers and the histogram list is read by
+                // broadcast; the products go out as shared-memory reductions (no read-back)
+                constexpr int kRegs = sizeof(Acc) == 8 ? 4 : 8;
+                for (int ch = 0; ch < nl; ch += 32 * kRegs) {
+                    uint32_t li[kRegs];
+                    Acc av[kRegs];
+#pragma unroll
+                    for (int k = 0; k < kRegs; ++k) {
+                        const int q = ch + lane + 32 * k;
+                        li[k] = q < nl ? list[q] : 0u;
+                        av[k] = q < nl ? acc[li[k]] : (Acc)0;
+                    }
+                    for (int j = 0; j < nh; ++j) {
+                        const uint64_t hw = hlist[j];
+                        const uint32_t hs = (uint32_t)hw;
+                        const Acc hv = (Acc)(hw >> 32);
+#pragma unroll
+                        for (int k = 0; k < kRegs; ++k)
+                            if (av[k]) atomicAdd(&out[li[k] + hs], hv * av[k]);
+                    }
+                }
+                __syncwarp();
+                Acc* t = acc;
+                acc = out;
+                out = t;
+            }
+            rows += cp.Sc;
+            __syncwarp();
+        }
+        // shift by the boundary's bin and add into the CTA's table
+        const int used = H.EO * MO;
+        for (int i = lane; i < used; i += 32) {
+            const Acc val = acc[i];
+            if (val) {
+                const int e1 = i / MO, m1 = i - e1 * MO;
+                const int row = (e_SS + e1) * (H.n + 1);
+                table_add(row + m_S + m1, (unsigned long long)val);
+                if (H.ns) table_add(row + H.n - m_S - m1, (unsigned long long)val);
+            }
+        }
+        __syncwarp();
+    }
+    if (bad) atomicOr(a.status, 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < H.n_bins; i += blockDim.x) {
+        const unsigned long long v = ((unsigned long long)thi[i] << 32) | tlo[i];
+        if (v) atomicAdd(&a.table[i], v);
+    }
+}
+
+#define ISG_CUDA(call)                                                                              \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            fail(e_ == cudaErrorMemoryAllocation ? ISG_ERR_NOMEM : ISG_ERR_CUDA,                    \
+                 std::string(#call) + ": " + cudaGetErrorString(e_));                               \
+    } while (0)
+
+}  // namespace isg
+
+using namespace isg;
+
+extern "C" isg_status isg_enumerate_split(const isg_graph* graph, void* stream, int64_t* g_out, int32_t g_out_on_device,
+                                          uint64_t boundary) {
+    try {
+        clear_error();
+        NvtxRange nvtx("isg_enumerate_split");
+        if (!graph || !g_out) fail(ISG_ERR_INVALID, "graph or g_out is NULL");
+        const std::shared_ptr<const SplitPrepared> prep = prepare_split(*graph, boundary, true);
+        const SplitPlan& p = prep->plan;
+        const std::vector<uint64_t>& blob = prep->blob;
+        const SplitHeader& H = *reinterpret_cast<const SplitHeader*>(blob.data());
+        const DeviceInfo d = device_info();
+        const size_t fixed = split_smem_bytes((int)blob.size(), H, p.use_u64, 0);
+        const size_t per_warp = split_warp_bytes(H, p.use_u64);
+        const size_t limit = (size_t)d.smem_optin;
+        if (fixed + per_warp > limit) fail(ISG_ERR_TOO_LARGE, "split buffers exceed shared memory");
+        const int warps = (int)std::min<size_t>(16, (limit - fixed) / per_warp);
+        const size_t smem = fixed + (size_t)warps * per_warp;
+        const int ctas_per_sm = std::max(1, (int)std::min<size_t>(4, (size_t)d.smem_per_sm / (smem + 1024)));
+        const unsigned long long n_s = 1ull << H.ns;
+        const unsigned long long want = (n_s + warps - 1) / warps;
+        const int grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(want, (unsigned long long)d.sms * ctas_per_sm));
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const size_t table_bytes = sizeof(int64_t) * (size_t)H.n_bins;
+        const size_t blob_bytes = blob.size() * 8;
+        // scratch: [status 16][program][table if host output]
+        const size_t o_blob = 16, o_tab = (o_blob + blob_bytes + 255) & ~(size_t)255;
+        char* scratch = static_cast<char*>(scratch_alloc(o_tab + (g_out_on_device ? 0 : table_bytes), s));
+        struct Free {
+            char* p; cudaStream_t s;
+            ~Free() { if (p) cudaFreeAsync(p, s); }
+        } guard{scratch, s};
+        unsigned long long* table = g_out_on_device ? reinterpret_cast<unsigned long long*>(g_out)
+                                                    : reinterpret_cast<unsigned long long*>(scratch + o_tab);
+        ISG_CUDA(cudaMemsetAsync(scratch, 0, 16, s));
+        ISG_CUDA(cudaMemcpyAsync(scratch + o_blob, blob.data(), blob_bytes, cudaMemcpyHostToDevice, s));
+        ISG_CUDA(cudaMemsetAsync(table, 0, table_bytes, s));
+        SplitArgs a{reinterpret_cast<const uint64_t*>(scratch + o_blob), (int)blob.size(), table,
+                    reinterpret_cast<unsigned int*>(scratch), n_s};
+        if (p.use_u64) {
+            ISG_CUDA(cudaFuncSetAttribute(split_kernel<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            split_kernel<unsigned long long><<<grid, 32 * warps, smem, s>>>(a);
+        } else {
+            ISG_CUDA(cudaFuncSetAttribute(split_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            split_kernel<uint32_t><<<grid, 32 * warps, smem, s>>>(a);
+        }
+        ISG_CUDA(cudaGetLastError());
+        if (!g_out_on_device) {
+            unsigned int status = 0;
+            ISG_CUDA(cudaMemcpyAsync(g_out, table, table_bytes, cudaMemcpyDeviceToHost, s));
+            ISG_CUDA(cudaMemcpyAsync(&status, scratch, sizeof status, cudaMemcpyDeviceToHost, s));
+            ISG_CUDA(cudaStreamSynchronize(s));
+            if (status) fail(ISG_ERR_INTERNAL, "split enumeration self-check failed");
+        }
+        return ISG_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return ISG_ERR_NOMEM;
+    } catch (...) {
+        set_error("unexpected exception");
+        return ISG_ERR_INTERNAL;
+    }
+}

@@ -1,0 +1,499 @@
+// split_host.cpp -- split-and-convolve enumeration on the host side: choice of the boundary set,
+// the device program, and an emulation of the split kernel's per-warp work (no CUDA calls here).
+//
+// A variant of the paper's full enumeration (Sec. 3): instead of visiting all 2^N configurations,
+// a boundary set S is enumerated and, for each of its configurations, the components left by
+// removing S are enumerated separately and their histograms convolved (the identity is written
+// out in split_internal.h). The tables are identical to the full enumeration's.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "isg_internal.h"
+#include "split_internal.h"
+
+namespace isg {
+
+namespace {
+
+inline int ctz64(uint64_t x) { return __builtin_ctzll(x); }
+inline int popc(uint64_t x) { return __builtin_popcountll(x); }
+inline uint64_t low_mask(int n) { return n >= 64 ? ~0ull : ((1ull << n) - 1); }
+
+std::vector<uint64_t> adjacency(const isg_graph& g) {
+    std::vector<uint64_t> adj(g.n, 0);
+    for (size_t b = 0; b < g.bi.size(); ++b) {
+        adj[g.bi[b]] |= 1ull << g.bj[b];
+        adj[g.bj[b]] |= 1ull << g.bi[b];
+    }
+    return adj;
+}
+
+// Connected components of the spins in `rem` (bit masks), by breadth-first growth.
+std::vector<uint64_t> components(const std::vector<uint64_t>& adj, uint64_t rem) {
+    std::vector<uint64_t> out;
+    while (rem) {
+        uint64_t comp = rem & (~rem + 1), front = comp;
+        while (front) {
+            uint64_t nb = 0;
+            for (uint64_t f = front; f; f &= f - 1) nb |= adj[ctz64(f)];
+            front = nb & rem & ~comp;
+            comp |= front;
+        }
+        out.push_back(comp);
+        rem &= ~comp;
+    }
+    return out;
+}
+
+int64_t touching_weight(const isg_graph& g, uint64_t comp) {
+    int64_t s = 0;
+    for (size_t b = 0; b < g.bi.size(); ++b)
+        if (((comp >> g.bi[b]) & 1) || ((comp >> g.bj[b]) & 1)) s += std::llabs(g.bJ[b]);
+    return s;
+}
+
+struct Candidate {
+    uint64_t S = 0;
+    std::vector<uint64_t> comps;     // largest histogram first
+    std::vector<int64_t> Sc;
+    double cost = INFINITY, visits = 0;
+    bool u64 = false;
+    int warps = 0;
+};
+
+double ceil32(double x) { return std::ceil(x / 32.0); }
+
+// Work model in warp instructions (see the kernel): per boundary configuration the boundary
+// energy, per component its fields, a walk of 2^|C| configurations over 32 lanes, and the
+// convolution of its histogram's nonzero bins with the accumulator's nonzero bins; then the
+// shift-add of the accumulator into the table. Also checks the shared-memory layout fits.
+void evaluate(const isg_graph& g, int n_cls, Candidate& c) {
+    const int ns = popc(c.S);
+    c.cost = INFINITY;
+    if (ns > 40) return;
+    const size_t k = c.comps.size();
+    if (k > (size_t)kSplitMaxComp) return;           // k = 0 (all spins boundary) is allowed
+    std::vector<int> nc(k);
+    c.Sc.assign(k, 0);
+    std::vector<size_t> order(k);
+    for (size_t i = 0; i < k; ++i) {
+        nc[i] = popc(c.comps[i]);
+        if (nc[i] > kSplitMaxCompSpins) return;
+        c.Sc[i] = touching_weight(g, c.comps[i]);
+        order[i] = i;
+    }
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        const int64_t ha = (c.Sc[a] + 1) * (nc[a] + 1), hb = (c.Sc[b] + 1) * (nc[b] + 1);
+        return ha != hb ? ha > hb : c.comps[a] < c.comps[b];
+    });
+    std::vector<uint64_t> comps2(k);
+    std::vector<int64_t> Sc2(k);
+    std::vector<int> nc2(k);
+    for (size_t i = 0; i < k; ++i) { comps2[i] = c.comps[order[i]]; Sc2[i] = c.Sc[order[i]]; nc2[i] = nc[order[i]]; }
+    c.comps = comps2;
+    c.Sc = Sc2;
+    nc = nc2;
+    int64_t EO = 1, MO = 1, hmax = 0;
+    for (size_t i = 0; i < k; ++i) {
+        EO += c.Sc[i];
+        MO += nc[i];
+        hmax = std::max<int64_t>(hmax, (c.Sc[i] + 1) * (nc[i] + 1));
+    }
+    const int inner = g.n - ns;
+    c.u64 = inner > 31;
+    const int64_t acc_words = (EO + 1) * MO;
+    const size_t acc_bytes = c.u64 ? 8 : 4;
+    const size_t per_warp = 12 * (size_t)hmax + 32 + (2 * acc_bytes + 4) * (size_t)acc_words;
+    const size_t prog_bytes = 64 + 8 * ((size_t)n_cls * (1 + ns) + 2 * k + (size_t)(g.n - ns) * 2 * n_cls);
+    const size_t table_bytes = 8 * (size_t)(g.S + 1) * (g.n + 1);
+    const size_t budget = 227 * 1024 - 1024;
+    if (prog_bytes + table_bytes + 2 * per_warp > budget) return;
+    c.warps = (int)std::min<size_t>(16, (budget - prog_bytes - table_bytes) / per_warp);
+    // cost per boundary configuration
+    double per_s = 20 + ceil32(ns) * (6 + 3.0 * n_cls);
+    double nnz_acc = 0, rows = 1;
+    double configs = 0;
+    for (size_t i = 0; i < k; ++i) {
+        const double hw = (double)(c.Sc[i] + 1) * (nc[i] + 1);
+        const double walk = std::ldexp(1.0, nc[i]);
+        configs += walk;
+        per_s += ceil32(nc[i]) * (4 + 3.0 * n_cls) + ceil32(hw) * 2 + nc[i] * (4 + 3.0 * n_cls) +
+                 std::max(1.0, walk / 32) * (8 + 3.0 * n_cls);
+        const double nnz_h = std::min(hw, walk);
+        if (i == 0) {
+            nnz_acc = nnz_h;
+        } else {
+            per_s += ceil32(hw) * 8 + ceil32(rows * MO) * 8 + std::ceil(nnz_acc / 256) * nnz_h * (3 + 8 * 3);
+            nnz_acc = std::min(nnz_acc * nnz_h, (rows + c.Sc[i]) * (double)MO);
+        }
+        rows += c.Sc[i];
+        per_s += ceil32(rows * MO) * 2;
+    }
+    per_s += ceil32((double)EO * MO) * 5;
+    c.visits = std::ldexp(configs, ns > 0 ? ns - 1 : 0);         // half the boundary: flip mirrors
+    c.cost = std::ldexp(per_s, ns > 0 ? ns - 1 : 0);
+}
+
+}  // namespace
+
+// The boundary set: the caller's (boundary != 0), or the cheapest under the work model among
+// (a) one or two windows of consecutive spin indices (cyclic), (b) the spins whose index lies in
+// a set of residues modulo p (2 <= p <= 8), (c) the complement of a greedy maximal independent
+// set. Windows and residues follow the lattices' index order, so rows, columns and layers are
+// among the candidates.
+SplitPlan plan_split(const isg_graph& g, uint64_t boundary, bool require_gain) {
+    const int n = g.n;
+    std::vector<int64_t> cls;
+    for (int64_t J : g.bJ) cls.push_back(J);
+    std::sort(cls.begin(), cls.end());
+    cls.erase(std::unique(cls.begin(), cls.end()), cls.end());
+    if ((int)cls.size() > kSplitMaxClasses)
+        fail(ISG_ERR_TOO_LARGE, "the split enumeration supports at most 16 distinct couplings");
+    const int n_cls = std::max<int>(1, (int)cls.size());
+    const std::vector<uint64_t> adj = adjacency(g);
+    const uint64_t all = low_mask(n);
+    Candidate best;
+    auto consider = [&](uint64_t S) {
+        S &= all;
+        Candidate c;
+        c.S = S;
+        c.comps = components(adj, all & ~S);
+        evaluate(g, n_cls, c);
+        if (c.cost < best.cost) best = std::move(c);
+    };
+    if (boundary) {
+        if (boundary & ~all) fail(ISG_ERR_INVALID, "boundary mask names spins beyond N");
+        consider(boundary);
+        if (!std::isfinite(best.cost))
+            fail(ISG_ERR_TOO_LARGE, "the given boundary leaves a component of more than 30 spins, more than 40 "
+                                    "boundary spins, or buffers beyond shared memory");
+    } else {
+        auto window = [&](int a, int w) {
+            uint64_t m = 0;
+            for (int i = 0; i < w; ++i) m |= 1ull << ((a + i) % n);
+            return m;
+        };
+        for (int w = 1; w <= n / 2; ++w)
+            for (int a = 0; a < n; ++a) {
+                const uint64_t w1 = window(a, w);
+                consider(w1);
+                for (int d = w + 1; d + w <= n; ++d) consider(w1 | window(a + d, w));
+            }
+        for (int p = 2; p <= 8 && p <= n; ++p)
+            for (uint32_t W = 1; W + 1 < (1u << p); ++W) {
+                uint64_t S = 0;
+                for (int i = 0; i < n; ++i) if ((W >> (i % p)) & 1) S |= 1ull << i;
+                consider(S);
+            }
+        {
+            std::vector<int> order(n);
+            for (int i = 0; i < n; ++i) order[i] = i;
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return popc(adj[a]) < popc(adj[b]); });
+            uint64_t I = 0, blocked = 0;
+            for (int i : order)
+                if (!((blocked >> i) & 1)) { I |= 1ull << i; blocked |= adj[i] | (1ull << i); }
+            consider(all & ~I);
+        }
+        if (!std::isfinite(best.cost)) fail(ISG_ERR_TOO_LARGE, "no boundary set gives components of at most 30 spins that fit");
+        if (require_gain && best.cost >= std::ldexp(2.86 / 32, n))
+            fail(ISG_ERR_TOO_LARGE, "no boundary set makes the split cheaper than the full enumeration for this graph");
+    }
+    SplitPlan p;
+    p.boundary = best.S;
+    for (int i = 0; i < n; ++i) if ((best.S >> i) & 1) p.S.push_back(i);
+    for (uint64_t c : best.comps) {
+        std::vector<int> v;
+        for (int i = 0; i < n; ++i) if ((c >> i) & 1) v.push_back(i);
+        p.comps.push_back(v);
+    }
+    p.visits = best.visits;
+    p.cost = best.cost;
+    p.direct_cost = std::ldexp(2.86 / 32, n);
+    p.use_u64 = best.u64;
+    p.warps = best.warps;
+    return p;
+}
+
+std::vector<uint64_t> build_split_program(const isg_graph& g, const SplitPlan& p) {
+    const int n = g.n, ns = (int)p.S.size(), k = (int)p.comps.size();
+    std::vector<int64_t> cls;
+    for (int64_t J : g.bJ) cls.push_back(J);
+    std::sort(cls.begin(), cls.end());
+    cls.erase(std::unique(cls.begin(), cls.end()), cls.end());
+    if (cls.empty()) cls.push_back(1);
+    const int n_cls = (int)cls.size();
+    auto coupling = [&](int i, int j) { return g.K[(size_t)i * n + j]; };
+    int n_in = 0;
+    for (const auto& c : p.comps) n_in += (int)c.size();
+    if (n_in + ns != n) fail(ISG_ERR_INTERNAL, "split plan does not cover every spin");
+    SplitHeader h{};
+    h.n = n; h.ns = ns; h.n_comp = k; h.n_cls = n_cls;
+    h.S_total = (int32_t)g.S;
+    h.off_cls = 8;
+    h.off_ss = h.off_cls + n_cls;
+    h.off_comp = h.off_ss + ns * n_cls;
+    h.off_spin = h.off_comp + 2 * k;                // a SplitComp record is two words
+    std::vector<uint64_t> blob((size_t)h.off_spin + (size_t)n_in * 2 * n_cls, 0);
+    int64_t S_SS = 0;
+    for (int a = 0; a < ns; ++a)
+        for (int b = a + 1; b < ns; ++b) S_SS += std::llabs(coupling(p.S[a], p.S[b]));
+    for (int t = 0; t < n_cls; ++t) std::memcpy(&blob[h.off_cls + t], &cls[t], 8);
+    for (int j = 0; j < ns; ++j)
+        for (int t = 0; t < n_cls; ++t) {
+            uint64_t m = 0;
+            for (int l = 0; l < ns; ++l) if (l != j && coupling(p.S[j], p.S[l]) == cls[t]) m |= 1ull << l;
+            blob[h.off_ss + (size_t)j * n_cls + t] = m;
+        }
+    int64_t EO = 1, MO = 1, hmax = 0, sumSc = 0;
+    int first = 0;
+    for (int c = 0; c < k; ++c) {
+        const auto& v = p.comps[c];
+        const int nc = (int)v.size();
+        int64_t Sc = 0;
+        for (int a = 0; a < nc; ++a) {
+            for (int b = a + 1; b < nc; ++b) Sc += std::llabs(coupling(v[a], v[b]));
+            for (int j = 0; j < ns; ++j) Sc += std::llabs(coupling(v[a], p.S[j]));
+        }
+        for (int c2 = 0; c2 < k; ++c2)            // no bond may join two components
+            if (c2 != c)
+                for (int a : v) for (int b : p.comps[c2])
+                    if (coupling(a, b)) fail(ISG_ERR_INTERNAL, "split components are not independent");
+        SplitComp rec{nc, (int32_t)Sc, first, (int32_t)((Sc + 1) * (nc + 1))};
+        static_assert(sizeof(SplitComp) == 16, "component record is two words");
+        std::memcpy(&blob[h.off_comp + 2 * (size_t)c], &rec, sizeof rec);
+        for (int a = 0; a < nc; ++a)
+            for (int t = 0; t < n_cls; ++t) {
+                uint64_t im = 0, sm = 0;
+                for (int b = 0; b < nc; ++b) if (b != a && coupling(v[a], v[b]) == cls[t]) im |= 1ull << b;
+                for (int j = 0; j < ns; ++j) if (coupling(v[a], p.S[j]) == cls[t]) sm |= 1ull << j;
+                const size_t o = h.off_spin + ((size_t)(first + a) * n_cls + t) * 2;
+                blob[o] = im;
+                blob[o + 1] = sm;
+            }
+        first += nc;
+        EO += Sc;
+        MO += nc;
+        sumSc += Sc;
+        hmax = std::max<int64_t>(hmax, (Sc + 1) * (nc + 1));
+    }
+    if (S_SS + sumSc != g.S) fail(ISG_ERR_INTERNAL, "split bond weights do not add up to the graph's");
+    h.S_SS = (int32_t)S_SS;
+    h.EO = (int32_t)EO;
+    h.MO = (int32_t)MO;
+    h.max_h = (int32_t)hmax;
+    h.acc_words = (int32_t)((EO + 1) * MO);
+    h.n_bins = (int32_t)((g.S + 1) * (n + 1));
+    std::memcpy(blob.data(), &h, sizeof h);
+    return blob;
+}
+
+// The split kernel's work, warp by warp and lane by lane, on the host with every index checked
+// (the device kernel follows the same steps; see split.cu).
+void emulate_split(const std::vector<uint64_t>& blob, int64_t* g_out) {
+    const SplitView v = split_view(blob.data());
+    const SplitHeader& h = *v.h;
+    // the device layout: 8-byte arrays at 8-byte aligned offsets, blocks at 16-byte multiples
+    for (bool u64 : {false, true}) {
+        const SplitWarpLayout L = split_warp_layout(h, u64);
+        const size_t base = split_prog_bytes((int)blob.size()) + split_table_bytes(h);
+        const size_t acc = (u64 ? 8 : 4) * (size_t)h.acc_words;
+        if (base % 16 || L.bytes % 16 || L.acc_a % 8 || L.acc_b % 8 || L.hlist % 8 || L.list % 4 || L.hist % 4 ||
+            L.acc_b < L.acc_a + acc || L.hlist < L.acc_b + acc || L.list < L.hlist + 8 * (size_t)h.max_h ||
+            L.hist < L.list + 4 * (size_t)h.acc_words || L.bytes < L.hist + 4 * (size_t)h.max_h)
+            fail(ISG_ERR_INTERNAL, "split kernel shared-memory layout misaligned or overlapping");
+    }
+    const int ncl = h.n_cls;
+    auto field = [&](const uint64_t* masks, int stride, uint64_t bits) {   // sum_t J_t (2 popc(m & bits) - popc(m))
+        int64_t f = 0;
+        for (int t = 0; t < ncl; ++t) {
+            const uint64_t m = masks[(size_t)t * stride];
+            f += v.cls[t] * (2 * split_popc64(m & bits) - split_popc64(m));
+        }
+        return f;
+    };
+    std::vector<uint64_t> acc((size_t)h.acc_words), out((size_t)h.acc_words);
+    std::vector<uint32_t> hist((size_t)h.max_h);
+    std::vector<uint32_t> list((size_t)h.acc_words);
+    const uint64_t n_s = 1ull << h.ns;
+    const uint64_t n_walk = h.ns ? n_s >> 1 : n_s;   // the others are global-flip mirrors
+    std::vector<uint64_t> hlist((size_t)h.max_h);
+    for (uint64_t s = 0; s < n_walk; ++s) {
+        int64_t two_neg_E = 0;                       // sum_j S_j a_j = -2 E_SS
+        for (int j = 0; j < h.ns; ++j) {
+            const int64_t a = field(v.ss + (size_t)j * ncl, 1, s);
+            two_neg_E += ((s >> j) & 1) ? a : -a;
+        }
+        if (two_neg_E & 1) fail(ISG_ERR_INTERNAL, "odd boundary energy");
+        const int64_t e_SS = (-two_neg_E / 2 + h.S_SS) / 2;
+        const int m_S = split_popc64(s);
+        if (e_SS < 0 || e_SS > h.S_SS) fail(ISG_ERR_INTERNAL, "boundary energy out of range");
+        int64_t rows = 0;                            // accumulator rows in use - 1
+        if (h.n_comp == 0) { std::fill(acc.begin(), acc.end(), 0); acc[0] = 1; }   // the empty convolution
+        for (int c = 0; c < h.n_comp; ++c) {
+            const SplitComp cp = v.comp[c];
+            const int nc = cp.nc, MC = nc + 1;
+            const uint64_t* sp = v.spin + (size_t)cp.first * ncl * 2;
+            std::vector<int64_t> f(nc);
+            for (int a = 0; a < nc; ++a) f[a] = field(sp + (size_t)a * ncl * 2 + 1, 2, s);
+            std::fill(hist.begin(), hist.end(), 0u);
+            const int L = nc > 5 ? nc - 5 : 0;
+            const int lanes = nc > 5 ? 32 : (1 << nc);
+            for (int lane = 0; lane < lanes; ++lane) {
+                uint32_t x = (uint32_t)lane << L;
+                int64_t twoE = 0;                    // 2 E_c(x) = -sum_a S_a (internal field + 2 f_a)
+                for (int a = 0; a < nc; ++a) {
+                    const int64_t hin = field(sp + (size_t)a * ncl * 2, 2, x);
+                    const int64_t sa = ((x >> a) & 1) ? 1 : -1;
+                    twoE -= sa * (hin + 2 * f[a]);
+                }
+                if ((twoE / 2 + cp.Sc) & 1) fail(ISG_ERR_INTERNAL, "component energy parity");
+                int64_t e = (twoE / 2 + cp.Sc) / 2;
+                int m = split_popc64(x);
+                for (uint32_t t = 0;; ++t) {
+                    if (e < 0 || e > cp.Sc || m < 0 || m > nc) fail(ISG_ERR_INTERNAL, "component bin out of range");
+                    hist[(size_t)e * MC + m] += 1;
+                    if (t + 1 >= (1u << L)) break;
+                    const int kk = __builtin_ctz(t + 1);
+                    const bool up = (x >> kk) & 1;
+                    const int64_t hk = field(sp + (size_t)kk * ncl * 2, 2, x) + f[kk];
+                    e += up ? hk : -hk;
+                    m += up ? -1 : 1;
+                    x ^= 1u << kk;
+                }
+            }
+            if (c == 0) {
+                std::fill(acc.begin(), acc.end(), 0);
+                for (int64_t e = 0; e <= cp.Sc; ++e)
+                    for (int m = 0; m < MC; ++m) acc[(size_t)e * h.MO + m] = hist[(size_t)e * MC + m];
+            } else {
+                const int64_t used = (rows + 1) * h.MO;
+                size_t nl = 0, nh = 0;
+                for (int64_t i = 0; i < used; ++i) if (acc[i]) list[nl++] = (uint32_t)i;
+                for (int64_t i = 0; i < (int64_t)cp.h_words; ++i)
+                    if (hist[i]) {
+                        const int64_t e1 = i / MC, m1 = i % MC;
+                        hlist[nh++] = (uint64_t)(uint32_t)(e1 * h.MO + m1) | ((uint64_t)hist[i] << 32);
+                    }
+                std::fill(out.begin(), out.end(), 0);
+                for (size_t q = 0; q < nl; ++q)
+                    for (size_t j = 0; j < nh; ++j) {
+                        const int64_t o = (int64_t)list[q] + (uint32_t)hlist[j];
+                        if (o >= h.acc_words) fail(ISG_ERR_INTERNAL, "convolution out of range");
+                        out[o] += (hlist[j] >> 32) * acc[list[q]];
+                    }
+                acc.swap(out);
+            }
+            rows += cp.Sc;
+        }
+        if (rows + 1 != h.EO) fail(ISG_ERR_INTERNAL, "accumulator rows");
+        for (int64_t i = 0; i < (int64_t)h.EO * h.MO; ++i) {
+            if (!acc[i]) continue;
+            const int64_t e = e_SS + i / h.MO, m = m_S + i % h.MO;
+            if (e > h.S_total || m > h.n) fail(ISG_ERR_INTERNAL, "table bin out of range");
+            g_out[e * (h.n + 1) + m] += (int64_t)acc[i];
+            if (h.ns) g_out[e * (h.n + 1) + (h.n - m)] += (int64_t)acc[i];
+        }
+    }
+}
+
+// Plans and programs of recent (graph, boundary) pairs: the boundary search costs milliseconds,
+// the enumeration of a small lattice microseconds. The key is the graph's content (N and its bond
+// list, compared in full on every hit), so graphs created separately share entries and a freed
+// handle's address cannot alias another graph.
+std::shared_ptr<const SplitPrepared> prepare_split(const isg_graph& g, uint64_t boundary, bool require_gain) {
+    static std::mutex mu;
+    static std::unordered_multimap<uint64_t, std::shared_ptr<const SplitPrepared>> cache;
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) { for (int b = 0; b < 8; ++b) { h ^= (v >> (8 * b)) & 0xff; h *= 1099511628211ull; } };
+    mix((uint64_t)g.n);
+    mix(boundary);
+    mix(require_gain ? 1 : 0);
+    for (size_t k = 0; k < g.bJ.size(); ++k) { mix((uint64_t)g.bi[k]); mix((uint64_t)g.bj[k]); mix((uint64_t)g.bJ[k]); }
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto range = cache.equal_range(h);
+        for (auto it = range.first; it != range.second; ++it) {
+            const SplitPrepared& e = *it->second;
+            if (e.n == g.n && e.boundary_arg == boundary && e.require_gain == require_gain && e.bi == g.bi &&
+                e.bj == g.bj && e.bJ == g.bJ)
+                return it->second;
+        }
+    }
+    auto e = std::make_shared<SplitPrepared>();
+    e->n = g.n;
+    e->bi = g.bi;
+    e->bj = g.bj;
+    e->bJ = g.bJ;
+    e->boundary_arg = boundary;
+    e->require_gain = require_gain;
+    e->plan = plan_split(g, boundary, require_gain);
+    e->blob = build_split_program(g, e->plan);
+    std::lock_guard<std::mutex> lk(mu);
+    if (cache.size() >= 256) cache.clear();
+    cache.emplace(h, e);
+    return e;
+}
+
+}  // namespace isg
+
+using namespace isg;
+
+extern "C" {
+
+isg_status isg_split_plan(const isg_graph* graph, uint64_t boundary, uint64_t* chosen, int32_t* n_components,
+                          int32_t* largest_component, double* visits, double* work_ratio) {
+    try {
+        clear_error();
+        if (!graph) fail(ISG_ERR_INVALID, "graph is NULL");
+        const std::shared_ptr<const SplitPrepared> e = prepare_split(*graph, boundary, false);
+        const SplitPlan& p = e->plan;
+        if (chosen) *chosen = p.boundary;
+        if (n_components) *n_components = (int32_t)p.comps.size();
+        if (largest_component) {
+            int32_t mx = 0;
+            for (const auto& c : p.comps) mx = std::max<int32_t>(mx, (int32_t)c.size());
+            *largest_component = mx;
+        }
+        if (visits) *visits = p.visits;
+        if (work_ratio) *work_ratio = p.cost / p.direct_cost;
+        return ISG_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return ISG_ERR_NOMEM;
+    } catch (...) {
+        set_error("unexpected exception");
+        return ISG_ERR_INTERNAL;
+    }
+}
+
+isg_status isg_debug_emulate_split(const isg_graph* graph, uint64_t boundary, int64_t* g_out) {
+    try {
+        clear_error();
+        if (!graph || !g_out) fail(ISG_ERR_INVALID, "NULL argument");
+        const std::shared_ptr<const SplitPrepared> e = prepare_split(*graph, boundary, false);
+        const std::vector<uint64_t>& blob = e->blob;
+        std::memset(g_out, 0, sizeof(int64_t) * (size_t)(graph->S + 1) * (graph->n + 1));
+        emulate_split(blob, g_out);
+        return ISG_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return ISG_ERR_NOMEM;
+    } catch (...) {
+        set_error("unexpected exception");
+        return ISG_ERR_INTERNAL;
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// split_internal.h -- split-and-convolve enumeration: the plan, the program layout shared by the
+// host (planner, program builder, emulation) and the device kernel.
+//
+// The method (a variant of the paper's full enumeration, Sec. 3, that visits fewer than 2^N
+// configurations): a boundary set S of spins is chosen whose removal leaves components C_1..C_k
+// with no bond between different components. For a fixed configuration s of S the components are
+// independent, so
+//   g(E, M) = sum_s  delta(E_SS(s), M_S(s)) * conv_c h_c(. | s),
+// where h_c(e_c, m_c | s) counts the configurations of C_c by their energy (bonds inside C_c and
+// between C_c and S, the latter through the field S exerts on each spin of C_c) and up count, and
+// conv is the 2-D convolution over (energy, up count). Bins: with S_c = sum |J| over the bonds
+// touching C_c, e_c = (E_c + S_c) / 2 in [0, S_c], m_c in [0, |C_c|]; the S part has
+// e_SS = (E_SS + S_SS) / 2, m_S = popcount(s); the table bin is (e_SS + sum e_c, m_S + sum m_c),
+// which is the public bin ((E + S) / 2, up count) because every bond lies in S x S, inside one
+// component, or between one component and S.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <memory>
+#include <vector>
+
+#include "../../include/isg.h"
+
+#ifdef __CUDACC__
+#define ISG_SPLIT_HD __host__ __device__
+#else
+#define ISG_SPLIT_HD
+#endif
+
+namespace isg {
+
+constexpr int kSplitMaxClasses = 16;     // distinct signed couplings
+constexpr int kSplitMaxComp = 64;
+constexpr int kSplitMaxCompSpins = 30;   // a component's configurations fit a 32-bit word walk
+
+// Program header (32-bit words at the start of the blob).
+struct SplitHeader {
+    int32_t n, ns, n_comp, n_cls;        // spins, boundary spins, components, coupling classes
+    int32_t S_total, S_SS, EO, MO;       // sum |J|; S x S part; convolution rows (sum S_c + 1), row stride (sum |C_c| + 1)
+    int32_t off_cls, off_ss, off_comp, off_spin;   // 64-bit word offsets of the sections below
+    int32_t max_h, acc_words, n_bins, reserved;    // largest component histogram; accumulator words per buffer; (S+1)(N+1)
+};
+static_assert(sizeof(SplitHeader) == 64, "header is 8 words");
+
+// Per component (two 64-bit words: four 32-bit fields).
+struct SplitComp {
+    int32_t nc, Sc, first, h_words;      // spins, sum |J| touching it, index of its first spin record, (Sc+1)(nc+1)
+};
+
+// Sections (64-bit words):
+//   cls[n_cls]                 signed coupling of each class (int64)
+//   ss[ns * n_cls]             for boundary spin j and class t: mask over boundary bits of its boundary
+//                              neighbours with that coupling
+//   comp[2 n_comp]             SplitComp records (two words each)
+//   spin[(sum nc) * 2 n_cls]   for component spin k (components in order) and class t: mask over the
+//                              component's own bits (internal neighbours), then mask over boundary bits
+struct SplitView {
+    const SplitHeader* h;
+    const int64_t* cls;
+    const uint64_t* ss;
+    const SplitComp* comp;
+    const uint64_t* spin;
+};
+
+ISG_SPLIT_HD inline SplitView split_view(const uint64_t* blob) {
+    SplitView v;
+    v.h = reinterpret_cast<const SplitHeader*>(blob);
+    v.cls = reinterpret_cast<const int64_t*>(blob + v.h->off_cls);
+    v.ss = blob + v.h->off_ss;
+    v.comp = reinterpret_cast<const SplitComp*>(blob + v.h->off_comp);
+    v.spin = blob + v.h->off_spin;
+    return v;
+}
+
+// Field on a spin from the spins in `bits` that its masks select: sum_t J_t (2 popc(mask_t & bits)
+// - popc(mask_t)), i.e. sum over those neighbours of J * S_j with S_j = +1 for a set bit.
+ISG_SPLIT_HD inline int64_t split_popc64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+    return __popcll(x);
+#else
+    return __builtin_popcountll(x);
+#endif
+}
+
+struct SplitPlan {
+    uint64_t boundary = 0;               // mask of boundary spins (graph indices)
+    std::vector<int> S;                  // boundary spins, boundary bit j <-> S[j]
+    std::vector<std::vector<int>> comps; // component spins, local bit k <-> comps[c][k]
+    double visits = 0;                   // configurations walked: 2^(|S|-1) * sum 2^|C_c| (flip mirrors)
+    double cost = 0, direct_cost = 0;    // model of the work, and of the full enumeration
+    bool use_u64 = false;                // accumulator counts may exceed 31 bits
+    int warps = 0;                       // warps per CTA whose buffers fit shared memory
+};
+
+// Host side (split_host.cpp).
+// boundary = 0: the cheapest admissible boundary set; with require_gain, refused (TOO_LARGE) unless
+// it is cheaper than the full enumeration under the work model.
+SplitPlan plan_split(const struct ::isg_graph& g, uint64_t boundary, bool require_gain);
+std::vector<uint64_t> build_split_program(const struct ::isg_graph& g, const SplitPlan& p);
+void emulate_split(const std::vector<uint64_t>& blob, int64_t* g_out);
+
+// A plan and its program for one graph content and boundary argument (cached).
+struct SplitPrepared {
+    int n = 0;
+    std::vector<int32_t> bi, bj;
+    std::vector<int64_t> bJ;
+    uint64_t boundary_arg = 0;
+    bool require_gain = false;
+    SplitPlan plan;
+    std::vector<uint64_t> blob;
+};
+std::shared_ptr<const SplitPrepared> prepare_split(const struct ::isg_graph& g, uint64_t boundary, bool require_gain);
+
+// Shared memory of the split kernel: the program, the CTA's table (32-bit low and high words per
+// bin), then per warp (each block 16-byte aligned): two accumulators, the histogram's nonzero
+// list (8-byte entries), the accumulator's nonzero list and a component histogram (4-byte
+// entries). The 8-byte arrays come first so that they stay 8-byte aligned whatever the sizes.
+struct SplitWarpLayout {
+    size_t acc_a, acc_b, hlist, list, hist, bytes;   // byte offsets within the warp's block; its size
+};
+ISG_SPLIT_HD inline SplitWarpLayout split_warp_layout(const SplitHeader& h, bool u64) {
+    SplitWarpLayout L;
+    const size_t acc = (u64 ? 8 : 4) * (size_t)h.acc_words;
+    L.acc_a = 0;
+    L.acc_b = (acc + 7) & ~(size_t)7;
+    L.hlist = L.acc_b + ((acc + 7) & ~(size_t)7);
+    L.list = L.hlist + 8 * (size_t)h.max_h;
+    L.hist = L.list + 4 * (size_t)h.acc_words;
+    L.bytes = (L.hist + 4 * (size_t)h.max_h + 15) & ~(size_t)15;
+    return L;
+}
+ISG_SPLIT_HD inline size_t split_prog_bytes(int blob_words) { return ((size_t)blob_words * 8 + 15) & ~(size_t)15; }
+ISG_SPLIT_HD inline size_t split_table_bytes(const SplitHeader& h) { return (8 * (size_t)h.n_bins + 15) & ~(size_t)15; }
+ISG_SPLIT_HD inline size_t split_warp_bytes(const SplitHeader& h, bool u64) { return split_warp_layout(h, u64).bytes; }
+ISG_SPLIT_HD inline size_t split_smem_bytes(int blob_words, const SplitHeader& h, bool u64, int warps) {
+    return split_prog_bytes(blob_words) + split_table_bytes(h) + (size_t)warps * split_warp_bytes(h, u64);
+}
+
+}  // namespace isg

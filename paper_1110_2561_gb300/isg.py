@@ -46,6 +46,10 @@ _SIGS = {
     "isg_graph_bins": (i32, [vp, vp, vp, vp, vp, vp]),
     "isg_graph_size": (i32, [vp, vp, vp]),
     "isg_enumerate": (i32, [vp, vp, vp, i32, vp]),
+    "isg_enumerate_split": (i32, [vp, vp, vp, i32, ctypes.c_uint64]),
+    "isg_split_plan": (i32, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i32),
+                             ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "isg_debug_emulate_split": (i32, [vp, ctypes.c_uint64, vp]),
     "isg_thermo": (i32, [vp, i32, vp, i32, vp, i32, vp, i32, vp, i32, vp, vp, vp, vp, vp]),
     "isg_magnetisation": (i32, [vp, i32, vp, i32, vp, i32, vp, i32, vp, i32, vp, vp, vp, vp]),
     "isg_last_error": (ctypes.c_char_p, []),
@@ -219,6 +223,42 @@ def isg_enumerate_noalloc(graph: Graph, g_out, stream=None, **options):
     o = _options(**options)
     _check(lib().isg_enumerate_noalloc(graph, _stream_handle(stream), g_out.data_ptr(), ctypes.byref(o)))
     return g_out
+
+
+def isg_enumerate_split(graph: Graph, g_out=None, stream=None, boundary: int = 0):
+    """The exact g(E, M) by split-and-convolve (a variant of the full enumeration that visits
+    2^(|S|-1) * sum 2^|C| configurations; see isg_split_plan). g_out as for isg_enumerate (the table is
+    overwritten). boundary: a mask of boundary spins, or 0 for the library's choice."""
+    shape = table_shape(graph)
+    if g_out is None:
+        g_out = np.zeros(shape, dtype=np.int64)
+    if isinstance(g_out, np.ndarray):
+        if g_out.dtype != np.int64 or not g_out.flags.c_contiguous or g_out.shape != shape:
+            raise ValueError(f"g_out must be a C-contiguous int64 array of shape {shape}")
+        _check(lib().isg_enumerate_split(graph, _stream_handle(stream) if stream is not None else None,
+                                         g_out.ctypes.data, 0, boundary))
+        return g_out
+    _check_tensor(g_out, shape, "int64")
+    _check(lib().isg_enumerate_split(graph, _stream_handle(stream), g_out.data_ptr(), 1, boundary))
+    return g_out
+
+
+def isg_split_plan(graph: Graph, boundary: int = 0) -> dict:
+    """The boundary set and cost isg_enumerate_split would use (host only)."""
+    chosen = ctypes.c_uint64()
+    nc, big = ctypes.c_int32(), ctypes.c_int32()
+    visits, ratio = ctypes.c_double(), ctypes.c_double()
+    _check(lib().isg_split_plan(graph, boundary, ctypes.byref(chosen), ctypes.byref(nc), ctypes.byref(big),
+                                ctypes.byref(visits), ctypes.byref(ratio)))
+    return {"boundary": chosen.value, "boundary_spins": bin(chosen.value).count("1"), "components": nc.value,
+            "largest_component": big.value, "visits": visits.value, "work_ratio": ratio.value}
+
+
+def isg_debug_emulate_split(graph: Graph, boundary: int = 0) -> np.ndarray:
+    """The split kernel's work run on the host with every index checked (small graphs only)."""
+    g = np.zeros(table_shape(graph), dtype=np.int64)
+    _check(lib().isg_debug_emulate_split(graph, boundary, g.ctypes.data))
+    return g
 
 
 def _graph_array(graphs):

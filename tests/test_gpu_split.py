@@ -1,0 +1,103 @@
+"""Split-and-convolve enumeration on the GPU (isg_enumerate_split): exact tables against the
+oracle's full enumeration, its frontier programme, and the direct GPU enumeration."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1110_2561_gb300 import workloads as w
+from closed_forms import kaufman_logz
+from test_split_host import CASES, mask
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("lat,boundary", CASES, ids=[c[0].name or "free-spins" for c in CASES])
+def test_split_small_graphs(isg, cuda, lat, boundary):
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    # small graphs: the automatic choice is refused (no gain), so pass the planner's set explicitly
+    # (an empty set, chosen for a graph without bonds, is written as spin 0 alone)
+    boundary = boundary or isg.isg_split_plan(gh)["boundary"] or 1
+    assert np.array_equal(isg.isg_enumerate_split(gh, boundary=boundary), oracle.g_masks(lat.n, lat.edges))
+
+
+def test_split_table1(isg, cuda, table1_triples):
+    lat = w.square(4, 4, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = isg.isg_enumerate_split(gh, boundary=mask(range(0, 4)) | mask(range(8, 12)))
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    assert {(int(g[e, m]), -lat.n + 2 * m, e_min + 2 * e) for e, m in zip(*np.nonzero(g))} == set(table1_triples)
+
+
+def test_split_torus_6x6(isg, cuda):
+    """The 6x6 torus with the library's boundary (two rows): every bin against the frontier oracle,
+    into a device tensor and into host memory."""
+    import torch
+    lat = w.square(6, 6, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    ref = oracle.g_frontier(lat.n, lat.edges, 16)
+    assert np.array_equal(isg.isg_enumerate_split(gh), ref)
+    g = torch.full(isg.table_shape(gh), 7, dtype=torch.int64, device=cuda)      # overwritten
+    isg.isg_enumerate_split(gh, g)
+    torch.cuda.synchronize()
+    assert np.array_equal(g.cpu().numpy(), ref)
+
+
+def test_split_cubic_against_direct(isg, cuda):
+    """3x3x4 cubic torus: the split table equals the direct enumeration's (itself parity-tested)."""
+    lat = w.cubic(3, 3, 4, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    assert np.array_equal(isg.isg_enumerate_split(gh), isg.isg_enumerate(gh))
+
+
+def test_split_ea_instances(isg, cuda):
+    """Edwards-Anderson +-J instances of every shape, against the frontier oracle."""
+    lats = w.ea_instances()
+    for lat in [next(l for l in lats if l.n == n) for n in (16, 20, 25, 30)]:
+        gh = isg.isg_graph_create(lat.n, lat.edges)
+        b = isg.isg_split_plan(gh)["boundary"]          # explicit: small instances gain nothing automatically
+        assert np.array_equal(isg.isg_enumerate_split(gh, boundary=b), oracle.g_frontier(lat.n, lat.edges, 16)), lat.name
+
+
+def test_split_serving_mix(isg, cuda):
+    """Request-stream graphs (square / triangular / cubic, periodic or free, J in {+-1, +-2})."""
+    reqs = w.serving_stream(40)
+    done = 0
+    for r in reqs:
+        lat = r.lattice
+        if lat.n > 26:
+            continue
+        gh = isg.isg_graph_create(lat.n, lat.edges)
+        try:
+            got = isg.isg_enumerate_split(gh)
+        except isg.IsgError as e:
+            assert "TOO_LARGE" in str(e)        # no boundary cheaper than the full enumeration
+            continue
+        assert np.array_equal(got, oracle.g_frontier(lat.n, lat.edges, 20)), lat.name
+        done += 1
+    assert done >= 3
+
+
+def test_split_torus_7x7(isg, cuda):
+    """The 7x7 torus, N = 49 (2^49 configurations): every bin against the oracle's frontier
+    programme, and ln Z against Kaufman's closed form."""
+    lat = w.square(7, 7, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = isg.isg_enumerate_split(gh)
+    assert int(g.sum()) == 2 ** 49
+    assert all(int(g[:, m].sum()) == math.comb(49, m) for m in range(50))
+    assert np.array_equal(g, oracle.g_frontier(lat.n, lat.edges, 16))
+    T = np.array([1.0, 2.269, 3.5])
+    lz = isg.isg_thermo(g, gh, T, [0.0], isg.ISG_FP64)[0][:, 0]
+    for t, l in zip(T, lz):
+        assert abs(l - kaufman_logz(7, 7, t)) <= 1e-12 * abs(l)
+
+
+def test_split_rejects(isg, cuda):
+    lat = w.square(4, 4, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    with pytest.raises(isg.IsgError, match="TOO_LARGE"):
+        isg.isg_enumerate_split(gh)              # a 16-spin lattice: no boundary beats the full walk
+    with pytest.raises(isg.IsgError, match="INVALID"):
+        isg.isg_enumerate_split(gh, boundary=1 << 20)
