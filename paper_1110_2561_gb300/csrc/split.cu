@@ -51,7 +51,9 @@ __device__ __forceinline__ int split_field(const int64_t* cls, int ncl, const ui
     return f;
 }
 
-template <class Acc>
+// kFew: at most two coupling classes (every lattice here: J = 1, or +-J), so a spin's field is
+// two masked popcounts of a 32-bit component word and a constant; otherwise a loop over classes.
+template <class Acc, bool kFew>
 __global__ void __launch_bounds__(512) split_kernel(const __grid_constant__ SplitArgs a) {
     extern __shared__ __align__(16) unsigned char sm[];
     uint64_t* prog = reinterpret_cast<uint64_t*>(sm);
@@ -72,6 +74,8 @@ __global__ void __launch_bounds__(512) split_kernel(const __grid_constant__ Spli
     uint64_t* hlist = reinterpret_cast<uint64_t*>(wbase + WL.hlist);
     uint32_t* list = reinterpret_cast<uint32_t*>(wbase + WL.list);
     uint32_t* hist = reinterpret_cast<uint32_t*>(wbase + WL.hist);
+    uint4* wsp = reinterpret_cast<uint4*>(wbase + WL.spins);     // per component spin: masks, constant, field
+    const int J0 = (int)v.cls[0], J1 = ncl > 1 ? (int)v.cls[1] : 0;
     for (int i = threadIdx.x; i < 2 * H.n_bins; i += blockDim.x) tlo[i] = 0;
     __syncthreads();
     auto table_add = [&](int i, unsigned long long v) {
@@ -109,21 +113,38 @@ __global__ void __launch_bounds__(512) split_kernel(const __grid_constant__ Spli
             const SplitComp cp = v.comp[c];
             const int nc = cp.nc, MC = nc + 1;
             const uint64_t* sp = v.spin + (size_t)cp.first * ncl * 2;
-            // field on component spin `lane` from the boundary (nc <= 30)
+            // field on component spin `lane` from the boundary (nc <= 30); with few classes its
+            // record {mask of class 0, mask of class 1, f - J0 deg0 - J1 deg1, f} in shared memory,
+            // so that field(x) = 2 (J0 popc(m0 & x) + J1 popc(m1 & x)) + constant
             const int myf = lane < nc ? split_field(v.cls, ncl, sp + (size_t)lane * ncl * 2 + 1, 2, s) : 0;
+            if (kFew && lane < nc) {
+                const uint32_t m0 = (uint32_t)sp[(size_t)lane * ncl * 2];
+                const uint32_t m1 = ncl > 1 ? (uint32_t)sp[((size_t)lane * ncl + 1) * 2] : 0u;
+                wsp[lane] = make_uint4(m0, m1, (uint32_t)(myf - J0 * __popc(m0) - J1 * __popc(m1)), (uint32_t)myf);
+            }
             for (int i = lane; i < cp.h_words; i += 32) hist[i] = 0;
             __syncwarp();
+            // internal field plus boundary field of component spin q at configuration x
+            auto field = [&](int q, uint32_t xx) -> int {
+                if (kFew) {
+                    const uint4 r = wsp[q];
+                    return 2 * (J0 * __popc(r.x & xx) + J1 * __popc(r.y & xx)) + (int)r.z;
+                }
+                return split_field(v.cls, ncl, sp + (size_t)q * ncl * 2, 2, xx) + __shfl_sync(FULL, myf, q);
+            };
+            auto twice_energy = [&](uint32_t xx) {        // 2 E_c = -sum_q S_q (internal_q + 2 f_q)
+                int t2 = 0;
+                for (int q = 0; q < nc; ++q) {
+                    const int fq = kFew ? (int)wsp[q].w : __shfl_sync(FULL, myf, q);
+                    const int hq = field(q, xx) + fq;
+                    t2 -= ((xx >> q) & 1) ? hq : -hq;
+                }
+                return t2;
+            };
             const int L = nc > 5 ? nc - 5 : 0;
             const bool active = nc > 5 || lane < (1 << nc);
             uint32_t x = (uint32_t)lane << L;
-            // 2 E_c(x) = -sum_q S_q (internal field_q + 2 f_q), from scratch
-            int twoE = 0;
-            for (int q = 0; q < nc; ++q) {
-                const int fq = __shfl_sync(FULL, myf, q);
-                const int hin = split_field(v.cls, ncl, sp + (size_t)q * ncl * 2, 2, x);
-                twoE -= ((x >> q) & 1) ? hin + 2 * fq : -(hin + 2 * fq);
-            }
-            int e = (twoE / 2 + cp.Sc) / 2;
+            int e = (twice_energy(x) / 2 + cp.Sc) / 2;
             int m = __popc(x);
             // a bin outside the histogram (a bug) is recorded and skipped, never written
             auto count = [&](int ee, int mm) {
@@ -134,22 +155,16 @@ __global__ void __launch_bounds__(512) split_kernel(const __grid_constant__ Spli
             for (uint32_t t = 1; t < (1u << L); ++t) {
                 const int k = __ffs(t) - 1;                          // the same spin in every lane
                 const bool up = (x >> k) & 1;
-                const int hk = split_field(v.cls, ncl, sp + (size_t)k * ncl * 2, 2, x) + __shfl_sync(FULL, myf, k);
+                const int hk = field(k, x);
                 e += up ? hk : -hk;
                 m += up ? -1 : 1;
                 x ^= 1u << k;
                 count(e, m);
             }
             // self-check: the tracked bin of the lane's last configuration against a recomputation
-            {
-                int twoE2 = 0;
-                for (int q = 0; q < nc; ++q) {
-                    const int fq = __shfl_sync(FULL, myf, q);
-                    const int hin = split_field(v.cls, ncl, sp + (size_t)q * ncl * 2, 2, x);
-                    twoE2 -= ((x >> q) & 1) ? hin + 2 * fq : -(hin + 2 * fq);
-                }
-                if (active && (e != (twoE2 / 2 + cp.Sc) / 2 || m != __popc(x))) bad = true;
-            }
+            // (computed in every lane: the recomputation may shuffle across the whole warp)
+            const int e_check = (twice_energy(x) / 2 + cp.Sc) / 2;
+            if (active && (e != e_check || m != __popc(x))) bad = true;
             __syncwarp();
             if (c == 0) {
                 for (int i = lane; i < H.acc_words; i += 32) acc[i] = 0;
@@ -171,16 +186,16 @@ __global__ void __launch_bounds__(512) split_kernel(const __grid_constant__ Spli
                 }
                 // the histogram's nonzero bins as (shift in the accumulator's layout, count)
                 int nh = 0;
+                int e1 = lane / MC, m1 = lane - e1 * MC;       // (row, column) of bin `lane`, stepped by 32
                 for (int base = 0; base < cp.h_words; base += 32) {
                     const int i = base + lane;
                     const uint32_t hv = i < cp.h_words ? hist[i] : 0u;
                     const unsigned bal = __ballot_sync(FULL, hv != 0);
-                    if (hv) {
-                        const int e1 = i / MC, m1 = i - e1 * MC;
+                    if (hv)
                         hlist[nh + __popc(bal & ((1u << lane) - 1u))] =
                             (uint64_t)(uint32_t)(e1 * MO + m1) | ((uint64_t)hv << 32);
-                    }
                     nh += __popc(bal);
+                    for (m1 += 32; m1 >= MC; m1 -= MC) ++e1;
                 }
                 for (int i = lane; i < H.acc_words; i += 32) out[i] = 0;
                 __syncwarp();
@@ -216,10 +231,11 @@ __global__ void __launch_bounds__(512) split_kernel(const __grid_constant__ Spli
         }
         // shift by the boundary's bin and add into the CTA's table
         const int used = H.EO * MO;
-        for (int i = lane; i < used; i += 32) {
+        int e1 = lane / MO, m1 = lane - e1 * MO;
+        for (int i = lane; i < used; i += 32, m1 += 32) {
+            for (; m1 >= MO; m1 -= MO) ++e1;
             const Acc val = acc[i];
             if (val) {
-                const int e1 = i / MO, m1 = i - e1 * MO;
                 const int row = (e_SS + e1) * (H.n + 1);
                 table_add(row + m_S + m1, (unsigned long long)val);
                 if (H.ns) table_add(row + H.n - m_S - m1, (unsigned long long)val);
@@ -285,12 +301,17 @@ extern "C" isg_status isg_enumerate_split(const isg_graph* graph, void* stream, 
         ISG_CUDA(cudaMemsetAsync(table, 0, table_bytes, s));
         SplitArgs a{reinterpret_cast<const uint64_t*>(scratch + o_blob), (int)blob.size(), table,
                     reinterpret_cast<unsigned int*>(scratch), n_s};
+        auto launch = [&](auto kernel) {
+            ISG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kernel<<<grid, 32 * warps, smem, s>>>(a);
+        };
+        const bool few = H.n_cls <= 2;
         if (p.use_u64) {
-            ISG_CUDA(cudaFuncSetAttribute(split_kernel<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            split_kernel<unsigned long long><<<grid, 32 * warps, smem, s>>>(a);
+            if (few) launch(split_kernel<unsigned long long, true>);
+            else launch(split_kernel<unsigned long long, false>);
         } else {
-            ISG_CUDA(cudaFuncSetAttribute(split_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            split_kernel<uint32_t><<<grid, 32 * warps, smem, s>>>(a);
+            if (few) launch(split_kernel<uint32_t, true>);
+            else launch(split_kernel<uint32_t, false>);
         }
         ISG_CUDA(cudaGetLastError());
         if (!g_out_on_device) {

@@ -109,7 +109,7 @@ void evaluate(const isg_graph& g, int n_cls, Candidate& c) {
     c.u64 = inner > 31;
     const int64_t acc_words = (EO + 1) * MO;
     const size_t acc_bytes = c.u64 ? 8 : 4;
-    const size_t per_warp = 12 * (size_t)hmax + 32 + (2 * acc_bytes + 4) * (size_t)acc_words;
+    const size_t per_warp = 512 + 12 * (size_t)hmax + 32 + (2 * acc_bytes + 4) * (size_t)acc_words;
     const size_t prog_bytes = 64 + 8 * ((size_t)n_cls * (1 + ns) + 2 * k + (size_t)(g.n - ns) * 2 * n_cls);
     const size_t table_bytes = 8 * (size_t)(g.S + 1) * (g.n + 1);
     const size_t budget = 227 * 1024 - 1024;
@@ -303,7 +303,7 @@ void emulate_split(const std::vector<uint64_t>& blob, int64_t* g_out) {
         const SplitWarpLayout L = split_warp_layout(h, u64);
         const size_t base = split_prog_bytes((int)blob.size()) + split_table_bytes(h);
         const size_t acc = (u64 ? 8 : 4) * (size_t)h.acc_words;
-        if (base % 16 || L.bytes % 16 || L.acc_a % 8 || L.acc_b % 8 || L.hlist % 8 || L.list % 4 || L.hist % 4 ||
+        if (base % 16 || L.bytes % 16 || L.spins % 16 || L.acc_a < L.spins + 16 * 32 || L.acc_a % 8 || L.acc_b % 8 || L.hlist % 8 || L.list % 4 || L.hist % 4 ||
             L.acc_b < L.acc_a + acc || L.hlist < L.acc_b + acc || L.list < L.hlist + 8 * (size_t)h.max_h ||
             L.hist < L.list + 4 * (size_t)h.acc_words || L.bytes < L.hist + 4 * (size_t)h.max_h)
             fail(ISG_ERR_INTERNAL, "split kernel shared-memory layout misaligned or overlapping");

@@ -112,17 +112,18 @@ struct SplitPrepared {
 std::shared_ptr<const SplitPrepared> prepare_split(const struct ::isg_graph& g, uint64_t boundary, bool require_gain);
 
 // Shared memory of the split kernel: the program, the CTA's table (32-bit low and high words per
-// bin), then per warp (each block 16-byte aligned): two accumulators, the histogram's nonzero
+// bin), then per warp (each block 16-byte aligned): 32 component-spin records, two accumulators, the histogram's nonzero
 // list (8-byte entries), the accumulator's nonzero list and a component histogram (4-byte
 // entries). The 8-byte arrays come first so that they stay 8-byte aligned whatever the sizes.
 struct SplitWarpLayout {
-    size_t acc_a, acc_b, hlist, list, hist, bytes;   // byte offsets within the warp's block; its size
+    size_t spins, acc_a, acc_b, hlist, list, hist, bytes;   // byte offsets within the warp's block; its size
 };
 ISG_SPLIT_HD inline SplitWarpLayout split_warp_layout(const SplitHeader& h, bool u64) {
     SplitWarpLayout L;
     const size_t acc = (u64 ? 8 : 4) * (size_t)h.acc_words;
-    L.acc_a = 0;
-    L.acc_b = (acc + 7) & ~(size_t)7;
+    L.spins = 0;                                      // 32 records of 16 bytes (component spins)
+    L.acc_a = 512;
+    L.acc_b = L.acc_a + ((acc + 7) & ~(size_t)7);
     L.hlist = L.acc_b + ((acc + 7) & ~(size_t)7);
     L.list = L.hlist + 8 * (size_t)h.max_h;
     L.hist = L.list + 4 * (size_t)h.acc_words;
