@@ -230,6 +230,7 @@ def run_isg(args):
         sm_max = clocks.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or SM_MAX_MHZ_FALLBACK
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         alu_peak = sms * 4 * 32 * sm_max * 1e6                     # 4 schedulers x 32 lanes per SM per clock
+        red_peak = sms * 32 * sm_max * 1e6                         # one 32-lane shared reduction per SM per clock
         achieved_ops = OPS_PER_CONFIG * n_configs / enum_s
         traffic = TRAFFIC_BYTES if TRAFFIC_SOURCES_SHA == kernel_sources_sha() else None
         line = {
@@ -242,16 +243,21 @@ def run_isg(args):
                        "plan": {k: plan[k] for k in ("q", "b", "tasks", "threads", "copies", "ctas_per_sm", "G",
                                                      "n_e_compact", "stride")},
                        "autotuned": tuned_fields},
-            "roofline": {"bound": "alu", "achieved": achieved_ops / 1e9, "peak": alu_peak / 1e9, "unit": "Gop/s",
-                         "frac": achieved_ops / alu_peak, "traffic": traffic,
-                         "kernel": f"enumerate_kernel<{plan['b']}>", "ops_per_config": OPS_PER_CONFIG,
-                         "peak_source": f"{sms} SMs x 128 lanes/clk x {sm_max:.0f} MHz (unit counts and clock)"},
-            "roofline_smem_atomic": {"bound": "smem_atomic", "achieved": n_configs / enum_s / 1e9,
-                                     "peak": peaks["red_conflict_free"] / 1e9,
-                                     "peak_scattered": peaks["red_scattered"] / 1e9,
-                                     "match_any_aggregated": peaks["match_aggregated"] / 1e9, "unit": "Gred/s",
-                                     "frac": n_configs / enum_s / peaks["red_conflict_free"],
-                                     "peak_source": "isg_probe_peaks (red.shared.add.u32, measured in this run)"},
+            # the binding unit: one shared-memory reduction per configuration; the shared-memory
+            # pipe executes one warp-wide (32-lane) reduction per clock per SM
+            "roofline": {"bound": "smem_atomic", "achieved": n_configs / enum_s / 1e9,
+                         "peak": red_peak / 1e9, "unit": "Gred/s", "frac": n_configs / enum_s / red_peak,
+                         "traffic": traffic, "kernel": f"enumerate_kernel<{plan['b']}>",
+                         "work_per_config": "1 red.shared.add.u32 (plus 1 integer add)",
+                         "peak_source": f"{sms} SMs x 32 lanes/clk x {sm_max:.0f} MHz (unit counts and clock)",
+                         "peak_measured": peaks["red_conflict_free"] / 1e9,
+                         "frac_of_measured": n_configs / enum_s / peaks["red_conflict_free"],
+                         "peak_measured_scattered": peaks["red_scattered"] / 1e9,
+                         "match_any_aggregated": peaks["match_aggregated"] / 1e9,
+                         "peak_measured_source": "isg_probe_peaks (red.shared.add.u32, measured in this run)"},
+            "roofline_alu": {"bound": "alu", "achieved": achieved_ops / 1e9, "peak": alu_peak / 1e9, "unit": "Gop/s",
+                             "frac": achieved_ops / alu_peak, "ops_per_config": OPS_PER_CONFIG,
+                             "peak_source": f"{sms} SMs x 128 lanes/clk x {sm_max:.0f} MHz (unit counts and clock)"},
             "enumerate_ms": statistics.mean(enum_ms), "thermo_ms": statistics.mean(
                 [b.elapsed_time(c) for a, b, c in evs]),
             "e2e": {"value": world * n_configs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

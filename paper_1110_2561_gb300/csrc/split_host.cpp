@@ -137,7 +137,9 @@ void evaluate(const isg_graph& g, int n_cls, Candidate& c) {
     }
     per_s += ceil32((double)EO * MO) * 5;
     c.visits = std::ldexp(configs, ns > 0 ? ns - 1 : 0);         // half the boundary: flip mirrors
-    c.cost = std::ldexp(per_s, ns > 0 ? ns - 1 : 0);
+    // the walk and the convolution are latency-bound: fewer than 8 warps per SM (large buffers)
+    // leave issue slots empty in proportion
+    c.cost = std::ldexp(per_s, ns > 0 ? ns - 1 : 0) * (8.0 / std::min(8, c.warps));
 }
 
 }  // namespace
