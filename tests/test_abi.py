@@ -132,3 +132,15 @@ def test_emulated_accumulate(isg):
     a = isg.isg_debug_emulate(g, shard_bits=1, shard_lo=0, shard_hi=1)
     b = isg.isg_debug_emulate(g, shard_bits=1, shard_lo=1, shard_hi=2)
     assert np.array_equal(a + b, ref)
+
+
+def test_smoke_calls_are_valid_plans(isg):
+    """The calls __graft_entry__.smoke() makes on the GPU pass the host-side planning: the 4x4 free
+    lattice goes through the main Gray-walk kernel (not the small-graph kernel), and the split
+    call's boundary (the second row) is admissible."""
+    from paper_1110_2561_gb300 import workloads as w
+    lat = w.square(4, 4, False)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    assert isg.isg_debug_plan(gh)["small"] == 0
+    p = isg.isg_split_plan(gh, 0xF0)
+    assert p["boundary"] == 0xF0 and p["components"] == 2
