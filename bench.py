@@ -528,7 +528,7 @@ def run_serving(args):
     torch.cuda.set_device(0)
     reqs = workloads.serving_stream(args.requests, rate_per_s=args.rate)
     graphs = [isg.isg_graph_create(r.lattice.n, r.lattice.edges) for r in reqs]
-    srv = isg.Server(step_ms=args.step_ms)
+    srv = isg.Server(step_ms=args.step_ms, split_work_ratio=args.split_ratio)
     warm = srv.submit(isg.isg_graph_create(20, workloads.square(4, 5, True).edges))
     srv.wait(warm)
     srv.result(warm)
@@ -568,6 +568,7 @@ def run_serving(args):
         "device_busy_frac": st["device_ms"] * 1e-3 / max(1e-9, time.perf_counter() - t0),
         "device_configs_per_s": st["configs"] / max(1e-9, st["device_ms"] * 1e-3),
         "steps": int(st["steps"]), "step_ms": args.step_ms, "invariant_failures": bad,
+        "split_work_ratio": args.split_ratio,
     }
     print(json.dumps(line), flush=True)
 
@@ -631,6 +632,8 @@ def main():
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--step-ms", type=float, default=20.0)
+    ap.add_argument("--split-ratio", type=float, default=0.0,
+                    help="serving: serve requests whose split-and-convolve work is below this fraction by split launches")
     ap.add_argument("--shard-bits", type=int, default=0,
                     help="profiling case: enumerate only shard 0 of 2^k per step (not a benchmark line)")
     args = ap.parse_args()

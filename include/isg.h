@@ -311,6 +311,11 @@ typedef struct {
     double step_ms;          /* device time per engine step (default 20 ms) */
     int32_t block_threads;   /* threads per CTA of the batched kernel, <= 512 (0 = 512) */
     int32_t ctas_per_sm;     /* 0 = 2 */
+    double split_work_ratio; /* 0 (default): every request is enumerated configuration by configuration.
+                                r in (0, 1]: a request of at least 24 spins whose split-and-convolve
+                                plan (isg_enumerate_split) models less than r of that work is served
+                                by one split launch instead; planned at submit, a few milliseconds
+                                of host time. The table is the same either way. */
 } isg_server_options;
 
 ISG_API void isg_server_options_init(isg_server_options* opt);

@@ -28,10 +28,13 @@
 #include "batch_internal.h"
 #include "isg_internal.h"
 #include "nvtx_range.h"
+#include "split_internal.h"
 
 namespace isg {
 
 DeviceInfo device_info();
+
+constexpr int kSplitMinSpins = 24;     // below this the tile path takes microseconds anyway
 
 using Clock = std::chrono::steady_clock;
 
@@ -47,7 +50,8 @@ struct Request {
     int b = 0;                       // low-block size of its program (0: small kernel)
     int q = 0;
     int bins = 0;                    // compact histogram bins (stride included)
-    std::vector<uint64_t> blob;
+    std::vector<uint64_t> blob;      // tile program, or the split program when `split` is set
+    std::shared_ptr<const SplitPrepared> split;   // served by split-and-convolve (one launch)
     size_t table_words = 0;          // public table
     uint64_t total_tasks = 0, next_task = 0;
     double configs = 0;
@@ -205,15 +209,19 @@ static bool issue_step_locked(isg_server* s) {
     uint64_t tiles = 0;
     double used = 0;
     std::vector<BatchInst> large, small;
-    std::vector<Request*> large_r, small_r;
+    std::vector<Request*> large_r, small_r, split_r;
     for (Request* r : order) {
-        if (used >= budget && !large.empty()) break;
+        if (used >= budget && (!large.empty() || !split_r.empty())) break;
         BatchInst in{};
         in.g = reinterpret_cast<int64_t*>(s->arena_dev + r->slot_off);
         const size_t tbytes = ((r->table_words * 8) + 255) & ~(size_t)255;
         in.blob_off = (uint32_t)((r->slot_off + tbytes) / 8);
         in.blob_words = (uint32_t)r->blob.size();
-        if (!r->b) {                                   // whole request in the small kernel
+        if (r->split) {                                // whole request in one split launch
+            split_r.push_back(r);
+            used += r->configs;
+            r->next_task = r->total_tasks;
+        } else if (!r->b) {                            // whole request in the small kernel
             small.push_back(in);
             small_r.push_back(r);
             used += r->configs;
@@ -266,8 +274,15 @@ static bool issue_step_locked(isg_server* s) {
         server_fail_cuda(cudaMemcpyAsync(s->small_dev[buf], s->small_host[buf], sizeof(int) * bp.small_ids.size(),
                                          cudaMemcpyHostToDevice, s->stream), "cudaMemcpyAsync(small ids)");
     server_fail_cuda(cudaMemsetAsync(s->ctr_dev[buf], 0, 16, s->stream), "cudaMemsetAsync(counter)");
-    launch_batch(bp, s->desc_dev[buf], reinterpret_cast<const uint64_t*>(s->arena_dev), s->small_dev[buf], s->ctr_dev[buf],
-                 reinterpret_cast<unsigned int*>(s->ctr_dev[buf] + 1), s->stream, s->opt.ctas_per_sm > 0 ? s->opt.ctas_per_sm : 2);
+    unsigned int* status = reinterpret_cast<unsigned int*>(s->ctr_dev[buf] + 1);
+    for (Request* r : split_r) {                       // split requests first: each one launch, table in its slot
+        const size_t tbytes = ((r->table_words * 8) + 255) & ~(size_t)255;
+        launch_split(*r->split, reinterpret_cast<const uint64_t*>(s->arena_dev + r->slot_off + tbytes),
+                     reinterpret_cast<unsigned long long*>(s->arena_dev + r->slot_off), status, s->stream);
+    }
+    if (!large.empty() || !small.empty())
+        launch_batch(bp, s->desc_dev[buf], reinterpret_cast<const uint64_t*>(s->arena_dev), s->small_dev[buf], s->ctr_dev[buf],
+                     status, s->stream, s->opt.ctas_per_sm > 0 ? s->opt.ctas_per_sm : 2);
     server_fail_cuda(cudaMemcpyAsync(s->status_host[buf], s->ctr_dev[buf] + 1, 4, cudaMemcpyDeviceToHost, s->stream),
                      "cudaMemcpyAsync(status)");
     // copy out the tables of requests whose last tile is in this step
@@ -283,6 +298,7 @@ static bool issue_step_locked(isg_server* s) {
     };
     for (Request* r : large_r) carried(r);
     for (Request* r : small_r) carried(r);
+    for (Request* r : split_r) carried(r);
     server_fail_cuda(cudaEventRecord(s->ev_done[buf], s->stream), "cudaEventRecord");
     st.configs = used;
     s->buf_busy[buf] = true;
@@ -442,6 +458,7 @@ void isg_server_options_init(isg_server_options* o) {
     o->max_queued = 1 << 16;
     o->arena_bytes = (int64_t)64 << 20;
     o->step_ms = 20.0;
+    o->split_work_ratio = 0.0;
 }
 
 isg_status isg_server_create(const isg_server_options* opt, isg_server** out) {
@@ -460,6 +477,7 @@ isg_status isg_server_create(const isg_server_options* opt, isg_server** out) {
         if (o.max_queued < 1) fail(ISG_ERR_INVALID, "max_queued must be >= 1");
         if (o.arena_bytes < (1 << 20)) fail(ISG_ERR_INVALID, "arena_bytes must be at least 1 MiB");
         if (!(o.step_ms > 0)) fail(ISG_ERR_INVALID, "step_ms must be > 0");
+        if (!(o.split_work_ratio >= 0 && o.split_work_ratio <= 1)) fail(ISG_ERR_INVALID, "split_work_ratio must lie in [0, 1]");
         isg_server* s = new isg_server();
         s->opt = o;
         s->t_create = Clock::now();
@@ -509,13 +527,30 @@ isg_status isg_server_submit(isg_server* s, const isg_graph* g, int64_t* ticket)
         r->n = g->n;
         r->t_submit = Clock::now();
         r->table_words = (size_t)public_bins(*g);
-        // plan outside the lock: a warp-task program (q inner bits) or the small kernel
+        // plan outside the lock: split-and-convolve when enabled and its modelled work is below
+        // split_work_ratio of the full enumeration's; else a warp-task program (q inner bits) or
+        // the small kernel
+        if (s->opt.split_work_ratio > 0 && g->n >= kSplitMinSpins) {
+            try {
+                auto sp = prepare_split(*g, 0, false);
+                if (sp->plan.cost < s->opt.split_work_ratio * sp->plan.direct_cost) {
+                    r->split = sp;
+                    r->blob = sp->blob;
+                    r->total_tasks = 1;
+                    r->configs = sp->plan.cost / (2.86 / 32);   // in full-enumeration configurations of work
+                }
+            } catch (const Error&) {
+                // no admissible boundary set: served by tiles
+            }
+        }
         isg_options o;
         isg_options_init(&o);
         o.max_spins = s->opt.max_spins;
         const DeviceInfo d = s->dinfo;       // the server's device, not the caller's current one
         Plan p;
-        if (g->n >= kMaxLow + 5) {
+        if (r->split) {
+            // planned above
+        } else if (g->n >= kMaxLow + 5) {
             o.inner_bits = std::min(16, g->n - 5);
             p = make_plan(*g, o, d);
             if (p.small || p.q < p.b) fail(ISG_ERR_INTERNAL, "unexpected plan for a served graph");
@@ -532,9 +567,11 @@ isg_status isg_server_submit(isg_server* s, const isg_graph* g, int64_t* ticket)
             r->b = 0;
             r->total_tasks = 1;
         }
-        r->blob = build_program(*g, p);
-        r->bins = (int)(g->n_e_c * (p.stride > 0 ? p.stride : g->n + 1));
-        r->configs = (double)(1ull << g->n);
+        if (!r->split) {
+            r->blob = build_program(*g, p);
+            r->bins = (int)(g->n_e_c * (p.stride > 0 ? p.stride : g->n + 1));
+            r->configs = (double)(1ull << g->n);
+        }
         const size_t need = ((r->table_words * 8 + 255) & ~(size_t)255) + r->blob.size() * 8;
         if (need > (size_t)s->opt.arena_bytes) fail(ISG_ERR_TOO_LARGE, "request does not fit the server's table arena");
         std::lock_guard<std::mutex> lk(s->mu);

@@ -263,6 +263,44 @@ __global__ void __launch_bounds__(512) split_kernel(const __grid_constant__ Spli
 
 using namespace isg;
 
+namespace isg {
+
+// Enqueue the split kernel for a prepared plan: program at d_blob (device), table (device,
+// (S + 1)(N + 1) counts) accumulated into, status bit 0 set if a walk's self-check fails.
+void launch_split(const SplitPrepared& prep, const uint64_t* d_blob, unsigned long long* table, unsigned int* status,
+                  void* stream) {
+    const SplitHeader& H = *reinterpret_cast<const SplitHeader*>(prep.blob.data());
+    const bool u64 = prep.plan.use_u64;
+    const DeviceInfo d = device_info();
+    const size_t fixed = split_smem_bytes((int)prep.blob.size(), H, u64, 0);
+    const size_t per_warp = split_warp_bytes(H, u64);
+    const size_t limit = (size_t)d.smem_optin;
+    if (fixed + per_warp > limit) fail(ISG_ERR_TOO_LARGE, "split buffers exceed shared memory");
+    const int warps = (int)std::min<size_t>(16, (limit - fixed) / per_warp);
+    const size_t smem = fixed + (size_t)warps * per_warp;
+    const int ctas_per_sm = std::max(1, (int)std::min<size_t>(4, (size_t)d.smem_per_sm / (smem + 1024)));
+    const unsigned long long n_s = 1ull << H.ns;
+    const unsigned long long want = (n_s + warps - 1) / warps;
+    const int grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(want, (unsigned long long)d.sms * ctas_per_sm));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    SplitArgs a{d_blob, (int)prep.blob.size(), table, status, n_s};
+    auto launch = [&](auto kernel) {
+        ISG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kernel<<<grid, 32 * warps, smem, s>>>(a);
+    };
+    const bool few = H.n_cls <= 2;
+    if (u64) {
+        if (few) launch(split_kernel<unsigned long long, true>);
+        else launch(split_kernel<unsigned long long, false>);
+    } else {
+        if (few) launch(split_kernel<uint32_t, true>);
+        else launch(split_kernel<uint32_t, false>);
+    }
+    ISG_CUDA(cudaGetLastError());
+}
+
+}  // namespace isg
+
 extern "C" isg_status isg_enumerate_split(const isg_graph* graph, void* stream, int64_t* g_out, int32_t g_out_on_device,
                                           uint64_t boundary) {
     try {
@@ -270,20 +308,8 @@ extern "C" isg_status isg_enumerate_split(const isg_graph* graph, void* stream, 
         NvtxRange nvtx("isg_enumerate_split");
         if (!graph || !g_out) fail(ISG_ERR_INVALID, "graph or g_out is NULL");
         const std::shared_ptr<const SplitPrepared> prep = prepare_split(*graph, boundary, true);
-        const SplitPlan& p = prep->plan;
         const std::vector<uint64_t>& blob = prep->blob;
         const SplitHeader& H = *reinterpret_cast<const SplitHeader*>(blob.data());
-        const DeviceInfo d = device_info();
-        const size_t fixed = split_smem_bytes((int)blob.size(), H, p.use_u64, 0);
-        const size_t per_warp = split_warp_bytes(H, p.use_u64);
-        const size_t limit = (size_t)d.smem_optin;
-        if (fixed + per_warp > limit) fail(ISG_ERR_TOO_LARGE, "split buffers exceed shared memory");
-        const int warps = (int)std::min<size_t>(16, (limit - fixed) / per_warp);
-        const size_t smem = fixed + (size_t)warps * per_warp;
-        const int ctas_per_sm = std::max(1, (int)std::min<size_t>(4, (size_t)d.smem_per_sm / (smem + 1024)));
-        const unsigned long long n_s = 1ull << H.ns;
-        const unsigned long long want = (n_s + warps - 1) / warps;
-        const int grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(want, (unsigned long long)d.sms * ctas_per_sm));
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         const size_t table_bytes = sizeof(int64_t) * (size_t)H.n_bins;
         const size_t blob_bytes = blob.size() * 8;
@@ -299,21 +325,7 @@ extern "C" isg_status isg_enumerate_split(const isg_graph* graph, void* stream, 
         ISG_CUDA(cudaMemsetAsync(scratch, 0, 16, s));
         ISG_CUDA(cudaMemcpyAsync(scratch + o_blob, blob.data(), blob_bytes, cudaMemcpyHostToDevice, s));
         ISG_CUDA(cudaMemsetAsync(table, 0, table_bytes, s));
-        SplitArgs a{reinterpret_cast<const uint64_t*>(scratch + o_blob), (int)blob.size(), table,
-                    reinterpret_cast<unsigned int*>(scratch), n_s};
-        auto launch = [&](auto kernel) {
-            ISG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kernel<<<grid, 32 * warps, smem, s>>>(a);
-        };
-        const bool few = H.n_cls <= 2;
-        if (p.use_u64) {
-            if (few) launch(split_kernel<unsigned long long, true>);
-            else launch(split_kernel<unsigned long long, false>);
-        } else {
-            if (few) launch(split_kernel<uint32_t, true>);
-            else launch(split_kernel<uint32_t, false>);
-        }
-        ISG_CUDA(cudaGetLastError());
+        launch_split(*prep, reinterpret_cast<const uint64_t*>(scratch + o_blob), table, reinterpret_cast<unsigned int*>(scratch), s);
         if (!g_out_on_device) {
             unsigned int status = 0;
             ISG_CUDA(cudaMemcpyAsync(g_out, table, table_bytes, cudaMemcpyDeviceToHost, s));

@@ -51,12 +51,32 @@ std::vector<uint64_t> components(const std::vector<uint64_t>& adj, uint64_t rem)
     return out;
 }
 
-int64_t touching_weight(const isg_graph& g, uint64_t comp) {
-    int64_t s = 0;
-    for (size_t b = 0; b < g.bi.size(); ++b)
-        if (((comp >> g.bi[b]) & 1) || ((comp >> g.bj[b]) & 1)) s += std::llabs(g.bJ[b]);
-    return s;
-}
+// Per spin: the sum of |J| over its bonds and its neighbours grouped by |J|, so that the bond weight
+// touching a set of spins is sum_i w_i - (weight inside the set) without a pass over all bonds.
+struct WeightIndex {
+    std::vector<int64_t> wsum;
+    std::vector<std::vector<std::pair<uint64_t, int64_t>>> groups;   // (neighbour mask, |J|)
+    explicit WeightIndex(const isg_graph& g) : wsum(g.n, 0), groups(g.n) {
+        for (int i = 0; i < g.n; ++i)
+            for (int j = 0; j < g.n; ++j) {
+                const int64_t a = std::llabs(g.K[(size_t)i * g.n + j]);
+                if (!a) continue;
+                wsum[i] += a;
+                auto it = std::find_if(groups[i].begin(), groups[i].end(), [&](const auto& p) { return p.second == a; });
+                if (it == groups[i].end()) groups[i].push_back({1ull << j, a});
+                else it->first |= 1ull << j;
+            }
+    }
+    int64_t touching(uint64_t set) const {
+        int64_t w = 0, twice_inside = 0;
+        for (uint64_t r = set; r; r &= r - 1) {
+            const int i = ctz64(r);
+            w += wsum[i];
+            for (const auto& p : groups[i]) twice_inside += p.second * popc(p.first & set);
+        }
+        return w - twice_inside / 2;
+    }
+};
 
 struct Candidate {
     uint64_t S = 0;
@@ -73,7 +93,7 @@ double ceil32(double x) { return std::ceil(x / 32.0); }
 // energy, per component its fields, a walk of 2^|C| configurations over 32 lanes, and the
 // convolution of its histogram's nonzero bins with the accumulator's nonzero bins; then the
 // shift-add of the accumulator into the table. Also checks the shared-memory layout fits.
-void evaluate(const isg_graph& g, int n_cls, Candidate& c) {
+void evaluate(const isg_graph& g, const WeightIndex& wi, int n_cls, Candidate& c) {
     const int ns = popc(c.S);
     c.cost = INFINITY;
     if (ns > 40) return;
@@ -85,7 +105,7 @@ void evaluate(const isg_graph& g, int n_cls, Candidate& c) {
     for (size_t i = 0; i < k; ++i) {
         nc[i] = popc(c.comps[i]);
         if (nc[i] > kSplitMaxCompSpins) return;
-        c.Sc[i] = touching_weight(g, c.comps[i]);
+        c.Sc[i] = wi.touching(c.comps[i]);
         order[i] = i;
     }
     std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
@@ -159,6 +179,7 @@ SplitPlan plan_split(const isg_graph& g, uint64_t boundary, bool require_gain) {
         fail(ISG_ERR_TOO_LARGE, "the split enumeration supports at most 16 distinct couplings");
     const int n_cls = std::max<int>(1, (int)cls.size());
     const std::vector<uint64_t> adj = adjacency(g);
+    const WeightIndex wi(g);
     const uint64_t all = low_mask(n);
     Candidate best;
     auto consider = [&](uint64_t S) {
@@ -166,7 +187,16 @@ SplitPlan plan_split(const isg_graph& g, uint64_t boundary, bool require_gain) {
         Candidate c;
         c.S = S;
         c.comps = components(adj, all & ~S);
-        evaluate(g, n_cls, c);
+        // the walks alone bound the work from below: skip the full model when that bound loses
+        double walk = 0;
+        for (uint64_t m : c.comps) {
+            const int nc = popc(m);
+            if (nc > kSplitMaxCompSpins) return;
+            walk += std::max(1.0, std::ldexp(1.0, nc) / 32);
+        }
+        const int ns = popc(S);
+        if (std::ldexp(walk * (8 + 3.0 * n_cls), ns > 0 ? ns - 1 : 0) >= best.cost) return;
+        evaluate(g, wi, n_cls, c);
         if (c.cost < best.cost) best = std::move(c);
     };
     if (boundary) {

@@ -111,6 +111,12 @@ struct SplitPrepared {
 };
 std::shared_ptr<const SplitPrepared> prepare_split(const struct ::isg_graph& g, uint64_t boundary, bool require_gain);
 
+// Device side (split.cu): enqueue the split kernel for a prepared plan on `stream` (a
+// cudaStream_t); program at d_blob, table (device) accumulated into, status bit 0 on a failed
+// self-check.
+void launch_split(const SplitPrepared& prep, const uint64_t* d_blob, unsigned long long* table, unsigned int* status,
+                  void* stream);
+
 // Shared memory of the split kernel: the program, the CTA's table (32-bit low and high words per
 // bin), then per warp (each block 16-byte aligned): 32 component-spin records, two accumulators, the histogram's nonzero
 // list (8-byte entries), the accumulator's nonzero list and a component histogram (4-byte

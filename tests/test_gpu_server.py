@@ -37,6 +37,32 @@ def test_mix_equals_alone(isg, cuda):
     srv.close()
 
 
+def test_mix_with_split_equals_alone(isg, cuda):
+    """With split-and-convolve enabled (split_work_ratio = 0.5), a stream of requests up to N = 36
+    (the large ones served by split launches, mixed with tile steps) gives every table equal to
+    isg_enumerate alone; the split planner is consulted on the host for each large request."""
+    reqs = w.serving_stream(40, n_range=(20, 36), seed=11)
+    srv = isg.Server(step_ms=5.0, split_work_ratio=0.5)
+    tickets = [(srv.submit(isg.isg_graph_create(r.lattice.n, r.lattice.edges)), r.lattice) for r in reqs]
+    n_split = 0
+    for t, lat in tickets:
+        srv.wait(t, 120000)
+        g, _ = srv.result(t)
+        assert np.array_equal(g, alone(isg, lat)), lat.name
+        gh = isg.isg_graph_create(lat.n, lat.edges)
+        try:
+            n_split += lat.n >= 24 and isg.isg_split_plan(gh)["work_ratio"] < 0.5
+        except isg.IsgError:
+            pass
+    assert n_split >= 5                          # the stream really exercises the split path
+    srv.close()
+
+
+def test_server_rejects_bad_split_ratio(isg, cuda):
+    with pytest.raises(isg.IsgError, match="INVALID"):
+        isg.Server(split_work_ratio=1.5)
+
+
 def test_staggered_arrivals_and_small_arena(isg, cuda):
     """Requests arriving while others run, with an arena that holds only a few tables at a time and
     two admission slots: all finish and match."""
