@@ -101,3 +101,21 @@ def test_split_rejects(isg, cuda):
         isg.isg_enumerate_split(gh)              # a 16-spin lattice: no boundary beats the full walk
     with pytest.raises(isg.IsgError, match="INVALID"):
         isg.isg_enumerate_split(gh, boundary=1 << 20)
+
+
+def test_split_random_graphs(isg, cuda):
+    """The seeded random graphs of the host tests (several coupling alphabets, isolated spins,
+    empty and full boundary sets) through the kernel: every table equals the oracle's."""
+    from test_split_host import _random_cases
+    done = 0
+    for lat, boundary in _random_cases():
+        gh = isg.isg_graph_create(lat.n, lat.edges)
+        try:
+            b = boundary or isg.isg_split_plan(gh)["boundary"] or 1
+            got = isg.isg_enumerate_split(gh, boundary=b)
+        except isg.IsgError as e:
+            assert "TOO_LARGE" in str(e)
+            continue
+        assert np.array_equal(got, oracle.g_edges(lat.n, lat.edges)), lat.name
+        done += 1
+    assert done >= 30

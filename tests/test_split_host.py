@@ -104,3 +104,38 @@ def test_split_rejections(isg):
     edges = np.array([[i, j, 1 + i * 8 + j] for i in range(8) for j in range(i + 1, 8)], np.int64)
     with pytest.raises(isg.IsgError, match="TOO_LARGE"):
         isg.isg_split_plan(isg.isg_graph_create(8, edges), 0)
+
+
+def _random_cases(count=40, seed=20260):
+    """Seeded random graphs of 6..18 spins: sparse and dense, couplings from several alphabets
+    (ferromagnetic, antiferromagnetic, +-J, +-1/+-2, wide), with isolated spins and disconnected
+    pieces, each with a random boundary mask (possibly empty or everything)."""
+    rng = w.SplitMix64(seed)
+    alphabets = [(1,), (-1,), (-1, 1), (-2, -1, 1, 2), (-7, 3, 5, 11)]
+    out = []
+    for k in range(count):
+        n = 6 + rng.below(13)
+        m = rng.below(3 * n)
+        lat = w.random_graph(n, m, rng, alphabets[k % len(alphabets)])
+        r = rng.below(4)
+        if r == 0:
+            boundary = 0                                   # the planner's choice
+        elif r == 1:
+            boundary = (1 << n) - 1                        # every spin boundary
+        else:
+            boundary = rng.below(1 << n)                   # an arbitrary set (0: the planner's)
+        out.append((lat, boundary))
+    return out
+
+
+@pytest.mark.parametrize("k", range(40))
+def test_emulated_split_random_graphs(isg, k):
+    lat, boundary = _random_cases()[k]
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    try:
+        got = isg.isg_debug_emulate_split(gh, boundary)
+    except isg.IsgError as e:
+        # an arbitrary set may leave a component over 30 spins or too many classes: refused, not wrong
+        assert "TOO_LARGE" in str(e)
+        return
+    assert np.array_equal(got, oracle.g_edges(lat.n, lat.edges))
