@@ -43,8 +43,8 @@ SM_MAX_MHZ_FALLBACK = 2070.0
 OPS_PER_CONFIG = 2
 # DRAM traffic of one enumeration launch on this workload from the committed ncu capture
 # (profiles/enumerate_kernel_torus6x6.md), valid only for the kernel sources it was taken on.
-TRAFFIC_BYTES = 32768          # dram__bytes_read.sum + dram__bytes_write.sum of one launch (program reads; table stays in L2)
-TRAFFIC_SOURCES_SHA = "1ebd481d381434c6"
+TRAFFIC_BYTES = 33020          # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu: 33.02 KB read, 0 written)
+TRAFFIC_SOURCES_SHA = "9d2d6198cb2b7864"
 
 
 def kernel_sources_sha() -> str:

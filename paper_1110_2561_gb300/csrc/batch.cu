@@ -138,14 +138,6 @@ __global__ void batch_mirror_kernel(const BatchInst* inst, const int* ids, const
     }
 }
 
-#define ISG_CUDA(call)                                                                              \
-    do {                                                                                            \
-        cudaError_t e_ = (call);                                                                    \
-        if (e_ != cudaSuccess)                                                                      \
-            fail(e_ == cudaErrorMemoryAllocation ? ISG_ERR_NOMEM : ISG_ERR_CUDA,                    \
-                 std::string(#call) + ": " + cudaGetErrorString(e_));                               \
-    } while (0)
-
 // ---------------------------------------------------------------------------------------------
 // Host planning of a batch
 // ---------------------------------------------------------------------------------------------
@@ -399,28 +391,10 @@ static void autotune_batch(int n, const isg_graph* const* graphs, isg_options& o
     o.autotune = 0;
 }
 
-template <class F>
-static isg_status guarded_cuda(F&& f) {
-    try {
-        clear_error();
-        f();
-        return ISG_OK;
-    } catch (const Error& e) {
-        set_error(e.msg);
-        return e.status;
-    } catch (const std::bad_alloc&) {
-        set_error("host allocation failed");
-        return ISG_ERR_NOMEM;
-    } catch (...) {
-        set_error("unexpected exception");
-        return ISG_ERR_INTERNAL;
-    }
-}
-
 extern "C" {
 
 isg_status isg_batch_create(int32_t n_graphs, const isg_graph* const* graphs, const isg_options* opt, isg_batch** out) {
-    return guarded_cuda([&] {
+    return guarded([&] {
         if (!out) fail(ISG_ERR_INVALID, "out is NULL");
         *out = nullptr;
         if (n_graphs < 1 || !graphs) fail(ISG_ERR_INVALID, "need at least one graph");
@@ -470,7 +444,7 @@ isg_status isg_batch_create(int32_t n_graphs, const isg_graph* const* graphs, co
 }
 
 isg_status isg_batch_run(isg_batch* b, void* stream) {
-    return guarded_cuda([&] {
+    return guarded([&] {
         if (!b) fail(ISG_ERR_INVALID, "batch is NULL");
         NvtxRange nvtx("isg_batch_run");
         std::lock_guard<std::mutex> lk(b->mu);
@@ -495,7 +469,7 @@ isg_status isg_batch_run(isg_batch* b, void* stream) {
 }
 
 isg_status isg_batch_table(const isg_batch* b, int32_t k, int64_t** device_table) {
-    return guarded_cuda([&] {
+    return guarded([&] {
         if (!b || !device_table) fail(ISG_ERR_INVALID, "NULL argument");
         if (k < 0 || k >= (int)b->table_off.size()) fail(ISG_ERR_INVALID, "graph index out of range");
         *device_table = b->d_tables + b->table_off[k];
@@ -503,7 +477,7 @@ isg_status isg_batch_table(const isg_batch* b, int32_t k, int64_t** device_table
 }
 
 isg_status isg_batch_status(isg_batch* b, void* stream) {
-    return guarded_cuda([&] {
+    return guarded([&] {
         if (!b) fail(ISG_ERR_INVALID, "batch is NULL");
         unsigned int st = 0;
         ISG_CUDA(cudaMemcpyAsync(&st, b->d_status, 4, cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream)));
@@ -530,7 +504,7 @@ isg_status isg_enumerate_batch(int32_t n_graphs, const isg_graph* const* graphs,
     isg_batch* b = nullptr;
     isg_status st = isg_batch_create(n_graphs, graphs, opt, &b);
     if (st != ISG_OK) return st;
-    st = guarded_cuda([&] {
+    st = guarded([&] {
         if (!g_out) fail(ISG_ERR_INVALID, "g_out is NULL");
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         batch_enqueue(b, s);

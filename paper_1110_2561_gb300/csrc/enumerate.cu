@@ -159,14 +159,6 @@ __global__ void mirror_kernel(const int64_t* half, int64_t* out, int n_e, int n_
 // ---------------------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------------------
-#define ISG_CUDA(call)                                                                              \
-    do {                                                                                            \
-        cudaError_t e_ = (call);                                                                    \
-        if (e_ != cudaSuccess)                                                                      \
-            fail(e_ == cudaErrorMemoryAllocation ? ISG_ERR_NOMEM : ISG_ERR_CUDA,                    \
-                 std::string(#call) + ": " + cudaGetErrorString(e_));                               \
-    } while (0)
-
 void* scratch_alloc(size_t bytes, void* stream) {
     static std::mutex mu;
     static std::vector<cudaMemPool_t> pools;
@@ -405,31 +397,19 @@ static void apply_autotune(const isg_graph& g, isg_options& o, cudaStream_t s) {
 using namespace isg;
 
 extern "C" isg_status isg_autotune(const isg_graph* graph, void* stream, const isg_options* opt, isg_options* tuned) {
-    try {
-        clear_error();
+    return guarded([&] {
         NvtxRange nvtx("isg_autotune");
         if (!graph || !tuned) fail(ISG_ERR_INVALID, "graph or tuned is NULL");
         isg_options o = resolve_options(opt);
         o.autotune = 1;
         apply_autotune(*graph, o, static_cast<cudaStream_t>(stream));
         *tuned = o;
-        return ISG_OK;
-    } catch (const Error& e) {
-        set_error(e.msg);
-        return e.status;
-    } catch (const std::bad_alloc&) {
-        set_error("host allocation failed");
-        return ISG_ERR_NOMEM;
-    } catch (...) {
-        set_error("unexpected exception");
-        return ISG_ERR_INTERNAL;
-    }
+    });
 }
 
 extern "C" isg_status isg_enumerate(const isg_graph* graph, void* stream, int64_t* g_out, int32_t g_out_on_device,
                                     const isg_options* opt) {
-    try {
-        clear_error();
+    return guarded([&] {
         NvtxRange nvtx("isg_enumerate");
         if (!graph || !g_out) fail(ISG_ERR_INVALID, "graph or g_out is NULL");
         isg_options o = resolve_options(opt);
@@ -478,15 +458,5 @@ extern "C" isg_status isg_enumerate(const isg_graph* graph, void* stream, int64_
             if (o.accumulate) for (size_t i = 0; i < host.size(); ++i) g_out[i] += host[i];
             else std::memcpy(g_out, host.data(), table_bytes);
         }
-        return ISG_OK;
-    } catch (const Error& e) {
-        set_error(e.msg);
-        return e.status;
-    } catch (const std::bad_alloc&) {
-        set_error("host allocation failed");
-        return ISG_ERR_NOMEM;
-    } catch (...) {
-        set_error("unexpected exception");
-        return ISG_ERR_INTERNAL;
-    }
+    });
 }

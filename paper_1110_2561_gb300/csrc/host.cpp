@@ -300,24 +300,6 @@ static void emulate_tasks(const ProgView& v, const Plan& p, std::vector<uint32_t
 
 using namespace isg;
 
-template <class F>
-static isg_status guarded(F&& f) {
-    try {
-        clear_error();
-        f();
-        return ISG_OK;
-    } catch (const Error& e) {
-        set_error(e.msg);
-        return e.status;
-    } catch (const std::bad_alloc&) {
-        set_error("host allocation failed");
-        return ISG_ERR_NOMEM;
-    } catch (...) {
-        set_error("unexpected exception");
-        return ISG_ERR_INTERNAL;
-    }
-}
-
 extern "C" {
 
 void isg_options_init(isg_options* opt) {

@@ -1,6 +1,7 @@
 // isg_internal.h -- host-side model shared by the library's translation units.
 #pragma once
 #include <cstdint>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -33,6 +34,37 @@ struct Error {
     std::string msg;
 };
 [[noreturn]] void fail(isg_status s, const std::string& msg);
+
+// Run the body of a C entry point: clears the thread's error message, and turns what the body
+// throws into the status the ABI returns (the message recorded for isg_last_error). No exception
+// leaves the library.
+template <class F>
+isg_status guarded(F&& f) {
+    try {
+        clear_error();
+        f();
+        return ISG_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return ISG_ERR_NOMEM;
+    } catch (...) {
+        set_error("unexpected exception");
+        return ISG_ERR_INTERNAL;
+    }
+}
+
+// A CUDA runtime call that throws ISG_ERR_NOMEM / ISG_ERR_CUDA with the call's text on failure
+// (for the .cu files; expands to CUDA runtime names only where it is used).
+#define ISG_CUDA(call)                                                                              \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            ::isg::fail(e_ == cudaErrorMemoryAllocation ? ISG_ERR_NOMEM : ISG_ERR_CUDA,             \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+    } while (0)
 
 // Resolved options with defaults applied.
 isg_options resolve_options(const isg_options* opt);

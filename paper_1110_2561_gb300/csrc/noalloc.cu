@@ -61,8 +61,7 @@ using namespace isg;
 
 extern "C" isg_status isg_enumerate_noalloc(const isg_graph* graph, void* stream, int64_t* g_out_device,
                                             const isg_options* opt) {
-    try {
-        clear_error();
+    return guarded([&] {
         if (!graph || !g_out_device) fail(ISG_ERR_INVALID, "graph or g_out_device is NULL");
         const isg_options o = resolve_options(opt);
         const DeviceInfo d = device_info();
@@ -88,15 +87,5 @@ extern "C" isg_status isg_enumerate_noalloc(const isg_graph* graph, void* stream
         launch_enumeration(p, reinterpret_cast<const uint64_t*>(scratch + kNoallocProgramOffset), (int)blob.size(),
                            g_out_device, reinterpret_cast<unsigned long long*>(scratch),
                            reinterpret_cast<unsigned int*>(scratch + 8), s, nullptr);
-        return ISG_OK;
-    } catch (const Error& e) {
-        set_error(e.msg);
-        return e.status;
-    } catch (const std::bad_alloc&) {
-        set_error("host allocation failed");
-        return ISG_ERR_NOMEM;
-    } catch (...) {
-        set_error("unexpected exception");
-        return ISG_ERR_INTERNAL;
-    }
+    });
 }

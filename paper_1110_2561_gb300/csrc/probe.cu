@@ -56,12 +56,6 @@ __global__ void __launch_bounds__(512) probe_kernel(int iters, unsigned* sink) {
     atomicAdd(sink, tot);
 }
 
-#define ISG_CUDA(call)                                                                              \
-    do {                                                                                            \
-        cudaError_t e_ = (call);                                                                    \
-        if (e_ != cudaSuccess) fail(ISG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-    } while (0)
-
 template <int MODE>
 static double probe_rate(cudaStream_t s, unsigned* sink, int sms, double ops_per_iter) {
     const int threads = 512, iters = 1 << 16, per_sm = 3;   // 3 x 64 KB tables: 48 warps per SM
@@ -89,8 +83,7 @@ using namespace isg;
 
 extern "C" isg_status isg_probe_peaks(void* stream, double* red_conflict_free, double* red_scattered, double* alu,
                                       double* match_aggregated) {
-    try {
-        clear_error();
+    return guarded([&] {
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         int dev = 0, sms = 0;
         ISG_CUDA(cudaGetDevice(&dev));
@@ -107,12 +100,5 @@ extern "C" isg_status isg_probe_peaks(void* stream, double* red_conflict_free, d
         if (red_scattered) *red_scattered = r1;
         if (alu) *alu = r2;
         if (match_aggregated) *match_aggregated = r3;
-        return ISG_OK;
-    } catch (const Error& e) {
-        set_error(e.msg);
-        return e.status;
-    } catch (...) {
-        set_error("unexpected exception");
-        return ISG_ERR_INTERNAL;
-    }
+    });
 }

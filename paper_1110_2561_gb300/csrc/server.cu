@@ -402,24 +402,6 @@ static void worker_main(isg_server* s) {
 
 }  // namespace isg
 
-template <class F>
-static isg_status guarded_srv(F&& f) {
-    try {
-        clear_error();
-        f();
-        return ISG_OK;
-    } catch (const Error& e) {
-        set_error(e.msg);
-        return e.status;
-    } catch (const std::bad_alloc&) {
-        set_error("host allocation failed");
-        return ISG_ERR_NOMEM;
-    } catch (...) {
-        set_error("unexpected exception");
-        return ISG_ERR_INTERNAL;
-    }
-}
-
 static void destroy_server(isg_server* s) {
     if (!s) return;
     if (s->worker.joinable()) {
@@ -462,7 +444,7 @@ void isg_server_options_init(isg_server_options* o) {
 }
 
 isg_status isg_server_create(const isg_server_options* opt, isg_server** out) {
-    return guarded_srv([&] {
+    return guarded([&] {
         if (!out) fail(ISG_ERR_INVALID, "out is NULL");
         *out = nullptr;
         isg_server_options o;
@@ -520,7 +502,7 @@ isg_status isg_server_create(const isg_server_options* opt, isg_server** out) {
 }
 
 isg_status isg_server_submit(isg_server* s, const isg_graph* g, int64_t* ticket) {
-    return guarded_srv([&] {
+    return guarded([&] {
         if (!s || !g || !ticket) fail(ISG_ERR_INVALID, "NULL argument");
         if (g->n > s->opt.max_spins) fail(ISG_ERR_TOO_LARGE, "graph has more than max_spins spins");
         std::unique_ptr<Request> r(new Request());
@@ -586,7 +568,7 @@ isg_status isg_server_submit(isg_server* s, const isg_graph* g, int64_t* ticket)
 }
 
 isg_status isg_server_poll(isg_server* s, int64_t ticket, int32_t* done) {
-    return guarded_srv([&] {
+    return guarded([&] {
         if (!s || !done) fail(ISG_ERR_INVALID, "NULL argument");
         std::lock_guard<std::mutex> lk(s->mu);
         auto it = s->reqs.find(ticket);
@@ -597,7 +579,7 @@ isg_status isg_server_poll(isg_server* s, int64_t ticket, int32_t* done) {
 }
 
 isg_status isg_server_wait(isg_server* s, int64_t ticket, int64_t timeout_ms) {
-    return guarded_srv([&] {
+    return guarded([&] {
         if (!s) fail(ISG_ERR_INVALID, "NULL argument");
         std::unique_lock<std::mutex> lk(s->mu);
         auto ready = [&] {
@@ -614,7 +596,7 @@ isg_status isg_server_wait(isg_server* s, int64_t ticket, int64_t timeout_ms) {
 }
 
 isg_status isg_server_result(isg_server* s, int64_t ticket, int64_t* g_out, double* times) {
-    return guarded_srv([&] {
+    return guarded([&] {
         if (!s || !g_out) fail(ISG_ERR_INVALID, "NULL argument");
         std::lock_guard<std::mutex> lk(s->mu);
         auto it = s->reqs.find(ticket);
@@ -639,7 +621,7 @@ isg_status isg_server_result(isg_server* s, int64_t ticket, int64_t* g_out, doub
 }
 
 isg_status isg_server_cancel(isg_server* s, int64_t ticket) {
-    return guarded_srv([&] {
+    return guarded([&] {
         if (!s) fail(ISG_ERR_INVALID, "NULL argument");
         std::lock_guard<std::mutex> lk(s->mu);
         auto it = s->reqs.find(ticket);
@@ -667,7 +649,7 @@ isg_status isg_server_cancel(isg_server* s, int64_t ticket) {
 }
 
 isg_status isg_server_stats(isg_server* s, double* stats) {
-    return guarded_srv([&] {
+    return guarded([&] {
         if (!s || !stats) fail(ISG_ERR_INVALID, "NULL argument");
         std::lock_guard<std::mutex> lk(s->mu);
         stats[0] = (double)s->steps_done;

@@ -251,14 +251,6 @@ __global__ void __launch_bounds__(512) split_kernel(const __grid_constant__ Spli
     }
 }
 
-#define ISG_CUDA(call)                                                                              \
-    do {                                                                                            \
-        cudaError_t e_ = (call);                                                                    \
-        if (e_ != cudaSuccess)                                                                      \
-            fail(e_ == cudaErrorMemoryAllocation ? ISG_ERR_NOMEM : ISG_ERR_CUDA,                    \
-                 std::string(#call) + ": " + cudaGetErrorString(e_));                               \
-    } while (0)
-
 }  // namespace isg
 
 using namespace isg;
@@ -303,8 +295,7 @@ void launch_split(const SplitPrepared& prep, const uint64_t* d_blob, unsigned lo
 
 extern "C" isg_status isg_enumerate_split(const isg_graph* graph, void* stream, int64_t* g_out, int32_t g_out_on_device,
                                           uint64_t boundary) {
-    try {
-        clear_error();
+    return guarded([&] {
         NvtxRange nvtx("isg_enumerate_split");
         if (!graph || !g_out) fail(ISG_ERR_INVALID, "graph or g_out is NULL");
         const std::shared_ptr<const SplitPrepared> prep = prepare_split(*graph, boundary, true);
@@ -333,15 +324,5 @@ extern "C" isg_status isg_enumerate_split(const isg_graph* graph, void* stream, 
             ISG_CUDA(cudaStreamSynchronize(s));
             if (status) fail(ISG_ERR_INTERNAL, "split enumeration self-check failed");
         }
-        return ISG_OK;
-    } catch (const Error& e) {
-        set_error(e.msg);
-        return e.status;
-    } catch (const std::bad_alloc&) {
-        set_error("host allocation failed");
-        return ISG_ERR_NOMEM;
-    } catch (...) {
-        set_error("unexpected exception");
-        return ISG_ERR_INTERNAL;
-    }
+    });
 }

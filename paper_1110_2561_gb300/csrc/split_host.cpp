@@ -480,8 +480,7 @@ extern "C" {
 
 isg_status isg_split_plan(const isg_graph* graph, uint64_t boundary, uint64_t* chosen, int32_t* n_components,
                           int32_t* largest_component, double* visits, double* work_ratio) {
-    try {
-        clear_error();
+    return guarded([&] {
         if (!graph) fail(ISG_ERR_INVALID, "graph is NULL");
         const std::shared_ptr<const SplitPrepared> e = prepare_split(*graph, boundary, false);
         const SplitPlan& p = e->plan;
@@ -494,38 +493,17 @@ isg_status isg_split_plan(const isg_graph* graph, uint64_t boundary, uint64_t* c
         }
         if (visits) *visits = p.visits;
         if (work_ratio) *work_ratio = p.cost / p.direct_cost;
-        return ISG_OK;
-    } catch (const Error& e) {
-        set_error(e.msg);
-        return e.status;
-    } catch (const std::bad_alloc&) {
-        set_error("host allocation failed");
-        return ISG_ERR_NOMEM;
-    } catch (...) {
-        set_error("unexpected exception");
-        return ISG_ERR_INTERNAL;
-    }
+    });
 }
 
 isg_status isg_debug_emulate_split(const isg_graph* graph, uint64_t boundary, int64_t* g_out) {
-    try {
-        clear_error();
+    return guarded([&] {
         if (!graph || !g_out) fail(ISG_ERR_INVALID, "NULL argument");
         const std::shared_ptr<const SplitPrepared> e = prepare_split(*graph, boundary, false);
         const std::vector<uint64_t>& blob = e->blob;
         std::memset(g_out, 0, sizeof(int64_t) * (size_t)(graph->S + 1) * (graph->n + 1));
         emulate_split(blob, g_out);
-        return ISG_OK;
-    } catch (const Error& e) {
-        set_error(e.msg);
-        return e.status;
-    } catch (const std::bad_alloc&) {
-        set_error("host allocation failed");
-        return ISG_ERR_NOMEM;
-    } catch (...) {
-        set_error("unexpected exception");
-        return ISG_ERR_INTERNAL;
-    }
+    });
 }
 
 }  // extern "C"

@@ -349,14 +349,6 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
     }
 }
 
-#define ISG_CUDA(call)                                                                              \
-    do {                                                                                            \
-        cudaError_t e_ = (call);                                                                    \
-        if (e_ != cudaSuccess)                                                                      \
-            fail(e_ == cudaErrorMemoryAllocation ? ISG_ERR_NOMEM : ISG_ERR_CUDA,                    \
-                 std::string(#call) + ": " + cudaGetErrorString(e_));                               \
-    } while (0)
-
 // Enqueue the thermodynamics kernels; all pointers on the device. lng: n_e * n_m doubles, lngf:
 // 2 * n_e * n_m floats of scratch.
 void launch_thermo(const ThermoParams& P, double* lng, float* lngf, int precision, cudaStream_t s) {
@@ -389,8 +381,7 @@ using namespace isg;
 extern "C" isg_status isg_specific_heat_peak(const int64_t* g, int32_t g_on_device, const isg_graph* graph, double h,
                                              double T_lo, double T_hi, int32_t precision, void* stream,
                                              double* T_peak, double* C_peak) {
-    try {
-        clear_error();
+    return guarded([&] {
         NvtxRange nvtx("isg_specific_heat_peak");
         if (!g || !graph || !T_peak) fail(ISG_ERR_INVALID, "NULL argument");
         if (!(T_lo > 0) || !(T_hi > T_lo) || !std::isfinite(T_hi) || !std::isfinite(h))
@@ -444,17 +435,7 @@ extern "C" isg_status isg_specific_heat_peak(const int64_t* g, int32_t g_on_devi
         }
         *T_peak = best_T;
         if (C_peak) *C_peak = best_C;
-        return ISG_OK;
-    } catch (const Error& e) {
-        set_error(e.msg);
-        return e.status;
-    } catch (const std::bad_alloc&) {
-        set_error("host allocation failed");
-        return ISG_ERR_NOMEM;
-    } catch (...) {
-        set_error("unexpected exception");
-        return ISG_ERR_INTERNAL;
-    }
+    });
 }
 
 // One evaluation of the grid T x h: validation, scratch, the kernels and the copies back. outs
@@ -525,43 +506,23 @@ static void thermo_grid(const int64_t* g, int32_t g_on_device, const isg_graph* 
     if (!out_on_device || !g_on_device) ISG_CUDA(cudaStreamSynchronize(s));
 }
 
-#define ISG_TRY_END                                                                                 \
-    catch (const Error& e) {                                                                        \
-        set_error(e.msg);                                                                           \
-        return e.status;                                                                            \
-    }                                                                                               \
-    catch (const std::bad_alloc&) {                                                                 \
-        set_error("host allocation failed");                                                        \
-        return ISG_ERR_NOMEM;                                                                       \
-    }                                                                                               \
-    catch (...) {                                                                                   \
-        set_error("unexpected exception");                                                          \
-        return ISG_ERR_INTERNAL;                                                                    \
-    }
-
 extern "C" isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const isg_graph* graph, int32_t nT,
                                  const double* T, int32_t nh, const double* h, int32_t precision, void* stream,
                                  int32_t out_on_device, double* logZ, double* E, double* M, double* C, double* chi) {
-    try {
-        clear_error();
+    return guarded([&] {
         NvtxRange nvtx("isg_thermo");
         double* const outs[kThermoOuts] = {logZ, E, M, C, chi, nullptr, nullptr, nullptr, nullptr};
         thermo_grid(g, g_on_device, graph, nT, T, nh, h, precision, stream, out_on_device, outs);
-        return ISG_OK;
-    }
-    ISG_TRY_END
+    });
 }
 
 extern "C" isg_status isg_magnetisation(const int64_t* g, int32_t g_on_device, const isg_graph* graph, int32_t nT,
                                         const double* T, int32_t nh, const double* h, int32_t precision,
                                         void* stream, int32_t out_on_device, double* abs_M, double* M2, double* M4,
                                         double* binder) {
-    try {
-        clear_error();
+    return guarded([&] {
         NvtxRange nvtx("isg_magnetisation");
         double* const outs[kThermoOuts] = {nullptr, nullptr, nullptr, nullptr, nullptr, abs_M, M2, M4, binder};
         thermo_grid(g, g_on_device, graph, nT, T, nh, h, precision, stream, out_on_device, outs);
-        return ISG_OK;
-    }
-    ISG_TRY_END
+    });
 }
