@@ -603,14 +603,15 @@ def run_profile_case(args):
             for _ in range(args.warmup):
                 isg.isg_thermo(g, gh, T, h, prec, stream, out=outs)
             res[name] = _event_ms(lambda: isg.isg_thermo(g, gh, T, h, prec, stream, out=outs), stream, args.steps)
-    elif args.profile_case == "split-torus6x6":
-        lat = workloads.square(6, 6, True)
+    elif args.profile_case in ("split-torus6x6", "split-torus7x7"):
+        L = 6 if args.profile_case == "split-torus6x6" else 7
+        lat = workloads.square(L, L, True)
         gh = isg.isg_graph_create(lat.n, lat.edges)
         g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=dev)
         for _ in range(args.warmup):
             isg.isg_enumerate_split(gh, g, stream)
         res["ms"] = _event_ms(lambda: isg.isg_enumerate_split(gh, g, stream), stream, args.steps)
-        res["sum_ok"] = int(g.sum().item()) == 2 ** 36
+        res["sum_ok"] = int(g.sum().item()) == 2 ** lat.n
     else:
         raise SystemExit(f"unknown profile case {args.profile_case}")
     torch.cuda.synchronize()
@@ -627,7 +628,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target seconds of the oracle sample")
     ap.add_argument("--serving", action="store_true", help="run the request-stream (serving) benchmark instead")
-    ap.add_argument("--profile-case", choices=("ea-batch", "cubic-thermo", "split-torus6x6"), default=None,
+    ap.add_argument("--profile-case", choices=("ea-batch", "cubic-thermo", "split-torus6x6", "split-torus7x7"),
+                    default=None,
                     help="run only a small case of another kernel (for ncu captures)")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=50.0)

@@ -1,13 +1,14 @@
 // split.cu -- split-and-convolve enumeration on the device (the identity and the program layout
-// are in split_internal.h): one warp per configuration s of the boundary set S.
+// are in split_internal.h): one CTA per configuration s of the boundary set S at a time.
 //
-// Per s (half of them: the other half are their global-flip mirrors), a warp computes the boundary
+// Per s (half of them: the other half are their global-flip mirrors), a CTA computes the boundary
 // energy and up count, then for each component C_c the field
-// S exerts on each of its spins, walks the 2^|C_c| configurations of C_c (32 lanes, each a
-// reflected Gray walk over the low |C_c| - 5 bits with its lane index in the top five) into a
-// 32-bit shared histogram, and convolves that histogram into the warp's accumulator: the nonzero
-// bins of both are listed, each lane holds a few accumulator bins in registers, and every product
-// is a shared-memory reduction into the next accumulator.
+// S exerts on each of its spins, walks the 2^|C_c| configurations of C_c (up to 512 threads, each
+// a reflected Gray walk over the low bits with its thread index in the top bits) into a 32-bit
+// shared histogram, and convolves that histogram into the CTA's accumulator: the nonzero bins of
+// both are listed, lanes hold a few accumulator bins in registers while the warps take the
+// histogram bins in turn, and every product is a shared-memory reduction into the next
+// accumulator.
 // The accumulator, shifted by the boundary's bin, is added into the CTA's int64 table in shared
 // memory, which is flushed to the output with 64-bit atomics at the end.
 //
@@ -51,10 +52,46 @@ __device__ __forceinline__ int split_field(const int64_t* cls, int ncl, const ui
     return f;
 }
 
+// A warp's accumulator buffer of `words` bins. 32-bit counts: one word per bin. 64-bit counts: a
+// plane of low words then a plane of high words (the same 8 bytes per bin), so that every update is
+// a 32-bit shared atomic: 64-bit shared atomics are several times slower on this GPU, and far
+// slower when lanes collide. An addition's carry out of the low word is detected from the value
+// the atomic returns and added to the high word with the value's own high half.
+template <class Acc>
+struct AccBuf {
+    uint32_t* lo;
+    uint32_t* hi;
+    __device__ AccBuf(void* base, int words)
+        : lo(static_cast<uint32_t*>(base)), hi(sizeof(Acc) == 8 ? static_cast<uint32_t*>(base) + words : nullptr) {}
+    __device__ Acc get(int i) const {
+        if (sizeof(Acc) == 8) return (Acc)(((unsigned long long)hi[i] << 32) | lo[i]);
+        return (Acc)lo[i];
+    }
+    __device__ void set(int i, Acc v) const {
+        lo[i] = (uint32_t)v;
+        if (sizeof(Acc) == 8) hi[i] = (uint32_t)((unsigned long long)v >> 32);
+    }
+    __device__ void add(int i, Acc v) const {
+        if (sizeof(Acc) == 8) {
+            const unsigned long long w = (unsigned long long)v;
+            const uint32_t vl = (uint32_t)w, vh = (uint32_t)(w >> 32);
+            const uint32_t old = atomicAdd(&lo[i], vl);
+            const uint32_t up = vh + (uint32_t)(old + vl < old);
+            if (up) atomicAdd(&hi[i], up);
+        } else {
+            atomicAdd(&lo[i], (uint32_t)v);
+        }
+    }
+};
+
 // kFew: at most two coupling classes (every lattice here: J = 1, or +-J), so a spin's field is
 // two masked popcounts of a 32-bit component word and a constant; otherwise a loop over classes.
+//
+// One CTA (kSplitThreads threads) per boundary configuration at a time, in a grid-stride loop:
+// the CTA's buffers (split_warp_layout) hold one accumulator pair, the lists and a histogram, so
+// large components do not cut the number of warps per SM.
 template <class Acc, bool kFew>
-__global__ void __launch_bounds__(512) split_kernel(const __grid_constant__ SplitArgs a) {
+__global__ void __launch_bounds__(kSplitThreads) split_kernel(const __grid_constant__ SplitArgs a) {
     extern __shared__ __align__(16) unsigned char sm[];
     uint64_t* prog = reinterpret_cast<uint64_t*>(sm);
     for (int i = threadIdx.x; i < a.blob_words; i += blockDim.x) prog[i] = a.blob[i];
@@ -66,142 +103,132 @@ __global__ void __launch_bounds__(512) split_kernel(const __grid_constant__ Spli
     // addition detected from the value it returned
     unsigned int* tlo = reinterpret_cast<unsigned int*>(sm + split_prog_bytes(a.blob_words));
     unsigned int* thi = tlo + H.n_bins;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const SplitWarpLayout WL = split_warp_layout(H, sizeof(Acc) == 8);
-    unsigned char* wbase = sm + split_prog_bytes(a.blob_words) + split_table_bytes(H) + (size_t)warp * WL.bytes;
-    Acc* bufA = reinterpret_cast<Acc*>(wbase + WL.acc_a);
-    Acc* bufB = reinterpret_cast<Acc*>(wbase + WL.acc_b);
-    uint64_t* hlist = reinterpret_cast<uint64_t*>(wbase + WL.hlist);
-    uint32_t* list = reinterpret_cast<uint32_t*>(wbase + WL.list);
-    uint32_t* hist = reinterpret_cast<uint32_t*>(wbase + WL.hist);
-    uint4* wsp = reinterpret_cast<uint4*>(wbase + WL.spins);     // per component spin: masks, constant, field
+    unsigned char* cbase = sm + split_prog_bytes(a.blob_words) + split_table_bytes(H);
+    const AccBuf<Acc> bufA(cbase + WL.acc_a, H.acc_words), bufB(cbase + WL.acc_b, H.acc_words);
+    uint64_t* hlist = reinterpret_cast<uint64_t*>(cbase + WL.hlist);
+    uint32_t* list = reinterpret_cast<uint32_t*>(cbase + WL.list);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(cbase + WL.hist);
+    uint4* wsp = reinterpret_cast<uint4*>(cbase + WL.spins);      // per component spin: masks, constant, field
+    int* sc = reinterpret_cast<int*>(cbase + WL.scalars);          // [0] list length, [1] histogram list length, [2] e_SS
     const int J0 = (int)v.cls[0], J1 = ncl > 1 ? (int)v.cls[1] : 0;
-    for (int i = threadIdx.x; i < 2 * H.n_bins; i += blockDim.x) tlo[i] = 0;
+    for (int i = tid; i < 2 * H.n_bins; i += blockDim.x) tlo[i] = 0;
     __syncthreads();
-    auto table_add = [&](int i, unsigned long long v) {
-        const unsigned int vl = (unsigned int)v, vh = (unsigned int)(v >> 32);
+    auto table_add = [&](int i, unsigned long long val) {
+        const unsigned int vl = (unsigned int)val, vh = (unsigned int)(val >> 32);
         const unsigned int old = atomicAdd(&tlo[i], vl);
         const unsigned int carry = (unsigned int)(old + vl < old);
         if (vh + carry) atomicAdd(&thi[i], vh + carry);
     };
 
-    const unsigned FULL = 0xffffffffu;
-    const unsigned long long wpb = blockDim.x >> 5;
     bool bad = false;
     // The global flip (every spin reversed) keeps E and negates M, so the boundary configurations
     // with the top boundary bit set give the mirror images of the others: only s < n_s / 2 are
     // walked and each result is added at M and at -M.
     const unsigned long long n_walk = H.ns ? a.n_s >> 1 : a.n_s;
-    for (unsigned long long s = blockIdx.x * wpb + warp; s < n_walk; s += gridDim.x * wpb) {
-        // boundary: sum_j S_j a_j = -2 E_SS over its own bonds; up count
-        int part = 0;
-        for (int j = lane; j < H.ns; j += 32) {
-            const int f = split_field(v.cls, ncl, v.ss + (size_t)j * ncl, 1, s);
-            part += ((s >> j) & 1) ? f : -f;
+    for (unsigned long long s = blockIdx.x; s < n_walk; s += gridDim.x) {
+        // boundary: sum_j S_j a_j = -2 E_SS over its own bonds (warp 0); up count
+        if (warp == 0) {
+            int part = 0;
+            for (int j = lane; j < H.ns; j += 32) {
+                const int f = split_field(v.cls, ncl, v.ss + (size_t)j * ncl, 1, s);
+                part += ((s >> j) & 1) ? f : -f;
+            }
+            part = warp_sum_i(part);
+            if (lane == 0) sc[2] = (-part / 2 + H.S_SS) / 2;
         }
-        part = warp_sum_i(part);
-        const int e_SS = (-part / 2 + H.S_SS) / 2;
-        const int m_S = __popcll(s);
-        Acc* acc = bufA;
-        Acc* out = bufB;
+        AccBuf<Acc> acc = bufA, out = bufB;
         int rows = 0;
-        if (H.n_comp == 0) {                  // every spin is boundary: the empty convolution
-            if (lane == 0) acc[0] = 1;
-            __syncwarp();
-        }
+        if (H.n_comp == 0 && tid == 0) acc.set(0, (Acc)1);     // every spin is boundary: the empty convolution
         for (int c = 0; c < H.n_comp; ++c) {
             const SplitComp cp = v.comp[c];
             const int nc = cp.nc, MC = nc + 1;
             const uint64_t* sp = v.spin + (size_t)cp.first * ncl * 2;
-            // field on component spin `lane` from the boundary (nc <= 30); with few classes its
-            // record {mask of class 0, mask of class 1, f - J0 deg0 - J1 deg1, f} in shared memory,
-            // so that field(x) = 2 (J0 popc(m0 & x) + J1 popc(m1 & x)) + constant
-            const int myf = lane < nc ? split_field(v.cls, ncl, sp + (size_t)lane * ncl * 2 + 1, 2, s) : 0;
-            if (kFew && lane < nc) {
-                const uint32_t m0 = (uint32_t)sp[(size_t)lane * ncl * 2];
-                const uint32_t m1 = ncl > 1 ? (uint32_t)sp[((size_t)lane * ncl + 1) * 2] : 0u;
-                wsp[lane] = make_uint4(m0, m1, (uint32_t)(myf - J0 * __popc(m0) - J1 * __popc(m1)), (uint32_t)myf);
+            // component spin records: the field from the boundary (both paths), and with few
+            // classes {mask of class 0, mask of class 1, f - J0 deg0 - J1 deg1} so that
+            // field(x) = 2 (J0 popc(m0 & x) + J1 popc(m1 & x)) + constant
+            if (tid < nc) {
+                const int f = split_field(v.cls, ncl, sp + (size_t)tid * ncl * 2 + 1, 2, s);
+                uint32_t m0 = 0, m1 = 0;
+                if (kFew) {
+                    m0 = (uint32_t)sp[(size_t)tid * ncl * 2];
+                    m1 = ncl > 1 ? (uint32_t)sp[((size_t)tid * ncl + 1) * 2] : 0u;
+                }
+                wsp[tid] = make_uint4(m0, m1, (uint32_t)(f - J0 * __popc(m0) - J1 * __popc(m1)), (uint32_t)f);
             }
-            for (int i = lane; i < cp.h_words; i += 32) hist[i] = 0;
-            __syncwarp();
+            for (int i = tid; i < cp.h_words; i += blockDim.x) hist[i] = 0;
+            __syncthreads();
             // internal field plus boundary field of component spin q at configuration x
             auto field = [&](int q, uint32_t xx) -> int {
                 if (kFew) {
                     const uint4 r = wsp[q];
                     return 2 * (J0 * __popc(r.x & xx) + J1 * __popc(r.y & xx)) + (int)r.z;
                 }
-                return split_field(v.cls, ncl, sp + (size_t)q * ncl * 2, 2, xx) + __shfl_sync(FULL, myf, q);
+                return split_field(v.cls, ncl, sp + (size_t)q * ncl * 2, 2, xx) + (int)wsp[q].w;
             };
             auto twice_energy = [&](uint32_t xx) {        // 2 E_c = -sum_q S_q (internal_q + 2 f_q)
                 int t2 = 0;
                 for (int q = 0; q < nc; ++q) {
-                    const int fq = kFew ? (int)wsp[q].w : __shfl_sync(FULL, myf, q);
-                    const int hq = field(q, xx) + fq;
+                    const int hq = field(q, xx) + (int)wsp[q].w;
                     t2 -= ((xx >> q) & 1) ? hq : -hq;
                 }
                 return t2;
             };
-            const int L = nc > 5 ? nc - 5 : 0;
-            const bool active = nc > 5 || lane < (1 << nc);
-            uint32_t x = (uint32_t)lane << L;
-            int e = (twice_energy(x) / 2 + cp.Sc) / 2;
-            int m = __popc(x);
-            // a bin outside the histogram (a bug) is recorded and skipped, never written
-            auto count = [&](int ee, int mm) {
-                if ((unsigned)ee <= (unsigned)cp.Sc && (unsigned)mm <= (unsigned)nc) atomicAdd(&hist[ee * MC + mm], 1u);
-                else bad = true;
-            };
-            if (active) count(e, m);
-            for (uint32_t t = 1; t < (1u << L); ++t) {
-                const int k = __ffs(t) - 1;                          // the same spin in every lane
-                const bool up = (x >> k) & 1;
-                const int hk = field(k, x);
-                e += up ? hk : -hk;
-                m += up ? -1 : 1;
-                x ^= 1u << k;
+            // walk: 2^P walker threads, each the reflected Gray walk over the low L = nc - P bits
+            // with its index in the top P bits
+            const int P = nc < kSplitWalkBits ? nc : kSplitWalkBits, L = nc - P;
+            if (tid < (1 << P)) {
+                uint32_t x = (uint32_t)tid << L;
+                int e = (twice_energy(x) / 2 + cp.Sc) / 2;
+                int m = __popc(x);
+                // a bin outside the histogram (a bug) is recorded and skipped, never written
+                auto count = [&](int ee, int mm) {
+                    if ((unsigned)ee <= (unsigned)cp.Sc && (unsigned)mm <= (unsigned)nc) atomicAdd(&hist[ee * MC + mm], 1u);
+                    else bad = true;
+                };
                 count(e, m);
+                for (uint32_t t = 1; t < (1u << L); ++t) {
+                    const int k = __ffs(t) - 1;                      // the same spin in every walker
+                    const bool up = (x >> k) & 1;
+                    const int hk = field(k, x);
+                    e += up ? hk : -hk;
+                    m += up ? -1 : 1;
+                    x ^= 1u << k;
+                    count(e, m);
+                }
+                // self-check: the tracked bin of the walker's last configuration, recomputed
+                if (e != (twice_energy(x) / 2 + cp.Sc) / 2 || m != __popc(x)) bad = true;
             }
-            // self-check: the tracked bin of the lane's last configuration against a recomputation
-            // (computed in every lane: the recomputation may shuffle across the whole warp)
-            const int e_check = (twice_energy(x) / 2 + cp.Sc) / 2;
-            if (active && (e != e_check || m != __popc(x))) bad = true;
-            __syncwarp();
             if (c == 0) {
-                for (int i = lane; i < H.acc_words; i += 32) acc[i] = 0;
-                __syncwarp();
-                for (int i = lane; i < cp.h_words; i += 32) {
+                for (int i = tid; i < H.acc_words; i += blockDim.x) acc.set(i, (Acc)0);
+                if (tid == 0) { sc[0] = 0; sc[1] = 0; }
+                __syncthreads();
+                for (int i = tid; i < cp.h_words; i += blockDim.x) {
                     const int e1 = i / MC, m1 = i - e1 * MC;
-                    acc[e1 * MO + m1] = hist[i];
+                    acc.set(e1 * MO + m1, (Acc)hist[i]);
                 }
             } else {
-                // the accumulator's nonzero bins, listed once
+                if (tid == 0) { sc[0] = 0; sc[1] = 0; }
+                __syncthreads();
+                // nonzero bins of the accumulator and of the histogram (order free: the products
+                // are summed), and the next accumulator cleared
                 const int used = (rows + 1) * MO;
-                int nl = 0;
-                for (int base = 0; base < used; base += 32) {
-                    const int i = base + lane;
-                    const bool nz = i < used && acc[i] != 0;
-                    const unsigned bal = __ballot_sync(FULL, nz);
-                    if (nz) list[nl + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)i;
-                    nl += __popc(bal);
+                for (int i = tid; i < used; i += blockDim.x)
+                    if (acc.get(i) != 0) list[atomicAdd(&sc[0], 1)] = (uint32_t)i;
+                for (int i = tid; i < cp.h_words; i += blockDim.x) {
+                    const uint32_t hv = hist[i];
+                    if (hv) {
+                        const int e1 = i / MC, m1 = i - e1 * MC;
+                        hlist[atomicAdd(&sc[1], 1)] = (uint64_t)(uint32_t)(e1 * MO + m1) | ((uint64_t)hv << 32);
+                    }
                 }
-                // the histogram's nonzero bins as (shift in the accumulator's layout, count)
-                int nh = 0;
-                int e1 = lane / MC, m1 = lane - e1 * MC;       // (row, column) of bin `lane`, stepped by 32
-                for (int base = 0; base < cp.h_words; base += 32) {
-                    const int i = base + lane;
-                    const uint32_t hv = i < cp.h_words ? hist[i] : 0u;
-                    const unsigned bal = __ballot_sync(FULL, hv != 0);
-                    if (hv)
-                        hlist[nh + __popc(bal & ((1u << lane) - 1u))] =
-                            (uint64_t)(uint32_t)(e1 * MO + m1) | ((uint64_t)hv << 32);
-                    nh += __popc(bal);
-                    for (m1 += 32; m1 >= MC; m1 -= MC) ++e1;
-                }
-                for (int i = lane; i < H.acc_words; i += 32) out[i] = 0;
-                __syncwarp();
-                // out[a + shift] += count * acc[a] over all pairs: each lane keeps up to kRegs of the
-                // accumulator's nonzero bins in registers and the histogram list is read by
-                // broadcast; the products go out as shared-memory reductions (no read-back)
+                for (int i = tid; i < H.acc_words; i += blockDim.x) out.set(i, (Acc)0);
+                __syncthreads();
+                const int nl = sc[0], nh = sc[1];
+                // out[a + shift] += count * acc[a] over all pairs: lanes hold up to kRegs accumulator
+                // bins in registers, warps take the histogram bins in turn, every product is a
+                // shared-memory reduction into the next accumulator
                 constexpr int kRegs = sizeof(Acc) == 8 ? 4 : 8;
                 for (int ch = 0; ch < nl; ch += 32 * kRegs) {
                     uint32_t li[kRegs];
@@ -210,44 +237,42 @@ __global__ void __launch_bounds__(512) split_kernel(const __grid_constant__ Spli
                     for (int k = 0; k < kRegs; ++k) {
                         const int q = ch + lane + 32 * k;
                         li[k] = q < nl ? list[q] : 0u;
-                        av[k] = q < nl ? acc[li[k]] : (Acc)0;
+                        av[k] = q < nl ? acc.get(li[k]) : (Acc)0;
                     }
-                    for (int j = 0; j < nh; ++j) {
+                    for (int j = warp; j < nh; j += nwarps) {
                         const uint64_t hw = hlist[j];
                         const uint32_t hs = (uint32_t)hw;
                         const Acc hv = (Acc)(hw >> 32);
 #pragma unroll
                         for (int k = 0; k < kRegs; ++k)
-                            if (av[k]) atomicAdd(&out[li[k] + hs], hv * av[k]);
+                            if (av[k]) out.add(li[k] + hs, hv * av[k]);
                     }
                 }
-                __syncwarp();
-                Acc* t = acc;
+                const AccBuf<Acc> t = acc;
                 acc = out;
                 out = t;
             }
             rows += cp.Sc;
-            __syncwarp();
+            __syncthreads();
         }
-        // shift by the boundary's bin and add into the CTA's table
+        // shift by the boundary's bin and add into the CTA's table (and at -M: the flip mirror)
+        const int e_SS = sc[2], m_S = __popcll(s);
         const int used = H.EO * MO;
-        int e1 = lane / MO, m1 = lane - e1 * MO;
-        for (int i = lane; i < used; i += 32, m1 += 32) {
-            for (; m1 >= MO; m1 -= MO) ++e1;
-            const Acc val = acc[i];
+        for (int i = tid; i < used; i += blockDim.x) {
+            const Acc val = acc.get(i);
             if (val) {
+                const int e1 = i / MO, m1 = i - e1 * MO;
                 const int row = (e_SS + e1) * (H.n + 1);
                 table_add(row + m_S + m1, (unsigned long long)val);
                 if (H.ns) table_add(row + H.n - m_S - m1, (unsigned long long)val);
             }
         }
-        __syncwarp();
+        __syncthreads();                      // the buffers and scalars are reused by the next s
     }
     if (bad) atomicOr(a.status, 1u);
-    __syncthreads();
-    for (int i = threadIdx.x; i < H.n_bins; i += blockDim.x) {
-        const unsigned long long v = ((unsigned long long)thi[i] << 32) | tlo[i];
-        if (v) atomicAdd(&a.table[i], v);
+    for (int i = tid; i < H.n_bins; i += blockDim.x) {
+        const unsigned long long val = ((unsigned long long)thi[i] << 32) | tlo[i];
+        if (val) atomicAdd(&a.table[i], val);
     }
 }
 
@@ -264,21 +289,18 @@ void launch_split(const SplitPrepared& prep, const uint64_t* d_blob, unsigned lo
     const SplitHeader& H = *reinterpret_cast<const SplitHeader*>(prep.blob.data());
     const bool u64 = prep.plan.use_u64;
     const DeviceInfo d = device_info();
-    const size_t fixed = split_smem_bytes((int)prep.blob.size(), H, u64, 0);
-    const size_t per_warp = split_warp_bytes(H, u64);
-    const size_t limit = (size_t)d.smem_optin;
-    if (fixed + per_warp > limit) fail(ISG_ERR_TOO_LARGE, "split buffers exceed shared memory");
-    const int warps = (int)std::min<size_t>(16, (limit - fixed) / per_warp);
-    const size_t smem = fixed + (size_t)warps * per_warp;
-    const int ctas_per_sm = std::max(1, (int)std::min<size_t>(4, (size_t)d.smem_per_sm / (smem + 1024)));
+    const size_t smem = split_smem_bytes((int)prep.blob.size(), H, u64, 1);
+    if (smem > (size_t)d.smem_optin) fail(ISG_ERR_TOO_LARGE, "split buffers exceed shared memory");
+    // 64 registers x 512 threads: at most two CTAs per SM
+    const int ctas_per_sm = std::max(1, (int)std::min<size_t>(2, (size_t)d.smem_per_sm / (smem + 1024)));
     const unsigned long long n_s = 1ull << H.ns;
-    const unsigned long long want = (n_s + warps - 1) / warps;
-    const int grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(want, (unsigned long long)d.sms * ctas_per_sm));
+    const unsigned long long n_walk = H.ns ? n_s >> 1 : n_s;
+    const int grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(n_walk, (unsigned long long)d.sms * ctas_per_sm));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     SplitArgs a{d_blob, (int)prep.blob.size(), table, status, n_s};
     auto launch = [&](auto kernel) {
         ISG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kernel<<<grid, 32 * warps, smem, s>>>(a);
+        kernel<<<grid, kSplitThreads, smem, s>>>(a);
     };
     const bool few = H.n_cls <= 2;
     if (u64) {

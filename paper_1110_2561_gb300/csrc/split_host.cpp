@@ -129,22 +129,24 @@ void evaluate(const isg_graph& g, const WeightIndex& wi, int n_cls, Candidate& c
     c.u64 = inner > 31;
     const int64_t acc_words = (EO + 1) * MO;
     const size_t acc_bytes = c.u64 ? 8 : 4;
-    const size_t per_warp = 512 + 12 * (size_t)hmax + 32 + (2 * acc_bytes + 4) * (size_t)acc_words;
+    const size_t per_cta = 768 + 12 * (size_t)hmax + 32 + (2 * acc_bytes + 4) * (size_t)acc_words;
     const size_t prog_bytes = 64 + 8 * ((size_t)n_cls * (1 + ns) + 2 * k + (size_t)(g.n - ns) * 2 * n_cls);
     const size_t table_bytes = 8 * (size_t)(g.S + 1) * (g.n + 1);
     const size_t budget = 227 * 1024 - 1024;
-    if (prog_bytes + table_bytes + 2 * per_warp > budget) return;
-    c.warps = (int)std::min<size_t>(16, (budget - prog_bytes - table_bytes) / per_warp);
+    if (prog_bytes + table_bytes + per_cta > budget) return;
+    c.warps = kSplitThreads / 32;
     // cost per boundary configuration
-    double per_s = 20 + ceil32(ns) * (6 + 3.0 * n_cls);
+    double per_s = 40 + ceil32(ns) * (6 + 3.0 * n_cls);            // plus a few CTA barriers
     double nnz_acc = 0, rows = 1;
     double configs = 0;
     for (size_t i = 0; i < k; ++i) {
         const double hw = (double)(c.Sc[i] + 1) * (nc[i] + 1);
         const double walk = std::ldexp(1.0, nc[i]);
         configs += walk;
-        per_s += ceil32(nc[i]) * (4 + 3.0 * n_cls) + ceil32(hw) * 2 + nc[i] * (4 + 3.0 * n_cls) +
-                 std::max(1.0, walk / 32) * (8 + 3.0 * n_cls);
+        // walkers: 2^min(9, nc) threads, each a from-scratch start (and recheck) and its walk
+        const double walkers = std::ldexp(1.0, std::min(nc[i], kSplitWalkBits));
+        per_s += ceil32(nc[i]) * (4 + 3.0 * n_cls) + ceil32(hw) * 2 +
+                 ceil32(walkers) * (2 * nc[i] * (4 + 3.0 * n_cls) + (walk / walkers) * (8 + 3.0 * n_cls));
         const double nnz_h = std::min(hw, walk);
         if (i == 0) {
             nnz_acc = nnz_h;
@@ -157,9 +159,10 @@ void evaluate(const isg_graph& g, const WeightIndex& wi, int n_cls, Candidate& c
     }
     per_s += ceil32((double)EO * MO) * 5;
     c.visits = std::ldexp(configs, ns > 0 ? ns - 1 : 0);         // half the boundary: flip mirrors
-    // the walk and the convolution are latency-bound: fewer than 8 warps per SM (large buffers)
-    // leave issue slots empty in proportion
-    c.cost = std::ldexp(per_s, ns > 0 ? ns - 1 : 0) * (8.0 / std::min(8, c.warps));
+    // one CTA per walked boundary configuration: fewer of them than CTA slots (about two per SM)
+    // leaves SMs idle, so the work counts at least one full wave
+    const double n_walk = std::ldexp(1.0, ns > 0 ? ns - 1 : 0), wave = 2.0 * 152;
+    c.cost = per_s * std::max(n_walk, wave);
 }
 
 }  // namespace
@@ -335,7 +338,8 @@ void emulate_split(const std::vector<uint64_t>& blob, int64_t* g_out) {
         const SplitWarpLayout L = split_warp_layout(h, u64);
         const size_t base = split_prog_bytes((int)blob.size()) + split_table_bytes(h);
         const size_t acc = (u64 ? 8 : 4) * (size_t)h.acc_words;
-        if (base % 16 || L.bytes % 16 || L.spins % 16 || L.acc_a < L.spins + 16 * 32 || L.acc_a % 8 || L.acc_b % 8 || L.hlist % 8 || L.list % 4 || L.hist % 4 ||
+        if (base % 16 || L.bytes % 16 || L.spins % 16 || L.scalars < L.spins + 16 * 32 || L.scalars % 4 ||
+            L.acc_a < L.scalars + 4 * 16 || L.acc_a % 8 || L.acc_b % 8 || L.hlist % 8 || L.list % 4 || L.hist % 4 ||
             L.acc_b < L.acc_a + acc || L.hlist < L.acc_b + acc || L.list < L.hlist + 8 * (size_t)h.max_h ||
             L.hist < L.list + 4 * (size_t)h.acc_words || L.bytes < L.hist + 4 * (size_t)h.max_h)
             fail(ISG_ERR_INTERNAL, "split kernel shared-memory layout misaligned or overlapping");
@@ -374,10 +378,9 @@ void emulate_split(const std::vector<uint64_t>& blob, int64_t* g_out) {
             std::vector<int64_t> f(nc);
             for (int a = 0; a < nc; ++a) f[a] = field(sp + (size_t)a * ncl * 2 + 1, 2, s);
             std::fill(hist.begin(), hist.end(), 0u);
-            const int L = nc > 5 ? nc - 5 : 0;
-            const int lanes = nc > 5 ? 32 : (1 << nc);
-            for (int lane = 0; lane < lanes; ++lane) {
-                uint32_t x = (uint32_t)lane << L;
+            const int P = nc < kSplitWalkBits ? nc : kSplitWalkBits, L = nc - P;
+            for (int walker = 0; walker < (1 << P); ++walker) {
+                uint32_t x = (uint32_t)walker << L;
                 int64_t twoE = 0;                    // 2 E_c(x) = -sum_a S_a (internal field + 2 f_a)
                 for (int a = 0; a < nc; ++a) {
                     const int64_t hin = field(sp + (size_t)a * ncl * 2, 2, x);

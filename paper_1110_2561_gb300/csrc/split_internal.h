@@ -32,6 +32,8 @@ namespace isg {
 constexpr int kSplitMaxClasses = 16;     // distinct signed couplings
 constexpr int kSplitMaxComp = 64;
 constexpr int kSplitMaxCompSpins = 30;   // a component's configurations fit a 32-bit word walk
+constexpr int kSplitThreads = 512;       // threads of a split CTA (one boundary configuration at a time)
+constexpr int kSplitWalkBits = 9;        // 2^9 = 512 walkers per component (fewer for small ones)
 
 // Program header (32-bit words at the start of the blob).
 struct SplitHeader {
@@ -118,17 +120,19 @@ void launch_split(const SplitPrepared& prep, const uint64_t* d_blob, unsigned lo
                   void* stream);
 
 // Shared memory of the split kernel: the program, the CTA's table (32-bit low and high words per
-// bin), then per warp (each block 16-byte aligned): 32 component-spin records, two accumulators, the histogram's nonzero
+// bin), then the CTA's working block (16-byte aligned): 32 component-spin records, scalars, two
+// accumulators, the histogram's nonzero
 // list (8-byte entries), the accumulator's nonzero list and a component histogram (4-byte
 // entries). The 8-byte arrays come first so that they stay 8-byte aligned whatever the sizes.
 struct SplitWarpLayout {
-    size_t spins, acc_a, acc_b, hlist, list, hist, bytes;   // byte offsets within the warp's block; its size
+    size_t spins, scalars, acc_a, acc_b, hlist, list, hist, bytes;   // byte offsets within the block; its size
 };
 ISG_SPLIT_HD inline SplitWarpLayout split_warp_layout(const SplitHeader& h, bool u64) {
     SplitWarpLayout L;
     const size_t acc = (u64 ? 8 : 4) * (size_t)h.acc_words;
     L.spins = 0;                                      // 32 records of 16 bytes (component spins)
-    L.acc_a = 512;
+    L.scalars = 512;                                  // a few ints shared by the CTA
+    L.acc_a = 768;
     L.acc_b = L.acc_a + ((acc + 7) & ~(size_t)7);
     L.hlist = L.acc_b + ((acc + 7) & ~(size_t)7);
     L.list = L.hlist + 8 * (size_t)h.max_h;
