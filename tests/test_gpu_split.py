@@ -119,3 +119,15 @@ def test_split_random_graphs(isg, cuda):
         assert np.array_equal(got, oracle.g_edges(lat.n, lat.edges)), lat.name
         done += 1
     assert done >= 30
+
+
+@pytest.mark.parametrize("shape,seed", [((6, 7), 21), ((7, 7), 21)], ids=["6x7-32bit", "7x7-64bit"])
+def test_split_large_four_classes(isg, cuda, shape, seed):
+    """Tori with couplings in {-2, -1, 1, 2} (four classes: the general field evaluation): on the
+    6x7 torus the counts fit 32 bits, on the 7x7 torus (N = 49) they need the 64-bit accumulators.
+    Every bin against the oracle's frontier programme."""
+    lat = w.with_random_couplings(w.square(*shape, True), w.SplitMix64(seed), (-2, -1, 1, 2))
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = isg.isg_enumerate_split(gh)
+    assert int(g.sum()) == 2 ** lat.n
+    assert np.array_equal(g, oracle.g_frontier(lat.n, lat.edges, 16))
