@@ -84,6 +84,21 @@ struct AccBuf {
     }
 };
 
+// The low block of a component walk: from its all-down state, steps T = 1 .. 2^B - 1 of the
+// reflected Gray code, unrolled at compile time (the flipped bit, its direction and the up count
+// are constants): one add and one shared reduction per configuration. h[k] is the field on low spin
+// k, constant over the block because low spins have no bond among them.
+template <int B, int T>
+__device__ __forceinline__ void split_low_steps(int e, int base, const int (&h)[B], uint32_t* hist, int MC) {
+    if constexpr (T < (1 << B)) {
+        constexpr int k = split_ctz(T);
+        constexpr bool was_up = (split_gray(T - 1) >> k) & 1;
+        e += was_up ? h[k] : -h[k];
+        atomicAdd(&hist[e * MC + base + split_popc(split_gray(T))], 1u);
+        split_low_steps<B, T + 1>(e, base, h, hist, MC);
+    }
+}
+
 // kFew: at most two coupling classes (every lattice here: J = 1, or +-J), so a spin's field is
 // two masked popcounts of a 32-bit component word and a constant; otherwise a loop over classes.
 //
@@ -177,28 +192,58 @@ __global__ void __launch_bounds__(kSplitThreads) split_kernel(const __grid_const
             };
             // walk: 2^P walker threads, each the reflected Gray walk over the low L = nc - P bits
             // with its index in the top P bits
-            const int P = nc < kSplitWalkBits ? nc : kSplitWalkBits, L = nc - P;
+            const int P = split_walk_bits(nc, cp.low), L = nc - P;
             if (tid < (1 << P)) {
                 uint32_t x = (uint32_t)tid << L;
                 int e = (twice_energy(x) / 2 + cp.Sc) / 2;
                 int m = __popc(x);
-                // a bin outside the histogram (a bug) is recorded and skipped, never written
-                auto count = [&](int ee, int mm) {
-                    if ((unsigned)ee <= (unsigned)cp.Sc && (unsigned)mm <= (unsigned)nc) atomicAdd(&hist[ee * MC + mm], 1u);
-                    else bad = true;
-                };
-                count(e, m);
-                for (uint32_t t = 1; t < (1u << L); ++t) {
-                    const int k = __ffs(t) - 1;                      // the same spin in every walker
-                    const bool up = (x >> k) & 1;
-                    const int hk = field(k, x);
-                    e += up ? hk : -hk;
-                    m += up ? -1 : 1;
-                    x ^= 1u << k;
+                if (cp.low == kSplitLow) {
+                    // mid bits in Gray order; at each mid state the low block from all down, its
+                    // fields in registers, checked once against the histogram's range
+                    for (uint32_t tm = 0; tm < (1u << (L - kSplitLow)); ++tm) {
+                        if (tm) {
+                            const int k = kSplitLow + __ffs(tm) - 1;         // the same spin in every walker
+                            const bool up = (x >> k) & 1;
+                            const int hk = field(k, x);
+                            e += up ? hk : -hk;
+                            m += up ? -1 : 1;
+                            x ^= 1u << k;
+                        }
+                        int h[kSplitLow];
+                        int lo = e, hi = e;
+#pragma unroll
+                        for (int j = 0; j < kSplitLow; ++j) {
+                            h[j] = field(j, x);
+                            lo -= h[j] > 0 ? h[j] : 0;
+                            hi -= h[j] < 0 ? h[j] : 0;
+                        }
+                        if (lo >= 0 && hi <= cp.Sc && m + kSplitLow <= nc) {
+                            atomicAdd(&hist[e * MC + m], 1u);
+                            split_low_steps<kSplitLow, 1>(e, m, h, hist, MC);
+                        } else {
+                            bad = true;                                       // a bug: recorded, not written
+                        }
+                    }
+                } else {
+                    // a bin outside the histogram (a bug) is recorded and skipped, never written
+                    auto count = [&](int ee, int mm) {
+                        if ((unsigned)ee <= (unsigned)cp.Sc && (unsigned)mm <= (unsigned)nc) atomicAdd(&hist[ee * MC + mm], 1u);
+                        else bad = true;
+                    };
                     count(e, m);
+                    for (uint32_t t = 1; t < (1u << L); ++t) {
+                        const int k = __ffs(t) - 1;                      // the same spin in every walker
+                        const bool up = (x >> k) & 1;
+                        const int hk = field(k, x);
+                        e += up ? hk : -hk;
+                        m += up ? -1 : 1;
+                        x ^= 1u << k;
+                        count(e, m);
+                    }
                 }
-                // self-check: the tracked bin of the walker's last configuration, recomputed
-                if (e != (twice_energy(x) / 2 + cp.Sc) / 2 || m != __popc(x)) bad = true;
+                // self-check (the first warp's walkers): the tracked bin of the last configuration
+                // (low bits all down in the low-block walk), recomputed
+                if (tid < 32 && (e != (twice_energy(x) / 2 + cp.Sc) / 2 || m != __popc(x))) bad = true;
             }
             if (c == 0) {
                 for (int i = tid; i < H.acc_words; i += blockDim.x) acc.set(i, (Acc)0);

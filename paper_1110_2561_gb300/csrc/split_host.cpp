@@ -130,7 +130,7 @@ void evaluate(const isg_graph& g, const WeightIndex& wi, int n_cls, Candidate& c
     const int64_t acc_words = (EO + 1) * MO;
     const size_t acc_bytes = c.u64 ? 8 : 4;
     const size_t per_cta = 768 + 12 * (size_t)hmax + 32 + (2 * acc_bytes + 4) * (size_t)acc_words;
-    const size_t prog_bytes = 64 + 8 * ((size_t)n_cls * (1 + ns) + 2 * k + (size_t)(g.n - ns) * 2 * n_cls);
+    const size_t prog_bytes = 64 + 8 * ((size_t)n_cls * (1 + ns) + 4 * k + (size_t)(g.n - ns) * 2 * n_cls);
     const size_t table_bytes = 8 * (size_t)(g.S + 1) * (g.n + 1);
     const size_t budget = 227 * 1024 - 1024;
     if (prog_bytes + table_bytes + per_cta > budget) return;
@@ -143,10 +143,14 @@ void evaluate(const isg_graph& g, const WeightIndex& wi, int n_cls, Candidate& c
         const double hw = (double)(c.Sc[i] + 1) * (nc[i] + 1);
         const double walk = std::ldexp(1.0, nc[i]);
         configs += walk;
-        // walkers: 2^min(9, nc) threads, each a from-scratch start (and recheck) and its walk
-        const double walkers = std::ldexp(1.0, std::min(nc[i], kSplitWalkBits));
-        per_s += ceil32(nc[i]) * (4 + 3.0 * n_cls) + ceil32(hw) * 2 +
-                 ceil32(walkers) * (2 * nc[i] * (4 + 3.0 * n_cls) + (walk / walkers) * (8 + 3.0 * n_cls));
+        // walkers: 2^P threads, each a from-scratch start and its walk (one warp also rechecks);
+        // components large enough for a low block (assumed found) walk it at about 4 operations
+        // per configuration plus its fields and the mid flip per 2^kSplitLow configurations
+        const int low = nc[i] >= kSplitLowMinSpins ? kSplitLow : 0;
+        const double walkers = std::ldexp(1.0, split_walk_bits(nc[i], low));
+        const double per_config = low ? 4 + (kSplitLow * (6 + 3.0 * n_cls) + 24 + 3.0 * n_cls) / 32 : 8 + 3.0 * n_cls;
+        per_s += ceil32(nc[i]) * (4 + 3.0 * n_cls) + ceil32(hw) * 2 + nc[i] * (4 + 3.0 * n_cls) +
+                 ceil32(walkers) * (nc[i] * (4 + 3.0 * n_cls) + (walk / walkers) * per_config);
         const double nnz_h = std::min(hw, walk);
         if (i == 0) {
             nnz_acc = nnz_h;
@@ -273,7 +277,7 @@ std::vector<uint64_t> build_split_program(const isg_graph& g, const SplitPlan& p
     h.off_cls = 8;
     h.off_ss = h.off_cls + n_cls;
     h.off_comp = h.off_ss + ns * n_cls;
-    h.off_spin = h.off_comp + 2 * k;                // a SplitComp record is two words
+    h.off_spin = h.off_comp + 4 * k;                // a SplitComp record is four words
     std::vector<uint64_t> blob((size_t)h.off_spin + (size_t)n_in * 2 * n_cls, 0);
     int64_t S_SS = 0;
     for (int a = 0; a < ns; ++a)
@@ -288,8 +292,32 @@ std::vector<uint64_t> build_split_program(const isg_graph& g, const SplitPlan& p
     int64_t EO = 1, MO = 1, hmax = 0, sumSc = 0;
     int first = 0;
     for (int c = 0; c < k; ++c) {
-        const auto& v = p.comps[c];
+        // a component of at least kSplitLowMinSpins spins gets a low block: kSplitLow of its spins
+        // with no bond among them (greedy, fewest bonds inside the component first) as its lowest
+        // local bits, so a walk can hold their fields in registers
+        std::vector<int> v = p.comps[c];
         const int nc = (int)v.size();
+        int low = 0;
+        if (nc >= kSplitLowMinSpins) {
+            std::vector<int> order(nc), pick;
+            for (int a = 0; a < nc; ++a) order[a] = a;
+            auto deg = [&](int a) { int d = 0; for (int b = 0; b < nc; ++b) d += b != a && coupling(v[a], v[b]) != 0; return d; };
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return deg(a) < deg(b); });
+            for (int a : order) {
+                bool free = true;
+                for (int b : pick) free = free && coupling(v[a], v[b]) == 0;
+                if (free) pick.push_back(a);
+                if ((int)pick.size() == kSplitLow) break;
+            }
+            if ((int)pick.size() == kSplitLow) {
+                std::vector<int> v2;
+                for (int a : pick) v2.push_back(v[a]);
+                for (int a = 0; a < nc; ++a)
+                    if (std::find(pick.begin(), pick.end(), a) == pick.end()) v2.push_back(v[a]);
+                v = v2;
+                low = kSplitLow;
+            }
+        }
         int64_t Sc = 0;
         for (int a = 0; a < nc; ++a) {
             for (int b = a + 1; b < nc; ++b) Sc += std::llabs(coupling(v[a], v[b]));
@@ -299,9 +327,9 @@ std::vector<uint64_t> build_split_program(const isg_graph& g, const SplitPlan& p
             if (c2 != c)
                 for (int a : v) for (int b : p.comps[c2])
                     if (coupling(a, b)) fail(ISG_ERR_INTERNAL, "split components are not independent");
-        SplitComp rec{nc, (int32_t)Sc, first, (int32_t)((Sc + 1) * (nc + 1))};
-        static_assert(sizeof(SplitComp) == 16, "component record is two words");
-        std::memcpy(&blob[h.off_comp + 2 * (size_t)c], &rec, sizeof rec);
+        SplitComp rec{nc, (int32_t)Sc, first, (int32_t)((Sc + 1) * (nc + 1)), low, {0, 0, 0}};
+        static_assert(sizeof(SplitComp) == 32, "component record is four words");
+        std::memcpy(&blob[h.off_comp + 4 * (size_t)c], &rec, sizeof rec);
         for (int a = 0; a < nc; ++a)
             for (int t = 0; t < n_cls; ++t) {
                 uint64_t im = 0, sm = 0;
@@ -378,10 +406,17 @@ void emulate_split(const std::vector<uint64_t>& blob, int64_t* g_out) {
             std::vector<int64_t> f(nc);
             for (int a = 0; a < nc; ++a) f[a] = field(sp + (size_t)a * ncl * 2 + 1, 2, s);
             std::fill(hist.begin(), hist.end(), 0u);
-            const int P = nc < kSplitWalkBits ? nc : kSplitWalkBits, L = nc - P;
+            const int P = split_walk_bits(nc, cp.low), L = nc - P;
+            auto count = [&](int64_t e, int m) {
+                if (e < 0 || e > cp.Sc || m < 0 || m > nc) fail(ISG_ERR_INTERNAL, "component bin out of range");
+                hist[(size_t)e * MC + m] += 1;
+            };
+            auto field_at = [&](int a, uint32_t x) {
+                return field(sp + (size_t)a * ncl * 2, 2, x) + f[a];
+            };
             for (int walker = 0; walker < (1 << P); ++walker) {
                 uint32_t x = (uint32_t)walker << L;
-                int64_t twoE = 0;                    // 2 E_c(x) = -sum_a S_a (internal field + 2 f_a)
+                int64_t twoE = 0;                    // 2 E_c(x) = -sum_q S_q (internal field + 2 f_q)
                 for (int a = 0; a < nc; ++a) {
                     const int64_t hin = field(sp + (size_t)a * ncl * 2, 2, x);
                     const int64_t sa = ((x >> a) & 1) ? 1 : -1;
@@ -390,16 +425,41 @@ void emulate_split(const std::vector<uint64_t>& blob, int64_t* g_out) {
                 if ((twoE / 2 + cp.Sc) & 1) fail(ISG_ERR_INTERNAL, "component energy parity");
                 int64_t e = (twoE / 2 + cp.Sc) / 2;
                 int m = split_popc64(x);
-                for (uint32_t t = 0;; ++t) {
-                    if (e < 0 || e > cp.Sc || m < 0 || m > nc) fail(ISG_ERR_INTERNAL, "component bin out of range");
-                    hist[(size_t)e * MC + m] += 1;
-                    if (t + 1 >= (1u << L)) break;
-                    const int kk = __builtin_ctz(t + 1);
-                    const bool up = (x >> kk) & 1;
-                    const int64_t hk = field(sp + (size_t)kk * ncl * 2, 2, x) + f[kk];
-                    e += up ? hk : -hk;
-                    m += up ? -1 : 1;
-                    x ^= 1u << kk;
+                if (cp.low) {
+                    // mid bits walked in Gray order; at each mid state the low block (all down to
+                    // start, its fields fixed) in its own Gray order
+                    if (cp.low != kSplitLow || L < cp.low) fail(ISG_ERR_INTERNAL, "bad low block");
+                    for (uint32_t tm = 0; tm < (1u << (L - cp.low)); ++tm) {
+                        if (tm) {
+                            const int kk = cp.low + __builtin_ctz(tm);
+                            const bool up = (x >> kk) & 1;
+                            const int64_t hk = field_at(kk, x);
+                            e += up ? hk : -hk;
+                            m += up ? -1 : 1;
+                            x ^= 1u << kk;
+                        }
+                        int64_t hl[kSplitLow];
+                        for (int j = 0; j < cp.low; ++j) hl[j] = field_at(j, x);
+                        count(e, m);
+                        int64_t el = e;
+                        for (int tl = 1; tl < (1 << cp.low); ++tl) {
+                            const int kk = split_ctz(tl);
+                            const bool was_up = (split_gray(tl - 1) >> kk) & 1;
+                            el += was_up ? hl[kk] : -hl[kk];
+                            count(el, m + split_popc(split_gray(tl)));
+                        }
+                    }
+                } else {
+                    for (uint32_t t = 0;; ++t) {
+                        count(e, m);
+                        if (t + 1 >= (1u << L)) break;
+                        const int kk = __builtin_ctz(t + 1);
+                        const bool up = (x >> kk) & 1;
+                        const int64_t hk = field_at(kk, x);
+                        e += up ? hk : -hk;
+                        m += up ? -1 : 1;
+                        x ^= 1u << kk;
+                    }
                 }
             }
             if (c == 0) {

@@ -33,7 +33,23 @@ constexpr int kSplitMaxClasses = 16;     // distinct signed couplings
 constexpr int kSplitMaxComp = 64;
 constexpr int kSplitMaxCompSpins = 30;   // a component's configurations fit a 32-bit word walk
 constexpr int kSplitThreads = 512;       // threads of a split CTA (one boundary configuration at a time)
-constexpr int kSplitWalkBits = 9;        // 2^9 = 512 walkers per component (fewer for small ones)
+constexpr int kSplitWalkBits = 9;        // at most 2^9 = 512 walkers per component
+constexpr int kSplitLow = 5;             // size of a component walk's low block
+constexpr int kSplitLowMinSpins = 12;    // components given a low block: at least this many spins
+
+// Walker bits P of a component of nc spins: 2^P walkers (every thread of the CTA where the
+// component is large enough: idle threads cost more than short walks), each walking
+// 2^(nc - P) configurations, and at least its low block when it has one.
+ISG_SPLIT_HD inline int split_walk_bits(int nc, int low) {
+    const int cap = nc - low;
+    return cap < kSplitWalkBits ? (cap < 0 ? 0 : cap) : kSplitWalkBits;
+}
+
+// Compile-time bit helpers for the unrolled low block (reflected Gray code: step t flips bit
+// ctz(t); the state after step t is gray(t)).
+ISG_SPLIT_HD constexpr int split_ctz(int x) { return (x & 1) ? 0 : 1 + split_ctz(x >> 1); }
+ISG_SPLIT_HD constexpr int split_popc(int x) { return x ? (x & 1) + split_popc(x >> 1) : 0; }
+ISG_SPLIT_HD constexpr int split_gray(int t) { return t ^ (t >> 1); }
 
 // Program header (32-bit words at the start of the blob).
 struct SplitHeader {
@@ -44,16 +60,18 @@ struct SplitHeader {
 };
 static_assert(sizeof(SplitHeader) == 64, "header is 8 words");
 
-// Per component (two 64-bit words: four 32-bit fields).
+// Per component (four 64-bit words).
 struct SplitComp {
     int32_t nc, Sc, first, h_words;      // spins, sum |J| touching it, index of its first spin record, (Sc+1)(nc+1)
+    int32_t low;                         // kSplitLow: local bits 0..4 are mutually unbonded (a low block); else 0
+    int32_t reserved[3];
 };
 
 // Sections (64-bit words):
 //   cls[n_cls]                 signed coupling of each class (int64)
 //   ss[ns * n_cls]             for boundary spin j and class t: mask over boundary bits of its boundary
 //                              neighbours with that coupling
-//   comp[2 n_comp]             SplitComp records (two words each)
+//   comp[4 n_comp]             SplitComp records (four words each)
 //   spin[(sum nc) * 2 n_cls]   for component spin k (components in order) and class t: mask over the
 //                              component's own bits (internal neighbours), then mask over boundary bits
 struct SplitView {

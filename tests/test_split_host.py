@@ -139,3 +139,13 @@ def test_emulated_split_random_graphs(isg, k):
         assert "TOO_LARGE" in str(e)
         return
     assert np.array_equal(got, oracle.g_edges(lat.n, lat.edges))
+
+
+@pytest.mark.parametrize("lat", [w.square(6, 6, True), w.with_random_couplings(w.square(5, 6, True), w.SplitMix64(4), (-1, 1))],
+                         ids=lambda l: l.name)
+def test_emulated_split_low_block(isg, lat):
+    """Lattices whose components are large enough for a low block (walked with its fields held
+    fixed and its configurations unrolled): the emulated kernel equals the frontier oracle."""
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    assert isg.isg_split_plan(gh)["largest_component"] >= 12
+    assert np.array_equal(isg.isg_debug_emulate_split(gh), oracle.g_frontier(lat.n, lat.edges, 16))
