@@ -401,12 +401,12 @@ def extra_measurements(stream, dev):
     # the same exact tables from 2^|S| * sum 2^|C| visits
     split = {}
     for name, lat in (("torus6x6", workloads.square(6, 6, True)), ("cubic3x3x4", workloads.cubic(3, 3, 4, True)),
-                      ("torus7x7", workloads.square(7, 7, True))):
+                      ("torus7x7", workloads.square(7, 7, True)), ("torus8x8", workloads.square(8, 8, True))):
         hs = isg.isg_graph_create(lat.n, lat.edges)
         gs = torch.zeros(isg.table_shape(hs), dtype=torch.int64, device=dev)
         plan_s = isg.isg_split_plan(hs)
         ms = _event_ms(lambda: isg.isg_enumerate_split(hs, gs, stream), stream, 3)
-        tot = int(gs.sum().item())
+        tot = sum(int(v) for v in gs.cpu().numpy().ravel())       # 2^64 for N = 64: Python integers
         split[name] = {"N": lat.n, "ms": ms, "boundary_spins": plan_s["boundary_spins"],
                        "components": plan_s["components"], "largest_component": plan_s["largest_component"],
                        "visits": plan_s["visits"], "effective_configs_per_s": 2.0 ** lat.n / (ms * 1e-3),

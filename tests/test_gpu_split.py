@@ -131,3 +131,22 @@ def test_split_large_four_classes(isg, cuda, shape, seed):
     g = isg.isg_enumerate_split(gh)
     assert int(g.sum()) == 2 ** lat.n
     assert np.array_equal(g, oracle.g_frontier(lat.n, lat.edges, 16))
+
+
+def test_split_torus_8x8(isg, cuda):
+    """The 8x8 torus, N = 64: all 2^64 configurations (the largest graph the library takes). No
+    table oracle reaches it, so it is pinned by facts that hold at any size: sum 2^64 (in Python
+    integers), every column C(64, m), the M -> -M and bipartite E -> -E symmetries, two ground
+    states, and ln Z from the table against Kaufman's closed form at four temperatures."""
+    lat = w.square(8, 8, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = isg.isg_enumerate_split(gh)
+    assert sum(int(v) for v in g.ravel()) == 2 ** 64
+    assert all(sum(int(v) for v in g[:, m]) == math.comb(64, m) for m in range(65))
+    assert np.array_equal(g, g[:, ::-1])
+    assert np.array_equal(g.sum(axis=1), g.sum(axis=1)[::-1])
+    assert int(g[0, 0]) == 1 and int(g[0, 64]) == 1 and not g[0, 1:64].any()
+    T = np.array([1.5, 2.269, 3.0, 5.0])
+    lz = isg.isg_thermo(g, gh, T, [0.0], isg.ISG_FP64)[0][:, 0]
+    for t, l in zip(T, lz):
+        assert abs(l - kaufman_logz(8, 8, t)) <= 1e-12 * abs(l)
