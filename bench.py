@@ -412,6 +412,27 @@ def extra_measurements(stream, dev):
                        "visits": plan_s["visits"], "effective_configs_per_s": 2.0 ** lat.n / (ms * 1e-3),
                        "visits_per_s": plan_s["visits"] / (ms * 1e-3), "sum_g_equals_2^N": tot == 2 ** lat.n}
     out["split_and_convolve"] = split
+    # derived physics at sizes only the split reaches: exact tables of the L x L tori (L >= 6 by
+    # split-and-convolve), their specific-heat maxima, and the Binder-cumulant crossings of
+    # neighbouring sizes (both approach the infinite-lattice 2 / ln(1 + sqrt 2) = 2.269)
+    Tb = np.linspace(1.8, 3.0, 2401)
+    series, u4 = {}, {}
+    t0 = time.perf_counter()
+    for L in range(4, 9):
+        lf = workloads.square(L, L, True)
+        hf = isg.isg_graph_create(lf.n, lf.edges)
+        tab = isg.isg_enumerate_split(hf) if L >= 6 else isg.isg_enumerate(hf)
+        tp, cpk = isg.isg_specific_heat_peak(tab, hf, 0.0, 1.5, 3.5, isg.ISG_FP64)
+        u4[L] = isg.isg_magnetisation(tab, hf, Tb, [0.0], isg.ISG_FP64)[3][:, 0]
+        series[f"{L}x{L}"] = {"N": lf.n, "T_peak": tp, "C_peak_per_spin": cpk / lf.n}
+    for L in range(4, 8):
+        d = u4[L + 1] - u4[L]
+        k = np.nonzero(np.diff(np.sign(d)))[0]
+        if len(k):
+            k = int(k[0])
+            series[f"binder_crossing_{L}x{L}_{L + 1}x{L + 1}"] = float(Tb[k] + (Tb[k + 1] - Tb[k]) * d[k] / (d[k] - d[k + 1]))
+    series["seconds"] = time.perf_counter() - t0
+    out["finite_size_series_tori"] = series
     # cubic 3x3x4 torus: thermodynamics on 512 T x 256 h, FP32 vs FP64
     lat = workloads.cubic(3, 3, 4, True)
     gh = isg.isg_graph_create(lat.n, lat.edges)

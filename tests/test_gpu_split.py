@@ -150,3 +150,17 @@ def test_split_torus_8x8(isg, cuda):
     lz = isg.isg_thermo(g, gh, T, [0.0], isg.ISG_FP64)[0][:, 0]
     for t, l in zip(T, lz):
         assert abs(l - kaufman_logz(8, 8, t)) <= 1e-12 * abs(l)
+
+
+def test_specific_heat_peak_8x8_kaufman(isg, cuda):
+    """The specific-heat maximum of the 8x8 torus (N = 64) from its exact table (split-and-
+    convolve, then isg_specific_heat_peak in FP64) against the maximum of Kaufman's closed-form
+    C(T), and the value of C there."""
+    from closed_forms import kaufman_C, kaufman_C_peak
+    lat = w.square(8, 8, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = isg.isg_enumerate_split(gh)
+    t_gpu, c_gpu = isg.isg_specific_heat_peak(g, gh, 0.0, 1.5, 3.5, isg.ISG_FP64)
+    t_k = kaufman_C_peak(8, 8, kaufman_C_peak(8, 8, t_gpu))
+    assert abs(t_gpu - t_k) <= 1e-5 * t_k
+    assert abs(c_gpu - kaufman_C(8, 8, t_gpu)) <= 1e-5 * c_gpu
