@@ -238,7 +238,6 @@ def run_isg(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": WORKLOAD if not shard else f"shard 0 of 2^{args.shard_bits} of: " + WORKLOAD,
-                       "global_batch": world, "seq_len": None,
                        "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)",
                        "plan": {k: plan[k] for k in ("q", "b", "tasks", "threads", "copies", "ctas_per_sm", "G",
                                                      "n_e_compact", "stride")},
@@ -531,7 +530,7 @@ def run_reference(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD, "global_batch": 1, "seq_len": None, "parallelism": "host cores"},
+        "config": {"workload": WORKLOAD, "parallelism": "host cores"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
