@@ -461,6 +461,9 @@ def extra_measurements(stream, dev):
                                 "grid": "512 T in [0.5,8] x 256 h in [-2,2]", "fp64_ms": t64, "fp32_ms": t32,
                                 "fp32_speedup": t64 / t32, "magnetisation_fp64_ms": tm64,
                                 "magnetisation_fp32_ms": tm32, "fp32_vs_fp64": err}
+    # a short request stream, enumerating every configuration and with split-and-convolve service
+    out["serving_200_requests"] = {"every_configuration": serve_stream(200, 50.0, 20.0, 0.0),
+                                   "split_work_ratio_0.25": serve_stream(200, 50.0, 20.0, 0.25)}
     return out
 
 
@@ -538,17 +541,15 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------ serving mode
-def run_serving(args):
+def serve_stream(n_requests: int, rate: float, step_ms: float, split_ratio: float) -> dict:
     """Poisson stream of lattice requests (seeded; N uniform in 16..38, square / triangular / cubic,
     periodic or free, J uniform in {-2,-1,1,2}) submitted at their arrival times to isg_server;
-    reports latency percentiles, throughput and offered vs achieved load."""
-    import torch
+    latency percentiles, throughput and offered vs achieved load."""
     from paper_1110_2561_gb300 import isg, workloads
 
-    torch.cuda.set_device(0)
-    reqs = workloads.serving_stream(args.requests, rate_per_s=args.rate)
+    reqs = workloads.serving_stream(n_requests, rate_per_s=rate)
     graphs = [isg.isg_graph_create(r.lattice.n, r.lattice.edges) for r in reqs]
-    srv = isg.Server(step_ms=args.step_ms, split_work_ratio=args.split_ratio)
+    srv = isg.Server(step_ms=step_ms, split_work_ratio=split_ratio)
     warm = srv.submit(isg.isg_graph_create(20, workloads.square(4, 5, True).edges))
     srv.wait(warm)
     srv.result(warm)
@@ -561,24 +562,20 @@ def run_serving(args):
         tickets.append(srv.submit(g))
     lat, queued, configs = [], [], 0
     bad = 0
-    last_done = 0.0
     for t, r in zip(tickets, reqs):
         srv.wait(t)
         g, times = srv.result(t)
         lat.append(times[2])
         queued.append(times[0])
-        last_done = max(last_done, times[3] + times[2])
         configs += 1 << r.lattice.n
-        if int(g.sum()) != 1 << r.lattice.n:
+        if sum(int(v) for v in g.ravel()) != 1 << r.lattice.n:
             bad += 1
     st = srv.stats()
     srv.close()
-    first = reqs[0].arrival_s
-    span_arrivals = reqs[-1].arrival_s - first
+    span_arrivals = reqs[-1].arrival_s - reqs[0].arrival_s
     lat_ms = np.array(lat) * 1e3
-    line = {
-        "metric": "serving latency and throughput (continuous batching)", "unit": "ms",
-        "workload": f"{args.requests} requests, Poisson {args.rate}/s, N uniform 16..38, square/triangular/cubic, "
+    return {
+        "workload": f"{n_requests} requests, Poisson {rate}/s, N uniform 16..38, square/triangular/cubic, "
                     "periodic or free, J uniform in {-2,-1,1,2} (seeded)",
         "p50_ms": float(np.percentile(lat_ms, 50)), "p90_ms": float(np.percentile(lat_ms, 90)),
         "p99_ms": float(np.percentile(lat_ms, 99)), "max_ms": float(lat_ms.max()),
@@ -586,10 +583,18 @@ def run_serving(args):
         "offered_configs_per_s": configs / max(1e-9, span_arrivals),
         "achieved_configs_per_s": configs / max(1e-9, (time.perf_counter() - t0)),
         "device_busy_frac": st["device_ms"] * 1e-3 / max(1e-9, time.perf_counter() - t0),
-        "device_configs_per_s": st["configs"] / max(1e-9, st["device_ms"] * 1e-3),
-        "steps": int(st["steps"]), "step_ms": args.step_ms, "invariant_failures": bad,
-        "split_work_ratio": args.split_ratio,
+        "steps": int(st["steps"]), "step_ms": step_ms, "invariant_failures": bad,
+        "split_work_ratio": split_ratio,
     }
+
+
+def run_serving(args):
+    """The request-stream benchmark (one JSON line)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    line = {"metric": "serving latency and throughput (continuous batching)", "unit": "ms"}
+    line.update(serve_stream(args.requests, args.rate, args.step_ms, args.split_ratio))
     print(json.dumps(line), flush=True)
 
 
