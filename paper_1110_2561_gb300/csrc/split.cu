@@ -102,7 +102,7 @@ __device__ __forceinline__ void split_low_steps(int e, int base, const int (&h)[
 // kFew: at most two coupling classes (every lattice here: J = 1, or +-J), so a spin's field is
 // two masked popcounts of a 32-bit component word and a constant; otherwise a loop over classes.
 //
-// One CTA (kSplitThreads threads) per boundary configuration at a time, in a grid-stride loop:
+// One CTA (256 or 512 threads, from the program header) per boundary configuration at a time, in a grid-stride loop:
 // the CTA's buffers (split_warp_layout) hold one accumulator pair, the lists and a histogram, so
 // large components do not cut the number of warps per SM.
 template <class Acc, bool kFew>
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kSplitThreads) split_kernel(const __grid_const
             };
             // walk: 2^P walker threads, each the reflected Gray walk over the low L = nc - P bits
             // with its index in the top P bits
-            const int P = split_walk_bits(nc, cp.low), L = nc - P;
+            const int P = split_walk_bits(nc, cp.low, H.cta_bits), L = nc - P;
             if (tid < (1 << P)) {
                 uint32_t x = (uint32_t)tid << L;
                 int e = (twice_energy(x) / 2 + cp.Sc) / 2;
@@ -336,8 +336,9 @@ void launch_split(const SplitPrepared& prep, const uint64_t* d_blob, unsigned lo
     const DeviceInfo d = device_info();
     const size_t smem = split_smem_bytes((int)prep.blob.size(), H, u64, 1);
     if (smem > (size_t)d.smem_optin) fail(ISG_ERR_TOO_LARGE, "split buffers exceed shared memory");
-    // 64 registers x 512 threads: at most two CTAs per SM
-    const int ctas_per_sm = std::max(1, (int)std::min<size_t>(2, (size_t)d.smem_per_sm / (smem + 1024)));
+    // 64 registers x 512 threads: at most two CTAs of 512 (four of 256) per SM
+    const int threads = 1 << H.cta_bits;
+    const int ctas_per_sm = std::max(1, (int)std::min<size_t>(2048 / threads, (size_t)d.smem_per_sm / (smem + 1024)));
     const unsigned long long n_s = 1ull << H.ns;
     const unsigned long long n_walk = H.ns ? n_s >> 1 : n_s;
     const int grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(n_walk, (unsigned long long)d.sms * ctas_per_sm));
@@ -345,7 +346,7 @@ void launch_split(const SplitPrepared& prep, const uint64_t* d_blob, unsigned lo
     SplitArgs a{d_blob, (int)prep.blob.size(), table, status, n_s};
     auto launch = [&](auto kernel) {
         ISG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kernel<<<grid, kSplitThreads, smem, s>>>(a);
+        kernel<<<grid, threads, smem, s>>>(a);
     };
     const bool few = H.n_cls <= 2;
     if (u64) {

@@ -80,6 +80,7 @@ struct WeightIndex {
 
 struct Candidate {
     uint64_t S = 0;
+    int cta_bits = kSplitWalkBits;
     std::vector<uint64_t> comps;     // largest histogram first
     std::vector<int64_t> Sc;
     double cost = INFINITY, visits = 0;
@@ -134,7 +135,8 @@ void evaluate(const isg_graph& g, const WeightIndex& wi, int n_cls, Candidate& c
     const size_t table_bytes = 8 * (size_t)(g.S + 1) * (g.n + 1);
     const size_t budget = 227 * 1024 - 1024;
     if (prog_bytes + table_bytes + per_cta > budget) return;
-    c.warps = kSplitThreads / 32;
+    c.cta_bits = split_cta_bits(prog_bytes + table_bytes + per_cta);
+    c.warps = (1 << c.cta_bits) / 32;
     // cost per boundary configuration
     double per_s = 40 + ceil32(ns) * (6 + 3.0 * n_cls);            // plus a few CTA barriers
     double nnz_acc = 0, rows = 1;
@@ -147,7 +149,7 @@ void evaluate(const isg_graph& g, const WeightIndex& wi, int n_cls, Candidate& c
         // components large enough for a low block (assumed found) walk it at about 4 operations
         // per configuration plus its fields and the mid flip per 2^kSplitLow configurations
         const int low = nc[i] >= kSplitLowMinSpins ? kSplitLow : 0;
-        const double walkers = std::ldexp(1.0, split_walk_bits(nc[i], low));
+        const double walkers = std::ldexp(1.0, split_walk_bits(nc[i], low, c.cta_bits));
         const double per_config = low ? 4 + (kSplitLow * (6 + 3.0 * n_cls) + 24 + 3.0 * n_cls) / 32 : 8 + 3.0 * n_cls;
         per_s += ceil32(nc[i]) * (4 + 3.0 * n_cls) + ceil32(hw) * 2 + nc[i] * (4 + 3.0 * n_cls) +
                  ceil32(walkers) * (nc[i] * (4 + 3.0 * n_cls) + (walk / walkers) * per_config);
@@ -165,7 +167,7 @@ void evaluate(const isg_graph& g, const WeightIndex& wi, int n_cls, Candidate& c
     c.visits = std::ldexp(configs, ns > 0 ? ns - 1 : 0);         // half the boundary: flip mirrors
     // one CTA per walked boundary configuration: fewer of them than CTA slots (about two per SM)
     // leaves SMs idle, so the work counts at least one full wave
-    const double n_walk = std::ldexp(1.0, ns > 0 ? ns - 1 : 0), wave = 2.0 * 152;
+    const double n_walk = std::ldexp(1.0, ns > 0 ? ns - 1 : 0), wave = (c.cta_bits == 8 ? 4.0 : 2.0) * 152;
     c.cost = per_s * std::max(n_walk, wave);
 }
 
@@ -255,6 +257,7 @@ SplitPlan plan_split(const isg_graph& g, uint64_t boundary, bool require_gain) {
     p.cost = best.cost;
     p.direct_cost = std::ldexp(2.86 / 32, n);
     p.use_u64 = best.u64;
+    p.cta_bits = best.cta_bits;
     p.warps = best.warps;
     return p;
 }
@@ -352,6 +355,7 @@ std::vector<uint64_t> build_split_program(const isg_graph& g, const SplitPlan& p
     h.max_h = (int32_t)hmax;
     h.acc_words = (int32_t)((EO + 1) * MO);
     h.n_bins = (int32_t)((g.S + 1) * (n + 1));
+    h.cta_bits = p.cta_bits;
     std::memcpy(blob.data(), &h, sizeof h);
     return blob;
 }
@@ -406,7 +410,7 @@ void emulate_split(const std::vector<uint64_t>& blob, int64_t* g_out) {
             std::vector<int64_t> f(nc);
             for (int a = 0; a < nc; ++a) f[a] = field(sp + (size_t)a * ncl * 2 + 1, 2, s);
             std::fill(hist.begin(), hist.end(), 0u);
-            const int P = split_walk_bits(nc, cp.low), L = nc - P;
+            const int P = split_walk_bits(nc, cp.low, h.cta_bits), L = nc - P;
             auto count = [&](int64_t e, int m) {
                 if (e < 0 || e > cp.Sc || m < 0 || m > nc) fail(ISG_ERR_INTERNAL, "component bin out of range");
                 hist[(size_t)e * MC + m] += 1;

@@ -33,17 +33,21 @@ constexpr int kSplitMaxClasses = 16;     // distinct signed couplings
 constexpr int kSplitMaxComp = 64;
 constexpr int kSplitMaxCompSpins = 30;   // a component's configurations fit a 32-bit word walk
 constexpr int kSplitThreads = 512;       // threads of a split CTA (one boundary configuration at a time)
-constexpr int kSplitWalkBits = 9;        // at most 2^9 = 512 walkers per component
+constexpr int kSplitWalkBits = 9;        // at most 2^9 = 512 walkers per component (one per thread)
 constexpr int kSplitLow = 5;             // size of a component walk's low block
 constexpr int kSplitLowMinSpins = 12;    // components given a low block: at least this many spins
 
 // Walker bits P of a component of nc spins: 2^P walkers (every thread of the CTA where the
 // component is large enough: idle threads cost more than short walks), each walking
 // 2^(nc - P) configurations, and at least its low block when it has one.
-ISG_SPLIT_HD inline int split_walk_bits(int nc, int low) {
+ISG_SPLIT_HD inline int split_walk_bits(int nc, int low, int cta_bits) {
     const int cap = nc - low;
-    return cap < kSplitWalkBits ? (cap < 0 ? 0 : cap) : kSplitWalkBits;
+    return cap < cta_bits ? (cap < 0 ? 0 : cap) : cta_bits;
 }
+
+// Threads per split CTA: 256 (up to four CTAs per SM, so one waits at a barrier while others
+// issue) when four CTAs' shared memory fits an SM, else 512.
+inline int split_cta_bits(size_t cta_smem_bytes) { return 4 * (cta_smem_bytes + 1024) <= 233472 ? 8 : kSplitWalkBits; }
 
 // Compile-time bit helpers for the unrolled low block (reflected Gray code: step t flips bit
 // ctz(t); the state after step t is gray(t)).
@@ -56,7 +60,8 @@ struct SplitHeader {
     int32_t n, ns, n_comp, n_cls;        // spins, boundary spins, components, coupling classes
     int32_t S_total, S_SS, EO, MO;       // sum |J|; S x S part; convolution rows (sum S_c + 1), row stride (sum |C_c| + 1)
     int32_t off_cls, off_ss, off_comp, off_spin;   // 64-bit word offsets of the sections below
-    int32_t max_h, acc_words, n_bins, reserved;    // largest component histogram; accumulator words per buffer; (S+1)(N+1)
+    int32_t max_h, acc_words, n_bins;    // largest component histogram; accumulator words per buffer; (S+1)(N+1)
+    int32_t cta_bits;                    // log2 of the threads of a CTA (8: 256, four CTAs per SM; 9: 512)
 };
 static_assert(sizeof(SplitHeader) == 64, "header is 8 words");
 
@@ -109,6 +114,7 @@ struct SplitPlan {
     double visits = 0;                   // configurations walked: 2^(|S|-1) * sum 2^|C_c| (flip mirrors)
     double cost = 0, direct_cost = 0;    // model of the work, and of the full enumeration
     bool use_u64 = false;                // accumulator counts may exceed 31 bits
+    int cta_bits = kSplitWalkBits;       // log2 of the threads per CTA
     int warps = 0;                       // warps per CTA whose buffers fit shared memory
 };
 
