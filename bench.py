@@ -628,9 +628,9 @@ def run_profile_case(args):
             for _ in range(args.warmup):
                 isg.isg_thermo(g, gh, T, h, prec, stream, out=outs)
             res[name] = _event_ms(lambda: isg.isg_thermo(g, gh, T, h, prec, stream, out=outs), stream, args.steps)
-    elif args.profile_case in ("split-torus6x6", "split-torus7x7"):
-        L = 6 if args.profile_case == "split-torus6x6" else 7
-        lat = workloads.square(L, L, True)
+    elif args.profile_case in ("split-torus6x6", "split-torus7x7", "split-cubic3x3x4"):
+        lat = {"split-torus6x6": workloads.square(6, 6, True), "split-torus7x7": workloads.square(7, 7, True),
+               "split-cubic3x3x4": workloads.cubic(3, 3, 4, True)}[args.profile_case]
         gh = isg.isg_graph_create(lat.n, lat.edges)
         g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=dev)
         for _ in range(args.warmup):
@@ -653,7 +653,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target seconds of the oracle sample")
     ap.add_argument("--serving", action="store_true", help="run the request-stream (serving) benchmark instead")
-    ap.add_argument("--profile-case", choices=("ea-batch", "cubic-thermo", "split-torus6x6", "split-torus7x7"),
+    ap.add_argument("--profile-case", choices=("ea-batch", "cubic-thermo", "split-torus6x6", "split-torus7x7",
+                                               "split-cubic3x3x4"),
                     default=None,
                     help="run only a small case of another kernel (for ncu captures)")
     ap.add_argument("--requests", type=int, default=2000)

@@ -519,7 +519,7 @@ isg_status isg_server_submit(isg_server* s, const isg_graph* g, int64_t* ticket)
                     r->split = sp;
                     r->blob = sp->blob;
                     r->total_tasks = 1;
-                    r->configs = sp->plan.cost / (2.86 / 32);   // in full-enumeration configurations of work
+                    r->configs = sp->plan.cost / kDirectWarpInstrPerConfig;   // in full-enumeration configurations of work
                 }
             } catch (const Error&) {
                 // no admissible boundary set: served by tiles

@@ -242,7 +242,7 @@ SplitPlan plan_split(const isg_graph& g, uint64_t boundary, bool require_gain) {
             consider(all & ~I);
         }
         if (!std::isfinite(best.cost)) fail(ISG_ERR_TOO_LARGE, "no boundary set gives components of at most 30 spins that fit");
-        if (require_gain && best.cost >= std::ldexp(2.86 / 32, n))
+        if (require_gain && best.cost >= std::ldexp(kDirectWarpInstrPerConfig, n))
             fail(ISG_ERR_TOO_LARGE, "no boundary set makes the split cheaper than the full enumeration for this graph");
     }
     SplitPlan p;
@@ -255,7 +255,7 @@ SplitPlan plan_split(const isg_graph& g, uint64_t boundary, bool require_gain) {
     }
     p.visits = best.visits;
     p.cost = best.cost;
-    p.direct_cost = std::ldexp(2.86 / 32, n);
+    p.direct_cost = std::ldexp(kDirectWarpInstrPerConfig, n);
     p.use_u64 = best.u64;
     p.cta_bits = best.cta_bits;
     p.warps = best.warps;

@@ -36,6 +36,9 @@ constexpr int kSplitThreads = 512;       // threads of a split CTA (one boundary
 constexpr int kSplitWalkBits = 9;        // at most 2^9 = 512 walkers per component (one per thread)
 constexpr int kSplitLow = 5;             // size of a component walk's low block
 constexpr int kSplitLowMinSpins = 12;    // components given a low block: at least this many spins
+// Warp instructions per configuration of the full enumeration (ncu on the 6x6 torus: 2.86 per 32
+// configurations): the unit in which the planner compares a split with the full enumeration.
+constexpr double kDirectWarpInstrPerConfig = 2.86 / 32;
 
 // Walker bits P of a component of nc spins: 2^P walkers (every thread of the CTA where the
 // component is large enough: idle threads cost more than short walks), each walking
