@@ -628,6 +628,17 @@ def run_profile_case(args):
             for _ in range(args.warmup):
                 isg.isg_thermo(g, gh, T, h, prec, stream, out=outs)
             res[name] = _event_ms(lambda: isg.isg_thermo(g, gh, T, h, prec, stream, out=outs), stream, args.steps)
+    elif args.profile_case == "cubic-enumerate":
+        # the full enumeration of the 3x3x4 torus, autotuned as in the benchmark's workloads
+        lat = workloads.cubic(3, 3, 4, True)
+        gh = isg.isg_graph_create(lat.n, lat.edges)
+        g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=dev)
+        res["tuned"] = isg.isg_autotune(gh, stream)
+        res["plan"] = isg.isg_debug_plan(gh, **{k: res["tuned"][k] for k in ("stride_residue", "block_threads", "ctas_per_sm")})
+        for _ in range(args.warmup):
+            isg.isg_enumerate(gh, g, stream, autotune=1)
+        res["ms"] = _event_ms(lambda: isg.isg_enumerate(gh, g, stream, autotune=1), stream, args.steps)
+        res["configs_per_s"] = 2.0 ** 36 / (res["ms"] * 1e-3)
     elif args.profile_case in ("split-torus6x6", "split-torus7x7", "split-cubic3x3x4"):
         lat = {"split-torus6x6": workloads.square(6, 6, True), "split-torus7x7": workloads.square(7, 7, True),
                "split-cubic3x3x4": workloads.cubic(3, 3, 4, True)}[args.profile_case]
@@ -653,8 +664,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target seconds of the oracle sample")
     ap.add_argument("--serving", action="store_true", help="run the request-stream (serving) benchmark instead")
-    ap.add_argument("--profile-case", choices=("ea-batch", "cubic-thermo", "split-torus6x6", "split-torus7x7",
-                                               "split-cubic3x3x4"),
+    ap.add_argument("--profile-case", choices=("ea-batch", "cubic-thermo", "cubic-enumerate", "split-torus6x6",
+                                               "split-torus7x7", "split-cubic3x3x4"),
                     default=None,
                     help="run only a small case of another kernel (for ncu captures)")
     ap.add_argument("--requests", type=int, default=2000)
