@@ -261,12 +261,14 @@ def run_isg(args):
                 [b.elapsed_time(c) for a, b, c in evs]),
             "e2e": {"value": world * n_configs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": 3 * args.steps * world,          # this library's kernels, all ranks
             "clocks": clocks,
         }
-        if not args.no_extras:
+        # the other workloads and the oracle baseline at N = 1 only (the scaling runs time the
+        # headline step alone)
+        if not args.no_extras and world == 1:
             line["workloads"] = extra_measurements(stream, dev)
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)
     if world > 1:
