@@ -412,6 +412,19 @@ def extra_measurements(stream, dev):
                        "components": plan_s["components"], "largest_component": plan_s["largest_component"],
                        "visits": plan_s["visits"], "effective_configs_per_s": 2.0 ** lat.n / (ms * 1e-3),
                        "visits_per_s": plan_s["visits"] / (ms * 1e-3), "sum_g_equals_2^N": tot == 2 ** lat.n}
+    # the EA ensemble as a prepared batch with options.split (instances whose split models less
+    # work go through split launches inside the captured graph), beside the plain prepared batch
+    hs_e = [isg.isg_graph_create(l.n, l.edges) for l in lats]
+    t0 = time.perf_counter()
+    bsp = isg.Batch(hs_e, split=1)
+    create_s = time.perf_counter() - t0
+    sb_ms = _event_ms(lambda: bsp.run(stream), stream, 3)
+    bsp.status(stream)
+    bsp.close()
+    split["ea_4096_prepared_batch"] = {"instances": len(lats), "ms": sb_ms, "create_s": create_s,
+                                       "instances_per_s": len(lats) / (sb_ms * 1e-3),
+                                       "effective_configs_per_s": configs / (sb_ms * 1e-3),
+                                       "plain_prepared_batch_ms": bat_ms, "speedup": bat_ms / sb_ms}
     out["split_and_convolve"] = split
     # derived physics at sizes only the split reaches: exact tables of the L x L tori (L >= 6 by
     # split-and-convolve), their specific-heat maxima, and the Binder-cumulant crossings of

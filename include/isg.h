@@ -93,7 +93,10 @@ typedef struct {
                                 mirror image M -> -M (a global flip keeps E and negates M for any
                                 couplings): the same exact table from half the visits. Not with
                                 shards; isg_enumerate_noalloc ignores it */
-    int32_t reserved2;
+    int32_t split;           /* batches (isg_batch_create, isg_enumerate_batch): 1 serves each graph whose
+                                split-and-convolve plan (isg_enumerate_split) models less work than its
+                                full enumeration, a launch's fixed cost included, by a split launch inside
+                                the batch; the others go to the tile queue. Same tables either way. */
 } isg_options;
 
 /* Fill *opt with the defaults (all planner choices, full range, overwrite). */
@@ -218,6 +221,19 @@ ISG_API isg_status isg_autotune(const isg_graph* graph, void* stream, const isg_
  */
 ISG_API isg_status isg_enumerate_split(const isg_graph* graph, void* stream, int64_t* g_out, int32_t g_out_on_device,
                                        uint64_t boundary);
+
+/*
+ * Exact tables of n graphs (for example disorder realisations of lattices of a few sizes), each by
+ * the cheaper method: split-and-convolve (library's boundary choice) where its plan models less
+ * work than the full enumeration, else the batched full enumeration (isg_enumerate_batch, default
+ * options). Planning is shared by graphs that differ only in coupling signs. The split programs go
+ * to the device in one copy and their launches are enqueued back to back on stream.
+ * g_out[k]: graph k's table (isg_graph_bins geometry), all on the device if g_out_on_device (only
+ * enqueued) or all on the host (synchronises). Tables are overwritten. Errors as
+ * isg_enumerate_split (TOO_LARGE when a graph admits no boundary set at all).
+ */
+ISG_API isg_status isg_enumerate_split_batch(int32_t n, const isg_graph* const* graphs, void* stream,
+                                             int64_t* const* g_out, int32_t g_out_on_device);
 
 /*
  * The boundary set isg_enumerate_split would use (boundary as there) and its cost: *chosen the

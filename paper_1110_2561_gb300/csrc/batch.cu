@@ -22,6 +22,7 @@
 
 #include "batch_internal.h"
 #include "isg_internal.h"
+#include "split_internal.h"
 #include "nvtx_range.h"
 
 namespace isg {
@@ -298,12 +299,23 @@ struct isg_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::mutex mu;
+    // graphs served by split-and-convolve (options.split): one launch each, before the tile kernel
+    struct SplitJob {
+        std::shared_ptr<const SplitPrepared> prep;
+        const uint64_t* d_blob;
+        int64_t* d_table;
+    };
+    std::vector<SplitJob> splits;
+    bool has_tiles = true;
 };
 
 static void batch_enqueue(isg_batch* b, cudaStream_t s) {
     ISG_CUDA(cudaMemsetAsync(b->d_tables, 0, b->table_words * 8, s));
     ISG_CUDA(cudaMemsetAsync(b->d_counter, 0, 16, s));
-    launch_batch(b->plan, b->d_inst, b->d_blobs, b->d_small, b->d_counter, b->d_status, s, b->ctas_per_sm);
+    for (const auto& j : b->splits)
+        launch_split(*j.prep, j.d_blob, reinterpret_cast<unsigned long long*>(j.d_table), b->d_status, s);
+    if (b->has_tiles)
+        launch_batch(b->plan, b->d_inst, b->d_blobs, b->d_small, b->d_counter, b->d_status, s, b->ctas_per_sm);
 }
 
 // Time a batch plan on a subset of the graphs: its own device buffers, one warm-up and two timed
@@ -405,8 +417,30 @@ isg_status isg_batch_create(int32_t n_graphs, const isg_graph* const* graphs, co
         std::unique_ptr<isg_batch> b(new isg_batch());
         ISG_CUDA(cudaGetDevice(&b->device));
         b->ctas_per_sm = o.ctas_per_sm > 0 ? o.ctas_per_sm : 2;
-        if (o.autotune) autotune_batch(n_graphs, graphs, o, b->ctas_per_sm);
-        b->plan = plan_batch(n_graphs, graphs, o, d);
+        // options.split: graphs whose split-and-convolve plan models less work than their full
+        // enumeration (a launch's fixed cost included) are served by split launches; the others
+        // (caller indices tile_of) by the tile queue
+        std::vector<std::shared_ptr<const SplitPrepared>> sprep(n_graphs);
+        std::vector<int> tile_of;
+        std::vector<const isg_graph*> tile_graphs;
+        for (int k = 0; k < n_graphs; ++k) {
+            if (o.split) {
+                try {
+                    auto sp = prepare_split(*graphs[k], 0, false);
+                    if (sp->plan.cost + kSplitLaunchWarpInstr < sp->plan.direct_cost) { sprep[k] = sp; continue; }
+                } catch (const Error&) {
+                    // no admissible boundary set: the tile queue
+                }
+            }
+            tile_of.push_back(k);
+            tile_graphs.push_back(graphs[k]);
+        }
+        b->has_tiles = !tile_of.empty();
+        if (b->has_tiles) {
+            if (o.autotune) autotune_batch((int)tile_graphs.size(), tile_graphs.data(), o, b->ctas_per_sm);
+            b->plan = plan_batch((int)tile_graphs.size(), tile_graphs.data(), o, d);
+            for (auto& c : b->plan.order) c = tile_of[c];          // plan order -> caller index
+        }
         BatchPlan& bp = b->plan;
         b->table_off.assign(n_graphs, 0);
         b->table_len.assign(n_graphs, 0);
@@ -417,15 +451,25 @@ isg_status isg_batch_create(int32_t n_graphs, const isg_graph* const* graphs, co
             b->table_len[c] = (size_t)public_bins(*graphs[c]);
             words += b->table_len[c];
         }
+        size_t split_words = 0;
+        for (int k = 0; k < n_graphs; ++k)
+            if (sprep[k]) {
+                b->table_off[k] = words;
+                b->table_len[k] = (size_t)public_bins(*graphs[k]);
+                words += b->table_len[k];
+                split_words += (sprep[k]->blob.size() + 31) & ~(size_t)31;       // 256-byte aligned programs
+            }
         b->table_words = words;
-        // layout: [counter 8][status 8][inst][small ids][blobs][tables], 256-byte aligned pieces
+        // layout: [counter 8][status 8][inst][small ids][blobs][split programs][tables], 256-byte
+        // aligned pieces
         size_t off = 0;
         auto take = [&](size_t bytes) { size_t o2 = off; off = (off + bytes + 255) & ~(size_t)255; return o2; };
         std::vector<int> ids(bp.small_ids);
         ids.insert(ids.end(), bp.mirror_ids.begin(), bp.mirror_ids.end());
-        const size_t o_cnt = take(16), o_inst = take(sizeof(BatchInst) * bp.inst.size());
+        const size_t o_cnt = take(16), o_inst = take(sizeof(BatchInst) * std::max<size_t>(1, bp.inst.size()));
         const size_t o_small = take(sizeof(int) * std::max<size_t>(1, ids.size()));
-        const size_t o_blobs = take(8 * bp.blobs.size()), o_tab = take(8 * words);
+        const size_t o_blobs = take(8 * std::max<size_t>(1, bp.blobs.size())), o_split = take(8 * std::max<size_t>(1, split_words));
+        const size_t o_tab = take(8 * std::max<size_t>(1, words));
         ISG_CUDA(cudaMalloc(reinterpret_cast<void**>(&b->mem), off));
         b->d_counter = reinterpret_cast<unsigned long long*>(b->mem + o_cnt);
         b->d_status = reinterpret_cast<unsigned int*>(b->mem + o_cnt + 8);
@@ -434,10 +478,25 @@ isg_status isg_batch_create(int32_t n_graphs, const isg_graph* const* graphs, co
         b->d_blobs = reinterpret_cast<uint64_t*>(b->mem + o_blobs);
         b->d_tables = reinterpret_cast<int64_t*>(b->mem + o_tab);
         for (size_t k = 0; k < bp.order.size(); ++k) bp.inst[k].g = b->d_tables + b->table_off[bp.order[k]];
-        ISG_CUDA(cudaMemcpy(b->d_inst, bp.inst.data(), sizeof(BatchInst) * bp.inst.size(), cudaMemcpyHostToDevice));
-        if (!ids.empty())
-            ISG_CUDA(cudaMemcpy(b->d_small, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice));
-        ISG_CUDA(cudaMemcpy(b->d_blobs, bp.blobs.data(), 8 * bp.blobs.size(), cudaMemcpyHostToDevice));
+        if (b->has_tiles) {
+            ISG_CUDA(cudaMemcpy(b->d_inst, bp.inst.data(), sizeof(BatchInst) * bp.inst.size(), cudaMemcpyHostToDevice));
+            if (!ids.empty())
+                ISG_CUDA(cudaMemcpy(b->d_small, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice));
+            ISG_CUDA(cudaMemcpy(b->d_blobs, bp.blobs.data(), 8 * bp.blobs.size(), cudaMemcpyHostToDevice));
+        }
+        if (split_words) {
+            std::vector<uint64_t> host(split_words, 0);
+            size_t w = 0;
+            for (int k = 0; k < n_graphs; ++k)
+                if (sprep[k]) {
+                    std::memcpy(host.data() + w, sprep[k]->blob.data(), 8 * sprep[k]->blob.size());
+                    b->splits.push_back({sprep[k], reinterpret_cast<const uint64_t*>(b->mem + o_split) + w,
+                                         b->d_tables + b->table_off[k]});
+                    w += (sprep[k]->blob.size() + 31) & ~(size_t)31;
+                }
+            ISG_CUDA(cudaMemcpy(b->mem + o_split, host.data(), 8 * split_words, cudaMemcpyHostToDevice));
+            split_prepare_launches();          // kernel attributes set now, not during graph capture
+        }
         ISG_CUDA(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
         *out = b.release();
     });

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -327,6 +329,25 @@ using namespace isg;
 
 namespace isg {
 
+// The kernels' dynamic shared-memory limit, raised once per device to the maximum (a per-launch
+// attribute call costs microseconds, which a batch of small launches would feel; and it must not
+// happen while a stream is being captured).
+void split_prepare_launches() {
+    static std::mutex mu;
+    static std::vector<char> raised;
+    int dev = 0;
+    ISG_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)raised.size() <= dev) raised.resize(dev + 1, 0);
+    if (raised[dev]) return;
+    const int lim = (int)device_info().smem_optin;
+    ISG_CUDA(cudaFuncSetAttribute(split_kernel<uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    ISG_CUDA(cudaFuncSetAttribute(split_kernel<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    ISG_CUDA(cudaFuncSetAttribute(split_kernel<unsigned long long, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    ISG_CUDA(cudaFuncSetAttribute(split_kernel<unsigned long long, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    raised[dev] = 1;
+}
+
 // Enqueue the split kernel for a prepared plan: program at d_blob (device), table (device,
 // (S + 1)(N + 1) counts) accumulated into, status bit 0 set if a walk's self-check fails.
 void launch_split(const SplitPrepared& prep, const uint64_t* d_blob, unsigned long long* table, unsigned int* status,
@@ -344,10 +365,8 @@ void launch_split(const SplitPrepared& prep, const uint64_t* d_blob, unsigned lo
     const int grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(n_walk, (unsigned long long)d.sms * ctas_per_sm));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     SplitArgs a{d_blob, (int)prep.blob.size(), table, status, n_s};
-    auto launch = [&](auto kernel) {
-        ISG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kernel<<<grid, threads, smem, s>>>(a);
-    };
+    split_prepare_launches();
+    auto launch = [&](auto kernel) { kernel<<<grid, threads, smem, s>>>(a); };
     const bool few = H.n_cls <= 2;
     if (u64) {
         if (few) launch(split_kernel<unsigned long long, true>);
@@ -360,6 +379,16 @@ void launch_split(const SplitPrepared& prep, const uint64_t* d_blob, unsigned lo
 }
 
 }  // namespace isg
+
+extern "C" isg_status isg_enumerate_split_batch(int32_t n, const isg_graph* const* graphs, void* stream,
+                                                int64_t* const* g_out, int32_t g_out_on_device) {
+    NvtxRange nvtx("isg_enumerate_split_batch");
+    isg_options o;
+    isg_options_init(&o);
+    o.split = 1;
+    o.max_spins = 62;
+    return isg_enumerate_batch(n, graphs, stream, g_out, g_out_on_device, &o);
+}
 
 extern "C" isg_status isg_enumerate_split(const isg_graph* graph, void* stream, int64_t* g_out, int32_t g_out_on_device,
                                           uint64_t boundary) {

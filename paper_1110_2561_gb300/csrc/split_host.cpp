@@ -173,6 +173,40 @@ void evaluate(const isg_graph& g, const WeightIndex& wi, int n_cls, Candidate& c
 
 }  // namespace
 
+// The boundary search depends on a graph only through its bonds' endpoints and magnitudes and the
+// number of distinct couplings: graphs that differ only in coupling signs (disorder realisations
+// of one lattice) share it. record = 0 looks a structure up (0: unknown); record != 0 stores the
+// boundary found for it.
+static uint64_t structural_boundary(const isg_graph& g, int n_cls, uint64_t record) {
+    struct Entry {
+        int n, n_cls;
+        std::vector<int32_t> bi, bj;
+        std::vector<int64_t> aJ;
+        uint64_t boundary;
+    };
+    static std::mutex mu;
+    static std::unordered_multimap<uint64_t, Entry> cache;
+    std::vector<int64_t> aJ(g.bJ.size());
+    for (size_t k = 0; k < g.bJ.size(); ++k) aJ[k] = std::llabs(g.bJ[k]);
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) { for (int b = 0; b < 8; ++b) { h ^= (v >> (8 * b)) & 0xff; h *= 1099511628211ull; } };
+    mix((uint64_t)g.n);
+    mix((uint64_t)n_cls);
+    for (size_t k = 0; k < aJ.size(); ++k) { mix((uint64_t)g.bi[k]); mix((uint64_t)g.bj[k]); mix((uint64_t)aJ[k]); }
+    std::lock_guard<std::mutex> lk(mu);
+    if (record) {
+        if (cache.size() >= 1024) cache.clear();
+        cache.emplace(h, Entry{g.n, n_cls, g.bi, g.bj, aJ, record});
+        return record;
+    }
+    auto range = cache.equal_range(h);
+    for (auto it = range.first; it != range.second; ++it) {
+        const Entry& e = it->second;
+        if (e.n == g.n && e.n_cls == n_cls && e.bi == g.bi && e.bj == g.bj && e.aJ == aJ) return e.boundary;
+    }
+    return 0;
+}
+
 // The boundary set: the caller's (boundary != 0), or the cheapest under the work model among
 // (a) one or two windows of consecutive spin indices (cyclic), (b) the spins whose index lies in
 // a set of residues modulo p (2 <= p <= 8), (c) the complement of a greedy maximal independent
@@ -214,6 +248,8 @@ SplitPlan plan_split(const isg_graph& g, uint64_t boundary, bool require_gain) {
         if (!std::isfinite(best.cost))
             fail(ISG_ERR_TOO_LARGE, "the given boundary leaves a component of more than 30 spins, more than 40 "
                                     "boundary spins, or buffers beyond shared memory");
+    } else if (const uint64_t known = structural_boundary(g, n_cls, 0)) {
+        consider(known);                             // same structure as a graph planned before
     } else {
         auto window = [&](int a, int w) {
             uint64_t m = 0;
@@ -242,6 +278,7 @@ SplitPlan plan_split(const isg_graph& g, uint64_t boundary, bool require_gain) {
             consider(all & ~I);
         }
         if (!std::isfinite(best.cost)) fail(ISG_ERR_TOO_LARGE, "no boundary set gives components of at most 30 spins that fit");
+        structural_boundary(g, n_cls, best.S);
         if (require_gain && best.cost >= std::ldexp(kDirectWarpInstrPerConfig, n))
             fail(ISG_ERR_TOO_LARGE, "no boundary set makes the split cheaper than the full enumeration for this graph");
     }

@@ -39,6 +39,9 @@ constexpr int kSplitLowMinSpins = 12;    // components given a low block: at lea
 // Warp instructions per configuration of the full enumeration (ncu on the 6x6 torus: 2.86 per 32
 // configurations): the unit in which the planner compares a split with the full enumeration.
 constexpr double kDirectWarpInstrPerConfig = 2.86 / 32;
+// The fixed cost of one split launch among many (host enqueue, table clear, a small grid's ramp):
+// about 20 us, in warp instructions of the whole GPU at full issue.
+constexpr double kSplitLaunchWarpInstr = 2.5e7;
 
 // Walker bits P of a component of nc spins: 2^P walkers (every thread of the CTA where the
 // component is large enough: idle threads cost more than short walks), each walking
@@ -145,6 +148,8 @@ std::shared_ptr<const SplitPrepared> prepare_split(const struct ::isg_graph& g, 
 // self-check.
 void launch_split(const SplitPrepared& prep, const uint64_t* d_blob, unsigned long long* table, unsigned int* status,
                   void* stream);
+// Set the split kernels' launch attributes on the current device (once; call before any capture).
+void split_prepare_launches();
 
 // Shared memory of the split kernel: the program, the CTA's table (32-bit low and high words per
 // bin), then the CTA's working block (16-byte aligned): 32 component-spin records, scalars, two

@@ -33,7 +33,7 @@ class isg_options(ctypes.Structure):
         ("shard_lo", ctypes.c_int64), ("shard_hi", ctypes.c_int64),
         ("accumulate", ctypes.c_int32), ("warp_aggregate", ctypes.c_int32),
         ("stride_residue", ctypes.c_int32), ("autotune", ctypes.c_int32),
-        ("symmetry", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+        ("symmetry", ctypes.c_int32), ("split", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -47,6 +47,7 @@ _SIGS = {
     "isg_graph_size": (i32, [vp, vp, vp]),
     "isg_enumerate": (i32, [vp, vp, vp, i32, vp]),
     "isg_enumerate_split": (i32, [vp, vp, vp, i32, ctypes.c_uint64]),
+    "isg_enumerate_split_batch": (i32, [i32, vp, vp, vp, i32]),
     "isg_split_plan": (i32, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i32),
                              ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "isg_debug_emulate_split": (i32, [vp, ctypes.c_uint64, vp]),
@@ -240,6 +241,29 @@ def isg_enumerate_split(graph: Graph, g_out=None, stream=None, boundary: int = 0
         return g_out
     _check_tensor(g_out, shape, "int64")
     _check(lib().isg_enumerate_split(graph, _stream_handle(stream), g_out.data_ptr(), 1, boundary))
+    return g_out
+
+
+def isg_enumerate_split_batch(graphs, g_out=None, stream=None):
+    """Exact tables of many graphs in one call, each by split-and-convolve where its plan models
+    less work than the full enumeration, else by the batched full enumeration. g_out: None (new numpy tables, synchronous), a list of numpy int64 tables, or a list
+    of torch int64 CUDA tensors (enqueued on `stream`)."""
+    shapes = [table_shape(g) for g in graphs]
+    if g_out is None:
+        g_out = [np.zeros(s, dtype=np.int64) for s in shapes]
+    on_device = len(g_out) > 0 and not isinstance(g_out[0], np.ndarray)
+    ptrs = []
+    for t, s in zip(g_out, shapes):
+        if on_device:
+            _check_tensor(t, s, "int64")
+            ptrs.append(t.data_ptr())
+        else:
+            if t.dtype != np.int64 or not t.flags.c_contiguous or t.shape != s:
+                raise ValueError(f"host tables must be C-contiguous int64 arrays of shape {s}")
+            ptrs.append(t.ctypes.data)
+    arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+    sh = _stream_handle(stream) if (stream is not None or on_device) else None
+    _check(lib().isg_enumerate_split_batch(len(graphs), _graph_array(graphs), sh, arr, 1 if on_device else 0))
     return g_out
 
 

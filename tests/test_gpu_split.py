@@ -164,3 +164,40 @@ def test_specific_heat_peak_8x8_kaufman(isg, cuda):
     t_k = kaufman_C_peak(8, 8, kaufman_C_peak(8, 8, t_gpu))
     assert abs(t_gpu - t_k) <= 1e-5 * t_k
     assert abs(c_gpu - kaufman_C(8, 8, t_gpu)) <= 1e-5 * c_gpu
+
+
+def test_split_batch_ea_ensemble(isg, cuda):
+    """isg_enumerate_split_batch over EA +-J instances of all four shapes (shared planning per
+    shape), into device tensors and into host tables: every table equals the batched full
+    enumeration's, and a sample equals the frontier oracle."""
+    import torch
+    lats = w.ea_instances()[:96]
+    hs = [isg.isg_graph_create(l.n, l.edges) for l in lats]
+    dev = [torch.zeros(isg.table_shape(h), dtype=torch.int64, device=cuda) for h in hs]
+    isg.isg_enumerate_split_batch(hs, dev)
+    host = isg.isg_enumerate_split_batch(hs)
+    torch.cuda.synchronize()
+    ref = isg.isg_enumerate_batch(hs)
+    for k, (l, d, h, r) in enumerate(zip(lats, dev, host, ref)):
+        assert np.array_equal(d.cpu().numpy(), r) and np.array_equal(h, r), l.name
+        if k % 24 == 0:
+            assert np.array_equal(h, oracle.g_frontier(l.n, l.edges, 16)), l.name
+
+
+def test_prepared_batch_with_split(isg, cuda):
+    """A prepared batch with options.split over EA instances of all shapes (the larger ones served
+    by split launches inside the captured graph, the others by the tile queue), replayed twice:
+    every table equals the plain batch's, and the self-check status is clean."""
+    import torch
+    lats = w.ea_instances()[:64]
+    hs = [isg.isg_graph_create(l.n, l.edges) for l in lats]
+    ref = isg.Batch(hs)
+    ref.run()
+    got = isg.Batch(hs, split=1)
+    for _ in range(2):
+        got.run()
+    torch.cuda.synchronize()
+    got.status()
+    for k, l in enumerate(lats):
+        assert torch.equal(got.table(k), ref.table(k)), l.name
+    assert sum(l.n == 30 for l in lats) >= 8            # some instances really take the split path
