@@ -228,9 +228,7 @@ static BatchPlan plan_batch(int n, const isg_graph* const* graphs, const isg_opt
 template <int B>
 static void launch_batch_b(const BatchPlan& bp, const BatchArgs& a, cudaStream_t s, int ctas_per_sm) {
     if (!bp.n_tiles) return;
-    ISG_CUDA(cudaFuncSetAttribute(batch_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bp.smem));
-    int occ = 0;
-    ISG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel<B>, bp.threads, bp.smem));
+    const int occ = kernel_occupancy(reinterpret_cast<const void*>(batch_kernel<B>), bp.threads, bp.smem);
     if (occ < 1) fail(ISG_ERR_TOO_LARGE, "batch kernel does not fit an SM");
     const DeviceInfo d = device_info();
     const uint64_t warps_needed = bp.n_tiles;
@@ -265,7 +263,7 @@ void launch_batch(const BatchPlan& bp, const BatchInst* d_inst, const uint64_t* 
     }
     if (!bp.small_ids.empty()) {
         const int smem = bp.small_max_words * 8;
-        ISG_CUDA(cudaFuncSetAttribute(batch_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        kernel_occupancy(reinterpret_cast<const void*>(batch_small_kernel), 256, (size_t)smem);
         batch_small_kernel<<<(int)bp.small_ids.size(), 256, smem, s>>>(d_inst, d_small, d_blobs);
         ISG_CUDA(cudaGetLastError());
     }

@@ -14,7 +14,9 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "isg_internal.h"
@@ -208,14 +210,37 @@ DeviceInfo device_info() {
     return cache[dev];
 }
 
+int kernel_occupancy(const void* kernel, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void*, int, size_t>, int> occ_cache;
+    static std::set<std::pair<int, const void*>> raised;
+    int dev = 0;
+    ISG_CUDA(cudaGetDevice(&dev));
+    const size_t optin = device_info().smem_optin;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_tuple(dev, kernel, threads, smem);
+    const auto it = occ_cache.find(key);
+    if (it != occ_cache.end()) return it->second;
+    if (!raised.count({dev, kernel})) {
+        // the dynamic limit may reach the device maximum less the kernel's static shared memory
+        cudaFuncAttributes fa;
+        ISG_CUDA(cudaFuncGetAttributes(&fa, kernel));
+        ISG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(optin - std::min(optin, fa.sharedSizeBytes))));
+        raised.insert({dev, kernel});
+    }
+    int occ = 0;
+    ISG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem));
+    occ_cache[key] = occ;
+    return occ;
+}
+
 // Grid: the planned CTAs per SM, capped by what the registers and shared memory of this
-// instantiation allow (cudaOccupancyMaxActiveBlocksPerMultiprocessor), never more than tasks.
+// instantiation allow (its occupancy), never more than tasks.
 template <int B, class Sink>
 static void launch_bs(const Plan& p, const EnumParams& a, cudaStream_t s) {
     const int smem = (int)(p.smem_bytes + 16);
-    ISG_CUDA(cudaFuncSetAttribute(enumerate_kernel<B, Sink>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    int occ = 0;
-    ISG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, enumerate_kernel<B, Sink>, p.threads, smem));
+    const int occ = kernel_occupancy(reinterpret_cast<const void*>(enumerate_kernel<B, Sink>), p.threads, (size_t)smem);
     if (occ < 1) fail(ISG_ERR_TOO_LARGE, "enumeration kernel does not fit an SM with this block size");
     const DeviceInfo d = device_info();
     const uint64_t want = (uint64_t)d.sms * (uint64_t)std::min(occ, p.ctas_per_sm);
@@ -248,8 +273,7 @@ void launch_enumeration(const Plan& p, const uint64_t* d_blob, int blob_words, i
         a.blob = d_blob;
         a.blob_words = blob_words;
         a.g = table;
-        ISG_CUDA(cudaFuncSetAttribute(enumerate_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      blob_words * 8));
+        kernel_occupancy(reinterpret_cast<const void*>(enumerate_small_kernel), p.threads, (size_t)blob_words * 8);
         enumerate_small_kernel<<<p.grid, p.threads, blob_words * 8, s>>>(*P, p.s_lo, p.s_hi);
         ISG_CUDA(cudaGetLastError());
         return;

@@ -115,6 +115,13 @@ void* scratch_alloc(size_t bytes, void* stream);
 // Row stride of the shared histogram for a graph (>= N + 1), padded against bank conflicts.
 int choose_stride(const isg_graph& g, int requested, int residue);
 
+// CTAs of `threads` threads and `smem` bytes of dynamic shared memory that fit one SM for a
+// kernel (a __global__ function's address) on the current device. The first call per device and
+// kernel raises the kernel's dynamic shared-memory limit to the device maximum less its static
+// shared memory. Results are cached per (device, kernel, threads, smem): both driver queries cost
+// microseconds that a small call would otherwise pay on every launch. Thread-safe.
+int kernel_occupancy(const void* kernel, int threads, size_t smem);
+
 inline int64_t public_bins(const isg_graph& g) { return (g.S + 1) * (int64_t)(g.n + 1); }
 
 }  // namespace isg
