@@ -643,6 +643,17 @@ def run_profile_case(args):
             for _ in range(args.warmup):
                 isg.isg_thermo(g, gh, T, h, prec, stream, out=outs)
             res[name] = _event_ms(lambda: isg.isg_thermo(g, gh, T, h, prec, stream, out=outs), stream, args.steps)
+    elif args.profile_case == "small-thermo":
+        # the 4x4 free lattice's FP64 thermodynamics on 64 temperatures at h = 0 (a clustered grid)
+        lat = workloads.square(4, 4, False)
+        gh = isg.isg_graph_create(lat.n, lat.edges)
+        g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=dev)
+        isg.isg_enumerate(gh, g, stream)
+        outs = tuple(torch.empty((64, 1), dtype=torch.float64, device=dev) for _ in range(5))
+        call = isg.prepare_thermo(g, gh, np.linspace(0.5, 5, 64), [0.0], outs, isg.ISG_FP64, stream)
+        for _ in range(args.warmup):
+            call()
+        res["fp64_ms"] = _event_ms(call, stream, args.steps)
     elif args.profile_case == "cubic-enumerate":
         # the full enumeration of the 3x3x4 torus, autotuned as in the benchmark's workloads
         lat = workloads.cubic(3, 3, 4, True)
@@ -679,7 +690,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target seconds of the oracle sample")
     ap.add_argument("--serving", action="store_true", help="run the request-stream (serving) benchmark instead")
-    ap.add_argument("--profile-case", choices=("ea-batch", "cubic-thermo", "cubic-enumerate", "split-torus6x6",
+    ap.add_argument("--profile-case", choices=("ea-batch", "cubic-thermo", "small-thermo", "cubic-enumerate", "split-torus6x6",
                                                "split-torus7x7", "split-cubic3x3x4"),
                     default=None,
                     help="run only a small case of another kernel (for ncu captures)")

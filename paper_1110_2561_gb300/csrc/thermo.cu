@@ -21,8 +21,10 @@
 // to float; every exponential and every sum runs in float, relative to the column maximum in
 // stage 1 and to the dominant column of each (T, h) point in stage 2, whose large offsets are
 // carried as pairs of floats; ln Z is finished in double from the float sum.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -33,6 +35,8 @@
 #include "nvtx_range.h"
 
 namespace isg {
+
+DeviceInfo device_info();
 
 constexpr int kInlineGrid = 1024;   // T and h values passed inside the kernel parameters
 constexpr int kThermoOuts = 9;      // logZ, E, M, C, chi, absM, M2, M4, binder
@@ -52,6 +56,8 @@ struct ThermoArgs {
     double* binder;     // 1 - <M^4> / (3 <M^2>^2)
     int n, n_e, n_m, nT, nh;
     int64_t e_min;
+    int e0, eg, n_on;   // energy sublattice of the graph: public bins e0 + eg k, k < n_on
+    int cluster;        // CTAs per temperature (a thread-block cluster when > 1)
 };
 
 // Kernel parameters: the arguments plus small grids inline, so a call on a small grid needs no
@@ -91,6 +97,37 @@ __device__ __forceinline__ F warp_sum(F v) {
     return v;
 }
 
+// Warp sums of two values with five additions per lane instead of ten: at the first level each
+// half-warp keeps one value and adds its partner's copy of it. Returns the sum of a in lanes
+// 0..15 and of b in lanes 16..31.
+template <class F>
+__device__ __forceinline__ F warp_sum2(F a, F b) {
+    const bool hi = threadIdx.x & 16;
+    F v = (hi ? b : a) + __shfl_xor_sync(0xffffffffu, hi ? a : b, 16);
+#pragma unroll
+    for (int o = 8; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Warp sums of eight values with nine additions per lane instead of forty (the same halving at
+// the first three levels). On return v[j] holds the full sum of value j in every lane.
+template <class F>
+__device__ __forceinline__ void warp_sum8(F (&v)[8]) {
+    const int lane = threadIdx.x & 31;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    F w[4], x[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w[i] = (b4 ? v[i + 4] : v[i]) + __shfl_xor_sync(0xffffffffu, b4 ? v[i] : v[i + 4], 16);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) x[i] = (b3 ? w[i + 2] : w[i]) + __shfl_xor_sync(0xffffffffu, b3 ? w[i] : w[i + 2], 8);
+    F y = (b2 ? x[1] : x[0]) + __shfl_xor_sync(0xffffffffu, b2 ? x[0] : x[1], 4);
+    y += __shfl_xor_sync(0xffffffffu, y, 2);
+    y += __shfl_xor_sync(0xffffffffu, y, 1);
+    // lane bits (4, 3, 2) name the value whose sum the lane now holds
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __shfl_sync(0xffffffffu, y, ((j & 4) << 2) | ((j & 2) << 2) | ((j & 1) << 2));
+}
+
 // ln g for every bin, computed in double from the int64 count and stored in double and (rounded)
 // in float; -inf marks an empty bin.
 __global__ void log_counts_kernel(const int64_t* g, int nbins, double* lng, float* lngf, float* lnglo) {
@@ -103,26 +140,88 @@ __global__ void log_counts_kernel(const int64_t* g, int nbins, double* lng, floa
     }
 }
 
+// One pass over every bin of a column for stage 1 (lane-strided, public bins e of column m in
+// table tab, energies El + Es j in precision U): the reference bin, the one maximising
+// ln g - E/T, and whether any count lies off the graph's energy sublattice (bins e0 + eg k,
+// e <= e_last; r is (e - e0) mod eg for the lane's first bin, stepped by r32 = 32 mod eg).
+// Returns the ballot of the lanes holding the warp maximum (0: empty column); the lane's best
+// bin goes to ebest and its off-sublattice finding to off.
+template <class U>
+__device__ __forceinline__ unsigned column_scan(const U* tab, int n_m, int m, int n_e, int e0, int eg, int e_last, int r,
+                                                int r32, U El, U Es, U invT, int& ebest, bool& off) {
+    U xmax = (U)-INFINITY;
+    ebest = 0;
+    off = false;
+    U En = El;
+    for (int e = threadIdx.x & 31; e < n_e; e += 32, En += Es) {
+        const U l = tab[(size_t)e * n_m + m];
+        const bool on = r == 0 && e >= e0 && e <= e_last;
+        r += r32;
+        if (r >= eg) r -= eg;
+        if (l == (U)-INFINITY) continue;
+        if (!on) off = true;
+        const U x = fmaF(-En, invT, l);
+        if (x > xmax) { xmax = x; ebest = e; }
+    }
+    const U wmax = warp_max(xmax);
+    return __ballot_sync(0xffffffffu, xmax == wmax && wmax != (U)-INFINITY);
+}
+
+// Dominant column of a stage-2 point: over m = mfirst, mfirst + mstep, ..., the one maximising
+// Lr[m] + (h/T) M_m, searched in precision U (Lr in that precision).
+template <class U>
+__device__ __forceinline__ int dominant_column(const U* Lr, int n, int n_m, int mfirst, int mstep, U hT, bool by_warp) {
+    U amax = (U)-INFINITY;
+    int ms = 0;
+    U Mm = (U)(2 * mfirst - n);
+    const U Ms = (U)(2 * mstep);
+    for (int m = mfirst; m < n_m; m += mstep, Mm += Ms) {
+        const U lr = Lr[m];
+        if (lr == (U)-INFINITY) continue;
+        const U am = fmaF(hT, Mm, lr);
+        if (am > amax) { amax = am; ms = m; }
+    }
+    if (by_warp) {                        // the lowest lane holding the warp maximum names m*
+        const U wm = warp_max(amax);
+        const unsigned hit = __ballot_sync(0xffffffffu, amax == wm && wm != (U)-INFINITY);
+        ms = __shfl_sync(0xffffffffu, ms, hit ? __ffs(hit) - 1 : 0);
+    }
+    return ms;
+}
+
 template <class F> __device__ __forceinline__ const F* pick(const double* d, const float* f);
 template <> __device__ __forceinline__ const double* pick<double>(const double* d, const float*) { return d; }
 template <> __device__ __forceinline__ const float* pick<float>(const double*, const float* f) { return f; }
 
-// One CTA per temperature. Shared memory: L[n_m] (double), mu, var, Lr, Llo, cs0, qin [n_m]
-// (F), ces[n_m] (int).
+// One CTA per temperature, or, for grids of fewer temperatures than half the SMs, one cluster of
+// a.cluster CTAs per temperature: the cluster's CTAs share stage 1's columns and write their
+// results into the shared memory of the cluster's first CTA, which alone runs the rest.
+// Shared memory: L[n_m] (double), mu, var, Lr, Llo, cs0, qin [n_m] (F), ces[n_m] (int), Lrf[n_m]
+// (float).
+//
+// Stage 1 walks, per column, the public energy bins e0 + eg k (k < n_on) on which the graph's
+// energies E = e_lo + G k' lie (eg = G / 2: every other bin on lattices with an energy stride of
+// 4); a column that holds counts off those bins (a table that is not this graph's) is walked
+// bin by bin.
 //
 // Stage 2 forms every exponent relative to the dominant column m* of its (T, h) point:
 //   d_m = (Lr[m] - Lr[m*]) + (Llo[m] - Llo[m*]) + (h/T)(M_m - M_m*),
 // with Lr + Llo = L - max L and h/T = hT + hTlo held as pairs of the working precision (for
 // float this is what keeps ln Z accurate to ~1e-7 although L - max L reaches hundreds), and
 // finishes ln Z = max L + (L[m*] - max L) + (h/T) M_m* + ln(sum exp d_m) in double.
+//
+// The reference bin of a column and the dominant column of a point are searched in float in
+// both precisions: they only need to lie near the maximum (every weight is formed relative to
+// them, and a reference a rounding error below the maximum leaves the weights near 1).
 template <class F>
 __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ ThermoParams P, const double* lngd,
                                                      const float* lngf, const float* lnglo) {
+    namespace cg = cooperative_groups;
     const ThermoArgs& a = P.a;
     const double* Tv = a.T ? a.T : P.grid;
     const double* hv = a.h ? a.h : P.grid + a.nT;
     const F* lng = pick<F>(lngd, lngf);
-    const bool pair = sizeof(F) == sizeof(float);   // float: ln g carried as lngf + lnglo
+    constexpr bool pair = sizeof(F) == sizeof(float);   // float: ln g carried as lngf + lnglo
     extern __shared__ __align__(16) unsigned char sm[];
     double* L = reinterpret_cast<double*>(sm);
     F* mu = reinterpret_cast<F*>(L + a.n_m);
@@ -134,44 +233,74 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
     // neighbouring columns' weights (0 for m = 0 or an empty neighbour)
     F* qin = cs0 + a.n_m;
     int* ces = reinterpret_cast<int*>(qin + a.n_m);   // per column: the largest bin e* (-1: empty)
+    float* Lrf = reinterpret_cast<float*>(ces + a.n_m);
     __shared__ double s_Lmax;
-    const int it = blockIdx.x;
+    const int csz = a.cluster;
+    const int rank = csz > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    const int it = blockIdx.x / csz;
     const double T = Tv[it], invTd = 1.0 / T;
     const F invT = (F)invTd, invTlo = (F)(invTd - (double)invT), invT2 = (F)(invTd * invTd);
+    const float invTf = (float)invTd;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // stage-1 results go to the cluster's first CTA (distributed shared memory); every CTA of
+    // the cluster must be running before any writes into another's shared memory
+    F *mu_d = mu, *var_d = var, *cs0_d = cs0;
+    int* ces_d = ces;
+    if (csz > 1) {
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        mu_d = cl.map_shared_rank(mu, 0);
+        var_d = cl.map_shared_rank(var, 0);
+        cs0_d = cl.map_shared_rank(cs0, 0);
+        ces_d = cl.map_shared_rank(ces, 0);
+    }
 
     // Stage 1: per column M (one warp each).
-    // Energies E_e = e_min + 2e are exact in F (|E| < 2^24); the loops step them by 64 (32 lanes
-    // x 2) in F instead of converting e, since integer-to-float conversions share the slow FP64
-    // pipe on this GPU.
-    const F Elane = (F)(a.e_min + 2 * lane);
-    for (int m = warp; m < a.n_m; m += nw) {
-        F xmax = (F)-INFINITY;
-        int earg = 0;
-        F En = Elane;
-        for (int e = lane; e < a.n_e; e += 32, En += (F)64) {
-            const F l = lng[(size_t)e * a.n_m + m];
-            if (l == (F)-INFINITY) continue;
-            const F x = l - En * invT;
-            if (x > xmax) { xmax = x; earg = e; }
-        }
-        const F wmax = warp_max(xmax);
+    // Energies E_e = e_min + 2e are exact in float (|E| < 2^24); the loops step them in float
+    // instead of converting e, since integer-to-float conversions share the slow FP64 pipe on
+    // this GPU. Lane energies of the sublattice walk (S) and of the dense walk (D):
+    const float ElS = (float)(a.e_min + 2 * (a.e0 + a.eg * lane)), EsS = (float)(64 * a.eg);
+    const float ElD = (float)(a.e_min + 2 * lane), EsD = 64.0f;
+    const bool sparse_graph = a.eg > 1 || a.n_on < a.n_e;
+    // The reference search runs in float where float keeps it within ~1e-3 of the maximum:
+    // every compared value is below S/T + 45 in magnitude, so for S/T <= 1e4 its rounding error
+    // stays below 1e-3. Otherwise (FP64 only) it runs in double.
+    const bool search_float = pair || (double)(-a.e_min) * invTd <= 1e4;
+    const double ElDd = (double)ElD, EsDd = 64.0;
+    const int e_last = a.e0 + a.eg * (a.n_on - 1), r32 = 32 % a.eg;
+    const int r0 = ((lane - a.e0) % a.eg + a.eg) % a.eg;
+    for (int m = rank + csz * warp; m < a.n_m; m += csz * nw) {
+        int ebest;
+        bool off;
         // a lane holding the maximum names the reference energy (any tie is fine)
-        const unsigned hit = __ballot_sync(0xffffffffu, xmax == wmax && wmax != (F)-INFINITY);
+        const unsigned hit =
+            search_float ? column_scan<float>(lngf, a.n_m, m, a.n_e, a.e0, a.eg, e_last, r0, r32, ElD, EsD, invTf, ebest, off)
+                         : column_scan<double>(lngd, a.n_m, m, a.n_e, a.e0, a.eg, e_last, r0, r32, ElDd, EsDd, invTd, ebest,
+                                               off);
         if (!hit) {
-            if (lane == 0) { ces[m] = -1; mu[m] = 0; var[m] = 0; }
+            if (lane == 0) { ces_d[m] = -1; mu_d[m] = 0; var_d[m] = 0; }
             continue;
         }
-        // exponents relative to the maximising bin e*: (ln g_e - ln g_e*) - (E_e - E_e*) / T, the
+        const int es = __shfl_sync(0xffffffffu, ebest, __ffs(hit) - 1);
+        // the exponential passes walk the sublattice unless the column holds counts off it
+        const bool dense = !sparse_graph || __any_sync(0xffffffffu, off);
+        const int cb = dense ? 0 : a.e0, cs = dense ? 1 : a.eg, cn = dense ? a.n_e : a.n_on;
+        const float El = dense ? ElD : ElS, Es = dense ? EsD : EsS;
+        // exponents relative to the reference bin e*: (ln g_e - ln g_e*) - (E_e - E_e*) / T, the
         // differences formed from the (hi, lo) pairs so no large value is rounded on the way
-        const int es = __shfl_sync(0xffffffffu, earg, __ffs(hit) - 1);
         const size_t is = (size_t)es * a.n_m + m;
-        const F ls = lng[is], lls = pair ? (F)lnglo[is] : (F)0;
+        const F ls = lng[is];
+        F lls = 0;
+        if constexpr (pair) lls = (F)lnglo[is];
         const F Eref = (F)(a.e_min + 2 * es);
-        auto arg = [&](int e, F l, F En) {
-            const F dE = En - Eref;
-            const F dl = (l - ls) + (pair ? (F)lnglo[(size_t)e * a.n_m + m] - lls : (F)0);
-            return dl - fmaF(dE, invT, dE * invTlo);
+        const F ElF = (F)El, EsF = (F)Es;
+        auto arg = [&](int e, F l, F dE) -> F {
+            if constexpr (pair) {
+                const F dl = (l - ls) + ((F)lnglo[(size_t)e * a.n_m + m] - lls);
+                return dl - fmaF(dE, invT, dE * invTlo);
+            } else {
+                return fmaF(-dE, invT, l - ls);
+            }
         };
         // weights of the first kCache bins of each lane stay in registers for the second pass
         constexpr int kCache = 8;
@@ -179,55 +308,68 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
         F s0 = 0, s1 = 0;
 #pragma unroll
         for (int j = 0; j < kCache; ++j) {
-            const int e = lane + 32 * j;
+            const int k = lane + 32 * j;
             wc[j] = 0;
-            if (e >= a.n_e) continue;
+            if (k >= cn) continue;
+            const int e = cb + cs * k;
             const F l = lng[(size_t)e * a.n_m + m];
             if (l == (F)-INFINITY) continue;
-            const F En = Elane + (F)(64 * j);
-            const F w = ex<F>(arg(e, l, En));
+            const F dE = fmaF(EsF, (F)j, ElF) - Eref;
+            const F w = ex<F>(arg(e, l, dE));
             wc[j] = w;
             s0 += w;
-            s1 += w * (En - Eref);
+            s1 += w * dE;
         }
         {
-            F En = Elane + (F)(64 * kCache);
-            for (int e = lane + 32 * kCache; e < a.n_e; e += 32, En += (F)64) {
+            F En = fmaF(EsF, (F)kCache, ElF);
+            for (int k = lane + 32 * kCache; k < cn; k += 32, En += EsF) {
+                const int e = cb + cs * k;
                 const F l = lng[(size_t)e * a.n_m + m];
                 if (l == (F)-INFINITY) continue;
-                const F w = ex<F>(arg(e, l, En));
+                const F dE = En - Eref;
+                const F w = ex<F>(arg(e, l, dE));
                 s0 += w;
-                s1 += w * (En - Eref);
+                s1 += w * dE;
             }
         }
-        s0 = warp_sum(s0);
-        s1 = warp_sum(s1);
-        const F m1 = Eref + s1 / s0;
+        {
+            const F v = warp_sum2(s0, s1);
+            s0 = __shfl_sync(0xffffffffu, v, 0);
+            s1 = __shfl_sync(0xffffffffu, v, 16);
+        }
+        const F inv0 = (F)1 / s0;
+        const F m1 = Eref + s1 * inv0;
         F s2 = 0;
         if (a.C) {
 #pragma unroll
             for (int j = 0; j < kCache; ++j) {
-                const F d = Elane + (F)(64 * j) - m1;
+                const F d = fmaF(EsF, (F)j, ElF) - m1;
                 s2 += wc[j] * d * d;
             }
-            F En = Elane + (F)(64 * kCache);
-            for (int e = lane + 32 * kCache; e < a.n_e; e += 32, En += (F)64) {
+            F En = fmaF(EsF, (F)kCache, ElF);
+            for (int k = lane + 32 * kCache; k < cn; k += 32, En += EsF) {
+                const int e = cb + cs * k;
                 const F l = lng[(size_t)e * a.n_m + m];
                 if (l == (F)-INFINITY) continue;
-                const F w = ex<F>(arg(e, l, En));
+                const F w = ex<F>(arg(e, l, En - Eref));
                 const F d = En - m1;
                 s2 += w * d * d;
             }
             s2 = warp_sum(s2);
         }
         if (lane == 0) {
-            cs0[m] = s0;
-            ces[m] = es;
-            mu[m] = m1;
-            var[m] = s2 / s0;
+            cs0_d[m] = s0;
+            ces_d[m] = es;
+            mu_d[m] = m1;
+            var_d[m] = s2 * inv0;
         }
     }
-    __syncthreads();
+    if (csz > 1) {
+        cg::this_cluster().sync();           // release / acquire: the first CTA sees every column
+        if (rank != 0) return;
+    } else {
+        __syncthreads();
+    }
     // L_T(M) in double, the columns side by side (double arithmetic occupies the narrow FP64 pipe
     // for a whole warp even with one lane active); ln of the relative sum s0 in [1, n_e] is taken
     // in the working precision.
@@ -246,10 +388,11 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
     __syncthreads();
     const double Lmax = s_Lmax;
     for (int m = threadIdx.x; m < a.n_m; m += blockDim.x) {
-        if (L[m] == -INFINITY) { Lr[m] = (F)-INFINITY; Llo[m] = 0; continue; }
+        if (L[m] == -INFINITY) { Lr[m] = (F)-INFINITY; Llo[m] = 0; Lrf[m] = -INFINITY; continue; }
         const double r = L[m] - Lmax;
         Lr[m] = (F)r;
         Llo[m] = (F)(r - (double)(F)r);
+        Lrf[m] = (float)r;
     }
     const bool by_warp = a.nh < 64;
     constexpr bool kChain = sizeof(F) == sizeof(double);
@@ -270,21 +413,13 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
     for (int ih = first; ih < a.nh; ih += step) {
         const double hd = hv[ih], hTd = hd * invTd;
         const F hT = (F)hTd, hTlo = (F)(hTd - (double)hT), hF = (F)hd;
-        F amax = (F)-INFINITY;
-        int ms = 0;
-        {
-            F Mm = (F)(2 * mfirst - a.n);
-            for (int m = mfirst; m < a.n_m; m += mstep, Mm += dstep) {
-                if (Lr[m] == (F)-INFINITY) continue;
-                const F am = Lr[m] + hT * Mm;
-                if (am > amax) { amax = am; ms = m; }
-            }
-        }
-        if (by_warp) {                        // the lowest lane holding the warp maximum names m*
-            const F wm = warp_max(amax);
-            const unsigned hit = __ballot_sync(0xffffffffu, amax == wm && wm != (F)-INFINITY);
-            ms = __shfl_sync(0xffffffffu, ms, hit ? __ffs(hit) - 1 : 0);
-        }
+        // In float where float keeps the choice within ~1e-3 of the maximum: the contenders' Lr
+        // lie within 2 |h/T| N of 0, so for |h/T| N <= 5e3 every compared value is below 1.5e4.
+        int ms;
+        if constexpr (pair) ms = dominant_column<float>(Lr, a.n, a.n_m, mfirst, mstep, hT, by_warp);
+        else
+            ms = fabs(hTd) * a.n <= 5e3 ? dominant_column<float>(Lrf, a.n, a.n_m, mfirst, mstep, (float)hTd, by_warp)
+                                        : dominant_column<double>(Lr, a.n, a.n_m, mfirst, mstep, hTd, by_warp);
         // One pass: weights p_m and the moments of dM = M_m - M_m* and dH = H_m - H_m* about the
         // dominant column. m* is the mode of p, so the mean lies within a few standard deviations
         // of it and Var = <d^2> - <d>^2 loses at most a small factor to cancellation.
@@ -304,12 +439,12 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
             if constexpr (kChain) {
                 const F f = by_warp ? (F)0 : qin[m] * R;
                 p = (!by_warp && pprev >= (F)1e-290 && f <= (F)1e290) ? pprev * f
-                                                                      : ex<F>((Lr[m] - Ls) + hT * dM);
+                                                                      : ex<F>(fmaF(hT, dM, Lr[m] - Ls));
             } else {
                 p = ex<F>((Lr[m] - Ls) + (Llo[m] - Lls) + fmaF(hT, dM, hTlo * dM));
             }
             pprev = p;
-            const F dH = (mu[m] - mus) - hF * dM;
+            const F dH = fmaF(-hF, dM, mu[m] - mus);
             const F pM = p * dM, pH = p * dH;
             z += p;
             sM += pM;
@@ -326,19 +461,19 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
             }
         }
         if (by_warp) {
-            z = warp_sum(z); sM = warp_sum(sM); sH = warp_sum(sH);
-            if (variances) { sMM = warp_sum(sMM); sHH = warp_sum(sHH); }
-            if (mag) { zA = warp_sum(zA); z2 = warp_sum(z2); z4 = warp_sum(z4); }
+            F v[8] = {z, sM, sH, sMM, sHH, zA, z2, z4};
+            warp_sum8(v);
             if (lane != 0) continue;
+            z = v[0]; sM = v[1]; sH = v[2]; sMM = v[3]; sHH = v[4]; zA = v[5]; z2 = v[6]; z4 = v[7];
         }
         const F iz = (F)1 / z;
         const F dm = sM * iz, dh = sH * iz;
         const size_t o = (size_t)it * a.nh + ih;
         if (a.logZ) a.logZ[o] = L[ms] + hTd * (double)Ms + (double)lg<F>(z);
-        if (a.E) a.E[o] = (double)((mus - hF * MsF) + dh);
+        if (a.E) a.E[o] = (double)(fmaF(-hF, MsF, mus) + dh);
         if (a.M) a.M[o] = (double)(MsF + dm);
-        if (a.C) a.C[o] = (double)((sHH * iz - dh * dh) * invT2);
-        if (a.chi) a.chi[o] = (double)((sMM * iz - dm * dm) * invT);
+        if (a.C) a.C[o] = (double)(fmaF(sHH, iz, -dh * dh) * invT2);
+        if (a.chi) a.chi[o] = (double)(fmaF(sMM, iz, -dm * dm) * invT);
         if (mag) {
             const F m2 = z2 * iz, m4 = z4 * iz;
             if (a.absM) a.absM[o] = (double)(zA * iz);
@@ -349,28 +484,56 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
     }
 }
 
+// The graph's energy sublattice in public bins: reachable energies E = e_lo + G k (k < n_e_c) sit
+// at bins (E + S) / 2 = e0 + (G / 2) k.
+void set_energy_sublattice(ThermoArgs& a, const isg_graph& g) {
+    a.e0 = (int)((g.e_lo + g.S) / 2);
+    a.eg = (int)(g.G / 2);
+    a.n_on = (int)g.n_e_c;
+}
+
 // Enqueue the thermodynamics kernels; all pointers on the device. lng: n_e * n_m doubles, lngf:
-// 2 * n_e * n_m floats of scratch.
-void launch_thermo(const ThermoParams& P, double* lng, float* lngf, int precision, cudaStream_t s) {
-    const ThermoArgs& a = P.a;
+// 2 * n_e * n_m floats of scratch. P.a.cluster is set here.
+void launch_thermo(ThermoParams& P, double* lng, float* lngf, int precision, cudaStream_t s) {
+    ThermoArgs& a = P.a;
     const int nbins = a.n_e * a.n_m;
     float* lnglo = lngf + nbins;
-    log_counts_kernel<<<std::min(1024, (nbins + 255) / 256), 256, 0, s>>>(a.g, nbins, lng, lngf, lnglo);
+    // 128 threads: one warp per SM sub-partition, so the FP64 logarithms of a small table spread
+    // over as many FP64 units as there are warps
+    log_counts_kernel<<<std::min(2048, (nbins + 127) / 128), 128, 0, s>>>(a.g, nbins, lng, lngf, lnglo);
     ISG_CUDA(cudaGetLastError());
-    // Few temperatures (fewer CTAs than SMs): one warp per column in stage 1, up to 32 warps, so
-    // latency-bound small grids run their columns side by side. Otherwise 256 threads per CTA,
-    // several CTAs per SM.
-    int sms = 0, dev = 0;
-    ISG_CUDA(cudaGetDevice(&dev));
-    ISG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int threads = a.nT < sms ? 32 * std::min(32, std::max(8, a.n_m)) : 256;
-    if (precision == ISG_FP64) {
-        const size_t smem = (size_t)a.n_m * (8 + 6 * sizeof(double) + 4);
-        thermo_kernel<double><<<a.nT, threads, smem, s>>>(P, lng, lngf, lnglo);
-    } else {
-        const size_t smem = (size_t)a.n_m * (8 + 6 * sizeof(float) + 4);
-        thermo_kernel<float><<<a.nT, threads, smem, s>>>(P, lng, lngf, lnglo);
-    }
+    // Few temperatures (fewer than half the SMs): a cluster of up to 8 CTAs per temperature
+    // shares stage 1's columns, one warp per column in each CTA. Fewer than the SMs: one CTA per
+    // temperature, one warp per column. Otherwise 256 threads per CTA, several CTAs per SM.
+    const int sms = device_info().sms;
+    int csz = 1;
+    if (2 * a.nT <= sms) csz = std::max(1, std::min(std::min(8, sms / a.nT), (a.n_m + 3) / 4));
+    a.cluster = csz;
+    const int cols = (a.n_m + csz - 1) / csz;
+    const int threads = a.nT < sms ? 32 * std::min(32, std::max(8, cols)) : 256;
+    const size_t smem = (size_t)a.n_m * (8 + 6 * (precision == ISG_FP64 ? sizeof(double) : sizeof(float)) + 4 + 4);
+    auto launch = [&](auto kernel) {
+        if (csz == 1) {
+            kernel<<<a.nT, threads, smem, s>>>(P, lng, lngf, lnglo);
+            return;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(a.nT * csz));
+        cfg.blockDim = dim3((unsigned)threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)csz;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        ISG_CUDA(cudaLaunchKernelEx(&cfg, kernel, (const ThermoParams)P, (const double*)lng, (const float*)lngf,
+                                    (const float*)lnglo));
+    };
+    if (precision == ISG_FP64) launch(thermo_kernel<double>);
+    else launch(thermo_kernel<float>);
     ISG_CUDA(cudaGetLastError());
 }
 
@@ -405,6 +568,7 @@ extern "C" isg_status isg_specific_heat_peak(const int64_t* g, int32_t g_on_devi
         std::unique_ptr<ThermoParams> P(new ThermoParams());
         ThermoArgs& a = P->a;
         a.n = graph->n; a.n_e = n_e; a.n_m = n_m; a.nT = kGrid; a.nh = 1; a.e_min = -graph->S;
+        set_energy_sublattice(a, *graph);
         a.T = nullptr;
         a.h = nullptr;
         if (g_on_device) a.g = g;
@@ -474,6 +638,7 @@ static void thermo_grid(const int64_t* g, int32_t g_on_device, const isg_graph* 
     std::unique_ptr<ThermoParams> P(new ThermoParams());
     ThermoArgs& a = P->a;
     a.n = graph->n; a.n_e = n_e; a.n_m = n_m; a.nT = nT; a.nh = nh; a.e_min = -graph->S;
+    set_energy_sublattice(a, *graph);
     if (inline_grid) {
         std::memcpy(P->grid, T, sizeof(double) * nT);
         std::memcpy(P->grid + nT, h, sizeof(double) * nh);

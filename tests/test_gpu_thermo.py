@@ -82,6 +82,59 @@ def test_cubic_grid_fp32_vs_fp64(isg, cuda):
         assert np.all(err <= np.maximum(1e-3 * np.abs(d[k]), 1e-3 * scale)), k
 
 
+@pytest.mark.parametrize("nT", [1, 5, 19, 40, 75, 76, 77])
+def test_fp64_cluster_shapes_torus_6x6(isg, cuda, nT):
+    """Grids of at most half as many temperatures as SMs split stage 1 over a thread-block cluster
+    per temperature (on 152 SMs: 8 CTAs for 1, 5 and 19 temperatures, 3 for 40, 2 for 75 and 76,
+    none for 77). Every shape against the oracle on the 6x6 torus's table, with few fields (a warp
+    per point) and many (a thread per point)."""
+    lat = w.square(6, 6, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = isg.isg_enumerate(gh)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    T = np.linspace(0.4, 6, nT)
+    for h in (np.array([-1.0, 0.0, 0.5]), np.linspace(-2, 2, 64)):
+        got = isg.isg_thermo(g, gh, T, h, isg.ISG_FP64)
+        ref = oracle.thermo(lat.n, e_min, g, T, h)
+        for k, (a, b) in enumerate(zip(got, ref)):
+            assert rel_close(a, b, 1e-12, 1e-12 * lat.n), (k, len(h), np.max(np.abs(a - b) / (np.abs(b) + 1e-300)))
+
+
+def test_table_off_energy_sublattice(isg, cuda):
+    """On the 4x4 torus every energy is a multiple of 4, so stage 1 walks every other energy bin.
+    A table with counts on the other bins (in every other column: the shape of this graph's table,
+    not its values) makes those columns fall back to the walk over every bin. FP64 against the
+    oracle on a clustered (64 T) and an unclustered (200 T) grid, few and many fields; FP32
+    within its ln Z bound of FP64."""
+    lat = w.square(4, 4, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = isg.isg_enumerate(gh)
+    rng = w.SplitMix64(21)
+    n_e, n_m = g.shape
+    for m in range(0, n_m, 2):
+        for e in range(n_e):
+            g[e, m] += rng.below(1000)
+    assert np.any(g[1::2, 0] > 0)                     # odd bins are off the sublattice here
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    for T in (np.linspace(0.5, 5, 64), np.linspace(0.3, 8, 200)):
+        for h in (np.array([-1.0, 0.0, 0.7]), np.linspace(-2, 2, 70)):
+            got = isg.isg_thermo(g, gh, T, h, isg.ISG_FP64)
+            ref = oracle.thermo(lat.n, e_min, g, T, h)
+            for k, (a, b) in enumerate(zip(got, ref)):
+                assert rel_close(a, b, 1e-12, 1e-12 * lat.n), (k, len(T), len(h))
+            f = isg.isg_thermo(g, gh, T, h, isg.ISG_FP32)
+            assert np.max(np.abs(f[0] - got[0])) <= 2e-5
+
+
+def test_fp64_extreme_temperatures_and_fields(isg, cuda):
+    """S/T up to 3.2e4 and |h/T| N up to 8e5, where the reference bins and dominant columns are
+    searched in double rather than float; against the oracle at 1e-12."""
+    T = np.array([1e-3, 2e-3, 0.01, 0.05, 0.5, 3.0, 1e3])
+    h = np.array([-50.0, -1.0, 0.0, 1e-3, 1.0, 50.0])
+    fp64_vs_oracle(isg, w.square(4, 4, True), T, h)
+    fp64_vs_oracle(isg, w.with_random_couplings(w.triangular(3, 4, True), w.SplitMix64(5), (-2, -1, 1, 2)), T, h)
+
+
 def test_thermo_device_outputs(isg, cuda):
     import torch
     lat = w.square(4, 4, True)
