@@ -87,17 +87,55 @@ struct AccBuf {
 };
 
 // The low block of a component walk: from its all-down state, steps T = 1 .. 2^B - 1 of the
-// reflected Gray code, unrolled at compile time (the flipped bit, its direction and the up count
-// are constants): one add and one shared reduction per configuration. h[k] is the field on low spin
-// k, constant over the block because low spins have no bond among them.
+// reflected Gray code, unrolled at compile time (the flipped bit and its direction are
+// constants): one add and one shared reduction per configuration. The shared byte address `addr`
+// of the current bin (e MC + m) moves by +-G[k] = +-4 (h_k MC - 1) when low spin k flips (e by
+// +-h_k, m by -+1), h_k the field on low spin k, constant over the block because low spins have
+// no bond among them. The address is an in/out operand of the reduction, so the chain of
+// addresses stays in step with the reductions.
 template <int B, int T>
-__device__ __forceinline__ void split_low_steps(int e, int base, const int (&h)[B], uint32_t* hist, int MC) {
+__device__ __forceinline__ void split_low_steps(uint32_t& addr, const int (&G)[B]) {
     if constexpr (T < (1 << B)) {
         constexpr int k = split_ctz(T);
         constexpr bool was_up = (split_gray(T - 1) >> k) & 1;
-        e += was_up ? h[k] : -h[k];
-        atomicAdd(&hist[e * MC + base + split_popc(split_gray(T))], 1u);
-        split_low_steps<B, T + 1>(e, base, h, hist, MC);
+        addr += was_up ? (uint32_t)G[k] : (uint32_t)-G[k];
+        asm volatile("red.shared.add.u32 [%0], 1;" : "+r"(addr) : : "memory");
+        split_low_steps<B, T + 1>(addr, G);
+    }
+}
+
+// A walker's configurations with a low block of B spins: the mid bits (L - B of them) in Gray
+// order, and at each mid state the low block from all down, its fields in registers, checked once
+// against the histogram's range (a bin outside it would be a bug: recorded in bad, not written).
+// x, e, m: the walker's configuration and its bin at the low block's all-down state.
+template <int B, class Field>
+__device__ __forceinline__ void split_walk_low(uint32_t& x, int& e, int& m, int L, int nc, int Sc, int MC, uint32_t hs,
+                                               const Field& field, bool& bad) {
+    for (uint32_t tm = 0; tm < (1u << (L - B)); ++tm) {
+        if (tm) {
+            const int k = B + __ffs(tm) - 1;         // the same spin in every walker
+            const bool up = (x >> k) & 1;
+            const int hk = field(k, x);
+            e += up ? hk : -hk;
+            m += up ? -1 : 1;
+            x ^= 1u << k;
+        }
+        int G[B];
+        int lo = e, hi = e;
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int h = field(j, x);
+            lo -= h > 0 ? h : 0;
+            hi -= h < 0 ? h : 0;
+            G[j] = 4 * (h * MC - 1);
+        }
+        if (lo >= 0 && hi <= Sc && m + B <= nc) {
+            uint32_t addr = hs + 4u * (uint32_t)(e * MC + m);
+            asm volatile("red.shared.add.u32 [%0], 1;" : "+r"(addr) : : "memory");
+            split_low_steps<B, 1>(addr, G);
+        } else {
+            bad = true;
+        }
     }
 }
 
@@ -199,33 +237,10 @@ __global__ void __launch_bounds__(kSplitThreads) split_kernel(const __grid_const
                 uint32_t x = (uint32_t)tid << L;
                 int e = (twice_energy(x) / 2 + cp.Sc) / 2;
                 int m = __popc(x);
-                if (cp.low == kSplitLow) {
-                    // mid bits in Gray order; at each mid state the low block from all down, its
-                    // fields in registers, checked once against the histogram's range
-                    for (uint32_t tm = 0; tm < (1u << (L - kSplitLow)); ++tm) {
-                        if (tm) {
-                            const int k = kSplitLow + __ffs(tm) - 1;         // the same spin in every walker
-                            const bool up = (x >> k) & 1;
-                            const int hk = field(k, x);
-                            e += up ? hk : -hk;
-                            m += up ? -1 : 1;
-                            x ^= 1u << k;
-                        }
-                        int h[kSplitLow];
-                        int lo = e, hi = e;
-#pragma unroll
-                        for (int j = 0; j < kSplitLow; ++j) {
-                            h[j] = field(j, x);
-                            lo -= h[j] > 0 ? h[j] : 0;
-                            hi -= h[j] < 0 ? h[j] : 0;
-                        }
-                        if (lo >= 0 && hi <= cp.Sc && m + kSplitLow <= nc) {
-                            atomicAdd(&hist[e * MC + m], 1u);
-                            split_low_steps<kSplitLow, 1>(e, m, h, hist, MC);
-                        } else {
-                            bad = true;                                       // a bug: recorded, not written
-                        }
-                    }
+                if (cp.low) {
+                    const uint32_t hs = (uint32_t)__cvta_generic_to_shared(hist);
+                    if (cp.low == kSplitLowLarge) split_walk_low<kSplitLowLarge>(x, e, m, L, nc, cp.Sc, MC, hs, field, bad);
+                    else split_walk_low<kSplitLow>(x, e, m, L, nc, cp.Sc, MC, hs, field, bad);
                 } else {
                     // a bin outside the histogram (a bug) is recorded and skipped, never written
                     auto count = [&](int ee, int mm) {

@@ -34,9 +34,10 @@ std::vector<uint64_t> adjacency(const isg_graph& g) {
     return adj;
 }
 
-// Connected components of the spins in `rem` (bit masks), by breadth-first growth.
-std::vector<uint64_t> components(const std::vector<uint64_t>& adj, uint64_t rem) {
-    std::vector<uint64_t> out;
+// Connected components of the spins in `rem` (bit masks), by breadth-first growth, into out[]
+// (at most 64 of them: one per spin); returns their number.
+int components(const std::vector<uint64_t>& adj, uint64_t rem, uint64_t (&out)[64]) {
+    int k = 0;
     while (rem) {
         uint64_t comp = rem & (~rem + 1), front = comp;
         while (front) {
@@ -45,10 +46,10 @@ std::vector<uint64_t> components(const std::vector<uint64_t>& adj, uint64_t rem)
             front = nb & rem & ~comp;
             comp |= front;
         }
-        out.push_back(comp);
+        out[k++] = comp;
         rem &= ~comp;
     }
-    return out;
+    return k;
 }
 
 // Per spin: the sum of |J| over its bonds and its neighbours grouped by |J|, so that the bond weight
@@ -77,6 +78,13 @@ struct WeightIndex {
         return w - twice_inside / 2;
     }
 };
+
+// Modelled operations per configuration of a component walk: with a low block (assumed found)
+// about 4 per configuration plus its fields and the mid flip per 2^low configurations; without
+// one a field and a count each.
+static double walk_cost_per_config(int low, int n_cls) {
+    return low ? 4 + (low * (6 + 3.0 * n_cls) + 24 + 3.0 * n_cls) / std::ldexp(1.0, low) : 8 + 3.0 * n_cls;
+}
 
 struct Candidate {
     uint64_t S = 0;
@@ -146,11 +154,9 @@ void evaluate(const isg_graph& g, const WeightIndex& wi, int n_cls, Candidate& c
         const double walk = std::ldexp(1.0, nc[i]);
         configs += walk;
         // walkers: 2^P threads, each a from-scratch start and its walk (one warp also rechecks);
-        // components large enough for a low block (assumed found) walk it at about 4 operations
-        // per configuration plus its fields and the mid flip per 2^kSplitLow configurations
-        const int low = nc[i] >= kSplitLowMinSpins ? kSplitLow : 0;
+        const int low = split_low_want(nc[i], c.cta_bits);
         const double walkers = std::ldexp(1.0, split_walk_bits(nc[i], low, c.cta_bits));
-        const double per_config = low ? 4 + (kSplitLow * (6 + 3.0 * n_cls) + 24 + 3.0 * n_cls) / 32 : 8 + 3.0 * n_cls;
+        const double per_config = walk_cost_per_config(low, n_cls);
         per_s += ceil32(nc[i]) * (4 + 3.0 * n_cls) + ceil32(hw) * 2 + nc[i] * (4 + 3.0 * n_cls) +
                  ceil32(walkers) * (nc[i] * (4 + 3.0 * n_cls) + (walk / walkers) * per_config);
         const double nnz_h = std::min(hw, walk);
@@ -225,20 +231,28 @@ SplitPlan plan_split(const isg_graph& g, uint64_t boundary, bool require_gain) {
     const WeightIndex wi(g);
     const uint64_t all = low_mask(n);
     Candidate best;
+    // The walks alone bound the work from below: per boundary configuration a component of nc
+    // spins costs at least walk_floor[nc] (its walk at its cheapest, with the largest low block
+    // any CTA size allows), and the model charges at least one wave of CTAs (two per SM of 512
+    // threads). Candidates whose bound loses skip the full model.
+    double walk_floor[kSplitMaxCompSpins + 1];
+    for (int nc = 0; nc <= kSplitMaxCompSpins; ++nc)
+        walk_floor[nc] = std::max(1.0, std::ldexp(1.0, nc) / 32) * walk_cost_per_config(split_low_want(nc, 8), n_cls);
     auto consider = [&](uint64_t S) {
         S &= all;
-        Candidate c;
-        c.S = S;
-        c.comps = components(adj, all & ~S);
-        // the walks alone bound the work from below: skip the full model when that bound loses
+        uint64_t comps[64];
+        const int k = components(adj, all & ~S, comps);
         double walk = 0;
-        for (uint64_t m : c.comps) {
-            const int nc = popc(m);
+        for (int i = 0; i < k; ++i) {
+            const int nc = popc(comps[i]);
             if (nc > kSplitMaxCompSpins) return;
-            walk += std::max(1.0, std::ldexp(1.0, nc) / 32);
+            walk += walk_floor[nc];
         }
         const int ns = popc(S);
-        if (std::ldexp(walk * (8 + 3.0 * n_cls), ns > 0 ? ns - 1 : 0) >= best.cost) return;
+        if (walk * std::max((double)(1ull << (ns > 0 ? ns - 1 : 0)), 2.0 * 152) >= best.cost) return;
+        Candidate c;
+        c.S = S;
+        c.comps.assign(comps, comps + k);
         evaluate(g, wi, n_cls, c);
         if (c.cost < best.cost) best = std::move(c);
     };
@@ -332,13 +346,15 @@ std::vector<uint64_t> build_split_program(const isg_graph& g, const SplitPlan& p
     int64_t EO = 1, MO = 1, hmax = 0, sumSc = 0;
     int first = 0;
     for (int c = 0; c < k; ++c) {
-        // a component of at least kSplitLowMinSpins spins gets a low block: kSplitLow of its spins
-        // with no bond among them (greedy, fewest bonds inside the component first) as its lowest
-        // local bits, so a walk can hold their fields in registers
+        // a component of at least kSplitLowMinSpins spins gets a low block: kSplitLowLarge or
+        // kSplitLow of its spins (split_low_want) with no bond among them (greedy, fewest bonds
+        // inside the component first) as its lowest local bits, so a walk can hold their fields in
+        // registers
         std::vector<int> v = p.comps[c];
         const int nc = (int)v.size();
         int low = 0;
-        if (nc >= kSplitLowMinSpins) {
+        for (int want = split_low_want(nc, p.cta_bits); want > 0 && !low;
+             want = want == kSplitLowLarge && nc >= kSplitLowMinSpins ? kSplitLow : 0) {
             std::vector<int> order(nc), pick;
             for (int a = 0; a < nc; ++a) order[a] = a;
             auto deg = [&](int a) { int d = 0; for (int b = 0; b < nc; ++b) d += b != a && coupling(v[a], v[b]) != 0; return d; };
@@ -347,15 +363,15 @@ std::vector<uint64_t> build_split_program(const isg_graph& g, const SplitPlan& p
                 bool free = true;
                 for (int b : pick) free = free && coupling(v[a], v[b]) == 0;
                 if (free) pick.push_back(a);
-                if ((int)pick.size() == kSplitLow) break;
+                if ((int)pick.size() == want) break;
             }
-            if ((int)pick.size() == kSplitLow) {
+            if ((int)pick.size() == want) {
                 std::vector<int> v2;
                 for (int a : pick) v2.push_back(v[a]);
                 for (int a = 0; a < nc; ++a)
                     if (std::find(pick.begin(), pick.end(), a) == pick.end()) v2.push_back(v[a]);
                 v = v2;
-                low = kSplitLow;
+                low = want;
             }
         }
         int64_t Sc = 0;
@@ -469,7 +485,8 @@ void emulate_split(const std::vector<uint64_t>& blob, int64_t* g_out) {
                 if (cp.low) {
                     // mid bits walked in Gray order; at each mid state the low block (all down to
                     // start, its fields fixed) in its own Gray order
-                    if (cp.low != kSplitLow || L < cp.low) fail(ISG_ERR_INTERNAL, "bad low block");
+                    if ((cp.low != kSplitLow && cp.low != kSplitLowLarge) || L < cp.low)
+                        fail(ISG_ERR_INTERNAL, "bad low block");
                     for (uint32_t tm = 0; tm < (1u << (L - cp.low)); ++tm) {
                         if (tm) {
                             const int kk = cp.low + __builtin_ctz(tm);
@@ -479,15 +496,23 @@ void emulate_split(const std::vector<uint64_t>& blob, int64_t* g_out) {
                             m += up ? -1 : 1;
                             x ^= 1u << kk;
                         }
-                        int64_t hl[kSplitLow];
-                        for (int j = 0; j < cp.low; ++j) hl[j] = field_at(j, x);
+                        // the kernel moves a histogram address by +-G_k = +-(h_k MC - 1) words per
+                        // step from e MC + m; it is checked here against the tracked bin
+                        int64_t hl[kSplitLowLarge], Gl[kSplitLowLarge];
+                        for (int j = 0; j < cp.low; ++j) {
+                            hl[j] = field_at(j, x);
+                            Gl[j] = hl[j] * MC - 1;
+                        }
                         count(e, m);
-                        int64_t el = e;
+                        int64_t el = e, addr = e * MC + m;
                         for (int tl = 1; tl < (1 << cp.low); ++tl) {
                             const int kk = split_ctz(tl);
                             const bool was_up = (split_gray(tl - 1) >> kk) & 1;
                             el += was_up ? hl[kk] : -hl[kk];
-                            count(el, m + split_popc(split_gray(tl)));
+                            addr += was_up ? Gl[kk] : -Gl[kk];
+                            const int ml = m + split_popc(split_gray(tl));
+                            if (addr != el * MC + ml) fail(ISG_ERR_INTERNAL, "low-block address lost its bin");
+                            count(el, ml);
                         }
                     }
                 } else {

@@ -34,7 +34,8 @@ constexpr int kSplitMaxComp = 64;
 constexpr int kSplitMaxCompSpins = 30;   // a component's configurations fit a 32-bit word walk
 constexpr int kSplitThreads = 512;       // threads of a split CTA (one boundary configuration at a time)
 constexpr int kSplitWalkBits = 9;        // at most 2^9 = 512 walkers per component (one per thread)
-constexpr int kSplitLow = 5;             // size of a component walk's low block
+constexpr int kSplitLow = 5;             // size of a component walk's low block ...
+constexpr int kSplitLowLarge = 7;        // ... or of the larger one, where a component has room for it
 constexpr int kSplitLowMinSpins = 12;    // components given a low block: at least this many spins
 // Warp instructions per configuration of the full enumeration (ncu on the 6x6 torus: 2.86 per 32
 // configurations): the unit in which the planner compares a split with the full enumeration.
@@ -49,6 +50,14 @@ constexpr double kSplitLaunchWarpInstr = 2.5e7;
 ISG_SPLIT_HD inline int split_walk_bits(int nc, int low, int cta_bits) {
     const int cap = nc - low;
     return cap < cta_bits ? (cap < 0 ? 0 : cap) : cta_bits;
+}
+
+// Low-block size wanted for a component of nc spins in CTAs of 2^cta_bits threads: the larger
+// block where the component still has a bit for every thread above it (its mid states are then
+// fewer per configuration: 1 in 128), else the smaller one from kSplitLowMinSpins spins, else
+// none. The program builder falls back to a smaller block when no such independent set exists.
+ISG_SPLIT_HD inline int split_low_want(int nc, int cta_bits) {
+    return nc - kSplitLowLarge >= cta_bits ? kSplitLowLarge : (nc >= kSplitLowMinSpins ? kSplitLow : 0);
 }
 
 // Threads per split CTA: 256 (up to four CTAs per SM, so one waits at a barrier while others
@@ -74,7 +83,7 @@ static_assert(sizeof(SplitHeader) == 64, "header is 8 words");
 // Per component (four 64-bit words).
 struct SplitComp {
     int32_t nc, Sc, first, h_words;      // spins, sum |J| touching it, index of its first spin record, (Sc+1)(nc+1)
-    int32_t low;                         // kSplitLow: local bits 0..4 are mutually unbonded (a low block); else 0
+    int32_t low;                         // kSplitLow or kSplitLowLarge: local bits 0..low-1 are mutually unbonded (a low block); else 0
     int32_t reserved[3];
 };
 
