@@ -89,10 +89,10 @@ struct AccBuf {
 // The low block of a component walk: from its all-down state, steps T = 1 .. 2^B - 1 of the
 // reflected Gray code, unrolled at compile time (the flipped bit and its direction are
 // constants): one add and one shared reduction per configuration. The shared byte address `addr`
-// of the current bin (e MC + m) moves by +-G[k] = +-4 (h_k MC - 1) when low spin k flips (e by
-// +-h_k, m by -+1), h_k the field on low spin k, constant over the block because low spins have
-// no bond among them. The address is an in/out operand of the reduction, so the chain of
-// addresses stays in step with the reductions.
+// of the current bin (e MC + m, MC the histogram's row stride) moves by +-G[k] = +-4 (h_k MC - 1)
+// when low spin k flips (e by +-h_k, m by -+1), h_k the field on low spin k, constant over the
+// block because low spins have no bond among them. The address is an in/out operand of the
+// reduction, so the chain of addresses stays in step with the reductions.
 template <int B, int T>
 __device__ __forceinline__ void split_low_steps(uint32_t& addr, const int (&G)[B]) {
     if constexpr (T < (1 << B)) {
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kSplitThreads) split_kernel(const __grid_const
         if (H.n_comp == 0 && tid == 0) acc.set(0, (Acc)1);     // every spin is boundary: the empty convolution
         for (int c = 0; c < H.n_comp; ++c) {
             const SplitComp cp = v.comp[c];
-            const int nc = cp.nc, MC = nc + 1;
+            const int nc = cp.nc, MC = cp.hstride;   // bin (e, m) at e MC + m; columns m > nc are padding
             const uint64_t* sp = v.spin + (size_t)cp.first * ncl * 2;
             // component spin records: the field from the boundary (both paths), and with few
             // classes {mask of class 0, mask of class 1, f - J0 deg0 - J1 deg1} so that
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kSplitThreads) split_kernel(const __grid_const
                 __syncthreads();
                 for (int i = tid; i < cp.h_words; i += blockDim.x) {
                     const int e1 = i / MC, m1 = i - e1 * MC;
-                    acc.set(e1 * MO + m1, (Acc)hist[i]);
+                    if (m1 <= nc) acc.set(e1 * MO + m1, (Acc)hist[i]);
                 }
             } else {
                 if (tid == 0) { sc[0] = 0; sc[1] = 0; }

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <memory>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -52,12 +53,40 @@ int components(const std::vector<uint64_t>& adj, uint64_t rem, uint64_t (&out)[6
     return k;
 }
 
+// Per spin i: the lowest set bit of gcd(|sum_j J_ij|, 2 gcd_j |J_ij|), the power-of-two part of
+// every energy step a flip of i can make (Delta e = +-h_i, h_i = sum_j J_ij S_j); 0 for a spin
+// with no bonds.
+std::vector<uint32_t> spin_step_lowbits(const isg_graph& g) {
+    std::vector<uint32_t> out(g.n, 0);
+    for (int i = 0; i < g.n; ++i) {
+        int64_t sum = 0, gq = 0;
+        for (int j = 0; j < g.n; ++j) {
+            const int64_t J = g.K[(size_t)i * g.n + j];
+            if (!J) continue;
+            sum += J;
+            gq = std::gcd(gq, std::llabs(J));
+        }
+        const int64_t r = std::gcd(std::llabs(sum), 2 * gq);
+        out[i] = (uint32_t)(r & -r);
+    }
+    return out;
+}
+
+// Row step of a component's histogram: the largest power of two dividing every energy step of
+// its spins (1 when none can change the energy).
+int component_row_step(const std::vector<uint32_t>& lowbits, uint64_t comp) {
+    uint32_t any = 0;
+    for (uint64_t r = comp; r; r &= r - 1) any |= lowbits[ctz64(r)];
+    return any ? (int)(any & (~any + 1)) : 1;
+}
+
 // Per spin: the sum of |J| over its bonds and its neighbours grouped by |J|, so that the bond weight
 // touching a set of spins is sum_i w_i - (weight inside the set) without a pass over all bonds.
 struct WeightIndex {
     std::vector<int64_t> wsum;
     std::vector<std::vector<std::pair<uint64_t, int64_t>>> groups;   // (neighbour mask, |J|)
-    explicit WeightIndex(const isg_graph& g) : wsum(g.n, 0), groups(g.n) {
+    std::vector<uint32_t> step_lowbits;                               // spin_step_lowbits
+    explicit WeightIndex(const isg_graph& g) : wsum(g.n, 0), groups(g.n), step_lowbits(spin_step_lowbits(g)) {
         for (int i = 0; i < g.n; ++i)
             for (int j = 0; j < g.n; ++j) {
                 const int64_t a = std::llabs(g.K[(size_t)i * g.n + j]);
@@ -129,10 +158,12 @@ void evaluate(const isg_graph& g, const WeightIndex& wi, int n_cls, Candidate& c
     c.Sc = Sc2;
     nc = nc2;
     int64_t EO = 1, MO = 1, hmax = 0;
+    std::vector<int> hstride(k);
     for (size_t i = 0; i < k; ++i) {
         EO += c.Sc[i];
         MO += nc[i];
-        hmax = std::max<int64_t>(hmax, (c.Sc[i] + 1) * (nc[i] + 1));
+        hstride[i] = split_hist_stride(nc[i], component_row_step(wi.step_lowbits, c.comps[i]));
+        hmax = std::max<int64_t>(hmax, (c.Sc[i] + 1) * hstride[i]);
     }
     const int inner = g.n - ns;
     c.u64 = inner > 31;
@@ -150,7 +181,7 @@ void evaluate(const isg_graph& g, const WeightIndex& wi, int n_cls, Candidate& c
     double nnz_acc = 0, rows = 1;
     double configs = 0;
     for (size_t i = 0; i < k; ++i) {
-        const double hw = (double)(c.Sc[i] + 1) * (nc[i] + 1);
+        const double hw = (double)(c.Sc[i] + 1) * hstride[i];       // histogram words, padding included
         const double walk = std::ldexp(1.0, nc[i]);
         configs += walk;
         // walkers: 2^P threads, each a from-scratch start and its walk (one warp also rechecks);
@@ -159,7 +190,7 @@ void evaluate(const isg_graph& g, const WeightIndex& wi, int n_cls, Candidate& c
         const double per_config = walk_cost_per_config(low, n_cls);
         per_s += ceil32(nc[i]) * (4 + 3.0 * n_cls) + ceil32(hw) * 2 + nc[i] * (4 + 3.0 * n_cls) +
                  ceil32(walkers) * (nc[i] * (4 + 3.0 * n_cls) + (walk / walkers) * per_config);
-        const double nnz_h = std::min(hw, walk);
+        const double nnz_h = std::min((double)(c.Sc[i] + 1) * (nc[i] + 1), walk);
         if (i == 0) {
             nnz_acc = nnz_h;
         } else {
@@ -322,6 +353,7 @@ std::vector<uint64_t> build_split_program(const isg_graph& g, const SplitPlan& p
     if (cls.empty()) cls.push_back(1);
     const int n_cls = (int)cls.size();
     auto coupling = [&](int i, int j) { return g.K[(size_t)i * n + j]; };
+    const std::vector<uint32_t> step_lowbits = spin_step_lowbits(g);
     int n_in = 0;
     for (const auto& c : p.comps) n_in += (int)c.size();
     if (n_in + ns != n) fail(ISG_ERR_INTERNAL, "split plan does not cover every spin");
@@ -383,7 +415,10 @@ std::vector<uint64_t> build_split_program(const isg_graph& g, const SplitPlan& p
             if (c2 != c)
                 for (int a : v) for (int b : p.comps[c2])
                     if (coupling(a, b)) fail(ISG_ERR_INTERNAL, "split components are not independent");
-        SplitComp rec{nc, (int32_t)Sc, first, (int32_t)((Sc + 1) * (nc + 1)), low, {0, 0, 0}};
+        uint64_t cmask = 0;
+        for (int a : v) cmask |= 1ull << a;
+        const int hstride = split_hist_stride(nc, component_row_step(step_lowbits, cmask));
+        SplitComp rec{nc, (int32_t)Sc, first, (int32_t)((Sc + 1) * hstride), low, hstride, {0, 0}};
         static_assert(sizeof(SplitComp) == 32, "component record is four words");
         std::memcpy(&blob[h.off_comp + 4 * (size_t)c], &rec, sizeof rec);
         for (int a = 0; a < nc; ++a)
@@ -399,7 +434,7 @@ std::vector<uint64_t> build_split_program(const isg_graph& g, const SplitPlan& p
         EO += Sc;
         MO += nc;
         sumSc += Sc;
-        hmax = std::max<int64_t>(hmax, (Sc + 1) * (nc + 1));
+        hmax = std::max<int64_t>(hmax, (Sc + 1) * hstride);
     }
     if (S_SS + sumSc != g.S) fail(ISG_ERR_INTERNAL, "split bond weights do not add up to the graph's");
     h.S_SS = (int32_t)S_SS;
@@ -458,7 +493,9 @@ void emulate_split(const std::vector<uint64_t>& blob, int64_t* g_out) {
         if (h.n_comp == 0) { std::fill(acc.begin(), acc.end(), 0); acc[0] = 1; }   // the empty convolution
         for (int c = 0; c < h.n_comp; ++c) {
             const SplitComp cp = v.comp[c];
-            const int nc = cp.nc, MC = nc + 1;
+            const int nc = cp.nc, MC = cp.hstride;
+            if (MC < nc + 1 || (int64_t)(cp.Sc + 1) * MC != cp.h_words || cp.h_words > h.max_h)
+                fail(ISG_ERR_INTERNAL, "component histogram stride or size inconsistent");
             const uint64_t* sp = v.spin + (size_t)cp.first * ncl * 2;
             std::vector<int64_t> f(nc);
             for (int a = 0; a < nc; ++a) f[a] = field(sp + (size_t)a * ncl * 2 + 1, 2, s);
@@ -531,7 +568,7 @@ void emulate_split(const std::vector<uint64_t>& blob, int64_t* g_out) {
             if (c == 0) {
                 std::fill(acc.begin(), acc.end(), 0);
                 for (int64_t e = 0; e <= cp.Sc; ++e)
-                    for (int m = 0; m < MC; ++m) acc[(size_t)e * h.MO + m] = hist[(size_t)e * MC + m];
+                    for (int m = 0; m <= nc; ++m) acc[(size_t)e * h.MO + m] = hist[(size_t)e * MC + m];
             } else {
                 const int64_t used = (rows + 1) * h.MO;
                 size_t nl = 0, nh = 0;
@@ -539,6 +576,7 @@ void emulate_split(const std::vector<uint64_t>& blob, int64_t* g_out) {
                 for (int64_t i = 0; i < (int64_t)cp.h_words; ++i)
                     if (hist[i]) {
                         const int64_t e1 = i / MC, m1 = i % MC;
+                        if (m1 > nc) fail(ISG_ERR_INTERNAL, "count in a histogram padding column");
                         hlist[nh++] = (uint64_t)(uint32_t)(e1 * h.MO + m1) | ((uint64_t)hist[i] << 32);
                     }
                 std::fill(out.begin(), out.end(), 0);

@@ -60,6 +60,22 @@ ISG_SPLIT_HD inline int split_low_want(int nc, int cta_bits) {
     return nc - kSplitLowLarge >= cta_bits ? kSplitLowLarge : (nc >= kSplitLowMinSpins ? kSplitLow : 0);
 }
 
+// Row stride of a component histogram: nc + 1, padded (by at most 10) so that the rows a walk
+// uses, every rs-th one, lie a good bank distance apart. rs is the largest power of two dividing
+// every energy step of the component (2 on the tori: all fields are even, so a walk keeps one
+// parity of e). The walkers of a warp differ in five spins, so their bins differ by a few rows and
+// columns; a row distance of 5-7, 9, 11, 13, 19, 21, 23 or 25-27 banks (mod 32) sends the common
+// small offsets to distinct banks. With no such stride within reach (rs >= 4) the rows stay
+// unpadded.
+ISG_SPLIT_HD inline int split_hist_stride(int nc, int rs) {
+    for (int s = nc + 1; s <= nc + 32; ++s) {
+        const int r = (rs * s) & 31;
+        if ((r >= 5 && r <= 7) || r == 9 || r == 11 || r == 13 || r == 19 || r == 21 || r == 23 || (r >= 25 && r <= 27))
+            return s;
+    }
+    return nc + 1;
+}
+
 // Threads per split CTA: 256 (up to four CTAs per SM, so one waits at a barrier while others
 // issue) when four CTAs' shared memory fits an SM, else 512.
 inline int split_cta_bits(size_t cta_smem_bytes) { return 4 * (cta_smem_bytes + 1024) <= 233472 ? 8 : kSplitWalkBits; }
@@ -82,9 +98,10 @@ static_assert(sizeof(SplitHeader) == 64, "header is 8 words");
 
 // Per component (four 64-bit words).
 struct SplitComp {
-    int32_t nc, Sc, first, h_words;      // spins, sum |J| touching it, index of its first spin record, (Sc+1)(nc+1)
+    int32_t nc, Sc, first, h_words;      // spins, sum |J| touching it, index of its first spin record, (Sc+1) hstride
     int32_t low;                         // kSplitLow or kSplitLowLarge: local bits 0..low-1 are mutually unbonded (a low block); else 0
-    int32_t reserved[3];
+    int32_t hstride;                     // histogram row stride (>= nc + 1): bin (e, m) at e hstride + m
+    int32_t reserved[2];
 };
 
 // Sections (64-bit words):
