@@ -109,10 +109,10 @@ struct WeightIndex {
 };
 
 // Modelled operations per configuration of a component walk: with a low block (assumed found)
-// about 4 per configuration plus its fields and the mid flip per 2^low configurations; without
-// one a field and a count each.
+// 2 per configuration (an add to the bin address and a reduction) plus its fields and the mid
+// flip per 2^low configurations; without one a field and a checked count each.
 static double walk_cost_per_config(int low, int n_cls) {
-    return low ? 4 + (low * (6 + 3.0 * n_cls) + 24 + 3.0 * n_cls) / std::ldexp(1.0, low) : 8 + 3.0 * n_cls;
+    return low ? 2 + (low * (6 + 3.0 * n_cls) + 24 + 3.0 * n_cls) / std::ldexp(1.0, low) : 8 + 3.0 * n_cls;
 }
 
 struct Candidate {
