@@ -277,6 +277,10 @@ void launch_batch(const BatchPlan& bp, const BatchInst* d_inst, const uint64_t* 
 
 using namespace isg;
 
+// Parallel branches for a batch's split launches (concurrent kernels: enough to keep the GPU busy
+// across the launches' ramps and tails).
+constexpr size_t kSplitBranches = 8;
+
 // A prepared batch: device-resident programs, descriptors and output tables, and the CUDA graph
 // of one run (zero the tables and the counter, launch the kernels), captured on first use.
 struct isg_batch {
@@ -305,15 +309,33 @@ struct isg_batch {
     };
     std::vector<SplitJob> splits;
     bool has_tiles = true;
+    // The split launches write disjoint tables (and the status word, by atomic OR), so they run as
+    // parallel branches: round-robin over these streams, forked from and joined back into the
+    // enqueuing stream (parallel nodes of the captured graph), beside the tile kernel.
+    std::vector<cudaStream_t> branch;
+    std::vector<cudaEvent_t> branch_done;
+    cudaEvent_t fork = nullptr;
 };
 
 static void batch_enqueue(isg_batch* b, cudaStream_t s) {
     ISG_CUDA(cudaMemsetAsync(b->d_tables, 0, b->table_words * 8, s));
     ISG_CUDA(cudaMemsetAsync(b->d_counter, 0, 16, s));
-    for (const auto& j : b->splits)
-        launch_split(*j.prep, j.d_blob, reinterpret_cast<unsigned long long*>(j.d_table), b->d_status, s);
+    const size_t nb = b->branch.size();
+    if (nb) {
+        ISG_CUDA(cudaEventRecord(b->fork, s));
+        for (cudaStream_t t : b->branch) ISG_CUDA(cudaStreamWaitEvent(t, b->fork, 0));
+    }
+    for (size_t k = 0; k < b->splits.size(); ++k) {
+        const auto& j = b->splits[k];
+        launch_split(*j.prep, j.d_blob, reinterpret_cast<unsigned long long*>(j.d_table), b->d_status,
+                     nb ? b->branch[k % nb] : s);
+    }
     if (b->has_tiles)
         launch_batch(b->plan, b->d_inst, b->d_blobs, b->d_small, b->d_counter, b->d_status, s, b->ctas_per_sm);
+    for (size_t i = 0; i < nb; ++i) {
+        ISG_CUDA(cudaEventRecord(b->branch_done[i], b->branch[i]));
+        ISG_CUDA(cudaStreamWaitEvent(s, b->branch_done[i], 0));
+    }
 }
 
 // Time a batch plan on a subset of the graphs: its own device buffers, one warm-up and two timed
@@ -496,6 +518,18 @@ isg_status isg_batch_create(int32_t n_graphs, const isg_graph* const* graphs, co
             split_prepare_launches();          // kernel attributes set now, not during graph capture
         }
         ISG_CUDA(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
+        if (b->splits.size() > 1) {
+            const size_t nb = std::min<size_t>(kSplitBranches, b->splits.size());
+            ISG_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+            for (size_t i = 0; i < nb; ++i) {
+                cudaStream_t t = nullptr;
+                cudaEvent_t e = nullptr;
+                ISG_CUDA(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking));
+                b->branch.push_back(t);
+                ISG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                b->branch_done.push_back(e);
+            }
+        }
         *out = b.release();
     });
 }
@@ -551,6 +585,9 @@ void isg_batch_destroy(isg_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    for (cudaStream_t t : b->branch) cudaStreamDestroy(t);
+    for (cudaEvent_t e : b->branch_done) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->mem) cudaFree(b->mem);
     cudaSetDevice(prev);
     delete b;
