@@ -511,16 +511,103 @@ def calibrate_sample(lat, threads: int, seconds: float) -> int:
     return max(1 << 20, min(1 << lat.n, 1 << max(20, target.bit_length() - 1)))
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_workloads(threads: int, rate: float) -> dict:
+    """The oracle on the other workloads, each a bounded sample extrapolated to the whole: the 4x4
+    free lattice whole on one thread (enumeration and the 64-T thermodynamics); the 4096 EA
+    instances by OpenMP O1 over two instances of each shape; the 3x3x4 cubic torus's enumeration
+    (OpenMP O1) and its FP64 thermodynamics on one core (4 of the 512 temperatures, all 256
+    fields). `rate`: the OpenMP O1 rate measured just before (configurations/s), which sizes each
+    enumeration sample to about a second."""
+    import oracle
+    from paper_1110_2561_gb300 import workloads
+    out = {}
+    lat = workloads.square(4, 4, False)
+    t0 = time.perf_counter()
+    g = oracle.g_masks(lat.n, lat.edges, threads=1)
+    t1 = time.perf_counter()
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    oracle.thermo(lat.n, e_min, g, np.linspace(0.5, 5, 64), [0.0])
+    t2 = time.perf_counter()
+    out["square4x4_free"] = {"what": "O1 on one thread (65,536 configurations) + FP64 thermodynamics on 64 T, one core",
+                             "enumerate_us": (t1 - t0) * 1e6, "thermo_us": (t2 - t1) * 1e6}
+    lats = workloads.ea_instances()
+    per_shape = {}
+    for l in lats:
+        per_shape.setdefault(l.n, []).append(l)
+    total_s, sampled = 0.0, []
+    budget = 1 << max(20, int(rate * 0.5).bit_length() - 1)      # about half a second per instance
+    for n, group in sorted(per_shape.items()):
+        k = min(len(group), 2)
+        cut = min(1 << n, budget)
+        t0 = time.perf_counter()
+        for l in group[:k]:
+            oracle.g_masks(l.n, l.edges, 0, cut, threads=threads)
+        dt = (time.perf_counter() - t0) / k * ((1 << n) / cut)
+        total_s += dt * len(group)
+        sampled.append(f"{k} of the {len(group)} N={n} instances ({cut} configurations each)")
+    out["ea_4096"] = {"what": f"OpenMP O1 ({threads} threads), instance by instance",
+                      "sample": "; ".join(sampled) + "; extrapolated to all 4096", "seconds": total_s,
+                      "instances_per_s": len(lats) / total_s}
+    lat = workloads.cubic(3, 3, 4, True)
+    cut = 1 << max(20, int(rate).bit_length() - 1)               # about a second
+    t0 = time.perf_counter()
+    g = oracle.g_masks(lat.n, lat.edges, 0, cut, threads=threads)
+    t_enum = time.perf_counter() - t0
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    T, h = np.linspace(0.5, 8, 512), np.linspace(-2, 2, 256)
+    t0 = time.perf_counter()
+    oracle.thermo(lat.n, e_min, g, T[::128], h)          # the sample's table: the same shape and sparsity
+    t_thermo = (time.perf_counter() - t0) * (len(T) / len(T[::128]))
+    out["cubic3x3x4"] = {"what": f"OpenMP O1 ({threads} threads) on the first {cut} configurations; FP64 thermodynamics "
+                                 f"on one core over that sample's table, 4 of 512 T x 256 h, extrapolated",
+                         "enumerate_configs_per_s": cut / t_enum, "thermo_s_512x256": t_thermo}
+    return out
+
+
 def cpu_baseline(seconds: float):
+    import oracle
     from paper_1110_2561_gb300 import workloads
     lat = workloads.square(6, 6, True)
     threads = os.cpu_count() or 1
     sample = calibrate_sample(lat, threads, seconds)
     t_enum, t_thermo = oracle_step(lat, sample, threads)
     full_step = t_enum * ((1 << lat.n) / sample) + t_thermo
+    # one thread: one to two seconds of O1 on the same torus
+    cut = 1 << 22
+    while True:
+        t0 = time.perf_counter()
+        oracle.g_masks(lat.n, lat.edges, 0, cut, threads=1)
+        dt1 = time.perf_counter() - t0
+        if dt1 > 1.0 or cut >= 1 << 30:
+            break
+        cut <<= 1
     return {"value": (1 << lat.n) / full_step, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"first {sample} of 2^36 configurations ({t_enum:.2f} s, O1 popcount oracle, {threads} OpenMP "
-                      f"threads) plus the full FP64 thermodynamics ({t_thermo:.3f} s); rate extrapolated to a full step"}
+                      f"threads) plus the full FP64 thermodynamics ({t_thermo:.3f} s); rate extrapolated to a full step",
+            "cpu": cpu_model(),
+            "single_thread_configs_per_s": cut / dt1,
+            "single_thread_sample": f"first {cut} configurations of the 6x6 torus, O1 on one thread ({dt1:.2f} s)",
+            "workloads": cpu_workloads(threads, sample / t_enum)}
 
 
 def run_reference(args):
