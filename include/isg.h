@@ -272,7 +272,9 @@ ISG_API isg_status isg_enumerate_noalloc(const isg_graph* graph, void* stream, i
  * C = Var(H)/T^2, chi = Var(M)/T; any output may be NULL. precision ISG_FP64 or ISG_FP32 (the
  * latter computes weights and sums in float, converting counts and finishing ln Z in double).
  * g on the device if g_on_device, outputs on the device if out_on_device; a call with any host
- * buffer synchronises stream. Errors: ISG_ERR_INVALID, ISG_ERR_NOMEM, ISG_ERR_CUDA.
+ * buffer synchronises stream. Any counts of this geometry are accepted; the graph's own tables,
+ * whose counts lie only on the energies its configurations reach, take the faster path.
+ * Errors: ISG_ERR_INVALID, ISG_ERR_NOMEM, ISG_ERR_CUDA.
  */
 ISG_API isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const isg_graph* graph, int32_t nT,
                       const double* T, int32_t nh, const double* h, int32_t precision, void* stream,
