@@ -93,18 +93,19 @@ def test_fp64_cluster_shapes_torus_6x6(isg, cuda, nT):
     g = isg.isg_enumerate(gh)
     e_min, _, _ = oracle.bins(lat.n, lat.edges)
     T = np.linspace(0.4, 6, nT)
-    for h in (np.array([-1.0, 0.0, 0.5]), np.linspace(-2, 2, 64)):
+    rows = np.unique(np.linspace(0, nT - 1, min(nT, 4)).astype(int))   # the oracle on sampled rows
+    for h, pick in ((np.array([-1.0, 0.0, 0.5]), np.arange(nT)), (np.linspace(-2, 2, 64), rows)):
         got = isg.isg_thermo(g, gh, T, h, isg.ISG_FP64)
-        ref = oracle.thermo(lat.n, e_min, g, T, h)
+        ref = oracle.thermo(lat.n, e_min, g, T[pick], h)
         for k, (a, b) in enumerate(zip(got, ref)):
-            assert rel_close(a, b, 1e-12, 1e-12 * lat.n), (k, len(h), np.max(np.abs(a - b) / (np.abs(b) + 1e-300)))
+            assert rel_close(a[pick], b, 1e-12, 1e-12 * lat.n), (k, len(h), np.max(np.abs(a[pick] - b) / (np.abs(b) + 1e-300)))
 
 
 def test_table_off_energy_sublattice(isg, cuda):
     """On the 4x4 torus every energy is a multiple of 4, so stage 1 walks every other energy bin.
     A table with counts on the other bins (in every other column: the shape of this graph's table,
     not its values) makes those columns fall back to the walk over every bin. FP64 against the
-    oracle on a clustered (64 T) and an unclustered (200 T) grid, few and many fields; FP32
+    oracle on a clustered (64 T) and an unclustered (160 T) grid, few and many fields; FP32
     within its ln Z bound of FP64."""
     lat = w.square(4, 4, True)
     gh = isg.isg_graph_create(lat.n, lat.edges)
@@ -116,12 +117,13 @@ def test_table_off_energy_sublattice(isg, cuda):
             g[e, m] += rng.below(1000)
     assert np.any(g[1::2, 0] > 0)                     # odd bins are off the sublattice here
     e_min, _, _ = oracle.bins(lat.n, lat.edges)
-    for T in (np.linspace(0.5, 5, 64), np.linspace(0.3, 8, 200)):
-        for h in (np.array([-1.0, 0.0, 0.7]), np.linspace(-2, 2, 70)):
+    for T in (np.linspace(0.5, 5, 64), np.linspace(0.3, 8, 160)):
+        for h in (np.array([-1.0, 0.0, 0.7]), np.linspace(-2, 2, 64)):
             got = isg.isg_thermo(g, gh, T, h, isg.ISG_FP64)
-            ref = oracle.thermo(lat.n, e_min, g, T, h)
+            pick = np.arange(len(T)) if len(h) < 64 else np.linspace(0, len(T) - 1, 6).astype(int)
+            ref = oracle.thermo(lat.n, e_min, g, T[pick], h)          # many fields: sampled rows
             for k, (a, b) in enumerate(zip(got, ref)):
-                assert rel_close(a, b, 1e-12, 1e-12 * lat.n), (k, len(T), len(h))
+                assert rel_close(a[pick], b, 1e-12, 1e-12 * lat.n), (k, len(T), len(h))
             f = isg.isg_thermo(g, gh, T, h, isg.ISG_FP32)
             assert np.max(np.abs(f[0] - got[0])) <= 2e-5
 
@@ -133,6 +135,42 @@ def test_fp64_extreme_temperatures_and_fields(isg, cuda):
     h = np.array([-50.0, -1.0, 0.0, 1e-3, 1.0, 50.0])
     fp64_vs_oracle(isg, w.square(4, 4, True), T, h)
     fp64_vs_oracle(isg, w.with_random_couplings(w.triangular(3, 4, True), w.SplitMix64(5), (-2, -1, 1, 2)), T, h)
+
+
+@pytest.mark.parametrize("nT,nh", [(1000, 25), (20, 1010)])
+def test_fp64_grids_beyond_kernel_parameters(isg, cuda, nT, nh):
+    """T and h grids of more than 1024 values together are copied to the device instead of
+    travelling in the kernel parameters: 1000 x 25 (a CTA per temperature, a warp per point) and
+    20 x 1010 (a cluster per temperature, a thread per point), 4x4 torus, against the oracle."""
+    lat = w.square(4, 4, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = isg.isg_enumerate(gh)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    T = np.linspace(0.3, 7, nT)
+    h = np.linspace(-3, 3, nh)
+    got = isg.isg_thermo(g, gh, T, h, isg.ISG_FP64)
+    ref = oracle.thermo(lat.n, e_min, g, T, h)
+    for k, (a, b) in enumerate(zip(got, ref)):
+        assert rel_close(a, b, 1e-12, 1e-12 * lat.n), (k, np.max(np.abs(a - b) / (np.abs(b) + 1e-300)))
+
+
+def test_fp64_torus_8x8_clusters(isg, cuda):
+    """The largest table (8x8 torus, N = 64: 129 x 65 bins, from split-and-convolve) on grids of
+    3 and 40 temperatures, split over clusters of 8 and 3 CTAs on 152 SMs, with a warp per point
+    and (3 temperatures) a thread per point, against the oracle."""
+    import torch
+    lat = w.square(8, 8, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=cuda)
+    isg.isg_enumerate_split(gh, g)
+    g_host = g.cpu().numpy()
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    for T, h in ((np.linspace(1.5, 4, 3), np.array([0.0, 0.3])), (np.linspace(1.5, 4, 3), np.linspace(-1, 1, 64)),
+                 (np.linspace(1.5, 4, 40), np.array([0.0, 0.3]))):
+        got = isg.isg_thermo(g, gh, T, h, isg.ISG_FP64)
+        ref = oracle.thermo(lat.n, e_min, g_host, T, h)
+        for k, (a, b) in enumerate(zip(got, ref)):
+            assert rel_close(a, b, 1e-12, 1e-12 * lat.n), (k, len(T), len(h))
 
 
 def test_thermo_device_outputs(isg, cuda):
