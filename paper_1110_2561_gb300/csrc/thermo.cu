@@ -84,6 +84,12 @@ __device__ __forceinline__ double absF(double x) { return fabs(x); }
 __device__ __forceinline__ float maxF(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double maxF(double a, double b) { return fmax(a, b); }
 
+// -inf marks empty bins and columns. For double the test reads the high word on the integer
+// pipe instead of occupying the narrow FP64 pipe; it is exact here because no finite double has an
+// all-ones exponent (and no value here is a NaN).
+__device__ __forceinline__ bool is_neg_inf(double x) { return __double2hiint(x) == (int)0xfff00000; }
+__device__ __forceinline__ bool is_neg_inf(float x) { return x == -INFINITY; }
+
 template <class F>
 __device__ __forceinline__ F warp_max(F v) {
 #pragma unroll
@@ -158,7 +164,7 @@ __device__ __forceinline__ unsigned column_scan(const U* tab, int n_m, int m, in
         const bool on = r == 0 && e >= e0 && e <= e_last;
         r += r32;
         if (r >= eg) r -= eg;
-        if (l == (U)-INFINITY) continue;
+        if (is_neg_inf(l)) continue;
         if (!on) off = true;
         const U x = fmaF(-En, invT, l);
         if (x > xmax) { xmax = x; ebest = e; }
@@ -177,7 +183,7 @@ __device__ __forceinline__ int dominant_column(const U* Lr, int n, int n_m, int 
     const U Ms = (U)(2 * mstep);
     for (int m = mfirst; m < n_m; m += mstep, Mm += Ms) {
         const U lr = Lr[m];
-        if (lr == (U)-INFINITY) continue;
+        if (is_neg_inf(lr)) continue;
         const U am = fmaF(hT, Mm, lr);
         if (am > amax) { amax = am; ms = m; }
     }
@@ -313,7 +319,7 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
             if (k >= cn) continue;
             const int e = cb + cs * k;
             const F l = lng[(size_t)e * a.n_m + m];
-            if (l == (F)-INFINITY) continue;
+            if (is_neg_inf(l)) continue;
             const F dE = fmaF(EsF, (F)j, ElF) - Eref;
             const F w = ex<F>(arg(e, l, dE));
             wc[j] = w;
@@ -325,7 +331,7 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
             for (int k = lane + 32 * kCache; k < cn; k += 32, En += EsF) {
                 const int e = cb + cs * k;
                 const F l = lng[(size_t)e * a.n_m + m];
-                if (l == (F)-INFINITY) continue;
+                if (is_neg_inf(l)) continue;
                 const F dE = En - Eref;
                 const F w = ex<F>(arg(e, l, dE));
                 s0 += w;
@@ -350,7 +356,7 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
             for (int k = lane + 32 * kCache; k < cn; k += 32, En += EsF) {
                 const int e = cb + cs * k;
                 const F l = lng[(size_t)e * a.n_m + m];
-                if (l == (F)-INFINITY) continue;
+                if (is_neg_inf(l)) continue;
                 const F w = ex<F>(arg(e, l, En - Eref));
                 const F d = En - m1;
                 s2 += w * d * d;
@@ -429,17 +435,20 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
         F z = 0, sM = 0, sH = 0, sMM = 0, sHH = 0, zA = 0, z2 = 0, z4 = 0;
         F dM = (F)(2 * mfirst - a.n - Ms);
         // FP64 chain: p_m = p_(m-1) qin[m] exp(2 h/T), one multiply instead of an exponential,
-        // while the previous weight is above 1e-290 and the factor is finite (<= 1e290); else, and
-        // for FP32, the exponential. <= 64 steps of a few ulp each keep p within ~1e-13.
+        // while the previous weight is at least 2^-964 (~6e-291) and the factor below 2^964
+        // (~1.6e290); else, and for FP32, the exponential. <= 64 steps of a few ulp each keep p
+        // within ~1e-13. The guards compare high words on the integer pipe (positive doubles
+        // order like their bit patterns).
         const F R = (kChain && !by_warp) ? ex<F>((F)2 * hT) : (F)0;
         F pprev = 0;
         for (int m = mfirst; m < a.n_m; m += mstep, dM += dstep) {
-            if (Lr[m] == (F)-INFINITY) { pprev = 0; continue; }
+            if (is_neg_inf(Lr[m])) { pprev = 0; continue; }
             F p;
             if constexpr (kChain) {
                 const F f = by_warp ? (F)0 : qin[m] * R;
-                p = (!by_warp && pprev >= (F)1e-290 && f <= (F)1e290) ? pprev * f
-                                                                      : ex<F>(fmaF(hT, dM, Lr[m] - Ls));
+                p = (!by_warp && __double2hiint(pprev) >= 0x03b00000 && __double2hiint(f) < 0x7c300000)
+                        ? pprev * f
+                        : ex<F>(fmaF(hT, dM, Lr[m] - Ls));
             } else {
                 p = ex<F>((Lr[m] - Ls) + (Llo[m] - Lls) + fmaF(hT, dM, hTlo * dM));
             }
