@@ -372,16 +372,20 @@ void launch_split(const SplitPrepared& prep, const uint64_t* d_blob, unsigned lo
     const DeviceInfo d = device_info();
     const size_t smem = split_smem_bytes((int)prep.blob.size(), H, u64, 1);
     if (smem > (size_t)d.smem_optin) fail(ISG_ERR_TOO_LARGE, "split buffers exceed shared memory");
-    // 64 registers x 512 threads: at most two CTAs of 512 (four of 256) per SM
+    // a grid of the CTAs that can be resident at once (registers and shared memory), never more
+    // than boundary configurations: the grid-stride loop over them then balances by itself
     const int threads = 1 << H.cta_bits;
-    const int ctas_per_sm = std::max(1, (int)std::min<size_t>(2048 / threads, (size_t)d.smem_per_sm / (smem + 1024)));
     const unsigned long long n_s = 1ull << H.ns;
     const unsigned long long n_walk = H.ns ? n_s >> 1 : n_s;
-    const int grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(n_walk, (unsigned long long)d.sms * ctas_per_sm));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     SplitArgs a{d_blob, (int)prep.blob.size(), table, status, n_s};
     split_prepare_launches();
-    auto launch = [&](auto kernel) { kernel<<<grid, threads, smem, s>>>(a); };
+    auto launch = [&](auto kernel) {
+        const int ctas_per_sm = std::max(1, kernel_occupancy(reinterpret_cast<const void*>(kernel), threads, smem));
+        const int grid = (int)std::max<unsigned long long>(
+            1, std::min<unsigned long long>(n_walk, (unsigned long long)d.sms * ctas_per_sm));
+        kernel<<<grid, threads, smem, s>>>(a);
+    };
     const bool few = H.n_cls <= 2;
     if (u64) {
         if (few) launch(split_kernel<unsigned long long, true>);
