@@ -478,6 +478,7 @@ def extra_measurements(stream, dev):
                                 "magnetisation_fp32_ms": tm32, "fp32_vs_fp64": err}
     # a short request stream, enumerating every configuration and with split-and-convolve service
     out["serving_200_requests"] = {"every_configuration": serve_stream(200, 50.0, 20.0, 0.0),
+                                   "symmetry_halving": serve_stream(200, 50.0, 20.0, 0.0, 1),
                                    "split_work_ratio_0.25": serve_stream(200, 50.0, 20.0, 0.25)}
     return out
 
@@ -643,15 +644,16 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------ serving mode
-def serve_stream(n_requests: int, rate: float, step_ms: float, split_ratio: float) -> dict:
+def serve_stream(n_requests: int, rate: float, step_ms: float, split_ratio: float, symmetry: int = 0) -> dict:
     """Poisson stream of lattice requests (seeded; N uniform in 16..38, square / triangular / cubic,
     periodic or free, J uniform in {-2,-1,1,2}) submitted at their arrival times to isg_server;
-    latency percentiles, throughput and offered vs achieved load."""
+    latency percentiles, throughput and offered vs achieved load (configurations counted into the
+    tables; with symmetry the server enumerates about half of them, reported apart)."""
     from paper_1110_2561_gb300 import isg, workloads
 
     reqs = workloads.serving_stream(n_requests, rate_per_s=rate)
     graphs = [isg.isg_graph_create(r.lattice.n, r.lattice.edges) for r in reqs]
-    srv = isg.Server(step_ms=step_ms, split_work_ratio=split_ratio)
+    srv = isg.Server(step_ms=step_ms, split_work_ratio=split_ratio, symmetry=symmetry)
     warm = srv.submit(isg.isg_graph_create(20, workloads.square(4, 5, True).edges))
     srv.wait(warm)
     srv.result(warm)
@@ -673,6 +675,7 @@ def serve_stream(n_requests: int, rate: float, step_ms: float, split_ratio: floa
         if sum(int(v) for v in g.ravel()) != 1 << r.lattice.n:
             bad += 1
     st = srv.stats()
+    elapsed = time.perf_counter() - t0
     srv.close()
     span_arrivals = reqs[-1].arrival_s - reqs[0].arrival_s
     lat_ms = np.array(lat) * 1e3
@@ -683,10 +686,10 @@ def serve_stream(n_requests: int, rate: float, step_ms: float, split_ratio: floa
         "p99_ms": float(np.percentile(lat_ms, 99)), "max_ms": float(lat_ms.max()),
         "mean_queue_ms": float(np.mean(queued) * 1e3),
         "offered_configs_per_s": configs / max(1e-9, span_arrivals),
-        "achieved_configs_per_s": configs / max(1e-9, (time.perf_counter() - t0)),
-        "device_busy_frac": st["device_ms"] * 1e-3 / max(1e-9, time.perf_counter() - t0),
+        "achieved_configs_per_s": configs / max(1e-9, elapsed),
+        "device_busy_frac": st["device_ms"] * 1e-3 / max(1e-9, elapsed),
         "steps": int(st["steps"]), "step_ms": step_ms, "invariant_failures": bad,
-        "split_work_ratio": split_ratio,
+        "split_work_ratio": split_ratio, "symmetry": symmetry,
     }
 
 
@@ -696,7 +699,7 @@ def run_serving(args):
 
     torch.cuda.set_device(0)
     line = {"metric": "serving latency and throughput (continuous batching)", "unit": "ms"}
-    line.update(serve_stream(args.requests, args.rate, args.step_ms, args.split_ratio))
+    line.update(serve_stream(args.requests, args.rate, args.step_ms, args.split_ratio, args.symmetry))
     print(json.dumps(line), flush=True)
 
 
@@ -786,6 +789,8 @@ def main():
     ap.add_argument("--step-ms", type=float, default=20.0)
     ap.add_argument("--split-ratio", type=float, default=0.0,
                     help="serving: serve requests whose split-and-convolve work is below this fraction by split launches")
+    ap.add_argument("--symmetry", type=int, choices=(0, 1), default=0,
+                    help="serving: enumerate each tile-served request's half with spin N-1 up and mirror it")
     ap.add_argument("--shard-bits", type=int, default=0,
                     help="profiling case: enumerate only shard 0 of 2^k per step (not a benchmark line)")
     args = ap.parse_args()

@@ -334,6 +334,11 @@ typedef struct {
                                 plan (isg_enumerate_split) models less than r of that work is served
                                 by one split launch instead; planned at submit, a few milliseconds
                                 of host time. The table is the same either way. */
+    int32_t symmetry;        /* 1: a request of at least 13 spins served by tile steps enumerates only
+                                the configurations with spin N-1 up, and its table is completed by the
+                                mirror M -> -M before it is copied out (the global spin flip maps
+                                (E, M) to (E, -M) for any couplings): half the work, the same table.
+                                0 (default): all 2^N configurations. */
 } isg_server_options;
 
 ISG_API void isg_server_options_init(isg_server_options* opt);

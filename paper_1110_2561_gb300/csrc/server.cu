@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -54,6 +55,8 @@ struct Request {
     std::shared_ptr<const SplitPrepared> split;   // served by split-and-convolve (one launch)
     size_t table_words = 0;          // public table
     uint64_t total_tasks = 0, next_task = 0;
+    uint64_t prefix_base = 0;        // lane prefix of task 0 (the upper half of the space with symmetry)
+    bool sym = false;                // only spin N-1 up enumerated; the step with its last tile mirrors
     double configs = 0;
     size_t slot_off = 0, slot_bytes = 0;   // arena slot: [table][program]
     int64_t last_step = -1;          // last step that carries one of its tiles
@@ -210,6 +213,7 @@ static bool issue_step_locked(isg_server* s) {
     double used = 0;
     std::vector<BatchInst> large, small;
     std::vector<Request*> large_r, small_r, split_r;
+    std::vector<int> mirror;                           // descriptors of halved requests finishing here
     for (Request* r : order) {
         if (used >= budget && (!large.empty() || !split_r.empty())) break;
         BatchInst in{};
@@ -230,10 +234,11 @@ static bool issue_step_locked(isg_server* s) {
             const double per_tile = 32.0 * (double)(1ull << r->q);
             uint64_t take = (uint64_t)std::max(1.0, (budget - used) / per_tile);
             take = std::min<uint64_t>(take, r->total_tasks - r->next_task);
-            in.prefix_base = 0;
+            in.prefix_base = r->prefix_base;
             in.task_lo = r->next_task;
             in.n_tiles = take;
             r->next_task += take;
+            if (r->sym && r->next_task == r->total_tasks) mirror.push_back((int)large.size());
             used += per_tile * (double)take;
             large.push_back(in);
             large_r.push_back(r);
@@ -254,6 +259,7 @@ static bool issue_step_locked(isg_server* s) {
     }
     bp.inst = desc;
     bp.n_tiles = tiles;
+    bp.mirror_ids = mirror;                            // large descriptors come first: same indices
     bp.prog_words = (max_words + 1) & ~1;
     bp.slot_words = (bp.prog_words + (max_bins + 1) / 2 + 1) & ~1;   // even: slots stay 16-byte aligned
     bp.threads = s->opt.block_threads > 0 ? std::min(512, s->opt.block_threads) : 512;
@@ -266,12 +272,15 @@ static bool issue_step_locked(isg_server* s) {
         bp.smem = (size_t)bp.slot_words * 8 * bp.warps_per_cta;
     }
     std::memcpy(s->desc_host[buf], desc.data(), sizeof(BatchInst) * desc.size());
-    if (!bp.small_ids.empty()) std::memcpy(s->small_host[buf], bp.small_ids.data(), sizeof(int) * bp.small_ids.size());
+    // the kernels read the small kernel's ids, then the mirror's (at most one id per request)
+    std::vector<int> ids(bp.small_ids);
+    ids.insert(ids.end(), bp.mirror_ids.begin(), bp.mirror_ids.end());
+    if (!ids.empty()) std::memcpy(s->small_host[buf], ids.data(), sizeof(int) * ids.size());
     server_fail_cuda(cudaEventRecord(s->ev_start[buf], s->stream), "cudaEventRecord");
     server_fail_cuda(cudaMemcpyAsync(s->desc_dev[buf], s->desc_host[buf], sizeof(BatchInst) * desc.size(),
                                      cudaMemcpyHostToDevice, s->stream), "cudaMemcpyAsync(descriptors)");
-    if (!bp.small_ids.empty())
-        server_fail_cuda(cudaMemcpyAsync(s->small_dev[buf], s->small_host[buf], sizeof(int) * bp.small_ids.size(),
+    if (!ids.empty())
+        server_fail_cuda(cudaMemcpyAsync(s->small_dev[buf], s->small_host[buf], sizeof(int) * ids.size(),
                                          cudaMemcpyHostToDevice, s->stream), "cudaMemcpyAsync(small ids)");
     server_fail_cuda(cudaMemsetAsync(s->ctr_dev[buf], 0, 16, s->stream), "cudaMemsetAsync(counter)");
     unsigned int* status = reinterpret_cast<unsigned int*>(s->ctr_dev[buf] + 1);
@@ -441,6 +450,7 @@ void isg_server_options_init(isg_server_options* o) {
     o->arena_bytes = (int64_t)64 << 20;
     o->step_ms = 20.0;
     o->split_work_ratio = 0.0;
+    o->symmetry = 0;
 }
 
 isg_status isg_server_create(const isg_server_options* opt, isg_server** out) {
@@ -460,6 +470,7 @@ isg_status isg_server_create(const isg_server_options* opt, isg_server** out) {
         if (o.arena_bytes < (1 << 20)) fail(ISG_ERR_INVALID, "arena_bytes must be at least 1 MiB");
         if (!(o.step_ms > 0)) fail(ISG_ERR_INVALID, "step_ms must be > 0");
         if (!(o.split_work_ratio >= 0 && o.split_work_ratio <= 1)) fail(ISG_ERR_INVALID, "split_work_ratio must lie in [0, 1]");
+        if (o.symmetry != 0 && o.symmetry != 1) fail(ISG_ERR_INVALID, "symmetry must be 0 or 1");
         isg_server* s = new isg_server();
         s->opt = o;
         s->t_create = Clock::now();
@@ -533,12 +544,20 @@ isg_status isg_server_submit(isg_server* s, const isg_graph* g, int64_t* ticket)
         if (r->split) {
             // planned above
         } else if (g->n >= kMaxLow + 5) {
-            o.inner_bits = std::min(16, g->n - 5);
+            // with symmetry, from 13 spins: the shard with spin N-1 up (12 or more free spins)
+            r->sym = s->opt.symmetry && g->n >= kMaxLow + 6;
+            if (r->sym) {
+                o.shard_bits = 1;
+                o.shard_lo = 1;
+                o.shard_hi = 2;
+            }
+            o.inner_bits = std::min(16, g->n - 5 - (r->sym ? 1 : 0));
             p = make_plan(*g, o, d);
             if (p.small || p.q < p.b) fail(ISG_ERR_INTERNAL, "unexpected plan for a served graph");
             r->b = p.b;
             r->q = p.q;
             r->total_tasks = p.n_tasks;
+            r->prefix_base = p.prefix_base;
         } else {
             p = make_plan(*g, o, d);
             p.small = true;
@@ -552,7 +571,7 @@ isg_status isg_server_submit(isg_server* s, const isg_graph* g, int64_t* ticket)
         if (!r->split) {
             r->blob = build_program(*g, p);
             r->bins = (int)(g->n_e_c * (p.stride > 0 ? p.stride : g->n + 1));
-            r->configs = (double)(1ull << g->n);
+            r->configs = std::ldexp(1.0, r->sym ? g->n - 1 : g->n);   // configurations enumerated
         }
         const size_t need = ((r->table_words * 8 + 255) & ~(size_t)255) + r->blob.size() * 8;
         if (need > (size_t)s->opt.arena_bytes) fail(ISG_ERR_TOO_LARGE, "request does not fit the server's table arena");

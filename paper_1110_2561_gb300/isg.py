@@ -355,7 +355,7 @@ class isg_server_options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("max_spins", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
                 ("max_queued", ctypes.c_int32), ("arena_bytes", ctypes.c_int64), ("step_ms", ctypes.c_double),
                 ("block_threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("split_work_ratio", ctypes.c_double)]
+                ("split_work_ratio", ctypes.c_double), ("symmetry", ctypes.c_int32)]
 
 
 class Server:

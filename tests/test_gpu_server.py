@@ -58,6 +58,28 @@ def test_mix_with_split_equals_alone(isg, cuda):
     srv.close()
 
 
+def test_mix_with_symmetry_equals_alone(isg, cuda):
+    """With symmetry = 1 the server enumerates only the configurations with spin N-1 up of every
+    tile-served request of 13 or more spins and mirrors the table in the step that carries its last
+    tile: every table equals isg_enumerate alone (all 2^N configurations), the small ones equal the
+    oracle, and the server counts about half the configurations enumerated."""
+    reqs = w.serving_stream(40, n_range=(10, 30), seed=13)
+    srv = isg.Server(step_ms=5.0, symmetry=1)
+    tickets = [(srv.submit(isg.isg_graph_create(r.lattice.n, r.lattice.edges)), r.lattice) for r in reqs]
+    for t, lat in tickets:
+        srv.wait(t, 60000)
+        g, _ = srv.result(t)
+        assert np.array_equal(g, alone(isg, lat)), lat.name
+        if lat.n <= 20:
+            assert np.array_equal(g, oracle.g_masks(lat.n, lat.edges, threads=THREADS)), lat.name
+    st = srv.stats()
+    full = sum(1 << lat.n for _, lat in tickets)
+    assert st["configs"] < 0.6 * full
+    srv.close()
+    with pytest.raises(isg.IsgError):
+        isg.Server(symmetry=2)
+
+
 def test_server_rejects_bad_split_ratio(isg, cuda):
     with pytest.raises(isg.IsgError, match="INVALID"):
         isg.Server(split_work_ratio=1.5)
