@@ -359,7 +359,10 @@ class isg_server_options(ctypes.Structure):
 
 
 class Server:
-    """isg_server_*: a continuously batching request server on the current device."""
+    """isg_server_*: a continuously batching request server on the current device.
+
+    options: fields of isg_server_options (max_spins, max_inflight, max_queued, arena_bytes,
+    step_ms, block_threads, ctas_per_sm, split_work_ratio, symmetry)."""
 
     def __init__(self, **options):
         o = isg_server_options()
