@@ -80,6 +80,20 @@ def test_mix_with_symmetry_equals_alone(isg, cuda):
         isg.Server(symmetry=2)
 
 
+def test_mix_with_split_and_symmetry_equals_alone(isg, cuda):
+    """Both options at once (split_work_ratio = 0.5, symmetry = 1): large requests by split launches,
+    the other tile-served ones halved and mirrored, in shared steps. Every table equals
+    isg_enumerate alone."""
+    reqs = w.serving_stream(32, n_range=(14, 34), seed=17)
+    srv = isg.Server(step_ms=5.0, split_work_ratio=0.5, symmetry=1)
+    tickets = [(srv.submit(isg.isg_graph_create(r.lattice.n, r.lattice.edges)), r.lattice) for r in reqs]
+    for t, lat in tickets:
+        srv.wait(t, 120000)
+        g, _ = srv.result(t)
+        assert np.array_equal(g, alone(isg, lat)), lat.name
+    srv.close()
+
+
 def test_server_rejects_bad_split_ratio(isg, cuda):
     with pytest.raises(isg.IsgError, match="INVALID"):
         isg.Server(split_work_ratio=1.5)

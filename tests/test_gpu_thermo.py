@@ -173,6 +173,30 @@ def test_fp64_torus_8x8_clusters(isg, cuda):
             assert rel_close(a, b, 1e-12, 1e-12 * lat.n), (k, len(T), len(h))
 
 
+def test_fp32_torus_8x8_within_bounds(isg, cuda):
+    """FP32 against FP64 on the largest table (8x8 torus, 129 x 65 bins, from split-and-convolve)
+    on a clustered grid (40 T) and an unclustered one (200 T), few and many fields, within the
+    stated bounds: |d ln Z| <= 2e-5, |d<E>| <= 1e-5 (S + N |h|max), |d<M>| <= 1e-5 N, C and chi
+    within 1e-3 relative or 1e-3 of the grid maximum."""
+    import torch
+    lat = w.square(8, 8, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=cuda)
+    isg.isg_enumerate_split(gh, g)
+    S, N = 128, 64
+    for T in (np.linspace(1.0, 6, 40), np.linspace(0.5, 8, 200)):
+        for h in (np.array([0.0, 0.2]), np.linspace(-1, 1, 64)):
+            d = isg.isg_thermo(g, gh, T, h, isg.ISG_FP64)
+            f = isg.isg_thermo(g, gh, T, h, isg.ISG_FP32)
+            hmax = float(np.max(np.abs(h)))
+            assert np.max(np.abs(f[0] - d[0])) <= 2e-5
+            assert np.max(np.abs(f[1] - d[1])) <= 1e-5 * (S + N * hmax)
+            assert np.max(np.abs(f[2] - d[2])) <= 1e-5 * N
+            for k in (3, 4):
+                scale = np.max(np.abs(d[k]))
+                assert np.all(np.abs(f[k] - d[k]) <= np.maximum(1e-3 * np.abs(d[k]), 1e-3 * scale)), (k, len(T), len(h))
+
+
 def test_thermo_device_outputs(isg, cuda):
     import torch
     lat = w.square(4, 4, True)
