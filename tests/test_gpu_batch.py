@@ -58,6 +58,25 @@ def test_batch_symmetry(isg, cuda):
     b.close()
 
 
+def test_batch_split_and_symmetry(isg, cuda):
+    """split = 1 and symmetry = 1 at once on a mixed batch (EA 5x6 instances that go to split
+    launches, smaller tile-served and small-kernel graphs): every table equals the per-instance
+    enumeration, and replaying the prepared batch gives the same tables."""
+    lats = [l for l in w.ea_instances(64) if l.n == 30][:6] + mixed_graphs()
+    hs = [isg.isg_graph_create(l.n, l.edges) for l in lats]
+    ref = [isg.isg_enumerate(h) for h in hs]
+    outs = isg.isg_enumerate_batch(hs, split=1, symmetry=1)
+    for l, g, r in zip(lats, outs, ref):
+        assert np.array_equal(g, r), l.name
+    b = isg.Batch(hs, split=1, symmetry=1)
+    for _ in range(2):
+        b.run()
+        b.status()
+        for k, l in enumerate(lats):
+            assert np.array_equal(b.table(k).cpu().numpy(), ref[k]), l.name
+    b.close()
+
+
 def test_batch_rejects_shards(isg, cuda):
     h = isg.isg_graph_create(16, w.square(4, 4, True).edges)
     with pytest.raises(isg.IsgError) as ei:
