@@ -442,8 +442,9 @@ extern "C" isg_status isg_enumerate(const isg_graph* graph, void* stream, int64_
         const bool sym = o.symmetry != 0;
         if (sym) { o.shard_bits = 1; o.shard_lo = 1; o.shard_hi = 2; }      // spin N-1 up only
         const DeviceInfo d = device_info();
-        const Plan p = make_plan(*graph, o, d);
-        const std::vector<uint64_t> blob = build_program(*graph, p);
+        const std::shared_ptr<const PlannedProgram> pp = planned_program(*graph, o, d);
+        const Plan& p = pp->plan;
+        const std::vector<uint64_t>& blob = pp->blob;
         const size_t table_bytes = sizeof(int64_t) * (size_t)public_bins(*graph);
         const size_t blob_bytes = blob.size() * 8;
         // scratch: [counter 8][status 8][blob][table: host mode or symmetry half]

@@ -270,6 +270,23 @@ std::vector<uint64_t> build_program(const isg_graph& g, const Plan& p) {
     return blob;
 }
 
+std::shared_ptr<const PlannedProgram> planned_program(const isg_graph& g, const isg_options& o, const DeviceInfo& d) {
+    std::string key(reinterpret_cast<const char*>(&o), sizeof o);   // padding bytes can only cause misses
+    key.append(reinterpret_cast<const char*>(&d), sizeof d);
+    {
+        std::lock_guard<std::mutex> lk(g.plan_mu);
+        for (const auto& e : g.plan_cache)
+            if (e.first == key) return e.second;
+    }
+    auto pp = std::make_shared<PlannedProgram>();
+    pp->plan = make_plan(g, o, d);
+    pp->blob = build_program(g, pp->plan);
+    std::lock_guard<std::mutex> lk(g.plan_mu);
+    if (g.plan_cache.size() >= 8) g.plan_cache.erase(g.plan_cache.begin());
+    g.plan_cache.emplace_back(std::move(key), pp);
+    return pp;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Host emulation of the kernels (same lane walk, bounds-checked counting)
 // ---------------------------------------------------------------------------------------------

@@ -1,13 +1,20 @@
 // isg_internal.h -- host-side model shared by the library's translation units.
 #pragma once
 #include <cstdint>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/isg.h"
 #include "../../include/isg_debug.h"
 #include "enum_core.cuh"
+
+namespace isg {
+struct PlannedProgram;
+}
 
 struct isg_graph {
     int n = 0;
@@ -20,6 +27,11 @@ struct isg_graph {
     int64_t e_lo = 0;                       // smallest reachable-class energy >= -S
     int64_t n_e_c = 1;                      // compact energy bins
     std::vector<int> degree;                // distinct neighbours per spin
+    // Plans and programs of recent isg_enumerate calls, keyed by the resolved options and the
+    // device shape (planned_program): planning costs microseconds that latency-bound calls of one
+    // graph would otherwise pay on every call.
+    mutable std::mutex plan_mu;
+    mutable std::vector<std::pair<std::string, std::shared_ptr<const isg::PlannedProgram>>> plan_cache;
 };
 
 namespace isg {
@@ -95,6 +107,16 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d);
 
 // Build the program blob (64-bit words) of graph g for a plan: spins in internal order.
 std::vector<uint64_t> build_program(const isg_graph& g, const Plan& p);
+
+// A plan and its program.
+struct PlannedProgram {
+    Plan plan;
+    std::vector<uint64_t> blob;
+};
+
+// make_plan and build_program for (g, o, d), from the graph's cache of recent calls when the same
+// options and device shape were planned before. Thread-safe.
+std::shared_ptr<const PlannedProgram> planned_program(const isg_graph& g, const isg_options& o, const DeviceInfo& d);
 
 // Map bin i = e' * stride + m of the internal histogram to the public table index (-1 for the
 // padding columns m > N, which are never counted).
