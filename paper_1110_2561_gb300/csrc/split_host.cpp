@@ -324,9 +324,11 @@ SplitPlan plan_split(const isg_graph& g, uint64_t boundary, bool require_gain) {
         }
         if (!std::isfinite(best.cost)) fail(ISG_ERR_TOO_LARGE, "no boundary set gives components of at most 30 spins that fit");
         structural_boundary(g, n_cls, best.S);
-        if (require_gain && best.cost >= std::ldexp(kDirectWarpInstrPerConfig, n))
-            fail(ISG_ERR_TOO_LARGE, "no boundary set makes the split cheaper than the full enumeration for this graph");
     }
+    // searched or known from a graph of the same structure (planned before without the gain
+    // requirement): either way a boundary that does not beat the full enumeration is refused
+    if (!boundary && require_gain && best.cost >= std::ldexp(kDirectWarpInstrPerConfig, n))
+        fail(ISG_ERR_TOO_LARGE, "no boundary set makes the split cheaper than the full enumeration for this graph");
     SplitPlan p;
     p.boundary = best.S;
     for (int i = 0; i < n; ++i) if ((best.S >> i) & 1) p.S.push_back(i);
