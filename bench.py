@@ -7,8 +7,11 @@ on 256 temperatures in [0.5, 5] at h = 0 in FP64 (Eq. 2). Inputs are synthetic a
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the launching
 stream, an L2 flush (a 256 MiB write) between steps outside the events, a barrier and
 synchronisation around the timed region, max over ranks. Under torchrun every rank runs the
-same workload on its own GPU (replicas; the method's shards need no exchange), so `value` is
-the configurations of all ranks per second of the slowest rank.
+same workload on its own GPU (replicas, weak scaling), so `value` is the configurations of all
+ranks per second of the slowest rank. With --shard the ranks share the one torus instead
+(strong scaling): each step, every rank enumerates its share of the 2^36 configurations
+(isg_enumerate_rank), one NCCL all-reduce sums the int64 tables, and every rank runs the
+thermodynamics on the summed table; `value` is 2^36 per second of the slowest rank.
 
 `--impl reference` runs the CPU oracle (oracle/, plain C, all host cores) on a bounded sample of
 the same workload and reports the same metric, extrapolated from the sample to a full step.
@@ -161,11 +164,18 @@ def run_isg(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     peaks = isg.isg_probe_peaks(stream)
+    sharded = args.shard and world > 1
+    if args.shard and shard:
+        raise SystemExit("--shard and --shard-bits exclude each other")
 
     def step(ev=None):
         if ev:
             ev[0].record(stream)
-        isg.isg_enumerate(gh, g, stream, autotune=1, **shard)
+        if sharded:
+            isg.isg_enumerate_rank(gh, rank, world, g, stream, autotune=1)
+            dist.all_reduce(g, op=dist.ReduceOp.SUM)
+        else:
+            isg.isg_enumerate(gh, g, stream, autotune=1, **shard)
         if ev:
             ev[1].record(stream)
         isg.isg_thermo(g, gh, T_GRID, H_GRID, isg.ISG_FP64, stream, out=outs)
@@ -213,7 +223,13 @@ def run_isg(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        gh_host = isg.isg_enumerate(gh, None, stream, autotune=1, **shard)  # host table: D2H inside
+        if sharded:                                   # host share, summed over the ranks through the GPUs
+            part = isg.isg_enumerate_rank(gh, rank, world, None, stream, autotune=1)
+            t = torch.from_numpy(part).to(dev)
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+            gh_host = t.cpu().numpy()
+        else:
+            gh_host = isg.isg_enumerate(gh, None, stream, autotune=1, **shard)  # host table: D2H inside
         isg.isg_thermo(gh_host, gh, T_GRID, H_GRID, isg.ISG_FP64, stream)  # host g: H2D inside, host outputs
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if world > 1:
@@ -222,35 +238,39 @@ def run_isg(args):
         e2e_s = float(t.item())
     assert np.array_equal(gh_host, gc)
 
+    isg.isg_device_status(stream)                     # the kernels' self-check of every device-output step
     clocks = clk.summary()
     if rank == 0:
         ms_per_step = total_ms / args.steps
-        value = world * n_configs / (ms_per_step * 1e-3)
-        enum_s = statistics.mean(enum_ms) * 1e-3
+        ranks_counted = 1 if sharded else world      # replicas: every rank its own torus
+        value = ranks_counted * n_configs / (ms_per_step * 1e-3)
+        enum_s = statistics.mean(enum_ms) * 1e-3     # with --shard: this rank's share plus the all-reduce
+        rank_configs = n_configs // world if sharded else n_configs   # enumerated by one rank per step
         sm_max = clocks.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or SM_MAX_MHZ_FALLBACK
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         alu_peak = sms * 4 * 32 * sm_max * 1e6                     # 4 schedulers x 32 lanes per SM per clock
         red_peak = sms * 32 * sm_max * 1e6                         # one 32-lane shared reduction per SM per clock
-        achieved_ops = OPS_PER_CONFIG * n_configs / enum_s
-        traffic = TRAFFIC_BYTES if TRAFFIC_SOURCES_SHA == kernel_sources_sha() else None
+        achieved_ops = OPS_PER_CONFIG * rank_configs / enum_s
+        traffic = TRAFFIC_BYTES if TRAFFIC_SOURCES_SHA == kernel_sources_sha() and not sharded else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": WORKLOAD if not shard else f"shard 0 of 2^{args.shard_bits} of: " + WORKLOAD,
-                       "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"shard{world}" if sharded else f"replicas{world}",
+                       "l2": "flushed between steps (256 MiB write)",
                        "plan": {k: plan[k] for k in ("q", "b", "tasks", "threads", "copies", "ctas_per_sm", "G",
                                                      "n_e_compact", "stride")},
                        "autotuned": tuned_fields},
             # the binding unit: one shared-memory reduction per configuration; the shared-memory
             # pipe executes one warp-wide (32-lane) reduction per clock per SM
-            "roofline": {"bound": "smem_atomic", "achieved": n_configs / enum_s / 1e9,
-                         "peak": red_peak / 1e9, "unit": "Gred/s", "frac": n_configs / enum_s / red_peak,
+            "roofline": {"bound": "smem_atomic", "achieved": rank_configs / enum_s / 1e9,
+                         "peak": red_peak / 1e9, "unit": "Gred/s", "frac": rank_configs / enum_s / red_peak,
                          "traffic": traffic, "kernel": f"enumerate_kernel<{plan['b']}>",
                          "work_per_config": "1 red.shared.add.u32 (plus 1 integer add)",
                          "peak_source": f"{sms} SMs x 32 lanes/clk x {sm_max:.0f} MHz (unit counts and clock)",
                          "peak_measured": peaks["red_conflict_free"] / 1e9,
-                         "frac_of_measured": n_configs / enum_s / peaks["red_conflict_free"],
+                         "frac_of_measured": rank_configs / enum_s / peaks["red_conflict_free"],
                          "peak_measured_scattered": peaks["red_scattered"] / 1e9,
                          "match_any_aggregated": peaks["match_aggregated"] / 1e9,
                          "peak_measured_source": "isg_probe_peaks (red.shared.add.u32, measured in this run)"},
@@ -259,7 +279,7 @@ def run_isg(args):
                              "peak_source": f"{sms} SMs x 128 lanes/clk x {sm_max:.0f} MHz (unit counts and clock)"},
             "enumerate_ms": statistics.mean(enum_ms), "thermo_ms": statistics.mean(
                 [b.elapsed_time(c) for a, b, c in evs]),
-            "e2e": {"value": world * n_configs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "e2e": {"value": ranks_counted * n_configs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": 3 * args.steps * world,          # this library's kernels, all ranks
             "clocks": clocks,
@@ -476,10 +496,11 @@ def extra_measurements(stream, dev):
                                 "grid": "512 T in [0.5,8] x 256 h in [-2,2]", "fp64_ms": t64, "fp32_ms": t32,
                                 "fp32_speedup": t64 / t32, "magnetisation_fp64_ms": tm64,
                                 "magnetisation_fp32_ms": tm32, "fp32_vs_fp64": err}
-    # a short request stream, enumerating every configuration and with split-and-convolve service
-    out["serving_200_requests"] = {"every_configuration": serve_stream(200, 50.0, 20.0, 0.0),
-                                   "symmetry_halving": serve_stream(200, 50.0, 20.0, 0.0, 1),
-                                   "split_work_ratio_0.25": serve_stream(200, 50.0, 20.0, 0.25)}
+    # the request stream: 2000 requests enumerating every configuration (the serving workload's
+    # count), and shorter streams of the same seed with symmetry halving and split service
+    out["serving"] = {"every_configuration_2000": serve_stream(2000, 50.0, 20.0, 0.0),
+                      "symmetry_halving_200": serve_stream(200, 50.0, 20.0, 0.0, 1),
+                      "split_work_ratio_0.25_200": serve_stream(200, 50.0, 20.0, 0.25)}
     return out
 
 
@@ -791,6 +812,8 @@ def main():
                     help="serving: serve requests whose split-and-convolve work is below this fraction by split launches")
     ap.add_argument("--symmetry", type=int, choices=(0, 1), default=0,
                     help="serving: enumerate each tile-served request's half with spin N-1 up and mirror it")
+    ap.add_argument("--shard", action="store_true",
+                    help="under torchrun: the ranks share the one torus (strong scaling, NCCL all-reduce per step)")
     ap.add_argument("--shard-bits", type=int, default=0,
                     help="profiling case: enumerate only shard 0 of 2^k per step (not a benchmark line)")
     args = ap.parse_args()

@@ -130,12 +130,53 @@ ISG_API isg_status isg_graph_size(const isg_graph* graph, int32_t* n_spins, int3
  * (Sec. 2: the degeneracy of M over E; Sec. 3: every configuration is visited).
  * g_out: n_e * n_m int64 (isg_graph_bins), on the device if g_out_on_device != 0 (the call then
  * only enqueues on stream) or on the host (the call synchronises stream). opt may be NULL.
+ * Self-check: every walk recomputes its last bin from scratch and compares it with the bin it
+ * tracked. A host-output call reports a mismatch as ISG_ERR_INTERNAL; a device-output call
+ * records it in the device's self-check word, which isg_device_status reports.
  * Errors: ISG_ERR_INVALID, ISG_ERR_TOO_LARGE (N > max_spins, or the table does not fit the
- * shared-memory histogram), ISG_ERR_NOMEM, ISG_ERR_CUDA, ISG_ERR_INTERNAL (host-buffer calls
- * only: a kernel self-check failed).
+ * shared-memory histogram), ISG_ERR_NOMEM, ISG_ERR_CUDA, ISG_ERR_INTERNAL (host output only).
  */
 ISG_API isg_status isg_enumerate(const isg_graph* graph, void* stream, int64_t* g_out, int32_t g_out_on_device,
                          const isg_options* opt);
+
+/*
+ * One graph over several ranks (processes, one GPU each), as the paper splits the outer loops of
+ * the enumeration over MPI processes and gathers the results at the root (Sec. 3d): the 2^N
+ * configurations are cut into 2^k shards of consecutive words (the top k spins fixed, as
+ * opt->shard_bits), and rank r of W takes the contiguous run [r 2^k / W, (r + 1) 2^k / W) (integer
+ * division). k = log2 W when W is a power of two, else ceil(log2 W) + 6 (shares within one shard
+ * in 64 of each other), at most N (at most N - 1 with symmetry; ranks beyond the shard count get
+ * an empty share). With symmetry the shards are those of the half with spin N-1 up.
+ * isg_rank_shards: the shard_bits and range [*shard_lo, *shard_hi) of rank `rank` (host only; any
+ * output may be NULL). Errors: ISG_ERR_INVALID (N outside [1, 64], world_size outside [1, 2^20],
+ * rank outside [0, world_size)).
+ */
+ISG_API isg_status isg_rank_shards(int32_t n_spins, int32_t rank, int32_t world_size, int32_t symmetry,
+                                   int32_t* shard_bits, int64_t* shard_lo, int64_t* shard_hi);
+
+/*
+ * Rank `rank`'s share of g (see isg_rank_shards): the counts of its configurations, so the sum of
+ * the W ranks' tables (one int64 all-reduce of n_e * n_m values) is the exact table. With
+ * opt->symmetry each rank enumerates its shards of the spin-(N-1)-up half and adds their mirror
+ * M -> -M (the mirror is linear, so the sum over ranks is again the whole table). A rank with an
+ * empty share writes zeros (adds nothing with accumulate). g_out, placement, synchronisation,
+ * self-check and errors as isg_enumerate; opt's shard fields must be 0.
+ */
+ISG_API isg_status isg_enumerate_rank(const isg_graph* graph, void* stream, int64_t* g_out, int32_t g_out_on_device,
+                                      int32_t rank, int32_t world_size, const isg_options* opt);
+
+/*
+ * The kernels' self-check of the device-output calls (isg_enumerate, isg_enumerate_rank,
+ * isg_enumerate_noalloc and isg_enumerate_split with their table on the device), which return before their kernels run:
+ * each such kernel ORs a failed check into one self-check word per device, shared by all streams
+ * and calls on that device. This call synchronises stream, reads the current device's word and,
+ * if clear != 0, resets it to zero (ordered on stream after the read). It returns ISG_ERR_INTERNAL
+ * (the message names the failed check) if the word was nonzero: some device-output call on this
+ * device since the last clear produced a table that is not valid; the word does not say which.
+ * Synchronise the streams of the calls to be covered before calling (or pass their stream).
+ * Makes no allocation. Errors: ISG_ERR_INTERNAL, ISG_ERR_CUDA.
+ */
+ISG_API isg_status isg_device_status(void* stream, int32_t clear);
 
 /*
  * Enumerate n_graphs independent graphs (for example disorder realisations) in one persistent
@@ -214,10 +255,12 @@ ISG_API isg_status isg_autotune(const isg_graph* graph, void* stream, const isg_
  * S at most 40, at most 16 distinct couplings, and the per-warp buffers (two (sum S_c + 2) x
  * (sum |C| + 1) accumulators) must fit in shared memory with the (S + 1)(N + 1) int64 table.
  * g_out: n_e * n_m int64 (isg_graph_bins), on the device if g_out_on_device (only enqueued) or on
- * the host (synchronises stream). The output is overwritten.
+ * the host (synchronises stream). The output is overwritten. A failed walk self-check is reported
+ * as ISG_ERR_INTERNAL by a host-output call, and recorded for isg_device_status by a device-output
+ * call.
  * Errors: ISG_ERR_INVALID (NULL, mask beyond N), ISG_ERR_TOO_LARGE (no admissible boundary, or
  * none cheaper than the full enumeration when boundary = 0), ISG_ERR_NOMEM, ISG_ERR_CUDA,
- * ISG_ERR_INTERNAL (a walk's self-check failed; host output only).
+ * ISG_ERR_INTERNAL (host output only).
  */
 ISG_API isg_status isg_enumerate_split(const isg_graph* graph, void* stream, int64_t* g_out, int32_t g_out_on_device,
                                        uint64_t boundary);
@@ -253,9 +296,13 @@ ISG_API isg_status isg_split_plan(const isg_graph* graph, uint64_t boundary, uin
  * of the graph program live in one 16 KiB array of device memory inside the library, which
  * every GPU that loads the library keeps until the process exits.
  * g_out_device: n_e * n_m int64 on the current device (isg_graph_bins); the call only enqueues
- * work on stream. opt as for isg_enumerate (NULL = defaults).
- * The first call on each device looks up that device's address of the array (with the device
- * current); make that first call before any stream capture. All calls share the array and it
+ * work on stream. opt as for isg_enumerate (NULL = defaults), except that symmetry is ignored and
+ * autotune only applies a choice already cached for this graph on this device by isg_autotune or
+ * an isg_enumerate call with autotune (timing candidates would allocate); without one the
+ * planner's defaults are used. The kernels' self-check goes to the device's self-check word:
+ * read it with isg_device_status after the stream has run the call.
+ * The first call on each device looks up that device's addresses of the array and of the
+ * self-check word (with the device current); make that first call before any stream capture. All calls share the array and it
  * keeps the last call's contents (each call clears the counter and status words it needs), so
  * calls whose work overlaps on the GPU (different streams, or different host threads) race and
  * give wrong tables: issue them on one stream.

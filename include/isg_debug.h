@@ -32,6 +32,29 @@ ISG_API isg_status isg_debug_plan(const isg_graph* graph, const isg_options* opt
 ISG_API isg_status isg_debug_emulate(const isg_graph* graph, const isg_options* opt, int64_t* g_out);
 
 /*
+ * isg_enumerate_rank's work for rank `rank` of `world_size` run on the host by the same walk as
+ * isg_debug_emulate (shards, symmetry half and mirror as there), into a host table. For small N
+ * only. Errors as isg_enumerate_rank and isg_debug_emulate.
+ */
+ISG_API isg_status isg_debug_emulate_rank(const isg_graph* graph, int32_t rank, int32_t world_size, const isg_options* opt,
+                                          int64_t* g_out);
+
+/*
+ * isg_debug_emulate with a mistake planted in the program first: delta is added to the field
+ * constant (the spin's sum of |J|) in the site record at internal position `site`, as a wrong
+ * program entry would. *word (may be NULL) receives the self-check word the walk produced (bit 0:
+ * a walk's tracked bin differed from its recomputation; bit 1: an address left the histogram);
+ * the return value is the status the library reports for that word (ISG_ERR_INTERNAL when
+ * nonzero, with the message that isg_device_status and the host-output calls give). The check
+ * compares each walk's last bin only, so it sees a mistake whose effects do not cancel over the
+ * walk: one in the spin at the top inner position (site = q - 1, flipped once per walk) always
+ * shows; the reflected Gray order undoes most others in pairs. The graph must take the Gray-walk
+ * kernel (at least 11 free spins, or forced inner_bits / low_bits); site < N.
+ */
+ISG_API isg_status isg_debug_emulate_planted(const isg_graph* graph, const isg_options* opt, int32_t site, int32_t delta,
+                                             int64_t* g_out, uint32_t* word);
+
+/*
  * Run the split kernel's per-warp work (isg_enumerate_split with the same boundary argument) on
  * the host, lane by lane, with every histogram, accumulator and table index checked, and write g
  * (host buffer, isg_graph_bins geometry). For small boundary sets and components only. Returns
@@ -50,6 +73,16 @@ ISG_API isg_status isg_debug_emulate_split(const isg_graph* graph, uint64_t boun
  */
 ISG_API isg_status isg_probe_peaks(void* stream, double* red_conflict_free, double* red_scattered, double* alu,
                                    double* match_aggregated);
+
+/*
+ * Host-side failure injection for tests of the request server's error handling (no GPU fault is
+ * made): where = 1 makes the server's next engine step fail on the host before its first enqueue,
+ * where = 2 after its kernels were enqueued (the server then drains its stream before failing the
+ * requests), 0 cancels a pending injection. The step fails like a failing CUDA call would: the
+ * admitted requests with tiles left report ISG_ERR_CUDA, their arena slots are released once no
+ * step in flight writes into them, and the server keeps serving. Errors: ISG_ERR_INVALID.
+ */
+ISG_API isg_status isg_debug_server_inject(isg_server* server, int32_t where);
 
 #ifdef __cplusplus
 }

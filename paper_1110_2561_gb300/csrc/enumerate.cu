@@ -158,9 +158,28 @@ __global__ void mirror_kernel(const int64_t* half, int64_t* out, int n_e, int n_
     }
 }
 
+// Self-check word of the device-output calls on this device: kernels OR a failed check into it
+// (atomicOr, so calls on any stream may share it); isg_device_status reads and clears it.
+static __device__ unsigned int g_device_status;
+
 // ---------------------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------------------
+unsigned int* device_status_word() {
+    static std::mutex mu;
+    static std::vector<unsigned int*> addr;
+    int dev = 0;
+    ISG_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)addr.size() <= dev) addr.resize(dev + 1, nullptr);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        ISG_CUDA(cudaGetSymbolAddress(&p, g_device_status));
+        addr[dev] = static_cast<unsigned int*>(p);
+    }
+    return addr[dev];
+}
+
 void* scratch_alloc(size_t bytes, void* stream) {
     static std::mutex mu;
     static std::vector<cudaMemPool_t> pools;
@@ -394,6 +413,22 @@ static TunedShape run_autotune(const isg_graph& g, const isg_options& base, cuda
     return best;
 }
 
+static void fill_tuned(isg_options& o, const TunedShape& t) {
+    if (!o.stride_residue && !o.bin_stride) o.stride_residue = t.stride_residue;
+    if (!o.block_threads) o.block_threads = t.block_threads;
+    if (!o.ctas_per_sm) o.ctas_per_sm = t.ctas_per_sm;
+}
+
+bool apply_cached_autotune(const isg_graph& g, isg_options& o) {
+    int dev = 0;
+    ISG_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const auto it = g_tune_cache.find(std::pair<int, uint64_t>(dev, graph_signature(g)));
+    if (it == g_tune_cache.end()) return false;
+    fill_tuned(o, it->second);
+    return true;
+}
+
 // Fill the unset planning fields of o from the cache (tuning on a miss).
 static void apply_autotune(const isg_graph& g, isg_options& o, cudaStream_t s) {
     int dev = 0;
@@ -411,9 +446,7 @@ static void apply_autotune(const isg_graph& g, isg_options& o, cudaStream_t s) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = t;
     }
-    if (!o.stride_residue && !o.bin_stride) o.stride_residue = t.stride_residue;
-    if (!o.block_threads) o.block_threads = t.block_threads;
-    if (!o.ctas_per_sm) o.ctas_per_sm = t.ctas_per_sm;
+    fill_tuned(o, t);
 }
 
 }  // namespace isg
@@ -431,6 +464,61 @@ extern "C" isg_status isg_autotune(const isg_graph* graph, void* stream, const i
     });
 }
 
+namespace isg {
+
+// Enumerate the shard range of o (planning fields resolved) into g_out; with `mirror` the range
+// holds only configurations with spin N-1 up and the counts are completed by the M -> -M mirror
+// (a global flip keeps E and negates M). Device output only enqueues; host output synchronises
+// and checks the kernels' self-check word.
+static void enumerate_range(const isg_graph& graph, cudaStream_t s, int64_t* g_out, bool g_out_on_device,
+                            const isg_options& o, bool mirror) {
+    const DeviceInfo d = device_info();
+    const std::shared_ptr<const PlannedProgram> pp = planned_program(graph, o, d);
+    const Plan& p = pp->plan;
+    const std::vector<uint64_t>& blob = pp->blob;
+    const size_t table_bytes = sizeof(int64_t) * (size_t)public_bins(graph);
+    const size_t blob_bytes = blob.size() * 8;
+    // scratch: [counter 8][status 8][blob][table: host mode or symmetry half]
+    const size_t off_blob = 16, off_table = (off_blob + blob_bytes + 255) & ~(size_t)255;
+    const bool own_table = !g_out_on_device || mirror;
+    const size_t scratch_bytes = off_table + (own_table ? table_bytes : 0) + (mirror && !g_out_on_device ? table_bytes : 0);
+    char* scratch = static_cast<char*>(scratch_alloc(scratch_bytes, s));
+    struct Free {
+        char* p; cudaStream_t s;
+        ~Free() { if (p) cudaFreeAsync(p, s); }
+    } guard{scratch, s};
+    ISG_CUDA(cudaMemsetAsync(scratch, 0, 16, s));
+    const bool inl = program_fits_inline(blob.size());
+    if (!inl) ISG_CUDA(cudaMemcpyAsync(scratch + off_blob, blob.data(), blob_bytes, cudaMemcpyHostToDevice, s));
+    int64_t* table = own_table ? reinterpret_cast<int64_t*>(scratch + off_table) : g_out;
+    if (own_table || !o.accumulate) ISG_CUDA(cudaMemsetAsync(table, 0, table_bytes, s));
+    // host output: the call's own status word, read below; device output: the device's word,
+    // which isg_device_status reports
+    unsigned int* status = g_out_on_device ? device_status_word() : reinterpret_cast<unsigned int*>(scratch + 8);
+    launch_enumeration(p, inl ? nullptr : reinterpret_cast<const uint64_t*>(scratch + off_blob), (int)blob.size(),
+                       table, reinterpret_cast<unsigned long long*>(scratch), status, s, blob.data());
+    if (mirror) {
+        const int n_m = graph.n + 1, n_e = (int)(graph.S + 1);
+        int64_t* full = g_out_on_device ? g_out : reinterpret_cast<int64_t*>(scratch + off_table + table_bytes);
+        const int acc = g_out_on_device ? o.accumulate : 0;
+        mirror_kernel<<<std::min(1024, (n_e * n_m + 255) / 256), 256, 0, s>>>(table, full, n_e, n_m, acc);
+        ISG_CUDA(cudaGetLastError());
+        table = full;
+    }
+    if (!g_out_on_device) {
+        std::vector<int64_t> host((size_t)public_bins(graph));
+        unsigned int word = 0;
+        ISG_CUDA(cudaMemcpyAsync(host.data(), table, table_bytes, cudaMemcpyDeviceToHost, s));
+        ISG_CUDA(cudaMemcpyAsync(&word, scratch + 8, sizeof word, cudaMemcpyDeviceToHost, s));
+        ISG_CUDA(cudaStreamSynchronize(s));
+        check_self_check_word(word, "enumeration");
+        if (o.accumulate) for (size_t i = 0; i < host.size(); ++i) g_out[i] += host[i];
+        else std::memcpy(g_out, host.data(), table_bytes);
+    }
+}
+
+}  // namespace isg
+
 extern "C" isg_status isg_enumerate(const isg_graph* graph, void* stream, int64_t* g_out, int32_t g_out_on_device,
                                     const isg_options* opt) {
     return guarded([&] {
@@ -441,47 +529,46 @@ extern "C" isg_status isg_enumerate(const isg_graph* graph, void* stream, int64_
         if (o.autotune) apply_autotune(*graph, o, s);
         const bool sym = o.symmetry != 0;
         if (sym) { o.shard_bits = 1; o.shard_lo = 1; o.shard_hi = 2; }      // spin N-1 up only
-        const DeviceInfo d = device_info();
-        const std::shared_ptr<const PlannedProgram> pp = planned_program(*graph, o, d);
-        const Plan& p = pp->plan;
-        const std::vector<uint64_t>& blob = pp->blob;
-        const size_t table_bytes = sizeof(int64_t) * (size_t)public_bins(*graph);
-        const size_t blob_bytes = blob.size() * 8;
-        // scratch: [counter 8][status 8][blob][table: host mode or symmetry half]
-        const size_t off_blob = 16, off_table = (off_blob + blob_bytes + 255) & ~(size_t)255;
-        const bool own_table = !g_out_on_device || sym;
-        const size_t scratch_bytes = off_table + (own_table ? table_bytes : 0) + (sym && !g_out_on_device ? table_bytes : 0);
-        char* scratch = nullptr;
-        scratch = static_cast<char*>(scratch_alloc(scratch_bytes, s));
-        struct Free {
-            char* p; cudaStream_t s;
-            ~Free() { if (p) cudaFreeAsync(p, s); }
-        } guard{scratch, s};
-        ISG_CUDA(cudaMemsetAsync(scratch, 0, 16, s));
-        const bool inl = program_fits_inline(blob.size());
-        if (!inl) ISG_CUDA(cudaMemcpyAsync(scratch + off_blob, blob.data(), blob_bytes, cudaMemcpyHostToDevice, s));
-        int64_t* table = own_table ? reinterpret_cast<int64_t*>(scratch + off_table) : g_out;
-        if (own_table || !o.accumulate) ISG_CUDA(cudaMemsetAsync(table, 0, table_bytes, s));
-        launch_enumeration(p, inl ? nullptr : reinterpret_cast<const uint64_t*>(scratch + off_blob), (int)blob.size(),
-                           table, reinterpret_cast<unsigned long long*>(scratch), reinterpret_cast<unsigned int*>(scratch + 8),
-                           s, blob.data());
-        if (sym) {
-            const int n_m = graph->n + 1, n_e = (int)(graph->S + 1);
-            int64_t* full = g_out_on_device ? g_out : reinterpret_cast<int64_t*>(scratch + off_table + table_bytes);
-            const int acc = g_out_on_device ? o.accumulate : 0;
-            mirror_kernel<<<std::min(1024, (n_e * n_m + 255) / 256), 256, 0, s>>>(table, full, n_e, n_m, acc);
-            ISG_CUDA(cudaGetLastError());
-            table = full;
+        enumerate_range(*graph, s, g_out, g_out_on_device != 0, o, sym);
+    });
+}
+
+extern "C" isg_status isg_enumerate_rank(const isg_graph* graph, void* stream, int64_t* g_out, int32_t g_out_on_device,
+                                         int32_t rank, int32_t world_size, const isg_options* opt) {
+    return guarded([&] {
+        NvtxRange nvtx("isg_enumerate_rank");
+        if (!graph || !g_out) fail(ISG_ERR_INVALID, "graph or g_out is NULL");
+        isg_options o = resolve_options(opt);
+        if (o.shard_bits || o.shard_lo || o.shard_hi) fail(ISG_ERR_INVALID, "the rank's shards come from rank and world_size");
+        const bool sym = o.symmetry != 0;
+        int32_t bits = 0;
+        int64_t lo = 0, hi = 0;
+        rank_shards(graph->n, rank, world_size, sym, bits, lo, hi);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (lo == hi) {                                // no configurations for this rank
+            const size_t table_bytes = sizeof(int64_t) * (size_t)public_bins(*graph);
+            if (o.accumulate) return;
+            if (g_out_on_device) ISG_CUDA(cudaMemsetAsync(g_out, 0, table_bytes, s));
+            else std::memset(g_out, 0, table_bytes);
+            return;
         }
-        if (!g_out_on_device) {
-            std::vector<int64_t> host((size_t)public_bins(*graph));
-            unsigned int status = 0;
-            ISG_CUDA(cudaMemcpyAsync(host.data(), table, table_bytes, cudaMemcpyDeviceToHost, s));
-            ISG_CUDA(cudaMemcpyAsync(&status, scratch + 8, sizeof status, cudaMemcpyDeviceToHost, s));
-            ISG_CUDA(cudaStreamSynchronize(s));
-            if (status) fail(ISG_ERR_INTERNAL, "enumeration self-check failed (status " + std::to_string(status) + ")");
-            if (o.accumulate) for (size_t i = 0; i < host.size(); ++i) g_out[i] += host[i];
-            else std::memcpy(g_out, host.data(), table_bytes);
-        }
+        if (o.autotune) apply_autotune(*graph, o, s);
+        o.symmetry = 0;
+        o.shard_bits = bits;
+        o.shard_lo = lo;
+        o.shard_hi = hi;
+        enumerate_range(*graph, s, g_out, g_out_on_device != 0, o, sym);
+    });
+}
+
+extern "C" isg_status isg_device_status(void* stream, int32_t clear) {
+    return guarded([&] {
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        unsigned int* w = device_status_word();
+        unsigned int word = 0;
+        ISG_CUDA(cudaMemcpyAsync(&word, w, sizeof word, cudaMemcpyDeviceToHost, s));
+        if (clear) ISG_CUDA(cudaMemsetAsync(w, 0, sizeof word, s));
+        ISG_CUDA(cudaStreamSynchronize(s));
+        check_self_check_word(word, "device-output call");
     });
 }

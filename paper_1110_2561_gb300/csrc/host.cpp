@@ -17,6 +17,15 @@ void set_error(const std::string& msg) { t_last_error = msg; }
 void clear_error() { t_last_error.clear(); }
 [[noreturn]] void fail(isg_status s, const std::string& msg) { throw Error{s, msg}; }
 
+void check_self_check_word(unsigned int word, const char* what) {
+    if (!word) return;
+    std::string msg = std::string(what) + " self-check failed (status " + std::to_string(word) + ":";
+    if (word & kSelfCheckLostBin) msg += " a walk's tracked bin differed from its recomputation;";
+    if (word & kSelfCheckOutOfRange) msg += " a walk's address left the histogram;";
+    msg.back() = ')';
+    fail(ISG_ERR_INTERNAL, msg);
+}
+
 isg_options resolve_options(const isg_options* opt) {
     isg_options o;
     isg_options_init(&o);
@@ -270,6 +279,26 @@ std::vector<uint64_t> build_program(const isg_graph& g, const Plan& p) {
     return blob;
 }
 
+void rank_shards(int n, int rank, int world, bool sym, int32_t& bits, int64_t& lo, int64_t& hi) {
+    if (world < 1 || world > (1 << 20)) fail(ISG_ERR_INVALID, "world_size must lie in [1, 2^20]");
+    if (rank < 0 || rank >= world) fail(ISG_ERR_INVALID, "rank must lie in [0, world_size)");
+    // A power-of-two world splits the space evenly on log2(world) bits; any other world gets 64
+    // times as many shards as ranks, so contiguous shares differ by at most one shard in 64.
+    int L = 0;
+    while ((1 << L) < world) ++L;
+    int k = ((1 << L) == world) ? L : L + 6;
+    k = std::min(k, sym ? n - 1 : n);
+    const int64_t shards = (int64_t)1 << k;
+    lo = (int64_t)rank * shards / world;
+    hi = (int64_t)(rank + 1) * shards / world;
+    bits = k;
+    if (sym) {                                         // the top bit (spin N-1) up
+        bits = k + 1;
+        lo += shards;
+        hi += shards;
+    }
+}
+
 std::shared_ptr<const PlannedProgram> planned_program(const isg_graph& g, const isg_options& o, const DeviceInfo& d) {
     std::string key(reinterpret_cast<const char*>(&o), sizeof o);   // padding bytes can only cause misses
     key.append(reinterpret_cast<const char*>(&d), sizeof d);
@@ -301,16 +330,69 @@ struct HostSink {
 };
 
 template <int B>
-static void emulate_tasks(const ProgView& v, const Plan& p, std::vector<uint32_t>& hist, bool& bad) {
+static void emulate_tasks(const ProgView& v, const Plan& p, std::vector<uint32_t>& hist, unsigned int& word) {
     HostSink sink{&hist, (uint32_t)(hist.size() * 4)};
     for (uint64_t t = 0; t < p.n_tasks; ++t)
         for (int lane = 0; lane < 32; ++lane) {
             uint64_t last_state;
             uint32_t last_idx;
             lane_walk<B>(v, p.prefix_base + t * 32 + lane, 0u, sink, last_state, last_idx);
-            if (last_idx != bin_offset(v, last_state)) bad = true;
+            if (last_idx != bin_offset(v, last_state)) word |= kSelfCheckLostBin;
         }
-    if (sink.bad) bad = true;
+    if (sink.bad) word |= kSelfCheckOutOfRange;
+}
+
+// The kernels' walk on the host (see isg_debug_emulate). plant_site >= 0 plants a mistake in the
+// program first: plant_delta is added to the field constant (sum |J|) in the site record at
+// internal position plant_site, as a wrong program entry would. Returns the self-check word the
+// walk produced.
+static unsigned int emulate(const isg_graph& g, isg_options o, int plant_site, int32_t plant_delta, int64_t* g_out) {
+    const bool sym = o.symmetry != 0;
+    if (sym) { o.shard_bits = 1; o.shard_lo = 1; o.shard_hi = 2; }     // spin N-1 up only
+    Plan p = make_plan(g, o, DeviceInfo{});
+    std::vector<uint64_t> blob = build_program(g, p);
+    if (plant_site >= 0) {
+        if (p.small || plant_site >= g.n) fail(ISG_ERR_INVALID, "no site record to plant a mistake in");
+        SiteRec* site = reinterpret_cast<SiteRec*>(blob.data() + reinterpret_cast<const ProgHeader*>(blob.data())->off_site);
+        site[plant_site].degw += plant_delta;
+    }
+    const ProgView v = make_view(blob.data());
+    const int64_t stride = p.stride > 0 ? p.stride : g.n + 1;
+    const int64_t nb = g.n_e_c * stride;
+    std::vector<uint32_t> hist((size_t)nb, 0);
+    unsigned int word = 0;
+    if (p.small) {
+        for (uint64_t s = p.s_lo; s < p.s_hi; ++s) {
+            const uint32_t off = bin_offset(v, s);
+            if ((off & 3u) || off >= nb * 4) { word |= kSelfCheckOutOfRange; continue; }
+            hist[off >> 2] += 1;
+        }
+    } else {
+        switch (p.b) {
+            case 1: emulate_tasks<1>(v, p, hist, word); break;
+            case 2: emulate_tasks<2>(v, p, hist, word); break;
+            case 3: emulate_tasks<3>(v, p, hist, word); break;
+            case 4: emulate_tasks<4>(v, p, hist, word); break;
+            case 5: emulate_tasks<5>(v, p, hist, word); break;
+            case 6: emulate_tasks<6>(v, p, hist, word); break;
+            case 7: emulate_tasks<7>(v, p, hist, word); break;
+            default: fail(ISG_ERR_INTERNAL, "bad low block size");
+        }
+    }
+    if (word) return word;
+    std::vector<int64_t> tab((size_t)public_bins(g), 0);
+    for (int64_t i = 0; i < nb; ++i)
+        if (hist[i]) {
+            const int64_t pb = public_bin(g, i, stride);
+            if (pb < 0) fail(ISG_ERR_INTERNAL, "emulated walk counted a padding column");
+            tab[pb] += hist[i];
+        }
+    if (!o.accumulate) std::memset(g_out, 0, sizeof(int64_t) * public_bins(g));
+    const int64_t n_m = g.n + 1;
+    for (int64_t e = 0; e <= g.S; ++e)
+        for (int64_t m = 0; m < n_m; ++m)
+            g_out[e * n_m + m] += tab[e * n_m + m] + (sym ? tab[e * n_m + (n_m - 1 - m)] : 0);
+    return 0;
 }
 
 }  // namespace isg
@@ -433,47 +515,59 @@ isg_status isg_debug_plan(const isg_graph* g, const isg_options* opt, int32_t sm
 isg_status isg_debug_emulate(const isg_graph* g, const isg_options* opt, int64_t* g_out) {
     return guarded([&] {
         if (!g || !g_out) fail(ISG_ERR_INVALID, "NULL argument");
+        check_self_check_word(emulate(*g, resolve_options(opt), -1, 0, g_out), "emulated enumeration");
+    });
+}
+
+isg_status isg_rank_shards(int32_t n_spins, int32_t rank, int32_t world_size, int32_t symmetry, int32_t* shard_bits,
+                           int64_t* shard_lo, int64_t* shard_hi) {
+    return guarded([&] {
+        if (n_spins < 1 || n_spins > kMaxSpins) fail(ISG_ERR_INVALID, "n_spins must lie in [1, 64]");
+        int32_t bits = 0;
+        int64_t lo = 0, hi = 0;
+        rank_shards(n_spins, rank, world_size, symmetry != 0, bits, lo, hi);
+        if (shard_bits) *shard_bits = bits;
+        if (shard_lo) *shard_lo = lo;
+        if (shard_hi) *shard_hi = hi;
+    });
+}
+
+isg_status isg_debug_emulate_rank(const isg_graph* g, int32_t rank, int32_t world_size, const isg_options* opt,
+                                  int64_t* g_out) {
+    return guarded([&] {
+        if (!g || !g_out) fail(ISG_ERR_INVALID, "NULL argument");
         isg_options o = resolve_options(opt);
+        if (o.shard_bits || o.shard_lo || o.shard_hi) fail(ISG_ERR_INVALID, "the rank's shards come from rank and world_size");
         const bool sym = o.symmetry != 0;
-        if (sym) { o.shard_bits = 1; o.shard_lo = 1; o.shard_hi = 2; }     // spin N-1 up only
-        Plan p = make_plan(*g, o, DeviceInfo{});
-        std::vector<uint64_t> blob = build_program(*g, p);
-        const ProgView v = make_view(blob.data());
-        const int64_t stride = p.stride > 0 ? p.stride : g->n + 1;
-        const int64_t nb = g->n_e_c * stride;
-        std::vector<uint32_t> hist((size_t)nb, 0);
-        bool bad = false;
-        if (p.small) {
-            for (uint64_t s = p.s_lo; s < p.s_hi; ++s) {
-                const uint32_t off = bin_offset(v, s);
-                if ((off & 3u) || off >= nb * 4) { bad = true; continue; }
-                hist[off >> 2] += 1;
-            }
-        } else {
-            switch (p.b) {
-                case 1: emulate_tasks<1>(v, p, hist, bad); break;
-                case 2: emulate_tasks<2>(v, p, hist, bad); break;
-                case 3: emulate_tasks<3>(v, p, hist, bad); break;
-                case 4: emulate_tasks<4>(v, p, hist, bad); break;
-                case 5: emulate_tasks<5>(v, p, hist, bad); break;
-                case 6: emulate_tasks<6>(v, p, hist, bad); break;
-                case 7: emulate_tasks<7>(v, p, hist, bad); break;
-                default: fail(ISG_ERR_INTERNAL, "bad low block size");
-            }
+        int32_t bits = 0;
+        int64_t lo = 0, hi = 0;
+        rank_shards(g->n, rank, world_size, sym, bits, lo, hi);
+        if (lo == hi) {
+            if (!o.accumulate) std::memset(g_out, 0, sizeof(int64_t) * public_bins(*g));
+            return;
         }
-        if (bad) fail(ISG_ERR_INTERNAL, "emulated walk left the histogram or lost track of its bin");
-        std::vector<int64_t> tab((size_t)public_bins(*g), 0);
-        for (int64_t i = 0; i < nb; ++i)
-            if (hist[i]) {
-                const int64_t pb = public_bin(*g, i, stride);
-                if (pb < 0) fail(ISG_ERR_INTERNAL, "emulated walk counted a padding column");
-                tab[pb] += hist[i];
-            }
+        o.symmetry = 0;
+        o.shard_bits = bits;
+        o.shard_lo = lo;
+        o.shard_hi = hi;
+        std::vector<int64_t> part((size_t)public_bins(*g), 0);
+        check_self_check_word(emulate(*g, o, -1, 0, part.data()), "emulated enumeration");
         if (!o.accumulate) std::memset(g_out, 0, sizeof(int64_t) * public_bins(*g));
         const int64_t n_m = g->n + 1;
         for (int64_t e = 0; e <= g->S; ++e)
             for (int64_t m = 0; m < n_m; ++m)
-                g_out[e * n_m + m] += tab[e * n_m + m] + (sym ? tab[e * n_m + (n_m - 1 - m)] : 0);
+                g_out[e * n_m + m] += part[e * n_m + m] + (sym ? part[e * n_m + (n_m - 1 - m)] : 0);
+    });
+}
+
+isg_status isg_debug_emulate_planted(const isg_graph* g, const isg_options* opt, int32_t site, int32_t delta,
+                                     int64_t* g_out, uint32_t* word) {
+    return guarded([&] {
+        if (!g || !g_out) fail(ISG_ERR_INVALID, "NULL argument");
+        if (site < 0) fail(ISG_ERR_INVALID, "site must be >= 0");
+        const unsigned int w = emulate(*g, resolve_options(opt), site, delta, g_out);
+        if (word) *word = w;
+        check_self_check_word(w, "emulated enumeration");
     });
 }
 

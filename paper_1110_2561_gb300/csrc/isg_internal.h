@@ -146,4 +146,30 @@ int kernel_occupancy(const void* kernel, int threads, size_t smem);
 
 inline int64_t public_bins(const isg_graph& g) { return (g.S + 1) * (int64_t)(g.n + 1); }
 
+// Bits of a kernel self-check word: a walk's incrementally tracked bin differed from the bin
+// recomputed from scratch (set by the kernels); a walk's address left the histogram (set only by
+// the host emulation, which checks every address).
+constexpr unsigned int kSelfCheckLostBin = 1u;
+constexpr unsigned int kSelfCheckOutOfRange = 2u;
+
+// Throw ISG_ERR_INTERNAL naming the failed checks of a nonzero self-check word (no-op for 0).
+// One function for every caller, so the kernels' word, the host emulation's and the device-wide
+// word of isg_device_status are reported alike.
+void check_self_check_word(unsigned int word, const char* what);
+
+// The current device's self-check word of device-output calls (a file-scope __device__ word,
+// looked up once per device; no allocation). Kernels OR their failures into it; isg_device_status
+// reads and clears it.
+unsigned int* device_status_word();
+
+// The shards of rank `rank` of `world` ranks (isg_rank_shards): shard_bits `bits` and the range
+// [lo, hi), empty (lo == hi) when there are more ranks than shards. With `sym` the range lies in
+// the upper half of the space (spin N-1 up). Throws ISG_ERR_INVALID for a bad rank or world.
+void rank_shards(int n, int rank, int world, bool sym, int32_t& bits, int64_t& lo, int64_t& hi);
+
+// Fill the unset planning fields of o from the autotuner's cache for this graph on the current
+// device, if isg_autotune (or isg_enumerate with autotune) tuned it before; no timing, no
+// allocation. Returns whether the cache held an entry.
+bool apply_cached_autotune(const isg_graph& g, isg_options& o);
+
 }  // namespace isg

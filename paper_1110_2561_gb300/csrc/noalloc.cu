@@ -24,8 +24,9 @@
 
 namespace isg {
 
-// Scratch of isg_enumerate_noalloc: [0, 8) task counter, [8, 12) status word, program from
-// byte 256 on. Shared by every call on a device.
+// Scratch of isg_enumerate_noalloc: [0, 8) task counter, program from byte 256 on. Shared by
+// every call on a device. (The kernels' self-check goes to the device's status word, a file-scope
+// __device__ word of its own that isg_device_status reads.)
 constexpr size_t kNoallocScratchBytes = 16384;
 constexpr size_t kNoallocProgramOffset = 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
@@ -63,7 +64,9 @@ extern "C" isg_status isg_enumerate_noalloc(const isg_graph* graph, void* stream
                                             const isg_options* opt) {
     return guarded([&] {
         if (!graph || !g_out_device) fail(ISG_ERR_INVALID, "graph or g_out_device is NULL");
-        const isg_options o = resolve_options(opt);
+        isg_options o = resolve_options(opt);
+        // autotune: the cached choice for this graph, if it was tuned before (timing allocates)
+        if (o.autotune) apply_cached_autotune(*graph, o);
         const DeviceInfo d = device_info();
         const Plan p = make_plan(*graph, o, d);
         const std::vector<uint64_t> blob = build_program(*graph, p);
@@ -77,15 +80,15 @@ extern "C" isg_status isg_enumerate_noalloc(const isg_graph* graph, void* stream
         auto check = [](cudaError_t e, const char* what) {
             if (e != cudaSuccess) fail(ISG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
         };
-        // the counter and the status word must start at zero; the program is overwritten whole
-        check(cudaMemsetAsync(scratch, 0, 16, s), "cudaMemsetAsync(counter)");
+        // the counter must start at zero; the program is overwritten whole
+        check(cudaMemsetAsync(scratch, 0, 8, s), "cudaMemsetAsync(counter)");
         check(cudaMemcpyAsync(scratch + kNoallocProgramOffset, blob.data(), blob_bytes, cudaMemcpyHostToDevice, s),
               "cudaMemcpyAsync(program)");
         if (!o.accumulate)
             check(cudaMemsetAsync(g_out_device, 0, sizeof(int64_t) * (size_t)public_bins(*graph), s),
                   "cudaMemsetAsync(g_out)");
         launch_enumeration(p, reinterpret_cast<const uint64_t*>(scratch + kNoallocProgramOffset), (int)blob.size(),
-                           g_out_device, reinterpret_cast<unsigned long long*>(scratch),
-                           reinterpret_cast<unsigned int*>(scratch + 8), s, nullptr);
+                           g_out_device, reinterpret_cast<unsigned long long*>(scratch), device_status_word(), s,
+                           nullptr);
     });
 }

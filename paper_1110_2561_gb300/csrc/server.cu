@@ -60,6 +60,7 @@ struct Request {
     double configs = 0;
     size_t slot_off = 0, slot_bytes = 0;   // arena slot: [table][program]
     int64_t last_step = -1;          // last step that carries one of its tiles
+    bool step_failed = false;        // a step carrying its tiles reported a failed self-check
     ReqState state = ReqState::Queued;
     isg_status status = ISG_OK;
     std::string message;
@@ -138,6 +139,7 @@ struct isg_server {
     std::deque<Step> inflight;
     int64_t next_ticket = 1, next_step = 0;
     size_t n_admitted = 0;                             // active + finishing
+    int inject = 0;                                    // host-side failure injection (isg_debug_server_inject)
     bool stop = false;
     std::thread worker;
     // statistics
@@ -166,13 +168,20 @@ static void admit_locked(isg_server* s) {
         r.slot_bytes = bytes;
         r.t_admit = Clock::now();
         r.state = ReqState::Active;
+        s->active.push_back(r.ticket);                 // admitted first: a failing call below fails it too
+        ++s->n_admitted;
         // zero the table and upload the program (ordered before any step that uses them)
         server_fail_cuda(cudaMemsetAsync(s->arena_dev + off, 0, r.table_words * 8, s->stream), "cudaMemsetAsync(table)");
         server_fail_cuda(cudaMemcpyAsync(s->arena_dev + off + tbytes, r.blob.data(), r.blob.size() * 8,
                                          cudaMemcpyHostToDevice, s->stream), "cudaMemcpyAsync(program)");
-        s->active.push_back(r.ticket);
-        ++s->n_admitted;
     }
+}
+
+// True while a step in flight carries one of the request's tiles (its slot is still written).
+static bool carried_inflight(const isg_server* s, int64_t ticket) {
+    for (const Step& st : s->inflight)
+        if (std::find(st.carried.begin(), st.carried.end(), ticket) != st.carried.end()) return true;
+    return false;
 }
 
 static void release_locked(isg_server* s, Request& r) {
@@ -276,6 +285,18 @@ static bool issue_step_locked(isg_server* s) {
     std::vector<int> ids(bp.small_ids);
     ids.insert(ids.end(), bp.mirror_ids.begin(), bp.mirror_ids.end());
     if (!ids.empty()) std::memcpy(s->small_host[buf], ids.data(), sizeof(int) * ids.size());
+    if (s->inject == 1) {
+        s->inject = 0;
+        fail(ISG_ERR_CUDA, "injected host-side failure before the step's first enqueue");
+    }
+    // From the first enqueue on, a failing call must not leave untracked work writing into the
+    // arena: the stream is drained before the error propagates, so the slots of the requests it
+    // fails can be released at once.
+    struct DrainOnThrow {
+        cudaStream_t st;
+        bool armed = true;
+        ~DrainOnThrow() { if (armed) cudaStreamSynchronize(st); }
+    } drain{s->stream};
     server_fail_cuda(cudaEventRecord(s->ev_start[buf], s->stream), "cudaEventRecord");
     server_fail_cuda(cudaMemcpyAsync(s->desc_dev[buf], s->desc_host[buf], sizeof(BatchInst) * desc.size(),
                                      cudaMemcpyHostToDevice, s->stream), "cudaMemcpyAsync(descriptors)");
@@ -292,6 +313,10 @@ static bool issue_step_locked(isg_server* s) {
     if (!large.empty() || !small.empty())
         launch_batch(bp, s->desc_dev[buf], reinterpret_cast<const uint64_t*>(s->arena_dev), s->small_dev[buf], s->ctr_dev[buf],
                      status, s->stream, s->opt.ctas_per_sm > 0 ? s->opt.ctas_per_sm : 2);
+    if (s->inject == 2) {
+        s->inject = 0;
+        fail(ISG_ERR_CUDA, "injected host-side failure after the step's launch");
+    }
     server_fail_cuda(cudaMemcpyAsync(s->status_host[buf], s->ctr_dev[buf] + 1, 4, cudaMemcpyDeviceToHost, s->stream),
                      "cudaMemcpyAsync(status)");
     // copy out the tables of requests whose last tile is in this step
@@ -309,6 +334,7 @@ static bool issue_step_locked(isg_server* s) {
     for (Request* r : small_r) carried(r);
     for (Request* r : split_r) carried(r);
     server_fail_cuda(cudaEventRecord(s->ev_done[buf], s->stream), "cudaEventRecord");
+    drain.armed = false;
     st.configs = used;
     s->buf_busy[buf] = true;
     s->active.erase(std::remove_if(s->active.begin(), s->active.end(),
@@ -329,15 +355,22 @@ static void complete_step_locked(isg_server* s, float ms) {
     s->configs_done += st.configs;
     if (ms > 0.05 && st.configs > 1e9) s->rate_est = 0.7 * s->rate_est + 0.3 * (st.configs / (ms * 1e-3));
     const Clock::time_point now = Clock::now();
+    // a failed self-check taints every request with tiles in the step, finishing here or not
+    if (status)
+        for (int64_t t : st.carried) {
+            auto it = s->reqs.find(t);
+            if (it != s->reqs.end()) it->second->step_failed = true;
+        }
     for (int64_t t : st.finishing) {
         auto it = s->reqs.find(t);
         if (it == s->reqs.end()) continue;
         Request& r = *it->second;
         if (r.state == ReqState::Cancelled) { release_locked(s, r); s->reqs.erase(it); continue; }
-        if (status) {
+        if (r.state == ReqState::Failed) continue;     // failed on the host meanwhile: released below
+        if (r.step_failed) {
             r.state = ReqState::Failed;
             r.status = ISG_ERR_INTERNAL;
-            r.message = "enumeration self-check failed (status " + std::to_string(status) + ")";
+            r.message = "enumeration self-check failed in a step carrying this request";
         } else {
             r.result.assign(reinterpret_cast<int64_t*>(s->arena_host + r.slot_off),
                             reinterpret_cast<int64_t*>(s->arena_host + r.slot_off) + r.table_words);
@@ -346,14 +379,39 @@ static void complete_step_locked(isg_server* s, float ms) {
         r.t_done = now;
         release_locked(s, r);
     }
-    // cancelled requests whose last carrying step is now done
+    // cancelled requests whose last carrying step is now done, and requests failed on the host
+    // while this step still wrote into their slots
     for (int64_t t : st.carried) {
         auto it = s->reqs.find(t);
-        if (it != s->reqs.end() && it->second->state == ReqState::Cancelled && it->second->last_step <= st.id) {
-            release_locked(s, *it->second);
+        if (it == s->reqs.end()) continue;
+        Request& r = *it->second;
+        if (r.state == ReqState::Cancelled && r.last_step <= st.id) {
+            release_locked(s, r);
             s->reqs.erase(it);
+        } else if (r.state == ReqState::Failed && !carried_inflight(s, t)) {
+            release_locked(s, r);
         }
     }
+}
+
+// Fail every admitted request that still has tiles to issue, after a host-side error while
+// admitting or issuing (caller holds mu). A slot no in-flight step writes into is released now;
+// the others when the last step carrying them completes.
+static void fail_active_locked(isg_server* s, isg_status status, const std::string& msg) {
+    const Clock::time_point now = Clock::now();
+    for (int64_t t : s->active) {
+        Request& r = *s->reqs[t];
+        if (r.state == ReqState::Cancelled) {
+            if (!carried_inflight(s, t)) { release_locked(s, r); s->reqs.erase(t); }
+            continue;
+        }
+        r.state = ReqState::Failed;
+        r.status = status;
+        r.message = msg;
+        r.t_done = now;
+        if (!carried_inflight(s, t)) release_locked(s, r);
+    }
+    s->active.clear();
 }
 
 static void worker_main(isg_server* s) {
@@ -369,14 +427,7 @@ static void worker_main(isg_server* s) {
             err = e.msg;
         }
         if (!err.empty()) {                            // fail everything admitted; keep serving
-            for (int64_t t : s->active) {
-                Request& r = *s->reqs[t];
-                r.state = ReqState::Failed;
-                r.status = ISG_ERR_CUDA;
-                r.message = err;
-                r.t_done = Clock::now();
-            }
-            s->active.clear();
+            fail_active_locked(s, ISG_ERR_CUDA, err);
             s->cv_done.notify_all();
         }
         if (!s->inflight.empty()) {
@@ -387,17 +438,26 @@ static void worker_main(isg_server* s) {
             if (e == cudaSuccess) cudaEventElapsedTime(&ms, s->ev_start[buf], s->ev_done[buf]);
             lk.lock();
             if (e != cudaSuccess) {
-                Step& st = s->inflight.front();
+                Step st = std::move(s->inflight.front());
+                s->inflight.pop_front();
+                s->buf_busy[buf] = false;
                 for (int64_t t : st.carried) {
                     auto it = s->reqs.find(t);
                     if (it == s->reqs.end()) continue;
-                    it->second->state = ReqState::Failed;
-                    it->second->status = ISG_ERR_CUDA;
-                    it->second->message = std::string("step failed: ") + cudaGetErrorString(e);
-                    it->second->t_done = Clock::now();
+                    Request& r = *it->second;
+                    if (r.state == ReqState::Cancelled) {
+                        if (!carried_inflight(s, t)) { release_locked(s, r); s->reqs.erase(it); }
+                        continue;
+                    }
+                    r.state = ReqState::Failed;
+                    r.status = ISG_ERR_CUDA;
+                    r.message = std::string("step failed: ") + cudaGetErrorString(e);
+                    r.t_done = Clock::now();
+                    if (!carried_inflight(s, t)) release_locked(s, r);
                 }
-                s->buf_busy[buf] = false;
-                s->inflight.pop_front();
+                s->active.erase(std::remove_if(s->active.begin(), s->active.end(),
+                                               [&](int64_t t) { return s->reqs[t]->state == ReqState::Failed; }),
+                                s->active.end());
             } else {
                 complete_step_locked(s, ms);
             }
@@ -624,7 +684,8 @@ isg_status isg_server_result(isg_server* s, int64_t ticket, int64_t* g_out, doub
         if (r.state == ReqState::Failed) {
             const isg_status st = r.status;
             const std::string msg = r.message;
-            s->reqs.erase(it);
+            if (r.slot_bytes) r.state = ReqState::Cancelled;   // released once no in-flight step writes into it
+            else s->reqs.erase(it);
             fail(st, msg);
         }
         if (r.state != ReqState::Done) fail(ISG_ERR_NOT_READY, "request not finished");
@@ -661,7 +722,8 @@ isg_status isg_server_cancel(isg_server* s, int64_t ticket) {
                 }
                 break;
             default:                                          // finished: just drop the result
-                s->reqs.erase(it);
+                if (r.slot_bytes) r.state = ReqState::Cancelled;   // failed, slot still written by a step
+                else s->reqs.erase(it);
         }
         s->cv_done.notify_all();
     });
@@ -683,5 +745,14 @@ isg_status isg_server_stats(isg_server* s, double* stats) {
 }
 
 void isg_server_destroy(isg_server* s) { destroy_server(s); }
+
+isg_status isg_debug_server_inject(isg_server* s, int32_t where) {
+    return guarded([&] {
+        if (!s) fail(ISG_ERR_INVALID, "NULL argument");
+        if (where < 0 || where > 2) fail(ISG_ERR_INVALID, "where must be 0, 1 or 2");
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->inject = where;
+    });
+}
 
 }  // extern "C"

@@ -432,13 +432,16 @@ extern "C" isg_status isg_enumerate_split(const isg_graph* graph, void* stream, 
         ISG_CUDA(cudaMemsetAsync(scratch, 0, 16, s));
         ISG_CUDA(cudaMemcpyAsync(scratch + o_blob, blob.data(), blob_bytes, cudaMemcpyHostToDevice, s));
         ISG_CUDA(cudaMemsetAsync(table, 0, table_bytes, s));
-        launch_split(*prep, reinterpret_cast<const uint64_t*>(scratch + o_blob), table, reinterpret_cast<unsigned int*>(scratch), s);
+        // host output: the call's own status word, read below; device output: the device's word,
+        // which isg_device_status reports
+        unsigned int* status = g_out_on_device ? device_status_word() : reinterpret_cast<unsigned int*>(scratch);
+        launch_split(*prep, reinterpret_cast<const uint64_t*>(scratch + o_blob), table, status, s);
         if (!g_out_on_device) {
-            unsigned int status = 0;
+            unsigned int word = 0;
             ISG_CUDA(cudaMemcpyAsync(g_out, table, table_bytes, cudaMemcpyDeviceToHost, s));
-            ISG_CUDA(cudaMemcpyAsync(&status, scratch, sizeof status, cudaMemcpyDeviceToHost, s));
+            ISG_CUDA(cudaMemcpyAsync(&word, scratch, sizeof word, cudaMemcpyDeviceToHost, s));
             ISG_CUDA(cudaStreamSynchronize(s));
-            if (status) fail(ISG_ERR_INTERNAL, "split enumeration self-check failed");
+            check_self_check_word(word, "split enumeration");
         }
     });
 }

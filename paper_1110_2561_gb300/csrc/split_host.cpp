@@ -293,37 +293,40 @@ SplitPlan plan_split(const isg_graph& g, uint64_t boundary, bool require_gain) {
         if (!std::isfinite(best.cost))
             fail(ISG_ERR_TOO_LARGE, "the given boundary leaves a component of more than 30 spins, more than 40 "
                                     "boundary spins, or buffers beyond shared memory");
-    } else if (const uint64_t known = structural_boundary(g, n_cls, 0)) {
-        consider(known);                             // same structure as a graph planned before
     } else {
-        auto window = [&](int a, int w) {
-            uint64_t m = 0;
-            for (int i = 0; i < w; ++i) m |= 1ull << ((a + i) % n);
-            return m;
-        };
-        for (int w = 1; w <= n / 2; ++w)
-            for (int a = 0; a < n; ++a) {
-                const uint64_t w1 = window(a, w);
-                consider(w1);
-                for (int d = w + 1; d + w <= n; ++d) consider(w1 | window(a + d, w));
+        // a boundary known from a graph of the same structure is tried first; the search runs
+        // when there is none, or when these couplings reject it (buffers beyond shared memory)
+        if (const uint64_t known = structural_boundary(g, n_cls, 0)) consider(known);
+        if (!std::isfinite(best.cost)) {
+            auto window = [&](int a, int w) {
+                uint64_t m = 0;
+                for (int i = 0; i < w; ++i) m |= 1ull << ((a + i) % n);
+                return m;
+            };
+            for (int w = 1; w <= n / 2; ++w)
+                for (int a = 0; a < n; ++a) {
+                    const uint64_t w1 = window(a, w);
+                    consider(w1);
+                    for (int d = w + 1; d + w <= n; ++d) consider(w1 | window(a + d, w));
+                }
+            for (int p = 2; p <= 8 && p <= n; ++p)
+                for (uint32_t W = 1; W + 1 < (1u << p); ++W) {
+                    uint64_t S = 0;
+                    for (int i = 0; i < n; ++i) if ((W >> (i % p)) & 1) S |= 1ull << i;
+                    consider(S);
+                }
+            {
+                std::vector<int> order(n);
+                for (int i = 0; i < n; ++i) order[i] = i;
+                std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return popc(adj[a]) < popc(adj[b]); });
+                uint64_t I = 0, blocked = 0;
+                for (int i : order)
+                    if (!((blocked >> i) & 1)) { I |= 1ull << i; blocked |= adj[i] | (1ull << i); }
+                consider(all & ~I);
             }
-        for (int p = 2; p <= 8 && p <= n; ++p)
-            for (uint32_t W = 1; W + 1 < (1u << p); ++W) {
-                uint64_t S = 0;
-                for (int i = 0; i < n; ++i) if ((W >> (i % p)) & 1) S |= 1ull << i;
-                consider(S);
-            }
-        {
-            std::vector<int> order(n);
-            for (int i = 0; i < n; ++i) order[i] = i;
-            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return popc(adj[a]) < popc(adj[b]); });
-            uint64_t I = 0, blocked = 0;
-            for (int i : order)
-                if (!((blocked >> i) & 1)) { I |= 1ull << i; blocked |= adj[i] | (1ull << i); }
-            consider(all & ~I);
+            if (!std::isfinite(best.cost)) fail(ISG_ERR_TOO_LARGE, "no boundary set gives components of at most 30 spins that fit");
+            structural_boundary(g, n_cls, best.S);
         }
-        if (!std::isfinite(best.cost)) fail(ISG_ERR_TOO_LARGE, "no boundary set gives components of at most 30 spins that fit");
-        structural_boundary(g, n_cls, best.S);
     }
     // searched or known from a graph of the same structure (planned before without the gain
     // requirement): either way a boundary that does not beat the full enumeration is refused

@@ -57,6 +57,12 @@ _SIGS = {
     "isg_version": (ctypes.c_char_p, []),
     "isg_debug_plan": (i32, [vp, vp, i32, vp]),
     "isg_debug_emulate": (i32, [vp, vp, vp]),
+    "isg_debug_emulate_planted": (i32, [vp, vp, i32, i32, vp, ctypes.POINTER(ctypes.c_uint32)]),
+    "isg_debug_server_inject": (i32, [vp, i32]),
+    "isg_device_status": (i32, [vp, i32]),
+    "isg_rank_shards": (i32, [i32, i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+    "isg_enumerate_rank": (i32, [vp, vp, vp, i32, i32, i32, vp]),
+    "isg_debug_emulate_rank": (i32, [vp, i32, i32, vp, vp]),
     "isg_probe_peaks": (i32, [vp, vp, vp, vp, vp]),
     "isg_enumerate_noalloc": (i32, [vp, vp, vp, vp]),
     "isg_autotune": (i32, [vp, vp, vp, vp]),
@@ -202,6 +208,74 @@ def isg_enumerate(graph: Graph, g_out=None, stream=None, **options):
     _check_tensor(g_out, shape, "int64")
     _check(lib().isg_enumerate(graph, _stream_handle(stream), g_out.data_ptr(), 1, ctypes.byref(o)))
     return g_out
+
+
+def isg_rank_shards(n_spins: int, rank: int, world_size: int, symmetry: bool = False):
+    """(shard_bits, shard_lo, shard_hi): the shards of the configuration space that rank `rank` of
+    `world_size` enumerates (see isg_enumerate_rank)."""
+    b, lo, hi = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().isg_rank_shards(n_spins, rank, world_size, 1 if symmetry else 0, ctypes.byref(b), ctypes.byref(lo),
+                                 ctypes.byref(hi)))
+    return b.value, lo.value, hi.value
+
+
+def isg_enumerate_rank(graph: Graph, rank: int, world_size: int, g_out=None, stream=None, **options):
+    """Rank `rank`'s share of g (the tables of all ranks sum to the exact table). g_out as for
+    isg_enumerate; options as there (symmetry allowed, shard fields not)."""
+    shape = table_shape(graph)
+    o = _options(**options)
+    if g_out is None:
+        g_out = np.zeros(shape, dtype=np.int64)
+    if isinstance(g_out, np.ndarray):
+        if g_out.dtype != np.int64 or not g_out.flags.c_contiguous or g_out.shape != shape:
+            raise ValueError(f"g_out must be a C-contiguous int64 array of shape {shape}")
+        _check(lib().isg_enumerate_rank(graph, _stream_handle(stream) if stream is not None else None,
+                                        g_out.ctypes.data, 0, rank, world_size, ctypes.byref(o)))
+        return g_out
+    _check_tensor(g_out, shape, "int64")
+    _check(lib().isg_enumerate_rank(graph, _stream_handle(stream), g_out.data_ptr(), 1, rank, world_size,
+                                    ctypes.byref(o)))
+    return g_out
+
+
+def enumerate_distributed(graph: Graph, g_out, group=None, stream=None, **options):
+    """The exact table of one graph enumerated by every rank of a torch.distributed process group:
+    isg_enumerate_rank on this rank's share, then one all-reduce (sum) of the int64 table over the
+    group. g_out: a torch int64 tensor of table_shape(graph), a CUDA tensor (NCCL reduces it in
+    place; a gloo group stages it through host memory) or a CPU tensor (gloo). Returns g_out."""
+    import torch
+    import torch.distributed as dist
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    if g_out.is_cuda:
+        st = stream if stream is not None else torch.cuda.current_stream(g_out.device)
+        isg_enumerate_rank(graph, rank, world, g_out, st, **options)
+        with torch.cuda.stream(st):             # the collective is ordered after the enumeration
+            if dist.get_backend(group) == "nccl":
+                dist.all_reduce(g_out, op=dist.ReduceOp.SUM, group=group)
+            else:
+                host = g_out.cpu()              # waits for the enumeration on st
+                dist.all_reduce(host, op=dist.ReduceOp.SUM, group=group)
+                g_out.copy_(host)
+        return g_out
+    if g_out.dtype != torch.int64 or not g_out.is_contiguous() or tuple(g_out.shape) != table_shape(graph):
+        raise ValueError(f"g_out must be a contiguous int64 tensor of shape {table_shape(graph)}")
+    isg_enumerate_rank(graph, rank, world, g_out.numpy(), **options)
+    dist.all_reduce(g_out, op=dist.ReduceOp.SUM, group=group)
+    return g_out
+
+
+def isg_debug_emulate_rank(graph: Graph, rank: int, world_size: int, **options) -> np.ndarray:
+    """isg_enumerate_rank's work run on the host by the kernels' walk (small N only)."""
+    g = np.zeros(table_shape(graph), dtype=np.int64)
+    o = _options(**options)
+    _check(lib().isg_debug_emulate_rank(graph, rank, world_size, ctypes.byref(o), g.ctypes.data))
+    return g
+
+
+def isg_device_status(stream=None, clear: bool = True):
+    """Raise IsgError (ISG_ERR_INTERNAL) if a kernel self-check of a device-output call on the
+    current device failed since the last clear (synchronises `stream`); clear resets the word."""
+    _check(lib().isg_device_status(_stream_handle(stream), 1 if clear else 0))
 
 
 def isg_autotune(graph: Graph, stream=None, **options) -> dict:
@@ -402,6 +476,11 @@ class Server:
         _check(lib().isg_server_cancel(self.ptr, ticket))
         self.shapes.pop(ticket, None)
 
+    def inject_failure(self, where: int):
+        """isg_debug_server_inject: make the next engine step fail on the host (1: before its first
+        enqueue, 2: after its launch; 0: cancel)."""
+        _check(lib().isg_debug_server_inject(self.ptr, where))
+
     def stats(self) -> dict:
         v = (ctypes.c_double * 8)()
         _check(lib().isg_server_stats(self.ptr, v))
@@ -560,6 +639,17 @@ def isg_debug_emulate(graph: Graph, **options) -> np.ndarray:
     o = _options(**options)
     _check(lib().isg_debug_emulate(graph, ctypes.byref(o), g.ctypes.data))
     return g
+
+
+def isg_debug_emulate_planted(graph: Graph, site: int, delta: int, **options):
+    """The host emulation with `delta` added to the field constant of internal site `site` (a
+    planted program mistake). Returns (status, word, message, table): the status the library
+    reports for the walk's self-check word, the word, isg_last_error's message and the table."""
+    g = np.zeros(table_shape(graph), dtype=np.int64)
+    o = _options(**options)
+    w = ctypes.c_uint32()
+    st = lib().isg_debug_emulate_planted(graph, ctypes.byref(o), site, delta, g.ctypes.data, ctypes.byref(w))
+    return st, w.value, (isg_last_error() if st else ""), g
 
 
 def isg_probe_peaks(stream=None) -> dict:

@@ -144,3 +144,28 @@ def test_smoke_calls_are_valid_plans(isg):
     assert isg.isg_debug_plan(gh)["small"] == 0
     p = isg.isg_split_plan(gh, 0xF0)
     assert p["boundary"] == 0xF0 and p["components"] == 2
+
+
+def test_self_check_word_reported_through_the_status_path(isg):
+    """The kernels' self-check (each walk's tracked last bin against its recomputation from
+    scratch) on the host emulation, with a mistake planted in the program: a wrong field constant
+    on the spin at the top inner position, which flips once per walk, must set bit 0 of the word,
+    and the library must report that word as ISG_ERR_INTERNAL with the message that the
+    host-output calls and isg_device_status give for it. Without a planted mistake the same walk
+    reports nothing and gives the oracle's table."""
+    lat = w.with_random_couplings(w.square(4, 5, True), w.SplitMix64(1), (-1, 1))
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    opt = dict(low_bits=3, inner_bits=9)
+    plan = isg.isg_debug_plan(g, **opt)
+    top = plan["q"] - 1
+    st, word, msg, tab = isg.isg_debug_emulate_planted(g, top, 0, **opt)
+    assert (st, word, msg) == (0, 0, "")
+    assert np.array_equal(tab, oracle.g_masks(lat.n, lat.edges))
+    for delta in (plan["G"], -plan["G"], 3 * plan["G"]):
+        st, word, msg, _ = isg.isg_debug_emulate_planted(g, top, delta, **opt)
+        assert st == 8 and word & 1, delta
+        assert "self-check failed" in msg and "tracked bin differed from its recomputation" in msg
+    # the same report through isg_debug_emulate's own path (a graph whose walk is consistent)
+    with pytest.raises(isg.IsgError) as ei:
+        isg.isg_debug_emulate(isg.isg_graph_create(lat.n, lat.edges), shard_bits=lat.n + 1)
+    assert ei.value.status == 1

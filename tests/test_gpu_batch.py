@@ -113,31 +113,34 @@ def test_autotuned_batch(isg, cuda):
     b1.close()
 
 
+@pytest.mark.slow
 def test_ea_4096_batch(isg, cuda):
     """The 4096 Edwards-Anderson +-J instances (4x4, 4x5, 5x5, 5x6 periodic, equal shares) in one
-    prepared batch: every table by invariants; a sample of each shape bit for bit against the
-    oracle; all instances equal to per-instance isg_enumerate."""
-    import torch
+    prepared batch, autotuned as in the benchmark, and in a prepared batch with split = 1 (the 5x6
+    instances by split launches): every one of the 4096 tables of both, bin for bin, equals the
+    oracle's frontier programme (sites renumbered along the short side, which leaves g unchanged;
+    instances spread over the host cores)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from relabel import short_side_fastest
     lats = w.ea_instances()
     hs = [isg.isg_graph_create(l.n, l.edges) for l in lats]
-    b = isg.Batch(hs)
-    b.run()
-    b.status()
-    tabs = [b.table(k) for k in range(len(lats))]
-    for l, t in zip(lats, tabs):
-        g = t.cpu().numpy()
-        assert int(g.sum()) == 1 << l.n
-        assert np.array_equal(g, g[:, ::-1])
-    seen = {}
-    for k, l in enumerate(lats):
-        key = l.n
-        if seen.get(key, 0) >= (1 if key == 30 else 3):
-            continue
-        seen[key] = seen.get(key, 0) + 1
-        assert np.array_equal(tabs[k].cpu().numpy(), oracle.g_masks(l.n, l.edges, threads=THREADS)), l.name
-    one = torch.zeros(1, dtype=torch.int64, device=cuda)
-    for k, (l, h) in enumerate(zip(lats, hs)):
-        ref = torch.zeros(isg.table_shape(h), dtype=torch.int64, device=cuda)
-        isg.isg_enumerate(h, ref)
-        assert torch.equal(ref, tabs[k]), l.name
-    b.close()
+    got = []
+    for opts in (dict(autotune=1), dict(split=1)):
+        b = isg.Batch(hs, **opts)
+        b.run()
+        b.status()
+        got.append([b.table(k).cpu().numpy() for k in range(len(lats))])
+        b.close()
+
+    def ref(l):
+        r = short_side_fastest(l)
+        return oracle.g_frontier(r.n, r.edges, max_active=20)
+    with ThreadPoolExecutor(max_workers=THREADS) as ex:
+        refs = list(ex.map(ref, lats))
+    shapes = set()
+    for k, (l, r) in enumerate(zip(lats, refs)):
+        assert int(r.sum()) == 1 << l.n
+        assert np.array_equal(got[0][k], r), l.name
+        assert np.array_equal(got[1][k], r), l.name
+        shapes.add(l.n)
+    assert shapes == {16, 20, 25, 30}

@@ -171,8 +171,28 @@ def test_cubic_3x3x4_full_invariants_and_shards(isg, cuda):
     assert (tot <= full).all()
 
 
+@pytest.mark.slow
+def test_cubic_3x3x4_full_against_popcount_oracle(isg, cuda):
+    """3x3x4 simple cubic torus, N = 36, in the benchmark's autotuned plan, and by split-and-convolve:
+    every bin of both tables equals the popcount oracle's table over all 2^36 configurations (O1 on
+    all host cores; minutes of CPU time). The oracle's frontier programme cannot reach this torus
+    (its cross-sections hold 2 x 9 or 2 x 12 sites), so the full enumeration is the pin."""
+    import torch
+    lat = w.cubic(3, 3, 4, True)
+    got = gpu_table(isg, cuda, lat, autotune=1)
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    split = torch.zeros(isg.table_shape(g), dtype=torch.int64, device=cuda)
+    isg.isg_enumerate_split(g, split)
+    ref = oracle.g_masks(lat.n, lat.edges, threads=THREADS)
+    assert np.array_equal(got, ref)
+    assert np.array_equal(split.cpu().numpy(), ref)
+    isg.isg_device_status()
+
+
 def test_largest_default_size_n40(isg, cuda):
-    """N = 40 (the default max_spins): 2^40 configurations; invariants at full size."""
+    """N = 40 (the default max_spins): 2^40 configurations; invariants at full size (the 5x8
+    torus with four coupling values is beyond the oracle's reach within a test: 2^40 popcount
+    visits, and a frontier of two 8-site rows over 5.6k bins)."""
     lat = w.with_random_couplings(w.square(5, 8, True), w.SplitMix64(40), (-2, -1, 1, 2))
     check_invariants(gpu_table(isg, cuda, lat), 40)
 
@@ -203,3 +223,23 @@ def test_checkpoint_and_resume(isg, cuda, tmp_path):
     resumed = np.load(tmp_path / "checkpoint.npy")
     isg.isg_enumerate(g, resumed, shard_bits=4, shard_lo=5, shard_hi=16, accumulate=1)
     assert np.array_equal(resumed, oracle.g_masks(lat.n, lat.edges, threads=THREADS))
+
+
+def test_device_status_clean_after_device_output_calls(isg, cuda):
+    """Device-output calls record their kernels' self-check in the device's word: after a run of
+    them (the Gray walk with and without symmetry, split-and-convolve, the no-allocation call) the
+    word is clear, isg_device_status reports it so, and the tables equal the oracle's."""
+    import torch
+    isg.isg_device_status(clear=True)
+    lat = w.with_random_couplings(w.triangular(4, 6, True), w.SplitMix64(31), (-2, -1, 1, 2))
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    ref = oracle.g_masks(lat.n, lat.edges, threads=THREADS)
+    outs = [torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=cuda) for _ in range(4)]
+    isg.isg_enumerate(gh, outs[0])
+    isg.isg_enumerate(gh, outs[1], symmetry=1)
+    isg.isg_enumerate_split(gh, outs[2])
+    isg.isg_enumerate_noalloc(gh, outs[3])
+    isg.isg_device_status()
+    for o in outs:
+        assert np.array_equal(o.cpu().numpy(), ref)
+    isg.isg_device_status(clear=False)

@@ -94,6 +94,33 @@ def test_mix_with_split_and_symmetry_equals_alone(isg, cuda):
     srv.close()
 
 
+@pytest.mark.parametrize("opts", [{}, dict(symmetry=1)], ids=["every-configuration", "symmetry"])
+def test_largest_requests_against_frontier_oracle(isg, cuda, opts):
+    """Requests of N = 37 and 38, the top of the request stream's range (square and triangular,
+    periodic and free, simple cubic free, J in {-2,-1,1,2}), served in one mix: every table equals
+    the oracle's frontier programme (sites renumbered along the short side). Periodic cubic
+    requests of this size are beyond the frontier's reach (cross-sections of 2 x 8 sites)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from relabel import short_side_fastest
+    rng = w.SplitMix64(3738)
+    lats = [w.induced_lattice(kind, n, per, rng) for n in (37, 38) for kind in ("square", "triangular")
+            for per in (True, False)] + [w.induced_lattice("cubic", n, False, rng) for n in (37, 38)]
+    srv = isg.Server(step_ms=5.0, **opts)
+    tickets = [srv.submit(isg.isg_graph_create(l.n, l.edges)) for l in lats]
+
+    def ref(l):
+        r = short_side_fastest(l)
+        return oracle.g_frontier(r.n, r.edges, max_active=20)
+    with ThreadPoolExecutor(max_workers=THREADS) as ex:
+        refs = list(ex.map(ref, lats))
+    for t, l, r in zip(tickets, lats, refs):
+        srv.wait(t, 120000)
+        g, _ = srv.result(t)
+        assert int(r.sum()) == 1 << l.n
+        assert np.array_equal(g, r), l.name
+    srv.close()
+
+
 def test_server_rejects_bad_split_ratio(isg, cuda):
     with pytest.raises(isg.IsgError, match="INVALID"):
         isg.Server(split_work_ratio=1.5)
@@ -140,4 +167,37 @@ def test_limits_cancel_timeout(isg, cuda):
     assert np.array_equal(srv.result(t2)[0], alone(isg, small))
     with pytest.raises(isg.IsgError):
         srv.poll(t1)                                        # cancelled ticket is gone
+    srv.close()
+
+
+@pytest.mark.parametrize("where", [1, 2], ids=["before-enqueue", "after-launch"])
+def test_host_side_step_failure_releases_slots(isg, cuda, where):
+    """A host-side failure of an engine step (injected on the host with isg_debug_server_inject; no
+    GPU fault): the admitted requests with tiles left fail with ISG_ERR_CUDA, every other request
+    finishes with its exact table, every arena slot comes back once no step in flight writes into
+    it (no admitted request, no open ticket), and the server keeps serving."""
+    lats = [w.with_random_couplings(w.square(5, 7, True), w.SplitMix64(60 + k), (-1, 1)) for k in range(6)]
+    srv = isg.Server(max_inflight=2, arena_bytes=1 << 20, step_ms=0.5)
+    tickets = [(srv.submit(isg.isg_graph_create(l.n, l.edges)), l) for l in lats]
+    srv.inject_failure(where)
+    failed = 0
+    for t, lat in tickets:
+        srv.wait(t, 60000)
+        try:
+            g, _ = srv.result(t)
+        except isg.IsgError as e:
+            assert e.status == 4 and "injected" in str(e), str(e)
+            failed += 1
+            continue
+        assert np.array_equal(g, alone(isg, lat)), lat.name
+    assert failed >= 1
+    t0 = time.time()
+    while (srv.stats()["admitted"] or srv.stats()["tickets"]) and time.time() - t0 < 10:
+        time.sleep(0.01)
+    st = srv.stats()
+    assert st["admitted"] == 0 and st["tickets"] == 0, st
+    again = w.square(4, 5, True)
+    t = srv.submit(isg.isg_graph_create(again.n, again.edges))
+    srv.wait(t, 60000)
+    assert np.array_equal(srv.result(t)[0], oracle.g_masks(again.n, again.edges))
     srv.close()

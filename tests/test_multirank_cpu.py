@@ -1,7 +1,9 @@
-"""Sharding across ranks on the CPU (gloo, world size 2): each rank enumerates its shard of the
-configuration space with the host emulation of the GPU walk (the same planner and program as the
-CUDA kernels), the int64 tables are summed with an all-reduce, and the sum equals the oracle's
-full table. This is the exchange a multi-GPU run of one large graph would make."""
+"""One graph over several ranks on the CPU (gloo, world sizes 2 and 3): each rank runs the host
+emulation of isg_enumerate_rank -- its share of the configuration space from isg_rank_shards,
+walked by the same planner and program as the CUDA kernels, optionally the spin-(N-1)-up half
+with its mirror -- and one int64 all-reduce of the tables gives the oracle's full table. This is
+the exchange of a multi-GPU run of one large graph (the paper's outer-loop split over processes
+with a gather at the root, Sec. 3d)."""
 import os
 import socket
 
@@ -22,7 +24,7 @@ def _free_port():
     return port
 
 
-def _rank_main(rank, world, port, result_path, symmetric=False):
+def _rank_main(rank, world, port, result_path, symmetric):
     import sys
     sys.path.insert(0, ROOT)
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
@@ -31,31 +33,32 @@ def _rank_main(rank, world, port, result_path, symmetric=False):
     import oracle
     lat = w.with_random_couplings(w.triangular(4, 4, True), w.SplitMix64(77), (-2, -1, 1, 2))
     g = isg.isg_graph_create(lat.n, lat.edges)
-    shard_bits = 3                                   # 8 shards dealt round-robin to the ranks
-    # symmetric: only the shards with spin N-1 up (the top shard bit), the rest from the mirror
-    first = (1 << (shard_bits - 1)) if symmetric else 0
-    part = np.zeros(isg.table_shape(g), dtype=np.int64)
-    for shard in range(first + rank, 1 << shard_bits, world):
-        part += isg.isg_debug_emulate(g, shard_bits=shard_bits, shard_lo=shard, shard_hi=shard + 1)
+    part = isg.isg_debug_emulate_rank(g, rank, world, symmetry=int(symmetric))
+    bits, lo, hi = isg.isg_rank_shards(lat.n, rank, world, symmetric)
+    shares = [None] * world
+    dist.all_gather_object(shares, (bits, lo, hi))
     t = torch.from_numpy(part)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     if rank == 0:
-        whole = t.numpy()
-        if symmetric:                                # the global flip maps (E, M) to (E, -M)
-            whole = whole + whole[:, ::-1]
-        ok = np.array_equal(whole, oracle.g_masks(lat.n, lat.edges))
+        # the ranks' shares tile the space (or its upper half) without gaps or overlaps
+        first = (1 << (bits - 1)) if symmetric else 0
+        tiled = all(shares[r][2] == shares[r + 1][1] for r in range(world - 1)) and \
+            shares[0][1] == first and shares[-1][2] == 1 << bits
+        ok = tiled and np.array_equal(t.numpy(), oracle.g_masks(lat.n, lat.edges))
         with open(result_path, "w") as f:
-            f.write("ok" if ok else "mismatch")
+            f.write("ok" if ok else f"mismatch (tiled={tiled})")
     dist.barrier()
     dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("world", [2, 3])
 @pytest.mark.parametrize("symmetric", [False, True], ids=["whole", "half-and-mirror"])
-def test_two_rank_shards_sum_to_the_whole(tmp_path, isg, symmetric):
-    """Whole: all 8 shards over the two ranks. Half-and-mirror: only the 4 shards with spin N-1 up,
-    summed, then completed by the M -> -M mirror (the symmetry halving of a multi-GPU run)."""
+def test_ranks_sum_to_the_whole(tmp_path, isg, world, symmetric):
+    """Whole: every configuration over the ranks. Half-and-mirror: each rank its shards of the
+    spin-(N-1)-up half plus their M -> -M mirror; the all-reduced sum is again the full table."""
     import oracle
     oracle.build()
     out = str(tmp_path / "result.txt")
-    mp.start_processes(_rank_main, args=(2, _free_port(), out, symmetric), nprocs=2, join=True, start_method="spawn")
+    mp.start_processes(_rank_main, args=(world, _free_port(), out, symmetric), nprocs=world, join=True,
+                       start_method="spawn")
     assert open(out).read() == "ok"

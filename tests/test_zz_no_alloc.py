@@ -41,3 +41,26 @@ def test_noalloc_small_graph_and_accumulate(isg, cuda):
     isg.isg_enumerate_noalloc(gh, got, shard_bits=1, shard_lo=1, shard_hi=2, accumulate=1)
     torch.cuda.synchronize()
     assert torch.equal(got, want)
+
+
+def test_noalloc_honours_a_cached_autotune_choice(isg, cuda):
+    """autotune = 1 applies the choice isg_autotune cached for the graph (no timing inside the call,
+    since timing allocates); on a graph never tuned it falls back to the planner's defaults. Both
+    give isg_enumerate's table."""
+    import torch
+    lat = w.square(6, 6, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    isg.isg_autotune(gh)
+    want = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=cuda)
+    isg.isg_enumerate(gh, want, autotune=1)
+    got = torch.full(isg.table_shape(gh), 3, dtype=torch.int64, device=cuda)
+    isg.isg_enumerate_noalloc(gh, got, autotune=1)
+    fresh = w.with_random_couplings(w.square(5, 6, True), w.SplitMix64(23), (-1, 1))
+    gf = isg.isg_graph_create(fresh.n, fresh.edges)
+    want_f = torch.zeros(isg.table_shape(gf), dtype=torch.int64, device=cuda)
+    isg.isg_enumerate(gf, want_f)
+    got_f = torch.zeros_like(want_f)
+    isg.isg_enumerate_noalloc(gf, got_f, autotune=1)
+    torch.cuda.synchronize()
+    assert torch.equal(got, want) and torch.equal(got_f, want_f)
+    isg.isg_device_status()
