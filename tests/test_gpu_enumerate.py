@@ -237,7 +237,7 @@ def test_device_status_clean_after_device_output_calls(isg, cuda):
     outs = [torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=cuda) for _ in range(4)]
     isg.isg_enumerate(gh, outs[0])
     isg.isg_enumerate(gh, outs[1], symmetry=1)
-    isg.isg_enumerate_split(gh, outs[2])
+    isg.isg_enumerate_split(gh, outs[2], boundary=0x3F)           # the first row: one component of 18
     isg.isg_enumerate_noalloc(gh, outs[3])
     isg.isg_device_status()
     for o in outs:
