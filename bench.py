@@ -151,7 +151,7 @@ def run_isg(args):
     gh = isg.isg_graph_create(lat.n, lat.edges)
     shape = isg.table_shape(gh)
     tuned = isg.isg_autotune(gh, torch.cuda.current_stream())
-    tuned_fields = {k: tuned[k] for k in ("stride_residue", "block_threads", "ctas_per_sm")} if tuned else {}
+    tuned_fields = {k: tuned[k] for k in ("stride_residue", "block_threads", "ctas_per_sm", "lane_model")} if tuned else {}
     plan = isg.isg_debug_plan(gh, **tuned_fields)
     # --shard-bits k (profiling case): each step enumerates shard 0 of 2^k with q - k inner bits,
     # so the launch has the same number of warp tasks as the full one
@@ -260,7 +260,8 @@ def run_isg(args):
                        "parallelism": f"shard{world}" if sharded else f"replicas{world}",
                        "l2": "flushed between steps (256 MiB write)",
                        "plan": {k: plan[k] for k in ("q", "b", "tasks", "threads", "copies", "ctas_per_sm", "G",
-                                                     "n_e_compact", "stride")},
+                                                     "n_e_compact", "stride", "lane_model", "lane_cost",
+                                                     "lane_cost_index_order")},
                        "autotuned": tuned_fields},
             # the binding unit: one shared-memory reduction per configuration; the shared-memory
             # pipe executes one warp-wide (32-lane) reduction per clock per SM
@@ -765,17 +766,28 @@ def run_profile_case(args):
         for _ in range(args.warmup):
             call()
         res["fp64_ms"] = _event_ms(call, stream, args.steps)
-    elif args.profile_case == "cubic-enumerate":
-        # the full enumeration of the 3x3x4 torus, autotuned as in the benchmark's workloads
-        lat = workloads.cubic(3, 3, 4, True)
+    elif args.profile_case in ("cubic-enumerate", "torus-enumerate"):
+        # the full enumeration of the 3x3x4 (or 6x6) torus, autotuned as in the benchmark; with
+        # --shard-bits k, shard 0 of 2^k with q - k inner bits (the full launch's task count)
+        lat = workloads.cubic(3, 3, 4, True) if args.profile_case == "cubic-enumerate" else workloads.square(6, 6, True)
         gh = isg.isg_graph_create(lat.n, lat.edges)
         g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=dev)
         res["tuned"] = isg.isg_autotune(gh, stream)
-        res["plan"] = isg.isg_debug_plan(gh, **{k: res["tuned"][k] for k in ("stride_residue", "block_threads", "ctas_per_sm")})
+        tf = {k: res["tuned"][k] for k in ("stride_residue", "block_threads", "ctas_per_sm", "lane_model")}
+        res["plan"] = isg.isg_debug_plan(gh, **tf)
+        shard = {}
+        if args.shard_bits:
+            shard = dict(shard_bits=args.shard_bits, shard_lo=0, shard_hi=1,
+                         inner_bits=max(res["plan"]["b"], res["plan"]["q"] - args.shard_bits))
+            res["shard_plan"] = isg.isg_debug_plan(gh, **tf, **shard)
         for _ in range(args.warmup):
-            isg.isg_enumerate(gh, g, stream, autotune=1)
-        res["ms"] = _event_ms(lambda: isg.isg_enumerate(gh, g, stream, autotune=1), stream, args.steps)
-        res["configs_per_s"] = 2.0 ** 36 / (res["ms"] * 1e-3)
+            isg.isg_enumerate(gh, g, stream, autotune=1, **shard)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("isg_timed")
+        res["ms"] = _event_ms(lambda: isg.isg_enumerate(gh, g, stream, autotune=1, **shard), stream, args.steps)
+        torch.cuda.nvtx.range_pop()
+        res["configs_per_s"] = 2.0 ** (36 - args.shard_bits) / (res["ms"] * 1e-3)
+        isg.isg_device_status(stream)
     elif args.profile_case in ("split-torus6x6", "split-torus7x7", "split-cubic3x3x4"):
         lat = {"split-torus6x6": workloads.square(6, 6, True), "split-torus7x7": workloads.square(7, 7, True),
                "split-cubic3x3x4": workloads.cubic(3, 3, 4, True)}[args.profile_case]
@@ -801,7 +813,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target seconds of the oracle sample")
     ap.add_argument("--serving", action="store_true", help="run the request-stream (serving) benchmark instead")
-    ap.add_argument("--profile-case", choices=("ea-batch", "cubic-thermo", "small-thermo", "cubic-enumerate", "split-torus6x6",
+    ap.add_argument("--profile-case", choices=("ea-batch", "cubic-thermo", "small-thermo", "cubic-enumerate", "torus-enumerate",
+                                               "split-torus6x6",
                                                "split-torus7x7", "split-cubic3x3x4"),
                     default=None,
                     help="run only a small case of another kernel (for ncu captures)")
@@ -815,7 +828,8 @@ def main():
     ap.add_argument("--shard", action="store_true",
                     help="under torchrun: the ranks share the one torus (strong scaling, NCCL all-reduce per step)")
     ap.add_argument("--shard-bits", type=int, default=0,
-                    help="profiling case: enumerate only shard 0 of 2^k per step (not a benchmark line)")
+                    help="profiling case: enumerate only shard 0 of 2^k per step (not a benchmark line); also for "
+                         "the cubic-enumerate and torus-enumerate profile cases")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "isg":
         ap.error("at least 3 warm-up steps")

@@ -97,6 +97,14 @@ typedef struct {
                                 split-and-convolve plan (isg_enumerate_split) models less work than its
                                 full enumeration, a launch's fixed cost included, by a split launch inside
                                 the batch; the others go to the tile queue. Same tables either way. */
+    int32_t lane_model;      /* which spins carry the lane index of a warp (the five spins at internal
+                                positions q .. q+4, in which the 32 lanes of a warp task differ):
+                                0 = plan: for isg_enumerate, isg_enumerate_rank, isg_enumerate_noalloc
+                                and isg_autotune on graphs of at least 30 free spins, the set and the
+                                histogram row stride with the fewest shared-memory bank conflicts under
+                                a model of the warp reductions (cached per graph structure); otherwise
+                                as 2. 1 = that model for any graph and call. 2 = the five free spins
+                                after the inner ones in index order, stride by a fixed preference. */
 } isg_options;
 
 /* Fill *opt with the defaults (all planner choices, full range, overwrite). */

@@ -15,10 +15,13 @@ extern "C" {
 
 /*
  * The plan isg_enumerate would use for this graph and these options on a device with `sms`
- * multiprocessors (0 = 152). out[0..13] = small-kernel flag, inner bits q, low-block size b,
+ * multiprocessors (0 = 152). out[0..17] = small-kernel flag, inner bits q, low-block size b,
  * warp tasks, threads per CTA, histogram copies, CTAs per SM, tasks per flush round, grid,
  * shared-memory bytes per CTA, energy stride G, compact energy bins, bytes of the program that
- * isg_enumerate copies to the device, histogram row stride. Errors as isg_enumerate.
+ * isg_enumerate copies to the device, histogram row stride, whether the lane spins come from the
+ * bank-conflict model (options.lane_model), the model's expected shared-memory wavefronts per warp
+ * reduction of the plan and of the index order's lane spins (both x 10^6; 0 without the model),
+ * and the mask of the five lane spins (caller numbering). Errors as isg_enumerate.
  */
 ISG_API isg_status isg_debug_plan(const isg_graph* graph, const isg_options* opt, int32_t sms, int64_t* out);
 

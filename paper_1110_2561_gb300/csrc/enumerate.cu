@@ -330,16 +330,19 @@ static uint64_t graph_signature(const isg_graph& g) {
 }
 
 struct TunedShape {
-    int stride_residue = 0, block_threads = 0, ctas_per_sm = 0;
+    int stride_residue = 0, block_threads = 0, ctas_per_sm = 0, lane_model = 0;
 };
 
 static std::mutex g_tune_mu;
 static std::map<std::pair<int, uint64_t>, TunedShape> g_tune_cache;
 
-// Time one plan on its own scratch: one warm-up and three timed launches, best of three (ms).
-static float time_plan(const isg_graph& g, const isg_options& o, cudaStream_t s, int64_t* table, char* scratch) {
+// Time one plan on its own scratch, its warp tasks capped at max_tasks: one warm-up and three
+// timed launches, best of three (ms).
+static float time_plan(const isg_graph& g, const isg_options& o, cudaStream_t s, int64_t* table, char* scratch,
+                       uint64_t max_tasks) {
     const DeviceInfo d = device_info();
-    const Plan p = make_plan(g, o, d);
+    Plan p = make_plan(g, o, d, true);
+    p.n_tasks = std::min(p.n_tasks, max_tasks);
     const std::vector<uint64_t> blob = build_program(g, p);
     ISG_CUDA(cudaMemcpyAsync(scratch + 16, blob.data(), blob.size() * 8, cudaMemcpyHostToDevice, s));
     cudaEvent_t e0, e1;
@@ -363,6 +366,10 @@ static float time_plan(const isg_graph& g, const isg_options& o, cudaStream_t s,
     return best;
 }
 
+// Candidates: the index order's lane spins at five row-stride residues and the bank-conflict
+// model's lane spins at its own stride (graphs of at least 30 free spins), each at three launch
+// shapes. A trial runs the full plan with tasks 2^k times shorter (q - k inner bits), cut to the
+// full launch's task count, so it keeps the launch's shape at 1/2^k of its work.
 static TunedShape run_autotune(const isg_graph& g, const isg_options& base, cudaStream_t s) {
     TunedShape best;
     if (g.n < 30) return best;
@@ -370,9 +377,10 @@ static TunedShape run_autotune(const isg_graph& g, const isg_options& base, cuda
     isg_options o0 = base;                          // the full launch at the planner's own split
     o0.autotune = 0;
     o0.shard_bits = 0; o0.shard_lo = 0; o0.shard_hi = 0; o0.accumulate = 0; o0.inner_bits = 0;
-    const Plan p0 = make_plan(g, o0, d);
+    if (!o0.lane_model) o0.lane_model = 2;
+    const Plan p0 = make_plan(g, o0, d, true);
     if (p0.small) return best;
-    const int k = std::min(4, p0.q - p0.b);      // a shard of 1/2^k with q - k inner bits: same task count
+    const int k = std::min(4, p0.q - p0.b);
     if (k < 1) return best;
     const size_t table_bytes = sizeof(int64_t) * (size_t)public_bins(g);
     char* scratch = nullptr;
@@ -385,35 +393,46 @@ static TunedShape run_autotune(const isg_graph& g, const isg_options& base, cuda
     ISG_CUDA(cudaMemsetAsync(table, 0, table_bytes, s));
     static const int residues[] = {6, 13, 19, 5, 27};
     static const int shapes[][2] = {{512, 2}, {256, 4}, {1024, 1}};
+    std::vector<int> lane_models;
+    if (base.lane_model) lane_models.push_back(base.lane_model);
+    else {
+        lane_models.push_back(2);
+        if (g.n >= kLaneModelMinFree) lane_models.push_back(1);
+    }
     float best_ms = 1e30f;
-    for (int r : residues)
-        for (auto& sh : shapes) {
-            isg_options c = o0;
-            c.stride_residue = base.stride_residue ? base.stride_residue : r;
-            c.block_threads = base.block_threads ? base.block_threads : sh[0];
-            c.ctas_per_sm = base.ctas_per_sm ? base.ctas_per_sm : sh[1];
-            c.shard_bits = k;
-            c.shard_lo = 0;
-            c.shard_hi = 1;
-            c.inner_bits = p0.q - k;
-            c.accumulate = 1;                       // the scratch table just absorbs the counts
-            float ms;
-            try {
-                ms = time_plan(g, c, s, table, scratch);
-            } catch (const Error&) {
-                continue;                           // a shape this graph cannot take
+    for (int lm : lane_models) {
+        std::vector<int> rs;
+        if (base.stride_residue) rs.push_back(base.stride_residue);
+        else if (lm == 1) rs.push_back(0);          // the model's own stride
+        else rs.assign(std::begin(residues), std::end(residues));
+        for (int r : rs)
+            for (auto& sh : shapes) {
+                isg_options c = o0;
+                c.lane_model = lm;
+                c.stride_residue = r;
+                c.block_threads = base.block_threads ? base.block_threads : sh[0];
+                c.ctas_per_sm = base.ctas_per_sm ? base.ctas_per_sm : sh[1];
+                c.inner_bits = p0.q - k;
+                float ms;
+                try {
+                    ms = time_plan(g, c, s, table, scratch, p0.n_tasks);
+                } catch (const Error&) {
+                    continue;                       // a shape this graph cannot take
+                }
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best.stride_residue = c.stride_residue;
+                    best.block_threads = c.block_threads;
+                    best.ctas_per_sm = c.ctas_per_sm;
+                    best.lane_model = lm;
+                }
             }
-            if (ms < best_ms) {
-                best_ms = ms;
-                best.stride_residue = c.stride_residue;
-                best.block_threads = c.block_threads;
-                best.ctas_per_sm = c.ctas_per_sm;
-            }
-        }
+    }
     return best;
 }
 
 static void fill_tuned(isg_options& o, const TunedShape& t) {
+    if (!o.lane_model) o.lane_model = t.lane_model;
     if (!o.stride_residue && !o.bin_stride) o.stride_residue = t.stride_residue;
     if (!o.block_threads) o.block_threads = t.block_threads;
     if (!o.ctas_per_sm) o.ctas_per_sm = t.ctas_per_sm;

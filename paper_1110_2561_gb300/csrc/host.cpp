@@ -1,6 +1,7 @@
 // host.cpp -- graph model, options, planner, program blobs, errors and the host emulation of the
 // enumeration kernels (no CUDA calls in this file).
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <numeric>
@@ -100,12 +101,71 @@ static size_t blob_words(int n, int nc) {
     return kHeaderWords + (size_t)n * (sizeof(SiteRec) / 8) + (size_t)n * (nc - 1) + ((size_t)nc + 1) / 2;
 }
 
-Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d) {
+// Minimum-residual-degree greedy independent set of at most bmax spins among the free spins
+// 0 .. free-1 outside `excluded`: repeatedly take the candidate with the fewest neighbours among
+// the remaining candidates (ties: lowest index), then drop it and its neighbours. Sorted.
+static std::vector<int> low_block_spins(const isg_graph& g, int free, int bmax, uint64_t excluded) {
+    const int n = g.n;
+    std::vector<char> alive(free, 1);
+    for (int c = 0; c < free; ++c) if ((excluded >> c) & 1) alive[c] = 0;
+    std::vector<int> low;
+    while ((int)low.size() < bmax) {
+        int best = -1, best_deg = 1 << 30;
+        for (int c = 0; c < free; ++c) {
+            if (!alive[c]) continue;
+            int d = 0;
+            for (int o = 0; o < free; ++o) if (alive[o] && o != c && g.K[(size_t)c * n + o] != 0) ++d;
+            if (d < best_deg) { best_deg = d; best = c; }
+        }
+        if (best < 0) break;
+        low.push_back(best);
+        alive[best] = 0;
+        for (int o = 0; o < free; ++o) if (g.K[(size_t)best * n + o] != 0) alive[o] = 0;
+    }
+    std::sort(low.begin(), low.end());
+    return low;
+}
+
+// Inner bits q for a low block of b spins (see make_plan).
+static int inner_bits_for(const isg_options& o, int free, int b, int shards_log2) {
+    if (o.inner_bits > 0) {
+        const int q = o.inner_bits;
+        if (q < b || q > free - 5 || q > 26)
+            fail(ISG_ERR_INVALID, "inner_bits must satisfy low block <= q <= N - shard_bits - 5 and q <= 26");
+        return q;
+    }
+    // about 2^15 warp tasks (several per resident warp, so the dynamic queue balances), but at
+    // least 2^12 configurations per lane so the from-scratch start of a task stays negligible
+    int q = free - 5 - std::max(0, 15 - shards_log2);
+    int qmin = std::min(12, free - 5);
+    // small problems are latency-bound: spread them over >= 256 warp tasks where they allow it
+    if (free - 5 - qmin < 8) qmin = std::max(b, free - 5 - 8);
+    q = std::max(q, qmin);
+    q = std::min(q, 20);
+    q = std::min(q, free - 5);
+    return std::max(q, b);
+}
+
+// Internal order: the low block, the other inner spins, the five lane spins (positions q..q+4),
+// the remaining free spins, then the shard spins in the caller's order at the top.
+static void order_spins(Plan& p, int n, int free, const std::vector<int>& low, const int* lanes) {
+    std::vector<char> used(n, 0);
+    int pos = 0;
+    for (int l : low) { p.perm[pos++] = l; used[l] = 1; }
+    if (lanes) for (int k = 0; k < 5; ++k) used[lanes[k]] = 1;
+    for (int s = 0; s < free && pos < p.q; ++s) if (!used[s]) { p.perm[pos++] = s; used[s] = 1; }
+    if (lanes) for (int k = 0; k < 5; ++k) p.perm[pos++] = lanes[k];
+    for (int s = 0; s < free; ++s) if (!used[s]) p.perm[pos++] = s;
+    for (int s = free; s < n; ++s) p.perm[pos++] = s;
+}
+
+Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d, bool single_graph) {
     Plan p;
     const int n = g.n;
     if (n > o.max_spins)
         fail(ISG_ERR_TOO_LARGE, "graph has " + std::to_string(n) + " spins, more than max_spins = " +
                                     std::to_string(o.max_spins));
+    if (o.lane_model < 0 || o.lane_model > 2) fail(ISG_ERR_INVALID, "lane_model must be 0, 1 or 2");
     const int k = o.shard_bits;
     if (k < 0 || k > n) fail(ISG_ERR_INVALID, "shard_bits must lie in [0, N]");
     int64_t lo = o.shard_lo, hi = o.shard_hi;
@@ -134,52 +194,49 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d) {
     int bmax = o.low_bits > 0 ? o.low_bits : kMaxLow;
     if (bmax > kMaxLow) fail(ISG_ERR_INVALID, "low_bits must be <= 7");
     bmax = std::min(bmax, free - 5);
-    // Minimum-residual-degree greedy: repeatedly take the candidate with the fewest neighbours
-    // among the remaining candidates (ties: lowest index), then drop it and its neighbours.
-    std::vector<char> alive(free, 1);
-    std::vector<int> low;
-    while ((int)low.size() < bmax) {
-        int best = -1, best_deg = 1 << 30;
-        for (int c = 0; c < free; ++c) {
-            if (!alive[c]) continue;
-            int d = 0;
-            for (int o = 0; o < free; ++o) if (alive[o] && o != c && g.K[(size_t)c * n + o] != 0) ++d;
-            if (d < best_deg) { best_deg = d; best = c; }
-        }
-        if (best < 0) break;
-        low.push_back(best);
-        alive[best] = 0;
-        for (int o = 0; o < free; ++o) if (g.K[(size_t)best * n + o] != 0) alive[o] = 0;
-    }
-    std::sort(low.begin(), low.end());
+    std::vector<int> low = low_block_spins(g, free, bmax, 0);
     if (o.low_bits > 0 && (int)low.size() < o.low_bits)
         fail(ISG_ERR_INVALID, "no independent set of low_bits spins below the shard bits");
     p.b = (int)low.size();
-    {
-        std::vector<char> used(n, 0);
-        int pos = 0;
-        for (int l : low) { p.perm[pos++] = l; used[l] = 1; }
-        for (int s = 0; s < free; ++s) if (!used[s]) p.perm[pos++] = s;
-        for (int s = free; s < n; ++s) p.perm[pos++] = s;
-    }
-
-    // Inner bits.
     const int shards_log2 = [&] { int t = 0; while (((int64_t)1 << t) < (hi - lo)) ++t; return t; }();
-    if (o.inner_bits > 0) {
-        p.q = o.inner_bits;
-        if (p.q < p.b || p.q > free - 5 || p.q > 26)
-            fail(ISG_ERR_INVALID, "inner_bits must satisfy low block <= q <= N - shard_bits - 5 and q <= 26");
-    } else {
-        // about 2^15 warp tasks (several per resident warp, so the dynamic queue balances), but at
-        // least 2^12 configurations per lane so the from-scratch start of a task stays negligible
-        int q = free - 5 - std::max(0, 15 - shards_log2);
-        int qmin = std::min(12, free - 5);
-        // small problems are latency-bound: spread them over >= 256 warp tasks where they allow it
-        if (free - 5 - qmin < 8) qmin = std::max(p.b, free - 5 - 8);
-        q = std::max(q, qmin);
-        q = std::min(q, 20);
-        q = std::min(q, free - 5);
-        p.q = std::max(q, p.b);
+    p.q = inner_bits_for(o, free, p.b, shards_log2);
+    order_spins(p, n, free, low, nullptr);
+
+    // Histogram geometry: the program's bytes and the widest row stride that fits shared memory.
+    std::vector<int32_t> w;
+    weight_classes(g, w);
+    const size_t prog_bytes = blob_words(n, (int)w.size()) * 8;
+    int max_stride = n + 1;
+    while (max_stride < n + 32 && prog_bytes + (size_t)g.n_e_c * (max_stride + 1) * 4 <= d.smem_optin) ++max_stride;
+
+    // Lane spins by the bank-conflict model (lanes.cpp): the index order's five spins at q..q+4
+    // are one candidate; another set moves to those positions, with the low block and the other
+    // inner spins chosen among the rest.
+    const bool use_model =
+        o.lane_model == 1 || (o.lane_model == 0 && single_graph && o.autotune && free >= kLaneModelMinFree);
+    LaneChoice lc;
+    if (use_model && prog_bytes + (size_t)g.n_e_c * (n + 1) * 4 <= d.smem_optin) {
+        const uint64_t pool = free >= 64 ? ~0ull : ((1ull << free) - 1);
+        lc = choose_lanes(g, pool, &p.perm[p.q], max_stride);
+    }
+    if (lc.valid) {
+        p.lane_model = true;
+        p.lane_cost = lc.cost;
+        p.lane_cost_index_order = lc.cost_index_order;
+        uint64_t lane_mask = 0;
+        for (int t = 0; t < 5; ++t) lane_mask |= 1ull << lc.spins[t];
+        bool same = true;
+        for (int t = 0; t < 5; ++t) same = same && p.perm[p.q + t] == lc.spins[t];
+        if (!same) {
+            std::vector<int> low2 = low_block_spins(g, free, bmax, lane_mask);
+            if (o.low_bits > 0 && (int)low2.size() < o.low_bits) {
+                p.lane_model = false;              // the forced low block needs the lane spins
+            } else {
+                p.b = (int)low2.size();
+                p.q = inner_bits_for(o, free, p.b, shards_log2);
+                order_spins(p, n, free, low2, lc.spins);
+            }
+        }
     }
     const int pk = free - p.q;               // outer bits below the shard bits
     p.prefix_base = (uint64_t)lo << pk;
@@ -189,10 +246,9 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d) {
     p.threads = o.block_threads > 0 ? o.block_threads : 512;
     if (p.threads % 32 || p.threads < 32 || p.threads > 1024) fail(ISG_ERR_INVALID, "block_threads must be a multiple of 32 in [32, 1024]");
     const int warps = p.threads / 32;
-    std::vector<int32_t> w;
-    weight_classes(g, w);
-    const size_t prog_bytes = blob_words(n, (int)w.size()) * 8;
-    p.stride = choose_stride(g, o.bin_stride, o.stride_residue);
+    // row stride: the model's pick for its lane spins, unless the caller fixes a stride or residue
+    if (p.lane_model && o.bin_stride == 0 && o.stride_residue == 0) p.stride = lc.stride;
+    else p.stride = choose_stride(g, o.bin_stride, o.stride_residue);
     if (prog_bytes + (size_t)g.n_e_c * p.stride * 4 > d.smem_optin && o.bin_stride == 0) p.stride = n + 1;
     const size_t bin_bytes = (size_t)g.n_e_c * p.stride * 4;
     if (prog_bytes + bin_bytes > d.smem_optin)
@@ -308,7 +364,7 @@ std::shared_ptr<const PlannedProgram> planned_program(const isg_graph& g, const 
             if (e.first == key) return e.second;
     }
     auto pp = std::make_shared<PlannedProgram>();
-    pp->plan = make_plan(g, o, d);
+    pp->plan = make_plan(g, o, d, true);
     pp->blob = build_program(g, pp->plan);
     std::lock_guard<std::mutex> lk(g.plan_mu);
     if (g.plan_cache.size() >= 8) g.plan_cache.erase(g.plan_cache.begin());
@@ -349,7 +405,7 @@ static void emulate_tasks(const ProgView& v, const Plan& p, std::vector<uint32_t
 static unsigned int emulate(const isg_graph& g, isg_options o, int plant_site, int32_t plant_delta, int64_t* g_out) {
     const bool sym = o.symmetry != 0;
     if (sym) { o.shard_bits = 1; o.shard_lo = 1; o.shard_hi = 2; }     // spin N-1 up only
-    Plan p = make_plan(g, o, DeviceInfo{});
+    Plan p = make_plan(g, o, DeviceInfo{}, true);
     std::vector<uint64_t> blob = build_program(g, p);
     if (plant_site >= 0) {
         if (p.small || plant_site >= g.n) fail(ISG_ERR_INVALID, "no site record to plant a mistake in");
@@ -494,7 +550,7 @@ isg_status isg_debug_plan(const isg_graph* g, const isg_options* opt, int32_t sm
         isg_options o = resolve_options(opt);
         DeviceInfo d;
         if (sms > 0) d.sms = sms;
-        Plan p = make_plan(*g, o, d);
+        Plan p = make_plan(*g, o, d, true);
         out[0] = p.small;
         out[1] = p.q;
         out[2] = p.b;
@@ -509,6 +565,12 @@ isg_status isg_debug_plan(const isg_graph* g, const isg_options* opt, int32_t sm
         out[11] = g->n_e_c;
         out[12] = (int64_t)build_program(*g, p).size() * 8;
         out[13] = p.stride;
+        out[14] = p.lane_model;
+        out[15] = (int64_t)std::llround(p.lane_cost * 1e6);
+        out[16] = (int64_t)std::llround(p.lane_cost_index_order * 1e6);
+        int64_t lanes = 0;
+        if (!p.small) for (int t = 0; t < 5; ++t) lanes |= (int64_t)1 << p.perm[p.q + t];
+        out[17] = lanes;
     });
 }
 

@@ -94,7 +94,24 @@ struct Plan {
     int threads = 512, copies = 1, ctas_per_sm = 2, flush_rounds = 1;
     int grid = 0;
     size_t smem_bytes = 0;
+    bool lane_model = false;   // lane spins and stride chosen by the bank-conflict model
+    double lane_cost = 0;      // the model's expected wavefronts per reduction (0 when not used)
+    double lane_cost_index_order = 0;
 };
+
+// The lane spins of a plan chosen by the bank-conflict model (lanes.cpp).
+struct LaneChoice {
+    bool valid = false;
+    int spins[5] = {0, 0, 0, 0, 0};  // caller spins for lane bits 0..4 (internal positions q..q+4)
+    int stride = 0;                  // histogram row stride the model picks with them
+    double cost = 0;                 // expected shared-memory wavefronts per warp reduction
+    double cost_index_order = 0;     // the same for the index order's lane spins (at its best stride)
+};
+
+// Choose five lane spins among `pool` (a mask of free spins) and a row stride in [N + 1,
+// max_stride] with the fewest expected wavefronts per warp reduction; `baseline` (the index
+// order's lane spins) is always a candidate. Cached per graph structure, pool and stride limit.
+LaneChoice choose_lanes(const isg_graph& g, uint64_t pool, const int* baseline, int max_stride);
 
 struct DeviceInfo {
     int sms = 152;
@@ -102,8 +119,15 @@ struct DeviceInfo {
     size_t smem_per_sm = 233472;
 };
 
-// Plan an enumeration of graph g under options o on a device with properties d.
-Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d);
+// Free spins from which autotuning considers lane spins chosen by the conflict model (smaller
+// enumerations take less time than the model's search).
+constexpr int kLaneModelMinFree = 30;
+
+// Plan an enumeration of graph g under options o on a device with properties d. single_graph:
+// the plan serves one graph's call (isg_enumerate and its relatives), where options.lane_model
+// = 0 with autotune set may use the lane model; batches and the server plan thousands of graphs
+// and keep the index order unless options.lane_model is 1.
+Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d, bool single_graph = false);
 
 // Build the program blob (64-bit words) of graph g for a plan: spins in internal order.
 std::vector<uint64_t> build_program(const isg_graph& g, const Plan& p);

@@ -68,7 +68,7 @@ extern "C" isg_status isg_enumerate_noalloc(const isg_graph* graph, void* stream
         // autotune: the cached choice for this graph, if it was tuned before (timing allocates)
         if (o.autotune) apply_cached_autotune(*graph, o);
         const DeviceInfo d = device_info();
-        const Plan p = make_plan(*graph, o, d);
+        const Plan p = make_plan(*graph, o, d, true);
         const std::vector<uint64_t> blob = build_program(*graph, p);
         const size_t blob_bytes = blob.size() * 8;
         if (blob_bytes > kNoallocScratchBytes - kNoallocProgramOffset)

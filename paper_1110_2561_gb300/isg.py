@@ -33,7 +33,7 @@ class isg_options(ctypes.Structure):
         ("shard_lo", ctypes.c_int64), ("shard_hi", ctypes.c_int64),
         ("accumulate", ctypes.c_int32), ("warp_aggregate", ctypes.c_int32),
         ("stride_residue", ctypes.c_int32), ("autotune", ctypes.c_int32),
-        ("symmetry", ctypes.c_int32), ("split", ctypes.c_int32)]
+        ("symmetry", ctypes.c_int32), ("split", ctypes.c_int32), ("lane_model", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -625,12 +625,16 @@ def isg_specific_heat_peak(g, graph: Graph, h: float, T_lo: float, T_hi: float, 
 
 
 def isg_debug_plan(graph: Graph, sms: int = 0, **options) -> dict:
-    out = np.zeros(14, dtype=np.int64)
+    out = np.zeros(18, dtype=np.int64)
     o = _options(**options)
     _check(lib().isg_debug_plan(graph, ctypes.byref(o), sms, out.ctypes.data))
     keys = ("small", "q", "b", "tasks", "threads", "copies", "ctas_per_sm", "flush_rounds", "grid", "smem_bytes",
-            "G", "n_e_compact", "blob_bytes", "stride")
-    return dict(zip(keys, (int(x) for x in out)))
+            "G", "n_e_compact", "blob_bytes", "stride", "lane_model", "lane_cost", "lane_cost_index_order",
+            "lane_mask")
+    d = dict(zip(keys, (int(x) for x in out)))
+    d["lane_cost"] /= 1e6
+    d["lane_cost_index_order"] /= 1e6
+    return d
 
 
 def isg_debug_emulate(graph: Graph, **options) -> np.ndarray:

@@ -96,7 +96,10 @@ EMU_GRAPHS = [w.square(4, 4, True), w.square(4, 4, False), w.square(3, 5, True),
 EMU_PLANS = [{}, dict(inner_bits=6), dict(low_bits=1, inner_bits=3), dict(low_bits=3, inner_bits=5),
              dict(low_bits=2, inner_bits=2), dict(shard_bits=2, shard_lo=1, shard_hi=3), dict(shard_bits=4, shard_lo=9, shard_hi=10),
              dict(bin_stride=64), dict(bin_stride=100, low_bits=4), dict(low_bits=7, inner_bits=8),
-             dict(symmetry=1), dict(symmetry=1, low_bits=3, inner_bits=4)]
+             dict(symmetry=1), dict(symmetry=1, low_bits=3, inner_bits=4),
+             dict(lane_model=1), dict(lane_model=1, inner_bits=6), dict(lane_model=1, low_bits=3, inner_bits=5),
+             dict(lane_model=1, shard_bits=2, shard_lo=1, shard_hi=3), dict(lane_model=1, symmetry=1),
+             dict(lane_model=1, stride_residue=13), dict(lane_model=2, autotune=0)]
 
 
 @pytest.mark.parametrize("lat", EMU_GRAPHS, ids=lambda l: l.name)
@@ -168,4 +171,29 @@ def test_self_check_word_reported_through_the_status_path(isg):
     # the same report through isg_debug_emulate's own path (a graph whose walk is consistent)
     with pytest.raises(isg.IsgError) as ei:
         isg.isg_debug_emulate(isg.isg_graph_create(lat.n, lat.edges), shard_bits=lat.n + 1)
+    assert ei.value.status == 1
+
+
+def test_lane_model_plans(isg):
+    """The bank-conflict model's lane spins (options.lane_model = 1): five spins outside the low
+    block, a stride in [N + 1, N + 32], and a modelled cost no worse than the index order's. On the
+    6x6 torus a spin with its four neighbours makes every warp reduction conflict-free under the
+    model; on the 3x3x4 torus the model's set is clearly better than the index order's."""
+    for lat, want in ((w.square(6, 6, True), 1.0), (w.cubic(3, 3, 4, True), None)):
+        g = isg.isg_graph_create(lat.n, lat.edges)
+        p = isg.isg_debug_plan(g, lane_model=1)
+        q = isg.isg_debug_plan(g, lane_model=2)
+        assert p["lane_model"] == 1 and q["lane_model"] == 0
+        lanes = [i for i in range(lat.n) if (p["lane_mask"] >> i) & 1]
+        assert len(lanes) == 5
+        assert lat.n + 1 <= p["stride"] <= lat.n + 32
+        assert p["lane_cost"] <= p["lane_cost_index_order"]
+        if want is not None:
+            assert p["lane_cost"] == want
+        else:
+            assert p["lane_cost"] < 0.95 * p["lane_cost_index_order"]
+        # the index order keeps the five free spins after the inner ones
+        assert [i for i in range(lat.n) if (q["lane_mask"] >> i) & 1] != lanes or p["lane_cost"] == p["lane_cost_index_order"]
+    with pytest.raises(isg.IsgError) as ei:
+        isg.isg_debug_plan(g, lane_model=3)
     assert ei.value.status == 1

@@ -73,7 +73,8 @@ PLANS = [dict(inner_bits=6), dict(low_bits=1, inner_bits=4), dict(low_bits=4, in
          dict(block_threads=64, copies=1), dict(block_threads=1024, copies=16), dict(block_threads=256, copies=3),
          dict(flush_tasks=1), dict(ctas_per_sm=1, flush_tasks=1, block_threads=96, copies=2), dict(low_bits=2, inner_bits=2),
          dict(warp_aggregate=1), dict(bin_stride=64), dict(bin_stride=33, warp_aggregate=1, copies=1),
-         dict(symmetry=1), dict(symmetry=1, low_bits=3, inner_bits=6, block_threads=128)]
+         dict(symmetry=1), dict(symmetry=1, low_bits=3, inner_bits=6, block_threads=128),
+         dict(lane_model=1), dict(lane_model=1, symmetry=1), dict(lane_model=1, inner_bits=9, stride_residue=19)]
 
 
 @pytest.mark.parametrize("kw", PLANS, ids=lambda k: ",".join(f"{a}={b}" for a, b in k.items()))
@@ -198,18 +199,25 @@ def test_largest_default_size_n40(isg, cuda):
 
 
 def test_autotune_torus_6x6(isg, cuda):
-    """The autotuner's choice (cached per graph) gives the same table as the oracle's frontier
-    programme; a second isg_autotune call returns the cached fields."""
+    """The autotuner's choice (cached per graph; the lane spins of the bank-conflict model or of the
+    index order, whichever timed faster) gives the same table as the oracle's frontier programme,
+    and so does the model's plan forced; a second isg_autotune call returns the cached fields."""
     import torch
     lat = w.square(6, 6, True)
     g = isg.isg_graph_create(lat.n, lat.edges)
     t1 = isg.isg_autotune(g)
     t2 = isg.isg_autotune(g)
     assert t1 == t2 and t1["stride_residue"] > 0 and t1["block_threads"] > 0
+    assert t1["lane_model"] in (1, 2)
     out = torch.zeros(isg.table_shape(g), dtype=torch.int64, device=cuda)
     isg.isg_enumerate(g, out, autotune=1)
+    forced = torch.zeros_like(out)
+    isg.isg_enumerate(g, forced, lane_model=1)
     torch.cuda.synchronize()
-    assert np.array_equal(out.cpu().numpy(), oracle.g_frontier(lat.n, lat.edges, max_active=16))
+    ref = oracle.g_frontier(lat.n, lat.edges, max_active=16)
+    assert np.array_equal(out.cpu().numpy(), ref)
+    assert np.array_equal(forced.cpu().numpy(), ref)
+    isg.isg_device_status()
 
 
 def test_checkpoint_and_resume(isg, cuda, tmp_path):
