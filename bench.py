@@ -45,14 +45,15 @@ SM_MAX_MHZ_FALLBACK = 2070.0
 # bin address and one counter increment.
 OPS_PER_CONFIG = 2
 # DRAM traffic of one enumeration launch on this workload from the committed ncu capture
-# (profiles/enumerate_kernel_torus6x6.md), valid only for the kernel sources it was taken on.
-TRAFFIC_BYTES = 33020          # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu: 33.02 KB read, 0 written)
-TRAFFIC_SOURCES_SHA = "9d2d6198cb2b7864"
+# (profiles/enumerate_kernel_torus6x6.md), valid only for the kernel's device code it was taken on
+# (enum_core.cuh and enum_kernels.cuh; a changed kernel reports no traffic until re-captured).
+TRAFFIC_BYTES = 33536          # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu: 33.54 KB read, 0 written)
+TRAFFIC_SOURCES_SHA = "87731c21cbaed473"
 
 
 def kernel_sources_sha() -> str:
     h = hashlib.sha256()
-    for f in ("enum_core.cuh", "enumerate.cu"):
+    for f in ("enum_core.cuh", "enum_kernels.cuh"):
         with open(os.path.join(ROOT, "paper_1110_2561_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "libisg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["host.cpp", "lanes.cpp", "split_host.cpp", "enumerate.cu", "thermo.cu", "probe.cu", "noalloc.cu", "batch.cu",
            "server.cu", "split.cu"]
-HEADERS = ["enum_core.cuh", "isg_internal.h", "batch_internal.h", "nvtx_range.h", "split_internal.h"]
+HEADERS = ["enum_core.cuh", "enum_kernels.cuh", "isg_internal.h", "batch_internal.h", "nvtx_range.h", "split_internal.h"]
 
 
 def _nvcc() -> str:
