@@ -99,12 +99,14 @@ typedef struct {
                                 the batch; the others go to the tile queue. Same tables either way. */
     int32_t lane_model;      /* which spins carry the lane index of a warp (the five spins at internal
                                 positions q .. q+4, in which the 32 lanes of a warp task differ):
-                                0 = plan: for isg_enumerate, isg_enumerate_rank, isg_enumerate_noalloc
-                                and isg_autotune on graphs of at least 30 free spins, the set and the
-                                histogram row stride with the fewest shared-memory bank conflicts under
-                                a model of the warp reductions (cached per graph structure); otherwise
-                                as 2. 1 = that model for any graph and call. 2 = the five free spins
-                                after the inner ones in index order, stride by a fixed preference. */
+                                0 = plan: the index order (as 2), except that autotuning (isg_autotune,
+                                autotune = 1, prepared batches with autotune) also times the set and
+                                the histogram row stride with the fewest shared-memory bank conflicts
+                                under a model of the warp reductions (graphs of at least 30 spins;
+                                searched once per graph structure, coupling signs aside) and keeps
+                                the faster. 1 = that model's set and stride for any graph and call.
+                                2 = the five free spins after the inner ones in index order, stride
+                                by a fixed preference. */
 } isg_options;
 
 /* Fill *opt with the defaults (all planner choices, full range, overwrite). */
@@ -207,8 +209,9 @@ typedef struct isg_batch isg_batch;
  * Prepare a batch once: plan every graph, and place the programs, the tile descriptors and one
  * output table per graph in device memory owned by the batch (on the current device). Options as
  * isg_enumerate_batch; with opt->autotune the unset fields among inner_bits (per-lane walk
- * length), block_threads and stride_residue are chosen by timing candidate plans on every 8th
- * graph first (synchronous; results never depend on them). The graphs may be destroyed
+ * length), block_threads, lane_model and stride_residue are chosen by timing candidate plans on
+ * every 8th graph first (synchronous; results never depend on them; the lane model's choice is
+ * searched once per graph structure, coupling signs aside). The graphs may be destroyed
  * afterwards. Errors: ISG_ERR_INVALID, ISG_ERR_TOO_LARGE, ISG_ERR_NOMEM, ISG_ERR_CUDA.
  */
 ISG_API isg_status isg_batch_create(int32_t n_graphs, const isg_graph* const* graphs, const isg_options* opt,

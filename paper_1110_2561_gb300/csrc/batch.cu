@@ -387,8 +387,10 @@ static float time_batch(int n, const isg_graph* const* graphs, const isg_options
     return best;
 }
 
-// Batch autotuner: per-lane walk length, block size and histogram stride residue, timed on every
-// 8th graph (the subset keeps the batch's mix of sizes). Unset fields of o are filled in.
+// Batch autotuner: per-lane walk length, block size, and either the index order's lane spins at a
+// histogram stride residue or the bank-conflict model's lane spins at their own stride (chosen once
+// per graph structure, coupling signs aside), timed on every 8th graph (the subset keeps the
+// batch's mix of sizes). Unset fields of o are filled in.
 static void autotune_batch(int n, const isg_graph* const* graphs, isg_options& o, int& ctas_per_sm) {
     std::vector<const isg_graph*> sub;
     for (int k = 0; k < n; k += 8) sub.push_back(graphs[k]);
@@ -400,17 +402,20 @@ static void autotune_batch(int n, const isg_graph* const* graphs, isg_options& o
     } dguard{s};
     static const int qs[] = {16, 18, 14};
     static const int threads[] = {512, 256};
-    static const int residues[] = {6, 13};
+    // (lane_model, stride residue): the index order at two residues, the model at its own stride
+    static const int lanes_residues[][2] = {{2, 6}, {2, 13}, {1, 0}};
     float best_ms = 1e30f;
     isg_options best = o;
     for (int q : qs)
         for (int t : threads)
-            for (int r : residues) {
+            for (const auto& lr : lanes_residues) {
+                if (o.lane_model && o.lane_model != lr[0]) continue;
                 isg_options c = o;
                 c.autotune = 0;
                 if (!c.inner_bits) c.inner_bits = q;
                 if (!c.block_threads) c.block_threads = t;
-                if (!c.stride_residue && !c.bin_stride) c.stride_residue = r;
+                c.lane_model = lr[0];
+                if (!c.stride_residue && !c.bin_stride) c.stride_residue = lr[1];
                 float ms;
                 try {
                     ms = time_batch((int)sub.size(), sub.data(), c, s, ctas_per_sm);

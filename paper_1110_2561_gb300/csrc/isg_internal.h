@@ -110,7 +110,8 @@ struct LaneChoice {
 
 // Choose five lane spins among `pool` (a mask of free spins) and a row stride in [N + 1,
 // max_stride] with the fewest expected wavefronts per warp reduction; `baseline` (the index
-// order's lane spins) is always a candidate. Cached per graph structure, pool and stride limit.
+// order's lane spins) is always a candidate. Cached per graph structure (bonds and coupling
+// magnitudes, energy stride, histogram rows; not the coupling signs), pool and stride limit.
 LaneChoice choose_lanes(const isg_graph& g, uint64_t pool, const int* baseline, int max_stride);
 
 struct DeviceInfo {

@@ -130,11 +130,23 @@ void connected_sets(const std::vector<uint64_t>& adj, uint64_t pool, int root, s
 std::mutex g_lane_mu;
 std::map<std::tuple<uint64_t, uint64_t, int>, LaneChoice> g_lane_cache;
 
+// Key of the cache: N, the bonds with the magnitudes of their couplings (not their signs), the
+// energy stride and the number of histogram rows. Graphs that differ only in coupling signs (the
+// disorder realisations of a batch) share one search: the chosen set is valid for every one of them
+// (any five spins are), its stride keeps 8 R divisible by their common energy stride, and its
+// modelled cost on another sign draw is close to that draw's own best (1.03-1.04 against 1.02 on
+// EA 5x6 instances, index order 1.07-1.10).
 uint64_t structure_hash(const isg_graph& g) {
-    uint64_t h = 1469598103934665603ull;                      // FNV-1a over N and the couplings
+    uint64_t h = 1469598103934665603ull;                      // FNV-1a
     auto mix = [&](uint64_t v) { for (int b = 0; b < 8; ++b) { h ^= (v >> (8 * b)) & 0xff; h *= 1099511628211ull; } };
     mix((uint64_t)g.n);
-    for (size_t k = 0; k < g.bJ.size(); ++k) { mix((uint64_t)g.bi[k]); mix((uint64_t)g.bj[k]); mix((uint64_t)g.bJ[k]); }
+    mix((uint64_t)g.G);
+    mix((uint64_t)g.n_e_c);
+    for (size_t k = 0; k < g.bJ.size(); ++k) {
+        mix((uint64_t)g.bi[k]);
+        mix((uint64_t)g.bj[k]);
+        mix((uint64_t)(g.bJ[k] < 0 ? -g.bJ[k] : g.bJ[k]));
+    }
     return h;
 }
 

@@ -36,7 +36,8 @@ def test_batch_device_tables_and_options(isg, cuda):
     lats = mixed_graphs()
     hs = [isg.isg_graph_create(l.n, l.edges) for l in lats]
     ref = [oracle.g_masks(l.n, l.edges, threads=THREADS) for l in lats]
-    for kw in [{}, dict(inner_bits=6), dict(low_bits=2, block_threads=64), dict(ctas_per_sm=1, block_threads=256)]:
+    for kw in [{}, dict(inner_bits=6), dict(low_bits=2, block_threads=64), dict(ctas_per_sm=1, block_threads=256),
+               dict(lane_model=1), dict(lane_model=1, inner_bits=7, symmetry=1)]:
         outs = [torch.zeros(isg.table_shape(h), dtype=torch.int64, device=cuda) for h in hs]
         isg.isg_enumerate_batch(hs, outs, **kw)
         for o, r, l in zip(outs, ref, lats):
@@ -99,7 +100,9 @@ def test_prepared_batch_replay(isg, cuda):
 
 
 def test_autotuned_batch(isg, cuda):
-    """A batch planned by the autotuner gives the same tables as the default plan."""
+    """A batch planned by the autotuner (lane spins of the index order or of the bank-conflict
+    model, shared by instances that differ only in coupling signs) gives the same tables as the
+    default plan."""
     import torch
     lats = w.ea_instances(count=256, seed=99)
     hs = [isg.isg_graph_create(l.n, l.edges) for l in lats]
