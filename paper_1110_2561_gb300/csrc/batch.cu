@@ -451,7 +451,7 @@ isg_status isg_batch_create(int32_t n_graphs, const isg_graph* const* graphs, co
         for (int k = 0; k < n_graphs; ++k) {
             if (o.split) {
                 try {
-                    auto sp = prepare_split(*graphs[k], 0, false);
+                    auto sp = prepare_split(*graphs[k], 0, false, true);
                     if (sp->plan.cost + kSplitLaunchWarpInstr < sp->plan.direct_cost) { sprep[k] = sp; continue; }
                 } catch (const Error&) {
                     // no admissible boundary set: the tile queue

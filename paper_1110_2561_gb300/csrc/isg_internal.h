@@ -114,6 +114,12 @@ struct LaneChoice {
 // magnitudes, energy stride, histogram rows; not the coupling signs), pool and stride limit.
 LaneChoice choose_lanes(const isg_graph& g, uint64_t pool, const int* baseline, int max_stride);
 
+// The same search over strides [stride_lo, stride_hi] (only those with 8 R divisible by the
+// energy stride if stride_times8_by_G) for histograms whose rows are `divisor` units of energy
+// apart (the split kernel's component histograms: divisor 2).
+LaneChoice choose_lanes_in(const isg_graph& g, uint64_t pool, const int* baseline, int stride_lo, int stride_hi,
+                           int64_t divisor, bool stride_times8_by_G);
+
 struct DeviceInfo {
     int sms = 152;
     size_t smem_optin = 232448;

@@ -43,13 +43,14 @@ uint64_t splitmix(uint64_t& s) {
 
 int popc(uint64_t x) { return __builtin_popcountll(x); }
 
-// Expected wavefronts per warp reduction of lane set L[0..4] for every stride in `strides`,
-// estimated from `samples` uniform draws of the states of the lane spins' other neighbours (the
+// Expected wavefronts per warp reduction of lane set L[0..4] for every stride in `strides`, with
+// histogram rows of `divisor` units of energy, estimated from `samples` uniform draws of the
+// states of the lane spins' other neighbours (the
 // draws come from `seed`; equal seeds give every candidate the same draws where their
 // neighbourhoods coincide). Distinct addresses are distinct (e', m) pairs at every stride above
 // 2 x 5, so the 32 lanes are merged once per draw and only their banks depend on the stride.
 std::vector<double> lane_costs(const isg_graph& g, const int* L, const std::vector<int>& strides, int samples,
-                               uint64_t seed) {
+                               uint64_t seed, int64_t divisor) {
     const int n = g.n;
     uint64_t inL = 0;
     for (int k = 0; k < 5; ++k) inL |= 1ull << L[k];
@@ -83,14 +84,14 @@ std::vector<double> lane_costs(const isg_graph& g, const int* L, const std::vect
             for (const auto& p : nb[k]) a += ((state >> p.first) & 1) ? p.second : -p.second;
             h[k] = a;
         }
-        // E(b) = ell(b) - sum_k s_k h_k; differences from lane 0 are multiples of G
+        // E(b) = ell(b) - sum_k s_k h_k; differences from lane 0 are multiples of the divisor
         int64_t e0 = 0;
         int nd = 0;
         for (int b = 0; b < 32; ++b) {
             int64_t e = ell[b];
             for (int k = 0; k < 5; ++k) e -= (((b >> k) & 1) ? 1 : -1) * h[k];
             if (b == 0) e0 = e;
-            de[b] = (e - e0) / g.G;
+            de[b] = (e - e0) / divisor;
             const int m = popc((uint64_t)b);
             bool dup = false;
             for (int t = 0; t < nd; ++t) if (dist_de[t] == de[b] && dist_m[t] == m) { dup = true; break; }
@@ -128,7 +129,7 @@ void connected_sets(const std::vector<uint64_t>& adj, uint64_t pool, int root, s
 }
 
 std::mutex g_lane_mu;
-std::map<std::tuple<uint64_t, uint64_t, int>, LaneChoice> g_lane_cache;
+std::map<std::tuple<uint64_t, uint64_t, int, int, int64_t>, LaneChoice> g_lane_cache;
 
 // Key of the cache: N, the bonds with the magnitudes of their couplings (not their signs), the
 // energy stride and the number of histogram rows. Graphs that differ only in coupling signs (the
@@ -153,16 +154,23 @@ uint64_t structure_hash(const isg_graph& g) {
 }  // namespace
 
 LaneChoice choose_lanes(const isg_graph& g, uint64_t pool, const int* baseline, int max_stride) {
+    // strides keep 8 R a multiple of the energy stride (the program's address step per unit of field)
+    return choose_lanes_in(g, pool, baseline, g.n + 1, std::min(max_stride, g.n + 32), g.G, true);
+}
+
+LaneChoice choose_lanes_in(const isg_graph& g, uint64_t pool, const int* baseline, int stride_lo, int stride_hi,
+                           int64_t divisor, bool stride_times8_by_G) {
     const int n = g.n;
-    const std::tuple<uint64_t, uint64_t, int> key(structure_hash(g), pool, max_stride);
+    const std::tuple<uint64_t, uint64_t, int, int, int64_t> key(structure_hash(g), pool, stride_lo, stride_hi,
+                                                                divisor * (stride_times8_by_G ? 1 : -1));
     {
         std::lock_guard<std::mutex> lk(g_lane_mu);
         const auto it = g_lane_cache.find(key);
         if (it != g_lane_cache.end()) return it->second;
     }
     std::vector<int> strides;
-    for (int R = n + 1; R <= std::min(max_stride, n + 32); ++R)
-        if ((8 * (int64_t)R) % g.G == 0) strides.push_back(R);
+    for (int R = stride_lo; R <= stride_hi; ++R)
+        if (!stride_times8_by_G || (8 * (int64_t)R) % g.G == 0) strides.push_back(R);
     LaneChoice best;
     if (strides.empty() || popc(pool) < 5) { best.valid = false; return best; }
     std::vector<uint64_t> adj(n, 0);
@@ -211,7 +219,7 @@ LaneChoice choose_lanes(const isg_graph& g, uint64_t pool, const int* baseline, 
         if (inner_bonds(S) + 1 < top) continue;
         int L[5];
         spins_of(S, L);
-        const std::vector<double> c = lane_costs(g, L, strides, 48, 0x1a7e5);
+        const std::vector<double> c = lane_costs(g, L, strides, 48, 0x1a7e5, divisor);
         screened.push_back({*std::min_element(c.begin(), c.end()), S});
     }
     std::sort(screened.begin(), screened.end());
@@ -223,7 +231,7 @@ LaneChoice choose_lanes(const isg_graph& g, uint64_t pool, const int* baseline, 
         int L[5];
         if (sc.second == base_mask) std::memcpy(L, baseline, sizeof L);
         else spins_of(sc.second, L);
-        const std::vector<double> c = lane_costs(g, L, strides, 1024, 0x5eed);
+        const std::vector<double> c = lane_costs(g, L, strides, 1024, 0x5eed, divisor);
         const size_t r = (size_t)(std::min_element(c.begin(), c.end()) - c.begin());
         if (sc.second == base_mask) best.cost_index_order = c[r];
         if (!best.valid || c[r] < best.cost) {

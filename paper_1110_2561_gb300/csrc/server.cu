@@ -585,7 +585,7 @@ isg_status isg_server_submit(isg_server* s, const isg_graph* g, int64_t* ticket)
         // the small kernel
         if (s->opt.split_work_ratio > 0 && g->n >= kSplitMinSpins) {
             try {
-                auto sp = prepare_split(*g, 0, false);
+                auto sp = prepare_split(*g, 0, false, false);   // per request: no lane search at submit
                 if (sp->plan.cost < s->opt.split_work_ratio * sp->plan.direct_cost) {
                     r->split = sp;
                     r->blob = sp->blob;

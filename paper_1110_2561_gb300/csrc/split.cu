@@ -414,7 +414,7 @@ extern "C" isg_status isg_enumerate_split(const isg_graph* graph, void* stream, 
     return guarded([&] {
         NvtxRange nvtx("isg_enumerate_split");
         if (!graph || !g_out) fail(ISG_ERR_INVALID, "graph or g_out is NULL");
-        const std::shared_ptr<const SplitPrepared> prep = prepare_split(*graph, boundary, true);
+        const std::shared_ptr<const SplitPrepared> prep = prepare_split(*graph, boundary, true, true);
         const std::vector<uint64_t>& blob = prep->blob;
         const SplitHeader& H = *reinterpret_cast<const SplitHeader*>(blob.data());
         cudaStream_t s = static_cast<cudaStream_t>(stream);

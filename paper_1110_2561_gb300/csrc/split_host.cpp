@@ -349,7 +349,7 @@ SplitPlan plan_split(const isg_graph& g, uint64_t boundary, bool require_gain) {
     return p;
 }
 
-std::vector<uint64_t> build_split_program(const isg_graph& g, const SplitPlan& p) {
+std::vector<uint64_t> build_split_program(const isg_graph& g, const SplitPlan& p, bool lane_model) {
     const int n = g.n, ns = (int)p.S.size(), k = (int)p.comps.size();
     std::vector<int64_t> cls;
     for (int64_t J : g.bJ) cls.push_back(J);
@@ -380,6 +380,23 @@ std::vector<uint64_t> build_split_program(const isg_graph& g, const SplitPlan& p
             for (int l = 0; l < ns; ++l) if (l != j && coupling(p.S[j], p.S[l]) == cls[t]) m |= 1ull << l;
             blob[h.off_ss + (size_t)j * n_cls + t] = m;
         }
+    // component energies and the planner's row strides: the largest component histogram is the
+    // budget that a row stride chosen by the lane model may not exceed (the CTA's buffers, and so
+    // its launch shape, stay as planned)
+    auto comp_Sc = [&](const std::vector<int>& v) {
+        int64_t Sc = 0;
+        for (size_t a = 0; a < v.size(); ++a) {
+            for (size_t b = a + 1; b < v.size(); ++b) Sc += std::llabs(coupling(v[a], v[b]));
+            for (int j = 0; j < ns; ++j) Sc += std::llabs(coupling(v[a], p.S[j]));
+        }
+        return Sc;
+    };
+    auto comp_mask = [](const std::vector<int>& v) { uint64_t m = 0; for (int a : v) m |= 1ull << a; return m; };
+    int64_t h_budget = 0;
+    for (int c = 0; c < k; ++c)
+        h_budget = std::max<int64_t>(h_budget, (comp_Sc(p.comps[c]) + 1) *
+                                                   split_hist_stride((int)p.comps[c].size(),
+                                                                     component_row_step(step_lowbits, comp_mask(p.comps[c]))));
     int64_t EO = 1, MO = 1, hmax = 0, sumSc = 0;
     int first = 0;
     for (int c = 0; c < k; ++c) {
@@ -389,40 +406,66 @@ std::vector<uint64_t> build_split_program(const isg_graph& g, const SplitPlan& p
         // registers
         std::vector<int> v = p.comps[c];
         const int nc = (int)v.size();
-        int low = 0;
-        for (int want = split_low_want(nc, p.cta_bits); want > 0 && !low;
-             want = want == kSplitLowLarge && nc >= kSplitLowMinSpins ? kSplitLow : 0) {
-            std::vector<int> order(nc), pick;
-            for (int a = 0; a < nc; ++a) order[a] = a;
-            auto deg = [&](int a) { int d = 0; for (int b = 0; b < nc; ++b) d += b != a && coupling(v[a], v[b]) != 0; return d; };
+        // `want` spins of the component outside `avoid` with no bond among them (greedy, fewest
+        // bonds inside the component first), or fewer if there is no such set
+        auto low_pick = [&](int want, uint64_t avoid) {
+            std::vector<int> order, pick;
+            for (int a : p.comps[c]) if (!((avoid >> a) & 1)) order.push_back(a);
+            auto deg = [&](int a) { int d = 0; for (int b : p.comps[c]) d += b != a && coupling(a, b) != 0; return d; };
             std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return deg(a) < deg(b); });
             for (int a : order) {
                 bool free = true;
-                for (int b : pick) free = free && coupling(v[a], v[b]) == 0;
+                for (int b : pick) free = free && coupling(a, b) == 0;
                 if (free) pick.push_back(a);
                 if ((int)pick.size() == want) break;
             }
+            return pick;
+        };
+        int low = 0;
+        for (int want = split_low_want(nc, p.cta_bits); want > 0 && !low;
+             want = want == kSplitLowLarge && nc >= kSplitLowMinSpins ? kSplitLow : 0) {
+            const std::vector<int> pick = low_pick(want, 0);
             if ((int)pick.size() == want) {
-                std::vector<int> v2;
-                for (int a : pick) v2.push_back(v[a]);
-                for (int a = 0; a < nc; ++a)
-                    if (std::find(pick.begin(), pick.end(), a) == pick.end()) v2.push_back(v[a]);
+                std::vector<int> v2(pick);
+                for (int a : p.comps[c])
+                    if (std::find(pick.begin(), pick.end(), a) == pick.end()) v2.push_back(a);
                 v = v2;
                 low = want;
             }
         }
-        int64_t Sc = 0;
-        for (int a = 0; a < nc; ++a) {
-            for (int b = a + 1; b < nc; ++b) Sc += std::llabs(coupling(v[a], v[b]));
-            for (int j = 0; j < ns; ++j) Sc += std::llabs(coupling(v[a], p.S[j]));
+        const int64_t Sc = comp_Sc(v);
+        uint64_t cmask = comp_mask(v);
+        int hstride = split_hist_stride(nc, component_row_step(step_lowbits, cmask));
+        // The walkers of a warp differ in the five spins at local positions Lp .. Lp+4 (the low bits
+        // of the thread index); for a large component the bank-conflict model (lanes.cpp, rows of 2
+        // units of energy: bin e = E/2) chooses them and the row stride within the budget.
+        const int P = split_walk_bits(nc, low, p.cta_bits), Lp = nc - P;
+        if (lane_model && nc >= kSplitLaneModelMinSpins && P >= 5 && Lp >= low) {
+            const int hi = (int)std::min<int64_t>(nc + 32, h_budget / (Sc + 1));
+            const LaneChoice lc = choose_lanes_in(g, cmask, &v[Lp], nc + 1, hi, 2, false);
+            bool ok = lc.valid;
+            if (ok) {
+                uint64_t lmask = 0;
+                for (int t = 0; t < 5; ++t) lmask |= 1ull << lc.spins[t];
+                const std::vector<int> pick = low ? low_pick(low, lmask) : std::vector<int>();
+                ok = (int)pick.size() == low;
+                if (ok) {
+                    std::vector<int> v2(pick), rest;
+                    for (int a : p.comps[c])
+                        if (!((lmask >> a) & 1) && std::find(pick.begin(), pick.end(), a) == pick.end()) rest.push_back(a);
+                    size_t r = 0;
+                    while ((int)v2.size() < Lp) v2.push_back(rest[r++]);
+                    for (int t = 0; t < 5; ++t) v2.push_back(lc.spins[t]);
+                    while (r < rest.size()) v2.push_back(rest[r++]);
+                    v = v2;
+                    hstride = lc.stride;
+                }
+            }
         }
         for (int c2 = 0; c2 < k; ++c2)            // no bond may join two components
             if (c2 != c)
                 for (int a : v) for (int b : p.comps[c2])
                     if (coupling(a, b)) fail(ISG_ERR_INTERNAL, "split components are not independent");
-        uint64_t cmask = 0;
-        for (int a : v) cmask |= 1ull << a;
-        const int hstride = split_hist_stride(nc, component_row_step(step_lowbits, cmask));
         SplitComp rec{nc, (int32_t)Sc, first, (int32_t)((Sc + 1) * hstride), low, hstride, {0, 0}};
         static_assert(sizeof(SplitComp) == 32, "component record is four words");
         std::memcpy(&blob[h.off_comp + 4 * (size_t)c], &rec, sizeof rec);
@@ -610,7 +653,8 @@ void emulate_split(const std::vector<uint64_t>& blob, int64_t* g_out) {
 // the enumeration of a small lattice microseconds. The key is the graph's content (N and its bond
 // list, compared in full on every hit), so graphs created separately share entries and a freed
 // handle's address cannot alias another graph.
-std::shared_ptr<const SplitPrepared> prepare_split(const isg_graph& g, uint64_t boundary, bool require_gain) {
+std::shared_ptr<const SplitPrepared> prepare_split(const isg_graph& g, uint64_t boundary, bool require_gain,
+                                                   bool lane_model) {
     static std::mutex mu;
     static std::unordered_multimap<uint64_t, std::shared_ptr<const SplitPrepared>> cache;
     uint64_t h = 1469598103934665603ull;
@@ -618,14 +662,15 @@ std::shared_ptr<const SplitPrepared> prepare_split(const isg_graph& g, uint64_t 
     mix((uint64_t)g.n);
     mix(boundary);
     mix(require_gain ? 1 : 0);
+    mix(lane_model ? 1 : 0);
     for (size_t k = 0; k < g.bJ.size(); ++k) { mix((uint64_t)g.bi[k]); mix((uint64_t)g.bj[k]); mix((uint64_t)g.bJ[k]); }
     {
         std::lock_guard<std::mutex> lk(mu);
         auto range = cache.equal_range(h);
         for (auto it = range.first; it != range.second; ++it) {
             const SplitPrepared& e = *it->second;
-            if (e.n == g.n && e.boundary_arg == boundary && e.require_gain == require_gain && e.bi == g.bi &&
-                e.bj == g.bj && e.bJ == g.bJ)
+            if (e.n == g.n && e.boundary_arg == boundary && e.require_gain == require_gain &&
+                e.lane_model == lane_model && e.bi == g.bi && e.bj == g.bj && e.bJ == g.bJ)
                 return it->second;
         }
     }
@@ -636,8 +681,9 @@ std::shared_ptr<const SplitPrepared> prepare_split(const isg_graph& g, uint64_t 
     e->bJ = g.bJ;
     e->boundary_arg = boundary;
     e->require_gain = require_gain;
+    e->lane_model = lane_model;
     e->plan = plan_split(g, boundary, require_gain);
-    e->blob = build_split_program(g, e->plan);
+    e->blob = build_split_program(g, e->plan, lane_model);
     std::lock_guard<std::mutex> lk(mu);
     if (cache.size() >= 256) cache.clear();
     cache.emplace(h, e);
@@ -654,7 +700,7 @@ isg_status isg_split_plan(const isg_graph* graph, uint64_t boundary, uint64_t* c
                           int32_t* largest_component, double* visits, double* work_ratio) {
     return guarded([&] {
         if (!graph) fail(ISG_ERR_INVALID, "graph is NULL");
-        const std::shared_ptr<const SplitPrepared> e = prepare_split(*graph, boundary, false);
+        const std::shared_ptr<const SplitPrepared> e = prepare_split(*graph, boundary, false, false);
         const SplitPlan& p = e->plan;
         if (chosen) *chosen = p.boundary;
         if (n_components) *n_components = (int32_t)p.comps.size();
@@ -671,7 +717,8 @@ isg_status isg_split_plan(const isg_graph* graph, uint64_t boundary, uint64_t* c
 isg_status isg_debug_emulate_split(const isg_graph* graph, uint64_t boundary, int64_t* g_out) {
     return guarded([&] {
         if (!graph || !g_out) fail(ISG_ERR_INVALID, "NULL argument");
-        const std::shared_ptr<const SplitPrepared> e = prepare_split(*graph, boundary, false);
+        // the program isg_enumerate_split runs (lane spins by the conflict model)
+        const std::shared_ptr<const SplitPrepared> e = prepare_split(*graph, boundary, false, true);
         const std::vector<uint64_t>& blob = e->blob;
         std::memset(g_out, 0, sizeof(int64_t) * (size_t)(graph->S + 1) * (graph->n + 1));
         emulate_split(blob, g_out);

@@ -37,6 +37,7 @@ constexpr int kSplitWalkBits = 9;        // at most 2^9 = 512 walkers per compon
 constexpr int kSplitLow = 5;             // size of a component walk's low block ...
 constexpr int kSplitLowLarge = 7;        // ... or of the larger one, where a component has room for it
 constexpr int kSplitLowMinSpins = 12;    // components given a low block: at least this many spins
+constexpr int kSplitLaneModelMinSpins = 16;   // components whose lane spins the conflict model may choose
 // Warp instructions per configuration of the full enumeration (ncu on the 6x6 torus: 2.86 per 32
 // configurations): the unit in which the planner compares a split with the full enumeration.
 constexpr double kDirectWarpInstrPerConfig = 2.86 / 32;
@@ -154,7 +155,7 @@ struct SplitPlan {
 // boundary = 0: the cheapest admissible boundary set; with require_gain, refused (TOO_LARGE) unless
 // it is cheaper than the full enumeration under the work model.
 SplitPlan plan_split(const struct ::isg_graph& g, uint64_t boundary, bool require_gain);
-std::vector<uint64_t> build_split_program(const struct ::isg_graph& g, const SplitPlan& p);
+std::vector<uint64_t> build_split_program(const struct ::isg_graph& g, const SplitPlan& p, bool lane_model);
 void emulate_split(const std::vector<uint64_t>& blob, int64_t* g_out);
 
 // A plan and its program for one graph content and boundary argument (cached).
@@ -164,10 +165,15 @@ struct SplitPrepared {
     std::vector<int64_t> bJ;
     uint64_t boundary_arg = 0;
     bool require_gain = false;
+    bool lane_model = false;
     SplitPlan plan;
     std::vector<uint64_t> blob;
 };
-std::shared_ptr<const SplitPrepared> prepare_split(const struct ::isg_graph& g, uint64_t boundary, bool require_gain);
+// lane_model: the walkers' lane spins and row strides of components of at least
+// kSplitLaneModelMinSpins spins chosen by the bank-conflict model (a search per component
+// structure, cached); without it the component order and the fixed stride preference.
+std::shared_ptr<const SplitPrepared> prepare_split(const struct ::isg_graph& g, uint64_t boundary, bool require_gain,
+                                                   bool lane_model);
 
 // Device side (split.cu): enqueue the split kernel for a prepared plan on `stream` (a
 // cudaStream_t); program at d_blob, table (device) accumulated into, status bit 0 on a failed

@@ -49,6 +49,10 @@ CASES = [
     (w.cubic(2, 3, 4, True), 0),
     (w.Lattice(7, np.zeros((0, 3), np.int64)), 0),                        # no bonds: seven components
     (w.square(3, 4, True), mask(range(12))),                               # everything boundary
+    # components of 16 or more spins: walker lane spins and row strides chosen by the conflict model
+    (w.square(4, 5, False), mask([0, 1, 2, 3])),                           # one component of 16
+    (w.with_random_couplings(w.square(4, 5, True), w.SplitMix64(11), (-1, 1)), mask(range(0, 5)) | mask([10, 11, 12])),
+    (w.with_random_couplings(w.triangular(3, 6, False), w.SplitMix64(12), (-2, -1, 1, 2)), mask([0])),   # 17 spins
 ]
 
 
