@@ -667,7 +667,8 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------ serving mode
-def serve_stream(n_requests: int, rate: float, step_ms: float, split_ratio: float, symmetry: int = 0) -> dict:
+def serve_stream(n_requests: int, rate: float, step_ms: float, split_ratio: float, symmetry: int = 0,
+                 lane_model: int = 0) -> dict:
     """Poisson stream of lattice requests (seeded; N uniform in 16..38, square / triangular / cubic,
     periodic or free, J uniform in {-2,-1,1,2}) submitted at their arrival times to isg_server;
     latency percentiles, throughput and offered vs achieved load (configurations counted into the
@@ -676,7 +677,7 @@ def serve_stream(n_requests: int, rate: float, step_ms: float, split_ratio: floa
 
     reqs = workloads.serving_stream(n_requests, rate_per_s=rate)
     graphs = [isg.isg_graph_create(r.lattice.n, r.lattice.edges) for r in reqs]
-    srv = isg.Server(step_ms=step_ms, split_work_ratio=split_ratio, symmetry=symmetry)
+    srv = isg.Server(step_ms=step_ms, split_work_ratio=split_ratio, symmetry=symmetry, lane_model=lane_model)
     warm = srv.submit(isg.isg_graph_create(20, workloads.square(4, 5, True).edges))
     srv.wait(warm)
     srv.result(warm)
@@ -712,7 +713,7 @@ def serve_stream(n_requests: int, rate: float, step_ms: float, split_ratio: floa
         "achieved_configs_per_s": configs / max(1e-9, elapsed),
         "device_busy_frac": st["device_ms"] * 1e-3 / max(1e-9, elapsed),
         "steps": int(st["steps"]), "step_ms": step_ms, "invariant_failures": bad,
-        "split_work_ratio": split_ratio, "symmetry": symmetry,
+        "split_work_ratio": split_ratio, "symmetry": symmetry, "lane_model": lane_model,
     }
 
 
@@ -722,7 +723,7 @@ def run_serving(args):
 
     torch.cuda.set_device(0)
     line = {"metric": "serving latency and throughput (continuous batching)", "unit": "ms"}
-    line.update(serve_stream(args.requests, args.rate, args.step_ms, args.split_ratio, args.symmetry))
+    line.update(serve_stream(args.requests, args.rate, args.step_ms, args.split_ratio, args.symmetry, args.lane_model))
     print(json.dumps(line), flush=True)
 
 
@@ -826,6 +827,8 @@ def main():
                     help="serving: serve requests whose split-and-convolve work is below this fraction by split launches")
     ap.add_argument("--symmetry", type=int, choices=(0, 1), default=0,
                     help="serving: enumerate each tile-served request's half with spin N-1 up and mirror it")
+    ap.add_argument("--lane-model", type=int, choices=(0, 1), default=0,
+                    help="serving: the quick lane search for requests of at least 36 spins")
     ap.add_argument("--shard", action="store_true",
                     help="under torchrun: the ranks share the one torus (strong scaling, NCCL all-reduce per step)")
     ap.add_argument("--shard-bits", type=int, default=0,

@@ -106,7 +106,8 @@ typedef struct {
                                 searched once per graph structure, coupling signs aside) and keeps
                                 the faster. 1 = that model's set and stride for any graph and call.
                                 2 = the five free spins after the inner ones in index order, stride
-                                by a fixed preference. */
+                                by a fixed preference. 3 = the model with a quick search (dense greedy
+                                sets only, fewer draws: milliseconds instead of a tenth of a second). */
 } isg_options;
 
 /* Fill *opt with the defaults (all planner choices, full range, overwrite). */
@@ -397,6 +398,11 @@ typedef struct {
                                 mirror M -> -M before it is copied out (the global spin flip maps
                                 (E, M) to (E, -M) for any couplings): half the work, the same table.
                                 0 (default): all 2^N configurations. */
+    int32_t lane_model;      /* 1: a tile-served request of at least 36 spins gets the lane spins and
+                                histogram row stride of a quick search under the bank-conflict model
+                                (options.lane_model = 3: a few milliseconds of host time at submit,
+                                inside the request's latency); 0: the index order. The table is the
+                                same either way. */
 } isg_server_options;
 
 ISG_API void isg_server_options_init(isg_server_options* opt);

@@ -165,7 +165,7 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d, bo
     if (n > o.max_spins)
         fail(ISG_ERR_TOO_LARGE, "graph has " + std::to_string(n) + " spins, more than max_spins = " +
                                     std::to_string(o.max_spins));
-    if (o.lane_model < 0 || o.lane_model > 2) fail(ISG_ERR_INVALID, "lane_model must be 0, 1 or 2");
+    if (o.lane_model < 0 || o.lane_model > 3) fail(ISG_ERR_INVALID, "lane_model must be 0, 1, 2 or 3");
     const int k = o.shard_bits;
     if (k < 0 || k > n) fail(ISG_ERR_INVALID, "shard_bits must lie in [0, N]");
     int64_t lo = o.shard_lo, hi = o.shard_hi;
@@ -212,12 +212,15 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d, bo
     // Lane spins by the bank-conflict model (lanes.cpp): the index order's five spins at q..q+4
     // are one candidate; another set moves to those positions, with the low block and the other
     // inner spins chosen among the rest.
-    const bool use_model =
-        o.lane_model == 1 || (o.lane_model == 0 && single_graph && o.autotune && free >= kLaneModelMinFree);
+    const bool use_model = o.lane_model == 1 || o.lane_model == 3 ||
+                           (o.lane_model == 0 && single_graph && o.autotune && free >= kLaneModelMinFree);
     LaneChoice lc;
     if (use_model && prog_bytes + (size_t)g.n_e_c * (n + 1) * 4 <= d.smem_optin) {
         const uint64_t pool = free >= 64 ? ~0ull : ((1ull << free) - 1);
-        lc = choose_lanes(g, pool, &p.perm[p.q], max_stride);
+        if (o.lane_model == 3)
+            lc = choose_lanes_in(g, pool, &p.perm[p.q], n + 1, std::min(max_stride, n + 32), g.G, true, true);
+        else
+            lc = choose_lanes(g, pool, &p.perm[p.q], max_stride);
     }
     if (lc.valid) {
         p.lane_model = true;

@@ -116,9 +116,10 @@ LaneChoice choose_lanes(const isg_graph& g, uint64_t pool, const int* baseline, 
 
 // The same search over strides [stride_lo, stride_hi] (only those with 8 R divisible by the
 // energy stride if stride_times8_by_G) for histograms whose rows are `divisor` units of energy
-// apart (the split kernel's component histograms: divisor 2).
+// apart (the split kernel's component histograms: divisor 2). quick: only the dense greedy sets,
+// fewer draws (a few milliseconds; for planning per request).
 LaneChoice choose_lanes_in(const isg_graph& g, uint64_t pool, const int* baseline, int stride_lo, int stride_hi,
-                           int64_t divisor, bool stride_times8_by_G);
+                           int64_t divisor, bool stride_times8_by_G, bool quick = false);
 
 struct DeviceInfo {
     int sms = 152;

@@ -155,14 +155,14 @@ uint64_t structure_hash(const isg_graph& g) {
 
 LaneChoice choose_lanes(const isg_graph& g, uint64_t pool, const int* baseline, int max_stride) {
     // strides keep 8 R a multiple of the energy stride (the program's address step per unit of field)
-    return choose_lanes_in(g, pool, baseline, g.n + 1, std::min(max_stride, g.n + 32), g.G, true);
+    return choose_lanes_in(g, pool, baseline, g.n + 1, std::min(max_stride, g.n + 32), g.G, true, false);
 }
 
 LaneChoice choose_lanes_in(const isg_graph& g, uint64_t pool, const int* baseline, int stride_lo, int stride_hi,
-                           int64_t divisor, bool stride_times8_by_G) {
+                           int64_t divisor, bool stride_times8_by_G, bool quick) {
     const int n = g.n;
     const std::tuple<uint64_t, uint64_t, int, int, int64_t> key(structure_hash(g), pool, stride_lo, stride_hi,
-                                                                divisor * (stride_times8_by_G ? 1 : -1));
+                                                                (divisor * 2 + (quick ? 1 : 0)) * (stride_times8_by_G ? 1 : -1));
     {
         std::lock_guard<std::mutex> lk(g_lane_mu);
         const auto it = g_lane_cache.find(key);
@@ -202,7 +202,8 @@ LaneChoice choose_lanes_in(const isg_graph& g, uint64_t pool, const int* baselin
         const int v = __builtin_ctzll(above);
         if (std::find(seeds.begin(), seeds.end(), v) == seeds.end()) seeds.push_back(v);
     }
-    for (int v : seeds) connected_sets(adj, pool, v, cand.size() + 2500, cand);
+    if (!quick)
+        for (int v : seeds) connected_sets(adj, pool, v, cand.size() + 2500, cand);
     auto inner_bonds = [&](uint64_t S) {
         int b = 0;
         for (uint64_t t = S; t; t &= t - 1) b += popc(adj[__builtin_ctzll(t)] & S);
@@ -219,11 +220,11 @@ LaneChoice choose_lanes_in(const isg_graph& g, uint64_t pool, const int* baselin
         if (inner_bonds(S) + 1 < top) continue;
         int L[5];
         spins_of(S, L);
-        const std::vector<double> c = lane_costs(g, L, strides, 48, 0x1a7e5, divisor);
+        const std::vector<double> c = lane_costs(g, L, strides, quick ? 24 : 48, 0x1a7e5, divisor);
         screened.push_back({*std::min_element(c.begin(), c.end()), S});
     }
     std::sort(screened.begin(), screened.end());
-    if (screened.size() > 12) screened.resize(12);
+    if (screened.size() > (quick ? 3u : 12u)) screened.resize(quick ? 3 : 12);
     screened.push_back({0.0, base_mask});
     // refine the best few (and the index order's set) with many more samples
     best.valid = false;
@@ -231,7 +232,7 @@ LaneChoice choose_lanes_in(const isg_graph& g, uint64_t pool, const int* baselin
         int L[5];
         if (sc.second == base_mask) std::memcpy(L, baseline, sizeof L);
         else spins_of(sc.second, L);
-        const std::vector<double> c = lane_costs(g, L, strides, 1024, 0x5eed, divisor);
+        const std::vector<double> c = lane_costs(g, L, strides, quick ? 192 : 1024, 0x5eed, divisor);
         const size_t r = (size_t)(std::min_element(c.begin(), c.end()) - c.begin());
         if (sc.second == base_mask) best.cost_index_order = c[r];
         if (!best.valid || c[r] < best.cost) {
@@ -242,6 +243,7 @@ LaneChoice choose_lanes_in(const isg_graph& g, uint64_t pool, const int* baselin
         }
     }
     std::lock_guard<std::mutex> lk(g_lane_mu);
+    if (g_lane_cache.size() >= 4096) g_lane_cache.clear();   // a server plans graph after graph
     g_lane_cache[key] = best;
     return best;
 }

@@ -36,6 +36,9 @@ namespace isg {
 DeviceInfo device_info();
 
 constexpr int kSplitMinSpins = 24;     // below this the tile path takes microseconds anyway
+// requests given the quick lane search (lane_model option): their enumeration takes tens of
+// milliseconds, against a few milliseconds of search
+constexpr int kServerLaneModelMinSpins = 36;
 
 using Clock = std::chrono::steady_clock;
 
@@ -511,6 +514,7 @@ void isg_server_options_init(isg_server_options* o) {
     o->step_ms = 20.0;
     o->split_work_ratio = 0.0;
     o->symmetry = 0;
+    o->lane_model = 0;
 }
 
 isg_status isg_server_create(const isg_server_options* opt, isg_server** out) {
@@ -531,6 +535,7 @@ isg_status isg_server_create(const isg_server_options* opt, isg_server** out) {
         if (!(o.step_ms > 0)) fail(ISG_ERR_INVALID, "step_ms must be > 0");
         if (!(o.split_work_ratio >= 0 && o.split_work_ratio <= 1)) fail(ISG_ERR_INVALID, "split_work_ratio must lie in [0, 1]");
         if (o.symmetry != 0 && o.symmetry != 1) fail(ISG_ERR_INVALID, "symmetry must be 0 or 1");
+        if (o.lane_model != 0 && o.lane_model != 1) fail(ISG_ERR_INVALID, "lane_model must be 0 or 1");
         isg_server* s = new isg_server();
         s->opt = o;
         s->t_create = Clock::now();
@@ -612,6 +617,7 @@ isg_status isg_server_submit(isg_server* s, const isg_graph* g, int64_t* ticket)
                 o.shard_hi = 2;
             }
             o.inner_bits = std::min(16, g->n - 5 - (r->sym ? 1 : 0));
+            if (s->opt.lane_model && g->n >= kServerLaneModelMinSpins) o.lane_model = 3;
             p = make_plan(*g, o, d);
             if (p.small || p.q < p.b) fail(ISG_ERR_INTERNAL, "unexpected plan for a served graph");
             r->b = p.b;

@@ -429,14 +429,14 @@ class isg_server_options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("max_spins", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
                 ("max_queued", ctypes.c_int32), ("arena_bytes", ctypes.c_int64), ("step_ms", ctypes.c_double),
                 ("block_threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("split_work_ratio", ctypes.c_double), ("symmetry", ctypes.c_int32)]
+                ("split_work_ratio", ctypes.c_double), ("symmetry", ctypes.c_int32), ("lane_model", ctypes.c_int32)]
 
 
 class Server:
     """isg_server_*: a continuously batching request server on the current device.
 
     options: fields of isg_server_options (max_spins, max_inflight, max_queued, arena_bytes,
-    step_ms, block_threads, ctas_per_sm, split_work_ratio, symmetry)."""
+    step_ms, block_threads, ctas_per_sm, split_work_ratio, symmetry, lane_model)."""
 
     def __init__(self, **options):
         o = isg_server_options()

@@ -99,7 +99,7 @@ EMU_PLANS = [{}, dict(inner_bits=6), dict(low_bits=1, inner_bits=3), dict(low_bi
              dict(symmetry=1), dict(symmetry=1, low_bits=3, inner_bits=4),
              dict(lane_model=1), dict(lane_model=1, inner_bits=6), dict(lane_model=1, low_bits=3, inner_bits=5),
              dict(lane_model=1, shard_bits=2, shard_lo=1, shard_hi=3), dict(lane_model=1, symmetry=1),
-             dict(lane_model=1, stride_residue=13), dict(lane_model=2, autotune=0)]
+             dict(lane_model=1, stride_residue=13), dict(lane_model=2, autotune=0), dict(lane_model=3)]
 
 
 @pytest.mark.parametrize("lat", EMU_GRAPHS, ids=lambda l: l.name)
@@ -194,6 +194,8 @@ def test_lane_model_plans(isg):
             assert p["lane_cost"] < 0.95 * p["lane_cost_index_order"]
         # the index order keeps the five free spins after the inner ones
         assert [i for i in range(lat.n) if (q["lane_mask"] >> i) & 1] != lanes or p["lane_cost"] == p["lane_cost_index_order"]
+    quick = isg.isg_debug_plan(g, lane_model=3)          # the quick search: still a valid, better set
+    assert quick["lane_model"] == 1 and quick["lane_cost"] <= quick["lane_cost_index_order"]
     with pytest.raises(isg.IsgError) as ei:
-        isg.isg_debug_plan(g, lane_model=3)
+        isg.isg_debug_plan(g, lane_model=4)
     assert ei.value.status == 1
