@@ -668,7 +668,7 @@ def run_reference(args):
 
 # ------------------------------------------------------------------------------ serving mode
 def serve_stream(n_requests: int, rate: float, step_ms: float, split_ratio: float, symmetry: int = 0,
-                 lane_model: int = 0) -> dict:
+                 lane_model: int = 1) -> dict:
     """Poisson stream of lattice requests (seeded; N uniform in 16..38, square / triangular / cubic,
     periodic or free, J uniform in {-2,-1,1,2}) submitted at their arrival times to isg_server;
     latency percentiles, throughput and offered vs achieved load (configurations counted into the
@@ -827,8 +827,9 @@ def main():
                     help="serving: serve requests whose split-and-convolve work is below this fraction by split launches")
     ap.add_argument("--symmetry", type=int, choices=(0, 1), default=0,
                     help="serving: enumerate each tile-served request's half with spin N-1 up and mirror it")
-    ap.add_argument("--lane-model", type=int, choices=(0, 1), default=0,
-                    help="serving: the quick lane search for requests of at least 36 spins")
+    ap.add_argument("--lane-model", type=int, choices=(0, 1), default=1,
+                    help="serving: the quick lane search for requests of at least 36 spins (1, the server's "
+                         "default) or the index order (0)")
     ap.add_argument("--shard", action="store_true",
                     help="under torchrun: the ranks share the one torus (strong scaling, NCCL all-reduce per step)")
     ap.add_argument("--shard-bits", type=int, default=0,

@@ -398,10 +398,11 @@ typedef struct {
                                 mirror M -> -M before it is copied out (the global spin flip maps
                                 (E, M) to (E, -M) for any couplings): half the work, the same table.
                                 0 (default): all 2^N configurations. */
-    int32_t lane_model;      /* 1: a tile-served request of at least 36 spins gets the lane spins and
-                                histogram row stride of a quick search under the bank-conflict model
-                                (options.lane_model = 3: a few milliseconds of host time at submit,
-                                inside the request's latency); 0: the index order. The table is the
+    int32_t lane_model;      /* 1 (default): a tile-served request of at least 36 spins gets the lane
+                                spins and histogram row stride of a quick search under the
+                                bank-conflict model (options.lane_model = 3: a few milliseconds of
+                                host time at submit, inside the request's latency, against tens of
+                                milliseconds of enumeration); 0: the index order. The table is the
                                 same either way. */
 } isg_server_options;
 

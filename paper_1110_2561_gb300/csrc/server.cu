@@ -514,7 +514,7 @@ void isg_server_options_init(isg_server_options* o) {
     o->step_ms = 20.0;
     o->split_work_ratio = 0.0;
     o->symmetry = 0;
-    o->lane_model = 0;
+    o->lane_model = 1;
 }
 
 isg_status isg_server_create(const isg_server_options* opt, isg_server** out) {

@@ -94,12 +94,12 @@ def test_mix_with_split_and_symmetry_equals_alone(isg, cuda):
     srv.close()
 
 
-@pytest.mark.parametrize("opts", [{}, dict(symmetry=1), dict(lane_model=1)], ids=["every-configuration", "symmetry",
-                                                                               "lane-model"])
+@pytest.mark.parametrize("opts", [{}, dict(symmetry=1), dict(lane_model=0)], ids=["every-configuration", "symmetry",
+                                                                               "index-order"])
 def test_largest_requests_against_frontier_oracle(isg, cuda, opts):
     """Requests of N = 37 and 38, the top of the request stream's range (square and triangular,
-    periodic and free, simple cubic free, J in {-2,-1,1,2}), served in one mix (every configuration,
-    halved by the spin flip, or with the quick lane search): every table equals the oracle's
+    periodic and free, simple cubic free, J in {-2,-1,1,2}), served in one mix (every configuration
+    with the default quick lane search, halved by the spin flip, or in index order): every table equals the oracle's
     frontier programme (sites renumbered along the short side). Periodic cubic requests of this
     size are beyond the frontier's reach (cross-sections of 2 x 8 sites)."""
     from concurrent.futures import ThreadPoolExecutor
