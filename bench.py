@@ -790,15 +790,16 @@ def run_profile_case(args):
         torch.cuda.nvtx.range_pop()
         res["configs_per_s"] = 2.0 ** (36 - args.shard_bits) / (res["ms"] * 1e-3)
         isg.isg_device_status(stream)
-    elif args.profile_case in ("split-torus6x6", "split-torus7x7", "split-cubic3x3x4"):
+    elif args.profile_case in ("split-torus6x6", "split-torus7x7", "split-torus8x8", "split-cubic3x3x4"):
         lat = {"split-torus6x6": workloads.square(6, 6, True), "split-torus7x7": workloads.square(7, 7, True),
-               "split-cubic3x3x4": workloads.cubic(3, 3, 4, True)}[args.profile_case]
+               "split-torus8x8": workloads.square(8, 8, True), "split-cubic3x3x4": workloads.cubic(3, 3, 4, True)}[
+                   args.profile_case]
         gh = isg.isg_graph_create(lat.n, lat.edges)
         g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=dev)
         for _ in range(args.warmup):
             isg.isg_enumerate_split(gh, g, stream)
         res["ms"] = _event_ms(lambda: isg.isg_enumerate_split(gh, g, stream), stream, args.steps)
-        res["sum_ok"] = int(g.sum().item()) == 2 ** lat.n
+        res["sum_ok"] = sum(int(v) for v in g.cpu().numpy().ravel()) == 2 ** lat.n    # 2^64: Python integers
     else:
         raise SystemExit(f"unknown profile case {args.profile_case}")
     torch.cuda.synchronize()
@@ -817,7 +818,7 @@ def main():
     ap.add_argument("--serving", action="store_true", help="run the request-stream (serving) benchmark instead")
     ap.add_argument("--profile-case", choices=("ea-batch", "cubic-thermo", "small-thermo", "cubic-enumerate", "torus-enumerate",
                                                "split-torus6x6",
-                                               "split-torus7x7", "split-cubic3x3x4"),
+                                               "split-torus7x7", "split-torus8x8", "split-cubic3x3x4"),
                     default=None,
                     help="run only a small case of another kernel (for ncu captures)")
     ap.add_argument("--requests", type=int, default=2000)

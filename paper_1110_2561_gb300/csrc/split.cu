@@ -107,10 +107,23 @@ __device__ __forceinline__ void split_low_steps(uint32_t& addr, const int (&G)[B
 // A walker's configurations with a low block of B spins: the mid bits (L - B of them) in Gray
 // order, and at each mid state the low block from all down, its fields in registers, checked once
 // against the histogram's range (a bin outside it would be a bug: recorded in bad, not written).
-// x, e, m: the walker's configuration and its bin at the low block's all-down state.
-template <int B, class Field>
+// x, e, m: the walker's configuration and its bin at the low block's all-down state. With kFew
+// (the register-rich kernel, see split_kernel) the low spins' records {class-0 mask, class-1 mask,
+// constant} are held in registers for the whole walk, so their fields at each mid state cost two
+// popcounts each and no shared-memory load (on the 8x8 torus those loads were about a tenth of
+// the walk's shared-memory wavefronts).
+template <int B, bool kFew, class Field>
 __device__ __forceinline__ void split_walk_low(uint32_t& x, int& e, int& m, int L, int nc, int Sc, int MC, uint32_t hs,
-                                               const Field& field, bool& bad) {
+                                               const Field& field, const uint4* wsp, int J0, int J1, bool& bad) {
+    uint4 lr[kFew ? B : 1];
+    if constexpr (kFew) {
+#pragma unroll
+        for (int j = 0; j < B; ++j) lr[j] = wsp[j];
+    }
+    auto low_field = [&](int j) -> int {
+        if constexpr (kFew) return 2 * (J0 * __popc(lr[j].x & x) + J1 * __popc(lr[j].y & x)) + (int)lr[j].z;
+        else return field(j, x);
+    };
     for (uint32_t tm = 0; tm < (1u << (L - B)); ++tm) {
         if (tm) {
             const int k = B + __ffs(tm) - 1;         // the same spin in every walker
@@ -124,7 +137,7 @@ __device__ __forceinline__ void split_walk_low(uint32_t& x, int& e, int& m, int 
         int lo = e, hi = e;
 #pragma unroll
         for (int j = 0; j < B; ++j) {
-            const int h = field(j, x);
+            const int h = low_field(j);
             lo -= h > 0 ? h : 0;
             hi -= h < 0 ? h : 0;
             G[j] = 4 * (h * MC - 1);
@@ -145,8 +158,12 @@ __device__ __forceinline__ void split_walk_low(uint32_t& x, int& e, int& m, int 
 // One CTA (256 or 512 threads, from the program header) per boundary configuration at a time, in a grid-stride loop:
 // the CTA's buffers (split_warp_layout) hold one accumulator pair, the lists and a histogram, so
 // large components do not cut the number of warps per SM.
-template <class Acc, bool kFew>
-__global__ void __launch_bounds__(kSplitThreads) split_kernel(const __grid_constant__ SplitArgs a) {
+// kMinCtas: CTAs of 512 threads the register budget leaves room for per SM. 2 (at most 64
+// registers a thread) for launches whose shared memory fits two or more CTAs per SM; 1 (up to 128)
+// for those held to one CTA per SM by their buffers, which then also keep the low spins' records
+// of the component walks in registers.
+template <class Acc, bool kFew, int kMinCtas>
+__global__ void __launch_bounds__(kSplitThreads, kMinCtas == 1 ? 1 : 0) split_kernel(const __grid_constant__ SplitArgs a) {
     extern __shared__ __align__(16) unsigned char sm[];
     uint64_t* prog = reinterpret_cast<uint64_t*>(sm);
     for (int i = threadIdx.x; i < a.blob_words; i += blockDim.x) prog[i] = a.blob[i];
@@ -239,8 +256,10 @@ __global__ void __launch_bounds__(kSplitThreads) split_kernel(const __grid_const
                 int m = __popc(x);
                 if (cp.low) {
                     const uint32_t hs = (uint32_t)__cvta_generic_to_shared(hist);
-                    if (cp.low == kSplitLowLarge) split_walk_low<kSplitLowLarge>(x, e, m, L, nc, cp.Sc, MC, hs, field, bad);
-                    else split_walk_low<kSplitLow>(x, e, m, L, nc, cp.Sc, MC, hs, field, bad);
+                    constexpr bool kRegLow = kFew && kMinCtas == 1;
+                    if (cp.low == kSplitLowLarge)
+                        split_walk_low<kSplitLowLarge, kRegLow>(x, e, m, L, nc, cp.Sc, MC, hs, field, wsp, J0, J1, bad);
+                    else split_walk_low<kSplitLow, kRegLow>(x, e, m, L, nc, cp.Sc, MC, hs, field, wsp, J0, J1, bad);
                 } else {
                     // a bin outside the histogram (a bug) is recorded and skipped, never written
                     auto count = [&](int ee, int mm) {
@@ -356,10 +375,14 @@ void split_prepare_launches() {
     if ((int)raised.size() <= dev) raised.resize(dev + 1, 0);
     if (raised[dev]) return;
     const int lim = (int)device_info().smem_optin;
-    ISG_CUDA(cudaFuncSetAttribute(split_kernel<uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    ISG_CUDA(cudaFuncSetAttribute(split_kernel<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    ISG_CUDA(cudaFuncSetAttribute(split_kernel<unsigned long long, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    ISG_CUDA(cudaFuncSetAttribute(split_kernel<unsigned long long, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    const void* kernels[] = {
+        reinterpret_cast<const void*>(split_kernel<uint32_t, true, 2>), reinterpret_cast<const void*>(split_kernel<uint32_t, false, 2>),
+        reinterpret_cast<const void*>(split_kernel<unsigned long long, true, 2>),
+        reinterpret_cast<const void*>(split_kernel<unsigned long long, false, 2>),
+        reinterpret_cast<const void*>(split_kernel<uint32_t, true, 1>), reinterpret_cast<const void*>(split_kernel<uint32_t, false, 1>),
+        reinterpret_cast<const void*>(split_kernel<unsigned long long, true, 1>),
+        reinterpret_cast<const void*>(split_kernel<unsigned long long, false, 1>)};
+    for (const void* k : kernels) ISG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     raised[dev] = 1;
 }
 
@@ -380,19 +403,23 @@ void launch_split(const SplitPrepared& prep, const uint64_t* d_blob, unsigned lo
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     SplitArgs a{d_blob, (int)prep.blob.size(), table, status, n_s};
     split_prepare_launches();
-    auto launch = [&](auto kernel) {
-        const int ctas_per_sm = std::max(1, kernel_occupancy(reinterpret_cast<const void*>(kernel), threads, smem));
+    // the register-rich variant where the 64-register one cannot have two CTAs per SM anyway
+    auto launch = [&](auto kernel2, auto kernel1) {
+        int ctas_per_sm = kernel_occupancy(reinterpret_cast<const void*>(kernel2), threads, smem);
+        const int occ1 = ctas_per_sm <= 1 ? kernel_occupancy(reinterpret_cast<const void*>(kernel1), threads, smem) : 0;
+        ctas_per_sm = std::max(1, std::max(ctas_per_sm, occ1));
         const int grid = (int)std::max<unsigned long long>(
             1, std::min<unsigned long long>(n_walk, (unsigned long long)d.sms * ctas_per_sm));
-        kernel<<<grid, threads, smem, s>>>(a);
+        if (occ1 >= 1) kernel1<<<grid, threads, smem, s>>>(a);
+        else kernel2<<<grid, threads, smem, s>>>(a);
     };
     const bool few = H.n_cls <= 2;
     if (u64) {
-        if (few) launch(split_kernel<unsigned long long, true>);
-        else launch(split_kernel<unsigned long long, false>);
+        if (few) launch(split_kernel<unsigned long long, true, 2>, split_kernel<unsigned long long, true, 1>);
+        else launch(split_kernel<unsigned long long, false, 2>, split_kernel<unsigned long long, false, 1>);
     } else {
-        if (few) launch(split_kernel<uint32_t, true>);
-        else launch(split_kernel<uint32_t, false>);
+        if (few) launch(split_kernel<uint32_t, true, 2>, split_kernel<uint32_t, true, 1>);
+        else launch(split_kernel<uint32_t, false, 2>, split_kernel<uint32_t, false, 1>);
     }
     ISG_CUDA(cudaGetLastError());
 }
