@@ -52,3 +52,35 @@ def test_two_ranks_on_one_gpu_sum_to_the_oracle(tmp_path, isg, cuda, symmetric):
     out = str(tmp_path / "result.txt")
     mp.start_processes(_rank_main, args=(2, _free_port(), out, symmetric), nprocs=2, join=True, start_method="spawn")
     assert open(out).read() == "ok"
+
+
+def test_rank_shares_edge_cases(isg, cuda):
+    """isg_enumerate_rank on one process: the W shares of a graph (W = 1, 3, 5, and more ranks than
+    shards) summed on the device, added with accumulate into one table, host and device outputs,
+    with and without symmetry: all equal the oracle; a rank beyond the shard count writes zeros."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1110_2561_gb300 import workloads as w
+    lat = w.with_random_couplings(w.triangular(4, 5, True), w.SplitMix64(44), (-2, -1, 1, 2))
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    ref = oracle.g_masks(lat.n, lat.edges)
+    for W in (1, 3, 5):
+        for sym in (0, 1):
+            acc = torch.zeros(isg.table_shape(g), dtype=torch.int64, device=cuda)
+            host = np.zeros(isg.table_shape(g), dtype=np.int64)
+            for r in range(W):
+                isg.isg_enumerate_rank(g, r, W, acc, symmetry=sym, accumulate=1)
+                host += isg.isg_enumerate_rank(g, r, W, symmetry=sym)
+            torch.cuda.synchronize()
+            assert np.array_equal(acc.cpu().numpy(), ref), (W, sym)
+            assert np.array_equal(host, ref), (W, sym)
+    tiny = w.ring(3)                                       # 3 spins: 8 shards at most
+    gt = isg.isg_graph_create(tiny.n, tiny.edges)
+    parts = [isg.isg_enumerate_rank(gt, r, 16) for r in range(16)]
+    assert sum(int(p.sum()) == 0 for p in parts) >= 8
+    assert np.array_equal(sum(parts), oracle.g_edges(tiny.n, tiny.edges))
+    with pytest.raises(isg.IsgError) as ei:
+        isg.isg_enumerate_rank(g, 3, 3)
+    assert ei.value.status == 1
+    isg.isg_device_status()
