@@ -99,12 +99,15 @@ typedef struct {
                                 the batch; the others go to the tile queue. Same tables either way. */
     int32_t lane_model;      /* which spins carry the lane index of a warp (the five spins at internal
                                 positions q .. q+4, in which the 32 lanes of a warp task differ):
-                                0 = plan: the index order (as 2), except that autotuning (isg_autotune,
-                                autotune = 1, prepared batches with autotune) also times the set and
-                                the histogram row stride with the fewest shared-memory bank conflicts
-                                under a model of the warp reductions (graphs of at least 30 spins;
-                                searched once per graph structure, coupling signs aside) and keeps
-                                the faster. 1 = that model's set and stride for any graph and call.
+                                0 = plan: for isg_enumerate, isg_enumerate_rank and
+                                isg_enumerate_noalloc on graphs of at least 36 free spins, the quick
+                                search under the model below (as 3); with autotune (isg_autotune,
+                                autotune = 1, prepared batches with autotune) the timed faster of the
+                                index order and the thorough search's set and histogram row stride
+                                (graphs of at least 30 spins); otherwise the index order (as 2).
+                                Searches are cached per graph structure, coupling signs aside.
+                                1 = the set and stride with the fewest shared-memory bank conflicts
+                                under a model of the warp reductions (thorough search), any graph.
                                 2 = the five free spins after the inner ones in index order, stride
                                 by a fixed preference. 3 = the model with a quick search (dense greedy
                                 sets only, fewer draws: milliseconds instead of a tenth of a second). */

@@ -212,12 +212,16 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d, bo
     // Lane spins by the bank-conflict model (lanes.cpp): the index order's five spins at q..q+4
     // are one candidate; another set moves to those positions, with the low block and the other
     // inner spins chosen among the rest.
-    const bool use_model = o.lane_model == 1 || o.lane_model == 3 ||
+    // lane_model 0: with autotune the thorough search (graphs of kLaneModelMinFree free spins or
+    // more), else the quick one from kLaneQuickMinFree free spins (enumerations of several
+    // milliseconds against a search of about three); batches and the server choose explicitly
+    const bool plain_quick = o.lane_model == 0 && single_graph && !o.autotune && free >= kLaneQuickMinFree;
+    const bool use_model = o.lane_model == 1 || o.lane_model == 3 || plain_quick ||
                            (o.lane_model == 0 && single_graph && o.autotune && free >= kLaneModelMinFree);
     LaneChoice lc;
     if (use_model && prog_bytes + (size_t)g.n_e_c * (n + 1) * 4 <= d.smem_optin) {
         const uint64_t pool = free >= 64 ? ~0ull : ((1ull << free) - 1);
-        if (o.lane_model == 3)
+        if (o.lane_model == 3 || plain_quick)
             lc = choose_lanes_in(g, pool, &p.perm[p.q], n + 1, std::min(max_stride, n + 32), g.G, true, true);
         else
             lc = choose_lanes(g, pool, &p.perm[p.q], max_stride);

@@ -130,6 +130,8 @@ struct DeviceInfo {
 // Free spins from which autotuning considers lane spins chosen by the conflict model (smaller
 // enumerations take less time than the model's search).
 constexpr int kLaneModelMinFree = 30;
+// Free spins from which plain single-graph calls (no autotune) take the quick lane search.
+constexpr int kLaneQuickMinFree = 36;
 
 // Plan an enumeration of graph g under options o on a device with properties d. single_graph:
 // the plan serves one graph's call (isg_enumerate and its relatives), where options.lane_model
