@@ -737,9 +737,10 @@ def run_profile_case(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
     res = {"case": args.profile_case}
-    if args.profile_case == "ea-batch":
+    if args.profile_case in ("ea-batch", "ea-batch-tuned"):
         lats = workloads.ea_instances()[:256]                     # shuffled order: all four shapes
-        b = isg.Batch([isg.isg_graph_create(l.n, l.edges) for l in lats])
+        tuned = {"autotune": 1} if args.profile_case == "ea-batch-tuned" else {}
+        b = isg.Batch([isg.isg_graph_create(l.n, l.edges) for l in lats], **tuned)
         for _ in range(args.warmup):
             b.run(stream)
         res["ms"] = _event_ms(lambda: b.run(stream), stream, args.steps)
@@ -816,7 +817,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target seconds of the oracle sample")
     ap.add_argument("--serving", action="store_true", help="run the request-stream (serving) benchmark instead")
-    ap.add_argument("--profile-case", choices=("ea-batch", "cubic-thermo", "small-thermo", "cubic-enumerate", "torus-enumerate",
+    ap.add_argument("--profile-case", choices=("ea-batch", "ea-batch-tuned", "cubic-thermo", "small-thermo", "cubic-enumerate", "torus-enumerate",
                                                "split-torus6x6",
                                                "split-torus7x7", "split-torus8x8", "split-cubic3x3x4"),
                     default=None,
