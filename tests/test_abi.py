@@ -199,3 +199,20 @@ def test_lane_model_plans(isg):
     with pytest.raises(isg.IsgError) as ei:
         isg.isg_debug_plan(g, lane_model=4)
     assert ei.value.status == 1
+
+
+def test_lane_model_is_deterministic_and_sign_free(isg):
+    """The lane model's choice depends only on the graph's structure: the same lattice built twice
+    (separate handles), and a copy with every coupling's sign flipped, get the same lane spins and
+    stride; a thorough and a quick search are both repeatable."""
+    lat = w.square(6, 6, True)
+    neg = w.Lattice(lat.n, lat.edges * np.array([1, 1, -1]), "torus6x6-antiferro")
+    plans = []
+    for l in (lat, lat, neg):
+        g = isg.isg_graph_create(l.n, l.edges)
+        plans.append({k: v for k, v in isg.isg_debug_plan(g, lane_model=1).items() if k in ("lane_mask", "stride")})
+    assert plans[0] == plans[1] == plans[2]
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    q1 = isg.isg_debug_plan(g, lane_model=3)
+    q2 = isg.isg_debug_plan(isg.isg_graph_create(lat.n, lat.edges), lane_model=3)
+    assert q1 == q2
