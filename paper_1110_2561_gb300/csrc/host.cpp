@@ -236,8 +236,11 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d, bo
         for (int t = 0; t < 5; ++t) same = same && p.perm[p.q + t] == lc.spins[t];
         if (!same) {
             std::vector<int> low2 = low_block_spins(g, free, bmax, lane_mask);
-            if (o.low_bits > 0 && (int)low2.size() < o.low_bits) {
-                p.lane_model = false;              // the forced low block needs the lane spins
+            if (low2.size() < low.size()) {
+                // the low block would shrink (more mid flips, each with its program loads), which
+                // costs more than the conflicts save: keep the index order
+                p.lane_model = false;
+                p.lane_cost = p.lane_cost_index_order = 0;
             } else {
                 p.b = (int)low2.size();
                 p.q = inner_bits_for(o, free, p.b, shards_log2);
