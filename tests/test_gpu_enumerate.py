@@ -251,3 +251,24 @@ def test_device_status_clean_after_device_output_calls(isg, cuda):
     for o in outs:
         assert np.array_equal(o.cpu().numpy(), ref)
     isg.isg_device_status(clear=False)
+
+
+def test_lane_model_with_symmetry_and_rank_shares_torus_6x6(isg, cuda):
+    """Lane-model plans where the top spin (symmetry halving) or the top shard bits (rank shares)
+    are fixed, so the lane spins come from the remaining free spins: the 6x6 torus's full table
+    from the model's plan with symmetry, and from two autotuned rank shares summed, equals the
+    oracle's frontier programme."""
+    import torch
+    lat = w.square(6, 6, True)
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    ref = oracle.g_frontier(lat.n, lat.edges, max_active=16)
+    sym = torch.zeros(isg.table_shape(g), dtype=torch.int64, device=cuda)
+    isg.isg_enumerate(g, sym, lane_model=1, symmetry=1)
+    ranks = torch.zeros_like(sym)
+    for r in range(2):
+        isg.isg_enumerate_rank(g, r, 2, ranks, autotune=1, accumulate=1)
+    torch.cuda.synchronize()
+    assert np.array_equal(sym.cpu().numpy(), ref)
+    assert np.array_equal(ranks.cpu().numpy(), ref)
+    assert isg.isg_debug_plan(g, lane_model=1, symmetry=0, shard_bits=1, shard_lo=1, shard_hi=2)["lane_model"] == 1
+    isg.isg_device_status()
