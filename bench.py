@@ -737,9 +737,13 @@ def run_profile_case(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
     res = {"case": args.profile_case}
-    if args.profile_case in ("ea-batch", "ea-batch-tuned"):
-        lats = workloads.ea_instances()[:256]                     # shuffled order: all four shapes
+    if args.profile_case in ("ea-batch", "ea-batch-tuned", "ea-split-batch"):
+        lats = workloads.ea_instances()
+        if args.profile_case != "ea-split-batch":
+            lats = lats[:256]                                     # shuffled order: all four shapes
         tuned = {"autotune": 1} if args.profile_case == "ea-batch-tuned" else {}
+        if args.profile_case == "ea-split-batch":
+            tuned = {"split": 1}                                  # all 4096, the 5x6 ones by split launches
         b = isg.Batch([isg.isg_graph_create(l.n, l.edges) for l in lats], **tuned)
         for _ in range(args.warmup):
             b.run(stream)
@@ -820,7 +824,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target seconds of the oracle sample")
     ap.add_argument("--serving", action="store_true", help="run the request-stream (serving) benchmark instead")
-    ap.add_argument("--profile-case", choices=("ea-batch", "ea-batch-tuned", "cubic-thermo", "small-thermo", "cubic-enumerate", "torus-enumerate",
+    ap.add_argument("--profile-case", choices=("ea-batch", "ea-batch-tuned", "ea-split-batch", "cubic-thermo", "small-thermo", "cubic-enumerate", "torus-enumerate",
                                                "split-torus6x6",
                                                "split-torus7x7", "split-torus8x8", "split-cubic3x3x4"),
                     default=None,
