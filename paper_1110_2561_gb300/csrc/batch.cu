@@ -328,7 +328,7 @@ static void batch_enqueue(isg_batch* b, cudaStream_t s) {
     for (size_t k = 0; k < b->splits.size(); ++k) {
         const auto& j = b->splits[k];
         launch_split(*j.prep, j.d_blob, reinterpret_cast<unsigned long long*>(j.d_table), b->d_status,
-                     nb ? b->branch[k % nb] : s);
+                     nb ? b->branch[k % nb] : s, (int)std::max<size_t>(1, std::min(nb, b->splits.size())));
     }
     if (b->has_tiles)
         launch_batch(b->plan, b->d_inst, b->d_blobs, b->d_small, b->d_counter, b->d_status, s, b->ctas_per_sm);

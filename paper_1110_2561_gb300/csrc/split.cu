@@ -389,7 +389,7 @@ void split_prepare_launches() {
 // Enqueue the split kernel for a prepared plan: program at d_blob (device), table (device,
 // (S + 1)(N + 1) counts) accumulated into, status bit 0 set if a walk's self-check fails.
 void launch_split(const SplitPrepared& prep, const uint64_t* d_blob, unsigned long long* table, unsigned int* status,
-                  void* stream) {
+                  void* stream, int share) {
     const SplitHeader& H = *reinterpret_cast<const SplitHeader*>(prep.blob.data());
     const bool u64 = prep.plan.use_u64;
     const DeviceInfo d = device_info();
@@ -408,8 +408,9 @@ void launch_split(const SplitPrepared& prep, const uint64_t* d_blob, unsigned lo
         int ctas_per_sm = kernel_occupancy(reinterpret_cast<const void*>(kernel2), threads, smem);
         const int occ1 = ctas_per_sm <= 1 ? kernel_occupancy(reinterpret_cast<const void*>(kernel1), threads, smem) : 0;
         ctas_per_sm = std::max(1, std::max(ctas_per_sm, occ1));
+        const unsigned long long resident = (unsigned long long)d.sms * ctas_per_sm;
         const int grid = (int)std::max<unsigned long long>(
-            1, std::min<unsigned long long>(n_walk, (unsigned long long)d.sms * ctas_per_sm));
+            1, std::min<unsigned long long>(n_walk, std::max<unsigned long long>(1, resident / std::max(1, share))));
         if (occ1 >= 1) kernel1<<<grid, threads, smem, s>>>(a);
         else kernel2<<<grid, threads, smem, s>>>(a);
     };

@@ -177,9 +177,11 @@ std::shared_ptr<const SplitPrepared> prepare_split(const struct ::isg_graph& g, 
 
 // Device side (split.cu): enqueue the split kernel for a prepared plan on `stream` (a
 // cudaStream_t); program at d_blob, table (device) accumulated into, status bit 0 on a failed
-// self-check.
+// self-check. share > 1: the launch runs beside share - 1 others of its kind (a batch's parallel
+// branches), so its grid takes a 1/share part of the CTAs the GPU holds at once (each CTA then
+// walks more boundary configurations for its fixed costs, and the launches overlap).
 void launch_split(const SplitPrepared& prep, const uint64_t* d_blob, unsigned long long* table, unsigned int* status,
-                  void* stream);
+                  void* stream, int share = 1);
 // Set the split kernels' launch attributes on the current device (once; call before any capture).
 void split_prepare_launches();
 
