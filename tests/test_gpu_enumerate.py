@@ -174,18 +174,23 @@ def test_cubic_3x3x4_full_invariants_and_shards(isg, cuda):
 
 @pytest.mark.slow
 def test_cubic_3x3x4_full_against_popcount_oracle(isg, cuda):
-    """3x3x4 simple cubic torus, N = 36, in the benchmark's autotuned plan, and by split-and-convolve:
-    every bin of both tables equals the popcount oracle's table over all 2^36 configurations (O1 on
+    """3x3x4 simple cubic torus, N = 36, in the benchmark's autotuned plan, the default plan (quick
+    lane search), the index order's plan, and by split-and-convolve: every bin of every table
+    equals the popcount oracle's table over all 2^36 configurations (O1 on
     all host cores; minutes of CPU time). The oracle's frontier programme cannot reach this torus
     (its cross-sections hold 2 x 9 or 2 x 12 sites), so the full enumeration is the pin."""
     import torch
     lat = w.cubic(3, 3, 4, True)
     got = gpu_table(isg, cuda, lat, autotune=1)
+    default = gpu_table(isg, cuda, lat)                     # the quick lane search's plan
+    index = gpu_table(isg, cuda, lat, lane_model=2)         # the index order's
     g = isg.isg_graph_create(lat.n, lat.edges)
     split = torch.zeros(isg.table_shape(g), dtype=torch.int64, device=cuda)
     isg.isg_enumerate_split(g, split)
     ref = oracle.g_masks(lat.n, lat.edges, threads=THREADS)
     assert np.array_equal(got, ref)
+    assert np.array_equal(default, ref)
+    assert np.array_equal(index, ref)
     assert np.array_equal(split.cpu().numpy(), ref)
     isg.isg_device_status()
 
