@@ -14,6 +14,8 @@ passage of Peretyatko et al. (arXiv:1110.2561) it follows:
                     (Sec. 3a-3c), still one configuration at a time; optional OpenMP threads.
 * ``g_frontier`` -- an exact dynamic programme over the site order (no 2^N loop), for pinning
                     large lattices.
+* ``g_frontier_cut`` -- the same programme for every configuration of a cut set of spins, the
+                    rest carrying the cut's fields; for tori whose frontier is too wide.
 * ``thermo``     -- Z, <H>, <M>, C, chi from g by the definition of Eq. (2), fp64/long double.
 * ``magnetisation`` -- <|M|>, <M^2>, <M^4> and Binder's cumulant from g by the same weights.
 """
@@ -57,12 +59,14 @@ def _bind(path: str):
     lib.oracle_g_masks.argtypes = [ctypes.c_int, i64, i32p, i32p, i32p,
                                    ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, i64p]
     lib.oracle_g_frontier.argtypes = [ctypes.c_int, i64, i32p, i32p, i32p, ctypes.c_int, i64p]
+    lib.oracle_g_frontier_cut.argtypes = [ctypes.c_int, i64, i32p, i32p, i32p, ctypes.c_uint64, ctypes.c_int,
+                                          ctypes.c_int, i64p]
     lib.oracle_thermo.argtypes = [ctypes.c_int, i64, i64, i64p, ctypes.c_int, f64p,
                                   ctypes.c_int, f64p, f64p, f64p, f64p, f64p, f64p]
     lib.oracle_magnetisation.argtypes = [ctypes.c_int, i64, i64, i64p, ctypes.c_int, f64p,
                                          ctypes.c_int, f64p, f64p, f64p, f64p, f64p]
-    for f in (lib.oracle_bins, lib.oracle_g_edges, lib.oracle_g_masks,
-              lib.oracle_g_frontier, lib.oracle_thermo, lib.oracle_magnetisation):
+    for f in (lib.oracle_bins, lib.oracle_g_edges, lib.oracle_g_masks, lib.oracle_g_frontier,
+              lib.oracle_g_frontier_cut, lib.oracle_thermo, lib.oracle_magnetisation):
         f.restype = ctypes.c_int
     return lib
 
@@ -137,6 +141,19 @@ def g_frontier(n: int, edges, max_active: int = 20, lib=None) -> np.ndarray:
     _check(lib.oracle_g_frontier(n, len(i), _ptr(i, ctypes.c_int32), _ptr(j, ctypes.c_int32),
                                  _ptr(J, ctypes.c_int32), max_active, _ptr(g, ctypes.c_int64)),
            "g_frontier")
+    return g
+
+
+def g_frontier_cut(n: int, edges, cut_mask: int, max_active: int = 20, threads: int = 1, lib=None) -> np.ndarray:
+    """Exact g by the frontier programme conditioned on the spins of cut_mask (every cut
+    configuration, the rest by a frontier with the cut's fields); for lattices whose own frontier
+    is too wide. Raises if the rest's frontier exceeds max_active sites."""
+    lib = lib or _load()
+    i, j, J = _edges(edges)
+    g = _table(n, edges, lib)
+    _check(lib.oracle_g_frontier_cut(n, len(i), _ptr(i, ctypes.c_int32), _ptr(j, ctypes.c_int32),
+                                     _ptr(J, ctypes.c_int32), cut_mask, max_active, threads, _ptr(g, ctypes.c_int64)),
+           "g_frontier_cut")
     return g
 
 

@@ -25,11 +25,19 @@
  *    the number of up spins. g is stored E-major: g[e * (N + 1) + m].
  *  - Thermodynamics: H = E - h*M (Eq. 1), Z = sum over states of exp(-H/T) (Eq. 2), k_B = 1.
  *    <E> denotes <H>, C = Var(H) / T^2, chi = Var(M) / T, all per system.
+ *
+ * Methods for g: oracle_g_edges (the definition, bond by bond), oracle_g_masks (the mask and
+ * popcount form of Sec. 3a-3c), oracle_g_frontier (a transfer matrix over the site order) and
+ * oracle_g_frontier_cut (the same, for every configuration of a cut set of spins). All four are
+ * pinned by the tests against Table 1 (Sec. 4), closed forms and brute force.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_ERR_INVALID 1
@@ -217,33 +225,39 @@ int oracle_g_masks(int n, int64_t n_edges, const int32_t* ei, const int32_t* ej,
  * last bond has been added is summed out. Cost grows as 2^(active sites); max_active bounds it.
  * Used to pin the other oracles and the enumerator on lattices too large for 2^N loops
  * (Sec. 2: g(E,M) is the degeneracy of the spin excess over the energy).
+ *
+ * frontier_rest runs the programme over the spins outside a cut set (cut bit i = spin i fixed
+ * elsewhere), each carrying the cut's field f[v] as a one-spin energy term -f[v] S_v; with an
+ * empty cut and f = 0 it is the plain programme of oracle_g_frontier.
  * ---------------------------------------------------------------------------------------- */
-int oracle_g_frontier(int n, int64_t n_edges, const int32_t* ei, const int32_t* ej, const int32_t* J,
-                      int max_active, int64_t* g) {
-    int64_t K[64 * 64];
-    int rc = build_couplings(n, n_edges, ei, ej, J, K);
-    if (rc != ORC_OK) return rc;
-    if (max_active > 24) max_active = 24;
-    int last_nb[64];                 /* largest neighbour index of each site, -1 if isolated */
+/* The rest's table out[e_r * (n_rest + 1) + m_r], e_r = (E_rest + S_rest) / 2, given the cut
+ * field f[v] on every rest spin v; out holds (S_rest + 1) * (n_rest + 1) entries, overwritten. */
+static int frontier_rest(int n, const int64_t* K, uint64_t cut, const int64_t* f, int64_t S_rest, int n_rest,
+                         int max_active, int64_t* out) {
+    int last_nb[64];                 /* largest rest neighbour index of each rest site, -1 if none */
     for (int i = 0; i < n; ++i) {
         last_nb[i] = -1;
+        if ((cut >> i) & 1) continue;
         for (int j = 0; j < n; ++j)
-            if (K[i * n + j] != 0 && j > last_nb[i]) last_nb[i] = j;
+            if (!((cut >> j) & 1) && K[i * n + j] != 0 && j > last_nb[i]) last_nb[i] = j;
     }
     int act[64];
-    int na = 0;                      /* active sites, bit t of a table index is site act[t] */
-    int64_t Sp = 0;                  /* sum |J| over bonds among added sites */
+    int na = 0, added = 0;
+    int64_t Sp = 0;                  /* sum |J| over the bonds included so far (rest-rest and to the cut) */
     int64_t* tab = (int64_t*)calloc(1, sizeof(int64_t));
     if (!tab) return ORC_ERR_NOMEM;
     tab[0] = 1;                      /* empty configuration: energy 0 (e = 0 at Sp = 0), 0 up */
-    /* layout: tab[(a * ne + e) * nm + m] with ne = Sp + 1 and nm = added + 1 */
+    /* layout: tab[(a * ne + e) * nm + m] with ne = Sp + 1 and nm = added + 1; bit t of a is the
+     * spin of active site act[t] */
     for (int v = 0; v < n; ++v) {
-        int added = v;               /* sites already added */
+        if ((cut >> v) & 1) continue;
         int64_t ne = Sp + 1, nm = added + 1;
         int64_t dS = 0;
         for (int t = 0; t < na; ++t) dS += llabs(K[act[t] * n + v]);
-        for (int u = 0; u < v; ++u)  /* every bond to an earlier site must reach an active one */
-            if (K[u * n + v] != 0) {
+        for (int j = 0; j < n; ++j)
+            if ((cut >> j) & 1) dS += llabs(K[v * n + j]);
+        for (int u = 0; u < v; ++u)  /* every rest bond to an earlier rest site must reach an active one */
+            if (!((cut >> u) & 1) && K[u * n + v] != 0) {
                 int ok = 0;
                 for (int t = 0; t < na; ++t) if (act[t] == u) ok = 1;
                 if (!ok) { free(tab); return ORC_ERR_INVALID; }
@@ -251,13 +265,12 @@ int oracle_g_frontier(int n, int64_t n_edges, const int32_t* ei, const int32_t* 
         int na1 = na + 1;
         if (na1 > max_active) { free(tab); return ORC_ERR_TOO_LARGE; }
         int64_t ne1 = Sp + dS + 1, nm1 = added + 2;
-        size_t sz1 = ((size_t)1 << na1) * (size_t)ne1 * (size_t)nm1;
-        int64_t* t1 = (int64_t*)calloc(sz1, sizeof(int64_t));
+        int64_t* t1 = (int64_t*)calloc(((size_t)1 << na1) * (size_t)ne1 * (size_t)nm1, sizeof(int64_t));
         if (!t1) { free(tab); return ORC_ERR_NOMEM; }
         for (int64_t a = 0; a < ((int64_t)1 << na); ++a) {
             for (int sv = 0; sv < 2; ++sv) {
                 int Sv = sv ? +1 : -1;
-                int64_t dE = 0;      /* -J S_u S_v over the new bonds */
+                int64_t dE = -f[v] * Sv;     /* the bonds to the cut, then to the active rest sites */
                 for (int t = 0; t < na; ++t) {
                     int64_t Kuv = K[act[t] * n + v];
                     if (Kuv == 0) continue;
@@ -278,8 +291,8 @@ int oracle_g_frontier(int n, int64_t n_edges, const int32_t* ei, const int32_t* 
         act[na] = v;
         na = na1;
         Sp += dS;
-        /* sum out sites whose last bond is now in */
-        int keep[64], nk = 0;
+        ++added;
+        int keep[64], nk = 0;        /* sum out rest sites whose last rest bond is now in */
         for (int t = 0; t < na; ++t)
             if (last_nb[act[t]] > v) keep[nk++] = t;
         if (nk < na) {
@@ -299,10 +312,111 @@ int oracle_g_frontier(int n, int64_t n_edges, const int32_t* ei, const int32_t* 
             na = nk;
         }
     }
-    /* na == 0 now: tab holds g with ne = Sp + 1, nm = n + 1 */
-    for (int64_t x = 0; x < (Sp + 1) * (int64_t)(n + 1); ++x) g[x] += tab[x];
+    if (Sp != S_rest || added != n_rest) { free(tab); return ORC_ERR_INVALID; }
+    memcpy(out, tab, sizeof(int64_t) * (size_t)(S_rest + 1) * (size_t)(n_rest + 1));
     free(tab);
     return ORC_OK;
+}
+
+int oracle_g_frontier(int n, int64_t n_edges, const int32_t* ei, const int32_t* ej, const int32_t* J,
+                      int max_active, int64_t* g) {
+    int64_t K[64 * 64];
+    int rc = build_couplings(n, n_edges, ei, ej, J, K);
+    if (rc != ORC_OK) return rc;
+    if (max_active > 24) max_active = 24;
+    const int64_t S = total_abs_coupling(n, K);
+    int64_t f[64];
+    for (int v = 0; v < 64; ++v) f[v] = 0;
+    int64_t* tab = (int64_t*)calloc((size_t)(S + 1) * (size_t)(n + 1), sizeof(int64_t));
+    if (!tab) return ORC_ERR_NOMEM;
+    rc = frontier_rest(n, K, 0, f, S, n, max_active, tab);
+    if (rc == ORC_OK)
+        for (int64_t x = 0; x < (S + 1) * (int64_t)(n + 1); ++x) g[x] += tab[x];
+    free(tab);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Frontier programme conditioned on a cut: an exact method for g(E,M) on lattices whose own
+ * frontier is too wide (on a torus every cross-section is crossed twice). For every
+ * configuration c of the spins in cut_mask (bit i = spin i), the other spins ("the rest") are
+ * added in index order as in oracle_g_frontier: among themselves by their bonds, and to the cut
+ * through the field f_v(c) = sum over cut spins j of J_vj S_j, a one-spin energy term -f_v S_v
+ * (each bond to the cut counted once, as in Eq. 1). The rest's table over its energy and up
+ * count is then shifted by the energy of the cut's own bonds and the cut's up count and added into
+ * g: every configuration is exactly one c with one configuration of the rest, so the sum over c
+ * counts every configuration once by its E and M (Sec. 2). Bins: e = (E + S)/2 splits as
+ * (E_cut + S_cut)/2 + (E_rest + S_rest)/2, S_cut the sum of |J| over bonds inside the cut and
+ * S_rest over the bonds touching the rest. threads > 1 hands the cut configurations to OpenMP
+ * threads, each with its own table, summed at the end. The cut may be empty or hold every spin.
+ * ---------------------------------------------------------------------------------------- */
+int oracle_g_frontier_cut(int n, int64_t n_edges, const int32_t* ei, const int32_t* ej, const int32_t* J,
+                          uint64_t cut_mask, int max_active, int threads, int64_t* g) {
+    int64_t K[64 * 64];
+    int rc = build_couplings(n, n_edges, ei, ej, J, K);
+    if (rc != ORC_OK) return rc;
+    if (n < 64 && (cut_mask >> n) != 0) return ORC_ERR_INVALID;
+    if (max_active > 24) max_active = 24;
+    int cut[64], k = 0;
+    for (int i = 0; i < n; ++i) if ((cut_mask >> i) & 1) cut[k++] = i;
+    if (k > 30) return ORC_ERR_TOO_LARGE;
+    const int64_t S = total_abs_coupling(n, K);
+    int64_t S_cut = 0;
+    for (int a = 0; a < k; ++a)
+        for (int b = a + 1; b < k; ++b) S_cut += llabs(K[cut[a] * n + cut[b]]);
+    const int64_t S_rest = S - S_cut;
+    const int n_rest = n - k;
+    const size_t nbins = (size_t)(S + 1) * (size_t)(n + 1);
+    const size_t rbins = (size_t)(S_rest + 1) * (size_t)(n_rest + 1);
+    if (threads < 1) threads = 1;
+    int64_t* part = (int64_t*)calloc((size_t)threads * nbins, sizeof(int64_t));
+    int64_t* rest = (int64_t*)calloc((size_t)threads * rbins, sizeof(int64_t));
+    if (!part || !rest) { free(part); free(rest); return ORC_ERR_NOMEM; }
+    const int64_t n_cut_configs = (int64_t)1 << k;
+    int status = ORC_OK;
+#pragma omp parallel for num_threads(threads) schedule(dynamic, 1)
+    for (int64_t c = 0; c < n_cut_configs; ++c) {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        int spin[64];
+        for (int i = 0; i < n; ++i) spin[i] = 0;
+        int up = 0;
+        for (int a = 0; a < k; ++a) {
+            spin[cut[a]] = ((c >> a) & 1) ? +1 : -1;
+            up += (int)((c >> a) & 1);
+        }
+        int64_t E_cut = 0;           /* -J S_i S_j over the bonds inside the cut */
+        for (int a = 0; a < k; ++a)
+            for (int b = a + 1; b < k; ++b) E_cut -= K[cut[a] * n + cut[b]] * spin[cut[a]] * spin[cut[b]];
+        int64_t f[64];               /* field of the cut on every rest spin */
+        for (int v = 0; v < n; ++v) {
+            f[v] = 0;
+            if ((cut_mask >> v) & 1) continue;
+            for (int a = 0; a < k; ++a) f[v] += K[v * n + cut[a]] * spin[cut[a]];
+        }
+        int64_t* rt = rest + (size_t)tid * rbins;
+        int rc2 = frontier_rest(n, K, cut_mask, f, S_rest, n_rest, max_active, rt);
+        if (rc2 != ORC_OK) {
+#pragma omp critical
+            status = rc2;
+            continue;
+        }
+        const int64_t e_cut = (E_cut + S_cut) / 2;
+        int64_t* gt = part + (size_t)tid * nbins;
+        for (int64_t er = 0; er <= S_rest; ++er)
+            for (int64_t mr = 0; mr <= n_rest; ++mr) {
+                const int64_t cnt = rt[er * (n_rest + 1) + mr];
+                if (cnt) gt[(e_cut + er) * (n + 1) + up + mr] += cnt;
+            }
+    }
+    if (status == ORC_OK)
+        for (int t = 0; t < threads; ++t)
+            for (size_t b = 0; b < nbins; ++b) g[b] += part[(size_t)t * nbins + b];
+    free(part);
+    free(rest);
+    return status;
 }
 
 /* ------------------------------------------------------------------------------------------

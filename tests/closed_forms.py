@@ -2,7 +2,9 @@
 results). Nothing here calls the oracle or the CUDA path.
 
 * Kaufman's partition function of the m x n periodic square lattice (B. Kaufman, Phys. Rev. 76,
-  1232 (1949)), J = 1, h = 0.
+  1232 (1949)), J = 1, h = 0; and from it, in exact arithmetic, the number of configurations
+  with every energy (the coefficients of Z as a polynomial in exp(-2K), as P. D. Beale, Phys.
+  Rev. Lett. 76, 78 (1996), obtained them).
 * The periodic chain in a field, from the 2 x 2 transfer matrix (Ising 1925).
 * Non-interacting spins in a field.
 * Run counting on a ring: the number of cyclic binary strings with U ones and 2r runs.
@@ -55,6 +57,54 @@ def kaufman_logz(m: int, n: int, T: float, J: float = 1.0) -> float:
     lmax = max(l for s, l in terms if s != 0)
     tot = math.fsum(s * math.exp(l - lmax) for s, l in terms if s != 0)
     return math.log(0.5) + (m * n / 2) * math.log(2 * math.sinh(2 * K)) + lmax + math.log(tot)
+
+
+def _kaufman_z_mp(m: int, n: int, K):
+    """Kaufman's Z of the m x n torus at coupling K (J = 1, h = 0) in mpmath at the working precision."""
+    import mpmath as mp
+    c = mp.cosh(2 * K) / mp.tanh(2 * K)
+
+    def gamma(l: int):
+        if l == 0:
+            return 2 * K + mp.log(mp.tanh(K))
+        return mp.acosh(c - mp.cos(mp.pi * l / n))
+
+    odd = [gamma(2 * r + 1) for r in range(n)]
+    even = [gamma(2 * r) for r in range(n)]
+    p = mp.mpf(0)
+    for gs in (odd, even):
+        p += mp.fprod(2 * mp.cosh(m * g / 2) for g in gs)
+        p += mp.fprod(2 * mp.sinh(m * g / 2) for g in gs)
+    return mp.mpf(1) / 2 * (2 * mp.sinh(2 * K)) ** (mp.mpf(m * n) / 2) * p
+
+
+def kaufman_energy_counts(m: int, n: int, digits: int = 0) -> list:
+    """Exact number of configurations of the m x n torus (J = 1) with k unsatisfied bonds, k = 0..2mn
+    (E = -2mn + 2k), from Kaufman's closed form alone: Z e^(-2mnK) = sum_k g_k x^k with x = e^(-2K)
+    is a polynomial of degree 2mn; it is evaluated at 2mn + 1 points of (0, 1) in high precision,
+    interpolated (Newton's divided differences, then the monomial coefficients) and rounded to
+    integers. Each coefficient is checked to be within 0.01 of its integer."""
+    import mpmath as mp
+    d = 2 * m * n
+    with mp.workdps(digits or 4 * d + 60):
+        xs = [mp.mpf(j + 1) / (d + 2) for j in range(d + 1)]
+        ys = [_kaufman_z_mp(m, n, -mp.log(x) / 2) * x ** (m * n) for x in xs]   # e^(-2mnK) = x^(mn)
+        coef = list(ys)                        # divided differences, in place
+        for lvl in range(1, d + 1):
+            for i in range(d, lvl - 1, -1):
+                coef[i] = (coef[i] - coef[i - 1]) / (xs[i] - xs[i - lvl])
+        poly = [mp.mpf(0)] * (d + 1)           # Newton form -> monomials, Horner from the top
+        for i in range(d, -1, -1):
+            for k in range(d, 0, -1):
+                poly[k] = poly[k - 1] - xs[i] * poly[k]
+            poly[0] = coef[i] - xs[i] * poly[0]
+        out = []
+        for c in poly:
+            r = int(mp.nint(c))
+            if abs(c - r) > mp.mpf("0.01"):
+                raise ArithmeticError("interpolated coefficient is not an integer: precision too low")
+            out.append(r)
+    return out
 
 
 def ring_logz(n: int, T: float, h: float = 0.0, J: float = 1.0) -> float:

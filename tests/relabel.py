@@ -5,7 +5,9 @@ that still have a bond to a site not yet added, so its cost grows as 2^(width of
 The table g(E, M) does not depend on how the spins are numbered (E and M are sums over bonds and
 spins), so a test may renumber a lattice before handing it to the oracle. Numbering the sites
 with the shortest side of the box varying fastest keeps the frontier to about one (free) or two
-(periodic) cross-sections of the box.
+(periodic) cross-sections of the box; conditioning the programme on the spins of the first
+cross-section along the longest side (``layer_cut``) turns a periodic box's wrap-around bonds into
+fields, so the rest's frontier holds about one cross-section.
 """
 from __future__ import annotations
 
@@ -35,3 +37,20 @@ def short_side_fastest(lat: w.Lattice) -> w.Lattice:
     e[:, 0] = new[e[:, 0]]
     e[:, 1] = new[e[:, 1]]
     return w.Lattice(lat.n, e, lat.name + "-relabelled", dict(lat.meta))
+
+
+def layer_cut(lat: w.Lattice):
+    """(the lattice numbered by short_side_fastest, cut mask): the cut holds the sites whose
+    coordinate along the box's longest side is 0 (the first cross-section in that numbering), for
+    the oracle's programme conditioned on a cut. A lattice without box dimensions gets an empty cut."""
+    dims = lat.meta.get("dims")
+    r = short_side_fastest(lat)
+    if not dims:
+        return r, 0
+    dims = tuple(int(d) for d in dims)
+    coords = np.array(np.unravel_index(np.arange(lat.n), dims)).T
+    slowest = max(range(len(dims)), key=lambda a: (dims[a], -a))
+    # short_side_fastest keeps the site order along the slowest side, so the sites with coordinate 0
+    # there are renumbered 0 .. k-1
+    k = int((coords[:, slowest] == 0).sum())
+    return r, (1 << k) - 1

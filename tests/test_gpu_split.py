@@ -1,16 +1,18 @@
 """Split-and-convolve enumeration on the GPU (isg_enumerate_split): exact tables against the
 oracle's full enumeration, its frontier programme, and the direct GPU enumeration."""
 import math
+import os
 
 import numpy as np
 import pytest
 
 import oracle
 from paper_1110_2561_gb300 import workloads as w
-from closed_forms import kaufman_logz
+from closed_forms import kaufman_energy_counts, kaufman_logz
 from test_split_host import CASES, mask
 
 pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 1
 
 
 @pytest.mark.parametrize("lat,boundary", CASES, ids=[c[0].name or "free-spins" for c in CASES])
@@ -134,10 +136,11 @@ def test_split_large_four_classes(isg, cuda, shape, seed):
 
 
 def test_split_torus_8x8(isg, cuda):
-    """The 8x8 torus, N = 64: all 2^64 configurations (the largest graph the library takes). No
-    table oracle reaches it, so it is pinned by facts that hold at any size: sum 2^64 (in Python
-    integers), every column C(64, m), the M -> -M and bipartite E -> -E symmetries, two ground
-    states, and ln Z from the table against Kaufman's closed form at four temperatures."""
+    """The 8x8 torus, N = 64: all 2^64 configurations (the largest graph the library takes). Every
+    one of the 129 x 65 bins equals the oracle's frontier programme conditioned on one row (2^8 rest
+    programmes of 56 spins, all host cores); every energy count equals Kaufman's exact count; and
+    the facts that hold at any size: sum 2^64 (in Python integers), every column C(64, m), the
+    M -> -M and bipartite E -> -E symmetries, two ground states, ln Z against Kaufman's closed form."""
     lat = w.square(8, 8, True)
     gh = isg.isg_graph_create(lat.n, lat.edges)
     g = isg.isg_enumerate_split(gh)
@@ -146,10 +149,13 @@ def test_split_torus_8x8(isg, cuda):
     assert np.array_equal(g, g[:, ::-1])
     assert np.array_equal(g.sum(axis=1), g.sum(axis=1)[::-1])
     assert int(g[0, 0]) == 1 and int(g[0, 64]) == 1 and not g[0, 1:64].any()
+    assert [int(x) for x in g.sum(axis=1)] == kaufman_energy_counts(8, 8)
     T = np.array([1.5, 2.269, 3.0, 5.0])
     lz = isg.isg_thermo(g, gh, T, [0.0], isg.ISG_FP64)[0][:, 0]
     for t, l in zip(T, lz):
         assert abs(l - kaufman_logz(8, 8, t)) <= 1e-12 * abs(l)
+    ref = oracle.g_frontier_cut(lat.n, lat.edges, mask(range(8)), max_active=18, threads=THREADS)
+    assert np.array_equal(g, ref)
 
 
 def test_specific_heat_peak_8x8_kaufman(isg, cuda):

@@ -25,6 +25,13 @@ MUTANTS = [
     ("masks: M from down spins", "g[((E + S) / 2) * (n + 1) + up] += 1;", "g[((E + S) / 2) * (n + 1) + (n - up) * (E != 0) + up * (E == 0)] += 1;"),
     ("frontier: energy sign", "dE -= Kuv * Su * Sv;", "dE += Kuv * Su * Sv;"),
     ("frontier: up count lost", "t1[(a1 * ne1 + e + de) * nm1 + m + sv] += c;", "t1[(a1 * ne1 + e + de) * nm1 + m + (sv && (v & 1))] += c;"),
+    ("frontier cut: field sign", "int64_t dE = -f[v] * Sv;", "int64_t dE = +f[v] * Sv;"),
+    ("frontier cut: cut's up count dropped", "if (cnt) gt[(e_cut + er) * (n + 1) + up + mr] += cnt;",
+     "if (cnt) gt[(e_cut + er) * (n + 1) + mr] += cnt;"),
+    ("frontier cut: bonds inside the cut dropped", "E_cut -= K[cut[a] * n + cut[b]] * spin[cut[a]] * spin[cut[b]];",
+     "E_cut -= 0 * K[cut[a] * n + cut[b]] * spin[cut[a]] * spin[cut[b]];"),
+    ("frontier cut: field of the last cut spin lost", "for (int a = 0; a < k; ++a) f[v] += K[v * n + cut[a]] * spin[cut[a]];",
+     "for (int a = 0; a + 1 < k; ++a) f[v] += K[v * n + cut[a]] * spin[cut[a]];"),
     ("thermo: field sign", "long double H = E - f * M;\n                    long double w = expl(logl((long double)c) - H / t - Lmax);\n                    Z += w;",
      "long double H = E + f * M;\n                    long double w = expl(logl((long double)c) - H / t - Lmax);\n                    Z += w;"),
     ("thermo: C over T", "C[p] = (double)(vH / (t * t));", "C[p] = (double)(vH / t);"),
@@ -64,6 +71,19 @@ def pins_pass(lib, table1_triples) -> bool:
             g = fn(fl.n, fl.edges, lib=lib)
             if g[0, 0] != 1 or g[0, fl.n] != 1 or any(int(g[:, m].sum()) != math.comb(fl.n, m) for m in range(fl.n + 1)):
                 return False
+        # the programme conditioned on a cut: Table 1 with one row cut, and a signed random graph
+        for cut in (0xF, 0xA5A5):
+            g = oracle.g_frontier_cut(lat.n, lat.edges, cut, lib=lib)
+            e_min, _, _ = oracle.bins(lat.n, lat.edges, lib=lib)
+            got = {(e_min + 2 * int(e), -lat.n + 2 * int(m)): int(g[e, m]) for e, m in zip(*np.nonzero(g))}
+            if got != want:
+                return False
+        cg = w.random_graph(10, 18, w.SplitMix64(12))
+        want_c = brute_force_g_range(cg.n, [tuple(int(x) for x in r) for r in cg.edges], 0, 1 << cg.n)
+        g = oracle.g_frontier_cut(cg.n, cg.edges, 0b1001101001, lib=lib)
+        e_min, _, _ = oracle.bins(cg.n, cg.edges, lib=lib)
+        if {(e_min + 2 * int(e), -cg.n + 2 * int(m)): int(g[e, m]) for e, m in zip(*np.nonzero(g))} != want_c:
+            return False
         # configuration ranges: which words a range holds (spin i is bit i)
         rg = w.random_graph(9, 14, w.SplitMix64(11))
         edges = [tuple(int(x) for x in r) for r in rg.edges]

@@ -5,6 +5,7 @@ or M, a transposed bin index, a wrong power of T -- fails at least one of them (
 tests in test_oracle_mutants.py check exactly that).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -12,8 +13,10 @@ import pytest
 import oracle
 from paper_1110_2561_gb300 import workloads as w
 from closed_forms import (brute_force_g, brute_force_g_range, brute_force_magnetisation, free_spin_moments,
-                          free_spins, golden_max, kaufman_C, kaufman_C_peak, kaufman_logz, ring_joint_count,
-                          ring_logz, ring_M2)
+                          free_spins, golden_max, kaufman_C, kaufman_C_peak, kaufman_energy_counts, kaufman_logz,
+                          ring_joint_count, ring_logz, ring_M2)
+
+THREADS = os.cpu_count() or 1
 
 
 def as_dict(g: np.ndarray, n: int, e_min: int):
@@ -190,6 +193,86 @@ def test_frontier_large_lattices_invariants():
     lz = oracle.thermo(lat.n, e_min, g, T, [0.0])[0][:, 0]
     for t, l in zip(T, lz):
         assert abs(l - kaufman_logz(6, 6, t)) <= 1e-13 * abs(l)
+
+
+# --------------------------------------------------------------------------- conditioned frontier
+def _mask(sites):
+    out = 0
+    for i in sites:
+        out |= 1 << i
+    return out
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_frontier_cut_brute_force(seed):
+    """The frontier programme conditioned on a cut set, on random multigraphs (couplings in
+    {-2,-1,1,2}, duplicate edges, isolated spins) with an empty, a full and two random cut sets,
+    against the pure-Python brute force of the definition."""
+    rng = w.SplitMix64(300 + seed)
+    n = 2 + rng.below(10)
+    lat = w.random_graph(n, rng.below(2 * n + 1), rng)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    want = {k: v for k, v in brute_force_g(lat.n, [tuple(int(x) for x in r) for r in lat.edges]).items() if v}
+    full = (1 << n) - 1
+    for cut in (0, full, rng.next_u64() & full, rng.next_u64() & full):
+        assert as_dict(oracle.g_frontier_cut(lat.n, lat.edges, cut, threads=2), lat.n, e_min) == want, cut
+
+
+@pytest.mark.parametrize("cut", [_mask(range(4)), _mask(i for i in range(16) if (i // 4 + i % 4) % 2 == 0),
+                                 _mask([0, 5, 10, 15]), _mask(range(16))], ids=["row", "checkerboard", "diagonal", "all"])
+def test_frontier_cut_table1(table1_triples, cut):
+    """Table 1 (Sec. 4) through the conditioned programme, for cut sets of several shapes."""
+    lat = w.square(4, 4, True)
+    g = oracle.g_frontier_cut(lat.n, lat.edges, cut)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    assert as_dict(g, lat.n, e_min) == {(E, M): nc for nc, M, E in table1_triples}
+
+
+def test_frontier_cut_rejects():
+    lat = w.square(4, 4, True)
+    with pytest.raises(ValueError):
+        oracle.g_frontier_cut(lat.n, lat.edges, 1 << 16)          # a cut spin outside the graph
+    with pytest.raises(ValueError):
+        oracle.g_frontier_cut(lat.n, lat.edges, 0, max_active=2)  # the rest's frontier is wider
+
+
+@pytest.mark.parametrize("m,n", [(3, 3), (4, 4), (3, 5), (5, 4), (4, 6)])
+def test_exact_energy_counts_kaufman(m, n):
+    """The energy marginal of g, bin for bin, against the exact counts that Kaufman's closed form
+    alone gives (the coefficients of Z as a polynomial in exp(-2K)), from every oracle."""
+    lat = w.square(m, n, True)
+    want = kaufman_energy_counts(m, n)
+    assert sum(want) == 2 ** (m * n)
+    tables = [oracle.g_frontier(lat.n, lat.edges), oracle.g_frontier_cut(lat.n, lat.edges, _mask(range(n)))]
+    if m * n <= 20:
+        tables.append(oracle.g_masks(lat.n, lat.edges, threads=THREADS))
+    for g in tables:
+        assert [int(x) for x in g.sum(axis=1)] == want
+
+
+def _torus_pins(g, m, n):
+    N = m * n
+    assert sum(int(v) for v in g.ravel()) == 2 ** N
+    assert all(sum(int(v) for v in g[:, k]) == math.comb(N, k) for k in range(N + 1))
+    assert np.array_equal(g, g[:, ::-1])
+    assert [int(x) for x in g.sum(axis=1)] == kaufman_energy_counts(m, n)
+    assert int(g[0, 0]) == 1 and int(g[0, N]) == 1 and not g[0, 1:N].any()
+
+
+def test_frontier_cut_torus_7x7():
+    """The 7x7 torus (N = 49) by the programme conditioned on one row: every energy count exactly
+    as Kaufman's closed form gives it, every spin-excess column C(49, m), the M -> -M mirror and
+    the two ground states."""
+    lat = w.square(7, 7, True)
+    _torus_pins(oracle.g_frontier_cut(lat.n, lat.edges, _mask(range(7)), max_active=16, threads=THREADS), 7, 7)
+
+
+def test_frontier_cut_torus_8x8():
+    """The 8x8 torus (N = 64, 2^64 configurations) by the programme conditioned on one row (2^8
+    rest programmes of 56 spins): the same pins as the 7x7 torus; the table's largest count is
+    2.6e18 and its sum 2^64 (checked in Python integers)."""
+    lat = w.square(8, 8, True)
+    _torus_pins(oracle.g_frontier_cut(lat.n, lat.edges, _mask(range(8)), max_active=18, threads=THREADS), 8, 8)
 
 
 # --------------------------------------------------------------------------- thermodynamics
