@@ -100,8 +100,9 @@ typedef struct {
     int32_t lane_model;      /* which spins carry the lane index of a warp (the five spins at internal
                                 positions q .. q+4, in which the 32 lanes of a warp task differ):
                                 0 = plan: for isg_enumerate, isg_enumerate_rank and
-                                isg_enumerate_noalloc on graphs of at least 36 free spins, the quick
-                                search under the model below (as 3); with autotune (isg_autotune,
+                                isg_enumerate_noalloc, lane tables (as 4) where one copy of them fits
+                                shared memory and no stride is fixed; else on graphs of at least 36
+                                free spins the quick search under the model below (as 3); with autotune (isg_autotune,
                                 autotune = 1, prepared batches with autotune) the timed faster of the
                                 index order and the thorough search's set and histogram row stride
                                 (graphs of at least 30 spins); otherwise the index order (as 2).
@@ -110,7 +111,13 @@ typedef struct {
                                 under a model of the warp reductions (thorough search), any graph.
                                 2 = the five free spins after the inner ones in index order, stride
                                 by a fixed preference. 3 = the model with a quick search (dense greedy
-                                sets only, fewer draws: milliseconds instead of a tenth of a second). */
+                                sets only, fewer draws: milliseconds instead of a tenth of a second).
+                                4 = lane tables: the index order's lane spins, every histogram copy
+                                split into ten sub-tables with a row stride that is a multiple of
+                                32, so that each lane's shared-memory bank is fixed by its up count
+                                and its sub-table; no warp reduction has a bank conflict, on any
+                                graph. A copy takes ten times the padded histogram; TOO_LARGE if one
+                                does not fit shared memory. */
 } isg_options;
 
 /* Fill *opt with the defaults (all planner choices, full range, overwrite). */

@@ -15,15 +15,27 @@ extern "C" {
 
 /*
  * The plan isg_enumerate would use for this graph and these options on a device with `sms`
- * multiprocessors (0 = 152). out[0..17] = small-kernel flag, inner bits q, low-block size b,
+ * multiprocessors (0 = 152). out[0..18] = small-kernel flag, inner bits q, low-block size b,
  * warp tasks, threads per CTA, histogram copies, CTAs per SM, tasks per flush round, grid,
  * shared-memory bytes per CTA, energy stride G, compact energy bins, bytes of the program that
  * isg_enumerate copies to the device, histogram row stride, whether the lane spins come from the
  * bank-conflict model (options.lane_model), the model's expected shared-memory wavefronts per warp
  * reduction of the plan and of the index order's lane spins (both x 10^6; 0 without the model),
- * and the mask of the five lane spins (caller numbering). Errors as isg_enumerate.
+ * the mask of the five lane spins (caller numbering), and the histogram sub-tables per copy
+ * (1, or 10 with lane tables: options.lane_model = 4). Errors as isg_enumerate.
  */
 ISG_API isg_status isg_debug_plan(const isg_graph* graph, const isg_options* opt, int32_t sms, int64_t* out);
+
+/*
+ * Shared-memory wavefronts of the enumeration kernel's warp reductions under the plan of *opt,
+ * sampled on the host: for `samples` draws (splitmix64 from `seed`) of a warp task and an inner
+ * configuration, the 32 lanes' word addresses (the lane's sub-table start plus its bin) at that
+ * step, and the most distinct addresses that fall in one of the 32 banks (the wavefronts the
+ * reduction takes; lanes at one address share one). Writes their mean and maximum. Errors:
+ * INVALID (NULL pointers, samples < 1, or a plan without warp tasks), as isg_enumerate otherwise.
+ */
+ISG_API isg_status isg_debug_lane_banks(const isg_graph* graph, const isg_options* opt, int32_t samples, uint64_t seed,
+                                        double* mean_wavefronts, int32_t* max_wavefronts);
 
 /*
  * Run the enumeration kernels' per-thread walk on the host, with every counter address checked,

@@ -38,6 +38,9 @@ namespace isg {
 constexpr int kMaxSpins = 64;
 constexpr int kMaxClasses = 21;   // |J| <= 2^20 decomposes into at most 21 binary weights
 constexpr int kMaxLow = 7;        // largest low block
+// Lane tables: sub-tables per histogram copy when every lane's bank is fixed by its up count
+// (the number of 5-bit lane values of the commonest popcount, C(5, 2))
+constexpr int kLaneTables = 10;
 
 // Per-spin record of a program, 48 bytes and 16-byte aligned, so a mid flip reads everything it
 // needs about its spin with three 128-bit shared-memory loads.

@@ -43,6 +43,11 @@ struct EnumArgs {
     int32_t blob_words;
     int32_t copies;
     int32_t flush_rounds;
+    int32_t copy_words;              // words of one histogram copy
+    int32_t n_sub;                   // sub-tables per copy (1, or kLaneTables for lane tables)
+    int32_t sub_words;               // words per sub-table
+    int32_t sub_off[kLaneTables];    // first bin of sub-table t lies sub_off[t] words into it
+    int32_t lane_word[32];           // lane l counts into the bins starting lane_word[l] words into its copy
     int32_t pad;
 };
 
@@ -59,15 +64,18 @@ struct EnumParams {
     uint64_t program[kInlineProgramWords];
 };
 
-// Add the CTA's privatised bins into the public int64 table and clear them.
-__device__ __forceinline__ void flush_bins(const ProgHeader* hd, uint32_t* hist, int copies, int64_t* g) {
+// Add the CTA's privatised bins (every sub-table of every copy) into the public int64 table and
+// clear them.
+__device__ __forceinline__ void flush_bins(const ProgHeader* hd, uint32_t* hist, const EnumArgs& a, int64_t* g) {
     const int nb = hd->nbins_c, n_m = hd->n_m, R = hd->stride;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         unsigned long long s = 0;
-        for (int c = 0; c < copies; ++c) {
-            s += hist[c * nb + i];
-            hist[c * nb + i] = 0;
-        }
+        for (int c = 0; c < a.copies; ++c)
+            for (int t = 0; t < a.n_sub; ++t) {
+                uint32_t& w = hist[c * a.copy_words + t * a.sub_words + a.sub_off[t] + i];
+                s += w;
+                w = 0;
+            }
         const int64_t ec = i / R, m = i - ec * R;
         if (s && m < n_m) {                 // padding columns m > N are never counted
             const int64_t e = (hd->e_lo + hd->G * ec + hd->S) / 2;
@@ -87,12 +95,12 @@ __global__ void __launch_bounds__(1024) enumerate_kernel(const __grid_constant__
     __syncthreads();
     const ProgHeader* hd = reinterpret_cast<const ProgHeader*>(smem);
     const ProgView v = make_view(smem);
-    const int nb = hd->nbins_c;
-    for (int i = threadIdx.x; i < a.copies * nb; i += blockDim.x) hist[i] = 0;
+    for (int i = threadIdx.x; i < a.copies * a.copy_words; i += blockDim.x) hist[i] = 0;
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(hist + (warp % a.copies) * nb));
+    const uint32_t base = static_cast<uint32_t>(
+        __cvta_generic_to_shared(hist + (warp % a.copies) * a.copy_words + a.lane_word[lane]));
     Sink sink;
     bool done = false;
     for (;;) {
@@ -108,7 +116,7 @@ __global__ void __launch_bounds__(1024) enumerate_kernel(const __grid_constant__
         }
         if (done) s_done = 1;
         __syncthreads();
-        flush_bins(hd, hist, a.copies, a.g);
+        flush_bins(hd, hist, a, a.g);
         __syncthreads();
         if (s_done) break;
     }

@@ -173,6 +173,11 @@ void launch_enumeration(const Plan& p, const uint64_t* d_blob, int blob_words, i
     a.blob_words = blob_words;
     a.copies = p.copies;
     a.flush_rounds = p.flush_rounds;
+    a.copy_words = p.copy_words;
+    a.n_sub = p.n_sub;
+    a.sub_words = p.sub_words;
+    for (int t = 0; t < kLaneTables; ++t) a.sub_off[t] = p.sub_off[t];
+    for (int l = 0; l < 32; ++l) a.lane_word[l] = p.lane_word[l];
     switch (p.b) {
         case 1: launch_b<1>(p, *P, s); break;
         case 2: launch_b<2>(p, *P, s); break;
@@ -233,9 +238,9 @@ static float time_plan(const isg_graph& g, const isg_options& o, cudaStream_t s,
     return best;
 }
 
-// Candidates: the index order's lane spins at five row-stride residues and the bank-conflict
-// model's lane spins at its own stride (graphs of at least 30 free spins), each at three launch
-// shapes. A trial runs the full plan with tasks 2^k times shorter (q - k inner bits), cut to the
+// Candidates: the index order's lane spins at five row-stride residues, the bank-conflict
+// model's lane spins at its own stride (graphs of at least 30 free spins) and lane tables (where
+// ten padded copies of the histogram fit shared memory), each at three launch shapes. A trial runs the full plan with tasks 2^k times shorter (q - k inner bits), cut to the
 // full launch's task count, so it keeps the launch's shape at 1/2^k of its work.
 static TunedShape run_autotune(const isg_graph& g, const isg_options& base, cudaStream_t s) {
     TunedShape best;
@@ -265,12 +270,13 @@ static TunedShape run_autotune(const isg_graph& g, const isg_options& base, cuda
     else {
         lane_models.push_back(2);
         if (g.n >= kLaneModelMinFree) lane_models.push_back(1);
+        lane_models.push_back(4);                   // lane tables, where they fit shared memory
     }
     float best_ms = 1e30f;
     for (int lm : lane_models) {
         std::vector<int> rs;
         if (base.stride_residue) rs.push_back(base.stride_residue);
-        else if (lm == 1) rs.push_back(0);          // the model's own stride
+        else if (lm == 1 || lm == 4) rs.push_back(0);   // the model's own stride; lane tables' multiple of 32
         else rs.assign(std::begin(residues), std::end(residues));
         for (int r : rs)
             for (auto& sh : shapes) {

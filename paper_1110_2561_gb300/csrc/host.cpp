@@ -159,13 +159,62 @@ static void order_spins(Plan& p, int n, int free, const std::vector<int>& low, c
     for (int s = free; s < n; ++s) p.perm[pos++] = s;
 }
 
+// Symmetric chain decomposition of the 5-bit lane values (de Bruijn, Tengbergen and Kruyswijk,
+// 1951): read the bits of a value from bit 0 up, a 0 as an opening and a 1 as a closing bracket,
+// and match brackets. Values with the same matched pairs (the same matched positions holding the
+// same bits) form one chain: the unmatched bits read 1..1 0..0, with one more 1 for each step up
+// the chain. Each chain holds consecutive popcounts. Laying the chains'
+// popcount ranges end to end over the 32 banks gives each sub-table its bank offset.
+void lane_table_layout(int sub_words, int32_t* sub_off, int32_t* lane_word) {
+    if (sub_words % 32) fail(ISG_ERR_INTERNAL, "lane sub-tables must be a multiple of 32 words");
+    std::vector<std::pair<uint32_t, uint32_t>> keys;    // (matched positions, their bits) per chain
+    int chain_of[32];
+    for (uint32_t l = 0; l < 32; ++l) {
+        int open[5], sp = 0;
+        uint32_t matched = 0;
+        for (int b = 0; b < 5; ++b) {
+            if (!((l >> b) & 1)) open[sp++] = b;
+            else if (sp) matched |= (1u << b) | (1u << open[--sp]);
+        }
+        const std::pair<uint32_t, uint32_t> key(matched, l & matched);   // the pairs and their bits
+        int t = 0;
+        while (t < (int)keys.size() && keys[t] != key) ++t;
+        if (t == (int)keys.size()) keys.push_back(key);
+        chain_of[l] = t;
+    }
+    if ((int)keys.size() != kLaneTables) fail(ISG_ERR_INTERNAL, "lane values do not form ten chains");
+    int low[kLaneTables], len[kLaneTables], order[kLaneTables];
+    for (int t = 0; t < kLaneTables; ++t) { low[t] = 5; len[t] = 0; order[t] = t; }
+    for (int l = 0; l < 32; ++l) {
+        const int t = chain_of[l];
+        low[t] = std::min(low[t], __builtin_popcount((unsigned)l));
+        ++len[t];
+    }
+    std::stable_sort(order, order + kLaneTables, [&](int x, int y) { return low[x] < low[y]; });
+    int bank = 0;
+    for (int i = 0; i < kLaneTables; ++i) {
+        const int t = order[i];
+        sub_off[t] = bank - low[t];
+        if (sub_off[t] < 0 || sub_off[t] >= 32) fail(ISG_ERR_INTERNAL, "lane sub-table offset out of range");
+        bank += len[t];
+    }
+    uint32_t banks = 0;
+    for (int l = 0; l < 32; ++l) {
+        const int t = chain_of[l];
+        lane_word[l] = t * sub_words + sub_off[t];
+        banks |= 1u << ((sub_off[t] + __builtin_popcount((unsigned)l)) & 31);
+    }
+    if (bank != 32 || banks != 0xffffffffu) fail(ISG_ERR_INTERNAL, "lane tables do not give every lane its own bank");
+}
+
 Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d, bool single_graph) {
     Plan p;
     const int n = g.n;
     if (n > o.max_spins)
         fail(ISG_ERR_TOO_LARGE, "graph has " + std::to_string(n) + " spins, more than max_spins = " +
                                     std::to_string(o.max_spins));
-    if (o.lane_model < 0 || o.lane_model > 3) fail(ISG_ERR_INVALID, "lane_model must be 0, 1, 2 or 3");
+    if (o.lane_model < 0 || o.lane_model > 4) fail(ISG_ERR_INVALID, "lane_model must lie in [0, 4]");
+    if (o.lane_model == 4 && o.bin_stride % 32 != 0) fail(ISG_ERR_INVALID, "lane tables need a row stride that is a multiple of 32");
     const int k = o.shard_bits;
     if (k < 0 || k > n) fail(ISG_ERR_INVALID, "shard_bits must lie in [0, N]");
     int64_t lo = o.shard_lo, hi = o.shard_hi;
@@ -206,6 +255,14 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d, bo
     std::vector<int32_t> w;
     weight_classes(g, w);
     const size_t prog_bytes = blob_words(n, (int)w.size()) * 8;
+    // Lane tables (lane_model 4) make every warp reduction conflict-free; single-graph plans take
+    // them by default wherever one copy (or the caller's copies) fits shared memory and the caller
+    // fixes no stride
+    const auto table_words = [&](int64_t stride) { return (int64_t)kLaneTables * (((int64_t)g.n_e_c * stride + 31) / 32 * 32 + 32); };
+    const bool lane_tables = o.lane_model == 4 ||
+                             (o.lane_model == 0 && single_graph && o.bin_stride == 0 && o.stride_residue == 0 &&
+                              !o.warp_aggregate &&
+                              prog_bytes + (size_t)std::max(1, o.copies) * table_words((n + 32) / 32 * 32) * 4 <= d.smem_optin);
     int max_stride = n + 1;
     while (max_stride < n + 32 && prog_bytes + (size_t)g.n_e_c * (max_stride + 1) * 4 <= d.smem_optin) ++max_stride;
 
@@ -219,7 +276,7 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d, bo
     const bool use_model = o.lane_model == 1 || o.lane_model == 3 || plain_quick ||
                            (o.lane_model == 0 && single_graph && o.autotune && free >= kLaneModelMinFree);
     LaneChoice lc;
-    if (use_model && prog_bytes + (size_t)g.n_e_c * (n + 1) * 4 <= d.smem_optin) {
+    if (use_model && !lane_tables && prog_bytes + (size_t)g.n_e_c * (n + 1) * 4 <= d.smem_optin) {
         const uint64_t pool = free >= 64 ? ~0ull : ((1ull << free) - 1);
         if (o.lane_model == 3 || plain_quick)
             lc = choose_lanes_in(g, pool, &p.perm[p.q], n + 1, std::min(max_stride, n + 32), g.G, true, true);
@@ -252,17 +309,34 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d, bo
     p.prefix_base = (uint64_t)lo << pk;
     p.n_tasks = ((uint64_t)(hi - lo) << pk) / 32;
 
-    // Launch shape and shared memory.
+    // Launch shape and shared memory. Lane tables too large for two CTAs per SM take one CTA of
+    // 1024 threads by default.
     p.threads = o.block_threads > 0 ? o.block_threads : 512;
+    if (lane_tables && o.block_threads == 0 && o.ctas_per_sm == 0 &&
+        2 * (prog_bytes + (size_t)table_words(o.bin_stride ? o.bin_stride : (n + 32) / 32 * 32) * 4 + 1024) > d.smem_per_sm)
+        p.threads = 1024;
     if (p.threads % 32 || p.threads < 32 || p.threads > 1024) fail(ISG_ERR_INVALID, "block_threads must be a multiple of 32 in [32, 1024]");
     const int warps = p.threads / 32;
-    // row stride: the model's pick for its lane spins, unless the caller fixes a stride or residue
-    if (p.lane_model && o.bin_stride == 0 && o.stride_residue == 0) p.stride = lc.stride;
+    // row stride: the model's pick for its lane spins, unless the caller fixes a stride or residue;
+    // lane tables take the smallest multiple of 32 (or the caller's)
+    if (lane_tables) p.stride = o.bin_stride ? o.bin_stride : (n + 1 + 31) / 32 * 32;
+    else if (p.lane_model && o.bin_stride == 0 && o.stride_residue == 0) p.stride = lc.stride;
     else p.stride = choose_stride(g, o.bin_stride, o.stride_residue);
-    if (prog_bytes + (size_t)g.n_e_c * p.stride * 4 > d.smem_optin && o.bin_stride == 0) p.stride = n + 1;
-    const size_t bin_bytes = (size_t)g.n_e_c * p.stride * 4;
+    if (!lane_tables && prog_bytes + (size_t)g.n_e_c * p.stride * 4 > d.smem_optin && o.bin_stride == 0) p.stride = n + 1;
+    const int64_t nb = (int64_t)g.n_e_c * p.stride;
+    if (lane_tables) {
+        p.n_sub = kLaneTables;
+        p.sub_words = (int)((nb + 31) / 32 * 32 + 32);          // room for a bank offset below 32
+        p.copy_words = p.n_sub * p.sub_words;
+        lane_table_layout(p.sub_words, p.sub_off, p.lane_word);
+    } else {
+        p.n_sub = 1;
+        p.sub_words = p.copy_words = (int)nb;
+    }
+    const size_t bin_bytes = (size_t)p.copy_words * 4;
     if (prog_bytes + bin_bytes > d.smem_optin)
-        fail(ISG_ERR_TOO_LARGE, "histogram of " + std::to_string(g.n_e_c * (n + 1)) + " bins does not fit shared memory");
+        fail(ISG_ERR_TOO_LARGE, "histogram of " + std::to_string(g.n_e_c * (n + 1)) + " bins" +
+                                    (lane_tables ? " in lane tables" : "") + " does not fit shared memory");
     p.ctas_per_sm = o.ctas_per_sm > 0 ? o.ctas_per_sm : 2;
     if (o.copies > 0) {
         p.copies = o.copies;
@@ -385,27 +459,30 @@ std::shared_ptr<const PlannedProgram> planned_program(const isg_graph& g, const 
 // ---------------------------------------------------------------------------------------------
 // Host emulation of the kernels (same lane walk, bounds-checked counting)
 // ---------------------------------------------------------------------------------------------
+// Counts into one histogram copy; every address must be 4-byte aligned and lie among the bins of
+// the counting lane's own sub-table, [lo, hi) in bytes.
 struct HostSink {
     std::vector<uint32_t>* hist;
-    uint32_t limit;
+    uint32_t lo, hi;
     bool bad = false;
     void operator()(uint32_t& idx) {
-        if ((idx & 3u) || idx >= limit) { bad = true; return; }
+        if ((idx & 3u) || idx < lo || idx >= hi || (idx >> 2) >= hist->size()) { bad = true; return; }
         (*hist)[idx >> 2] += 1;
     }
 };
 
 template <int B>
-static void emulate_tasks(const ProgView& v, const Plan& p, std::vector<uint32_t>& hist, unsigned int& word) {
-    HostSink sink{&hist, (uint32_t)(hist.size() * 4)};
+static void emulate_tasks(const ProgView& v, const Plan& p, int64_t nb, std::vector<uint32_t>& hist, unsigned int& word) {
     for (uint64_t t = 0; t < p.n_tasks; ++t)
         for (int lane = 0; lane < 32; ++lane) {
+            const uint32_t base = (uint32_t)p.lane_word[lane] * 4u;
+            HostSink sink{&hist, base, base + (uint32_t)(nb * 4)};
             uint64_t last_state;
             uint32_t last_idx;
-            lane_walk<B>(v, p.prefix_base + t * 32 + lane, 0u, sink, last_state, last_idx);
-            if (last_idx != bin_offset(v, last_state)) word |= kSelfCheckLostBin;
+            lane_walk<B>(v, p.prefix_base + t * 32 + lane, base, sink, last_state, last_idx);
+            if (last_idx != base + bin_offset(v, last_state)) word |= kSelfCheckLostBin;
+            if (sink.bad) word |= kSelfCheckOutOfRange;
         }
-    if (sink.bad) word |= kSelfCheckOutOfRange;
 }
 
 // The kernels' walk on the host (see isg_debug_emulate). plant_site >= 0 plants a mistake in the
@@ -425,7 +502,7 @@ static unsigned int emulate(const isg_graph& g, isg_options o, int plant_site, i
     const ProgView v = make_view(blob.data());
     const int64_t stride = p.stride > 0 ? p.stride : g.n + 1;
     const int64_t nb = g.n_e_c * stride;
-    std::vector<uint32_t> hist((size_t)nb, 0);
+    std::vector<uint32_t> hist((size_t)std::max<int64_t>(nb, p.copy_words), 0);   // one copy
     unsigned int word = 0;
     if (p.small) {
         for (uint64_t s = p.s_lo; s < p.s_hi; ++s) {
@@ -435,23 +512,26 @@ static unsigned int emulate(const isg_graph& g, isg_options o, int plant_site, i
         }
     } else {
         switch (p.b) {
-            case 1: emulate_tasks<1>(v, p, hist, word); break;
-            case 2: emulate_tasks<2>(v, p, hist, word); break;
-            case 3: emulate_tasks<3>(v, p, hist, word); break;
-            case 4: emulate_tasks<4>(v, p, hist, word); break;
-            case 5: emulate_tasks<5>(v, p, hist, word); break;
-            case 6: emulate_tasks<6>(v, p, hist, word); break;
-            case 7: emulate_tasks<7>(v, p, hist, word); break;
+            case 1: emulate_tasks<1>(v, p, nb, hist, word); break;
+            case 2: emulate_tasks<2>(v, p, nb, hist, word); break;
+            case 3: emulate_tasks<3>(v, p, nb, hist, word); break;
+            case 4: emulate_tasks<4>(v, p, nb, hist, word); break;
+            case 5: emulate_tasks<5>(v, p, nb, hist, word); break;
+            case 6: emulate_tasks<6>(v, p, nb, hist, word); break;
+            case 7: emulate_tasks<7>(v, p, nb, hist, word); break;
             default: fail(ISG_ERR_INTERNAL, "bad low block size");
         }
     }
     if (word) return word;
     std::vector<int64_t> tab((size_t)public_bins(g), 0);
-    for (int64_t i = 0; i < nb; ++i)
-        if (hist[i]) {
+    const int n_sub = p.small ? 1 : p.n_sub;
+    for (int t = 0; t < n_sub; ++t)                    // the flush: every sub-table's bins
+        for (int64_t i = 0; i < nb; ++i) {
+            const uint32_t c = hist[(size_t)(p.small ? i : (int64_t)t * p.sub_words + p.sub_off[t] + i)];
+            if (!c) continue;
             const int64_t pb = public_bin(g, i, stride);
             if (pb < 0) fail(ISG_ERR_INTERNAL, "emulated walk counted a padding column");
-            tab[pb] += hist[i];
+            tab[pb] += c;
         }
     if (!o.accumulate) std::memset(g_out, 0, sizeof(int64_t) * public_bins(g));
     const int64_t n_m = g.n + 1;
@@ -581,6 +661,48 @@ isg_status isg_debug_plan(const isg_graph* g, const isg_options* opt, int32_t sm
         int64_t lanes = 0;
         if (!p.small) for (int t = 0; t < 5; ++t) lanes |= (int64_t)1 << p.perm[p.q + t];
         out[17] = lanes;
+        out[18] = p.n_sub;
+    });
+}
+
+isg_status isg_debug_lane_banks(const isg_graph* g, const isg_options* opt, int32_t samples, uint64_t seed,
+                                double* mean_wavefronts, int32_t* max_wavefronts) {
+    return guarded([&] {
+        if (!g || !mean_wavefronts || !max_wavefronts || samples < 1) fail(ISG_ERR_INVALID, "bad argument");
+        const isg_options o = resolve_options(opt);
+        const Plan p = make_plan(*g, o, DeviceInfo{}, true);
+        if (p.small) fail(ISG_ERR_INVALID, "a thread-per-configuration plan has no warp reductions");
+        const std::vector<uint64_t> blob = build_program(*g, p);
+        const ProgView v = make_view(blob.data());
+        uint64_t x = seed;
+        auto next = [&x] {                       // splitmix64
+            uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            return z ^ (z >> 31);
+        };
+        double total = 0;
+        int worst = 0;
+        for (int sample = 0; sample < samples; ++sample) {
+            const uint64_t t = next() % p.n_tasks;
+            const uint64_t inner = next() & ((1ull << p.q) - 1);
+            uint32_t addr[32];
+            for (int lane = 0; lane < 32; ++lane) {
+                const uint64_t st = ((p.prefix_base + t * 32 + lane) << p.q) | inner;
+                addr[lane] = (uint32_t)p.lane_word[lane] + bin_offset(v, st) / 4;
+            }
+            int per_bank[32] = {};
+            for (int lane = 0; lane < 32; ++lane) {
+                bool seen = false;
+                for (int j = 0; j < lane; ++j) seen = seen || addr[j] == addr[lane];
+                if (!seen) ++per_bank[addr[lane] & 31];
+            }
+            const int wf = *std::max_element(per_bank, per_bank + 32);
+            total += wf;
+            worst = std::max(worst, wf);
+        }
+        *mean_wavefronts = total / samples;
+        *max_wavefronts = worst;
     });
 }
 

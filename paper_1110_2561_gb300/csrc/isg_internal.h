@@ -97,7 +97,21 @@ struct Plan {
     bool lane_model = false;   // lane spins and stride chosen by the bank-conflict model
     double lane_cost = 0;      // the model's expected wavefronts per reduction (0 when not used)
     double lane_cost_index_order = 0;
+    // Histogram layout of one copy: n_sub sub-tables of sub_words words; lane l counts into the
+    // sub-table starting lane_word[l] words into the copy (sub_off[t] words past the start of
+    // sub-table t). One sub-table (the default): sub_words = copy_words = bins, offsets 0.
+    int n_sub = 1, sub_words = 0, copy_words = 0;
+    int32_t sub_off[kLaneTables] = {};
+    int32_t lane_word[32] = {};
 };
+
+// Lane tables (options.lane_model = 4): with the row stride a multiple of 32 words, a lane's
+// bank is its up count plus the bank offset of its sub-table. The 32 lane values are split into
+// the kLaneTables chains of a symmetric chain decomposition of the 5-bit cube (each chain holds
+// consecutive popcounts), and the chains' offsets make the banks of all 32 lanes distinct.
+// Fills sub_off (kLaneTables entries, each < 32) and lane_word (32 entries) for sub-tables of
+// sub_words words (a multiple of 32).
+void lane_table_layout(int sub_words, int32_t* sub_off, int32_t* lane_word);
 
 // The lane spins of a plan chosen by the bank-conflict model (lanes.cpp).
 struct LaneChoice {

@@ -57,6 +57,7 @@ _SIGS = {
     "isg_version": (ctypes.c_char_p, []),
     "isg_debug_plan": (i32, [vp, vp, i32, vp]),
     "isg_debug_emulate": (i32, [vp, vp, vp]),
+    "isg_debug_lane_banks": (i32, [vp, vp, i32, ctypes.c_uint64, vp, vp]),
     "isg_debug_emulate_planted": (i32, [vp, vp, i32, i32, vp, ctypes.POINTER(ctypes.c_uint32)]),
     "isg_debug_server_inject": (i32, [vp, i32]),
     "isg_device_status": (i32, [vp, i32]),
@@ -625,16 +626,25 @@ def isg_specific_heat_peak(g, graph: Graph, h: float, T_lo: float, T_hi: float, 
 
 
 def isg_debug_plan(graph: Graph, sms: int = 0, **options) -> dict:
-    out = np.zeros(18, dtype=np.int64)
+    out = np.zeros(19, dtype=np.int64)
     o = _options(**options)
     _check(lib().isg_debug_plan(graph, ctypes.byref(o), sms, out.ctypes.data))
     keys = ("small", "q", "b", "tasks", "threads", "copies", "ctas_per_sm", "flush_rounds", "grid", "smem_bytes",
             "G", "n_e_compact", "blob_bytes", "stride", "lane_model", "lane_cost", "lane_cost_index_order",
-            "lane_mask")
+            "lane_mask", "lane_tables")
     d = dict(zip(keys, (int(x) for x in out)))
     d["lane_cost"] /= 1e6
     d["lane_cost_index_order"] /= 1e6
     return d
+
+
+def isg_debug_lane_banks(graph: Graph, samples: int = 4096, seed: int = 1, **options):
+    """(mean, max) shared-memory wavefronts of sampled warp reductions of the plan (host only)."""
+    mean = ctypes.c_double()
+    worst = ctypes.c_int32()
+    o = _options(**options)
+    _check(lib().isg_debug_lane_banks(graph, ctypes.byref(o), samples, seed, ctypes.byref(mean), ctypes.byref(worst)))
+    return mean.value, worst.value
 
 
 def isg_debug_emulate(graph: Graph, **options) -> np.ndarray:

@@ -197,8 +197,74 @@ def test_lane_model_plans(isg):
     quick = isg.isg_debug_plan(g, lane_model=3)          # the quick search: still a valid, better set
     assert quick["lane_model"] == 1 and quick["lane_cost"] <= quick["lane_cost_index_order"]
     with pytest.raises(isg.IsgError) as ei:
-        isg.isg_debug_plan(g, lane_model=4)
+        isg.isg_debug_plan(g, lane_model=5)
     assert ei.value.status == 1
+
+
+def test_lane_model_against_sampled_reductions(isg):
+    """The bank-conflict model's expected wavefronts per warp reduction (lanes.cpp) against the
+    wavefronts of sampled reductions of the actual plan (isg_debug_lane_banks: the 32 lanes' word
+    addresses at one step of a task, the most distinct addresses in one bank)."""
+    rng = w.SplitMix64(17)
+    for lat in (w.square(6, 6, True), w.cubic(3, 3, 4, True), w.with_random_couplings(w.square(5, 6, True), rng, (-1, 1)),
+                w.triangular(5, 6, True)):
+        g = isg.isg_graph_create(lat.n, lat.edges)
+        for lm in (1, 3):
+            p = isg.isg_debug_plan(g, lane_model=lm)
+            if not p["lane_model"]:
+                continue
+            mean, worst = isg.isg_debug_lane_banks(g, samples=6000, seed=3, lane_model=lm)
+            assert abs(mean - p["lane_cost"]) <= 0.06, (lat.name, lm, mean, p["lane_cost"])
+            assert 1 <= worst <= 32
+
+
+@pytest.mark.parametrize("lat", [w.cubic(3, 3, 4, True), w.square(6, 6, True), w.triangular(5, 6, True),
+                                 w.with_random_couplings(w.square(5, 6, True), w.SplitMix64(4), (-2, -1, 1, 2)),
+                                 w.random_graph(30, 90, w.SplitMix64(5))], ids=lambda l: l.name)
+def test_lane_tables_make_every_reduction_conflict_free(isg, lat):
+    """Lane tables (options.lane_model = 4): ten sub-tables per copy and a row stride that is a
+    multiple of 32, so each lane's bank is its up count plus its sub-table's offset. Every sampled
+    warp reduction of the plan takes exactly one wavefront, whatever the graph and couplings."""
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    p = isg.isg_debug_plan(g, lane_model=4)
+    assert p["lane_tables"] == 10 and p["stride"] % 32 == 0 and p["stride"] >= lat.n + 1
+    sub = ((p["n_e_compact"] * p["stride"] + 31) // 32 * 32 + 32)
+    assert p["smem_bytes"] == p["blob_bytes"] + p["copies"] * 10 * sub * 4
+    mean, worst = isg.isg_debug_lane_banks(g, samples=3000, seed=5, lane_model=4)
+    assert mean == 1.0 and worst == 1
+    for sym in (0, 1):
+        mean, worst = isg.isg_debug_lane_banks(g, samples=500, seed=6, lane_model=4, symmetry=sym)
+        assert worst == 1
+
+
+def test_lane_tables_emulated_against_the_oracle(isg):
+    """The kernel's walk on the host with lane tables (every address checked to lie among its own
+    lane's sub-table bins; the flush sums the ten sub-tables): the oracle's table, whole, halved by
+    the spin flip, in a shard range, and in a forced small shape with two copies."""
+    rng = w.SplitMix64(9)
+    for lat in (w.square(4, 5, True), w.cubic(2, 2, 4, True), w.with_random_couplings(w.square(4, 5, True), rng, (-2, -1, 1, 2)),
+                w.triangular(4, 4, False), w.random_graph(18, 40, rng)):
+        g = isg.isg_graph_create(lat.n, lat.edges)
+        ref = oracle.g_edges(lat.n, lat.edges)
+        assert np.array_equal(isg.isg_debug_emulate(g, lane_model=4), ref)
+        assert np.array_equal(isg.isg_debug_emulate(g, lane_model=4, symmetry=1), ref)
+        assert np.array_equal(isg.isg_debug_emulate(g, lane_model=4, inner_bits=6, low_bits=3, block_threads=64, copies=2), ref)
+        part = oracle.g_edges(lat.n, lat.edges, 1 << (lat.n - 2), 3 << (lat.n - 2))
+        assert np.array_equal(isg.isg_debug_emulate(g, lane_model=4, shard_bits=2, shard_lo=1, shard_hi=3), part)
+
+
+def test_lane_tables_rejects(isg):
+    lat = w.with_random_couplings(w.square(5, 8, True), w.SplitMix64(40), (-2, -1, 1, 2))
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    with pytest.raises(isg.IsgError) as ei:                    # ten padded copies of 4838 bins
+        isg.isg_debug_plan(g, lane_model=4)
+    assert ei.value.status == 2
+    t = w.square(6, 6, True)
+    gt = isg.isg_graph_create(t.n, t.edges)
+    with pytest.raises(isg.IsgError) as ei:
+        isg.isg_debug_plan(gt, lane_model=4, bin_stride=45)
+    assert ei.value.status == 1
+    assert isg.isg_debug_plan(gt, lane_model=4, bin_stride=96)["stride"] == 96
 
 
 def test_lane_model_is_deterministic_and_sign_free(isg):

@@ -75,7 +75,10 @@ PLANS = [dict(inner_bits=6), dict(low_bits=1, inner_bits=4), dict(low_bits=4, in
          dict(flush_tasks=1), dict(ctas_per_sm=1, flush_tasks=1, block_threads=96, copies=2), dict(low_bits=2, inner_bits=2),
          dict(warp_aggregate=1), dict(bin_stride=64), dict(bin_stride=33, warp_aggregate=1, copies=1),
          dict(symmetry=1), dict(symmetry=1, low_bits=3, inner_bits=6, block_threads=128),
-         dict(lane_model=1), dict(lane_model=1, symmetry=1), dict(lane_model=1, inner_bits=9, stride_residue=19)]
+         dict(lane_model=1), dict(lane_model=1, symmetry=1), dict(lane_model=1, inner_bits=9, stride_residue=19),
+         dict(lane_model=2), dict(lane_model=2, block_threads=1024, copies=16), dict(lane_model=3),
+         dict(lane_model=4, inner_bits=6, low_bits=3), dict(lane_model=4, symmetry=1, flush_tasks=1),
+         dict(lane_model=4, block_threads=64)]
 
 
 @pytest.mark.parametrize("kw", PLANS, ids=lambda k: ",".join(f"{a}={b}" for a, b in k.items()))
@@ -84,6 +87,25 @@ def test_plan_invariance(isg, cuda, kw):
     lat = w.with_random_couplings(w.triangular(4, 5, True), w.SplitMix64(8), (-2, -1, 1, 2))
     ref = oracle.g_masks(lat.n, lat.edges, threads=THREADS)
     assert np.array_equal(gpu_table(isg, cuda, lat, **kw), ref)
+
+
+@pytest.mark.parametrize("kw", [dict(copies=2), dict(copies=3, block_threads=96, flush_tasks=1), dict(bin_stride=96),
+                                dict(symmetry=1, copies=2), dict(shard_bits=3, shard_lo=2, shard_hi=7, inner_bits=8)],
+                         ids=lambda k: ",".join(f"{a}={b}" for a, b in k.items()))
+def test_lane_tables_forced_shapes(isg, cuda, kw):
+    """Lane tables (ten sub-tables per copy) with several copies per CTA (warps sharing them), a
+    wider row stride, a flush after every task, symmetry halving and a shard range, on a +-1 torus
+    of 20 spins: the oracle's table (or shard range) bin for bin."""
+    lat = w.with_random_couplings(w.square(4, 5, True), w.SplitMix64(21), (-1, 1))
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    assert isg.isg_debug_plan(g, lane_model=4, **kw)["lane_tables"] == 10
+    if "shard_bits" in kw:
+        k = kw["shard_bits"]
+        ref = oracle.g_masks(lat.n, lat.edges, kw["shard_lo"] << (lat.n - k), kw["shard_hi"] << (lat.n - k))
+    else:
+        ref = oracle.g_masks(lat.n, lat.edges)
+    assert np.array_equal(gpu_table(isg, cuda, lat, lane_model=4, **kw), ref)
+    isg.isg_device_status()
 
 
 def test_symmetry_host_device_accumulate(isg, cuda):
@@ -171,9 +193,9 @@ def test_cubic_3x3x4_full_invariants_and_shards(isg, cuda):
 
 
 def test_cubic_3x3x4_full_against_layer_conditioned_oracle(isg, cuda):
-    """3x3x4 simple cubic torus, N = 36, in the benchmark's autotuned plan, the default plan (quick
-    lane search), the index order's plan, and by split-and-convolve: every bin of every table
-    equals the oracle's frontier programme conditioned on one z layer (2^9 configurations of that
+    """3x3x4 simple cubic torus, N = 36, in the benchmark's autotuned plan, the default plan (lane
+    tables), the quick lane search's and the index order's plans, and by split-and-convolve: every
+    bin of every table equals the oracle's frontier programme conditioned on one z layer (2^9 configurations of that
     layer, each with the other 27 spins by the frontier; sites renumbered layer by layer)."""
     import torch
     from relabel import layer_cut
@@ -181,14 +203,17 @@ def test_cubic_3x3x4_full_against_layer_conditioned_oracle(isg, cuda):
     r, cut = layer_cut(lat)
     assert bin(cut).count("1") == 9
     got = gpu_table(isg, cuda, lat, autotune=1)
-    default = gpu_table(isg, cuda, lat)
+    default = gpu_table(isg, cuda, lat)                     # lane tables
+    quick = gpu_table(isg, cuda, lat, lane_model=3)         # the quick lane search
     index = gpu_table(isg, cuda, lat, lane_model=2)
     g = isg.isg_graph_create(lat.n, lat.edges)
+    assert isg.isg_debug_plan(g)["lane_tables"] == 10
     split = torch.zeros(isg.table_shape(g), dtype=torch.int64, device=cuda)
     isg.isg_enumerate_split(g, split)
     ref = oracle.g_frontier_cut(r.n, r.edges, cut, max_active=20, threads=THREADS)
     assert np.array_equal(got, ref)
     assert np.array_equal(default, ref)
+    assert np.array_equal(quick, ref)
     assert np.array_equal(index, ref)
     assert np.array_equal(split.cpu().numpy(), ref)
     isg.isg_device_status()
@@ -196,15 +221,15 @@ def test_cubic_3x3x4_full_against_layer_conditioned_oracle(isg, cuda):
 
 @pytest.mark.slow
 def test_cubic_3x3x4_full_against_popcount_oracle(isg, cuda):
-    """3x3x4 simple cubic torus, N = 36, in the benchmark's autotuned plan, the default plan (quick
-    lane search), the index order's plan, and by split-and-convolve: every bin of every table
+    """3x3x4 simple cubic torus, N = 36, in the benchmark's autotuned plan, the quick lane search's
+    plan, the index order's plan, and by split-and-convolve: every bin of every table
     equals the popcount oracle's table over all 2^36 configurations (O1 on
     all host cores; minutes of CPU time): the plainest definition, beside the layer-conditioned
     frontier programme of the test above."""
     import torch
     lat = w.cubic(3, 3, 4, True)
     got = gpu_table(isg, cuda, lat, autotune=1)
-    default = gpu_table(isg, cuda, lat)                     # the quick lane search's plan
+    default = gpu_table(isg, cuda, lat, lane_model=3)       # the quick lane search's plan
     index = gpu_table(isg, cuda, lat, lane_model=2)         # the index order's
     g = isg.isg_graph_create(lat.n, lat.edges)
     split = torch.zeros(isg.table_shape(g), dtype=torch.int64, device=cuda)
@@ -231,15 +256,15 @@ def test_largest_default_size_n40(isg, cuda):
 
 def test_autotune_torus_6x6(isg, cuda):
     """The autotuner's choice (cached per graph; the lane spins of the bank-conflict model or of the
-    index order, whichever timed faster) gives the same table as the oracle's frontier programme,
+    index order, or lane tables, whichever timed fastest) gives the same table as the oracle's frontier programme,
     and so does the model's plan forced; a second isg_autotune call returns the cached fields."""
     import torch
     lat = w.square(6, 6, True)
     g = isg.isg_graph_create(lat.n, lat.edges)
     t1 = isg.isg_autotune(g)
     t2 = isg.isg_autotune(g)
-    assert t1 == t2 and t1["block_threads"] > 0 and t1["lane_model"] in (1, 2)
-    assert t1["stride_residue"] > 0 or t1["lane_model"] == 1      # the model's lane set keeps its own stride
+    assert t1 == t2 and t1["block_threads"] > 0 and t1["lane_model"] in (1, 2, 4)
+    assert t1["stride_residue"] > 0 or t1["lane_model"] in (1, 4)   # the model's stride; lane tables' multiple of 32
     out = torch.zeros(isg.table_shape(g), dtype=torch.int64, device=cuda)
     isg.isg_enumerate(g, out, autotune=1)
     forced = torch.zeros_like(out)
