@@ -47,6 +47,51 @@ unsigned int* device_status_word() {
     return addr[dev];
 }
 
+// The pool of pinned staging buffers (at most kStagePool kept; larger requests replace smaller
+// buffers). Never freed at exit: the driver reclaims pinned memory with the process.
+static std::mutex g_stage_mu;
+static std::vector<std::pair<char*, size_t>> g_stage_free;
+constexpr size_t kStagePool = 8;
+
+PinnedStage::PinnedStage(size_t bytes, void* stream) : stream_(stream) {
+    bytes = std::max<size_t>(bytes, 1);
+    {
+        std::lock_guard<std::mutex> lk(g_stage_mu);
+        size_t best = g_stage_free.size();
+        for (size_t i = 0; i < g_stage_free.size(); ++i)
+            if (g_stage_free[i].second >= bytes && (best == g_stage_free.size() || g_stage_free[i].second < g_stage_free[best].second))
+                best = i;
+        if (best < g_stage_free.size()) {
+            p_ = g_stage_free[best].first;
+            cap_ = g_stage_free[best].second;
+            g_stage_free.erase(g_stage_free.begin() + (std::ptrdiff_t)best);
+            return;
+        }
+    }
+    cap_ = std::max<size_t>(64 << 10, (bytes + 4095) & ~(size_t)4095);
+    void* p = nullptr;
+    const cudaError_t e = cudaMallocHost(&p, cap_);
+    if (e != cudaSuccess) fail(ISG_ERR_NOMEM, std::string("cudaMallocHost(staging): ") + cudaGetErrorString(e));
+    p_ = static_cast<char*>(p);
+}
+
+PinnedStage::~PinnedStage() {
+    if (!synced_) cudaStreamSynchronize(static_cast<cudaStream_t>(stream_));
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    if (g_stage_free.size() < kStagePool) {
+        g_stage_free.emplace_back(p_, cap_);
+        return;
+    }
+    size_t smallest = 0;                          // keep the larger buffers
+    for (size_t i = 1; i < g_stage_free.size(); ++i)
+        if (g_stage_free[i].second < g_stage_free[smallest].second) smallest = i;
+    if (g_stage_free[smallest].second < cap_) {
+        std::swap(g_stage_free[smallest].first, p_);
+        std::swap(g_stage_free[smallest].second, cap_);
+    }
+    cudaFreeHost(p_);
+}
+
 void* scratch_alloc(size_t bytes, void* stream) {
     static std::mutex mu;
     static std::vector<cudaMemPool_t> pools;
@@ -398,14 +443,18 @@ static void enumerate_range(const isg_graph& graph, cudaStream_t s, int64_t* g_o
         table = full;
     }
     if (!g_out_on_device) {
-        std::vector<int64_t> host((size_t)public_bins(graph));
-        unsigned int word = 0;
-        ISG_CUDA(cudaMemcpyAsync(host.data(), table, table_bytes, cudaMemcpyDeviceToHost, s));
-        ISG_CUDA(cudaMemcpyAsync(&word, scratch + 8, sizeof word, cudaMemcpyDeviceToHost, s));
+        // the table and the status word into pinned memory by asynchronous copies, one synchronisation
+        PinnedStage stage(table_bytes + 16, s);
+        const int64_t* host = reinterpret_cast<const int64_t*>(stage.data());
+        unsigned int* word = reinterpret_cast<unsigned int*>(stage.data() + table_bytes);
+        ISG_CUDA(cudaMemcpyAsync(stage.data(), table, table_bytes, cudaMemcpyDeviceToHost, s));
+        ISG_CUDA(cudaMemcpyAsync(word, scratch + 8, sizeof *word, cudaMemcpyDeviceToHost, s));
         ISG_CUDA(cudaStreamSynchronize(s));
-        check_self_check_word(word, "enumeration");
-        if (o.accumulate) for (size_t i = 0; i < host.size(); ++i) g_out[i] += host[i];
-        else std::memcpy(g_out, host.data(), table_bytes);
+        stage.synced();
+        check_self_check_word(*word, "enumeration");
+        const size_t nb = (size_t)public_bins(graph);
+        if (o.accumulate) for (size_t i = 0; i < nb; ++i) g_out[i] += host[i];
+        else std::memcpy(g_out, host, table_bytes);
     }
 }
 

@@ -182,6 +182,28 @@ inline int64_t public_bin(const isg_graph& g, int64_t compact, int64_t stride) {
 // cudaStream_t.
 void* scratch_alloc(size_t bytes, void* stream);
 
+// Pinned host memory for the host-buffer forms of the calls: results are copied into it
+// asynchronously and from it into the caller's arrays after one synchronisation (a pageable
+// destination makes every copy a synchronous staged transfer), and host inputs go the other way.
+// Buffers come from a small process-wide pool and return to it. The caller synchronises `stream`
+// and then calls synced(); a stage destroyed without that (an error on the way) synchronises the
+// stream first, so no copy in flight can touch a buffer that is back in the pool.
+class PinnedStage {
+   public:
+    PinnedStage(size_t bytes, void* stream);
+    ~PinnedStage();
+    PinnedStage(const PinnedStage&) = delete;
+    PinnedStage& operator=(const PinnedStage&) = delete;
+    char* data() const { return p_; }
+    void synced() { synced_ = true; }
+
+   private:
+    char* p_ = nullptr;
+    size_t cap_ = 0;
+    void* stream_ = nullptr;
+    bool synced_ = false;
+};
+
 // Row stride of the shared histogram for a graph (>= N + 1), padded against bank conflicts.
 int choose_stride(const isg_graph& g, int requested, int residue);
 

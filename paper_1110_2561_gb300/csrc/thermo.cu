@@ -659,9 +659,14 @@ static void thermo_grid(const int64_t* g, int32_t g_on_device, const isg_graph* 
         ISG_CUDA(cudaMemcpyAsync(scratch + o_T, T, sizeof(double) * nT, cudaMemcpyHostToDevice, s));
         ISG_CUDA(cudaMemcpyAsync(scratch + o_h, h, sizeof(double) * nh, cudaMemcpyHostToDevice, s));
     }
+    // host buffers go through one pinned stage: [g][requested outputs]
+    std::unique_ptr<PinnedStage> stage;
+    if (!g_on_device || !out_on_device)
+        stage.reset(new PinnedStage((g_on_device ? 0 : gbytes) + (out_on_device ? 0 : n_out * sizeof(double) * pts), s));
     if (g_on_device) a.g = g;
     else {
-        ISG_CUDA(cudaMemcpyAsync(scratch + o_g, g, gbytes, cudaMemcpyHostToDevice, s));
+        std::memcpy(stage->data(), g, gbytes);
+        ISG_CUDA(cudaMemcpyAsync(scratch + o_g, stage->data(), gbytes, cudaMemcpyHostToDevice, s));
         a.g = reinterpret_cast<int64_t*>(scratch + o_g);
     }
     double* outs_dev[kThermoOuts];
@@ -673,11 +678,17 @@ static void thermo_grid(const int64_t* g, int32_t g_on_device, const isg_graph* 
     a.absM = outs_dev[5]; a.M2 = outs_dev[6]; a.M4 = outs_dev[7]; a.binder = outs_dev[8];
     launch_thermo(*P, reinterpret_cast<double*>(scratch + o_lng), reinterpret_cast<float*>(scratch + o_lngf), precision, s);
     if (!out_on_device) {
-        for (int k = 0; k < kThermoOuts; ++k)
-            if (outs_host[k])
-                ISG_CUDA(cudaMemcpyAsync(outs_host[k], outs_dev[k], sizeof(double) * pts, cudaMemcpyDeviceToHost, s));
+        // the requested outputs lie side by side in the scratch: one copy into the stage
+        char* out_host = stage->data() + (g_on_device ? 0 : gbytes);
+        ISG_CUDA(cudaMemcpyAsync(out_host, scratch + o_out, n_out * sizeof(double) * pts, cudaMemcpyDeviceToHost, s));
+        ISG_CUDA(cudaStreamSynchronize(s));
+        stage->synced();
+        for (int k = 0, j = 0; k < kThermoOuts; ++k)
+            if (outs_host[k]) std::memcpy(outs_host[k], out_host + (j++) * sizeof(double) * pts, sizeof(double) * pts);
+    } else if (!g_on_device) {
+        ISG_CUDA(cudaStreamSynchronize(s));
+        stage->synced();
     }
-    if (!out_on_device || !g_on_device) ISG_CUDA(cudaStreamSynchronize(s));
 }
 
 extern "C" isg_status isg_thermo(const int64_t* g, int32_t g_on_device, const isg_graph* graph, int32_t nT,
