@@ -61,6 +61,21 @@ def test_single_and_isolated_spins(isg, cuda):
     assert np.array_equal(gpu_table(isg, cuda, lat), oracle.g_masks(lat.n, lat.edges))
 
 
+def test_degenerate_graphs_in_lane_tables(isg, cuda):
+    """Warp-task plans (lane tables by default) on graphs with a single energy row (no bonds at
+    all), with bonds whose duplicate couplings cancel to nothing, and a ring with a cancelled chord:
+    the oracle's tables."""
+    cases = [w.Lattice(20, np.zeros((0, 3), np.int64), "free20"),
+             w.Lattice(16, np.array([(0, 1, 2), (1, 0, -2), (2, 3, 1), (4, 5, -1), (5, 4, 1)], np.int64), "cancel16"),
+             w.Lattice(24, np.array([(i, (i + 1) % 24, 1) for i in range(24)] + [(0, 12, 3), (12, 0, -3)], np.int64),
+                       "ring24-cancel")]
+    for lat in cases:
+        g = isg.isg_graph_create(lat.n, lat.edges)
+        assert isg.isg_debug_plan(g)["lane_tables"] == 10
+        assert np.array_equal(gpu_table(isg, cuda, lat), oracle.g_edges(lat.n, lat.edges)), lat.name
+    isg.isg_device_status()
+
+
 def test_table1_on_gpu(isg, cuda, table1_triples):
     """Table 1 of the paper from the GPU: the 4x4 periodic ferromagnet, all 80 cells."""
     lat = w.square(4, 4, True)
@@ -252,6 +267,23 @@ def test_largest_default_size_n40(isg, cuda):
     check_invariants(got, 40)
     r, cut = layer_cut(lat)
     assert np.array_equal(got, oracle.g_frontier_cut(r.n, r.edges, cut, max_active=20, threads=THREADS))
+
+
+def test_torus_5x8_n40_lane_tables(isg, cuda):
+    """N = 40 ferromagnetic 5x8 torus (2^40 configurations) in the default plan, lane tables: every
+    bin against the oracle's frontier programme conditioned on one row, every energy count exactly
+    as Kaufman's closed form gives it, and the invariants."""
+    from closed_forms import kaufman_energy_counts
+    from relabel import layer_cut
+    lat = w.square(5, 8, True)
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    assert isg.isg_debug_plan(g)["lane_tables"] == 10
+    got = gpu_table(isg, cuda, lat)
+    check_invariants(got, 40)
+    assert [int(x) for x in got.sum(axis=1)] == kaufman_energy_counts(5, 8)
+    r, cut = layer_cut(lat)
+    assert np.array_equal(got, oracle.g_frontier_cut(r.n, r.edges, cut, max_active=20, threads=THREADS))
+    isg.isg_device_status()
 
 
 def test_autotune_torus_6x6(isg, cuda):

@@ -267,6 +267,15 @@ def test_frontier_cut_torus_7x7():
     _torus_pins(oracle.g_frontier_cut(lat.n, lat.edges, _mask(range(7)), max_active=16, threads=THREADS), 7, 7)
 
 
+def test_frontier_cut_torus_5x8():
+    """The 5x8 torus (N = 40) by the programme conditioned on its first row of five spins, after
+    renumbering the sites along the short side: the same pins as the 7x7 torus."""
+    from relabel import layer_cut
+    lat = w.square(5, 8, True)
+    r, cut = layer_cut(lat)
+    _torus_pins(oracle.g_frontier_cut(r.n, r.edges, cut, max_active=16, threads=THREADS), 5, 8)
+
+
 def test_frontier_cut_torus_8x8():
     """The 8x8 torus (N = 64, 2^64 configurations) by the programme conditioned on one row (2^8
     rest programmes of 56 spins): the same pins as the 7x7 torus; the table's largest count is
