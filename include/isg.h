@@ -338,7 +338,8 @@ ISG_API isg_status isg_enumerate_noalloc(const isg_graph* graph, void* stream, i
  * Thermodynamics on the grid T[0..nT) x h[0..nh) from a table g of this graph's geometry
  * (Eq. 2 summed over the degeneracy table of Sec. 2). T > 0, host arrays. Outputs are
  * nT * nh doubles each, point (a, b) at index a * nh + b: logZ = ln Z, E = <H>, M = <M>,
- * C = Var(H)/T^2, chi = Var(M)/T; any output may be NULL. precision ISG_FP64 or ISG_FP32 (the
+ * C = Var(H)/T^2, chi = Var(M)/T; any output may be NULL. H = E_J - h M (Eq. 1), so the mean
+ * exchange energy is <E_J> = E + h M from the same point's outputs. precision ISG_FP64 or ISG_FP32 (the
  * latter computes weights and sums in float, converting counts and finishing ln Z in double).
  * g on the device if g_on_device, outputs on the device if out_on_device; a call with any host
  * buffer synchronises stream. Any counts of this geometry are accepted; the graph's own tables,

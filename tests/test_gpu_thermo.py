@@ -35,6 +35,30 @@ def test_fp64_small(isg, cuda, lat):
     fp64_vs_oracle(isg, lat, T, h)
 
 
+def test_exchange_energy_from_the_outputs(isg, cuda):
+    """The mean exchange energy <E_J> = <H> + h <M> (H = E_J - h M, Eq. 1) from the FP64 outputs,
+    against the exchange energy averaged directly over the oracle's table (every bin's E_J with
+    the Boltzmann weight of its H, in long double)."""
+    lat = w.with_random_couplings(w.square(4, 4, True), w.SplitMix64(31), (-2, -1, 1, 2))
+    g = oracle.g_masks(lat.n, lat.edges)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    T = np.array([0.6, 1.3, 2.5, 4.0])
+    h = np.array([-1.5, 0.0, 0.4, 2.0])
+    _, E, M, _, _ = isg.isg_thermo(g, gh, T, h, isg.ISG_FP64)
+    Ev = (e_min + 2 * np.arange(g.shape[0], dtype=np.longdouble))[:, None]
+    Mv = (-lat.n + 2 * np.arange(g.shape[1], dtype=np.longdouble))[None, :]
+    gl = g.astype(np.longdouble)
+    for a, t in enumerate(T):
+        for b, f in enumerate(h):
+            x = -(Ev - f * Mv) / t
+            wgt = np.where(gl > 0, gl * np.exp(x - x[gl > 0].max()), 0)
+            want = float((wgt * Ev).sum() / wgt.sum())
+            got = E[a, b] + f * M[a, b]
+            # the bounds of the two outputs: 1e-12 relative on <H>, 1e-12 N on <M> (times |h|)
+            assert abs(got - want) <= 1e-12 * (abs(E[a, b]) + (abs(f) + 1) * lat.n), (t, f, got, want)
+
+
 def test_config_4x4_free_fp64(isg, cuda):
     """4x4 free ferromagnet, 64 temperatures in [0.5, 5] at h = 0, FP64."""
     fp64_vs_oracle(isg, w.square(4, 4, False), np.linspace(0.5, 5, 64), np.array([0.0]))
