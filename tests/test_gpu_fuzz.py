@@ -41,3 +41,27 @@ def test_enumeration_fuzz(isg, cuda, seed):
         done += 1
     assert done >= 35
     isg.isg_device_status()
+
+
+@pytest.mark.parametrize("seed", [31, 32, 33])
+def test_batch_fuzz(isg, cuda, seed):
+    """Random batches: 3 to 40 graphs of 3 to 24 spins (tiny ones for the thread-per-configuration
+    kernel among them), options drawn from symmetry, split-and-convolve service, the lane model and
+    the inner bits; every table equals the oracle's."""
+    from paper_1110_2561_gb300 import workloads as w
+    rng = w.SplitMix64(seed)
+    for _ in range(4):
+        lats = [fc.draw_lattice(rng, 3, 24) for _ in range(3 + rng.below(38))]
+        o = {}
+        if rng.below(2):
+            o["symmetry"] = 1
+        if rng.below(2):
+            o["split"] = 1
+        o["lane_model"] = (0, 1, 2, 3)[rng.below(4)]
+        if rng.below(3) == 0:
+            o["inner_bits"] = 7 + rng.below(6)
+        graphs = [isg.isg_graph_create(l.n, l.edges) for l in lats]
+        got = isg.isg_enumerate_batch(graphs, **o)
+        for l, t in zip(lats, got):
+            assert np.array_equal(t, oracle.g_masks(l.n, l.edges, threads=THREADS)), (l.name, o)
+    isg.isg_device_status()
