@@ -117,7 +117,8 @@ typedef struct {
                                 32, so that each lane's shared-memory bank is fixed by its up count
                                 and its sub-table; no warp reduction has a bank conflict, on any
                                 graph. A copy takes ten times the padded histogram; TOO_LARGE if one
-                                does not fit shared memory. */
+                                does not fit shared memory. Single-graph calls only: batches (one
+                                histogram per warp) refuse 4 with INVALID. */
 } isg_options;
 
 /* Fill *opt with the defaults (all planner choices, full range, overwrite). */

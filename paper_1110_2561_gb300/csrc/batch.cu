@@ -147,6 +147,8 @@ static BatchPlan plan_batch(int n, const isg_graph* const* graphs, const isg_opt
     BatchPlan bp;
     if (o.shard_bits || o.shard_lo || o.shard_hi || o.accumulate)
         fail(ISG_ERR_INVALID, "batches take no shard or accumulate options");
+    if (o.lane_model == 4)
+        fail(ISG_ERR_INVALID, "lane tables (lane_model 4) are for single-graph enumerations; a batch keeps one histogram per warp");
     const bool sym = o.symmetry != 0;
     // common low block: the largest size every large-enough instance supports
     std::vector<int> b_of(n, 0);

@@ -83,6 +83,9 @@ def test_batch_rejects_shards(isg, cuda):
     with pytest.raises(isg.IsgError) as ei:
         isg.isg_enumerate_batch([h], shard_bits=1, shard_hi=1)
     assert ei.value.status == 1
+    with pytest.raises(isg.IsgError) as ei:                    # lane tables: single-graph calls only
+        isg.isg_enumerate_batch([h], lane_model=4)
+    assert ei.value.status == 1
 
 
 def test_prepared_batch_replay(isg, cuda):
