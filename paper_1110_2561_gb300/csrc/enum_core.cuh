@@ -20,7 +20,10 @@
 // offset 4 (e' R + m), m = number of up spins, R >= N + 1 the row stride. One unit of field moves
 // the address by sE = 8 R / G bytes: dE = 2 S_k h_k gives de' = 2 S_k h_k / G, and dm = -S_k.
 // R is padded so that lanes whose bins differ by a few rows and a few columns fall in different
-// shared-memory banks (R = -1 mod 32, for instance, puts (e' + d, m + d) in the same bank).
+// shared-memory banks (R = -1 mod 32, for instance, puts (e' + d, m + d) in the same bank). Lane
+// tables instead take R a multiple of 32, so that a bin's bank depends on m alone, and count each
+// lane into its own sub-table of the copy, offset so that the 32 lanes' banks differ (the walk
+// only sees the lane's base address; enum_kernels.cuh and the planner lay the sub-tables out).
 #pragma once
 #include <cstdint>
 #include <utility>
