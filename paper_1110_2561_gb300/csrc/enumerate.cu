@@ -48,7 +48,7 @@ unsigned int* device_status_word() {
 }
 
 // The pool of pinned staging buffers (at most kStagePool kept; larger requests replace smaller
-// buffers). Never freed at exit: the driver reclaims pinned memory with the process.
+// buffers). Never freed at exit: pinned memory goes back to the system with the process.
 static std::mutex g_stage_mu;
 static std::vector<std::pair<char*, size_t>> g_stage_free;
 constexpr size_t kStagePool = 8;
