@@ -360,3 +360,39 @@ def test_lane_model_with_symmetry_and_rank_shares_torus_6x6(isg, cuda):
     assert np.array_equal(ranks.cpu().numpy(), ref)
     assert isg.isg_debug_plan(g, lane_model=1, symmetry=0, shard_bits=1, shard_lo=1, shard_hi=2)["lane_model"] == 1
     isg.isg_device_status()
+
+
+def test_concurrent_host_buffer_calls(isg, cuda):
+    """Host-buffer calls from several threads at once, each on its own stream (the library releases
+    the interpreter during a call): their pinned staging buffers come from one shared pool, and every
+    table and every thermodynamic output equals the single-threaded result."""
+    import threading
+    import torch
+    lats = [w.square(4, 5, True), w.triangular(4, 4, True), w.cubic(2, 2, 4, True),
+            w.with_random_couplings(w.square(4, 4, True), w.SplitMix64(5), (-2, -1, 1, 2))]
+    graphs = [isg.isg_graph_create(l.n, l.edges) for l in lats]
+    refs = [oracle.g_masks(l.n, l.edges) for l in lats]
+    T, h = np.linspace(0.5, 5, 40), np.array([0.0, 0.5])
+    thermo_refs = [isg.isg_thermo(r, g, T, h, isg.ISG_FP64) for r, g in zip(refs, graphs)]
+    errors = []
+
+    def worker(k):
+        st = torch.cuda.Stream()
+        try:
+            for rep in range(6):
+                i = (k + rep) % len(lats)
+                tab = isg.isg_enumerate(graphs[i], None, st)
+                if not np.array_equal(tab, refs[i]):
+                    errors.append(("table", k, i))
+                out = isg.isg_thermo(tab, graphs[i], T, h, isg.ISG_FP64, st)
+                if not all(np.array_equal(a, b) for a, b in zip(out, thermo_refs[i])):
+                    errors.append(("thermo", k, i))
+        except Exception as e:                       # reported below, not lost in the thread
+            errors.append(("raised", k, repr(e)))
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in range(6)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
