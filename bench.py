@@ -283,7 +283,10 @@ def run_isg(args):
                 [b.elapsed_time(c) for a, b, c in evs]),
             "e2e": {"value": ranks_counted * n_configs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": 3 * args.steps * world,          # this library's kernels, all ranks
+            # this library's kernels, all ranks: the enumeration, then the thermodynamics: one
+            # kernel when every field is zero and the table has at most 1024 energy bins (the
+            # per-energy path), else the ln g conversion and the grid kernel
+            "gpu_launches": (1 + (1 if np.all(H_GRID == 0) and shape[0] <= 1024 else 2)) * args.steps * world,
             "clocks": clocks,
         }
         # the other workloads and the oracle baseline at N = 1 only (the scaling runs time the

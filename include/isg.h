@@ -341,7 +341,10 @@ ISG_API isg_status isg_enumerate_noalloc(const isg_graph* graph, void* stream, i
  * nT * nh doubles each, point (a, b) at index a * nh + b: logZ = ln Z, E = <H>, M = <M>,
  * C = Var(H)/T^2, chi = Var(M)/T; any output may be NULL. H = E_J - h M (Eq. 1), so the mean
  * exchange energy is <E_J> = E + h M from the same point's outputs. precision ISG_FP64 or ISG_FP32 (the
- * latter computes weights and sums in float, converting counts and finishing ln Z in double).
+ * latter computes weights and sums in float, converting counts and finishing ln Z in double). A
+ * grid whose fields are all zero (with at most 1024 energy bins) takes a per-energy path in double
+ * in either precision: the sums over M are formed once per energy, then one exponential per
+ * temperature and energy.
  * g on the device if g_on_device, outputs on the device if out_on_device; a call with any host
  * buffer synchronises stream. Any counts of this geometry are accepted; the graph's own tables,
  * whose counts lie only on the energies its configurations reach, take the faster path.

@@ -493,6 +493,136 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
     }
 }
 
+// Fields all zero: the sum over M of Eq. (2) is the same at every temperature, so it is taken once
+// per energy. The CTA first forms, for every energy bin e, ln G0(e) with G0(e) = sum_M g(e, M), and
+// the mean, variance, <|M|>, <M^2> and <M^4> of M within that bin, from exact integer sums (a
+// flip-symmetric row has a mean of exactly zero). One warp per temperature then weighs
+// the bins by w_e = G0(e) exp(-E_e/T), relative to the largest: ln Z = max + ln sum w, <H> = <E>,
+// C = Var(E)/T^2 (two passes), <M> = sum w mu_e / sum w, chi = sum w (var_e + (mu_e - <M>)^2) /
+// (T sum w), and the magnetisation moments from the bins' moments. Everything in double; one
+// exponential per (temperature, energy) instead of one per (temperature, energy, M).
+constexpr int kH0MaxE = 1024;            // energy bins whose moments fit the CTA's shared memory
+constexpr int kH0Warps = 8;              // at most this many temperatures per CTA
+
+// 128-bit integers to double (two roundings: within 2 ulp)
+__device__ __forceinline__ double u128_to_double(unsigned __int128 x) {
+    return (double)(uint64_t)(x >> 64) * 18446744073709551616.0 + (double)(uint64_t)x;
+}
+__device__ __forceinline__ double i128_to_double(__int128 x) {
+    return x < 0 ? -u128_to_double((unsigned __int128)(-x)) : u128_to_double((unsigned __int128)x);
+}
+
+__global__ void __launch_bounds__(32 * kH0Warps) thermo_h0_kernel(const __grid_constant__ ThermoParams P) {
+    const ThermoArgs& a = P.a;
+    const double* Tv = a.T ? a.T : P.grid;
+    extern __shared__ __align__(16) unsigned char sm[];
+    double* lnG0 = reinterpret_cast<double*>(sm);
+    double* mu = lnG0 + a.n_e;
+    double* vr = mu + a.n_e;
+    double* ab = vr + a.n_e;
+    double* q2 = ab + a.n_e;
+    double* q4 = q2 + a.n_e;
+    const int N = a.n, n_m = a.n_m;
+    for (int e = threadIdx.x; e < a.n_e; e += blockDim.x) {
+        // exact integer moments of the row (128-bit: c < 2^63, |M|^4 <= 2^24, at most 65 columns),
+        // on the integer pipe; the variance about the integer Mp nearest the mean, also exact
+        const int64_t* row = a.g + (size_t)e * n_m;
+        unsigned __int128 G0 = 0, SA = 0, S2 = 0, S4 = 0;
+        __int128 S1 = 0;
+        for (int m = 0; m < n_m; ++m) {
+            const uint64_t c = (uint64_t)row[m];
+            if (!c) continue;
+            const int M = 2 * m - N;
+            const uint64_t aM = (uint64_t)(M < 0 ? -M : M), M2 = aM * aM;
+            G0 += c;
+            SA += (unsigned __int128)c * aM;
+            S2 += (unsigned __int128)c * M2;
+            S4 += (unsigned __int128)c * (M2 * M2);
+            S1 += M < 0 ? -(__int128)((unsigned __int128)c * aM) : (__int128)((unsigned __int128)c * aM);
+        }
+        if (G0 == 0) {
+            lnG0[e] = -INFINITY;
+            mu[e] = vr[e] = ab[e] = q2[e] = q4[e] = 0;
+            continue;
+        }
+        const double G0d = u128_to_double(G0), inv = 1.0 / G0d, mean = i128_to_double(S1) * inv;
+        const int64_t Mp = llrint(mean);
+        const __int128 Q = (__int128)S2 - 2 * (__int128)Mp * S1 + (__int128)(Mp * Mp) * (__int128)G0;   // sum c (M - Mp)^2
+        const double dm = mean - (double)Mp;                                                            // |dm| <= 1/2
+        lnG0[e] = log(G0d);
+        mu[e] = mean;
+        vr[e] = fmax(0.0, i128_to_double(Q) * inv - dm * dm);
+        ab[e] = u128_to_double(SA) * inv;
+        q2[e] = u128_to_double(S2) * inv;
+        q4[e] = u128_to_double(S4) * inv;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    constexpr int kCache = 8;                          // weights kept in registers for the second pass
+    for (int it = blockIdx.x * nw + warp; it < a.nT; it += gridDim.x * nw) {
+        const double invT = 1.0 / Tv[it];
+        double xmax = -INFINITY;
+        for (int e = lane; e < a.n_e; e += 32)
+            if (lnG0[e] != -INFINITY) xmax = fmax(xmax, lnG0[e] - (double)(a.e_min + 2 * e) * invT);
+        xmax = warp_max(xmax);
+        auto weight = [&](int e) { return lnG0[e] == -INFINITY ? 0.0 : exp(lnG0[e] - (double)(a.e_min + 2 * e) * invT - xmax); };
+        double wc[kCache];
+        double z = 0, sE = 0, sM = 0;
+#pragma unroll
+        for (int j = 0; j < kCache; ++j) {
+            const int e = lane + 32 * j;
+            wc[j] = e < a.n_e ? weight(e) : 0.0;
+            if (e < a.n_e) {
+                z += wc[j];
+                sE += wc[j] * (double)(a.e_min + 2 * e);
+                sM += wc[j] * mu[e];
+            }
+        }
+        for (int e = lane + 32 * kCache; e < a.n_e; e += 32) {
+            const double w = weight(e);
+            z += w;
+            sE += w * (double)(a.e_min + 2 * e);
+            sM += w * mu[e];
+        }
+        z = warp_sum(z);
+        sE = warp_sum(sE);
+        sM = warp_sum(sM);
+        const double iz = 1.0 / z, mE = sE * iz, mM = sM * iz;
+        double vE = 0, vM = 0, sa = 0, s2 = 0, s4 = 0;
+        auto add = [&](int e, double w) {
+            const double dE = (double)(a.e_min + 2 * e) - mE, dM = mu[e] - mM;
+            vE += w * dE * dE;
+            vM += w * (vr[e] + dM * dM);
+            sa += w * ab[e];
+            s2 += w * q2[e];
+            s4 += w * q4[e];
+        };
+#pragma unroll
+        for (int j = 0; j < kCache; ++j)
+            if (lane + 32 * j < a.n_e) add(lane + 32 * j, wc[j]);
+        for (int e = lane + 32 * kCache; e < a.n_e; e += 32) add(e, weight(e));
+        vE = warp_sum(vE);
+        vM = warp_sum(vM);
+        sa = warp_sum(sa);
+        s2 = warp_sum(s2);
+        s4 = warp_sum(s4);
+        if (lane == 0)
+            for (int ih = 0; ih < a.nh; ++ih) {         // every field of the grid is zero
+                const size_t o = (size_t)it * a.nh + ih;
+                if (a.logZ) a.logZ[o] = xmax + log(z);
+                if (a.E) a.E[o] = mE;
+                if (a.M) a.M[o] = mM;
+                if (a.C) a.C[o] = vE * iz * invT * invT;
+                if (a.chi) a.chi[o] = vM * iz * invT;
+                const double m2 = s2 * iz, m4 = s4 * iz;
+                if (a.absM) a.absM[o] = sa * iz;
+                if (a.M2) a.M2[o] = m2;
+                if (a.M4) a.M4[o] = m4;
+                if (a.binder) a.binder[o] = m2 > 0 ? 1.0 - m4 / (3.0 * m2 * m2) : 0.0;
+            }
+    }
+}
+
 // The graph's energy sublattice in public bins: reachable energies E = e_lo + G k (k < n_e_c) sit
 // at bins (E + S) / 2 = e0 + (G / 2) k.
 void set_energy_sublattice(ThermoArgs& a, const isg_graph& g) {
@@ -502,9 +632,21 @@ void set_energy_sublattice(ThermoArgs& a, const isg_graph& g) {
 }
 
 // Enqueue the thermodynamics kernels; all pointers on the device. lng: n_e * n_m doubles, lngf:
-// 2 * n_e * n_m floats of scratch. P.a.cluster is set here.
-void launch_thermo(ThermoParams& P, double* lng, float* lngf, int precision, cudaStream_t s) {
+// 2 * n_e * n_m floats of scratch. P.a.cluster is set here. h_zero: every field of the grid is 0
+// (the per-energy path, which needs neither scratch array).
+void launch_thermo(ThermoParams& P, double* lng, float* lngf, int precision, cudaStream_t s, bool h_zero) {
     ThermoArgs& a = P.a;
+    if (h_zero && a.n_e <= kH0MaxE) {
+        // every field zero: the per-energy path (thermo_h0_kernel), in double whatever the precision
+        // few temperatures: fewer warps a CTA, so the per-temperature chains of double operations
+        // spread over more SMs (each CTA forms the energies' moments on the integer pipe)
+        a.cluster = 1;
+        const int warps = std::max(1, std::min(kH0Warps, a.nT / device_info().sms));
+        const int ctas = (a.nT + warps - 1) / warps;
+        thermo_h0_kernel<<<ctas, 32 * warps, 6 * sizeof(double) * (size_t)a.n_e, s>>>(P);
+        ISG_CUDA(cudaGetLastError());
+        return;
+    }
     const int nbins = a.n_e * a.n_m;
     float* lnglo = lngf + nbins;
     // 128 threads: one warp per SM sub-partition, so the FP64 logarithms of a small table spread
@@ -594,7 +736,7 @@ extern "C" isg_status isg_specific_heat_peak(const int64_t* g, int32_t g_on_devi
             for (int k = 0; k < kGrid; ++k) P->grid[k] = lo + (hi - lo) * k / (kGrid - 1);
             P->grid[kGrid] = h;
             launch_thermo(*P, reinterpret_cast<double*>(scratch + o_lng), reinterpret_cast<float*>(scratch + o_lngf),
-                          precision, s);
+                          precision, s, h == 0.0);
             ISG_CUDA(cudaMemcpyAsync(C.data(), a.C, sizeof(double) * kGrid, cudaMemcpyDeviceToHost, s));
             ISG_CUDA(cudaStreamSynchronize(s));
             int kb = 0;
@@ -676,7 +818,10 @@ static void thermo_grid(const int64_t* g, int32_t g_on_device, const isg_graph* 
                                       : reinterpret_cast<double*>(scratch + o_out) + (j++) * pts;
     a.logZ = outs_dev[0]; a.E = outs_dev[1]; a.M = outs_dev[2]; a.C = outs_dev[3]; a.chi = outs_dev[4];
     a.absM = outs_dev[5]; a.M2 = outs_dev[6]; a.M4 = outs_dev[7]; a.binder = outs_dev[8];
-    launch_thermo(*P, reinterpret_cast<double*>(scratch + o_lng), reinterpret_cast<float*>(scratch + o_lngf), precision, s);
+    bool h_zero = true;
+    for (int k = 0; k < nh; ++k) h_zero = h_zero && h[k] == 0.0;
+    launch_thermo(*P, reinterpret_cast<double*>(scratch + o_lng), reinterpret_cast<float*>(scratch + o_lngf), precision, s,
+                  h_zero);
     if (!out_on_device) {
         // the requested outputs lie side by side in the scratch: one copy into the stage
         char* out_host = stage->data() + (g_on_device ? 0 : gbytes);

@@ -347,3 +347,46 @@ def test_binder_cumulants_cross_near_onsager(isg, cuda):
     assert len(sign_changes) == 1
     t_cross = T[sign_changes[0]]
     assert abs(t_cross - 2 / np.log(1 + np.sqrt(2))) < 0.1, t_cross
+
+
+@pytest.mark.parametrize("lat", [w.square(4, 4, False), w.square(6, 6, True), w.cubic(3, 3, 4, True),
+                                 w.with_random_couplings(w.triangular(4, 5, True), w.SplitMix64(9), (-2, -1, 1, 2))],
+                         ids=lambda l: l.name)
+def test_zero_field_path_against_the_general_path(isg, cuda, lat):
+    """Grids whose fields are all zero take the per-energy path (the sum over M once per energy);
+    its outputs, thermodynamic and magnetic, equal those of the general kernel (the h = 0 row of a
+    grid that also holds a nonzero field) within 1e-12 relative."""
+    g = oracle.g_masks(lat.n, lat.edges) if lat.n <= 24 else \
+        oracle.g_frontier(lat.n, lat.edges, 16) if lat.meta.get("kind") == "square" else None
+    if g is None:
+        from relabel import layer_cut
+        r, cut = layer_cut(lat)
+        g = oracle.g_frontier_cut(r.n, r.edges, cut, max_active=20)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    T = np.linspace(0.4, 6, 97)
+    zero = isg.isg_thermo(g, gh, T, [0.0], isg.ISG_FP64)
+    gen = isg.isg_thermo(g, gh, T, [0.0, 0.25], isg.ISG_FP64)
+    for k, (a, b) in enumerate(zip(zero, gen)):
+        assert rel_close(a[:, 0], b[:, 0], 1e-12, 1e-12 * lat.n), k
+    mz = isg.isg_magnetisation(g, gh, T, [0.0], isg.ISG_FP64)
+    mg = isg.isg_magnetisation(g, gh, T, [0.0, 0.25], isg.ISG_FP64)
+    for k, (a, b) in enumerate(zip(mz, mg)):
+        assert rel_close(a[:, 0], b[:, 0], 1e-12, 1e-12), k
+
+
+def test_zero_field_path_on_asymmetric_counts(isg, cuda):
+    """The per-energy path on a table of arbitrary counts (no M -> -M symmetry, so <M> is not zero
+    and the per-energy variances matter) against the oracle at h = 0, FP64 and FP32 requests."""
+    lat = w.square(4, 4, True)
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    rng = np.random.default_rng(7)
+    g = oracle.g_masks(lat.n, lat.edges)
+    g = np.where(g > 0, g * rng.integers(1, 50, size=g.shape) + rng.integers(0, 3, size=g.shape), 0).astype(np.int64)
+    g[:, -1] += 5                                     # a heavier all-up column
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    T = np.linspace(0.5, 5, 31)
+    ref = oracle.thermo(lat.n, e_min, g, T, [0.0])
+    for prec in (isg.ISG_FP64, isg.ISG_FP32):
+        got = isg.isg_thermo(g, gh, T, [0.0], prec)
+        for k, (a, b) in enumerate(zip(got, ref)):
+            assert rel_close(a, b, 1e-12, 1e-12 * lat.n), (prec, k, np.max(np.abs(a - b) / (np.abs(b) + 1e-300)))
