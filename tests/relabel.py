@@ -54,3 +54,15 @@ def layer_cut(lat: w.Lattice):
     # there are renumbered 0 .. k-1
     k = int((coords[:, slowest] == 0).sum())
     return r, (1 << k) - 1
+
+
+def frontier_table(lat: w.Lattice, threads: int = 1):
+    """The oracle's exact table of a box lattice by its frontier programme: sites renumbered along
+    the short side, and for periodic cubic lattices (whose frontier spans two cross-sections and
+    their wrap-around) conditioned on the first cross-section."""
+    import oracle
+    if lat.meta.get("kind") == "cubic" and lat.meta.get("periodic"):
+        r, cut = layer_cut(lat)
+        return oracle.g_frontier_cut(r.n, r.edges, cut, max_active=20, threads=threads)
+    r = short_side_fastest(lat)
+    return oracle.g_frontier(r.n, r.edges, max_active=20)

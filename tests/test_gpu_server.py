@@ -18,10 +18,16 @@ def alone(isg, lat):
     return isg.isg_enumerate(isg.isg_graph_create(lat.n, lat.edges))
 
 
+def reference(lat):
+    """The oracle's table: the popcount oracle up to 22 spins, else the frontier programme."""
+    from relabel import frontier_table
+    return oracle.g_masks(lat.n, lat.edges, threads=THREADS) if lat.n <= 22 else frontier_table(lat, THREADS)
+
+
 def test_mix_equals_alone(isg, cuda):
     """A seeded request stream (N 16..32, square / triangular / cubic, free or periodic, J in
-    {-2,-1,1,2}) submitted at once from one thread: each table equals isg_enumerate alone, and the
-    small ones equal the oracle."""
+    {-2,-1,1,2}) submitted at once from one thread: each table equals isg_enumerate alone and the
+    oracle's (the popcount oracle up to 22 spins, the frontier programme above)."""
     reqs = w.serving_stream(48, n_range=(16, 32), seed=7)
     srv = isg.Server(step_ms=5.0)
     tickets = [(srv.submit(isg.isg_graph_create(r.lattice.n, r.lattice.edges)), r.lattice) for r in reqs]
@@ -30,8 +36,7 @@ def test_mix_equals_alone(isg, cuda):
         g, times = srv.result(t)
         assert np.array_equal(g, alone(isg, lat)), lat.name
         assert times[2] >= times[1] >= 0 and times[0] >= 0
-        if lat.n <= 22:
-            assert np.array_equal(g, oracle.g_masks(lat.n, lat.edges, threads=THREADS)), lat.name
+        assert np.array_equal(g, reference(lat)), lat.name
     st = srv.stats()
     assert st["tickets"] == 0 and st["admitted"] == 0 and st["steps"] >= 1
     srv.close()
@@ -40,7 +45,8 @@ def test_mix_equals_alone(isg, cuda):
 def test_mix_with_split_equals_alone(isg, cuda):
     """With split-and-convolve enabled (split_work_ratio = 0.5), a stream of requests up to N = 36
     (the large ones served by split launches, mixed with tile steps) gives every table equal to
-    isg_enumerate alone; the split planner is consulted on the host for each large request."""
+    isg_enumerate alone and to the oracle's; the split planner is consulted on the host for each
+    large request."""
     reqs = w.serving_stream(40, n_range=(20, 36), seed=11)
     srv = isg.Server(step_ms=5.0, split_work_ratio=0.5)
     tickets = [(srv.submit(isg.isg_graph_create(r.lattice.n, r.lattice.edges)), r.lattice) for r in reqs]
@@ -49,6 +55,7 @@ def test_mix_with_split_equals_alone(isg, cuda):
         srv.wait(t, 120000)
         g, _ = srv.result(t)
         assert np.array_equal(g, alone(isg, lat)), lat.name
+        assert np.array_equal(g, reference(lat)), lat.name
         gh = isg.isg_graph_create(lat.n, lat.edges)
         try:
             n_split += lat.n >= 24 and isg.isg_split_plan(gh)["work_ratio"] < 0.5
@@ -61,8 +68,8 @@ def test_mix_with_split_equals_alone(isg, cuda):
 def test_mix_with_symmetry_equals_alone(isg, cuda):
     """With symmetry = 1 the server enumerates only the configurations with spin N-1 up of every
     tile-served request of 13 or more spins and mirrors the table in the step that carries its last
-    tile: every table equals isg_enumerate alone (all 2^N configurations), the small ones equal the
-    oracle, and the server counts about half the configurations enumerated."""
+    tile: every table equals isg_enumerate alone (all 2^N configurations) and the oracle's, and the
+    server counts about half the configurations enumerated."""
     reqs = w.serving_stream(40, n_range=(10, 30), seed=13)
     srv = isg.Server(step_ms=5.0, symmetry=1)
     tickets = [(srv.submit(isg.isg_graph_create(r.lattice.n, r.lattice.edges)), r.lattice) for r in reqs]
@@ -70,8 +77,7 @@ def test_mix_with_symmetry_equals_alone(isg, cuda):
         srv.wait(t, 60000)
         g, _ = srv.result(t)
         assert np.array_equal(g, alone(isg, lat)), lat.name
-        if lat.n <= 20:
-            assert np.array_equal(g, oracle.g_masks(lat.n, lat.edges, threads=THREADS)), lat.name
+        assert np.array_equal(g, reference(lat)), lat.name
     st = srv.stats()
     full = sum(1 << lat.n for _, lat in tickets)
     assert st["configs"] < 0.6 * full
@@ -83,7 +89,7 @@ def test_mix_with_symmetry_equals_alone(isg, cuda):
 def test_mix_with_split_and_symmetry_equals_alone(isg, cuda):
     """Both options at once (split_work_ratio = 0.5, symmetry = 1): large requests by split launches,
     the other tile-served ones halved and mirrored, in shared steps. Every table equals
-    isg_enumerate alone."""
+    isg_enumerate alone and the oracle's."""
     reqs = w.serving_stream(32, n_range=(14, 34), seed=17)
     srv = isg.Server(step_ms=5.0, split_work_ratio=0.5, symmetry=1)
     tickets = [(srv.submit(isg.isg_graph_create(r.lattice.n, r.lattice.edges)), r.lattice) for r in reqs]
@@ -91,6 +97,7 @@ def test_mix_with_split_and_symmetry_equals_alone(isg, cuda):
         srv.wait(t, 120000)
         g, _ = srv.result(t)
         assert np.array_equal(g, alone(isg, lat)), lat.name
+        assert np.array_equal(g, reference(lat)), lat.name
     srv.close()
 
 
