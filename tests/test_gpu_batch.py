@@ -61,11 +61,13 @@ def test_batch_symmetry(isg, cuda):
 
 def test_batch_split_and_symmetry(isg, cuda):
     """split = 1 and symmetry = 1 at once on a mixed batch (EA 5x6 instances that go to split
-    launches, smaller tile-served and small-kernel graphs): every table equals the per-instance
-    enumeration, and replaying the prepared batch gives the same tables."""
+    launches, smaller tile-served and small-kernel graphs): every table equals the oracle's (the
+    frontier programme for the EA instances), and replaying the prepared batch gives the same
+    tables."""
+    from relabel import frontier_table
     lats = [l for l in w.ea_instances(64) if l.n == 30][:6] + mixed_graphs()
     hs = [isg.isg_graph_create(l.n, l.edges) for l in lats]
-    ref = [isg.isg_enumerate(h) for h in hs]
+    ref = [frontier_table(l, THREADS) if l.n > 22 else oracle.g_masks(l.n, l.edges, threads=THREADS) for l in lats]
     outs = isg.isg_enumerate_batch(hs, split=1, symmetry=1)
     for l, g, r in zip(lats, outs, ref):
         assert np.array_equal(g, r), l.name
@@ -105,16 +107,21 @@ def test_prepared_batch_replay(isg, cuda):
 def test_autotuned_batch(isg, cuda):
     """A batch planned by the autotuner (lane spins of the index order or of the bank-conflict
     model, shared by instances that differ only in coupling signs) gives the same tables as the
-    default plan."""
+    default plan, and every one equals the oracle's frontier programme."""
     import torch
+    from concurrent.futures import ThreadPoolExecutor
+    from relabel import frontier_table
     lats = w.ea_instances(count=256, seed=99)
     hs = [isg.isg_graph_create(l.n, l.edges) for l in lats]
     b0, b1 = isg.Batch(hs), isg.Batch(hs, autotune=1)
     b0.run()
     b1.run()
     b1.status()
+    with ThreadPoolExecutor(max_workers=THREADS) as ex:
+        refs = list(ex.map(frontier_table, lats))
     for k in range(len(lats)):
         assert torch.equal(b0.table(k), b1.table(k)), lats[k].name
+        assert np.array_equal(b1.table(k).cpu().numpy(), refs[k]), lats[k].name
     b0.close()
     b1.close()
 
