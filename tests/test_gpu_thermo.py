@@ -390,3 +390,20 @@ def test_zero_field_path_on_asymmetric_counts(isg, cuda):
         got = isg.isg_thermo(g, gh, T, [0.0], prec)
         for k, (a, b) in enumerate(zip(got, ref)):
             assert rel_close(a, b, 1e-12, 1e-12 * lat.n), (prec, k, np.max(np.abs(a - b) / (np.abs(b) + 1e-300)))
+
+
+def test_zero_field_path_at_its_size_limit(isg, cuda):
+    """Tables of nearly 1024 energy bins (the per-energy path's largest shared-memory block) and of
+    more (the general kernel), from graphs with large couplings, at h = 0 against the oracle."""
+    for J, expect_fast in (((-23, 17, 29, -31), True), ((-31, 37, 41, -43), False)):
+        lat = w.random_graph(18, 36, w.SplitMix64(5), couplings=J)
+        gh = isg.isg_graph_create(lat.n, lat.edges)
+        n_e = isg.table_shape(gh)[0]
+        assert (n_e <= 1024) == expect_fast, n_e
+        g = oracle.g_masks(lat.n, lat.edges)
+        e_min, _, _ = oracle.bins(lat.n, lat.edges)
+        T = np.linspace(2.0, 60.0, 37)
+        got = isg.isg_thermo(g, gh, T, [0.0], isg.ISG_FP64)
+        ref = oracle.thermo(lat.n, e_min, g, T, [0.0])
+        for k, (a, b) in enumerate(zip(got, ref)):
+            assert rel_close(a, b, 1e-12, 1e-12 * lat.n), (J, k)
