@@ -780,6 +780,22 @@ def run_profile_case(args):
         for _ in range(args.warmup):
             call()
         res["fp64_ms"] = _event_ms(call, stream, args.steps)
+    elif args.profile_case == "small-pair":
+        # the 4x4 free lattice's prepared call pair (enumerate + FP64 thermodynamics on 64 T at
+        # h = 0) as the default benchmark times it; the timed pairs inside the NVTX range isg_timed
+        lat = workloads.square(4, 4, False)
+        gh = isg.isg_graph_create(lat.n, lat.edges)
+        g = torch.zeros(isg.table_shape(gh), dtype=torch.int64, device=dev)
+        outs = tuple(torch.empty((64, 1), dtype=torch.float64, device=dev) for _ in range(5))
+        pe = isg.prepare_enumerate(gh, g, stream)
+        pt = isg.prepare_thermo(g, gh, np.linspace(0.5, 5, 64), [0.0], outs, isg.ISG_FP64, stream)
+        for _ in range(args.warmup):
+            pe()
+            pt()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("isg_timed")
+        res["pair_ms"] = _event_ms(lambda: (pe(), pt()), stream, args.steps)
+        torch.cuda.nvtx.range_pop()
     elif args.profile_case in ("cubic-enumerate", "torus-enumerate"):
         # the full enumeration of the 3x3x4 (or 6x6) torus, autotuned as in the benchmark; with
         # --shard-bits k, shard 0 of 2^k with q - k inner bits (the full launch's task count)
@@ -828,7 +844,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target seconds of the oracle sample")
     ap.add_argument("--serving", action="store_true", help="run the request-stream (serving) benchmark instead")
-    ap.add_argument("--profile-case", choices=("ea-batch", "ea-batch-tuned", "ea-split-batch", "cubic-thermo", "small-thermo", "cubic-enumerate", "torus-enumerate",
+    ap.add_argument("--profile-case", choices=("ea-batch", "ea-batch-tuned", "ea-split-batch", "cubic-thermo", "small-thermo", "small-pair", "cubic-enumerate", "torus-enumerate",
                                                "split-torus6x6",
                                                "split-torus7x7", "split-torus8x8", "split-cubic3x3x4"),
                     default=None,
