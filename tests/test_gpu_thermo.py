@@ -407,3 +407,33 @@ def test_zero_field_path_at_its_size_limit(isg, cuda):
         ref = oracle.thermo(lat.n, e_min, g, T, [0.0])
         for k, (a, b) in enumerate(zip(got, ref)):
             assert rel_close(a, b, 1e-12, 1e-12 * lat.n), (J, k)
+
+
+@pytest.mark.parametrize("index", [0, 3])
+def test_fp32_within_bounds_on_frustrated_instances(isg, cuda, index):
+    """FP32 against FP64 on Edwards-Anderson +-J 5x6 instances (frustrated, many degenerate ground
+    states), down to T = 0.2 and across h in [-2, 2]: the stated bounds |dlnZ| <= 2e-5,
+    |d<E>| <= 1e-5 (S + N |h|max), |d<M>| <= 1e-5 N, C and chi within 1e-3 relative (or 1e-3 of the
+    grid maximum); the FP64 path against the oracle on sampled points."""
+    lat = [l for l in w.ea_instances(64) if l.n == 30][index]
+    gh = isg.isg_graph_create(lat.n, lat.edges)
+    g = oracle.g_frontier(lat.n, lat.edges, 16)
+    T = np.linspace(0.2, 5, 97)
+    h = np.linspace(-2, 2, 65)
+    d = isg.isg_thermo(g, gh, T, h, isg.ISG_FP64)
+    f = isg.isg_thermo(g, gh, T, h, isg.ISG_FP32)
+    e_min, _, _ = oracle.bins(lat.n, lat.edges)
+    rng = w.SplitMix64(40 + index)
+    for _ in range(12):
+        a, b = rng.below(len(T)), rng.below(len(h))
+        ref = oracle.thermo(lat.n, e_min, g, T[a:a + 1], h[b:b + 1])
+        for k in range(5):
+            assert abs(d[k][a, b] - ref[k][0, 0]) <= 1e-12 * abs(ref[k][0, 0]) + 1e-12 * lat.n, (k, a, b)
+    S, N = int(np.abs(lat.edges[:, 2]).sum()), lat.n
+    assert np.max(np.abs(f[0] - d[0])) <= 2e-5
+    assert np.max(np.abs(f[1] - d[1])) <= 1e-5 * (S + N * 2)
+    assert np.max(np.abs(f[2] - d[2])) <= 1e-5 * N
+    for k in (3, 4):
+        scale = np.max(np.abs(d[k]))
+        err = np.abs(f[k] - d[k])
+        assert np.all(err <= np.maximum(1e-3 * np.abs(d[k]), 1e-3 * scale)), k
