@@ -38,6 +38,18 @@ ISG_API isg_status isg_debug_lane_banks(const isg_graph* graph, const isg_option
                                         double* mean_wavefronts, int32_t* max_wavefronts);
 
 /*
+ * The histogram layout of one copy under the plan of *opt (host only), as 99 int32 in out:
+ * [0] row stride R, [1] words of one copy, [2] sub-tables n_sub (1, or 10 with lane tables),
+ * [3..13) sub_off, [13..23) m_lo, [23..33) m_hi, [33..65) lane_word, [65..97) lane_sub,
+ * [97] packed (1: the lane tables share each row; 0: each is a block of its own), [98] 0.
+ * Bin (e', m) of sub-table t is word sub_off[t] + e' R + m of the copy, for m in [m_lo[t], m_hi[t]];
+ * lane l counts into sub-table lane_sub[l], starting at word lane_word[l]. Entries past n_sub
+ * are 0. Errors: INVALID (NULL pointers, or a thread-per-configuration plan), as isg_enumerate
+ * otherwise.
+ */
+ISG_API isg_status isg_debug_lane_layout(const isg_graph* graph, const isg_options* opt, int32_t* out);
+
+/*
  * Run the enumeration kernels' per-thread walk on the host, with every counter address checked,
  * and write g (host buffer, isg_graph_bins geometry) as isg_enumerate would. The walk visits
  * 2^N configurations one by one (Sec. 3), so this is for small N. Returns ISG_ERR_INTERNAL if

@@ -45,9 +45,10 @@ struct EnumArgs {
     int32_t flush_rounds;
     int32_t copy_words;              // words of one histogram copy
     int32_t n_sub;                   // sub-tables per copy (1, or kLaneTables for lane tables)
-    int32_t sub_words;               // words per sub-table
-    int32_t sub_off[kLaneTables];    // first bin of sub-table t lies sub_off[t] words into it
-    int32_t lane_word[32];           // lane l counts into the bins starting lane_word[l] words into its copy
+    int32_t sub_off[kLaneTables];    // bin (e', m) of sub-table t is word sub_off[t] + e' stride + m,
+    int32_t sub_m_lo[kLaneTables];   // for the columns m in [sub_m_lo[t], sub_m_hi[t]] only (the
+    int32_t sub_m_hi[kLaneTables];   // other words of those rows may be another sub-table's)
+    int32_t lane_word[32];           // lane l counts into the sub-table starting lane_word[l] words into its copy
     int32_t pad;
 };
 
@@ -65,20 +66,21 @@ struct EnumParams {
 };
 
 // Add the CTA's privatised bins (every sub-table of every copy) into the public int64 table and
-// clear them.
+// clear them. Thread i takes bin (e', m) = (i / n_m, i % n_m) of every sub-table holding column m.
 __device__ __forceinline__ void flush_bins(const ProgHeader* hd, uint32_t* hist, const EnumArgs& a, int64_t* g) {
-    const int nb = hd->nbins_c, n_m = hd->n_m, R = hd->stride;
+    const int n_m = hd->n_m, R = hd->stride, nb = hd->n_e_c * n_m;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const int ec = i / n_m, m = i - ec * n_m;
         unsigned long long s = 0;
         for (int c = 0; c < a.copies; ++c)
-            for (int t = 0; t < a.n_sub; ++t) {
-                uint32_t& w = hist[c * a.copy_words + t * a.sub_words + a.sub_off[t] + i];
-                s += w;
-                w = 0;
-            }
-        const int64_t ec = i / R, m = i - ec * R;
-        if (s && m < n_m) {                 // padding columns m > N are never counted
-            const int64_t e = (hd->e_lo + hd->G * ec + hd->S) / 2;
+            for (int t = 0; t < a.n_sub; ++t)
+                if (m >= a.sub_m_lo[t] && m <= a.sub_m_hi[t]) {
+                    uint32_t& w = hist[c * a.copy_words + a.sub_off[t] + ec * R + m];
+                    s += w;
+                    w = 0;
+                }
+        if (s) {
+            const int64_t e = (hd->e_lo + (int64_t)hd->G * ec + hd->S) / 2;
             atomicAdd(reinterpret_cast<unsigned long long*>(g + e * n_m + m), s);
         }
     }

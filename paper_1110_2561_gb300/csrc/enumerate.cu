@@ -220,8 +220,11 @@ void launch_enumeration(const Plan& p, const uint64_t* d_blob, int blob_words, i
     a.flush_rounds = p.flush_rounds;
     a.copy_words = p.copy_words;
     a.n_sub = p.n_sub;
-    a.sub_words = p.sub_words;
-    for (int t = 0; t < kLaneTables; ++t) a.sub_off[t] = p.sub_off[t];
+    for (int t = 0; t < kLaneTables; ++t) {
+        a.sub_off[t] = p.sub_off[t];
+        a.sub_m_lo[t] = p.sub_m_lo[t];
+        a.sub_m_hi[t] = p.sub_m_hi[t];
+    }
     for (int l = 0; l < 32; ++l) a.lane_word[l] = p.lane_word[l];
     switch (p.b) {
         case 1: launch_b<1>(p, *P, s); break;

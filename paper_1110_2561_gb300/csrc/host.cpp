@@ -4,6 +4,8 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -163,12 +165,9 @@ static void order_spins(Plan& p, int n, int free, const std::vector<int>& low, c
 // 1951): read the bits of a value from bit 0 up, a 0 as an opening and a 1 as a closing bracket,
 // and match brackets. Values with the same matched pairs (the same matched positions holding the
 // same bits) form one chain: the unmatched bits read 1..1 0..0, with one more 1 for each step up
-// the chain. Each chain holds consecutive popcounts. Laying the chains'
-// popcount ranges end to end over the 32 banks gives each sub-table its bank offset.
-void lane_table_layout(int sub_words, int32_t* sub_off, int32_t* lane_word) {
-    if (sub_words % 32) fail(ISG_ERR_INTERNAL, "lane sub-tables must be a multiple of 32 words");
+// the chain. Each chain holds consecutive popcounts: chain t holds [low[t], low[t] + len[t]).
+static void lane_chains(int* chain_of, int* low, int* len) {
     std::vector<std::pair<uint32_t, uint32_t>> keys;    // (matched positions, their bits) per chain
-    int chain_of[32];
     for (uint32_t l = 0; l < 32; ++l) {
         int open[5], sp = 0;
         uint32_t matched = 0;
@@ -183,28 +182,162 @@ void lane_table_layout(int sub_words, int32_t* sub_off, int32_t* lane_word) {
         chain_of[l] = t;
     }
     if ((int)keys.size() != kLaneTables) fail(ISG_ERR_INTERNAL, "lane values do not form ten chains");
-    int low[kLaneTables], len[kLaneTables], order[kLaneTables];
-    for (int t = 0; t < kLaneTables; ++t) { low[t] = 5; len[t] = 0; order[t] = t; }
+    for (int t = 0; t < kLaneTables; ++t) { low[t] = 5; len[t] = 0; }
     for (int l = 0; l < 32; ++l) {
-        const int t = chain_of[l];
-        low[t] = std::min(low[t], __builtin_popcount((unsigned)l));
-        ++len[t];
+        low[chain_of[l]] = std::min(low[chain_of[l]], __builtin_popcount((unsigned)l));
+        ++len[chain_of[l]];
     }
-    std::stable_sort(order, order + kLaneTables, [&](int x, int y) { return low[x] < low[y]; });
-    int bank = 0;
-    for (int i = 0; i < kLaneTables; ++i) {
-        const int t = order[i];
-        sub_off[t] = bank - low[t];
-        if (sub_off[t] < 0 || sub_off[t] >= 32) fail(ISG_ERR_INTERNAL, "lane sub-table offset out of range");
-        bank += len[t];
+}
+
+// Order of the packed layout. The chains' bank ranges tile the 32 banks in a circular order
+// (slot k: banks [beta[k], beta[k] + len[k]), the length-6 chain at bank 0), and the row holds
+// them in the order path[0..9] of slots. A chain spans len + N - 5 words of a row; the next one
+// starts at the first word after it whose bank is its beta, c = (N - 5) mod 32 banks on, plus
+// gap[k] words. For each circular arrangement of the lengths (126: which four of the other nine
+// slots hold the length-4 chains) a dynamic programme over subsets finds the path of least total
+// gap; the least over all arrangements is kept. Depends on N only through c, so it is computed
+// once per residue.
+struct PackedOrder {
+    int len[kLaneTables], beta[kLaneTables], path[kLaneTables], gap[kLaneTables];
+    int total_gap;
+};
+
+static PackedOrder packed_order_search(int c) {
+    PackedOrder best{};
+    best.total_gap = 1 << 30;
+    constexpr int S = 1 << kLaneTables;
+    std::vector<int> dp((size_t)S * kLaneTables), from((size_t)S * kLaneTables);
+    for (int sel = 0; sel < (1 << (kLaneTables - 1)); ++sel) {
+        if (__builtin_popcount((unsigned)sel) != 4) continue;
+        int len[kLaneTables], beta[kLaneTables];
+        len[0] = 6;
+        for (int k = 1; k < kLaneTables; ++k) len[k] = ((sel >> (k - 1)) & 1) ? 4 : 2;
+        beta[0] = 0;
+        for (int k = 1; k < kLaneTables; ++k) beta[k] = beta[k - 1] + len[k - 1];
+        auto gap = [&](int i, int j) { return (((beta[j] - beta[i] - len[i] - c) % 32) + 32) % 32; };
+        std::fill(dp.begin(), dp.end(), 1 << 29);
+        for (int j = 0; j < kLaneTables; ++j) dp[((size_t)1 << j) * kLaneTables + j] = 0;
+        for (int m = 1; m < S; ++m)
+            for (int i = 0; i < kLaneTables; ++i) {
+                const int v = dp[(size_t)m * kLaneTables + i];
+                if (!((m >> i) & 1) || v >= best.total_gap) continue;
+                for (int j = 0; j < kLaneTables; ++j) {
+                    if ((m >> j) & 1) continue;
+                    const size_t to = (size_t)(m | (1 << j)) * kLaneTables + j;
+                    if (v + gap(i, j) < dp[to]) { dp[to] = v + gap(i, j); from[to] = i; }
+                }
+            }
+        for (int j = 0; j < kLaneTables; ++j) {
+            const int v = dp[(size_t)(S - 1) * kLaneTables + j];
+            if (v >= best.total_gap) continue;
+            best.total_gap = v;
+            std::copy(len, len + kLaneTables, best.len);
+            std::copy(beta, beta + kLaneTables, best.beta);
+            for (int m = S - 1, x = j, k = kLaneTables - 1; k >= 0; --k) {
+                best.path[k] = x;
+                const int px = from[(size_t)m * kLaneTables + x];
+                m ^= 1 << x;
+                x = px;
+            }
+            for (int k = 0; k + 1 < kLaneTables; ++k) best.gap[k] = gap(best.path[k], best.path[k + 1]);
+            best.gap[kLaneTables - 1] = 0;
+        }
     }
+    return best;
+}
+
+static const PackedOrder& packed_order(int c) {
+    static std::mutex mu;
+    static std::unique_ptr<PackedOrder> cache[32];
+    std::lock_guard<std::mutex> lk(mu);
+    if (!cache[c]) cache[c].reset(new PackedOrder(packed_order_search(c)));
+    return *cache[c];
+}
+
+void lane_table_layout(Plan& p, int n, int64_t rows, int64_t G, int fixed_stride) {
+    int chain_of[32], low[kLaneTables], len[kLaneTables];
+    lane_chains(chain_of, low, len);
+    const int rest = n - 5;                        // spins outside the lane bits
+    // strides R with R % 32 == 0 and (8 R) % G == 0: the multiples of `unit`
+    const int64_t unit = 32 / igcd(32, G / igcd(G, 8)) * (G / igcd(G, 8));
+    auto round_up = [&](int64_t x) { return (x + unit - 1) / unit * unit; };
+    if (fixed_stride > 0 && (fixed_stride % 32 || (8 * (int64_t)fixed_stride) % G || fixed_stride < n + 1))
+        fail(ISG_ERR_INVALID, "lane tables need a row stride that is a multiple of 32, at least N + 1, with "
+                              "8 x stride a multiple of the energy stride " + std::to_string(G));
+    for (int t = 0; t < kLaneTables; ++t) { p.sub_m_lo[t] = low[t]; p.sub_m_hi[t] = low[t] + len[t] - 1 + rest; }
+
+    // separate: chains in order of their lowest popcount take consecutive banks
+    const int64_t Rs = fixed_stride > 0 ? fixed_stride : round_up(n + 1);
+    const int64_t sub_words = rows * Rs + 32;
+    const int64_t sep_words = kLaneTables * sub_words;
+    // packed: the searched order, rotated so that the first chain's first word is word 0
+    const PackedOrder& po = packed_order(rest % 32);
+    int64_t A[kLaneTables];
+    int slot_chain[kLaneTables];
+    {
+        bool taken[kLaneTables] = {};
+        for (int k = 0; k < kLaneTables; ++k) {      // any chain of a slot's length takes the slot
+            int t = 0;
+            while (taken[t] || len[t] != po.len[k]) ++t;
+            taken[t] = true;
+            slot_chain[k] = t;
+        }
+    }
+    int64_t span = 0;
+    for (int k = 0; k < kLaneTables; ++k) {
+        const int s = po.path[k];
+        A[s] = span;
+        span += po.len[s] + rest + po.gap[k];
+    }
+    const int64_t Rp = round_up(span);
+    const int64_t packed_words = (rows - 1) * Rp + span;
+    const bool packed = fixed_stride == 0 && packed_words < sep_words;
+
+    int32_t off[kLaneTables];
+    if (packed) {
+        const int rot = ((low[slot_chain[po.path[0]]] - po.beta[po.path[0]]) % 32 + 32) % 32;
+        for (int k = 0; k < kLaneTables; ++k) {
+            const int t = slot_chain[k];
+            // first word of chain t's range: A (bank beta + rot), minus its lowest column
+            off[t] = (int32_t)(A[k] + low[slot_chain[po.path[0]]] - low[t]);
+            if (((off[t] + low[t]) % 32 + 32) % 32 != (po.beta[k] + rot) % 32)
+                fail(ISG_ERR_INTERNAL, "packed lane table lost its bank");
+        }
+        p.stride = (int)Rp;
+        p.copy_words = (int)(packed_words + low[slot_chain[po.path[0]]]);
+    } else {
+        int order[kLaneTables];
+        for (int t = 0; t < kLaneTables; ++t) order[t] = t;
+        std::stable_sort(order, order + kLaneTables, [&](int x, int y) { return low[x] < low[y]; });
+        int bank = 0;
+        for (int i = 0; i < kLaneTables; ++i) {
+            const int t = order[i];
+            if (bank - low[t] < 0 || bank - low[t] >= 32) fail(ISG_ERR_INTERNAL, "lane sub-table offset out of range");
+            off[t] = (int32_t)(t * sub_words + bank - low[t]);
+            bank += len[t];
+        }
+        p.stride = (int)Rs;
+        p.copy_words = (int)sep_words;
+    }
+    p.n_sub = kLaneTables;
+    p.packed = packed;
+    for (int t = 0; t < kLaneTables; ++t) p.sub_off[t] = off[t];
+    for (int l = 0; l < 32; ++l) { p.lane_sub[l] = (int8_t)chain_of[l]; p.lane_word[l] = off[chain_of[l]]; }
+
+    // every lane its own bank; every word of a sub-table its own and inside the copy
     uint32_t banks = 0;
-    for (int l = 0; l < 32; ++l) {
-        const int t = chain_of[l];
-        lane_word[l] = t * sub_words + sub_off[t];
-        banks |= 1u << ((sub_off[t] + __builtin_popcount((unsigned)l)) & 31);
-    }
-    if (bank != 32 || banks != 0xffffffffu) fail(ISG_ERR_INTERNAL, "lane tables do not give every lane its own bank");
+    for (int l = 0; l < 32; ++l) banks |= 1u << ((p.lane_word[l] + __builtin_popcount((unsigned)l)) & 31);
+    if (p.stride % 32 || (8 * (int64_t)p.stride) % G || banks != 0xffffffffu)
+        fail(ISG_ERR_INTERNAL, "lane tables do not give every lane its own bank");
+    std::vector<uint8_t> owner((size_t)p.copy_words, 0xff);
+    for (int t = 0; t < kLaneTables; ++t)
+        for (int64_t e = 0; e < rows; ++e)
+            for (int m = p.sub_m_lo[t]; m <= p.sub_m_hi[t]; ++m) {
+                const int64_t w = p.sub_off[t] + e * p.stride + m;
+                if (w < 0 || w >= p.copy_words || owner[(size_t)w] != 0xff)
+                    fail(ISG_ERR_INTERNAL, "lane sub-tables overlap or leave the copy");
+                owner[(size_t)w] = (uint8_t)t;
+            }
 }
 
 Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d, bool single_graph) {
@@ -257,12 +390,23 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d, bo
     const size_t prog_bytes = blob_words(n, (int)w.size()) * 8;
     // Lane tables (lane_model 4) make every warp reduction conflict-free; single-graph plans take
     // them by default wherever one copy (or the caller's copies) fits shared memory and the caller
-    // fixes no stride
-    const auto table_words = [&](int64_t stride) { return (int64_t)kLaneTables * (((int64_t)g.n_e_c * stride + 31) / 32 * 32 + 32); };
-    const bool lane_tables = o.lane_model == 4 ||
-                             (o.lane_model == 0 && single_graph && o.bin_stride == 0 && o.stride_residue == 0 &&
-                              !o.warp_aggregate &&
-                              prog_bytes + (size_t)std::max(1, o.copies) * table_words((n + 32) / 32 * 32) * 4 <= d.smem_optin);
+    // fixes no stride. Any layout takes at least n_e_c (10 (N - 5) + 32) words a copy: above that
+    // bound no layout is computed.
+    Plan lt;
+    bool lane_tables = false;
+    if (o.lane_model == 4 || (o.lane_model == 0 && single_graph && o.bin_stride == 0 && o.stride_residue == 0 &&
+                              !o.warp_aggregate)) {
+        const int64_t least_words = g.n_e_c * (int64_t)(10 * (n - 5) + 32);
+        if (prog_bytes + (size_t)least_words * 4 > d.smem_optin) {
+            if (o.lane_model == 4)
+                fail(ISG_ERR_TOO_LARGE, "histogram of " + std::to_string(g.n_e_c * (n + 1)) +
+                                            " bins in lane tables does not fit shared memory");
+        } else {
+            lane_table_layout(lt, n, g.n_e_c, g.G, o.lane_model == 4 ? o.bin_stride : 0);
+            lane_tables = o.lane_model == 4 ||
+                          prog_bytes + (size_t)std::max(1, o.copies) * (size_t)lt.copy_words * 4 <= d.smem_optin;
+        }
+    }
     int max_stride = n + 1;
     while (max_stride < n + 32 && prog_bytes + (size_t)g.n_e_c * (max_stride + 1) * 4 <= d.smem_optin) ++max_stride;
 
@@ -313,25 +457,32 @@ Plan make_plan(const isg_graph& g, const isg_options& o, const DeviceInfo& d, bo
     // 1024 threads by default.
     p.threads = o.block_threads > 0 ? o.block_threads : 512;
     if (lane_tables && o.block_threads == 0 && o.ctas_per_sm == 0 &&
-        2 * (prog_bytes + (size_t)table_words(o.bin_stride ? o.bin_stride : (n + 32) / 32 * 32) * 4 + 1024) > d.smem_per_sm)
+        2 * (prog_bytes + (size_t)lt.copy_words * 4 + 1024) > d.smem_per_sm)
         p.threads = 1024;
     if (p.threads % 32 || p.threads < 32 || p.threads > 1024) fail(ISG_ERR_INVALID, "block_threads must be a multiple of 32 in [32, 1024]");
     const int warps = p.threads / 32;
     // row stride: the model's pick for its lane spins, unless the caller fixes a stride or residue;
-    // lane tables take the smallest multiple of 32 (or the caller's)
-    if (lane_tables) p.stride = o.bin_stride ? o.bin_stride : (n + 1 + 31) / 32 * 32;
+    // lane tables take their layout's (the caller's, if fixed)
+    if (lane_tables) p.stride = lt.stride;
     else if (p.lane_model && o.bin_stride == 0 && o.stride_residue == 0) p.stride = lc.stride;
     else p.stride = choose_stride(g, o.bin_stride, o.stride_residue);
     if (!lane_tables && prog_bytes + (size_t)g.n_e_c * p.stride * 4 > d.smem_optin && o.bin_stride == 0) p.stride = n + 1;
     const int64_t nb = (int64_t)g.n_e_c * p.stride;
     if (lane_tables) {
-        p.n_sub = kLaneTables;
-        p.sub_words = (int)((nb + 31) / 32 * 32 + 32);          // room for a bank offset below 32
-        p.copy_words = p.n_sub * p.sub_words;
-        lane_table_layout(p.sub_words, p.sub_off, p.lane_word);
+        p.n_sub = lt.n_sub;
+        p.packed = lt.packed;
+        p.copy_words = lt.copy_words;
+        std::copy(lt.sub_off, lt.sub_off + kLaneTables, p.sub_off);
+        std::copy(lt.sub_m_lo, lt.sub_m_lo + kLaneTables, p.sub_m_lo);
+        std::copy(lt.sub_m_hi, lt.sub_m_hi + kLaneTables, p.sub_m_hi);
+        std::copy(lt.lane_word, lt.lane_word + 32, p.lane_word);
+        std::copy(lt.lane_sub, lt.lane_sub + 32, p.lane_sub);
     } else {
         p.n_sub = 1;
-        p.sub_words = p.copy_words = (int)nb;
+        p.copy_words = (int)nb;
+        p.sub_off[0] = 0;
+        p.sub_m_lo[0] = 0;
+        p.sub_m_hi[0] = n;
     }
     const size_t bin_bytes = (size_t)p.copy_words * 4;
     if (prog_bytes + bin_bytes > d.smem_optin)
@@ -460,23 +611,26 @@ std::shared_ptr<const PlannedProgram> planned_program(const isg_graph& g, const 
 // Host emulation of the kernels (same lane walk, bounds-checked counting)
 // ---------------------------------------------------------------------------------------------
 // Counts into one histogram copy; every address must be 4-byte aligned and lie among the bins of
-// the counting lane's own sub-table, [lo, hi) in bytes.
+// the counting lane's own sub-table: word first + e' stride + m with e' < rows and m in [m_lo, m_hi].
 struct HostSink {
     std::vector<uint32_t>* hist;
-    uint32_t lo, hi;
+    int64_t first, stride, rows, m_lo, m_hi;
     bool bad = false;
     void operator()(uint32_t& idx) {
-        if ((idx & 3u) || idx < lo || idx >= hi || (idx >> 2) >= hist->size()) { bad = true; return; }
+        const int64_t w = (int64_t)(idx >> 2) - first;
+        const int64_t e = w >= 0 ? w / stride : -1, m = w - e * stride;
+        if ((idx & 3u) || w < 0 || e >= rows || m < m_lo || m > m_hi || (idx >> 2) >= hist->size()) { bad = true; return; }
         (*hist)[idx >> 2] += 1;
     }
 };
 
 template <int B>
-static void emulate_tasks(const ProgView& v, const Plan& p, int64_t nb, std::vector<uint32_t>& hist, unsigned int& word) {
+static void emulate_tasks(const ProgView& v, const Plan& p, int64_t rows, std::vector<uint32_t>& hist, unsigned int& word) {
     for (uint64_t t = 0; t < p.n_tasks; ++t)
         for (int lane = 0; lane < 32; ++lane) {
             const uint32_t base = (uint32_t)p.lane_word[lane] * 4u;
-            HostSink sink{&hist, base, base + (uint32_t)(nb * 4)};
+            const int sub = p.lane_sub[lane];
+            HostSink sink{&hist, p.lane_word[lane], p.stride, rows, p.sub_m_lo[sub], p.sub_m_hi[sub]};
             uint64_t last_state;
             uint32_t last_idx;
             lane_walk<B>(v, p.prefix_base + t * 32 + lane, base, sink, last_state, last_idx);
@@ -512,27 +666,31 @@ static unsigned int emulate(const isg_graph& g, isg_options o, int plant_site, i
         }
     } else {
         switch (p.b) {
-            case 1: emulate_tasks<1>(v, p, nb, hist, word); break;
-            case 2: emulate_tasks<2>(v, p, nb, hist, word); break;
-            case 3: emulate_tasks<3>(v, p, nb, hist, word); break;
-            case 4: emulate_tasks<4>(v, p, nb, hist, word); break;
-            case 5: emulate_tasks<5>(v, p, nb, hist, word); break;
-            case 6: emulate_tasks<6>(v, p, nb, hist, word); break;
-            case 7: emulate_tasks<7>(v, p, nb, hist, word); break;
+            case 1: emulate_tasks<1>(v, p, g.n_e_c, hist, word); break;
+            case 2: emulate_tasks<2>(v, p, g.n_e_c, hist, word); break;
+            case 3: emulate_tasks<3>(v, p, g.n_e_c, hist, word); break;
+            case 4: emulate_tasks<4>(v, p, g.n_e_c, hist, word); break;
+            case 5: emulate_tasks<5>(v, p, g.n_e_c, hist, word); break;
+            case 6: emulate_tasks<6>(v, p, g.n_e_c, hist, word); break;
+            case 7: emulate_tasks<7>(v, p, g.n_e_c, hist, word); break;
             default: fail(ISG_ERR_INTERNAL, "bad low block size");
         }
     }
     if (word) return word;
     std::vector<int64_t> tab((size_t)public_bins(g), 0);
-    const int n_sub = p.small ? 1 : p.n_sub;
-    for (int t = 0; t < n_sub; ++t)                    // the flush: every sub-table's bins
+    if (p.small) {
         for (int64_t i = 0; i < nb; ++i) {
-            const uint32_t c = hist[(size_t)(p.small ? i : (int64_t)t * p.sub_words + p.sub_off[t] + i)];
-            if (!c) continue;
+            if (!hist[(size_t)i]) continue;
             const int64_t pb = public_bin(g, i, stride);
             if (pb < 0) fail(ISG_ERR_INTERNAL, "emulated walk counted a padding column");
-            tab[pb] += c;
+            tab[pb] += hist[(size_t)i];
         }
+    } else {
+        for (int t = 0; t < p.n_sub; ++t)              // the flush: each sub-table's own columns
+            for (int64_t e = 0; e < g.n_e_c; ++e)
+                for (int64_t m = p.sub_m_lo[t]; m <= p.sub_m_hi[t]; ++m)
+                    tab[public_bin(g, e * stride + m, stride)] += hist[(size_t)(p.sub_off[t] + e * stride + m)];
+    }
     if (!o.accumulate) std::memset(g_out, 0, sizeof(int64_t) * public_bins(g));
     const int64_t n_m = g.n + 1;
     for (int64_t e = 0; e <= g.S; ++e)
@@ -703,6 +861,28 @@ isg_status isg_debug_lane_banks(const isg_graph* g, const isg_options* opt, int3
         }
         *mean_wavefronts = total / samples;
         *max_wavefronts = worst;
+    });
+}
+
+isg_status isg_debug_lane_layout(const isg_graph* g, const isg_options* opt, int32_t* out) {
+    return guarded([&] {
+        if (!g || !out) fail(ISG_ERR_INVALID, "NULL argument");
+        const Plan p = make_plan(*g, resolve_options(opt), DeviceInfo{}, true);
+        if (p.small) fail(ISG_ERR_INVALID, "a thread-per-configuration plan has no histogram copies");
+        std::fill(out, out + 99, 0);
+        out[0] = p.stride;
+        out[1] = p.copy_words;
+        out[2] = p.n_sub;
+        for (int t = 0; t < p.n_sub; ++t) {
+            out[3 + t] = p.sub_off[t];
+            out[13 + t] = p.sub_m_lo[t];
+            out[23 + t] = p.sub_m_hi[t];
+        }
+        for (int l = 0; l < 32; ++l) {
+            out[33 + l] = p.lane_word[l];
+            out[65 + l] = p.lane_sub[l];
+        }
+        out[97] = p.packed;
     });
 }
 

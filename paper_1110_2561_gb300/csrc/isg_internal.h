@@ -97,21 +97,34 @@ struct Plan {
     bool lane_model = false;   // lane spins and stride chosen by the bank-conflict model
     double lane_cost = 0;      // the model's expected wavefronts per reduction (0 when not used)
     double lane_cost_index_order = 0;
-    // Histogram layout of one copy: n_sub sub-tables of sub_words words; lane l counts into the
-    // sub-table starting lane_word[l] words into the copy (sub_off[t] words past the start of
-    // sub-table t). One sub-table (the default): sub_words = copy_words = bins, offsets 0.
-    int n_sub = 1, sub_words = 0, copy_words = 0;
+    // Histogram layout of one copy (copy_words words): bin (e', m) of sub-table t is the word
+    // sub_off[t] + e' stride + m, and sub-table t holds only the columns m in
+    // [sub_m_lo[t], sub_m_hi[t]] (the words outside them may belong to another sub-table). Lane l
+    // counts into sub-table lane_sub[l], whose first word is lane_word[l] = sub_off[lane_sub[l]].
+    // One sub-table (the default): offset 0, columns [0, N], copy_words = n_e_c stride.
+    int n_sub = 1, copy_words = 0;
+    bool packed = false;       // lane tables side by side in each row (else a block each)
     int32_t sub_off[kLaneTables] = {};
+    int32_t sub_m_lo[kLaneTables] = {};
+    int32_t sub_m_hi[kLaneTables] = {};
     int32_t lane_word[32] = {};
+    int8_t lane_sub[32] = {};
 };
 
-// Lane tables (options.lane_model = 4): with the row stride a multiple of 32 words, a lane's
-// bank is its up count plus the bank offset of its sub-table. The 32 lane values are split into
+// Lane tables (options.lane_model = 4). With the row stride R a multiple of 32 words, a lane's
+// bank is its up count plus its sub-table's offset (mod 32). The 32 lane values are split into
 // the kLaneTables chains of a symmetric chain decomposition of the 5-bit cube (each chain holds
-// consecutive popcounts), and the chains' offsets make the banks of all 32 lanes distinct.
-// Fills sub_off (kLaneTables entries, each < 32) and lane_word (32 entries) for sub-tables of
-// sub_words words (a multiple of 32).
-void lane_table_layout(int sub_words, int32_t* sub_off, int32_t* lane_word);
+// consecutive popcounts), and the offsets make the banks of all 32 lanes distinct. A chain of
+// popcounts [lo, lo + len) reaches the columns m in [lo, lo + len + N - 6]. Two layouts:
+//   separate  sub-table t is a block of its own (n_e_c R + 32 words), R = `stride`;
+//   packed    the ten sub-tables share each row, side by side in an order that keeps the row
+//             short (R >= the row's span), so a copy takes about n_e_c (10 (N - 5) + 32) words.
+// lane_table_layout fills p.stride, copy_words, n_sub, sub_off, sub_m_lo, sub_m_hi, lane_word
+// and lane_sub for n spins, rows energy rows and energy stride G: with fixed_stride > 0 the
+// separate layout at that stride (INVALID unless it is a multiple of 32 with 8 R / G whole and
+// at least N + 1), else the smaller of the two at the least admissible strides. Every word of
+// every sub-table is checked to be its sub-table's alone and every lane's bank its own.
+void lane_table_layout(Plan& p, int n, int64_t rows, int64_t G, int fixed_stride);
 
 // The lane spins of a plan chosen by the bank-conflict model (lanes.cpp).
 struct LaneChoice {

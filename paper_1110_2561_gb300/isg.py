@@ -58,6 +58,7 @@ _SIGS = {
     "isg_debug_plan": (i32, [vp, vp, i32, vp]),
     "isg_debug_emulate": (i32, [vp, vp, vp]),
     "isg_debug_lane_banks": (i32, [vp, vp, i32, ctypes.c_uint64, vp, vp]),
+    "isg_debug_lane_layout": (i32, [vp, vp, vp]),
     "isg_debug_emulate_planted": (i32, [vp, vp, i32, i32, vp, ctypes.POINTER(ctypes.c_uint32)]),
     "isg_debug_server_inject": (i32, [vp, i32]),
     "isg_device_status": (i32, [vp, i32]),
@@ -645,6 +646,18 @@ def isg_debug_lane_banks(graph: Graph, samples: int = 4096, seed: int = 1, **opt
     o = _options(**options)
     _check(lib().isg_debug_lane_banks(graph, ctypes.byref(o), samples, seed, ctypes.byref(mean), ctypes.byref(worst)))
     return mean.value, worst.value
+
+
+def isg_debug_lane_layout(graph: Graph, **options) -> dict:
+    """The histogram layout of one copy under the plan (host only): row stride, words per copy,
+    sub-tables with their first words and column ranges, each lane's first word and sub-table."""
+    out = np.zeros(99, dtype=np.int32)
+    o = _options(**options)
+    _check(lib().isg_debug_lane_layout(graph, ctypes.byref(o), out.ctypes.data))
+    n = int(out[2])
+    return {"stride": int(out[0]), "copy_words": int(out[1]), "n_sub": n, "sub_off": out[3:3 + n].copy(),
+            "m_lo": out[13:13 + n].copy(), "m_hi": out[23:23 + n].copy(), "lane_word": out[33:65].copy(),
+            "lane_sub": out[65:97].copy(), "packed": bool(out[97])}
 
 
 def isg_debug_emulate(graph: Graph, **options) -> np.ndarray:

@@ -218,6 +218,56 @@ def test_lane_model_against_sampled_reductions(isg):
             assert 1 <= worst <= 32
 
 
+def check_lane_layout(isg, g, lat, **options):
+    """The lane-table layout of the plan, checked from its definition: every (sub-table, row,
+    column) word is distinct and inside the copy; lane l's columns popcount(l) + [0, N - 5] lie in
+    its sub-table's range; the 32 lanes fall in 32 banks at any column; the row stride is a
+    multiple of 32 with 8 R / G whole; the copy is no larger than ten separate padded blocks."""
+    L = isg.isg_debug_lane_layout(g, **options)
+    p = isg.isg_debug_plan(g, **options)
+    n, rows, G, R = lat.n, p["n_e_compact"], p["G"], L["stride"]
+    assert L["n_sub"] == 10 and R % 32 == 0 and (8 * R) % G == 0 and R >= n + 1
+    words = np.concatenate([off + np.arange(rows)[:, None] * R + np.arange(lo, hi + 1)[None, :]
+                            for off, lo, hi in zip(L["sub_off"], L["m_lo"], L["m_hi"])], axis=None)
+    assert words.min() >= 0 and words.max() < L["copy_words"]
+    assert len(np.unique(words)) == len(words)
+    pc = np.array([bin(l).count("1") for l in range(32)])
+    sub = L["lane_sub"]
+    assert np.array_equal(L["lane_word"], L["sub_off"][sub])
+    assert np.all(L["m_lo"][sub] <= pc) and np.all(pc + n - 5 <= L["m_hi"][sub])
+    assert len(set((L["lane_word"] + pc) % 32)) == 32
+    unit = 32
+    while (8 * unit) % G:
+        unit += 32
+    separate = 10 * (rows * ((n + 1 + unit - 1) // unit * unit) + 32)
+    assert L["copy_words"] <= separate
+    assert p["smem_bytes"] == p["blob_bytes"] + p["copies"] * L["copy_words"] * 4
+    return L
+
+
+def _ring(n, J):
+    return w.Lattice(n, np.array([(i, (i + 1) % n, J) for i in range(n)], np.int64), f"ring{n}-J{J}")
+
+
+def test_lane_table_layouts_across_sizes(isg):
+    """Lane-table layouts for N = 11 .. 62 (every residue of N - 5 mod 32, which sets the packed
+    order) and energy strides G with odd factors (J = 3 rings: G = 12 where 8 (N + 1) allows it),
+    each checked from its definition; packed wherever it takes fewer words than ten blocks."""
+    packed = 0
+    for n in range(11, 63):
+        for J in (1, 3):
+            lat = _ring(n, J)
+            g = isg.isg_graph_create(n, lat.edges)
+            packed += check_lane_layout(isg, g, lat, lane_model=4, max_spins=62)["packed"]
+    assert packed >= 90
+    for lat in (w.with_random_couplings(w.triangular(6, 6, True), w.SplitMix64(3), (-2, -1, 1, 2)),
+                w.with_random_couplings(w.cubic(3, 3, 4, True), w.SplitMix64(3), (-2, -1, 1, 2))):
+        g = isg.isg_graph_create(lat.n, lat.edges)
+        assert isg.isg_debug_plan(g)["n_e_compact"] == 163
+        assert isg.isg_debug_plan(g)["lane_tables"] == 10          # packed, they fit
+        assert check_lane_layout(isg, g, lat)["packed"]
+
+
 @pytest.mark.parametrize("lat", [w.cubic(3, 3, 4, True), w.square(6, 6, True), w.triangular(5, 6, True),
                                  w.with_random_couplings(w.square(5, 6, True), w.SplitMix64(4), (-2, -1, 1, 2)),
                                  w.random_graph(30, 90, w.SplitMix64(5))], ids=lambda l: l.name)
@@ -227,9 +277,8 @@ def test_lane_tables_make_every_reduction_conflict_free(isg, lat):
     warp reduction of the plan takes exactly one wavefront, whatever the graph and couplings."""
     g = isg.isg_graph_create(lat.n, lat.edges)
     p = isg.isg_debug_plan(g, lane_model=4)
-    assert p["lane_tables"] == 10 and p["stride"] % 32 == 0 and p["stride"] >= lat.n + 1
-    sub = ((p["n_e_compact"] * p["stride"] + 31) // 32 * 32 + 32)
-    assert p["smem_bytes"] == p["blob_bytes"] + p["copies"] * 10 * sub * 4
+    assert p["lane_tables"] == 10
+    check_lane_layout(isg, g, lat, lane_model=4)
     mean, worst = isg.isg_debug_lane_banks(g, samples=3000, seed=5, lane_model=4)
     assert mean == 1.0 and worst == 1
     for sym in (0, 1):
@@ -243,7 +292,9 @@ def test_lane_tables_emulated_against_the_oracle(isg):
     the spin flip, in a shard range, and in a forced small shape with two copies."""
     rng = w.SplitMix64(9)
     for lat in (w.square(4, 5, True), w.cubic(2, 2, 4, True), w.with_random_couplings(w.square(4, 5, True), rng, (-2, -1, 1, 2)),
-                w.triangular(4, 4, False), w.random_graph(18, 40, rng)):
+                w.triangular(4, 4, False), w.random_graph(18, 40, rng), _ring(17, 3),
+                w.with_random_couplings(w.triangular(4, 5, True), rng, (-3, 3)), w.random_graph(19, 50, rng),
+                w.with_random_couplings(w.square(3, 7, False), rng, (-2, -1, 1, 2)), w.random_graph(22, 44, rng)):
         g = isg.isg_graph_create(lat.n, lat.edges)
         ref = oracle.g_edges(lat.n, lat.edges)
         assert np.array_equal(isg.isg_debug_emulate(g, lane_model=4), ref)
@@ -254,9 +305,9 @@ def test_lane_tables_emulated_against_the_oracle(isg):
 
 
 def test_lane_tables_rejects(isg):
-    lat = w.with_random_couplings(w.square(5, 8, True), w.SplitMix64(40), (-2, -1, 1, 2))
+    lat = w.with_random_couplings(w.triangular(5, 8, True), w.SplitMix64(40), (-2, -1, 1, 2))
     g = isg.isg_graph_create(lat.n, lat.edges)
-    with pytest.raises(isg.IsgError) as ei:                    # ten padded copies of 4838 bins
+    with pytest.raises(isg.IsgError) as ei:                    # about 180 rows of 416 words
         isg.isg_debug_plan(g, lane_model=4)
     assert ei.value.status == 2
     t = w.square(6, 6, True)

@@ -286,6 +286,57 @@ def test_torus_5x8_n40_lane_tables(isg, cuda):
     isg.isg_device_status()
 
 
+def test_lane_tables_odd_energy_stride(isg, cuda):
+    """Graphs whose energy stride G has an odd factor (J = 3 rings and a J = +-3 triangular torus:
+    G = 12), where the lane tables' row stride must make 8 R / G whole: the oracle's tables, with
+    a clean self-check."""
+    cases = [w.Lattice(17, np.array([(i, (i + 1) % 17, 3) for i in range(17)], np.int64), "ring17-J3"),
+             w.Lattice(23, np.array([(i, (i + 1) % 23, 3) for i in range(23)], np.int64), "ring23-J3"),
+             w.with_random_couplings(w.triangular(4, 5, True), w.SplitMix64(9), (-3, 3))]
+    for lat in cases:
+        g = isg.isg_graph_create(lat.n, lat.edges)
+        p = isg.isg_debug_plan(g)
+        assert p["lane_tables"] == 10 and p["G"] == 12 and p["stride"] % 96 == 0, lat.name
+        assert np.array_equal(gpu_table(isg, cuda, lat), oracle.g_masks(lat.n, lat.edges, threads=THREADS)), lat.name
+        assert np.array_equal(isg.isg_enumerate(g), oracle.g_masks(lat.n, lat.edges, threads=THREADS)), lat.name
+    isg.isg_device_status()
+
+
+def test_packed_lane_tables_across_sizes(isg, cuda):
+    """Packed lane tables (the ten sub-tables side by side in each row, in an order searched per
+    residue of N - 5 mod 32) on +-1/+-2 graphs of 16 to 26 spins, one packed order each: the
+    oracle's tables."""
+    rng = w.SplitMix64(44)
+    seen = set()
+    for n in range(16, 27):
+        lat = w.random_graph(n, 2 * n, rng, couplings=(-2, -1, 1, 2))
+        g = isg.isg_graph_create(lat.n, lat.edges)
+        L = isg.isg_debug_lane_layout(g)
+        assert L["n_sub"] == 10 and L["packed"], lat.name
+        seen.add((n - 5) % 32)
+        assert np.array_equal(gpu_table(isg, cuda, lat), oracle.g_masks(lat.n, lat.edges, threads=THREADS)), lat.name
+    assert len(seen) == 11
+    isg.isg_device_status()
+
+
+@pytest.mark.parametrize("kind", ["square", "triangular"])
+def test_packed_lane_tables_n36_two_coupling_classes(isg, cuda, kind):
+    """36-spin tori with J in {-2, -1, 1, 2} (114 and 163 energy rows), whose lane tables fit
+    shared memory only packed: in the default plan, every bin against the oracle's frontier
+    programme (sites renumbered along the short side) and the invariants."""
+    from relabel import frontier_table
+    lat = w.with_random_couplings(getattr(w, kind)(6, 6, True), w.SplitMix64(3), (-2, -1, 1, 2))
+    g = isg.isg_graph_create(lat.n, lat.edges)
+    assert isg.isg_debug_plan(g)["lane_tables"] == 10 and isg.isg_debug_lane_layout(g)["packed"]
+    got = gpu_table(isg, cuda, lat)
+    assert int(got.sum()) == 2 ** 36
+    for m in range(37):
+        assert int(got[:, m].sum()) == math.comb(36, m)
+    assert np.array_equal(got, got[:, ::-1])
+    assert np.array_equal(got, frontier_table(lat, THREADS))
+    isg.isg_device_status()
+
+
 def test_autotune_torus_6x6(isg, cuda):
     """The autotuner's choice (cached per graph; the lane spins of the bank-conflict model or of the
     index order, or lane tables, whichever timed fastest) gives the same table as the oracle's frontier programme,
