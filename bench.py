@@ -47,8 +47,8 @@ OPS_PER_CONFIG = 2
 # DRAM traffic of one enumeration launch on this workload from the committed ncu capture
 # (profiles/enumerate_kernel_torus6x6.md), valid only for the kernel's device code it was taken on
 # (enum_core.cuh and enum_kernels.cuh; a changed kernel reports no traffic until re-captured).
-TRAFFIC_BYTES = 35072          # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu: 35.07 KB read, 0 written)
-TRAFFIC_SOURCES_SHA = "95c2feb90b7cdd06"
+TRAFFIC_BYTES = 34816          # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu: 34.82 KB read, 0 written)
+TRAFFIC_SOURCES_SHA = "0d5e8403033bc6bd"
 
 
 def kernel_sources_sha() -> str:
