@@ -111,6 +111,13 @@ ISG_API isg_status isg_probe_peaks(void* stream, double* red_conflict_free, doub
  */
 ISG_API isg_status isg_debug_server_inject(isg_server* server, int32_t where);
 
+/*
+ * How the request server has served its lane-table requests so far: *requests = requests
+ * submitted with lane tables (served by the single-graph enumeration kernel in task ranges),
+ * *launches = enumeration-kernel launches issued for them. Errors: ISG_ERR_INVALID.
+ */
+ISG_API isg_status isg_debug_server_lane_counts(isg_server* server, int64_t* requests, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

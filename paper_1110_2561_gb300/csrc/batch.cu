@@ -275,6 +275,12 @@ void launch_batch(const BatchPlan& bp, const BatchInst* d_inst, const uint64_t* 
     }
 }
 
+void launch_mirror(const BatchInst* d_inst, const int* d_ids, int n, const uint64_t* d_blobs, cudaStream_t s) {
+    if (n <= 0) return;
+    batch_mirror_kernel<<<n, 256, 0, s>>>(d_inst, d_ids, d_blobs);
+    ISG_CUDA(cudaGetLastError());
+}
+
 }  // namespace isg
 
 using namespace isg;

@@ -37,4 +37,8 @@ struct BatchPlan {
 void launch_batch(const BatchPlan& bp, const BatchInst* d_inst, const uint64_t* d_blobs, const int* d_small,
                   unsigned long long* counter, unsigned int* status, cudaStream_t s, int ctas_per_sm);
 
+// The symmetry mirror alone (one CTA per instance): descriptors d_inst[d_ids[0 .. n)] hold the
+// halves with spin N-1 up, completed in place.
+void launch_mirror(const BatchInst* d_inst, const int* d_ids, int n, const uint64_t* d_blobs, cudaStream_t s);
+
 }  // namespace isg

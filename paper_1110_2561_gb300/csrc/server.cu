@@ -8,7 +8,10 @@
 // arena are free; its int64 table stays on the device, accumulating over the steps that carry
 // its tiles, and is copied out (to a pinned mirror, then to the result buffer) by the step that
 // carries its last tile. Two steps can be in flight, so planning the next step overlaps the
-// current one. The paper distributes the outer loops of one lattice over processes with uniform
+// current one. Requests of at least 36 spins whose lane tables fit one CTA's shared memory are
+// the exception: a step gives each of them (up to kMaxLaneLaunches) one launch of the
+// single-graph enumeration kernel over a range of its tasks, whose warp reductions are
+// conflict-free, where the batch kernel's per-warp histograms are bound by bank conflicts. The paper distributes the outer loops of one lattice over processes with uniform
 // shares (Sec. 3d); this is the same decomposition applied to a stream of lattices.
 #include <cuda_runtime.h>
 
@@ -34,11 +37,17 @@
 namespace isg {
 
 DeviceInfo device_info();
+void launch_enumeration(const Plan& p, const uint64_t* d_blob, int blob_words, int64_t* table,
+                        unsigned long long* counter, unsigned int* status, cudaStream_t s,
+                        const uint64_t* host_blob);
 
 constexpr int kSplitMinSpins = 24;     // below this the tile path takes microseconds anyway
 // requests given the quick lane search (lane_model option): their enumeration takes tens of
 // milliseconds, against a few milliseconds of search
 constexpr int kServerLaneModelMinSpins = 36;
+// enumeration-kernel launches per step for requests with lane tables (task counters in the step's
+// counter block: words 2 .. 2 + kMaxLaneLaunches)
+constexpr int kMaxLaneLaunches = 8;
 
 using Clock = std::chrono::steady_clock;
 
@@ -56,6 +65,7 @@ struct Request {
     int bins = 0;                    // compact histogram bins (stride included)
     std::vector<uint64_t> blob;      // tile program, or the split program when `split` is set
     std::shared_ptr<const SplitPrepared> split;   // served by split-and-convolve (one launch)
+    std::shared_ptr<const Plan> lane;   // lane-table plan: served by the enumeration kernel, task ranges per step
     size_t table_words = 0;          // public table
     uint64_t total_tasks = 0, next_task = 0;
     uint64_t prefix_base = 0;        // lane prefix of task 0 (the upper half of the space with symmetry)
@@ -149,6 +159,7 @@ struct isg_server {
     double rate_est = 5e12;                            // configurations per second, running estimate
     int64_t steps_done = 0;
     double configs_done = 0, device_ms = 0;
+    int64_t lane_requests = 0, lane_launches = 0;      // isg_debug_server_lane_counts
     Clock::time_point t_create;
 };
 
@@ -223,11 +234,14 @@ static bool issue_step_locked(isg_server* s) {
     int max_words = 0, max_bins = 0;
     uint64_t tiles = 0;
     double used = 0;
-    std::vector<BatchInst> large, small;
-    std::vector<Request*> large_r, small_r, split_r;
+    std::vector<BatchInst> large, small, lane_mirror;
+    std::vector<Request*> large_r, small_r, split_r, lane_r;
+    std::vector<uint64_t> lane_lo, lane_n;             // task range of each lane-table launch
     std::vector<int> mirror;                           // descriptors of halved requests finishing here
+    // a lane-table launch takes at least one full wave of warps (or the request's rest)
+    const uint64_t lane_min_tasks = (uint64_t)std::max(1, s->dinfo.sms) * 32;
     for (Request* r : order) {
-        if (used >= budget && (!large.empty() || !split_r.empty())) break;
+        if (used >= budget && (!large.empty() || !split_r.empty() || !lane_r.empty())) break;
         BatchInst in{};
         in.g = reinterpret_cast<int64_t*>(s->arena_dev + r->slot_off);
         const size_t tbytes = ((r->table_words * 8) + 255) & ~(size_t)255;
@@ -237,6 +251,17 @@ static bool issue_step_locked(isg_server* s) {
             split_r.push_back(r);
             used += r->configs;
             r->next_task = r->total_tasks;
+        } else if (r->lane) {                          // a task range in one enumeration launch
+            if ((int)lane_r.size() >= kMaxLaneLaunches) continue;
+            const double per_tile = 32.0 * (double)(1ull << r->q);
+            uint64_t take = (uint64_t)std::max(1.0, (budget - used) / per_tile);
+            take = std::min<uint64_t>(std::max(take, lane_min_tasks), r->total_tasks - r->next_task);
+            lane_r.push_back(r);
+            lane_lo.push_back(r->next_task);
+            lane_n.push_back(take);
+            r->next_task += take;
+            if (r->sym && r->next_task == r->total_tasks) lane_mirror.push_back(in);
+            used += per_tile * (double)take;
         } else if (!r->b) {                            // whole request in the small kernel
             small.push_back(in);
             small_r.push_back(r);
@@ -271,6 +296,9 @@ static bool issue_step_locked(isg_server* s) {
     }
     bp.inst = desc;
     bp.n_tiles = tiles;
+    // descriptors of the halved lane-table requests finishing here, for their mirror (not the batch's)
+    const size_t lane_mirror_first = desc.size();
+    desc.insert(desc.end(), lane_mirror.begin(), lane_mirror.end());
     bp.mirror_ids = mirror;                            // large descriptors come first: same indices
     bp.prog_words = (max_words + 1) & ~1;
     bp.slot_words = (bp.prog_words + (max_bins + 1) / 2 + 1) & ~1;   // even: slots stay 16-byte aligned
@@ -287,6 +315,7 @@ static bool issue_step_locked(isg_server* s) {
     // the kernels read the small kernel's ids, then the mirror's (at most one id per request)
     std::vector<int> ids(bp.small_ids);
     ids.insert(ids.end(), bp.mirror_ids.begin(), bp.mirror_ids.end());
+    for (size_t k = 0; k < lane_mirror.size(); ++k) ids.push_back((int)(lane_mirror_first + k));
     if (!ids.empty()) std::memcpy(s->small_host[buf], ids.data(), sizeof(int) * ids.size());
     if (s->inject == 1) {
         s->inject = 0;
@@ -306,7 +335,7 @@ static bool issue_step_locked(isg_server* s) {
     if (!ids.empty())
         server_fail_cuda(cudaMemcpyAsync(s->small_dev[buf], s->small_host[buf], sizeof(int) * ids.size(),
                                          cudaMemcpyHostToDevice, s->stream), "cudaMemcpyAsync(small ids)");
-    server_fail_cuda(cudaMemsetAsync(s->ctr_dev[buf], 0, 16, s->stream), "cudaMemsetAsync(counter)");
+    server_fail_cuda(cudaMemsetAsync(s->ctr_dev[buf], 0, 8 * (2 + kMaxLaneLaunches), s->stream), "cudaMemsetAsync(counters)");
     unsigned int* status = reinterpret_cast<unsigned int*>(s->ctr_dev[buf] + 1);
     for (Request* r : split_r) {                       // split requests first: each one launch, table in its slot
         const size_t tbytes = ((r->table_words * 8) + 255) & ~(size_t)255;
@@ -316,6 +345,20 @@ static bool issue_step_locked(isg_server* s) {
     if (!large.empty() || !small.empty())
         launch_batch(bp, s->desc_dev[buf], reinterpret_cast<const uint64_t*>(s->arena_dev), s->small_dev[buf], s->ctr_dev[buf],
                      status, s->stream, s->opt.ctas_per_sm > 0 ? s->opt.ctas_per_sm : 2);
+    s->lane_launches += (int64_t)lane_r.size();
+    for (size_t k = 0; k < lane_r.size(); ++k) {       // lane-table requests: their task ranges
+        Request* r = lane_r[k];
+        Plan lp = *r->lane;
+        lp.prefix_base = r->prefix_base + lane_lo[k] * 32;
+        lp.n_tasks = lane_n[k];
+        const size_t tbytes = ((r->table_words * 8) + 255) & ~(size_t)255;
+        launch_enumeration(lp, reinterpret_cast<const uint64_t*>(s->arena_dev + r->slot_off + tbytes), (int)r->blob.size(),
+                           reinterpret_cast<int64_t*>(s->arena_dev + r->slot_off), s->ctr_dev[buf] + 2 + k, status,
+                           s->stream, nullptr);
+    }
+    if (!lane_mirror.empty())
+        launch_mirror(s->desc_dev[buf], s->small_dev[buf] + bp.small_ids.size() + bp.mirror_ids.size(),
+                      (int)lane_mirror.size(), reinterpret_cast<const uint64_t*>(s->arena_dev), s->stream);
     if (s->inject == 2) {
         s->inject = 0;
         fail(ISG_ERR_CUDA, "injected host-side failure after the step's launch");
@@ -334,6 +377,7 @@ static bool issue_step_locked(isg_server* s) {
         }
     };
     for (Request* r : large_r) carried(r);
+    for (Request* r : lane_r) carried(r);
     for (Request* r : small_r) carried(r);
     for (Request* r : split_r) carried(r);
     server_fail_cuda(cudaEventRecord(s->ev_done[buf], s->stream), "cudaEventRecord");
@@ -617,8 +661,20 @@ isg_status isg_server_submit(isg_server* s, const isg_graph* g, int64_t* ticket)
                 o.shard_hi = 2;
             }
             o.inner_bits = std::min(16, g->n - 5 - (r->sym ? 1 : 0));
-            if (s->opt.lane_model && g->n >= kServerLaneModelMinSpins) o.lane_model = 3;
-            p = make_plan(*g, o, d);
+            if (s->opt.lane_model && g->n >= kServerLaneModelMinSpins) {
+                // lane tables where one copy fits a CTA (the enumeration kernel serves the
+                // request), else the quick lane search for the batch kernel's tiles
+                isg_options lo = o;
+                lo.lane_model = 4;
+                try {
+                    Plan lp = make_plan(*g, lo, d, true);
+                    if (!lp.small && lp.n_sub == kLaneTables) r->lane = std::make_shared<const Plan>(std::move(lp));
+                } catch (const Error&) {
+                    // too many energy rows for lane tables
+                }
+                if (!r->lane) o.lane_model = 3;
+            }
+            p = r->lane ? *r->lane : make_plan(*g, o, d);
             if (p.small || p.q < p.b) fail(ISG_ERR_INTERNAL, "unexpected plan for a served graph");
             r->b = p.b;
             r->q = p.q;
@@ -645,6 +701,7 @@ isg_status isg_server_submit(isg_server* s, const isg_graph* g, int64_t* ticket)
         if (s->stop) fail(ISG_ERR_INVALID, "server is shutting down");
         if ((int64_t)s->queue.size() >= s->opt.max_queued) fail(ISG_ERR_BUSY, "server queue is full");
         r->ticket = s->next_ticket++;
+        if (r->lane) ++s->lane_requests;
         *ticket = r->ticket;
         s->queue.push_back(r->ticket);
         s->reqs.emplace(r->ticket, std::move(r));
@@ -751,6 +808,15 @@ isg_status isg_server_stats(isg_server* s, double* stats) {
 }
 
 void isg_server_destroy(isg_server* s) { destroy_server(s); }
+
+isg_status isg_debug_server_lane_counts(isg_server* s, int64_t* requests, int64_t* launches) {
+    return guarded([&] {
+        if (!s || !requests || !launches) fail(ISG_ERR_INVALID, "NULL argument");
+        std::lock_guard<std::mutex> lk(s->mu);
+        *requests = s->lane_requests;
+        *launches = s->lane_launches;
+    });
+}
 
 isg_status isg_debug_server_inject(isg_server* s, int32_t where) {
     return guarded([&] {

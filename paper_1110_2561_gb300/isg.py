@@ -61,6 +61,7 @@ _SIGS = {
     "isg_debug_lane_layout": (i32, [vp, vp, vp]),
     "isg_debug_emulate_planted": (i32, [vp, vp, i32, i32, vp, ctypes.POINTER(ctypes.c_uint32)]),
     "isg_debug_server_inject": (i32, [vp, i32]),
+    "isg_debug_server_lane_counts": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
     "isg_device_status": (i32, [vp, i32]),
     "isg_rank_shards": (i32, [i32, i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
     "isg_enumerate_rank": (i32, [vp, vp, vp, i32, i32, i32, vp]),
@@ -482,6 +483,12 @@ class Server:
         """isg_debug_server_inject: make the next engine step fail on the host (1: before its first
         enqueue, 2: after its launch; 0: cancel)."""
         _check(lib().isg_debug_server_inject(self.ptr, where))
+
+    def lane_counts(self) -> dict:
+        """isg_debug_server_lane_counts: requests given lane tables, and enumeration launches for them."""
+        req, lau = i64(), i64()
+        _check(lib().isg_debug_server_lane_counts(self.ptr, ctypes.byref(req), ctypes.byref(lau)))
+        return {"requests": req.value, "launches": lau.value}
 
     def stats(self) -> dict:
         v = (ctypes.c_double * 8)()

@@ -132,6 +132,34 @@ def test_largest_requests_against_frontier_oracle(isg, cuda, opts):
         g, _ = srv.result(t)
         assert int(r.sum()) == 1 << l.n
         assert np.array_equal(g, r), l.name
+    # lane tables fit one CTA for all but the two triangular 38-spin requests (about 180 rows)
+    lc = srv.lane_counts()
+    assert lc["requests"] == (0 if opts.get("lane_model") == 0 else 10)
+    assert lc["launches"] >= lc["requests"]
+    srv.close()
+
+
+@pytest.mark.parametrize("sym", [0, 1], ids=["every-configuration", "symmetry"])
+def test_lane_table_requests_across_steps(isg, cuda, sym):
+    """36-spin tori with J in {-2,-1,1,2} (lane tables fit one CTA only packed), served by the
+    enumeration kernel in task ranges over many 1 ms steps, next to small requests that go to the
+    batch kernel in the same steps, with or without the spin-flip halving: every table equals the
+    oracle's (the frontier programme for the tori)."""
+    rng = w.SplitMix64(36)
+    big = [w.with_random_couplings(getattr(w, k)(6, 6, True), w.SplitMix64(3), (-2, -1, 1, 2))
+           for k in ("square", "triangular")] + [w.with_random_couplings(w.cubic(3, 3, 4, True), w.SplitMix64(3), (-2, -1, 1, 2))]
+    small = [w.induced_lattice(k, n, per, rng) for n in (16, 20) for k in ("square", "triangular") for per in (True, False)]
+    lats = [x for pair in zip(big, small) for x in pair] + small[len(big):]
+    srv = isg.Server(step_ms=1.0, symmetry=sym)
+    tickets = [srv.submit(isg.isg_graph_create(l.n, l.edges)) for l in lats]
+    refs = [reference(l) for l in lats]
+    for t, l, r in zip(tickets, lats, refs):
+        srv.wait(t, 120000)
+        g, _ = srv.result(t)
+        assert np.array_equal(g, r), l.name
+    lc = srv.lane_counts()
+    assert lc["requests"] == 3
+    assert lc["launches"] >= 6                 # each torus over more than one step
     srv.close()
 
 
