@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -516,13 +517,16 @@ __global__ void __launch_bounds__(32 * kH0Warps) thermo_h0_kernel(const __grid_c
     const ThermoArgs& a = P.a;
     const double* Tv = a.T ? a.T : P.grid;
     extern __shared__ __align__(16) unsigned char sm[];
-    double* lnG0 = reinterpret_cast<double*>(sm);
-    double* mu = lnG0 + a.n_e;
+    double* G0v = reinterpret_cast<double*>(sm);      // configurations at energy e (as double)
+    double* mu = G0v + a.n_e;
     double* vr = mu + a.n_e;
     double* ab = vr + a.n_e;
     double* q2 = ab + a.n_e;
     double* q4 = q2 + a.n_e;
     const int N = a.n, n_m = a.n_m;
+    __shared__ int s_egs;                              // lowest energy bin with a configuration
+    if (threadIdx.x == 0) s_egs = INT_MAX;
+    __syncthreads();
     for (int e = threadIdx.x; e < a.n_e; e += blockDim.x) {
         // exact integer moments of the row (128-bit: c < 2^63, |M|^4 <= 2^24, at most 65 columns),
         // on the integer pipe; the variance about the integer Mp nearest the mean, also exact
@@ -541,15 +545,16 @@ __global__ void __launch_bounds__(32 * kH0Warps) thermo_h0_kernel(const __grid_c
             S1 += M < 0 ? -(__int128)((unsigned __int128)c * aM) : (__int128)((unsigned __int128)c * aM);
         }
         if (G0 == 0) {
-            lnG0[e] = -INFINITY;
+            G0v[e] = 0;
             mu[e] = vr[e] = ab[e] = q2[e] = q4[e] = 0;
             continue;
         }
+        atomicMin(&s_egs, e);
         const double G0d = u128_to_double(G0), inv = 1.0 / G0d, mean = i128_to_double(S1) * inv;
         const int64_t Mp = llrint(mean);
         const __int128 Q = (__int128)S2 - 2 * (__int128)Mp * S1 + (__int128)(Mp * Mp) * (__int128)G0;   // sum c (M - Mp)^2
         const double dm = mean - (double)Mp;                                                            // |dm| <= 1/2
-        lnG0[e] = log(G0d);
+        G0v[e] = G0d;
         mu[e] = mean;
         vr[e] = fmax(0.0, i128_to_double(Q) * inv - dm * dm);
         ab[e] = u128_to_double(SA) * inv;
@@ -559,13 +564,13 @@ __global__ void __launch_bounds__(32 * kH0Warps) thermo_h0_kernel(const __grid_c
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     constexpr int kCache = 8;                          // weights kept in registers for the second pass
+    const int egs = s_egs;
     for (int it = blockIdx.x * nw + warp; it < a.nT; it += gridDim.x * nw) {
+        // weights relative to the lowest occupied energy E0: w(E) = g0(E) exp(-(E - E0)/T), at
+        // most 1 per configuration, so Z exp(E0/T) = sum w <= 2^64 and ln Z = -E0/T + ln sum w
         const double invT = 1.0 / Tv[it];
-        double xmax = -INFINITY;
-        for (int e = lane; e < a.n_e; e += 32)
-            if (lnG0[e] != -INFINITY) xmax = fmax(xmax, lnG0[e] - (double)(a.e_min + 2 * e) * invT);
-        xmax = warp_max(xmax);
-        auto weight = [&](int e) { return lnG0[e] == -INFINITY ? 0.0 : exp(lnG0[e] - (double)(a.e_min + 2 * e) * invT - xmax); };
+        const double xmax = -(double)(a.e_min + 2 * egs) * invT;
+        auto weight = [&](int e) { return G0v[e] == 0.0 ? 0.0 : G0v[e] * exp(-2.0 * (double)(e - egs) * invT); };
         double wc[kCache];
         double z = 0, sE = 0, sM = 0;
 #pragma unroll
