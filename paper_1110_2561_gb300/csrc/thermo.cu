@@ -495,10 +495,11 @@ __global__ void __launch_bounds__(1024) thermo_kernel(const __grid_constant__ Th
 }
 
 // Fields all zero: the sum over M of Eq. (2) is the same at every temperature, so it is taken once
-// per energy. The CTA first forms, for every energy bin e, ln G0(e) with G0(e) = sum_M g(e, M), and
-// the mean, variance, <|M|>, <M^2> and <M^4> of M within that bin, from exact integer sums (a
+// per energy. The CTA first forms, for every energy bin e, G0(e) = sum_M g(e, M) and the lowest
+// occupied bin, and the mean, variance, <|M|>, <M^2> and <M^4> of M within that bin, from exact integer sums (a
 // flip-symmetric row has a mean of exactly zero). One warp per temperature then weighs
-// the bins by w_e = G0(e) exp(-E_e/T), relative to the largest: ln Z = max + ln sum w, <H> = <E>,
+// the bins by w_e = G0(e) exp(-(E_e - E_0)/T), E_0 the lowest occupied energy (so w_e <= G0(e)
+// and sum w <= 2^64): ln Z = -E_0/T + ln sum w, <H> = <E>,
 // C = Var(E)/T^2 (two passes), <M> = sum w mu_e / sum w, chi = sum w (var_e + (mu_e - <M>)^2) /
 // (T sum w), and the magnetisation moments from the bins' moments. Everything in double; one
 // exponential per (temperature, energy) instead of one per (temperature, energy, M).
