@@ -113,12 +113,17 @@ typedef struct {
                                 by a fixed preference. 3 = the model with a quick search (dense greedy
                                 sets only, fewer draws: milliseconds instead of a tenth of a second).
                                 4 = lane tables: the index order's lane spins, every histogram copy
-                                split into ten sub-tables with a row stride that is a multiple of
-                                32, so that each lane's shared-memory bank is fixed by its up count
-                                and its sub-table; no warp reduction has a bank conflict, on any
-                                graph. A copy takes ten times the padded histogram; TOO_LARGE if one
-                                does not fit shared memory. Single-graph calls only: batches (one
-                                histogram per warp) refuse 4 with INVALID. */
+                                split into ten sub-tables with a row stride R that is a multiple of
+                                32 (and makes 8 R / G whole, G the graph's energy stride), so that
+                                each lane's shared-memory bank is fixed by its up count and its
+                                sub-table; no warp reduction has a bank conflict, on any graph. Each
+                                sub-table holds only the columns its lanes reach, and the ten share
+                                each row side by side where that is smaller than ten padded blocks:
+                                about n_e (10 (N - 5) + 32) words a copy. A bin_stride set by the
+                                caller selects the blocks at that stride (INVALID unless it meets
+                                the rules above). One copy per CTA unless copies is set; TOO_LARGE if
+                                one does not fit shared memory. Single-graph calls only: batches
+                                (one histogram per warp) refuse 4 with INVALID. */
 } isg_options;
 
 /* Fill *opt with the defaults (all planner choices, full range, overwrite). */
