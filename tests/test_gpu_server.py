@@ -212,13 +212,19 @@ def test_limits_cancel_timeout(isg, cuda):
     srv.close()
 
 
+@pytest.mark.parametrize("lane", [0, 1], ids=["tiles", "lane-tables"])
 @pytest.mark.parametrize("where", [1, 2], ids=["before-enqueue", "after-launch"])
-def test_host_side_step_failure_releases_slots(isg, cuda, where):
+def test_host_side_step_failure_releases_slots(isg, cuda, where, lane):
     """A host-side failure of an engine step (injected on the host with isg_debug_server_inject; no
     GPU fault): the admitted requests with tiles left fail with ISG_ERR_CUDA, every other request
     finishes with its exact table, every arena slot comes back once no step in flight writes into
-    it (no admitted request, no open ticket), and the server keeps serving."""
-    lats = [w.with_random_couplings(w.square(5, 7, True), w.SplitMix64(60 + k), (-1, 1)) for k in range(6)]
+    it (no admitted request, no open ticket), and the server keeps serving. With 35-spin requests
+    the steps carry batch-kernel tiles; with 36-spin ones, task ranges of the enumeration kernel
+    (lane tables), several steps each."""
+    if lane:
+        lats = [w.with_random_couplings(w.square(6, 6, True), w.SplitMix64(60 + k), (-1, 1)) for k in range(4)]
+    else:
+        lats = [w.with_random_couplings(w.square(5, 7, True), w.SplitMix64(60 + k), (-1, 1)) for k in range(6)]
     srv = isg.Server(max_inflight=2, arena_bytes=1 << 20, step_ms=0.5)
     tickets = [(srv.submit(isg.isg_graph_create(l.n, l.edges)), l) for l in lats]
     srv.inject_failure(where)
@@ -233,6 +239,7 @@ def test_host_side_step_failure_releases_slots(isg, cuda, where):
             continue
         assert np.array_equal(g, alone(isg, lat)), lat.name
     assert failed >= 1
+    assert srv.lane_counts()["requests"] == (len(lats) if lane else 0)
     t0 = time.time()
     while (srv.stats()["admitted"] or srv.stats()["tickets"]) and time.time() - t0 < 10:
         time.sleep(0.01)
