@@ -418,15 +418,15 @@ typedef struct {
                                 mirror M -> -M before it is copied out (the global spin flip maps
                                 (E, M) to (E, -M) for any couplings): half the work, the same table.
                                 0 (default): all 2^N configurations. */
-    int32_t lane_model;      /* 1 (default): a tile-served request of at least 36 spins gets lane
+    int32_t lane_model;      /* 1 (default): a tile-served request of at least 28 spins gets lane
                                 tables (options.lane_model = 4) where one copy fits a CTA's shared
                                 memory, and each step then serves a range of its tasks by a launch of
                                 the single-graph enumeration kernel (conflict-free warp reductions;
-                                at most 8 such launches a step); otherwise it gets the lane spins and
-                                row stride of a quick search under the bank-conflict model
-                                (options.lane_model = 3: a few milliseconds of host time at submit)
-                                for the batch kernel's tiles. 0: the index order in the batch
-                                kernel. The table is the same either way. */
+                                at most 16 such launches a step); otherwise a request of at least 36
+                                spins gets the lane spins and row stride of a quick search under the
+                                bank-conflict model (options.lane_model = 3: a few milliseconds of
+                                host time at submit) for the batch kernel's tiles. 0: the index order
+                                in the batch kernel. The table is the same either way. */
 } isg_server_options;
 
 ISG_API void isg_server_options_init(isg_server_options* opt);

@@ -8,7 +8,7 @@
 // arena are free; its int64 table stays on the device, accumulating over the steps that carry
 // its tiles, and is copied out (to a pinned mirror, then to the result buffer) by the step that
 // carries its last tile. Two steps can be in flight, so planning the next step overlaps the
-// current one. Requests of at least 36 spins whose lane tables fit one CTA's shared memory are
+// current one. Requests of at least 28 spins whose lane tables fit one CTA's shared memory are
 // the exception: a step gives each of them (up to kMaxLaneLaunches) one launch of the
 // single-graph enumeration kernel over a range of its tasks, whose warp reductions are
 // conflict-free, where the batch kernel's per-warp histograms are bound by bank conflicts. The paper distributes the outer loops of one lattice over processes with uniform
@@ -45,9 +45,12 @@ constexpr int kSplitMinSpins = 24;     // below this the tile path takes microse
 // requests given the quick lane search (lane_model option): their enumeration takes tens of
 // milliseconds, against a few milliseconds of search
 constexpr int kServerLaneModelMinSpins = 36;
+// requests served with lane tables by the enumeration kernel: from this size on a request has
+// enough warp tasks (at least 2^13, with inner bits min(16, N - 18)) to fill the GPU
+constexpr int kServerLaneTableMinSpins = 28;
 // enumeration-kernel launches per step for requests with lane tables (task counters in the step's
-// counter block: words 2 .. 2 + kMaxLaneLaunches)
-constexpr int kMaxLaneLaunches = 8;
+// counter block: words 2 .. 2 + kMaxLaneLaunches, inside its 256 bytes)
+constexpr int kMaxLaneLaunches = 16;
 
 using Clock = std::chrono::steady_clock;
 
@@ -661,18 +664,20 @@ isg_status isg_server_submit(isg_server* s, const isg_graph* g, int64_t* ticket)
                 o.shard_hi = 2;
             }
             o.inner_bits = std::min(16, g->n - 5 - (r->sym ? 1 : 0));
-            if (s->opt.lane_model && g->n >= kServerLaneModelMinSpins) {
+            if (s->opt.lane_model && g->n >= kServerLaneTableMinSpins) {
                 // lane tables where one copy fits a CTA (the enumeration kernel serves the
-                // request), else the quick lane search for the batch kernel's tiles
+                // request), else, from kServerLaneModelMinSpins, the quick lane search for the
+                // batch kernel's tiles
                 isg_options lo = o;
                 lo.lane_model = 4;
+                lo.inner_bits = std::min(16, g->n - 18 - (r->sym ? 1 : 0));
                 try {
                     Plan lp = make_plan(*g, lo, d, true);
                     if (!lp.small && lp.n_sub == kLaneTables) r->lane = std::make_shared<const Plan>(std::move(lp));
                 } catch (const Error&) {
                     // too many energy rows for lane tables
                 }
-                if (!r->lane) o.lane_model = 3;
+                if (!r->lane && g->n >= kServerLaneModelMinSpins) o.lane_model = 3;
             }
             p = r->lane ? *r->lane : make_plan(*g, o, d);
             if (p.small || p.q < p.b) fail(ISG_ERR_INTERNAL, "unexpected plan for a served graph");

@@ -218,14 +218,14 @@ def test_host_side_step_failure_releases_slots(isg, cuda, where, lane):
     """A host-side failure of an engine step (injected on the host with isg_debug_server_inject; no
     GPU fault): the admitted requests with tiles left fail with ISG_ERR_CUDA, every other request
     finishes with its exact table, every arena slot comes back once no step in flight writes into
-    it (no admitted request, no open ticket), and the server keeps serving. With 35-spin requests
-    the steps carry batch-kernel tiles; with 36-spin ones, task ranges of the enumeration kernel
-    (lane tables), several steps each."""
+    it (no admitted request, no open ticket), and the server keeps serving. With lane_model = 0
+    the steps carry batch-kernel tiles of 35-spin requests; with the default, task ranges of the
+    enumeration kernel (lane tables) of 36-spin ones, several steps each."""
     if lane:
         lats = [w.with_random_couplings(w.square(6, 6, True), w.SplitMix64(60 + k), (-1, 1)) for k in range(4)]
     else:
         lats = [w.with_random_couplings(w.square(5, 7, True), w.SplitMix64(60 + k), (-1, 1)) for k in range(6)]
-    srv = isg.Server(max_inflight=2, arena_bytes=1 << 20, step_ms=0.5)
+    srv = isg.Server(max_inflight=2, arena_bytes=1 << 20, step_ms=0.5, lane_model=lane)
     tickets = [(srv.submit(isg.isg_graph_create(l.n, l.edges)), l) for l in lats]
     srv.inject_failure(where)
     failed = 0
