@@ -270,7 +270,7 @@ void lane_table_layout(Plan& p, int n, int64_t rows, int64_t G, int fixed_stride
     const int64_t Rs = fixed_stride > 0 ? fixed_stride : round_up(n + 1);
     const int64_t sub_words = rows * Rs + 32;
     const int64_t sep_words = kLaneTables * sub_words;
-    // packed: the searched order, rotated so that the first chain's first word is word 0
+    // packed: the searched order, its banks rotated so that the first chain's sub-table starts at word 0
     const PackedOrder& po = packed_order(rest % 32);
     int64_t A[kLaneTables];
     int slot_chain[kLaneTables];
