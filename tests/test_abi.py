@@ -304,6 +304,35 @@ def test_lane_tables_emulated_against_the_oracle(isg):
         assert np.array_equal(isg.isg_debug_emulate(g, lane_model=4, shard_bits=2, shard_lo=1, shard_hi=3), part)
 
 
+def test_packed_lane_tables_emulated_on_shards_of_large_graphs(isg):
+    """Lane tables of 27 to 40 spins (fourteen residues of N - 5 mod 32: twelve packed orders, and
+    the padded blocks at 30 and 31 spins, where they are smaller) on graphs with J in
+    {-2, -1, 1, 2} or {-1, 1}: the kernel's walk on the host over one shard of 2^18
+    configurations (every address checked against its lane's own sub-table columns) equals the
+    oracle's table of the same range. A draw whose energy rows fit no lane-table layout would be
+    refused with TOO_LARGE; at least twelve sizes run."""
+    rng = w.SplitMix64(2740)
+    done = 0
+    for n in range(27, 41):
+        kind = ("square", "triangular", "cubic")[n % 3]
+        J = (-2, -1, 1, 2) if n % 2 else (-1, 1)
+        lat = w.induced_lattice(kind, n, bool(n % 4 < 2), rng, couplings=J)
+        g = isg.isg_graph_create(lat.n, lat.edges)
+        k = n - 18
+        lo = rng.below(1 << k)
+        opts = dict(lane_model=4, shard_bits=k, shard_lo=lo, shard_hi=lo + 1)
+        try:
+            L = isg.isg_debug_lane_layout(g, **opts)
+        except isg.IsgError as e:                  # too many energy rows for any lane-table layout
+            assert e.status == 2, (lat.name, str(e))
+            continue
+        assert L["n_sub"] == 10 and L["packed"] == (n not in (30, 31)), lat.name   # blocks are smaller at 30, 31
+        got = isg.isg_debug_emulate(g, **opts)
+        assert np.array_equal(got, oracle.g_masks(n, lat.edges, lo << 18, (lo + 1) << 18)), lat.name
+        done += 1
+    assert done >= 12
+
+
 def test_lane_tables_rejects(isg):
     lat = w.with_random_couplings(w.triangular(5, 8, True), w.SplitMix64(40), (-2, -1, 1, 2))
     g = isg.isg_graph_create(lat.n, lat.edges)
