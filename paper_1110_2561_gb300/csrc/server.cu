@@ -51,6 +51,7 @@ constexpr int kServerLaneTableMinSpins = 28;
 // enumeration-kernel launches per step for requests with lane tables (task counters in the step's
 // counter block: words 2 .. 2 + kMaxLaneLaunches, inside its 256 bytes)
 constexpr int kMaxLaneLaunches = 16;
+static_assert(8 * (2 + kMaxLaneLaunches) <= 256, "lane-launch counters must fit the step's 256-byte counter block");
 
 using Clock = std::chrono::steady_clock;
 
